@@ -1,0 +1,1135 @@
+/*
+ * fw_oracle.c -- plain FP64 CPU oracle of the SDF contact substep (Factory, Sec. III).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the benchmark's
+ * CPU-baseline leg, never by the product path.  Written for a reader checking it
+ * against the paper: brute-force loops, FP64, steps in the paper's order.
+ *
+ * Readings of places where the paper is silent (each one a config field or a stated
+ * constant, listed again in the project's design notes):
+ *   R1 sign: phi < 0 inside the solid (Sec. III-A says only that the sign tells inside
+ *      from outside).
+ *   R2 grid: node-centred, dims^3 nodes spanning the padded bounding box (cubic).
+ *   R3 gradient: the analytic gradient of the trilinear interpolant, i.e. the finite
+ *      difference of neighbouring nodes weighted bilinearly in the other two axes
+ *      ("gradients via finite-differencing", Sec. III-A).
+ *   R4 a point outside the grid box, or with |grad| < 1e-12, makes no candidate.
+ *   R5 candidate iff phi < contact_offset; the contact normal is the world-frame
+ *      normalised SDF gradient of body B; the point on B is x_A - phi n.
+ *   R6 Algorithm 1: batches of batch_size samples in sample order; Assign joins the
+ *      existing patch of largest n.n_P if that is >= cos_patch (ties: lowest patch);
+ *      FindDeepest = min phi (ties: lowest sample); BinReduce joins remaining
+ *      candidates with n.n_best >= cos_patch; normals only, as Algorithm 1 states.
+ *   R7 patch contents: slot 0 the deepest member, slots 1..6 the members extreme
+ *      along u_k = cos(k pi/3) t1 + sin(k pi/3) t2 (k = 0..5) from the anchor; emitted
+ *      contacts are the distinct slot members in slot order, patches in list order.
+ *   R8 AddPatch: append below max_patches; at capacity replace the patch with the most
+ *      similar normal iff M(new) > M(old), M = -phi_deepest + sqrt(area of the
+ *      direction-slot polygon in the patch plane).
+ *   R9 solver: velocity-level projected Gauss-Seidel; per contact the normal row
+ *      (lambda_n >= 0) then the two friction rows projected jointly on the disk
+ *      |lambda_t| <= mu lambda_n; bias phi/hs when phi > 0 (speculative), baumgarte *
+ *      phi/hs otherwise; no warm start; mu of a pair = sqrt(mu_a mu_b).
+ *   R10 integration: semi-implicit Euler on the centre of mass and
+ *      q <- normalize(q + hs/2 (omega,0) q); |omega| clamped to max_angvel if set.
+ *   R11 tangent basis: t1 = normalize(n x e_x) if |n_x| < 0.57735 else
+ *      normalize(n x e_y); t2 = n x t1.
+ */
+#include "fw_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------------------ */
+/* small vector helpers                                                                   */
+/* ------------------------------------------------------------------------------------ */
+static void v_sub(const double a[3], const double b[3], double r[3]) { r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2]; }
+static void v_add(const double a[3], const double b[3], double r[3]) { r[0] = a[0] + b[0]; r[1] = a[1] + b[1]; r[2] = a[2] + b[2]; }
+static void v_scale(const double a[3], double s, double r[3]) { r[0] = a[0] * s; r[1] = a[1] * s; r[2] = a[2] * s; }
+static void v_axpy(double s, const double a[3], double r[3]) { r[0] += s * a[0]; r[1] += s * a[1]; r[2] += s * a[2]; }
+static double v_dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void v_cross(const double a[3], const double b[3], double r[3]) {
+    double x = a[1] * b[2] - a[2] * b[1], y = a[2] * b[0] - a[0] * b[2], z = a[0] * b[1] - a[1] * b[0];
+    r[0] = x; r[1] = y; r[2] = z;
+}
+static double v_norm(const double a[3]) { return sqrt(v_dot(a, a)); }
+static void m_vec(const double M[9], const double v[3], double r[3]) {
+    double x = M[0] * v[0] + M[1] * v[1] + M[2] * v[2];
+    double y = M[3] * v[0] + M[4] * v[1] + M[5] * v[2];
+    double z = M[6] * v[0] + M[7] * v[1] + M[8] * v[2];
+    r[0] = x; r[1] = y; r[2] = z;
+}
+static void m_mul(const double A[9], const double B[9], double C[9]) {
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+    memcpy(C, T, sizeof T);
+}
+static void m_transpose(const double A[9], double B[9]) {
+    double T[9] = {A[0], A[3], A[6], A[1], A[4], A[7], A[2], A[5], A[8]};
+    memcpy(B, T, sizeof T);
+}
+static int m_inverse(const double A[9], double B[9]) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (det == 0.0) return -1;
+    double id = 1.0 / det;
+    B[0] = c00 * id; B[1] = (A[2] * A[7] - A[1] * A[8]) * id; B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = c01 * id; B[4] = (A[0] * A[8] - A[2] * A[6]) * id; B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = c02 * id; B[7] = (A[1] * A[6] - A[0] * A[7]) * id; B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return 0;
+}
+/* rotation matrix of a unit quaternion (x, y, z, w) */
+static void q_to_m(const double q[4], double R[9]) {
+    double x = q[0], y = q[1], z = q[2], w = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+    R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+    R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+}
+static void q_normalize(double q[4]) {
+    double s = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] *= s;
+}
+static void load3(const float *f, double d[3]) { d[0] = f[0]; d[1] = f[1]; d[2] = f[2]; }
+
+/* ------------------------------------------------------------------------------------ */
+/* closest point on a triangle (Ericson 5.1.5: classify p against the Voronoi regions   */
+/* of the vertices, then of the edges, else project onto the face)                        */
+/* ------------------------------------------------------------------------------------ */
+int or_closest_point_triangle(const double p[3], const double a[3], const double b[3],
+                              const double c[3], double q[3]) {
+    double ab[3], ac[3], ap[3], bp[3], cp[3];
+    v_sub(b, a, ab); v_sub(c, a, ac); v_sub(p, a, ap);
+    double d1 = v_dot(ab, ap), d2 = v_dot(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) { memcpy(q, a, 3 * sizeof(double)); return 1; }
+    v_sub(p, b, bp);
+    double d3 = v_dot(ab, bp), d4 = v_dot(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) { memcpy(q, b, 3 * sizeof(double)); return 2; }
+    v_sub(p, c, cp);
+    double d5 = v_dot(ab, cp), d6 = v_dot(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) { memcpy(q, c, 3 * sizeof(double)); return 3; }
+    /* edge regions: the barycentric coordinate of the opposite vertex is <= 0 */
+    double vc = d1 * d4 - d3 * d2;          /* weight of c */
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+        double t = d1 / (d1 - d3);
+        q[0] = a[0] + t * ab[0]; q[1] = a[1] + t * ab[1]; q[2] = a[2] + t * ab[2];
+        return 4;
+    }
+    double va = d3 * d6 - d5 * d4;          /* weight of a */
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+        double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        q[0] = b[0] + t * (c[0] - b[0]); q[1] = b[1] + t * (c[1] - b[1]); q[2] = b[2] + t * (c[2] - b[2]);
+        return 5;
+    }
+    double vb = d5 * d2 - d1 * d6;          /* weight of b */
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+        double t = d2 / (d2 - d6);
+        q[0] = a[0] + t * ac[0]; q[1] = a[1] + t * ac[1]; q[2] = a[2] + t * ac[2];
+        return 6;
+    }
+    double s = 1.0 / (va + vb + vc);
+    double v = vb * s, w = vc * s;
+    q[0] = a[0] + v * ab[0] + w * ac[0];
+    q[1] = a[1] + v * ab[1] + w * ac[1];
+    q[2] = a[2] + v * ab[2] + w * ac[2];
+    return 0;
+}
+
+/* Van Oosterom & Strackee (1983): tan(Omega/2) = det[a b c] /
+ * (|a||b||c| + (a.b)|c| + (b.c)|a| + (c.a)|b|), vectors taken from p. */
+double or_solid_angle(const double p[3], const double a[3], const double b[3], const double c[3]) {
+    double A[3], B[3], C[3], bxc[3];
+    v_sub(a, p, A); v_sub(b, p, B); v_sub(c, p, C);
+    double la = v_norm(A), lb = v_norm(B), lc = v_norm(C);
+    v_cross(B, C, bxc);
+    double num = v_dot(A, bxc);
+    double den = la * lb * lc + v_dot(A, B) * lc + v_dot(B, C) * la + v_dot(C, A) * lb;
+    return 2.0 * atan2(num, den);
+}
+
+double or_winding_number(const double p[3], const float *V, const int *T, int nt) {
+    double sum = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        double a[3], b[3], c[3];
+        load3(V + 3 * T[3 * t], a); load3(V + 3 * T[3 * t + 1], b); load3(V + 3 * T[3 * t + 2], c);
+        sum += or_solid_angle(p, a, b, c);
+    }
+    return sum / (4.0 * M_PI);
+}
+
+double or_point_mesh_distance(const double p[3], const float *V, const int *T, int nt) {
+    double best = INFINITY;
+    for (int t = 0; t < nt; ++t) {
+        double a[3], b[3], c[3], q[3], d[3];
+        load3(V + 3 * T[3 * t], a); load3(V + 3 * T[3 * t + 1], b); load3(V + 3 * T[3 * t + 2], c);
+        or_closest_point_triangle(p, a, b, c, q);
+        v_sub(p, q, d);
+        double dd = v_dot(d, d);
+        if (dd < best) best = dd;
+    }
+    return sqrt(best);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* mass properties: sum over tetrahedra (0, a, b, c) of signed volume, first and second */
+/* moments.  For a tetrahedron with vertices p0..p3 the second moment is                  */
+/*   int x x^T dV = V/20 (sum_i p_i p_i^T + (sum_i p_i)(sum_i p_i)^T).                     */
+/* ------------------------------------------------------------------------------------ */
+void or_mass_properties(const float *V, const int *T, int nt, double density,
+                        double *mass, double com[3], double inertia[9]) {
+    double vol = 0.0, m1[3] = {0, 0, 0}, C[9] = {0};
+    for (int t = 0; t < nt; ++t) {
+        double a[3], b[3], c[3], bxc[3];
+        load3(V + 3 * T[3 * t], a); load3(V + 3 * T[3 * t + 1], b); load3(V + 3 * T[3 * t + 2], c);
+        v_cross(b, c, bxc);
+        double v = v_dot(a, bxc) / 6.0;
+        double s[3] = {a[0] + b[0] + c[0], a[1] + b[1] + c[1], a[2] + b[2] + c[2]};
+        vol += v;
+        for (int i = 0; i < 3; ++i) m1[i] += v * s[i] / 4.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                C[3 * i + j] += v / 20.0 * (a[i] * a[j] + b[i] * b[j] + c[i] * c[j] + s[i] * s[j]);
+    }
+    double m = density * vol;
+    double cm[3] = {m1[0] / vol, m1[1] / vol, m1[2] / vol};
+    /* inertia about the origin: rho (tr(C) I - C); shift to the centre of mass */
+    double tr = C[0] + C[4] + C[8];
+    double c2 = v_dot(cm, cm);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double Io = density * ((i == j ? tr : 0.0) - C[3 * i + j]);
+            double sh = m * ((i == j ? c2 : 0.0) - cm[i] * cm[j]);
+            inertia[3 * i + j] = Io - sh;
+        }
+    *mass = m;
+    memcpy(com, cm, sizeof cm);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* grid placement (R2): padded bounding box, h = L/(res-1) with L the longest padded    */
+/* extent; every value is rounded to float32 because the grid is stored in float32;     */
+/* cubic: res^3 nodes centred on the box centre.                                          */
+/* ------------------------------------------------------------------------------------ */
+void or_grid_params(const float *V, int nv, int res, float pad, int cubic,
+                    float lo[3], float *h, int dims[3]) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double x = V[3 * i + a];
+            if (x < mn[a]) mn[a] = x;
+            if (x > mx[a]) mx[a] = x;
+        }
+    double ext[3], L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        ext[a] = mx[a] - mn[a] + 2.0 * (double)pad;
+        if (ext[a] > L) L = ext[a];
+    }
+    float hf = (float)(L / (double)(res - 1));
+    *h = hf;
+    for (int a = 0; a < 3; ++a) {
+        int n = res;
+        if (!cubic) n = (int)ceil(ext[a] / (double)hf - 1e-9) + 1;
+        dims[a] = n;
+        lo[a] = (float)(0.5 * (mn[a] + mx[a]) - (double)hf * (double)(n - 1) * 0.5);
+    }
+}
+
+static double node_phi(const double x[3], const float *V, const int *T, int nt) {
+    double d = or_point_mesh_distance(x, V, T, nt);
+    if (d == 0.0) return 0.0;
+    double w = or_winding_number(x, V, T, nt);
+    return (w > 0.5) ? -d : d;        /* R1 */
+}
+
+void or_bake_nodes(const float *V, const int *T, int nt, const float lo[3], float h,
+                   const int dims[3], const long long *nodes, long long n_nodes,
+                   double *phi, int n_threads) {
+    long long total = nodes ? n_nodes : (long long)dims[0] * dims[1] * dims[2];
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (long long q = 0; q < total; ++q) {
+        long long id = nodes ? nodes[q] : q;
+        long long i = id % dims[0], j = (id / dims[0]) % dims[1], k = id / ((long long)dims[0] * dims[1]);
+        double x[3] = {(double)lo[0] + (double)i * (double)h, (double)lo[1] + (double)j * (double)h,
+                       (double)lo[2] + (double)k * (double)h};
+        phi[q] = node_phi(x, V, T, nt);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* trilinear value and gradient (Sec. III-A; R3, R4)                                     */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    double lo[3], h;
+    int dims[3];
+    double *val;          /* nx*ny*nz */
+    unsigned char *done;  /* lazy bake: 1 when val is set */
+    int lazy;
+} grid_t;
+
+static long long gidx(const grid_t *g, int i, int j, int k) {
+    return ((long long)k * g->dims[1] + j) * g->dims[0] + i;
+}
+
+/* returns 0 when the point is outside the grid box; *margin = distance (m) to the box */
+static int trilinear(const grid_t *g, const double x[3], double *phi, double grad[3], double *margin) {
+    double u[3], f[3];
+    int c[3];
+    double mg = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        u[a] = (x[a] - g->lo[a]) / g->h;
+        double m = fmin(u[a], (double)(g->dims[a] - 1) - u[a]) * g->h;
+        if (fabs(m) < mg) mg = fabs(m);
+    }
+    if (margin) *margin = mg;
+    for (int a = 0; a < 3; ++a)
+        if (!(u[a] >= 0.0 && u[a] <= (double)(g->dims[a] - 1))) return 0;
+    for (int a = 0; a < 3; ++a) {
+        int ci = (int)floor(u[a]);
+        if (ci > g->dims[a] - 2) ci = g->dims[a] - 2;
+        if (ci < 0) ci = 0;
+        c[a] = ci;
+        f[a] = u[a] - ci;
+    }
+    double v[2][2][2];
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di)
+                v[dk][dj][di] = g->val[gidx(g, c[0] + di, c[1] + dj, c[2] + dk)];
+    double wx[2] = {1 - f[0], f[0]}, wy[2] = {1 - f[1], f[1]}, wz[2] = {1 - f[2], f[2]};
+    double p = 0, gx = 0, gy = 0, gz = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di)
+                p += wx[di] * wy[dj] * wz[dk] * v[dk][dj][di];
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj) gx += wy[dj] * wz[dk] * (v[dk][dj][1] - v[dk][dj][0]);
+    for (int dk = 0; dk < 2; ++dk)
+        for (int di = 0; di < 2; ++di) gy += wx[di] * wz[dk] * (v[dk][1][di] - v[dk][0][di]);
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) gz += wx[di] * wy[dj] * (v[1][dj][di] - v[0][dj][di]);
+    *phi = p;
+    grad[0] = gx / g->h; grad[1] = gy / g->h; grad[2] = gz / g->h;
+    return 1;
+}
+
+void or_query(const double *grid, const float lo[3], float h, const int dims[3],
+              const float *pts, int n, double *phi, double *grad, int *valid) {
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    for (int a = 0; a < 3; ++a) { g.lo[a] = lo[a]; g.dims[a] = dims[a]; }
+    g.h = h;
+    g.val = (double *)grid;
+    for (int i = 0; i < n; ++i) {
+        double x[3], gr[3], p;
+        load3(pts + 3 * i, x);
+        int ok = trilinear(&g, x, &p, gr, NULL);
+        valid[i] = ok;
+        phi[i] = ok ? p : 0.0;
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = ok ? gr[a] : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* world                                                                                  */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    float *V; int nv; int *T; int nt;
+    float *S; int ns;
+    double density, mass, com[3], I[9];
+    int has_grid;
+    grid_t grid;
+} asset_t;
+
+typedef struct {
+    int asset, type;
+    double mass, mu;
+    double invm, Ib[9], Ib_inv[9], com_b[3];
+    double axis[3], force[3], torque[3];
+    double p[3], q[4], v[3], w[3];
+} body_t;
+
+typedef struct { int a, b; double mu; } pair_t;   /* global body ids */
+
+typedef struct {
+    int first_body, n_bodies, first_pair, n_pairs;
+} env_t;
+
+typedef struct {
+    or_contact *c; int n, cap;
+    double m_len, m_dot;        /* margins of the last detection of this pair */
+    int n_patches;
+} pair_contacts_t;
+
+struct or_world {
+    or_config cfg;
+    asset_t *assets; int n_assets, cap_assets;
+    body_t *bodies; int n_bodies;
+    pair_t *pairs; int n_pairs;
+    env_t *envs; int n_envs;
+    pair_contacts_t *pc;
+    double *env_mlen, *env_mdot;
+    double **imp; int *imp_n;               /* per env friction record */
+};
+
+or_world *or_create(const or_config *cfg) {
+    or_world *w = (or_world *)calloc(1, sizeof(or_world));
+    w->cfg = *cfg;
+    return w;
+}
+
+void or_destroy(or_world *w) {
+    if (!w) return;
+    for (int i = 0; i < w->n_assets; ++i) {
+        asset_t *a = &w->assets[i];
+        free(a->V); free(a->T); free(a->S); free(a->grid.val); free(a->grid.done);
+    }
+    for (int i = 0; i < w->n_pairs; ++i) free(w->pc[i].c);
+    free(w->assets); free(w->bodies); free(w->pairs); free(w->envs); free(w->pc);
+    for (int e = 0; e < w->n_envs; ++e) free(w->imp[e]);
+    free(w->env_mlen); free(w->env_mdot); free(w->imp); free(w->imp_n);
+    free(w);
+}
+
+int or_add_asset(or_world *w, const float *V, int nv, const int *T, int nt,
+                 const float *samples, int ns, double density) {
+    if (w->n_assets == w->cap_assets) {
+        w->cap_assets = w->cap_assets ? 2 * w->cap_assets : 4;
+        w->assets = (asset_t *)realloc(w->assets, w->cap_assets * sizeof(asset_t));
+    }
+    asset_t *a = &w->assets[w->n_assets];
+    memset(a, 0, sizeof *a);
+    a->V = (float *)malloc(3 * sizeof(float) * nv); memcpy(a->V, V, 3 * sizeof(float) * nv);
+    a->T = (int *)malloc(3 * sizeof(int) * nt); memcpy(a->T, T, 3 * sizeof(int) * nt);
+    a->nv = nv; a->nt = nt;
+    if (samples && ns > 0) {
+        a->S = (float *)malloc(3 * sizeof(float) * ns); memcpy(a->S, samples, 3 * sizeof(float) * ns);
+        a->ns = ns;
+    }
+    a->density = density;
+    or_mass_properties(V, T, nt, density, &a->mass, a->com, a->I);
+    return w->n_assets++;
+}
+
+static void grid_alloc(grid_t *g, const float lo[3], float h, const int dims[3], int lazy) {
+    for (int a = 0; a < 3; ++a) { g->lo[a] = lo[a]; g->dims[a] = dims[a]; }
+    g->h = h;
+    long long n = (long long)dims[0] * dims[1] * dims[2];
+    free(g->val); free(g->done);
+    g->val = (double *)calloc(n, sizeof(double));
+    g->done = lazy ? (unsigned char *)calloc(n, 1) : NULL;
+    g->lazy = lazy;
+}
+
+int or_asset_bake(or_world *w, int asset, int res, float pad, int cubic, int lazy) {
+    asset_t *a = &w->assets[asset];
+    float lo[3], h; int dims[3];
+    or_grid_params(a->V, a->nv, res, pad, cubic, lo, &h, dims);
+    grid_alloc(&a->grid, lo, h, dims, lazy);
+    if (!lazy) or_bake_nodes(a->V, a->T, a->nt, lo, h, dims, NULL, 0, a->grid.val, w->cfg.n_threads);
+    a->has_grid = 1;
+    return 0;
+}
+
+int or_asset_set_grid(or_world *w, int asset, const float lo[3], float h, const int dims[3],
+                      const float *values) {
+    asset_t *a = &w->assets[asset];
+    grid_alloc(&a->grid, lo, h, dims, 0);
+    long long n = (long long)dims[0] * dims[1] * dims[2];
+    for (long long i = 0; i < n; ++i) a->grid.val[i] = values[i];
+    a->has_grid = 1;
+    return 0;
+}
+
+int or_asset_get_grid(const or_world *w, int asset, float lo[3], float *h, int dims[3]) {
+    const asset_t *a = &w->assets[asset];
+    if (!a->has_grid) return -1;
+    for (int i = 0; i < 3; ++i) { lo[i] = (float)a->grid.lo[i]; dims[i] = a->grid.dims[i]; }
+    *h = (float)a->grid.h;
+    return 0;
+}
+
+int or_asset_mass(const or_world *w, int asset, double *mass, double com[3], double inertia[9]) {
+    const asset_t *a = &w->assets[asset];
+    *mass = a->mass;
+    memcpy(com, a->com, sizeof a->com);
+    memcpy(inertia, a->I, sizeof a->I);
+    return 0;
+}
+
+/* world inverse inertia and inertia of a body at its current orientation */
+static void body_world_inertia(const body_t *b, double Iw[9], double Iw_inv[9]) {
+    double R[9], Rt[9], tmp[9];
+    q_to_m(b->q, R);
+    m_transpose(R, Rt);
+    if (b->type == 2 || b->type == 3) {
+        m_mul(R, b->Ib, tmp); m_mul(tmp, Rt, Iw);
+        if (b->type == 2) {
+            m_mul(R, b->Ib_inv, tmp); m_mul(tmp, Rt, Iw_inv);
+        } else {
+            double Iaa = 0;
+            double Ia[3];
+            m_vec(Iw, b->axis, Ia);
+            Iaa = v_dot(b->axis, Ia);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Iw_inv[3 * i + j] = b->axis[i] * b->axis[j] / Iaa;
+        }
+    } else {
+        memset(Iw, 0, 9 * sizeof(double));
+        memset(Iw_inv, 0, 9 * sizeof(double));
+    }
+}
+
+static void body_com_world(const body_t *b, double c[3]) {
+    double R[9];
+    q_to_m(b->q, R);
+    m_vec(R, b->com_b, c);
+    v_add(c, b->p, c);
+}
+
+int or_add_envs(or_world *w, int n_envs, const or_body_desc *bd, int n_per_env,
+                const int *pairs, int n_pairs) {
+    int nb0 = w->n_bodies, np0 = w->n_pairs, ne0 = w->n_envs;
+    w->bodies = (body_t *)realloc(w->bodies, sizeof(body_t) * (nb0 + n_envs * n_per_env));
+    w->pairs = (pair_t *)realloc(w->pairs, sizeof(pair_t) * (np0 + n_envs * n_pairs));
+    w->pc = (pair_contacts_t *)realloc(w->pc, sizeof(pair_contacts_t) * (np0 + n_envs * n_pairs));
+    w->envs = (env_t *)realloc(w->envs, sizeof(env_t) * (ne0 + n_envs));
+    w->env_mlen = (double *)realloc(w->env_mlen, sizeof(double) * (ne0 + n_envs));
+    w->env_mdot = (double *)realloc(w->env_mdot, sizeof(double) * (ne0 + n_envs));
+    w->imp = (double **)realloc(w->imp, sizeof(double *) * (ne0 + n_envs));
+    w->imp_n = (int *)realloc(w->imp_n, sizeof(int) * (ne0 + n_envs));
+    for (int e = 0; e < n_envs; ++e) { w->imp[ne0 + e] = NULL; w->imp_n[ne0 + e] = 0; }
+    for (int e = 0; e < n_envs; ++e) {
+        env_t *E = &w->envs[ne0 + e];
+        E->first_body = nb0 + e * n_per_env;
+        E->n_bodies = n_per_env;
+        E->first_pair = np0 + e * n_pairs;
+        E->n_pairs = n_pairs;
+        w->env_mlen[ne0 + e] = INFINITY;
+        w->env_mdot[ne0 + e] = INFINITY;
+        for (int i = 0; i < n_per_env; ++i) {
+            const or_body_desc *d = &bd[e * n_per_env + i];
+            body_t *b = &w->bodies[E->first_body + i];
+            memset(b, 0, sizeof *b);
+            const asset_t *A = &w->assets[d->asset];
+            b->asset = d->asset; b->type = d->type; b->mu = d->mu;
+            double scale = 1.0;
+            b->mass = A->mass;
+            if (d->mass > 0.0f) { scale = (double)d->mass / A->mass; b->mass = d->mass; }
+            for (int k = 0; k < 9; ++k) b->Ib[k] = A->I[k] * scale;
+            m_inverse(b->Ib, b->Ib_inv);
+            memcpy(b->com_b, A->com, sizeof A->com);
+            b->invm = (b->type == 2) ? 1.0 / b->mass : 0.0;
+            load3(d->axis, b->axis);
+            double an = v_norm(b->axis);
+            if (an > 0) v_scale(b->axis, 1.0 / an, b->axis);
+            load3(d->force, b->force); load3(d->torque, b->torque);
+            load3(d->pos, b->p);
+            for (int k = 0; k < 4; ++k) b->q[k] = d->quat[k];
+            q_normalize(b->q);
+            /* linvel / angvel are of the centre of mass; fixed-axis bodies keep the
+               centre fixed and spin about the axis only */
+            load3(d->linvel, b->v); load3(d->angvel, b->w);
+            if (b->type == 0) { memset(b->v, 0, sizeof b->v); memset(b->w, 0, sizeof b->w); }
+            if (b->type == 3) { double s = v_dot(b->w, b->axis); memset(b->v, 0, sizeof b->v); v_scale(b->axis, s, b->w); }
+        }
+        for (int p = 0; p < n_pairs; ++p) {
+            pair_t *P = &w->pairs[E->first_pair + p];
+            P->a = E->first_body + pairs[2 * p];
+            P->b = E->first_body + pairs[2 * p + 1];
+            P->mu = sqrt((double)w->bodies[P->a].mu * (double)w->bodies[P->b].mu);
+            pair_contacts_t *pc = &w->pc[E->first_pair + p];
+            memset(pc, 0, sizeof *pc);
+            pc->m_len = INFINITY; pc->m_dot = INFINITY;
+        }
+    }
+    w->n_bodies = nb0 + n_envs * n_per_env;
+    w->n_pairs = np0 + n_envs * n_pairs;
+    w->n_envs = ne0 + n_envs;
+    return ne0;
+}
+
+int or_n_envs(const or_world *w) { return w->n_envs; }
+int or_n_bodies(const or_world *w) { return w->n_bodies; }
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 1 (Sec. III-C)                                                               */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { int idx; double phi, x[3], n[3]; } cand_t;
+
+#define NSLOT 7
+typedef struct {
+    double n[3], a[3], t1[3], t2[3];
+    int idx[NSLOT];
+    double best[NSLOT], second[NSLOT];
+    cand_t mem[NSLOT];
+} patch_t;
+
+typedef struct { double len, dot; } margin_t;
+
+static void mark_len(margin_t *m, double v) { v = fabs(v); if (v < m->len) m->len = v; }
+static void mark_dot(margin_t *m, double v) { v = fabs(v); if (v < m->dot) m->dot = v; }
+
+/* R11 */
+static void tangent_basis(const double n[3], double t1[3], double t2[3], margin_t *m) {
+    static const double ex[3] = {1, 0, 0}, ey[3] = {0, 1, 0};
+    if (m) mark_dot(m, fabs(n[0]) - 0.57735);
+    if (fabs(n[0]) < 0.57735) v_cross(n, ex, t1); else v_cross(n, ey, t1);
+    v_scale(t1, 1.0 / v_norm(t1), t1);
+    v_cross(n, t1, t2);
+}
+
+static double slot_score(const patch_t *P, const cand_t *c, int s) {
+    if (s == 0) return -c->phi;                         /* deepest */
+    double ang = (double)(s - 1) * M_PI / 3.0;
+    double u[3], d[3];
+    for (int i = 0; i < 3; ++i) u[i] = cos(ang) * P->t1[i] + sin(ang) * P->t2[i];
+    v_sub(c->x, P->a, d);
+    return v_dot(d, u);
+}
+
+static void patch_init(patch_t *P, const cand_t *seed, margin_t *m) {
+    memcpy(P->n, seed->n, sizeof P->n);
+    memcpy(P->a, seed->x, sizeof P->a);
+    tangent_basis(P->n, P->t1, P->t2, m);
+    for (int s = 0; s < NSLOT; ++s) { P->idx[s] = -1; P->best[s] = -INFINITY; P->second[s] = -INFINITY; }
+}
+
+/* running argmax per slot, ties to the lowest sample index; margin = best - second */
+static void patch_add_member(patch_t *P, const cand_t *c) {
+    for (int s = 0; s < NSLOT; ++s) {
+        double v = slot_score(P, c, s);
+        if (P->idx[s] < 0 || v > P->best[s] || (v == P->best[s] && c->idx < P->idx[s])) {
+            P->second[s] = P->best[s];
+            P->best[s] = v; P->idx[s] = c->idx; P->mem[s] = *c;
+        } else if (v > P->second[s]) {
+            P->second[s] = v;
+        }
+    }
+}
+
+static void patch_slot_margins(const patch_t *P, margin_t *m) {
+    for (int s = 0; s < NSLOT; ++s)
+        if (P->idx[s] >= 0 && P->second[s] > -INFINITY) mark_len(m, P->best[s] - P->second[s]);
+}
+
+/* R8: M = -phi_deepest + sqrt(area of the polygon through the distinct direction-slot
+ * points, in slot order, in the (t1, t2) plane) */
+static double patch_measure(const patch_t *P) {
+    double xs[6], ys[6];
+    int n = 0, seen[6];
+    for (int s = 1; s < NSLOT; ++s) {
+        int dup = 0;
+        if (P->idx[s] < 0) continue;
+        for (int t = 0; t < n; ++t) if (seen[t] == P->idx[s]) dup = 1;
+        if (dup) continue;
+        double d[3];
+        v_sub(P->mem[s].x, P->a, d);
+        xs[n] = v_dot(d, P->t1); ys[n] = v_dot(d, P->t2);
+        seen[n++] = P->idx[s];
+    }
+    double area2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        area2 += xs[i] * ys[j] - xs[j] * ys[i];
+    }
+    double area = 0.5 * fabs(area2);
+    return -P->mem[0].phi + sqrt(area);
+}
+
+typedef struct {
+    patch_t *p; int n, cap;
+} patch_list_t;
+
+/* AddPatch (Sec. III-C): append below capacity, else replace the most similar patch
+ * if the new one scores higher on M, else drop it */
+static void add_patch(patch_list_t *L, const patch_t *P, int max_patches, margin_t *m) {
+    if (L->n < max_patches) { L->p[L->n++] = *P; return; }
+    int k = 0; double bd = -INFINITY, sd = -INFINITY;
+    for (int j = 0; j < L->n; ++j) {
+        double d = v_dot(P->n, L->p[j].n);
+        if (d > bd) { sd = bd; bd = d; k = j; } else if (d > sd) sd = d;
+    }
+    if (sd > -INFINITY) mark_dot(m, bd - sd);
+    double mn = patch_measure(P), mo = patch_measure(&L->p[k]);
+    mark_len(m, mn - mo);
+    if (mn > mo) L->p[k] = *P;
+}
+
+/* Algorithm 1 over one shape pair.  cands must be sorted by sample index. */
+static int reduce_pair(const cand_t *cands, int nc, double cos_patch, int max_patches,
+                       int batch_size, or_contact *out, int cap, int *n_patches, margin_t *m) {
+    patch_list_t L;
+    L.cap = max_patches; L.n = 0;
+    L.p = (patch_t *)malloc(sizeof(patch_t) * (max_patches > 0 ? max_patches : 1));
+    int *assigned = (int *)malloc(sizeof(int) * (nc > 0 ? nc : 1));
+    int start = 0;
+    while (start < nc) {
+        /* Generate: the candidates of this batch of samples */
+        int bidx = cands[start].idx / batch_size, end = start;
+        while (end < nc && cands[end].idx / batch_size == bidx) ++end;
+        /* Assign to existing patches by normal similarity */
+        int n_existing = L.n;
+        for (int i = start; i < end; ++i) {
+            assigned[i] = 0;
+            int best = -1; double bd = -INFINITY, sd = -INFINITY;
+            for (int j = 0; j < n_existing; ++j) {
+                double d = v_dot(cands[i].n, L.p[j].n);
+                if (d > bd) { sd = bd; bd = d; best = j; } else if (d > sd) sd = d;
+            }
+            if (best < 0) continue;
+            mark_dot(m, bd - cos_patch);
+            if (bd >= cos_patch) {
+                if (sd > -INFINITY) mark_dot(m, bd - sd);
+                patch_add_member(&L.p[best], &cands[i]);
+                assigned[i] = 1;
+            }
+        }
+        /* while candidates remain: FindDeepest, BinReduce, AddPatch */
+        for (;;) {
+            int best = -1; double bphi = INFINITY, sphi = INFINITY;
+            for (int i = start; i < end; ++i) {
+                if (assigned[i]) continue;
+                /* candidates are visited in sample order, so '<' keeps the lowest index on ties */
+                if (cands[i].phi < bphi) {
+                    sphi = bphi; bphi = cands[i].phi; best = i;
+                } else if (cands[i].phi < sphi) sphi = cands[i].phi;
+            }
+            if (best < 0) break;
+            if (sphi < INFINITY) mark_len(m, sphi - bphi);
+            patch_t P;
+            patch_init(&P, &cands[best], m);
+            for (int i = start; i < end; ++i) {
+                if (assigned[i]) continue;
+                double d = v_dot(cands[i].n, P.n);
+                if (i != best) mark_dot(m, d - cos_patch);
+                if (i == best || d >= cos_patch) {
+                    patch_add_member(&P, &cands[i]);
+                    assigned[i] = 1;
+                }
+            }
+            add_patch(&L, &P, max_patches, m);
+        }
+        start = end;
+    }
+    /* emit: patches in list order, distinct slot members in slot order */
+    int n = 0;
+    for (int j = 0; j < L.n; ++j) {
+        patch_slot_margins(&L.p[j], m);
+        for (int s = 0; s < NSLOT; ++s) {
+            int id = L.p[j].idx[s], dup = 0;
+            if (id < 0) continue;
+            for (int t = 0; t < s; ++t) if (L.p[j].idx[t] == id) dup = 1;
+            if (dup) continue;
+            if (n < cap) {
+                const cand_t *c = &L.p[j].mem[s];
+                or_contact *o = &out[n];
+                o->sample = c->idx; o->patch = j; o->phi = c->phi;
+                for (int a = 0; a < 3; ++a) {
+                    o->xa[a] = c->x[a]; o->n[a] = c->n[a];
+                    o->xb[a] = c->x[a] - c->phi * c->n[a];
+                }
+            }
+            ++n;
+        }
+    }
+    *n_patches = L.n;
+    free(L.p); free(assigned);
+    return n;
+}
+
+int or_reduce(const or_candidate *cand, int n, double cos_patch, int max_patches,
+              int batch_size, or_contact *out, int cap, int *n_out, int *n_patches,
+              double *min_margin_len, double *min_margin_dot) {
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        c[i].idx = cand[i].sample; c[i].phi = cand[i].phi;
+        load3(cand[i].x, c[i].x); load3(cand[i].n, c[i].n);
+    }
+    /* insertion into sample order (stable) */
+    for (int i = 1; i < n; ++i) {
+        cand_t t = c[i]; int j = i - 1;
+        while (j >= 0 && c[j].idx > t.idx) { c[j + 1] = c[j]; --j; }
+        c[j + 1] = t;
+    }
+    margin_t m = {INFINITY, INFINITY};
+    int np = 0;
+    int k = reduce_pair(c, n, cos_patch, max_patches, batch_size, out, cap, &np, &m);
+    *n_out = k; *n_patches = np;
+    *min_margin_len = m.len; *min_margin_dot = m.dot;
+    free(c);
+    return k > cap ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* narrow phase of one pair at the current poses (Sec. III-A; R4, R5)                    */
+/* ------------------------------------------------------------------------------------ */
+static void ensure_nodes(or_world *w);
+
+static int generate_candidates(const or_world *w, const pair_t *P, cand_t *out, margin_t *m) {
+    const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
+    const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
+    double RA[9], RB[9], RBt[9];
+    q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+    int n = 0;
+    for (int i = 0; i < aa->ns; ++i) {
+        double s[3], xw[3], xb[3], d[3], phi, g[3], bm;
+        load3(aa->S + 3 * i, s);
+        m_vec(RA, s, xw); v_add(xw, A->p, xw);
+        v_sub(xw, B->p, d); m_vec(RBt, d, xb);
+        int ok = trilinear(&ab->grid, xb, &phi, g, &bm);
+        mark_len(m, bm);
+        if (!ok) continue;
+        double gn = v_norm(g);
+        if (gn < 1e-12) continue;
+        mark_len(m, phi - w->cfg.contact_offset);
+        if (!(phi < w->cfg.contact_offset)) continue;
+        double nb[3];
+        v_scale(g, 1.0 / gn, nb);
+        cand_t *c = &out[n++];
+        c->idx = i; c->phi = phi;
+        memcpy(c->x, xw, sizeof xw);
+        m_vec(RB, nb, c->n);
+    }
+    return n;
+}
+
+static void detect_pair(or_world *w, int pi) {
+    const pair_t *P = &w->pairs[pi];
+    const asset_t *aa = &w->assets[w->bodies[P->a].asset];
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (aa->ns > 0 ? aa->ns : 1));
+    margin_t m = {INFINITY, INFINITY};
+    int nc = generate_candidates(w, P, c, &m);
+    pair_contacts_t *pc = &w->pc[pi];
+    int cap = w->cfg.max_patches * NSLOT;
+    if (pc->cap < cap) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * cap); pc->cap = cap; }
+    pc->n = reduce_pair(c, nc, w->cfg.cos_patch, w->cfg.max_patches, w->cfg.batch_size,
+                        pc->c, pc->cap, &pc->n_patches, &m);
+    pc->m_len = m.len; pc->m_dot = m.dot;
+    free(c);
+}
+
+/* lazy bake: compute every grid node the next detection will read */
+static void ensure_nodes(or_world *w) {
+    for (int ai = 0; ai < w->n_assets; ++ai) {
+        asset_t *ab = &w->assets[ai];
+        if (!ab->has_grid || !ab->grid.lazy) continue;
+        grid_t *g = &ab->grid;
+        long long cap = 1024, nn = 0;
+        long long *need = (long long *)malloc(sizeof(long long) * cap);
+        for (int pi = 0; pi < w->n_pairs; ++pi) {
+            const pair_t *P = &w->pairs[pi];
+            const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
+            if (B->asset != ai) continue;
+            const asset_t *aa = &w->assets[A->asset];
+            double RA[9], RB[9], RBt[9];
+            q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+            for (int i = 0; i < aa->ns; ++i) {
+                double s[3], xw[3], xb[3], d[3];
+                load3(aa->S + 3 * i, s);
+                m_vec(RA, s, xw); v_add(xw, A->p, xw);
+                v_sub(xw, B->p, d); m_vec(RBt, d, xb);
+                int c[3], inside = 1;
+                for (int a = 0; a < 3; ++a) {
+                    double u = (xb[a] - g->lo[a]) / g->h;
+                    if (!(u >= 0.0 && u <= g->dims[a] - 1)) inside = 0;
+                    int ci = (int)floor(u);
+                    if (ci > g->dims[a] - 2) ci = g->dims[a] - 2;
+                    if (ci < 0) ci = 0;
+                    c[a] = ci;
+                }
+                if (!inside) continue;
+                for (int k = 0; k < 8; ++k) {
+                    long long id = gidx(g, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + ((k >> 2) & 1));
+                    if (g->done[id]) continue;
+                    g->done[id] = 2;    /* queued */
+                    if (nn == cap) { cap *= 2; need = (long long *)realloc(need, sizeof(long long) * cap); }
+                    need[nn++] = id;
+                }
+            }
+        }
+        if (nn > 0) {
+            double *vals = (double *)malloc(sizeof(double) * nn);
+            float lo[3] = {(float)g->lo[0], (float)g->lo[1], (float)g->lo[2]};
+            or_bake_nodes(ab->V, ab->T, ab->nt, lo, (float)g->h, g->dims, need, nn, vals, w->cfg.n_threads);
+            for (long long q = 0; q < nn; ++q) { g->val[need[q]] = vals[q]; g->done[need[q]] = 1; }
+            free(vals);
+        }
+        free(need);
+    }
+}
+
+int or_collide(or_world *w) {
+    ensure_nodes(w);
+#ifdef _OPENMP
+    if (w->cfg.n_threads > 0) omp_set_num_threads(w->cfg.n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int pi = 0; pi < w->n_pairs; ++pi) detect_pair(w, pi);
+    for (int e = 0; e < w->n_envs; ++e) {
+        const env_t *E = &w->envs[e];
+        for (int p = 0; p < E->n_pairs; ++p) {
+            const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+            if (pc->m_len < w->env_mlen[e]) w->env_mlen[e] = pc->m_len;
+            if (pc->m_dot < w->env_mdot[e]) w->env_mdot[e] = pc->m_dot;
+        }
+    }
+    return 0;
+}
+
+int or_get_contacts(const or_world *w, int env, or_contact *out, int cap, int *n_out,
+                    double *min_margin_len, double *min_margin_dot) {
+    const env_t *E = &w->envs[env];
+    int n = 0;
+    double ml = INFINITY, md = INFINITY;
+    for (int p = 0; p < E->n_pairs; ++p) {
+        const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+        for (int i = 0; i < pc->n; ++i) {
+            if (n < cap) out[n] = pc->c[i];
+            ++n;
+        }
+        if (pc->m_len < ml) ml = pc->m_len;
+        if (pc->m_dot < md) md = pc->m_dot;
+    }
+    *n_out = n;
+    if (min_margin_len) *min_margin_len = ml;
+    if (min_margin_dot) *min_margin_dot = md;
+    return n > cap ? -1 : 0;
+}
+
+/* contacts of an env go to its first pair (the solve only needs them in order) */
+int or_set_contacts(or_world *w, int env, const or_contact *in, int n) {
+    const env_t *E = &w->envs[env];
+    for (int p = 0; p < E->n_pairs; ++p) w->pc[E->first_pair + p].n = 0;
+    pair_contacts_t *pc = &w->pc[E->first_pair];
+    if (pc->cap < n) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * n); pc->cap = n; }
+    memcpy(pc->c, in, sizeof(or_contact) * n);
+    pc->n = n;
+    return 0;
+}
+
+int or_env_margins(const or_world *w, int env, double *len, double *dot) {
+    *len = w->env_mlen[env]; *dot = w->env_mdot[env];
+    return 0;
+}
+
+void or_reset_margins(or_world *w) {
+    for (int e = 0; e < w->n_envs; ++e) { w->env_mlen[e] = INFINITY; w->env_mdot[e] = INFINITY; }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* substep (R9, R10)                                                                      */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    int a, b;                     /* local body index in the env */
+    double ra[3], rb[3], n[3], t1[3], t2[3];
+    double kn, kt1, kt2, bias, mu;
+    double ln, lt1, lt2;
+} row_t;
+
+/* effective mass of direction d at the contact: 1 / (J M^-1 J^T) */
+static double eff_mass(const body_t *A, const body_t *B, const double IA[9], const double IB[9],
+                       const double ra[3], const double rb[3], const double d[3]) {
+    double ca[3], cb[3], ta[3], tb[3];
+    v_cross(ra, d, ca); v_cross(rb, d, cb);
+    m_vec(IA, ca, ta); m_vec(IB, cb, tb);
+    double den = A->invm + B->invm + v_dot(ca, ta) + v_dot(cb, tb);
+    return den > 0.0 ? 1.0 / den : 0.0;
+}
+
+/* apply impulse p (world vector) at the contact: +p on A, -p on B */
+static void apply_impulse(body_t *A, body_t *B, const double IA[9], const double IB[9],
+                          const double ra[3], const double rb[3], const double p[3]) {
+    double c[3], dw[3];
+    v_axpy(A->invm, p, A->v);
+    v_cross(ra, p, c); m_vec(IA, c, dw); v_add(A->w, dw, A->w);
+    v_axpy(-B->invm, p, B->v);
+    v_cross(rb, p, c); m_vec(IB, c, dw); v_sub(B->w, dw, B->w);
+}
+
+static void rel_vel(const body_t *A, const body_t *B, const double ra[3], const double rb[3], double vr[3]) {
+    double wa[3], wb[3];
+    v_cross(A->w, ra, wa); v_cross(B->w, rb, wb);
+    for (int i = 0; i < 3; ++i) vr[i] = (A->v[i] + wa[i]) - (B->v[i] + wb[i]);
+}
+
+static void sweep(body_t *bodies, row_t *rows, int nr, double (*Iinv)[9], int use_bias) {
+    for (int r = 0; r < nr; ++r) {
+        row_t *R = &rows[r];
+        if (R->kn == 0.0) continue;
+        body_t *A = &bodies[R->a], *B = &bodies[R->b];
+        double vr[3], p[3];
+        /* normal row: lambda_n >= 0 */
+        rel_vel(A, B, R->ra, R->rb, vr);
+        double vn = v_dot(R->n, vr) + (use_bias ? R->bias : 0.0);
+        double ln = R->ln - R->kn * vn;
+        if (ln < 0.0) ln = 0.0;
+        double dl = ln - R->ln;
+        R->ln = ln;
+        v_scale(R->n, dl, p);
+        apply_impulse(A, B, Iinv[R->a], Iinv[R->b], R->ra, R->rb, p);
+        /* friction rows, projected jointly on the disk |lambda_t| <= mu lambda_n */
+        rel_vel(A, B, R->ra, R->rb, vr);
+        double l1 = R->lt1 - R->kt1 * v_dot(R->t1, vr);
+        double l2 = R->lt2 - R->kt2 * v_dot(R->t2, vr);
+        double lim = R->mu * R->ln;
+        double lt = sqrt(l1 * l1 + l2 * l2);
+        if (lt > lim) {
+            double s = lt > 0.0 ? lim / lt : 0.0;
+            l1 *= s; l2 *= s;
+        }
+        double d1 = l1 - R->lt1, d2 = l2 - R->lt2;
+        R->lt1 = l1; R->lt2 = l2;
+        for (int i = 0; i < 3; ++i) p[i] = d1 * R->t1[i] + d2 * R->t2[i];
+        apply_impulse(A, B, Iinv[R->a], Iinv[R->b], R->ra, R->rb, p);
+    }
+}
+
+static void env_substep(or_world *w, int e, double hs, int n_iters) {
+    const env_t *E = &w->envs[e];
+    body_t *bodies = &w->bodies[E->first_body];
+    int nb = E->n_bodies;
+    double (*Iw)[9] = malloc(sizeof(double) * 9 * nb);
+    double (*Iinv)[9] = malloc(sizeof(double) * 9 * nb);
+    double (*com)[3] = malloc(sizeof(double) * 3 * nb);
+    /* 1. external forces (gravity, applied force and torque, gyroscopic term) */
+    for (int i = 0; i < nb; ++i) {
+        body_t *b = &bodies[i];
+        body_world_inertia(b, Iw[i], Iinv[i]);
+        body_com_world(b, com[i]);
+        if (b->type == 2) {
+            for (int k = 0; k < 3; ++k) b->v[k] += hs * (w->cfg.gravity[k] + b->force[k] / b->mass);
+            double Lw[3], gyro[3], t[3], dw[3];
+            m_vec(Iw[i], b->w, Lw);
+            v_cross(b->w, Lw, gyro);
+            v_sub(b->torque, gyro, t);
+            m_vec(Iinv[i], t, dw);
+            v_axpy(hs, dw, b->w);
+        } else if (b->type == 3) {
+            double Ia[3];
+            m_vec(Iw[i], b->axis, Ia);
+            double Iaa = v_dot(b->axis, Ia);
+            v_axpy(hs * v_dot(b->axis, b->torque) / Iaa, b->axis, b->w);
+        }
+    }
+    /* 3. prep: rows from the contacts of every pair of the env, in pair order */
+    int nr = 0;
+    for (int p = 0; p < E->n_pairs; ++p) nr += w->pc[E->first_pair + p].n;
+    row_t *rows = (row_t *)calloc(nr > 0 ? nr : 1, sizeof(row_t));
+    int r = 0;
+    for (int p = 0; p < E->n_pairs; ++p) {
+        const pair_t *P = &w->pairs[E->first_pair + p];
+        const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+        int la = P->a - E->first_body, lb = P->b - E->first_body;
+        for (int i = 0; i < pc->n; ++i, ++r) {
+            const or_contact *c = &pc->c[i];
+            row_t *R = &rows[r];
+            R->a = la; R->b = lb;
+            v_sub(c->xa, com[la], R->ra);
+            v_sub(c->xb, com[lb], R->rb);
+            memcpy(R->n, c->n, sizeof R->n);
+            margin_t tm = {INFINITY, INFINITY};
+            tangent_basis(R->n, R->t1, R->t2, &tm);
+            if (tm.dot < w->env_mdot[e]) w->env_mdot[e] = tm.dot;
+            R->kn = eff_mass(&bodies[la], &bodies[lb], Iinv[la], Iinv[lb], R->ra, R->rb, R->n);
+            R->kt1 = eff_mass(&bodies[la], &bodies[lb], Iinv[la], Iinv[lb], R->ra, R->rb, R->t1);
+            R->kt2 = eff_mass(&bodies[la], &bodies[lb], Iinv[la], Iinv[lb], R->ra, R->rb, R->t2);
+            R->bias = (c->phi > 0.0) ? c->phi / hs : w->cfg.baumgarte * c->phi / hs;
+            R->mu = P->mu;
+        }
+    }
+    /* 4. Gauss-Seidel sweeps */
+    for (int it = 0; it < n_iters; ++it) sweep(bodies, rows, nr, Iinv, 1);
+    /* 5. integrate */
+    for (int i = 0; i < nb; ++i) {
+        body_t *b = &bodies[i];
+        if (b->type == 0) continue;
+        if ((b->type == 2 || b->type == 3) && w->cfg.max_angvel > 0.0) {
+            double wn = v_norm(b->w);
+            if (wn > w->cfg.max_angvel) v_scale(b->w, w->cfg.max_angvel / wn, b->w);
+        }
+        double c[3], R[9], rc[3];
+        memcpy(c, com[i], sizeof c);
+        v_axpy(hs, b->v, c);
+        double wq[4] = {b->w[0], b->w[1], b->w[2], 0.0}, dq[4];
+        /* (omega, 0) (x) q */
+        dq[0] = wq[3] * b->q[0] + b->q[3] * wq[0] + wq[1] * b->q[2] - wq[2] * b->q[1];
+        dq[1] = wq[3] * b->q[1] + b->q[3] * wq[1] + wq[2] * b->q[0] - wq[0] * b->q[2];
+        dq[2] = wq[3] * b->q[2] + b->q[3] * wq[2] + wq[0] * b->q[1] - wq[1] * b->q[0];
+        dq[3] = wq[3] * b->q[3] - (wq[0] * b->q[0] + wq[1] * b->q[1] + wq[2] * b->q[2]);
+        for (int k = 0; k < 4; ++k) b->q[k] += 0.5 * hs * dq[k];
+        q_normalize(b->q);
+        q_to_m(b->q, R);
+        m_vec(R, b->com_b, rc);
+        v_sub(c, rc, b->p);
+    }
+    /* 6. optional bias-free sweeps */
+    for (int it = 0; it < w->cfg.n_vel_iters; ++it) sweep(bodies, rows, nr, Iinv, 0);
+    /* friction-cone record of this solve: (lambda_n, |lambda_t|, mu) per row */
+    double *rec = (double *)malloc(sizeof(double) * 3 * (nr > 0 ? nr : 1));
+    for (int k = 0; k < nr; ++k) {
+        rec[3 * k] = rows[k].ln;
+        rec[3 * k + 1] = sqrt(rows[k].lt1 * rows[k].lt1 + rows[k].lt2 * rows[k].lt2);
+        rec[3 * k + 2] = rows[k].mu;
+    }
+    free(w->imp[e]);
+    w->imp[e] = rec;
+    w->imp_n[e] = nr;
+    free(rows); free(Iw); free(Iinv); free(com);
+}
+
+int or_substep(or_world *w, double hs, int n_iters, int detect) {
+    if (detect) or_collide(w);
+#ifdef _OPENMP
+    if (w->cfg.n_threads > 0) omp_set_num_threads(w->cfg.n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int e = 0; e < w->n_envs; ++e) env_substep(w, e, hs, n_iters);
+    return 0;
+}
+
+int or_step(or_world *w, int n_substeps, int n_iters) {
+    double hs = w->cfg.dt / (double)n_substeps;
+    for (int s = 0; s < n_substeps; ++s) or_substep(w, hs, n_iters, 1);
+    return 0;
+}
+
+int or_get_state(const or_world *w, double *pos, double *quat, double *linvel, double *angvel) {
+    for (int i = 0; i < w->n_bodies; ++i) {
+        const body_t *b = &w->bodies[i];
+        memcpy(pos + 3 * i, b->p, 3 * sizeof(double));
+        memcpy(quat + 4 * i, b->q, 4 * sizeof(double));
+        memcpy(linvel + 3 * i, b->v, 3 * sizeof(double));
+        memcpy(angvel + 3 * i, b->w, 3 * sizeof(double));
+    }
+    return 0;
+}
+
+int or_set_state(or_world *w, const double *pos, const double *quat, const double *linvel,
+                 const double *angvel) {
+    for (int i = 0; i < w->n_bodies; ++i) {
+        body_t *b = &w->bodies[i];
+        memcpy(b->p, pos + 3 * i, 3 * sizeof(double));
+        memcpy(b->q, quat + 4 * i, 4 * sizeof(double));
+        q_normalize(b->q);
+        memcpy(b->v, linvel + 3 * i, 3 * sizeof(double));
+        memcpy(b->w, angvel + 3 * i, 3 * sizeof(double));
+    }
+    return 0;
+}
+
+int or_get_impulses(const or_world *w, int env, double *out, int cap, int *n_out) {
+    int n = w->imp_n[env];
+    for (int k = 0; k < n && k < cap; ++k) memcpy(out + 3 * k, w->imp[env] + 3 * k, 3 * sizeof(double));
+    *n_out = n;
+    return n > cap ? -1 : 0;
+}
