@@ -1,0 +1,268 @@
+/*
+ * fw.h -- C ABI of libfw, a single-GPU (sm_103a) implementation of the batched
+ * contact-simulation substep of Factory (Narang et al., arXiv 2205.03532, Sec. III):
+ *
+ *   (a) SDF narrow phase: surface sample points of one body are transformed into the
+ *       other body's frame and looked up in its voxel signed-distance field
+ *       (trilinear value + gradient), Sec. III-A;
+ *   (b) contact reduction of the candidates into normal-similar patches,
+ *       Sec. III-C and Algorithm 1;
+ *   (c) a Gauss-Seidel contact solve with Coulomb friction and substepped
+ *       integration, Sec. III-B (the paper cites the solver; the update rule used here
+ *       is stated at fw_step).
+ *
+ * Conventions for every call:
+ *   - Units are SI (metres, seconds, kilograms).  Quaternions are (x, y, z, w).
+ *   - Every input array is COPIED; the caller keeps ownership of its buffers.
+ *   - Output arrays are caller-owned.  Where a call takes `device_ptrs`, 0 means host
+ *     pointers and 1 means device pointers (for example torch CUDA tensors) on the
+ *     world's device.
+ *   - Nothing throws across the ABI.  Every call returns an fw_status; on failure
+ *     fw_last_error() holds a message.  A NULL world returns FW_ERR_ARG.
+ *   - A world is used by one host thread at a time.  GPU work is enqueued on the
+ *     world's stream (fw_config.cuda_stream, or a stream the world creates) and is
+ *     stream-ordered; calls that return data to host memory synchronise that stream.
+ *   - Device-side problems (non-finite state, a contact buffer overflow) set a status
+ *     word on the device; fw_sync() and every synchronising call report it.
+ */
+#ifndef FW_H
+#define FW_H
+
+#if defined(__GNUC__)
+#define FW_API __attribute__((visibility("default")))
+#else
+#define FW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fw_world fw_world;   /* opaque; owned by the library */
+
+typedef enum {
+    FW_OK = 0,
+    FW_ERR_ARG = -1,            /* bad argument (NULL pointer, size, id out of range) */
+    FW_ERR_OOM = -2,            /* device or host allocation failed */
+    FW_ERR_CUDA = -3,           /* a CUDA runtime call failed (message in fw_last_error) */
+    FW_ERR_STATE = -4,          /* call out of order (e.g. SDF body without a baked SDF) */
+    FW_ERR_NONFINITE = -5,      /* a body state became NaN/Inf on the device */
+    FW_ERR_OVERFLOW = -6,       /* an output buffer was too small */
+    FW_ERR_TIMEOUT = -7,        /* a bounded device wait gave up */
+    FW_ERR_DEVICE_BOUNDS = -8   /* a device-side index check failed */
+} fw_status;
+
+typedef enum {
+    FW_BODY_STATIC = 0,         /* never moves; infinite mass */
+    FW_BODY_KINEMATIC = 1,      /* moves with its prescribed linvel/angvel; infinite mass */
+    FW_BODY_DYNAMIC = 2,        /* free rigid body */
+    FW_BODY_FIXED_AXIS = 3      /* centre of mass fixed; spins about `axis` only (gears) */
+} fw_body_type;
+
+/* Simulation constants.  The paper states none of these except the frame time and the
+ * batch size; the defaults are this library's readings (fw_config_default). */
+typedef struct {
+    float gravity[3];           /* m/s^2, default (0, 0, -9.81) */
+    float dt;                   /* frame time, default 1/60 s (Table perf caption) */
+    float contact_offset;       /* candidate iff phi < contact_offset; default 1e-4 m */
+    float cos_patch;            /* normal similarity for Assign/BinReduce; default 0.97 */
+    int max_patches;            /* N of Sec. III-C (128 <= N <= 256); default 128 */
+    int batch_size;             /* samples per Generate batch; must be 1024 (Sec. III-C) */
+    float baumgarte;            /* bias factor for penetrating contacts; default 0.2 */
+    int n_vel_iters;            /* bias-free sweeps after integration; default 0 */
+    float max_angvel;           /* |omega| clamp at integration, 0 = off; default 0 */
+    int sdf_fp16;               /* 1: look up FP16 copies of the grids (phi/h); default 0 */
+    int device;                 /* CUDA device ordinal, default 0 */
+    void *cuda_stream;          /* cudaStream_t to enqueue on, NULL: the world's own */
+} fw_config;
+
+/* One body of an environment.  104 bytes, no padding. */
+typedef struct {
+    int asset;                  /* asset id from fw_add_mesh_asset */
+    int type;                   /* fw_body_type */
+    float mass;                 /* kg; <= 0: from the asset's density (inertia scales) */
+    float mu;                   /* friction coefficient; a pair uses sqrt(mu_a mu_b) */
+    float pos[3];               /* world position of the asset frame */
+    float quat[4];              /* world orientation of the asset frame (x, y, z, w) */
+    float linvel[3];            /* centre-of-mass velocity */
+    float angvel[3];            /* angular velocity (world) */
+    float axis[3];              /* FIXED_AXIS: world spin axis */
+    float force[3];             /* constant applied force at the centre of mass */
+    float torque[3];            /* constant applied torque (world) */
+} fw_body_desc;
+
+/* A reduced contact as returned to callers.  52 bytes. */
+typedef struct {
+    int sample;                 /* index of the point in the point body's sample list */
+    int patch;                  /* patch slot the contact came from */
+    int pair;                   /* pair index within its environment */
+    float phi;                  /* signed distance of the sample from body B (m) */
+    float xa[3];                /* contact point on body A (world) */
+    float xb[3];                /* xa - phi * n (world) */
+    float n[3];                 /* unit normal out of body B toward body A (world) */
+} fw_contact;
+
+/* A reduction input for fw_reduce.  32 bytes. */
+typedef struct {
+    int sample;
+    float phi;
+    float x[3];
+    float n[3];
+} fw_candidate;
+
+/* ---------------------------------------------------------------- world lifetime */
+
+/* Fills *cfg with the defaults listed in fw_config. */
+FW_API void fw_config_default(fw_config *cfg);
+
+/* Creates a world on cfg->device.  *out receives the handle (NULL on failure).
+ * Errors: FW_ERR_ARG for batch_size != 1024, max_patches outside 1..256, dt <= 0. */
+FW_API fw_status fw_create(const fw_config *cfg, fw_world **out);
+
+/* Frees every device and host resource of the world.  NULL is accepted. */
+FW_API fw_status fw_destroy(fw_world *w);
+
+/* ---------------------------------------------------------------- assets */
+
+/* Adds a closed, outward-wound triangle mesh (verts n_verts x 3, tris n_tris x 3, both
+ * row-major host arrays).  sample_pts (n_samples x 3, asset frame, may be NULL when the
+ * asset is only ever an SDF body) are the points queried against other bodies' SDFs
+ * (Sec. II-A1 and III-A: surface points of the mesh body are tested against the SDF of
+ * the other body); their order defines the sample index and the Generate batches of
+ * Algorithm 1.  Mass, centre of mass and inertia come from the divergence theorem at
+ * `density` (kg/m^3).  Errors: FW_ERR_ARG for bad sizes, n_samples > 2^24, or a mesh
+ * enclosing no volume. */
+FW_API fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const int *tris,
+                                   int n_tris, const float *sample_pts, int n_samples,
+                                   float density, int *asset_id_out);
+
+/* Bakes the asset's SDF on the GPU once, at set-up (Sec. III-A: the SDF is sampled from
+ * the triangle mesh when the object is created).  Node-centred grid over the box padded
+ * by padding_m; `resolution` nodes along the longest padded axis (the per-asset SDF
+ * resolution of the appendix on using the contact methods); cubic = 1 gives
+ * resolution^3 nodes.  h, lo are float32: h = fl(L / (res - 1)),
+ * lo_a = fl(centre_a - h (dims_a - 1) / 2).  Value at a node: -(distance) inside the
+ * solid, +(distance) outside; distance to the closest triangle found in float32 and
+ * re-evaluated in float64, sign from the closest feature's angle-weighted pseudonormal
+ * (float64 winding number where that test is ambiguous).  Synchronous.
+ * Errors: FW_ERR_ARG (resolution < 2), FW_ERR_OOM. */
+FW_API fw_status fw_bake_sdf(fw_world *w, int asset_id, int resolution, float padding_m, int cubic);
+
+/* Installs a caller-made SDF grid instead of baking (values: host, dims[2] x dims[1] x
+ * dims[0], x fastest).  Used to test the lookup on exactly known grids. */
+FW_API fw_status fw_set_sdf(fw_world *w, int asset_id, const float lo[3], float h,
+                            const int dims[3], const float *values);
+
+/* Reads back the grid placement and, if values != NULL, the float32 node values (host
+ * array of dims product). */
+FW_API fw_status fw_get_sdf(fw_world *w, int asset_id, float lo[3], float *h, int dims[3],
+                            float *values);
+
+/* Mass properties used for the asset (density based): mass, centre of mass (asset
+ * frame) and inertia about it (row-major 3x3), host arrays. */
+FW_API fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3],
+                             double inertia[9]);
+
+/* ---------------------------------------------------------------- environments */
+
+/* Adds n_envs environments of n_per_env bodies each (per_env: n_envs x n_per_env
+ * descriptors, env-major; 1..8 bodies) and n_pairs contact pairs per environment
+ * (pairs: n_pairs x 2 local body ids (a, b), 0..63 pairs); a is queried with its sample
+ * points against b's SDF (appendix on using the contact methods: the body with the
+ * SDF is queried by the other body's mesh).  Envs are independent.  May be called
+ * several times with different structures (uneven batches).  *first_env_out receives
+ * the id of the first new env.  Errors: FW_ERR_STATE if a b body's asset has no SDF or
+ * an a body's asset has no samples; FW_ERR_ARG for bad ids or sizes. */
+FW_API fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *per_env,
+                                   int n_per_env, const int *pairs, int n_pairs,
+                                   int *first_env_out);
+
+/* ---------------------------------------------------------------- stepping */
+
+/* Advances every environment by one frame dt as n_substeps substeps of
+ * hs = dt / n_substeps.  Each substep: external forces (gravity, applied force and
+ * torque, gyroscopic term); contact detection and reduction at the current poses;
+ * constraint rows per contact (normal, two tangents, effective masses, bias
+ * phi/hs if phi > 0 else baumgarte*phi/hs); n_iters Gauss-Seidel sweeps, each contact's
+ * normal impulse clamped to >= 0 and then its two friction impulses projected jointly
+ * on the disk of radius mu * normal impulse; semi-implicit Euler integration of the
+ * centre of mass and q <- normalize(q + hs/2 (omega,0) q); n_vel_iters bias-free sweeps.
+ * Enqueued as one CUDA graph (captured on first use for a given (n_substeps, n_iters)
+ * and topology); does not synchronise.
+ * Errors: FW_ERR_ARG for n_substeps < 1 or n_iters < 0. */
+FW_API fw_status fw_step(fw_world *w, int n_substeps, int n_iters);
+
+/* One substep of length hs.  detect = 0 reuses the contacts now in the contact buffer
+ * (from fw_collide or fw_set_contacts).  Enqueued; does not synchronise. */
+FW_API fw_status fw_substep(fw_world *w, float hs, int n_iters, int detect);
+
+/* Contact detection and reduction at the current poses, into the contact buffer. */
+FW_API fw_status fw_collide(fw_world *w);
+
+/* Contacts of one env from the contact buffer, pairs in order (host array; synchronises).
+ * Errors: FW_ERR_OVERFLOW when more than cap (n_out still receives the count). */
+FW_API fw_status fw_get_contacts(fw_world *w, int env, fw_contact *out, int cap, int *n_out);
+
+/* Replaces the contacts of one env (host array; `pair` selects the pair of each one;
+ * the contacts of a pair must be contiguous and in sweep order).  For solving given
+ * contacts with fw_substep(detect = 0). */
+FW_API fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int n);
+
+/* ---------------------------------------------------------------- state */
+
+/* Body state of all bodies (global body order = env order, then body order):
+ * pos n x 3, quat n x 4, linvel n x 3, angvel n x 3 (float32).  Any pointer may be NULL
+ * to skip it.  device_ptrs = 0 synchronises. */
+FW_API fw_status fw_get_state(fw_world *w, float *pos, float *quat, float *linvel,
+                              float *angvel, int device_ptrs);
+/* Sets the state; quaternions are normalised on the device.  device_ptrs = 0 synchronises
+ * before returning so host buffers may be reused. */
+FW_API fw_status fw_set_state(fw_world *w, const float *pos, const float *quat,
+                              const float *linvel, const float *angvel, int device_ptrs);
+
+/* ---------------------------------------------------------------- test hooks */
+
+/* Trilinear SDF value and gradient of an asset's grid at n points given in the asset
+ * frame (Sec. III-A); phi n, grad n x 3.  Points outside the grid give phi = +inf and
+ * grad = 0.  Synchronises when device_ptrs = 0. */
+FW_API fw_status fw_query_sdf(fw_world *w, int asset_id, const float *pts, int n, float *phi,
+                              float *grad, int device_ptrs);
+
+/* The narrow phase of one pair at the current poses, for every sample point of body a:
+ * phi (n_samples) and the world normal (n_samples x 3); phi = +inf where the point is
+ * outside the grid or the gradient vanishes.  Same device code as the step. */
+FW_API fw_status fw_query_pair(fw_world *w, int env, int pair, float *phi, float *normal,
+                               int device_ptrs);
+
+/* Algorithm 1 on a caller-given candidate list (host array, any order, unique samples)
+ * with the world's cos_patch and max_patches: the same device code as the step's
+ * reduction.  Outputs contacts (host, pair = 0) and the number of patches. */
+FW_API fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_contact *out,
+                           int cap, int *n_out, int *n_patches);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Waits for the world's stream and reports the device status word. */
+FW_API fw_status fw_sync(fw_world *w);
+
+/* Per-kernel timing.  enable = 1 makes later fw_step calls launch their kernels
+ * directly (no graph) with a CUDA event pair around each launch; fw_get_timings then
+ * synchronises and returns, summed over the launches since the previous call:
+ * ms[0] detection + reduction kernel ms, ms[1] solve + integration kernel ms,
+ * ms[2] number of detection launches, ms[3] number of solve launches (n >= 4). */
+FW_API fw_status fw_set_timing(fw_world *w, int enable);
+FW_API fw_status fw_get_timings(fw_world *w, float *ms, int n);
+
+/* Sizes: n_envs, n_bodies, n_pairs (any pointer may be NULL). */
+FW_API fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs);
+
+/* Number of kernel launches one fw_step(n_substeps, ...) enqueues. */
+FW_API int fw_launches_per_step(fw_world *w, int n_substeps);
+
+/* Message of the last failed call on this world (never NULL). */
+FW_API const char *fw_last_error(const fw_world *w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FW_H */

@@ -868,6 +868,52 @@ static void ensure_nodes(or_world *w) {
     }
 }
 
+/* narrow phase of one pair, every sample: phi and world normal (valid = 0 where the
+ * sample is outside the grid or the gradient vanishes) */
+int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid) {
+    ensure_nodes(w);
+    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
+    const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
+    double RA[9], RB[9], RBt[9];
+    q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+    for (int i = 0; i < aa->ns; ++i) {
+        double s[3], xw[3], xb[3], d[3], g[3], f;
+        load3(aa->S + 3 * i, s);
+        m_vec(RA, s, xw); v_add(xw, A->p, xw);
+        v_sub(xw, B->p, d); m_vec(RBt, d, xb);
+        int ok = trilinear(&ab->grid, xb, &f, g, NULL);
+        double gn = ok ? v_norm(g) : 0.0;
+        valid[i] = ok && gn >= 1e-12;
+        phi[i] = valid[i] ? f : 0.0;
+        for (int a = 0; a < 3; ++a) nrm[3 * i + a] = 0.0;
+        if (valid[i]) {
+            double nb[3];
+            v_scale(g, 1.0 / gn, nb);
+            m_vec(RB, nb, nrm + 3 * i);
+        }
+    }
+    return 0;
+}
+
+/* the candidates of one pair (Generate of Algorithm 1), rounded to float */
+int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int cap, int *n_out) {
+    ensure_nodes(w);
+    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const asset_t *aa = &w->assets[w->bodies[P->a].asset];
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (aa->ns > 0 ? aa->ns : 1));
+    margin_t m = {INFINITY, INFINITY};
+    int n = generate_candidates(w, P, c, &m);
+    for (int i = 0; i < n && i < cap; ++i) {
+        out[i].sample = c[i].idx;
+        out[i].phi = (float)c[i].phi;
+        for (int a = 0; a < 3; ++a) { out[i].x[a] = (float)c[i].x[a]; out[i].n[a] = (float)c[i].n[a]; }
+    }
+    *n_out = n;
+    free(c);
+    return n > cap ? -1 : 0;
+}
+
 int or_collide(or_world *w) {
     ensure_nodes(w);
 #ifdef _OPENMP

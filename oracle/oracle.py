@@ -95,6 +95,8 @@ def lib():
             L.or_get_state.argtypes = [vp, _f64, _f64, _f64, _f64]
             L.or_set_state.argtypes = [vp, _f64, _f64, _f64, _f64]
             L.or_get_impulses.argtypes = [vp, C.c_int, _f64, C.c_int, C.POINTER(C.c_int)]
+            L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32]
+            L.or_pair_candidates.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
             L.or_reduce.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, vp, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]
@@ -300,6 +302,17 @@ class OracleWorld:
     def set_state(self, p, q, v, w):
         f = lambda a, k: np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1, k))
         lib().or_set_state(self.h, f(p, 3), f(q, 4), f(v, 3), f(w, 3))
+
+    def query_pair(self, env: int, pair: int, n_samples: int):
+        phi, nrm, valid = np.zeros(n_samples), np.zeros((n_samples, 3)), np.zeros(n_samples, np.int32)
+        lib().or_query_pair(self.h, env, pair, phi, nrm, valid)
+        return phi, nrm, valid.astype(bool)
+
+    def pair_candidates(self, env: int, pair: int, cap: int = 1 << 20) -> np.ndarray:
+        out = np.zeros(cap, CANDIDATE_DTYPE)
+        n = C.c_int()
+        lib().or_pair_candidates(self.h, env, pair, out.ctypes.data, cap, C.byref(n))
+        return out[: min(n.value, cap)].copy()
 
     def impulses(self, env: int) -> np.ndarray:
         cap = 8192

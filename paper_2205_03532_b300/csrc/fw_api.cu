@@ -1,0 +1,999 @@
+// fw_api.cu -- host implementation of the C ABI declared in include/fw.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fw_internal.h"
+
+using namespace fw;
+
+namespace {
+
+struct AssetHost {
+    std::vector<float> V;
+    std::vector<int> T;
+    std::vector<float> S;   // samples, 3 per point
+    double density = 0, mass = 0, com[3] = {0, 0, 0}, I[9] = {0};
+    float4 *d_samples = nullptr;
+    bool has_sdf = false;
+    float lo[3] = {0, 0, 0}, h = 0;
+    int dims[3] = {0, 0, 0};
+    float *d_grid = nullptr;
+    __half *d_grid16 = nullptr;
+};
+
+}  // namespace
+
+struct fw_world {
+    fw_config cfg;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    bool own_stream = false;
+    std::vector<AssetHost> assets;
+    AssetDev *d_assets = nullptr;
+    // topology and initial state (host)
+    std::vector<BodyProps> props;
+    std::vector<PairDev> pairs;
+    std::vector<EnvDev> envs;
+    std::vector<float> h_pos, h_quat, h_vel, h_ang;
+    // device
+    BodyProps *d_props = nullptr;
+    PairDev *d_pairs = nullptr;
+    EnvDev *d_envs = nullptr;
+    float *d_pos = nullptr, *d_quat = nullptr, *d_vel = nullptr, *d_ang = nullptr;
+    DContact *d_contacts = nullptr;
+    int *d_counts = nullptr;
+    float4 *d_scratch = nullptr;
+    Row *d_rows = nullptr;
+    unsigned *d_status = nullptr;
+    int dev_bodies = 0;          // bodies whose state is on the device
+    bool topo_dirty = true, assets_dirty = true;
+    long long scratch_len = 0, rows_len = 0;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int g_sub = -1, g_iters = -1;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_used;   // triples per substep
+    std::string err;
+};
+
+namespace {
+
+fw_status fail(fw_world *w, fw_status s, const std::string &msg) {
+    if (w) w->err = msg;
+    return s;
+}
+fw_status cuda_fail(fw_world *w, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return fail(w, e == cudaErrorMemoryAllocation ? FW_ERR_OOM : FW_ERR_CUDA, m);
+}
+#define CK(expr)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (expr);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(w, e_, #expr);       \
+    } while (0)
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// ---- mass properties: polyhedral volume integrals of 1, x, y, z, x^2, y^2, z^2, xy, yz,
+// zx via the divergence theorem (Eberly, "Polyhedral Mass Properties (Revisited)").
+void mass_props(const std::vector<float> &V, const std::vector<int> &T, double density, double &mass,
+                double com[3], double I[9]) {
+    double in[10] = {0};
+    auto sub = [](double w0, double w1, double w2, double &f1, double &f2, double &f3, double &g0, double &g1,
+                  double &g2) {
+        const double t0 = w0 + w1;
+        f1 = t0 + w2;
+        const double t1 = w0 * w0;
+        const double t2 = t1 + w1 * t0;
+        f2 = t2 + w2 * f1;
+        f3 = w0 * t1 + w1 * t2 + w2 * f2;
+        g0 = f2 + w0 * (f1 + w0);
+        g1 = f2 + w1 * (f1 + w1);
+        g2 = f2 + w2 * (f1 + w2);
+    };
+    for (size_t t = 0; t < T.size() / 3; ++t) {
+        const float *p0 = &V[3 * T[3 * t]], *p1 = &V[3 * T[3 * t + 1]], *p2 = &V[3 * T[3 * t + 2]];
+        const double x0 = p0[0], y0 = p0[1], z0 = p0[2], x1 = p1[0], y1 = p1[1], z1 = p1[2];
+        const double x2 = p2[0], y2 = p2[1], z2 = p2[2];
+        const double a1 = x1 - x0, b1 = y1 - y0, c1 = z1 - z0, a2 = x2 - x0, b2 = y2 - y0, c2 = z2 - z0;
+        const double d0 = b1 * c2 - b2 * c1, d1 = a2 * c1 - a1 * c2, d2 = a1 * b2 - a2 * b1;
+        double f1x, f2x, f3x, g0x, g1x, g2x, f1y, f2y, f3y, g0y, g1y, g2y, f1z, f2z, f3z, g0z, g1z, g2z;
+        sub(x0, x1, x2, f1x, f2x, f3x, g0x, g1x, g2x);
+        sub(y0, y1, y2, f1y, f2y, f3y, g0y, g1y, g2y);
+        sub(z0, z1, z2, f1z, f2z, f3z, g0z, g1z, g2z);
+        in[0] += d0 * f1x;
+        in[1] += d0 * f2x; in[2] += d1 * f2y; in[3] += d2 * f2z;
+        in[4] += d0 * f3x; in[5] += d1 * f3y; in[6] += d2 * f3z;
+        in[7] += d0 * (y0 * g0x + y1 * g1x + y2 * g2x);
+        in[8] += d1 * (z0 * g0y + z1 * g1y + z2 * g2y);
+        in[9] += d2 * (x0 * g0z + x1 * g1z + x2 * g2z);
+    }
+    in[0] /= 6.0;
+    for (int k = 1; k <= 3; ++k) in[k] /= 24.0;
+    for (int k = 4; k <= 6; ++k) in[k] /= 60.0;
+    for (int k = 7; k <= 9; ++k) in[k] /= 120.0;
+    const double m = in[0];
+    const double cx = in[1] / m, cy = in[2] / m, cz = in[3] / m;
+    const double Ixx = in[5] + in[6] - m * (cy * cy + cz * cz);
+    const double Iyy = in[4] + in[6] - m * (cz * cz + cx * cx);
+    const double Izz = in[4] + in[5] - m * (cx * cx + cy * cy);
+    const double Ixy = -(in[7] - m * cx * cy);
+    const double Iyz = -(in[8] - m * cy * cz);
+    const double Ixz = -(in[9] - m * cz * cx);
+    mass = m * density;
+    com[0] = cx; com[1] = cy; com[2] = cz;
+    const double M[9] = {Ixx, Ixy, Ixz, Ixy, Iyy, Iyz, Ixz, Iyz, Izz};
+    for (int k = 0; k < 9; ++k) I[k] = M[k] * density;
+}
+
+bool inv3(const double A[9], double B[9]) {
+    const double c0 = A[4] * A[8] - A[5] * A[7], c1 = A[5] * A[6] - A[3] * A[8], c2 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+    if (!(std::fabs(det) > 0)) return false;
+    const double id = 1.0 / det;
+    B[0] = c0 * id; B[3] = c1 * id; B[6] = c2 * id;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) * id; B[4] = (A[0] * A[8] - A[2] * A[6]) * id; B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) * id; B[5] = (A[2] * A[3] - A[0] * A[5]) * id; B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
+// ---- grid placement: padded bounding box; h = fl32(L / (res - 1)) with L the longest
+// padded extent; lo_a = fl32(centre_a - h (dims_a - 1) / 2)
+void grid_placement(const std::vector<float> &V, int res, float pad, int cubic, float lo[3], float &h, int dims[3]) {
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = 0; i < V.size() / 3; ++i)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min(mn[a], (double)V[3 * i + a]);
+            mx[a] = std::max(mx[a], (double)V[3 * i + a]);
+        }
+    double ext[3], L = 0;
+    for (int a = 0; a < 3; ++a) {
+        ext[a] = (mx[a] - mn[a]) + 2.0 * (double)pad;
+        L = std::max(L, ext[a]);
+    }
+    h = (float)(L / (double)(res - 1));
+    for (int a = 0; a < 3; ++a) {
+        dims[a] = cubic ? res : (int)std::ceil(ext[a] / (double)h - 1e-9) + 1;
+        lo[a] = (float)(0.5 * (mn[a] + mx[a]) - (double)h * (double)(dims[a] - 1) * 0.5);
+    }
+}
+
+AssetDev asset_view(const AssetHost &A, bool fp16) {
+    AssetDev g;
+    memset(&g, 0, sizeof g);
+    g.samples = A.d_samples;
+    g.ns = (int)(A.S.size() / 3);
+    g.grid = A.d_grid;
+    g.grid16 = fp16 ? A.d_grid16 : nullptr;
+    for (int a = 0; a < 3; ++a) { g.lo[a] = A.lo[a]; g.dims[a] = A.dims[a]; }
+    g.h = A.h;
+    const double ih = A.h > 0 ? 1.0 / (double)A.h : 0.0;
+    g.inv_h = (float)ih;
+    g.inv_h_lo = (float)(ih - (double)g.inv_h);
+    return g;
+}
+
+void drop_graph(fw_world *w) {
+    if (w->gexec) cudaGraphExecDestroy(w->gexec);
+    w->gexec = nullptr;
+}
+
+fw_status upload_assets(fw_world *w) {
+    if (!w->assets_dirty) return FW_OK;
+    std::vector<AssetDev> v;
+    for (auto &A : w->assets) v.push_back(asset_view(A, w->cfg.sdf_fp16 != 0 && A.d_grid16));
+    dfree(w->d_assets);
+    if (!v.empty()) {
+        CK(cudaMalloc(&w->d_assets, sizeof(AssetDev) * v.size()));
+        CK(cudaMemcpy(w->d_assets, v.data(), sizeof(AssetDev) * v.size(), cudaMemcpyHostToDevice));
+    }
+    w->assets_dirty = false;
+    drop_graph(w);
+    return FW_OK;
+}
+
+int cap_pair(const fw_world *w) { return w->cfg.max_patches * kSlots; }
+
+// (Re)builds the device copies of the topology, keeping the device state of bodies that
+// are already there.
+fw_status ensure_device(fw_world *w) {
+    fw_status st = upload_assets(w);
+    if (st != FW_OK) return st;
+    if (!w->topo_dirty) return FW_OK;
+    const int nb = (int)w->props.size();
+    if (w->dev_bodies > 0) {   // keep the live state of existing bodies
+        CK(cudaStreamSynchronize(w->stream));
+        CK(cudaMemcpy(w->h_pos.data(), w->d_pos, sizeof(float) * 3 * w->dev_bodies, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(w->h_quat.data(), w->d_quat, sizeof(float) * 4 * w->dev_bodies, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(w->h_vel.data(), w->d_vel, sizeof(float) * 3 * w->dev_bodies, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(w->h_ang.data(), w->d_ang, sizeof(float) * 3 * w->dev_bodies, cudaMemcpyDeviceToHost));
+    }
+    dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
+    dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
+    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows);
+    const int np = (int)w->pairs.size(), ne = (int)w->envs.size();
+    const int cp = cap_pair(w);
+    if (nb > 0) {
+        CK(cudaMalloc(&w->d_props, sizeof(BodyProps) * nb));
+        CK(cudaMemcpy(w->d_props, w->props.data(), sizeof(BodyProps) * nb, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&w->d_pos, sizeof(float) * 3 * nb));
+        CK(cudaMalloc(&w->d_quat, sizeof(float) * 4 * nb));
+        CK(cudaMalloc(&w->d_vel, sizeof(float) * 3 * nb));
+        CK(cudaMalloc(&w->d_ang, sizeof(float) * 3 * nb));
+        CK(cudaMemcpy(w->d_pos, w->h_pos.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w->d_quat, w->h_quat.data(), sizeof(float) * 4 * nb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w->d_vel, w->h_vel.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w->d_ang, w->h_ang.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice));
+    }
+    if (np > 0) {
+        CK(cudaMalloc(&w->d_pairs, sizeof(PairDev) * np));
+        CK(cudaMemcpy(w->d_pairs, w->pairs.data(), sizeof(PairDev) * np, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&w->d_contacts, sizeof(DContact) * (size_t)np * cp));
+        CK(cudaMalloc(&w->d_counts, sizeof(int) * np));
+        CK(cudaMemset(w->d_counts, 0, sizeof(int) * np));
+        long long sl = 0;
+        for (auto &P : w->pairs)
+            sl = std::max(sl, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
+        w->scratch_len = std::max(sl, 2LL);
+        CK(cudaMalloc(&w->d_scratch, sizeof(float4) * w->scratch_len));
+    }
+    if (ne > 0) {
+        CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
+        CK(cudaMemcpy(w->d_envs, w->envs.data(), sizeof(EnvDev) * ne, cudaMemcpyHostToDevice));
+        long long rl = 0;
+        for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + E.row_cap);
+        w->rows_len = std::max(rl, 1LL);
+        CK(cudaMalloc(&w->d_rows, sizeof(Row) * w->rows_len));
+    }
+    w->dev_bodies = nb;
+    w->topo_dirty = false;
+    drop_graph(w);
+    return FW_OK;
+}
+
+SimParams sim_params(const fw_world *w, float hs, int n_iters) {
+    SimParams p;
+    memset(&p, 0, sizeof p);
+    p.assets = w->d_assets;
+    p.pairs = w->d_pairs;
+    p.envs = w->d_envs;
+    p.props = w->d_props;
+    p.pos = w->d_pos; p.quat = w->d_quat; p.linvel = w->d_vel; p.angvel = w->d_ang;
+    p.contacts = w->d_contacts;
+    p.counts = w->d_counts;
+    p.scratch = w->d_scratch;
+    p.rows = w->d_rows;
+    p.status = w->d_status;
+    p.n_pairs = (int)w->pairs.size();
+    p.n_envs = (int)w->envs.size();
+    p.cap_pair = cap_pair(w);
+    p.max_patches = w->cfg.max_patches;
+    p.contact_offset = w->cfg.contact_offset;
+    p.cos_patch = w->cfg.cos_patch;
+    p.baumgarte = w->cfg.baumgarte;
+    p.max_angvel = w->cfg.max_angvel;
+    for (int a = 0; a < 3; ++a) p.gravity[a] = w->cfg.gravity[a];
+    p.hs = hs;
+    p.n_iters = n_iters;
+    p.n_vel_iters = w->cfg.n_vel_iters;
+    return p;
+}
+
+fw_status check_status(fw_world *w) {
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, w->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(w->d_status, 0, sizeof st));
+        if (st & kStatusNonFinite) return fail(w, FW_ERR_NONFINITE, "a body state became non-finite");
+        if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts than fit");
+        if (st & kStatusBounds) return fail(w, FW_ERR_DEVICE_BOUNDS, "device index check failed");
+    }
+    return FW_OK;
+}
+
+cudaEvent_t take_event(fw_world *w) {
+    cudaEvent_t e;
+    if (!w->ev_pool.empty()) {
+        e = w->ev_pool.back();
+        w->ev_pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    w->ev_used.push_back(e);
+    return e;
+}
+
+fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs, int n_iters, bool detect,
+                           bool timed) {
+    SimParams p = sim_params(w, hs, n_iters);
+    for (int k = 0; k < n_substeps; ++k) {
+        if (timed) CK(cudaEventRecord(take_event(w), s));
+        if (detect) CK(launch_detect(p, s));
+        if (timed) CK(cudaEventRecord(take_event(w), s));
+        CK(launch_solve(p, s));
+        if (timed) CK(cudaEventRecord(take_event(w), s));
+    }
+    return FW_OK;
+}
+
+bool ready(fw_world *w) { return w && cudaSetDevice(w->cfg.device) == cudaSuccess; }
+
+}  // namespace
+
+// ===================================================================================== ABI
+extern "C" {
+
+void fw_config_default(fw_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->gravity[2] = -9.81f;
+    c->dt = 1.0f / 60.0f;
+    c->contact_offset = 1e-4f;
+    c->cos_patch = 0.97f;
+    c->max_patches = 128;
+    c->batch_size = kBatch;
+    c->baumgarte = 0.2f;
+    c->n_vel_iters = 0;
+    c->max_angvel = 0.0f;
+    c->sdf_fp16 = 0;
+    c->device = 0;
+    c->cuda_stream = nullptr;
+}
+
+fw_status fw_create(const fw_config *cfg, fw_world **out) {
+    if (!cfg || !out) return FW_ERR_ARG;
+    *out = nullptr;
+    if (cfg->batch_size != kBatch || cfg->max_patches < 1 || cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0))
+        return FW_ERR_ARG;
+    fw_world *w = new fw_world();
+    w->cfg = *cfg;
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e == cudaSuccess && cfg->cuda_stream) w->stream = (cudaStream_t)cfg->cuda_stream;
+    if (e == cudaSuccess && !cfg->cuda_stream) {
+        e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+        w->own_stream = (e == cudaSuccess);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(w->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = prepare_detect(cfg->max_patches);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fw_destroy(w);
+        return e == cudaErrorMemoryAllocation ? FW_ERR_OOM : FW_ERR_CUDA;
+    }
+    *out = w;
+    return FW_OK;
+}
+
+fw_status fw_destroy(fw_world *w) {
+    if (!w) return FW_OK;
+    cudaSetDevice(w->cfg.device);
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    drop_graph(w);
+    for (auto &A : w->assets) {
+        dfree(A.d_samples); dfree(A.d_grid); dfree(A.d_grid16);
+    }
+    dfree(w->d_assets);
+    dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
+    dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
+    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
+    for (auto e : w->ev_pool) cudaEventDestroy(e);
+    for (auto e : w->ev_used) cudaEventDestroy(e);
+    if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    if (w->own_stream && w->stream) cudaStreamDestroy(w->stream);
+    delete w;
+    return FW_OK;
+}
+
+fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const int *tris, int n_tris,
+                            const float *sample_pts, int n_samples, float density, int *asset_id_out) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (!verts || !tris || n_verts < 3 || n_tris < 1 || n_samples < 0 || n_samples > (1 << 24) ||
+        (n_samples > 0 && !sample_pts) || !(density > 0))
+        return fail(w, FW_ERR_ARG, "fw_add_mesh_asset: bad argument");
+    for (int i = 0; i < 3 * n_tris; ++i)
+        if (tris[i] < 0 || tris[i] >= n_verts) return fail(w, FW_ERR_ARG, "fw_add_mesh_asset: triangle index out of range");
+    AssetHost A;
+    A.V.assign(verts, verts + 3 * n_verts);
+    A.T.assign(tris, tris + 3 * n_tris);
+    if (n_samples > 0) A.S.assign(sample_pts, sample_pts + 3 * n_samples);
+    A.density = density;
+    mass_props(A.V, A.T, density, A.mass, A.com, A.I);
+    if (!(A.mass > 0)) return fail(w, FW_ERR_ARG, "fw_add_mesh_asset: mesh encloses no volume (winding?)");
+    if (n_samples > 0) {
+        std::vector<float4> s4(n_samples);
+        for (int i = 0; i < n_samples; ++i) s4[i] = make_float4(A.S[3 * i], A.S[3 * i + 1], A.S[3 * i + 2], 0.f);
+        CK(cudaMalloc(&A.d_samples, sizeof(float4) * n_samples));
+        CK(cudaMemcpy(A.d_samples, s4.data(), sizeof(float4) * n_samples, cudaMemcpyHostToDevice));
+    }
+    w->assets.push_back(std::move(A));
+    w->assets_dirty = true;
+    if (asset_id_out) *asset_id_out = (int)w->assets.size() - 1;
+    return FW_OK;
+}
+
+fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3], double inertia[9]) {
+    if (!w || asset_id < 0 || asset_id >= (int)w->assets.size()) return fail(w, FW_ERR_ARG, "bad asset");
+    const AssetHost &A = w->assets[asset_id];
+    if (mass) *mass = A.mass;
+    if (com) memcpy(com, A.com, sizeof A.com);
+    if (inertia) memcpy(inertia, A.I, sizeof A.I);
+    return FW_OK;
+}
+
+static fw_status finish_grid(fw_world *w, AssetHost &A) {
+    const long long n = (long long)A.dims[0] * A.dims[1] * A.dims[2];
+    dfree(A.d_grid16);
+    CK(cudaMalloc(&A.d_grid16, sizeof(__half) * n));
+    CK(launch_to_half(A.d_grid, A.d_grid16, 1.0f / A.h, n, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    A.has_sdf = true;
+    w->assets_dirty = true;
+    return FW_OK;
+}
+
+fw_status fw_bake_sdf(fw_world *w, int asset_id, int resolution, float padding_m, int cubic) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (asset_id < 0 || asset_id >= (int)w->assets.size() || resolution < 2 || !(padding_m >= 0))
+        return fail(w, FW_ERR_ARG, "fw_bake_sdf: bad argument");
+    AssetHost &A = w->assets[asset_id];
+    grid_placement(A.V, resolution, padding_m, cubic, A.lo, A.h, A.dims);
+    const int nt = (int)A.T.size() / 3;
+    const int nv = (int)A.V.size() / 3;
+    // triangles in Morton order of their centroids, so that shared-memory tiles are compact
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min(mn[a], (double)A.V[3 * i + a]);
+            mx[a] = std::max(mx[a], (double)A.V[3 * i + a]);
+        }
+    auto spread = [](unsigned v) {
+        v &= 0x3FF;
+        v = (v | (v << 16)) & 0x030000FF;
+        v = (v | (v << 8)) & 0x0300F00F;
+        v = (v | (v << 4)) & 0x030C30C3;
+        v = (v | (v << 2)) & 0x09249249;
+        return v;
+    };
+    std::vector<std::pair<unsigned, int>> order(nt);
+    for (int t = 0; t < nt; ++t) {
+        unsigned q[3];
+        for (int a = 0; a < 3; ++a) {
+            const double c = (A.V[3 * A.T[3 * t] + a] + A.V[3 * A.T[3 * t + 1] + a] + A.V[3 * A.T[3 * t + 2] + a]) / 3.0;
+            const double u = (c - mn[a]) / std::max(mx[a] - mn[a], 1e-30);
+            q[a] = (unsigned)std::min(1023.0, std::max(0.0, std::floor(u * 1023.999)));
+        }
+        order[t] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), t};
+    }
+    std::stable_sort(order.begin(), order.end());
+    // per triangle: vertices; unit face normal, edge and vertex pseudonormals
+    std::vector<double> fn(3 * (size_t)nt);
+    std::vector<double> vn(3 * (size_t)nv, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        const float *p[3] = {&A.V[3 * A.T[3 * t]], &A.V[3 * A.T[3 * t + 1]], &A.V[3 * A.T[3 * t + 2]]};
+        double e1[3], e2[3], n[3];
+        for (int a = 0; a < 3; ++a) { e1[a] = (double)p[1][a] - p[0][a]; e2[a] = (double)p[2][a] - p[0][a]; }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1]; n[1] = e1[2] * e2[0] - e1[0] * e2[2]; n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int a = 0; a < 3; ++a) fn[3 * t + a] = l > 0 ? n[a] / l : 0.0;
+        for (int k = 0; k < 3; ++k) {   // interior angle at corner k
+            const float *o = p[k], *u = p[(k + 1) % 3], *v = p[(k + 2) % 3];
+            double du[3], dv[3];
+            for (int a = 0; a < 3; ++a) { du[a] = (double)u[a] - o[a]; dv[a] = (double)v[a] - o[a]; }
+            const double cr[3] = {du[1] * dv[2] - du[2] * dv[1], du[2] * dv[0] - du[0] * dv[2], du[0] * dv[1] - du[1] * dv[0]};
+            const double ang = std::atan2(std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
+                                          du[0] * dv[0] + du[1] * dv[1] + du[2] * dv[2]);
+            for (int a = 0; a < 3; ++a) vn[3 * A.T[3 * t + k] + a] += ang * fn[3 * t + a];
+        }
+    }
+    std::map<std::pair<int, int>, int> edge_tri;
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) edge_tri[{A.T[3 * t + k], A.T[3 * t + (k + 1) % 3]}] = t;
+    std::vector<float> tri(9 * (size_t)nt), pn(21 * (size_t)nt);
+    const int ts = bake_tile_size();
+    const int ntile = (nt + ts - 1) / ts;
+    std::vector<float> box(6 * (size_t)ntile);
+    for (int tt = 0; tt < ntile; ++tt)
+        for (int a = 0; a < 3; ++a) { box[6 * tt + a] = 3e38f; box[6 * tt + 3 + a] = -3e38f; }
+    for (int s = 0; s < nt; ++s) {
+        const int t = order[s].second;
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const float c = A.V[3 * A.T[3 * t + k] + a];
+                tri[9 * (size_t)s + 3 * k + a] = c;
+                float &lo = box[6 * (s / ts) + a], &hi = box[6 * (s / ts) + 3 + a];
+                lo = std::min(lo, c);
+                hi = std::max(hi, c);
+            }
+        double nrm[7][3];
+        for (int a = 0; a < 3; ++a) nrm[0][a] = fn[3 * t + a];
+        for (int k = 0; k < 3; ++k) {   // edges ab, bc, ca: the two adjacent face normals
+            const int i0 = A.T[3 * t + k], i1 = A.T[3 * t + (k + 1) % 3];
+            auto it = edge_tri.find({i1, i0});
+            const int o = (it == edge_tri.end()) ? t : it->second;
+            double s3[3], l = 0;
+            for (int a = 0; a < 3; ++a) { s3[a] = fn[3 * t + a] + fn[3 * o + a]; l += s3[a] * s3[a]; }
+            l = std::sqrt(l);
+            for (int a = 0; a < 3; ++a) nrm[1 + k][a] = l > 0 ? s3[a] / l : fn[3 * t + a];
+        }
+        for (int k = 0; k < 3; ++k) {   // vertices a, b, c: angle-weighted face normals
+            const int vi = A.T[3 * t + k];
+            const double l = std::sqrt(vn[3 * vi] * vn[3 * vi] + vn[3 * vi + 1] * vn[3 * vi + 1] + vn[3 * vi + 2] * vn[3 * vi + 2]);
+            for (int a = 0; a < 3; ++a) nrm[4 + k][a] = l > 0 ? vn[3 * vi + a] / l : fn[3 * t + a];
+        }
+        for (int q = 0; q < 7; ++q)
+            for (int a = 0; a < 3; ++a) pn[21 * (size_t)s + 3 * q + a] = (float)nrm[q][a];
+    }
+    const long long n_nodes = (long long)A.dims[0] * A.dims[1] * A.dims[2];
+    float *d_tri = nullptr, *d_pn = nullptr, *d_box = nullptr;
+    int *d_flags = nullptr;
+    dfree(A.d_grid);
+    dfree(A.d_grid16);
+    CK(cudaMalloc(&A.d_grid, sizeof(float) * n_nodes));
+    CK(cudaMalloc(&d_tri, sizeof(float) * tri.size()));
+    CK(cudaMalloc(&d_pn, sizeof(float) * pn.size()));
+    CK(cudaMalloc(&d_box, sizeof(float) * box.size()));
+    CK(cudaMalloc(&d_flags, sizeof(int) * (n_nodes + 1)));
+    CK(cudaMemcpy(d_tri, tri.data(), sizeof(float) * tri.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_pn, pn.data(), sizeof(float) * pn.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_box, box.data(), sizeof(float) * box.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_flags, 0, sizeof(int)));
+    const AssetDev g = asset_view(A, false);
+    CK(launch_bake(d_tri, nt, d_pn, d_box, g, A.d_grid, d_flags, w->stream));
+    int nflag = 0;
+    CK(cudaMemcpyAsync(&nflag, d_flags, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    if (nflag > 0) CK(launch_bake_fix_sign(d_tri, nt, g, A.d_grid, d_flags + 1, nflag, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    cudaFree(d_tri); cudaFree(d_pn); cudaFree(d_box); cudaFree(d_flags);
+    return finish_grid(w, A);
+}
+
+fw_status fw_set_sdf(fw_world *w, int asset_id, const float lo[3], float h, const int dims[3], const float *values) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (asset_id < 0 || asset_id >= (int)w->assets.size() || !lo || !dims || !values || !(h > 0) || dims[0] < 2 ||
+        dims[1] < 2 || dims[2] < 2)
+        return fail(w, FW_ERR_ARG, "fw_set_sdf: bad argument");
+    AssetHost &A = w->assets[asset_id];
+    for (int a = 0; a < 3; ++a) { A.lo[a] = lo[a]; A.dims[a] = dims[a]; }
+    A.h = h;
+    const long long n = (long long)dims[0] * dims[1] * dims[2];
+    dfree(A.d_grid);
+    CK(cudaMalloc(&A.d_grid, sizeof(float) * n));
+    CK(cudaMemcpy(A.d_grid, values, sizeof(float) * n, cudaMemcpyHostToDevice));
+    return finish_grid(w, A);
+}
+
+fw_status fw_get_sdf(fw_world *w, int asset_id, float lo[3], float *h, int dims[3], float *values) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (asset_id < 0 || asset_id >= (int)w->assets.size()) return fail(w, FW_ERR_ARG, "fw_get_sdf: bad asset");
+    AssetHost &A = w->assets[asset_id];
+    if (!A.has_sdf) return fail(w, FW_ERR_STATE, "fw_get_sdf: asset has no SDF");
+    if (lo) for (int a = 0; a < 3; ++a) lo[a] = A.lo[a];
+    if (h) *h = A.h;
+    if (dims) for (int a = 0; a < 3; ++a) dims[a] = A.dims[a];
+    if (values) {
+        const long long n = (long long)A.dims[0] * A.dims[1] * A.dims[2];
+        CK(cudaMemcpy(values, A.d_grid, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    }
+    return FW_OK;
+}
+
+fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int n_per_env, const int *pairs,
+                            int n_pairs, int *first_env_out) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n_envs < 1 || !bd || n_per_env < 1 || n_per_env > 8 || n_pairs < 0 || n_pairs > 63 || (n_pairs > 0 && !pairs))
+        return fail(w, FW_ERR_ARG, "fw_add_env_bodies: bad sizes (1..8 bodies, 0..63 pairs per env)");
+    for (int k = 0; k < n_pairs; ++k) {
+        const int a = pairs[2 * k], b = pairs[2 * k + 1];
+        if (a < 0 || a >= n_per_env || b < 0 || b >= n_per_env || a == b)
+            return fail(w, FW_ERR_ARG, "fw_add_env_bodies: bad pair");
+    }
+    for (int i = 0; i < n_envs * n_per_env; ++i) {
+        const fw_body_desc &d = bd[i];
+        if (d.asset < 0 || d.asset >= (int)w->assets.size() || d.type < 0 || d.type > 3)
+            return fail(w, FW_ERR_ARG, "fw_add_env_bodies: bad body descriptor");
+    }
+    for (int e = 0; e < n_envs; ++e)
+        for (int k = 0; k < n_pairs; ++k) {
+            const AssetHost &Aa = w->assets[bd[e * n_per_env + pairs[2 * k]].asset];
+            const AssetHost &Ab = w->assets[bd[e * n_per_env + pairs[2 * k + 1]].asset];
+            if (Aa.S.empty()) return fail(w, FW_ERR_STATE, "fw_add_env_bodies: point body has no sample points");
+            if (!Ab.has_sdf) return fail(w, FW_ERR_STATE, "fw_add_env_bodies: SDF body has no baked SDF");
+        }
+    // validate everything before appending anything
+    for (int i = 0; i < n_envs * n_per_env; ++i) {
+        const fw_body_desc &d = bd[i];
+        const double qn = (double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] +
+                          (double)d.quat[2] * d.quat[2] + (double)d.quat[3] * d.quat[3];
+        const double an = (double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] + (double)d.axis[2] * d.axis[2];
+        if (!(qn > 0)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: zero quaternion");
+        if (d.type == FW_BODY_FIXED_AXIS && !(an > 0)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: zero axis");
+    }
+    const int e0 = (int)w->envs.size();
+    long long scratch = 0, rows = 0;
+    for (auto &P : w->pairs)
+        scratch = std::max(scratch, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
+    for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap);
+    for (int e = 0; e < n_envs; ++e) {
+        EnvDev E;
+        memset(&E, 0, sizeof E);
+        E.first_body = (int)w->props.size();
+        E.n_bodies = n_per_env;
+        E.first_pair = (int)w->pairs.size();
+        E.n_pairs = n_pairs;
+        E.row_off = (int)rows;
+        E.row_cap = n_pairs * cap_pair(w);
+        rows += E.row_cap;
+        for (int i = 0; i < n_per_env; ++i) {
+            const fw_body_desc &d = bd[e * n_per_env + i];
+            const AssetHost &A = w->assets[d.asset];
+            BodyProps P;
+            memset(&P, 0, sizeof P);
+            P.type = d.type;
+            P.asset = d.asset;
+            double scale = 1.0, mass = A.mass;
+            if (d.mass > 0.0f) { scale = (double)d.mass / A.mass; mass = d.mass; }
+            double Ib[9], Ii[9];
+            for (int k = 0; k < 9; ++k) Ib[k] = A.I[k] * scale;
+            if (!inv3(Ib, Ii)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: singular inertia");
+            P.mass = (float)mass;
+            P.invm = d.type == FW_BODY_DYNAMIC ? (float)(1.0 / mass) : 0.0f;
+            for (int a = 0; a < 3; ++a) P.com_b[a] = (float)A.com[a];
+            const int sym[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+            for (int k = 0; k < 6; ++k) {
+                P.Ib[k] = (float)Ib[3 * sym[k][0] + sym[k][1]];
+                P.Ib_inv[k] = (float)Ii[3 * sym[k][0] + sym[k][1]];
+            }
+            const double an = std::sqrt((double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] +
+                                        (double)d.axis[2] * d.axis[2]);
+            for (int a = 0; a < 3; ++a) {
+                P.axis[a] = an > 0 ? (float)(d.axis[a] / an) : 0.0f;
+                P.force[a] = d.force[a];
+                P.torque[a] = d.torque[a];
+            }
+            P.mu = d.mu;
+            w->props.push_back(P);
+            const double qn = std::sqrt((double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] +
+                                        (double)d.quat[2] * d.quat[2] + (double)d.quat[3] * d.quat[3]);
+            for (int a = 0; a < 3; ++a) w->h_pos.push_back(d.pos[a]);
+            for (int a = 0; a < 4; ++a) w->h_quat.push_back((float)(d.quat[a] / qn));
+            float v[3] = {d.linvel[0], d.linvel[1], d.linvel[2]}, om[3] = {d.angvel[0], d.angvel[1], d.angvel[2]};
+            if (d.type == FW_BODY_STATIC) { v[0] = v[1] = v[2] = 0; om[0] = om[1] = om[2] = 0; }
+            if (d.type == FW_BODY_FIXED_AXIS) {
+                const float s = om[0] * P.axis[0] + om[1] * P.axis[1] + om[2] * P.axis[2];
+                v[0] = v[1] = v[2] = 0;
+                for (int a = 0; a < 3; ++a) om[a] = s * P.axis[a];
+            }
+            for (int a = 0; a < 3; ++a) { w->h_vel.push_back(v[a]); w->h_ang.push_back(om[a]); }
+        }
+        for (int k = 0; k < n_pairs; ++k) {
+            PairDev P;
+            memset(&P, 0, sizeof P);
+            P.local_a = pairs[2 * k];
+            P.local_b = pairs[2 * k + 1];
+            P.a = E.first_body + P.local_a;
+            P.b = E.first_body + P.local_b;
+            P.asset_a = w->props[P.a].asset;
+            P.asset_b = w->props[P.b].asset;
+            P.env = e0 + e;
+            P.mu = (float)std::sqrt((double)w->props[P.a].mu * (double)w->props[P.b].mu);
+            P.scratch_off = (int)scratch;
+            scratch += 2LL * (long long)(w->assets[P.asset_a].S.size() / 3);
+            if (scratch > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many samples in total");
+            w->pairs.push_back(P);
+        }
+        w->envs.push_back(E);
+    }
+    w->topo_dirty = true;
+    if (first_env_out) *first_env_out = e0;
+    return FW_OK;
+}
+
+fw_status fw_step(fw_world *w, int n_substeps, int n_iters) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n_substeps < 1 || n_iters < 0) return fail(w, FW_ERR_ARG, "fw_step: bad substeps/iterations");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const float hs = w->cfg.dt / (float)n_substeps;
+    if (w->timing) return enqueue_substeps(w, w->stream, n_substeps, hs, n_iters, true, true);
+    if (!w->gexec || w->g_sub != n_substeps || w->g_iters != n_iters) {
+        drop_graph(w);
+        CK(cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const fw_status s2 = enqueue_substeps(w, w->cap_stream, n_substeps, hs, n_iters, true, false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(w->cap_stream, &g);
+        if (s2 != FW_OK) { if (g) cudaGraphDestroy(g); return s2; }
+        if (e != cudaSuccess) return cuda_fail(w, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&w->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { w->gexec = nullptr; return cuda_fail(w, e, "cudaGraphInstantiate"); }
+        w->g_sub = n_substeps;
+        w->g_iters = n_iters;
+    }
+    CK(cudaGraphLaunch(w->gexec, w->stream));
+    return FW_OK;
+}
+
+fw_status fw_substep(fw_world *w, float hs, int n_iters, int detect) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (!(hs > 0) || n_iters < 0) return fail(w, FW_ERR_ARG, "fw_substep: bad arguments");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    return enqueue_substeps(w, w->stream, 1, hs, n_iters, detect != 0, false);
+}
+
+fw_status fw_collide(fw_world *w) {
+    if (!ready(w)) return FW_ERR_ARG;
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const SimParams p = sim_params(w, w->cfg.dt, 0);
+    CK(launch_detect(p, w->stream));
+    return FW_OK;
+}
+
+fw_status fw_get_contacts(fw_world *w, int env, fw_contact *out, int cap, int *n_out) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size() || (cap > 0 && !out) || !n_out)
+        return fail(w, FW_ERR_ARG, "fw_get_contacts: bad argument");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const EnvDev &E = w->envs[env];
+    const int cp = cap_pair(w);
+    std::vector<int> counts(E.n_pairs);
+    CK(cudaMemcpyAsync(counts.data(), w->d_counts + E.first_pair, sizeof(int) * E.n_pairs, cudaMemcpyDeviceToHost,
+                       w->stream));
+    std::vector<DContact> dc((size_t)E.n_pairs * cp);
+    CK(cudaMemcpyAsync(dc.data(), w->d_contacts + (size_t)E.first_pair * cp, sizeof(DContact) * dc.size(),
+                       cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    int n = 0;
+    for (int k = 0; k < E.n_pairs; ++k)
+        for (int i = 0; i < std::min(counts[k], cp); ++i, ++n) {
+            if (n >= cap) continue;
+            const DContact &c = dc[(size_t)k * cp + i];
+            fw_contact &o = out[n];
+            o.sample = c.sample_patch & 0xFFFFFF;
+            o.patch = (int)((unsigned)c.sample_patch >> 24);
+            o.pair = k;
+            o.phi = c.phi;
+            for (int a = 0; a < 3; ++a) {
+                o.xa[a] = c.xa[a];
+                o.n[a] = c.n[a];
+                o.xb[a] = c.xa[a] - c.phi * c.n[a];
+            }
+        }
+    *n_out = n;
+    st = check_status(w);
+    if (st != FW_OK) return st;
+    return n > cap ? fail(w, FW_ERR_OVERFLOW, "fw_get_contacts: cap too small") : FW_OK;
+}
+
+fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int n) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size() || n < 0 || (n > 0 && !in))
+        return fail(w, FW_ERR_ARG, "fw_set_contacts: bad argument");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const EnvDev &E = w->envs[env];
+    const int cp = cap_pair(w);
+    std::vector<int> counts(E.n_pairs, 0);
+    std::vector<DContact> dc((size_t)E.n_pairs * cp);
+    int last_pair = 0;
+    for (int i = 0; i < n; ++i) {
+        const int k = in[i].pair;
+        if (k < 0 || k >= E.n_pairs || k < last_pair)
+            return fail(w, FW_ERR_ARG, "fw_set_contacts: pairs must be grouped in order");
+        last_pair = k;
+        if (counts[k] >= cp) return fail(w, FW_ERR_OVERFLOW, "fw_set_contacts: too many contacts for a pair");
+        DContact &c = dc[(size_t)k * cp + counts[k]++];
+        for (int a = 0; a < 3; ++a) { c.xa[a] = in[i].xa[a]; c.n[a] = in[i].n[a]; }
+        c.phi = in[i].phi;
+        c.sample_patch = (in[i].sample & 0xFFFFFF) | ((in[i].patch & 0xFF) << 24);
+    }
+    CK(cudaMemcpyAsync(w->d_counts + E.first_pair, counts.data(), sizeof(int) * E.n_pairs, cudaMemcpyHostToDevice,
+                       w->stream));
+    CK(cudaMemcpyAsync(w->d_contacts + (size_t)E.first_pair * cp, dc.data(), sizeof(DContact) * dc.size(),
+                       cudaMemcpyHostToDevice, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    return FW_OK;
+}
+
+fw_status fw_get_state(fw_world *w, float *pos, float *quat, float *linvel, float *angvel, int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const size_t nb = w->props.size();
+    const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (pos) CK(cudaMemcpyAsync(pos, w->d_pos, sizeof(float) * 3 * nb, k, w->stream));
+    if (quat) CK(cudaMemcpyAsync(quat, w->d_quat, sizeof(float) * 4 * nb, k, w->stream));
+    if (linvel) CK(cudaMemcpyAsync(linvel, w->d_vel, sizeof(float) * 3 * nb, k, w->stream));
+    if (angvel) CK(cudaMemcpyAsync(angvel, w->d_ang, sizeof(float) * 3 * nb, k, w->stream));
+    if (!device_ptrs) {
+        CK(cudaStreamSynchronize(w->stream));
+        return check_status(w);
+    }
+    return FW_OK;
+}
+
+fw_status fw_set_state(fw_world *w, const float *pos, const float *quat, const float *linvel, const float *angvel,
+                       int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const size_t nb = w->props.size();
+    const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (pos) CK(cudaMemcpyAsync(w->d_pos, pos, sizeof(float) * 3 * nb, k, w->stream));
+    if (quat) {
+        CK(cudaMemcpyAsync(w->d_quat, quat, sizeof(float) * 4 * nb, k, w->stream));
+        CK(launch_normalize_quats(w->d_quat, (int)nb, w->stream));
+    }
+    if (linvel) CK(cudaMemcpyAsync(w->d_vel, linvel, sizeof(float) * 3 * nb, k, w->stream));
+    if (angvel) CK(cudaMemcpyAsync(w->d_ang, angvel, sizeof(float) * 3 * nb, k, w->stream));
+    if (!device_ptrs) CK(cudaStreamSynchronize(w->stream));   // host buffers may be reused at return
+    return FW_OK;
+}
+
+fw_status fw_query_sdf(fw_world *w, int asset_id, const float *pts, int n, float *phi, float *grad, int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (asset_id < 0 || asset_id >= (int)w->assets.size() || n < 0 || (n > 0 && (!pts || !phi || !grad)))
+        return fail(w, FW_ERR_ARG, "fw_query_sdf: bad argument");
+    AssetHost &A = w->assets[asset_id];
+    if (!A.has_sdf) return fail(w, FW_ERR_STATE, "fw_query_sdf: asset has no SDF");
+    if (n == 0) return FW_OK;
+    const AssetDev g = asset_view(A, w->cfg.sdf_fp16 != 0);
+    if (device_ptrs) {
+        CK(launch_query_sdf(g, pts, n, phi, grad, w->stream));
+        return FW_OK;
+    }
+    float *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(float) * 7 * (size_t)n));
+    CK(cudaMemcpyAsync(d, pts, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, w->stream));
+    CK(launch_query_sdf(g, d, n, d + 3 * (size_t)n, d + 4 * (size_t)n, w->stream));
+    CK(cudaMemcpyAsync(phi, d + 3 * (size_t)n, sizeof(float) * n, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemcpyAsync(grad, d + 4 * (size_t)n, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    cudaFree(d);
+    return FW_OK;
+}
+
+fw_status fw_query_pair(fw_world *w, int env, int pair, float *phi, float *normal, int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size() || pair < 0 || pair >= w->envs[env].n_pairs || !phi || !normal)
+        return fail(w, FW_ERR_ARG, "fw_query_pair: bad argument");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const int pi = w->envs[env].first_pair + pair;
+    const int ns = (int)(w->assets[w->pairs[pi].asset_a].S.size() / 3);
+    const SimParams p = sim_params(w, w->cfg.dt, 0);
+    if (device_ptrs) {
+        CK(launch_query_pair(p, pi, phi, normal, w->stream, ns));
+        return FW_OK;
+    }
+    float *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(float) * 4 * (size_t)ns));
+    CK(launch_query_pair(p, pi, d, d + ns, w->stream, ns));
+    CK(cudaMemcpyAsync(phi, d, sizeof(float) * ns, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemcpyAsync(normal, d + ns, sizeof(float) * 3 * (size_t)ns, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    cudaFree(d);
+    return FW_OK;
+}
+
+fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_contact *out, int cap, int *n_out,
+                    int *n_patches) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n < 0 || (n > 0 && !cands) || !n_out || (cap > 0 && !out)) return fail(w, FW_ERR_ARG, "fw_reduce: bad argument");
+    std::vector<fw_candidate> c(cands, cands + n);
+    std::stable_sort(c.begin(), c.end(), [](const fw_candidate &a, const fw_candidate &b) { return a.sample < b.sample; });
+    int max_s = -1;
+    for (int i = 0; i < n; ++i) {
+        if (c[i].sample < 0 || c[i].sample >= (1 << 24)) return fail(w, FW_ERR_ARG, "fw_reduce: sample out of range");
+        if (i > 0 && c[i].sample == c[i - 1].sample) return fail(w, FW_ERR_ARG, "fw_reduce: duplicate sample");
+        max_s = std::max(max_s, c[i].sample);
+    }
+    const int cp = cap_pair(w);
+    float *d_c = nullptr;
+    float4 *d_scr = nullptr;
+    DContact *d_out = nullptr;
+    int *d_cnt = nullptr;
+    CK(cudaMalloc(&d_c, sizeof(fw_candidate) * std::max(n, 1)));
+    CK(cudaMalloc(&d_scr, sizeof(float4) * 2 * (size_t)(max_s + 2)));
+    CK(cudaMalloc(&d_out, sizeof(DContact) * cp));
+    CK(cudaMalloc(&d_cnt, sizeof(int) * 2));
+    if (n > 0) CK(cudaMemcpy(d_c, c.data(), sizeof(fw_candidate) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_cnt, 0, sizeof(int) * 2));
+    SimParams p = sim_params(w, w->cfg.dt, 0);
+    p.scratch = d_scr;
+    CK(launch_reduce_list(p, d_c, n, d_out, d_cnt, d_cnt + 1, w->stream));
+    int hc[2];
+    std::vector<DContact> h(cp);
+    CK(cudaMemcpyAsync(hc, d_cnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemcpyAsync(h.data(), d_out, sizeof(DContact) * cp, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    cudaFree(d_c); cudaFree(d_scr); cudaFree(d_out); cudaFree(d_cnt);
+    const int k = hc[0];
+    for (int i = 0; i < k && i < cap; ++i) {
+        fw_contact &o = out[i];
+        o.sample = h[i].sample_patch & 0xFFFFFF;
+        o.patch = (int)((unsigned)h[i].sample_patch >> 24);
+        o.pair = 0;
+        o.phi = h[i].phi;
+        for (int a = 0; a < 3; ++a) {
+            o.xa[a] = h[i].xa[a];
+            o.n[a] = h[i].n[a];
+            o.xb[a] = h[i].xa[a] - h[i].phi * h[i].n[a];
+        }
+    }
+    *n_out = k;
+    if (n_patches) *n_patches = hc[1];
+    const fw_status st = check_status(w);
+    if (st != FW_OK) return st;
+    return k > cap ? fail(w, FW_ERR_OVERFLOW, "fw_reduce: cap too small") : FW_OK;
+}
+
+fw_status fw_sync(fw_world *w) {
+    if (!ready(w)) return FW_ERR_ARG;
+    CK(cudaStreamSynchronize(w->stream));
+    return check_status(w);
+}
+
+fw_status fw_set_timing(fw_world *w, int enable) {
+    if (!w) return FW_ERR_ARG;
+    w->timing = enable != 0;
+    return FW_OK;
+}
+
+fw_status fw_get_timings(fw_world *w, float *ms, int n) {
+    if (!ready(w) || !ms || n < 4) return fail(w, FW_ERR_ARG, "fw_get_timings: need 4 outputs");
+    CK(cudaStreamSynchronize(w->stream));
+    double det = 0, sol = 0;
+    int nd = 0, ns = 0;
+    for (size_t i = 0; i + 2 < w->ev_used.size(); i += 3) {
+        float a = 0, b = 0;
+        CK(cudaEventElapsedTime(&a, w->ev_used[i], w->ev_used[i + 1]));
+        CK(cudaEventElapsedTime(&b, w->ev_used[i + 1], w->ev_used[i + 2]));
+        det += a;
+        sol += b;
+        ++nd;
+        ++ns;
+    }
+    for (auto e : w->ev_used) w->ev_pool.push_back(e);
+    w->ev_used.clear();
+    ms[0] = (float)det; ms[1] = (float)sol; ms[2] = (float)nd; ms[3] = (float)ns;
+    for (int i = 4; i < n; ++i) ms[i] = 0.f;
+    return FW_OK;
+}
+
+fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs) {
+    if (!w) return FW_ERR_ARG;
+    if (n_envs) *n_envs = (int)w->envs.size();
+    if (n_bodies) *n_bodies = (int)w->props.size();
+    if (n_pairs) *n_pairs = (int)w->pairs.size();
+    return FW_OK;
+}
+
+int fw_launches_per_step(fw_world *w, int n_substeps) {
+    if (!w || n_substeps < 1) return 0;
+    return 2 * n_substeps;
+}
+
+const char *fw_last_error(const fw_world *w) {
+    if (!w) return "null world";
+    return w->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// fw_device.cuh -- device helpers: small vector algebra, quaternions, the SDF lookup.
+#pragma once
+
+#include "fw_internal.h"
+
+namespace fw {
+
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 ld3(const float *p) { return {p[0], p[1], p[2]}; }
+__device__ __forceinline__ void st3(float *p, V3 a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+
+// Row-major 3x3 rotation of the unit quaternion q = (x, y, z, w).
+struct M3 {
+    float m[9];
+};
+__device__ __forceinline__ M3 quat_to_mat(float4 q) {
+    float x = q.x, y = q.y, z = q.z, w = q.w;
+    M3 R;
+    R.m[0] = 1.f - 2.f * (y * y + z * z); R.m[1] = 2.f * (x * y - z * w);       R.m[2] = 2.f * (x * z + y * w);
+    R.m[3] = 2.f * (x * y + z * w);       R.m[4] = 1.f - 2.f * (x * x + z * z); R.m[5] = 2.f * (y * z - x * w);
+    R.m[6] = 2.f * (x * z - y * w);       R.m[7] = 2.f * (y * z + x * w);       R.m[8] = 1.f - 2.f * (x * x + y * y);
+    return R;
+}
+__device__ __forceinline__ V3 mul(const M3 &R, V3 v) {
+    return {R.m[0] * v.x + R.m[1] * v.y + R.m[2] * v.z, R.m[3] * v.x + R.m[4] * v.y + R.m[5] * v.z,
+            R.m[6] * v.x + R.m[7] * v.y + R.m[8] * v.z};
+}
+__device__ __forceinline__ V3 mul_t(const M3 &R, V3 v) {   // R^T v
+    return {R.m[0] * v.x + R.m[3] * v.y + R.m[6] * v.z, R.m[1] * v.x + R.m[4] * v.y + R.m[7] * v.z,
+            R.m[2] * v.x + R.m[5] * v.y + R.m[8] * v.z};
+}
+// symmetric matrix stored xx yy zz xy xz yz
+__device__ __forceinline__ V3 sym_mul(const float *S, V3 v) {
+    return {S[0] * v.x + S[3] * v.y + S[4] * v.z, S[3] * v.x + S[1] * v.y + S[5] * v.z,
+            S[4] * v.x + S[5] * v.y + S[2] * v.z};
+}
+// R S R^T for symmetric S (result symmetric, stored the same way)
+__device__ __forceinline__ void rot_sym(const M3 &R, const float *S, float *out) {
+    float T[9];  // R S
+    for (int i = 0; i < 3; ++i) {
+        V3 r = v3(R.m[3 * i], R.m[3 * i + 1], R.m[3 * i + 2]);
+        V3 c = sym_mul(S, r);   // (S r)^T = r^T S (S symmetric)
+        T[3 * i] = c.x; T[3 * i + 1] = c.y; T[3 * i + 2] = c.z;
+    }
+    auto e = [&](int i, int j) {
+        return T[3 * i] * R.m[3 * j] + T[3 * i + 1] * R.m[3 * j + 1] + T[3 * i + 2] * R.m[3 * j + 2];
+    };
+    out[0] = e(0, 0); out[1] = e(1, 1); out[2] = e(2, 2);
+    out[3] = e(0, 1); out[4] = e(0, 2); out[5] = e(1, 2);
+}
+
+// Tangent basis of a unit normal: t1 = normalize(n x e_x) when |n_x| < 0.57735, else
+// normalize(n x e_y); t2 = n x t1.
+__device__ __forceinline__ void tangent_basis(V3 n, V3 &t1, V3 &t2) {
+    V3 t = (fabsf(n.x) < 0.57735f) ? v3(0.f, n.z, -n.y) : v3(-n.z, 0.f, n.x);
+    float inv = 1.0f / sqrtf(dot(t, t));
+    t1 = inv * t;
+    t2 = cross(n, t1);
+}
+
+// ----------------------------------------------------------------------------------------
+// SDF lookup (Sec. III-A): trilinear value and the analytic gradient of the trilinear
+// interpolant.  The grid coordinate u = (x - lo) / h is formed as an unevaluated sum
+// p + corr (TwoSum for x - lo, FMA residual for the product, and the float32 residual of
+// 1/h), so the cell fraction is exact to float32 rounding of f itself instead of carrying
+// the ~N * 2^-24 voxel error of a plain float32 (x - lo) * inv_h.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_coord(float x, float lo, float inv_h, float inv_h_lo, int dim,
+                                           int &c, float &f) {
+    float s = x - lo;
+    float bb = s - x;
+    float e = (x - (s - bb)) + (-lo - bb);       // s + e == x - lo exactly
+    float p = s * inv_h;
+    float pe = __fmaf_rn(s, inv_h, -p);          // s * inv_h - p exactly
+    float corr = pe + __fmaf_rn(s, inv_h_lo, e * inv_h);
+    if (!(p > -2.0f && p < (float)dim + 1.0f)) return false;   // also rejects NaN
+    float fl = floorf(p);
+    float fr = (p - fl) + corr;
+    if (fr < 0.0f) { fl -= 1.0f; fr += 1.0f; }
+    else if (fr >= 1.0f) { fl += 1.0f; fr -= 1.0f; }
+    int ci = (int)fl;
+    if (ci < 0 || ci > dim - 1 || (ci == dim - 1 && fr > 0.0f)) return false;
+    if (ci == dim - 1) { ci = dim - 2; fr = 1.0f; }
+    c = ci;
+    f = fr;
+    return true;
+}
+
+__device__ __forceinline__ float lerp_(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
+
+template <bool kHalf>
+__device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
+    int ci, cj, ck;
+    float fx, fy, fz;
+    if (!grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx)) return false;
+    if (!grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy)) return false;
+    if (!grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz)) return false;
+    const long long nx = g.dims[0], nxy = (long long)g.dims[0] * g.dims[1];
+    const long long o = (long long)ck * nxy + (long long)cj * nx + ci;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if (kHalf) {
+        const __half *b = g.grid16 + o;
+        v000 = __half2float(b[0]);        v100 = __half2float(b[1]);
+        v010 = __half2float(b[nx]);       v110 = __half2float(b[nx + 1]);
+        v001 = __half2float(b[nxy]);      v101 = __half2float(b[nxy + 1]);
+        v011 = __half2float(b[nxy + nx]); v111 = __half2float(b[nxy + nx + 1]);
+    } else {
+        const float *b = g.grid + o;
+        v000 = __ldg(b);            v100 = __ldg(b + 1);
+        v010 = __ldg(b + nx);       v110 = __ldg(b + nx + 1);
+        v001 = __ldg(b + nxy);      v101 = __ldg(b + nxy + 1);
+        v011 = __ldg(b + nxy + nx); v111 = __ldg(b + nxy + nx + 1);
+    }
+    // value: lerp along x, then y, then z
+    float a00 = lerp_(v000, v100, fx), a10 = lerp_(v010, v110, fx);
+    float a01 = lerp_(v001, v101, fx), a11 = lerp_(v011, v111, fx);
+    float b0 = lerp_(a00, a10, fy), b1 = lerp_(a01, a11, fy);
+    float val = lerp_(b0, b1, fz);
+    // gradient: bilinear blend of the node differences along each axis
+    float gx = lerp_(lerp_(v100 - v000, v110 - v010, fy), lerp_(v101 - v001, v111 - v011, fy), fz);
+    float gy = lerp_(lerp_(v010 - v000, v110 - v100, fx), lerp_(v011 - v001, v111 - v101, fx), fz);
+    float gz = lerp_(lerp_(v001 - v000, v101 - v100, fx), lerp_(v011 - v010, v111 - v110, fx), fy);
+    if (kHalf) {   // nodes hold phi / h
+        phi = val * g.h;
+        grad = v3(gx, gy, gz);
+    } else {
+        phi = val;
+        grad = g.inv_h * v3(gx, gy, gz);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool sdf_lookup_any(const AssetDev &g, V3 x, float &phi, V3 &grad) {
+    return g.grid16 ? sdf_lookup<true>(g, x, phi, grad) : sdf_lookup<false>(g, x, phi, grad);
+}
+
+// Order-preserving map of a float to uint32 (larger float -> larger integer).
+__device__ __forceinline__ unsigned ord_f32(float f) {
+    f = f + 0.0f;   // -0 -> +0
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+}  // namespace fw

@@ -1,0 +1,123 @@
+// fw_internal.h -- structures shared by libfw's host code and kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/fw.h"
+
+namespace fw {
+
+constexpr int kBatch = 1024;        // Generate batch of Algorithm 1 (Sec. III-C)
+constexpr int kSlots = 7;           // per patch: deepest + 6 direction extremes
+constexpr int kDetectThreads = 256; // detection CTA size: 4 samples per thread per batch
+constexpr int kMaxPatchesCap = 256; // upper end of the paper's 128 <= N <= 256
+
+// device status word bits
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusOverflow = 2u;
+constexpr unsigned kStatusBounds = 4u;
+
+// Grid view of one asset's SDF.  Value at node (i, j, k) = val[(k*ny + j)*nx + i]; FP16
+// grids store phi / h.
+struct AssetDev {
+    const float4 *samples;   // asset-frame sample points (x, y, z, 0)
+    const float *grid;       // float32 nodes or nullptr
+    const __half *grid16;    // float16 nodes (phi / h) or nullptr
+    float lo[3];
+    float h, inv_h, inv_h_lo; // inv_h + inv_h_lo = 1/h to ~1e-14 relative
+    int dims[3];
+    int ns;
+    int pad_;
+};
+
+struct BodyProps {           // constant per body
+    int type, asset;
+    float invm, mass;
+    float com_b[3];
+    float Ib[6];             // inertia about the COM, asset frame: xx yy zz xy xz yz
+    float Ib_inv[6];
+    float axis[3];
+    float force[3], torque[3];
+    float mu;
+    float pad_[3];
+};
+
+struct PairDev {
+    int a, b;                // global body ids (a: sample points, b: SDF)
+    int asset_a, asset_b;
+    int env;
+    int scratch_off;         // offset (in float4) of this pair's per-sample scratch
+    float mu;                // sqrt(mu_a mu_b)
+    int local_a, local_b;    // body ids within the env
+    int pad_[3];
+};
+
+struct EnvDev {
+    int first_body, n_bodies;
+    int first_pair, n_pairs;
+    int row_off;             // offset of the env's rows in the row buffer
+    int row_cap;             // rows available to the env
+    int pad_[2];
+};
+
+// A reduced contact on the device.  sample_patch = sample | (patch << 24).
+struct __align__(16) DContact {
+    float xa[3];
+    float phi;
+    float n[3];
+    int sample_patch;
+};
+
+// One contact's constraint rows (normal, tangent 1, tangent 2), Sec. III-B.
+struct __align__(16) Row {
+    float n[3], t1[3], t2[3];          // directions (world)
+    float ra_n[3], ra_t1[3], ra_t2[3]; // r_A x d
+    float rb_n[3], rb_t1[3], rb_t2[3]; // r_B x d
+    float ia_n[3], ia_t1[3], ia_t2[3]; // I_A^-1 (r_A x d)
+    float ib_n[3], ib_t1[3], ib_t2[3]; // I_B^-1 (r_B x d)
+    float kn, kt1, kt2, bias;          // effective masses, bias velocity
+    float mu, ln, lt1, lt2;            // friction coefficient, accumulated impulses
+    int a, b;                          // local body ids
+    int pad_[2];
+};
+
+struct SimParams {
+    const AssetDev *assets;
+    const PairDev *pairs;
+    const EnvDev *envs;
+    const BodyProps *props;
+    float *pos, *quat, *linvel, *angvel;   // state (n_bodies x 3 / 4)
+    DContact *contacts;                    // n_pairs x cap_pair
+    int *counts;                           // n_pairs
+    float4 *scratch;                       // per pair per sample: (x, phi), (n, 0)
+    Row *rows;
+    unsigned *status;
+    int n_pairs, n_envs, cap_pair, max_patches;
+    float contact_offset, cos_patch, baumgarte, max_angvel;
+    float gravity[3];
+    float hs;
+    int n_iters, n_vel_iters;
+};
+
+// launchers (defined in the .cu files)
+cudaError_t launch_bake(const float *d_tri, int n_tri, const float *d_tri_pn, const float *d_tile_box,
+                        const AssetDev &g, float *d_out, int *d_flags, cudaStream_t s);
+cudaError_t launch_bake_fix_sign(const float *d_tri, int n_tri, const AssetDev &g, float *d_out,
+                                 const int *d_idx, int n_idx, cudaStream_t s);
+cudaError_t launch_to_half(const float *src, __half *dst, float inv_h, long long n, cudaStream_t s);
+int bake_tile_size();
+cudaError_t launch_query_sdf(const AssetDev &g, const float *pts, int n, float *phi, float *grad,
+                             cudaStream_t s);
+cudaError_t launch_query_pair(const SimParams &p, int pair, float *phi, float *nrm, cudaStream_t s, int ns);
+cudaError_t prepare_detect(int max_patches);
+size_t detect_smem_bytes(int max_patches);
+cudaError_t launch_detect(const SimParams &p, cudaStream_t s);
+cudaError_t launch_reduce_list(const SimParams &p, const float *d_cands, int n, DContact *out,
+                               int *d_count, int *d_npatch, cudaStream_t s);
+cudaError_t launch_solve(const SimParams &p, cudaStream_t s);
+cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
+
+}  // namespace fw

@@ -1,0 +1,248 @@
+// fw_solve.cu -- contact solution of one substep (Sec. III-B): external forces,
+// constraint preparation, Gauss-Seidel sweeps with Coulomb friction, integration.
+// One warp per environment: lanes prepare rows and integrate bodies in parallel; the
+// sweep itself is the serial Gauss-Seidel chain and runs on lane 0 with the env's body
+// velocities in shared memory.
+//
+// Update rule (velocity-level projected Gauss-Seidel; the paper cites the solver without
+// restating it): per contact, the normal row
+//     lambda_n <- max(0, lambda_n - k_n (n . v_rel + b)),
+// then both friction rows from the updated velocities, lambda_t <- lambda_t - k_t (t . v_rel),
+// projected jointly on the disk |lambda_t| <= mu lambda_n; every change is applied to
+// both bodies at once.  b = phi/hs for phi > 0 (speculative contact), baumgarte*phi/hs
+// otherwise.  Integration: semi-implicit Euler of the centre of mass and
+// q <- normalize(q + hs/2 (omega, 0) q).
+#include "fw_device.cuh"
+
+namespace fw {
+
+namespace {
+
+constexpr int kMaxBodies = 8;
+
+struct BodySm {
+    float v[kMaxBodies][3], w[kMaxBodies][3];
+    float invm[kMaxBodies];
+    float Iinv[kMaxBodies][6];
+    float com[kMaxBodies][3];
+};
+
+__device__ __forceinline__ V3 smv(const float (*a)[3], int i) { return v3(a[i][0], a[i][1], a[i][2]); }
+__device__ __forceinline__ void smv_set(float (*a)[3], int i, V3 x) { a[i][0] = x.x; a[i][1] = x.y; a[i][2] = x.z; }
+
+// effective mass 1 / (m_a^-1 + m_b^-1 + (r_a x d) I_a^-1 (r_a x d) + (r_b x d) I_b^-1 (r_b x d))
+__device__ __forceinline__ float eff_mass(float ima, float imb, V3 rad, V3 iad, V3 rbd, V3 ibd) {
+    const float den = ima + imb + dot(rad, iad) + dot(rbd, ibd);
+    return den > 0.0f ? 1.0f / den : 0.0f;
+}
+
+__device__ __forceinline__ void build_row(Row &R, const DContact &c, const BodySm &B, int a, int b, float mu,
+                                          float hs, float baumgarte) {
+    const V3 n = ld3(c.n), xa = ld3(c.xa);
+    const float phi = c.phi;
+    const V3 xb = xa - phi * n;
+    const V3 ra = xa - smv(B.com, a), rb = xb - smv(B.com, b);
+    V3 t1, t2;
+    tangent_basis(n, t1, t2);
+    const V3 ran = cross(ra, n), rat1 = cross(ra, t1), rat2 = cross(ra, t2);
+    const V3 rbn = cross(rb, n), rbt1 = cross(rb, t1), rbt2 = cross(rb, t2);
+    const V3 ian = sym_mul(B.Iinv[a], ran), iat1 = sym_mul(B.Iinv[a], rat1), iat2 = sym_mul(B.Iinv[a], rat2);
+    const V3 ibn = sym_mul(B.Iinv[b], rbn), ibt1 = sym_mul(B.Iinv[b], rbt1), ibt2 = sym_mul(B.Iinv[b], rbt2);
+    st3(R.n, n); st3(R.t1, t1); st3(R.t2, t2);
+    st3(R.ra_n, ran); st3(R.ra_t1, rat1); st3(R.ra_t2, rat2);
+    st3(R.rb_n, rbn); st3(R.rb_t1, rbt1); st3(R.rb_t2, rbt2);
+    st3(R.ia_n, ian); st3(R.ia_t1, iat1); st3(R.ia_t2, iat2);
+    st3(R.ib_n, ibn); st3(R.ib_t1, ibt1); st3(R.ib_t2, ibt2);
+    const float ima = B.invm[a], imb = B.invm[b];
+    R.kn = eff_mass(ima, imb, ran, ian, rbn, ibn);
+    R.kt1 = eff_mass(ima, imb, rat1, iat1, rbt1, ibt1);
+    R.kt2 = eff_mass(ima, imb, rat2, iat2, rbt2, ibt2);
+    R.bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    R.mu = mu;
+    R.ln = 0.0f; R.lt1 = 0.0f; R.lt2 = 0.0f;
+    R.a = a; R.b = b;
+}
+
+// One Gauss-Seidel sweep over the env's rows (lane 0 only).
+__device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
+    for (int r = 0; r < nr; ++r) {
+        Row &R = rows[r];
+        if (R.kn == 0.0f) continue;
+        const int a = R.a, b = R.b;
+        V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
+        const float ima = B.invm[a], imb = B.invm[b];
+        // normal row
+        const V3 n = ld3(R.n);
+        float jv = dot(n, va - vb) + dot(ld3(R.ra_n), wa) - dot(ld3(R.rb_n), wb);
+        if (use_bias) jv += R.bias;
+        const float ln = fmaxf(R.ln - R.kn * jv, 0.0f);
+        const float dl = ln - R.ln;
+        R.ln = ln;
+        va = va + (dl * ima) * n;
+        wa = wa + dl * ld3(R.ia_n);
+        vb = vb - (dl * imb) * n;
+        wb = wb - dl * ld3(R.ib_n);
+        // friction rows, projected jointly on the disk of radius mu lambda_n
+        const V3 t1 = ld3(R.t1), t2 = ld3(R.t2);
+        const V3 dv = va - vb;
+        const float j1 = dot(t1, dv) + dot(ld3(R.ra_t1), wa) - dot(ld3(R.rb_t1), wb);
+        const float j2 = dot(t2, dv) + dot(ld3(R.ra_t2), wa) - dot(ld3(R.rb_t2), wb);
+        float l1 = R.lt1 - R.kt1 * j1, l2 = R.lt2 - R.kt2 * j2;
+        const float lim = R.mu * ln;
+        const float lt = sqrtf(l1 * l1 + l2 * l2);
+        if (lt > lim) {
+            const float s = lt > 0.0f ? lim / lt : 0.0f;
+            l1 *= s;
+            l2 *= s;
+        }
+        const float d1 = l1 - R.lt1, d2 = l2 - R.lt2;
+        R.lt1 = l1;
+        R.lt2 = l2;
+        const V3 pt = d1 * t1 + d2 * t2;
+        va = va + ima * pt;
+        wa = wa + d1 * ld3(R.ia_t1) + d2 * ld3(R.ia_t2);
+        vb = vb - imb * pt;
+        wb = wb - (d1 * ld3(R.ib_t1) + d2 * ld3(R.ib_t2));
+        smv_set(B.v, a, va); smv_set(B.w, a, wa);
+        smv_set(B.v, b, vb); smv_set(B.w, b, wb);
+    }
+}
+
+__global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
+    const int e = blockIdx.x;
+    const int lane = threadIdx.x;
+    const EnvDev E = p.envs[e];
+    __shared__ BodySm B;
+    __shared__ float q_new[kMaxBodies][4];
+    __shared__ int row_base[64];
+    const float hs = p.hs;
+    // 1. external forces; world inertia at the substep's start
+    if (lane < E.n_bodies) {
+        const int bi = E.first_body + lane;
+        const BodyProps P = p.props[bi];
+        const float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
+        const M3 R = quat_to_mat(q);
+        V3 pos = ld3(p.pos + 3 * bi), v = ld3(p.linvel + 3 * bi), w = ld3(p.angvel + 3 * bi);
+        const V3 com = mul(R, ld3(P.com_b)) + pos;
+        float Iw[6], Ii[6] = {0, 0, 0, 0, 0, 0};
+        rot_sym(R, P.Ib, Iw);
+        if (P.type == FW_BODY_DYNAMIC) {
+            rot_sym(R, P.Ib_inv, Ii);
+            const V3 g = v3(p.gravity[0], p.gravity[1], p.gravity[2]);
+            v = v + hs * (g + P.invm * ld3(P.force));
+            const V3 tau = ld3(P.torque) - cross(w, sym_mul(Iw, w));
+            w = w + hs * sym_mul(Ii, tau);
+        } else if (P.type == FW_BODY_FIXED_AXIS) {
+            const V3 ax = ld3(P.axis);
+            const float Iaa = dot(ax, sym_mul(Iw, ax));
+            const float s = 1.0f / Iaa;
+            Ii[0] = ax.x * ax.x * s; Ii[1] = ax.y * ax.y * s; Ii[2] = ax.z * ax.z * s;
+            Ii[3] = ax.x * ax.y * s; Ii[4] = ax.x * ax.z * s; Ii[5] = ax.y * ax.z * s;
+            w = w + (hs * dot(ax, ld3(P.torque)) * s) * ax;
+        }
+        smv_set(B.v, lane, v);
+        smv_set(B.w, lane, w);
+        smv_set(B.com, lane, com);
+        B.invm[lane] = P.invm;
+        for (int k = 0; k < 6; ++k) B.Iinv[lane][k] = Ii[k];
+    }
+    // row offsets of the env's pairs
+    if (lane == 0) {
+        int acc = 0;
+        for (int k = 0; k < E.n_pairs; ++k) {
+            row_base[k] = acc;
+            const int c = p.counts[E.first_pair + k];
+            acc += c < p.cap_pair ? c : p.cap_pair;
+        }
+        row_base[E.n_pairs] = acc;
+    }
+    __syncwarp();
+    const int nr = row_base[E.n_pairs];
+    Row *rows = p.rows + E.row_off;
+    // 2. constraint preparation, one contact per lane
+    for (int k = 0; k < E.n_pairs; ++k) {
+        const int pi = E.first_pair + k;
+        const PairDev P = p.pairs[pi];
+        const int cnt = row_base[k + 1] - row_base[k];
+        for (int i = lane; i < cnt; i += 32)
+            build_row(rows[row_base[k] + i], p.contacts[(long long)pi * p.cap_pair + i], B, P.local_a, P.local_b,
+                      P.mu, hs, p.baumgarte);
+    }
+    __syncwarp();
+    // 3. Gauss-Seidel sweeps
+    if (lane == 0)
+        for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
+    __syncwarp();
+    // 4. integration
+    if (lane < E.n_bodies) {
+        const int bi = E.first_body + lane;
+        const BodyProps P = p.props[bi];
+        if (P.type != FW_BODY_STATIC) {
+            V3 w = smv(B.w, lane);
+            const V3 v = smv(B.v, lane);
+            if ((P.type == FW_BODY_DYNAMIC || P.type == FW_BODY_FIXED_AXIS) && p.max_angvel > 0.0f) {
+                const float wn = sqrtf(dot(w, w));
+                if (wn > p.max_angvel) w = (p.max_angvel / wn) * w;
+                smv_set(B.w, lane, w);
+            }
+            const V3 com = smv(B.com, lane) + hs * v;
+            float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
+            // dq = (omega, 0) (x) q
+            const float dx = q.w * w.x + w.y * q.z - w.z * q.y;
+            const float dy = q.w * w.y + w.z * q.x - w.x * q.z;
+            const float dz = q.w * w.z + w.x * q.y - w.y * q.x;
+            const float dw = -(w.x * q.x + w.y * q.y + w.z * q.z);
+            const float hh = 0.5f * hs;
+            q.x += hh * dx; q.y += hh * dy; q.z += hh * dz; q.w += hh * dw;
+            const float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+            q.x *= inv; q.y *= inv; q.z *= inv; q.w *= inv;
+            const M3 R = quat_to_mat(q);
+            const V3 pos = com - mul(R, ld3(P.com_b));
+            st3(p.pos + 3 * bi, pos);
+            q_new[lane][0] = q.x; q_new[lane][1] = q.y; q_new[lane][2] = q.z; q_new[lane][3] = q.w;
+            const bool bad = !(isfinite(pos.x) && isfinite(pos.y) && isfinite(pos.z) && isfinite(q.x) &&
+                               isfinite(q.y) && isfinite(q.z) && isfinite(q.w));
+            if (bad) atomicOr(p.status, kStatusNonFinite);
+        } else {
+            for (int k = 0; k < 4; ++k) q_new[lane][k] = p.quat[4 * bi + k];
+        }
+    }
+    __syncwarp();
+    // 5. optional bias-free sweeps
+    if (lane == 0)
+        for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
+    __syncwarp();
+    if (lane < E.n_bodies) {
+        const int bi = E.first_body + lane;
+        for (int k = 0; k < 4; ++k) p.quat[4 * bi + k] = q_new[lane][k];
+        const V3 v = smv(B.v, lane), w = smv(B.w, lane);
+        st3(p.linvel + 3 * bi, v);
+        st3(p.angvel + 3 * bi, w);
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z)))
+            atomicOr(p.status, kStatusNonFinite);
+    }
+}
+
+__global__ void normalize_quats_kernel(float *q, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = q[4 * i], y = q[4 * i + 1], z = q[4 * i + 2], w = q[4 * i + 3];
+    const float inv = 1.0f / sqrtf(x * x + y * y + z * z + w * w);
+    q[4 * i] = x * inv; q[4 * i + 1] = y * inv; q[4 * i + 2] = z * inv; q[4 * i + 3] = w * inv;
+}
+
+}  // namespace
+
+cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    normalize_quats_kernel<<<(n + 255) / 256, 256, 0, s>>>(quat, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const SimParams &p, cudaStream_t s) {
+    if (p.n_envs == 0) return cudaSuccess;
+    solve_kernel<<<p.n_envs, 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fw

@@ -1,0 +1,318 @@
+"""Python binding of libfw's C ABI (include/fw.h): argument marshalling only.
+
+Every computation happens in libfw.so; this module converts numpy arrays / torch CUDA
+tensors to pointers and status codes to exceptions.  There is no fallback: if the
+library is missing, creating a World fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfw.so")
+
+STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_OOM", -3: "FW_ERR_CUDA", -4: "FW_ERR_STATE",
+          -5: "FW_ERR_NONFINITE", -6: "FW_ERR_OVERFLOW", -7: "FW_ERR_TIMEOUT",
+          -8: "FW_ERR_DEVICE_BOUNDS"}
+
+# every function include/fw.h declares
+ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_asset", "fw_bake_sdf",
+                 "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
+                 "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
+                 "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_sync",
+                 "fw_set_timing", "fw_get_timings", "fw_get_counts", "fw_launches_per_step",
+                 "fw_last_error"]
+
+
+class FwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FwConfig(C.Structure):
+    _fields_ = [("gravity", C.c_float * 3), ("dt", C.c_float), ("contact_offset", C.c_float),
+                ("cos_patch", C.c_float), ("max_patches", C.c_int), ("batch_size", C.c_int),
+                ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
+                ("sdf_fp16", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("pair", np.int32),
+                          ("phi", np.float32), ("xa", np.float32, 3), ("xb", np.float32, 3),
+                          ("n", np.float32, 3)])
+CANDIDATE_DTYPE = np.dtype([("sample", np.int32), ("phi", np.float32), ("x", np.float32, 3),
+                            ("n", np.float32, 3)])
+assert CONTACT_DTYPE.itemsize == 52 and CANDIDATE_DTYPE.itemsize == 32
+assert scenes.BODY_DTYPE.itemsize == 104
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libfw.so and declares the ABI's signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"libfw.so not built at {path}; run paper_2205_03532_b300.csrc.build")
+    L = C.CDLL(path)
+    vp, i, f, st = C.c_void_p, C.c_int, C.c_float, C.c_int
+    sig = {
+        "fw_config_default": (None, [C.POINTER(FwConfig)]),
+        "fw_create": (st, [C.POINTER(FwConfig), C.POINTER(vp)]),
+        "fw_destroy": (st, [vp]),
+        "fw_add_mesh_asset": (st, [vp, vp, i, vp, i, vp, i, f, C.POINTER(i)]),
+        "fw_bake_sdf": (st, [vp, i, i, f, i]),
+        "fw_set_sdf": (st, [vp, i, vp, f, vp, vp]),
+        "fw_get_sdf": (st, [vp, i, vp, C.POINTER(f), vp, vp]),
+        "fw_get_mass": (st, [vp, i, vp, vp, vp]),
+        "fw_add_env_bodies": (st, [vp, i, vp, i, vp, i, C.POINTER(i)]),
+        "fw_step": (st, [vp, i, i]),
+        "fw_substep": (st, [vp, f, i, i]),
+        "fw_collide": (st, [vp]),
+        "fw_get_contacts": (st, [vp, i, vp, i, C.POINTER(i)]),
+        "fw_set_contacts": (st, [vp, i, vp, i]),
+        "fw_get_state": (st, [vp, vp, vp, vp, vp, i]),
+        "fw_set_state": (st, [vp, vp, vp, vp, vp, i]),
+        "fw_query_sdf": (st, [vp, i, vp, i, vp, vp, i]),
+        "fw_query_pair": (st, [vp, i, i, vp, vp, i]),
+        "fw_reduce": (st, [vp, vp, i, vp, i, C.POINTER(i), C.POINTER(i)]),
+        "fw_sync": (st, [vp]),
+        "fw_set_timing": (st, [vp, i]),
+        "fw_get_timings": (st, [vp, vp, i]),
+        "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "fw_launches_per_step": (i, [vp, i]),
+        "fw_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def default_config(**over) -> FwConfig:
+    cfg = FwConfig()
+    load_library().fw_config_default(C.byref(cfg))
+    for k, v in over.items():
+        if k == "gravity":
+            cfg.gravity[:] = list(v)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, False
+
+
+class World:
+    """One libfw world.  Methods map one to one to the ABI calls."""
+
+    def __init__(self, cfg: Optional[FwConfig] = None, **over):
+        self.lib = load_library()
+        self.cfg = cfg if cfg is not None else default_config(**over)
+        h = C.c_void_p()
+        st = self.lib.fw_create(C.byref(self.cfg), C.byref(h))
+        if st != 0:
+            raise FwError(st, "fw_create failed")
+        self.h = h
+
+    def _check(self, status):
+        if status != 0:
+            msg = self.lib.fw_last_error(self.h) or b""
+            raise FwError(status, msg.decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- assets
+    def add_mesh_asset(self, verts, tris, samples=None, density=7800.0) -> int:
+        V = np.ascontiguousarray(verts, np.float32)
+        T = np.ascontiguousarray(tris, np.int32)
+        S = None if samples is None else np.ascontiguousarray(samples, np.float32)
+        out = C.c_int()
+        self._check(self.lib.fw_add_mesh_asset(self.h, V.ctypes.data, len(V), T.ctypes.data, len(T),
+                                               None if S is None else S.ctypes.data,
+                                               0 if S is None else len(S), density, C.byref(out)))
+        return out.value
+
+    def bake_sdf(self, asset: int, resolution: int, padding: float = 1e-3, cubic: bool = True):
+        self._check(self.lib.fw_bake_sdf(self.h, asset, resolution, padding, int(cubic)))
+
+    def set_sdf(self, asset: int, lo, h: float, dims, values):
+        lo = np.ascontiguousarray(lo, np.float32)
+        dims = np.ascontiguousarray(dims, np.int32)
+        v = np.ascontiguousarray(values, np.float32)
+        self._check(self.lib.fw_set_sdf(self.h, asset, lo.ctypes.data, float(h), dims.ctypes.data, v.ctypes.data))
+
+    def get_sdf(self, asset: int, values: bool = True):
+        lo, dims, h = np.zeros(3, np.float32), np.zeros(3, np.int32), C.c_float()
+        self._check(self.lib.fw_get_sdf(self.h, asset, lo.ctypes.data, C.byref(h), dims.ctypes.data, None))
+        vals = None
+        if values:
+            vals = np.zeros((dims[2], dims[1], dims[0]), np.float32)
+            self._check(self.lib.fw_get_sdf(self.h, asset, None, None, None, vals.ctypes.data))
+        return lo, np.float32(h.value), dims, vals
+
+    def get_mass(self, asset: int):
+        m, com, I = np.zeros(1), np.zeros(3), np.zeros(9)
+        self._check(self.lib.fw_get_mass(self.h, asset, m.ctypes.data, com.ctypes.data, I.ctypes.data))
+        return float(m[0]), com, I.reshape(3, 3)
+
+    # -- environments
+    def add_env_bodies(self, bodies: np.ndarray, pairs) -> int:
+        b = np.ascontiguousarray(bodies, dtype=scenes.BODY_DTYPE)
+        p = np.ascontiguousarray(pairs, np.int32).reshape(-1)
+        out = C.c_int()
+        self._check(self.lib.fw_add_env_bodies(self.h, b.shape[0], b.ctypes.data, b.shape[1],
+                                               p.ctypes.data if len(p) else None, len(p) // 2, C.byref(out)))
+        return out.value
+
+    def counts(self) -> Tuple[int, int, int]:
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.fw_get_counts(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    # -- stepping
+    def step(self, n_substeps: int, n_iters: int):
+        self._check(self.lib.fw_step(self.h, n_substeps, n_iters))
+
+    def substep(self, hs: float, n_iters: int, detect: bool = True):
+        self._check(self.lib.fw_substep(self.h, hs, n_iters, int(detect)))
+
+    def collide(self):
+        self._check(self.lib.fw_collide(self.h))
+
+    def sync(self):
+        self._check(self.lib.fw_sync(self.h))
+
+    def get_contacts(self, env: int) -> np.ndarray:
+        cap = 2048
+        while True:
+            out = np.zeros(cap, CONTACT_DTYPE)
+            n = C.c_int()
+            st = self.lib.fw_get_contacts(self.h, env, out.ctypes.data, cap, C.byref(n))
+            if st == -6 and n.value > cap:
+                cap = n.value
+                continue
+            self._check(st)
+            return out[: n.value].copy()
+
+    def set_contacts(self, env: int, contacts: np.ndarray):
+        c = np.ascontiguousarray(contacts, CONTACT_DTYPE)
+        self._check(self.lib.fw_set_contacts(self.h, env, c.ctypes.data, len(c)))
+
+    # -- state
+    def get_state(self, out=None):
+        """(pos, quat, linvel, angvel) as float32 numpy arrays, or fills the given torch
+        CUDA tensors (device copies, no synchronisation)."""
+        nb = self.counts()[1]
+        if out is None:
+            p, q = np.zeros((nb, 3), np.float32), np.zeros((nb, 4), np.float32)
+            v, w = np.zeros((nb, 3), np.float32), np.zeros((nb, 3), np.float32)
+            self._check(self.lib.fw_get_state(self.h, p.ctypes.data, q.ctypes.data, v.ctypes.data,
+                                              w.ctypes.data, 0))
+            return p, q, v, w
+        ptrs = [_ptr(t) for t in out]
+        dev = any(d for _, d in ptrs)
+        self._check(self.lib.fw_get_state(self.h, *[pp for pp, _ in ptrs], int(dev)))
+        return out
+
+    def set_state(self, pos=None, quat=None, linvel=None, angvel=None):
+        conv = []
+        for a in (pos, quat, linvel, angvel):
+            conv.append(a if (a is None or hasattr(a, "data_ptr")) else np.ascontiguousarray(a, np.float32))
+        ptrs = [_ptr(a) for a in conv]
+        dev = any(d for _, d in ptrs)
+        self._check(self.lib.fw_set_state(self.h, *[pp for pp, _ in ptrs], int(dev)))
+
+    # -- test hooks
+    def query_sdf(self, asset: int, pts):
+        if hasattr(pts, "data_ptr"):
+            import torch
+            n = pts.shape[0]
+            phi = torch.empty(n, device=pts.device, dtype=torch.float32)
+            grad = torch.empty((n, 3), device=pts.device, dtype=torch.float32)
+            self._check(self.lib.fw_query_sdf(self.h, asset, pts.data_ptr(), n, phi.data_ptr(), grad.data_ptr(), 1))
+            return phi, grad
+        P = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
+        phi, grad = np.zeros(len(P), np.float32), np.zeros((len(P), 3), np.float32)
+        self._check(self.lib.fw_query_sdf(self.h, asset, P.ctypes.data, len(P), phi.ctypes.data,
+                                          grad.ctypes.data, 0))
+        return phi, grad
+
+    def query_pair(self, env: int, pair: int, n_samples: int):
+        phi, nrm = np.zeros(n_samples, np.float32), np.zeros((n_samples, 3), np.float32)
+        self._check(self.lib.fw_query_pair(self.h, env, pair, phi.ctypes.data, nrm.ctypes.data, 0))
+        return phi, nrm
+
+    def reduce(self, cands: np.ndarray):
+        c = np.ascontiguousarray(cands).view(CANDIDATE_DTYPE)
+        cap = 7 * 256
+        out = np.zeros(cap, CONTACT_DTYPE)
+        n, npch = C.c_int(), C.c_int()
+        self._check(self.lib.fw_reduce(self.h, c.ctypes.data if len(c) else None, len(c), out.ctypes.data,
+                                       cap, C.byref(n), C.byref(npch)))
+        return out[: n.value].copy(), npch.value
+
+    # -- diagnostics
+    def set_timing(self, enable: bool):
+        self._check(self.lib.fw_set_timing(self.h, int(enable)))
+
+    def get_timings(self):
+        ms = np.zeros(4, np.float32)
+        self._check(self.lib.fw_get_timings(self.h, ms.ctypes.data, 4))
+        return {"detect_ms": float(ms[0]), "solve_ms": float(ms[1]), "detect_launches": int(ms[2]),
+                "solve_launches": int(ms[3])}
+
+    def launches_per_step(self, n_substeps: int) -> int:
+        return self.lib.fw_launches_per_step(self.h, n_substeps)
+
+
+def world_from_scene(scene, fp16: bool = False, stream=None, **over) -> World:
+    """Builds a World from a scenes.Scene: assets, SDF bakes, env groups."""
+    sim = scene.sim
+    cfg = default_config(gravity=sim.gravity, dt=sim.dt, contact_offset=sim.contact_offset,
+                         cos_patch=sim.cos_patch, max_patches=sim.max_patches,
+                         baumgarte=sim.baumgarte, n_vel_iters=sim.n_vel_iters,
+                         max_angvel=sim.max_angvel, sdf_fp16=int(fp16))
+    for k, v in over.items():
+        if k == "gravity":
+            cfg.gravity[:] = list(v)
+        else:
+            setattr(cfg, k, v)
+    if stream is not None:
+        cfg.cuda_stream = stream
+    w = World(cfg)
+    for a in scene.assets:
+        i = w.add_mesh_asset(a.verts, a.tris, a.samples, a.density)
+        if a.sdf_res:
+            w.bake_sdf(i, a.sdf_res, a.sdf_pad, True)
+    for g in scene.groups:
+        w.add_env_bodies(g.bodies, g.pairs)
+    return w

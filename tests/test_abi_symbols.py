@@ -1,0 +1,45 @@
+"""CPU checks of the boundary: libfw.so builds, loads without a GPU, and exports every
+function include/fw.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+from paper_2205_03532_b300 import fw
+from paper_2205_03532_b300.csrc import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fw_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(fw.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.build())
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_library_exports_nothing_else():
+    out = subprocess.run(["nm", "-D", "--defined-only", B.build()], capture_output=True, text=True).stdout
+    ours = {l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("fw_")}
+    assert ours == set(_declared())
+
+
+def test_config_defaults_without_gpu():
+    cfg = fw.default_config()
+    assert cfg.batch_size == 1024 and cfg.max_patches == 128
+    assert abs(cfg.dt - 1 / 60) < 1e-7 and abs(cfg.gravity[2] + 9.81) < 1e-6
+    assert abs(cfg.contact_offset - 1e-4) < 1e-9 and abs(cfg.cos_patch - 0.97) < 1e-7
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(fw.FwConfig) == 64   # 11 four-byte fields, pad, pointer
+    assert fw.CONTACT_DTYPE.itemsize == 52 and fw.CANDIDATE_DTYPE.itemsize == 32
