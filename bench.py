@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the contact-simulation substep: env-substeps/s on procedural M16
+nut-on-bolt environments (1000 envs, 256^3 float32 bolt SDF shared by all envs, 10k
+samples on each nut, 60 Hz frames of 8 substeps x 32 Gauss-Seidel sweeps).
+
+One bench step = one frame (fw_step): 8 x (detection + reduction kernel, solve +
+integration kernel).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fw|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Per-launch DRAM traffic (read + write bytes) of the dominant kernels from an ncu capture,
+# keyed by the sha256 of the CUDA sources it was taken on; reported only while the
+# sources are unchanged (see profiles/).
+NCU_TRAFFIC = {}
+
+FP32_LANES_PER_SM = 128
+SOLVE_FLOPS_PER_CONTACT_SWEEP = 150   # one normal row + the joint friction rows (generic two-body form)
+SOLVE_FLOPS_PER_CONTACT_PREP = 300    # rows, effective masses, bias
+DETECT_BYTES_PER_QUERY = 16 + 32      # float4 sample + 8 float32 corners
+DETECT_BYTES_PER_CONTACT = 32         # reduced contact written
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2205_03532_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), d.get("sm_max_mhz", 2032.0), "measured"
+    return 6400.0, 2032.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(n_envs: int, seed: int, frames: int = 1):
+    """The FP64 oracle as it stands, on host cores, on a bounded sample of the workload:
+    n_envs nut-bolt envs for `frames` frames after one warm-up detection; the oracle's lazy
+    SDF bake (set-up work on both sides) is excluded."""
+    from oracle import oracle as O
+    from paper_2205_03532_b300 import scenes as S
+    sc = S.nut_bolt_scene(n_envs=n_envs, seed=seed)
+    w = O.world_from_scene(sc, lazy_bake=True)
+    w.collide()
+    b0 = w.bake_seconds()
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    el = time.perf_counter() - t0 - (w.bake_seconds() - b0)
+    units = n_envs * sc.sim.n_substeps * frames
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return units / el, cores, f"{n_envs} envs x {frames} frame(s) of {sc.sim.n_substeps} substeps x {sc.sim.n_iters} sweeps"
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on this bench's workload, each step a bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2205_03532_b300 import scenes as S
+    n = args.ref_envs
+    sc = S.nut_bolt_scene(n_envs=n, seed=args.seed)
+    w = O.world_from_scene(sc, lazy_bake=True)
+    w.collide()
+    for _ in range(args.warmup):
+        w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    b0 = w.bake_seconds()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    el = time.perf_counter() - t0 - (w.bake_seconds() - b0)
+    units = n * sc.sim.n_substeps * args.steps
+    v = units / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": "env-substeps/s", "value": v, "unit": "env-substeps/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)",
+           "config": {"workload": "nut_bolt_m16", "n_envs": n, "sample_of_envs": 1000, "sdf": "256^3 lazy",
+                      "substeps": 8, "iters": 32},
+           "cpu_baseline": {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{n} envs per step, lazy SDF bake excluded"},
+           "e2e": {"value": v, "unit": "env-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_fw(args):
+    import torch
+    from paper_2205_03532_b300 import fw, scenes as S
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = local
+    stream = torch.cuda.Stream(device=dev)
+    t_setup = time.perf_counter()
+    sc = S.nut_bolt_scene(n_envs=args.envs, seed=args.seed + 1000 * rank)
+    sim = sc.sim
+    with torch.cuda.stream(stream):
+        t_b = time.perf_counter()
+        w = fw.world_from_scene(sc, fp16=args.fp16, stream=stream.cuda_stream, device=dev)
+        bake_s = time.perf_counter() - t_b
+    n_env, n_body, n_pair = w.counts()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
+
+    def one_step():
+        w.step(sim.n_substeps, sim.n_iters)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize()
+    w.sync()
+    # ---- timed region: K frames, each bracketed by events; L2 flushed between frames
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                one_step()
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    w.sync()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = ws * n_env * sim.n_substeps * args.steps
+    value = units / (total_ms * 1e-3)
+    # ---- per-kernel durations (direct launches with events on the world stream)
+    w.set_timing(True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            one_step()
+    tim = w.get_timings()
+    w.set_timing(False)
+    det_ms = tim["detect_ms"] / max(tim["detect_launches"], 1)
+    sol_ms = tim["solve_ms"] / max(tim["solve_launches"], 1)
+    # contacts per env (sample of envs) for the algorithmic counts
+    sample_envs = list(range(0, n_env, max(1, n_env // 50)))
+    cper = [len(w.get_contacts(e)) for e in sample_envs]
+    c_mean = float(np.mean(cper))
+    ns = len(sc.assets[0].samples)
+    hbm, sm_max, peak_kind = _peaks()
+    det_bytes = n_pair * ns * DETECT_BYTES_PER_QUERY + n_env * c_mean * DETECT_BYTES_PER_CONTACT
+    det_gbs = det_bytes / (det_ms * 1e-3) / 1e9
+    sol_flops = n_env * c_mean * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
+    alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
+    src = _src_hash()
+    traffic = NCU_TRAFFIC.get(src, {})
+    kernels = {
+        "detect_kernel": {"bound": "hbm", "achieved": det_gbs, "peak": hbm, "unit": "GB/s",
+                          "frac": det_gbs / hbm, "traffic": traffic.get("detect_kernel"),
+                          "avg_launch_ms": det_ms, "algorithmic_bytes": det_bytes,
+                          "peak_source": f"{peak_kind} hbm_gbs"},
+        "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": sol_tf / alu_peak, "traffic": traffic.get("solve_kernel"),
+                         "avg_launch_ms": sol_ms, "algorithmic_flops": sol_flops,
+                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x max SM clock"},
+    }
+    dominant = "solve_kernel" if tim["solve_ms"] >= tim["detect_ms"] else "detect_kernel"
+    roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dominant
+    # ---- end to end through the public API with host buffers: state in, frame, state out
+    pin = [torch.empty((n_body, k), dtype=torch.float32).pin_memory() for k in (3, 4, 3, 3)]
+    w.get_state(out=pin)
+    torch.cuda.synchronize()
+    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e2e_ev[0].record(stream)
+        for k in range(args.steps):
+            w.set_state(*pin)
+            one_step()
+            w.get_state(out=pin)
+        e2e_ev[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2e_ev[0].elapsed_time(e2e_ev[1])
+    e2e_value = ws * n_env * sim.n_substeps * args.steps / (e2e_ms * 1e-3)
+    state_bytes = n_body * (3 + 4 + 3 + 3) * 4
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline(args.cpu_envs, args.seed)
+        cpu = {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        out = {"metric": "env-substeps/s", "value": value, "unit": "env-substeps/s", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)",
+               "config": {"workload": "nut_bolt_m16", "n_envs": n_env, "samples_per_nut": ns,
+                          "sdf": "256^3 " + ("fp16" if args.fp16 else "fp32"), "substeps": sim.n_substeps,
+                          "iters": sim.n_iters, "frame_dt": sim.dt, "l2": "flushed between steps (256 MB write)",
+                          "parallelism": f"replicas x{ws}"},
+               "roofline": roof, "kernels": kernels,
+               "phase_ms_per_frame": {"detect": det_ms * sim.n_substeps, "solve": sol_ms * sim.n_substeps},
+               "contacts_per_env": c_mean,
+               "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
+               "cpu_baseline": cpu, "clocks": clk.summary(),
+               "e2e": {"value": e2e_value, "unit": "env-substeps/s", "h2d_bytes_per_step": state_bytes,
+                       "d2h_bytes_per_step": state_bytes},
+               "gpu_launches": args.steps * w.launches_per_step(sim.n_substeps),
+               "bake_s": bake_s, "setup_s": time.perf_counter() - t_setup, "src": src}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fw", choices=["fw", "reference"])
+    ap.add_argument("--envs", type=int, default=1000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-envs", type=int, default=4)
+    ap.add_argument("--ref-envs", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fw(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -42,6 +42,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -379,6 +380,7 @@ struct or_world {
     pair_contacts_t *pc;
     double *env_mlen, *env_mdot;
     double **imp; int *imp_n;               /* per env friction record */
+    double bake_seconds;                    /* wall time spent in lazy SDF bakes */
 };
 
 or_world *or_create(const or_config *cfg) {
@@ -819,7 +821,14 @@ static void detect_pair(or_world *w, int pi) {
 }
 
 /* lazy bake: compute every grid node the next detection will read */
+static double wall_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 static void ensure_nodes(or_world *w) {
+    const double t0 = wall_seconds();
     for (int ai = 0; ai < w->n_assets; ++ai) {
         asset_t *ab = &w->assets[ai];
         if (!ab->has_grid || !ab->grid.lazy) continue;
@@ -866,7 +875,10 @@ static void ensure_nodes(or_world *w) {
         }
         free(need);
     }
+    w->bake_seconds += wall_seconds() - t0;
 }
+
+double or_bake_seconds(const or_world *w) { return w->bake_seconds; }
 
 /* narrow phase of one pair, every sample: phi and world normal (valid = 0 where the
  * sample is outside the grid or the gradient vanishes) */

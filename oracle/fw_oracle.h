@@ -147,6 +147,8 @@ void or_reset_margins(or_world *w);
 int or_get_state(const or_world *w, double *pos, double *quat, double *linvel, double *angvel);
 int or_set_state(or_world *w, const double *pos, const double *quat, const double *linvel,
                  const double *angvel);
+/* Wall seconds spent so far in lazy SDF bakes (set-up work, excluded from step timing). */
+double or_bake_seconds(const or_world *w);
 /* Friction-cone record of the last solve: per contact row of env, (lambda_n, |lambda_t|, mu). */
 int or_get_impulses(const or_world *w, int env, double *out, int cap, int *n_out);
 

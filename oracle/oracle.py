@@ -95,6 +95,8 @@ def lib():
             L.or_get_state.argtypes = [vp, _f64, _f64, _f64, _f64]
             L.or_set_state.argtypes = [vp, _f64, _f64, _f64, _f64]
             L.or_get_impulses.argtypes = [vp, C.c_int, _f64, C.c_int, C.POINTER(C.c_int)]
+            L.or_bake_seconds.argtypes = [vp]
+            L.or_bake_seconds.restype = C.c_double
             L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32]
             L.or_pair_candidates.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
             L.or_reduce.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, vp, C.c_int,
@@ -302,6 +304,9 @@ class OracleWorld:
     def set_state(self, p, q, v, w):
         f = lambda a, k: np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1, k))
         lib().or_set_state(self.h, f(p, 3), f(q, 4), f(v, 3), f(w, 3))
+
+    def bake_seconds(self) -> float:
+        return lib().or_bake_seconds(self.h)
 
     def query_pair(self, env: int, pair: int, n_samples: int):
         phi, nrm, valid = np.zeros(n_samples), np.zeros((n_samples, 3)), np.zeros(n_samples, np.int32)

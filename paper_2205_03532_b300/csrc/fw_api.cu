@@ -368,7 +368,7 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&w->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(w->d_status, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = prepare_detect(cfg->max_patches);
+    if (e == cudaSuccess) e = prepare_detect(kMaxPatchesCap);   // any later world fits
     if (e != cudaSuccess) {
         cudaGetLastError();
         fw_destroy(w);
