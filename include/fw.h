@@ -65,7 +65,7 @@ typedef struct {
     float gravity[3];           /* m/s^2, default (0, 0, -9.81) */
     float dt;                   /* frame time, default 1/60 s (Table perf caption) */
     float contact_offset;       /* candidate iff phi < contact_offset; default 1e-4 m */
-    float cos_patch;            /* normal similarity for Assign/BinReduce; default 0.97 */
+    float cos_patch;            /* normal similarity for Assign/BinReduce; default 0.94 */
     int max_patches;            /* N of Sec. III-C (128 <= N <= 256); default 128 */
     int batch_size;             /* samples per Generate batch; must be 1024 (Sec. III-C) */
     float baumgarte;            /* bias factor for penetrating contacts; default 0.2 */

@@ -619,8 +619,8 @@ static void patch_add_member(patch_t *P, const cand_t *c) {
     }
 }
 
-static void patch_slot_margins(const patch_t *P, margin_t *m) {
-    for (int s = 0; s < NSLOT; ++s)
+static void patch_slot_margins(const patch_t *P, margin_t *m, int exact_phi) {
+    for (int s = exact_phi ? 1 : 0; s < NSLOT; ++s)
         if (P->idx[s] >= 0 && P->second[s] > -INFINITY) mark_len(m, P->best[s] - P->second[s]);
 }
 
@@ -668,8 +668,12 @@ static void add_patch(patch_list_t *L, const patch_t *P, int max_patches, margin
 }
 
 /* Algorithm 1 over one shape pair.  cands must be sorted by sample index. */
+/* exact_phi = 1 when both sides compare the very same phi values (float inputs): the
+ * decisions that compare phi only (FindDeepest, the deepest slot) then cannot differ and
+ * are not counted as margins. */
 static int reduce_pair(const cand_t *cands, int nc, double cos_patch, int max_patches,
-                       int batch_size, or_contact *out, int cap, int *n_patches, margin_t *m) {
+                       int batch_size, or_contact *out, int cap, int *n_patches, margin_t *m,
+                       int exact_phi) {
     patch_list_t L;
     L.cap = max_patches; L.n = 0;
     L.p = (patch_t *)malloc(sizeof(patch_t) * (max_patches > 0 ? max_patches : 1));
@@ -707,7 +711,7 @@ static int reduce_pair(const cand_t *cands, int nc, double cos_patch, int max_pa
                 } else if (cands[i].phi < sphi) sphi = cands[i].phi;
             }
             if (best < 0) break;
-            if (sphi < INFINITY) mark_len(m, sphi - bphi);
+            if (sphi < INFINITY && !exact_phi) mark_len(m, sphi - bphi);
             patch_t P;
             patch_init(&P, &cands[best], m);
             for (int i = start; i < end; ++i) {
@@ -726,7 +730,7 @@ static int reduce_pair(const cand_t *cands, int nc, double cos_patch, int max_pa
     /* emit: patches in list order, distinct slot members in slot order */
     int n = 0;
     for (int j = 0; j < L.n; ++j) {
-        patch_slot_margins(&L.p[j], m);
+        patch_slot_margins(&L.p[j], m, exact_phi);
         for (int s = 0; s < NSLOT; ++s) {
             int id = L.p[j].idx[s], dup = 0;
             if (id < 0) continue;
@@ -765,7 +769,7 @@ int or_reduce(const or_candidate *cand, int n, double cos_patch, int max_patches
     }
     margin_t m = {INFINITY, INFINITY};
     int np = 0;
-    int k = reduce_pair(c, n, cos_patch, max_patches, batch_size, out, cap, &np, &m);
+    int k = reduce_pair(c, n, cos_patch, max_patches, batch_size, out, cap, &np, &m, 1);
     *n_out = k; *n_patches = np;
     *min_margin_len = m.len; *min_margin_dot = m.dot;
     free(c);
@@ -815,7 +819,7 @@ static void detect_pair(or_world *w, int pi) {
     int cap = w->cfg.max_patches * NSLOT;
     if (pc->cap < cap) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * cap); pc->cap = cap; }
     pc->n = reduce_pair(c, nc, w->cfg.cos_patch, w->cfg.max_patches, w->cfg.batch_size,
-                        pc->c, pc->cap, &pc->n_patches, &m);
+                        pc->c, pc->cap, &pc->n_patches, &m, 0);
     pc->m_len = m.len; pc->m_dot = m.dot;
     free(c);
 }
@@ -882,7 +886,7 @@ double or_bake_seconds(const or_world *w) { return w->bake_seconds; }
 
 /* narrow phase of one pair, every sample: phi and world normal (valid = 0 where the
  * sample is outside the grid or the gradient vanishes) */
-int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid) {
+int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid, double *gnorm) {
     ensure_nodes(w);
     const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
     const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
@@ -898,6 +902,7 @@ int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int 
         double gn = ok ? v_norm(g) : 0.0;
         valid[i] = ok && gn >= 1e-12;
         phi[i] = valid[i] ? f : 0.0;
+        if (gnorm) gnorm[i] = gn;
         for (int a = 0; a < 3; ++a) nrm[3 * i + a] = 0.0;
         if (valid[i]) {
             double nb[3];

@@ -132,7 +132,8 @@ int or_step(or_world *w, int n_substeps, int n_iters);
 /* One substep of length hs; detect = 0 reuses the contacts currently stored. */
 int or_substep(or_world *w, double hs, int n_iters, int detect);
 /* Narrow phase of one pair at the current state, every sample of body a. */
-int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid);
+int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid,
+                  double *gnorm);
 /* The pair's candidates (phi < contact_offset) rounded to float, in sample order. */
 int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int cap, int *n_out);
 /* Contact detection + reduction at the current state. */

@@ -97,7 +97,7 @@ def lib():
             L.or_get_impulses.argtypes = [vp, C.c_int, _f64, C.c_int, C.POINTER(C.c_int)]
             L.or_bake_seconds.argtypes = [vp]
             L.or_bake_seconds.restype = C.c_double
-            L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32]
+            L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32, _f64]
             L.or_pair_candidates.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
             L.or_reduce.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, vp, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -174,7 +174,7 @@ def query(grid: np.ndarray, lo, h, dims, pts):
     return phi, grad, valid.astype(bool)
 
 
-def reduce(cands: np.ndarray, cos_patch: float = 0.97, max_patches: int = 128,
+def reduce(cands: np.ndarray, cos_patch: float = 0.94, max_patches: int = 128,
            batch_size: int = 1024):
     """Algorithm 1 on a CANDIDATE_DTYPE array -> (contacts, n_patches, margin_len, margin_dot)."""
     cands = np.ascontiguousarray(cands, dtype=CANDIDATE_DTYPE)
@@ -197,7 +197,7 @@ class OracleWorld:
         cfg.gravity[:] = list(over.get("gravity", g))
         cfg.dt = over.get("dt", getattr(sim, "dt", 1.0 / 60.0))
         cfg.contact_offset = over.get("contact_offset", getattr(sim, "contact_offset", 1e-4))
-        cfg.cos_patch = over.get("cos_patch", getattr(sim, "cos_patch", 0.97))
+        cfg.cos_patch = over.get("cos_patch", getattr(sim, "cos_patch", 0.94))
         cfg.max_patches = over.get("max_patches", getattr(sim, "max_patches", 128))
         cfg.batch_size = over.get("batch_size", getattr(sim, "batch_size", 1024))
         cfg.baumgarte = over.get("baumgarte", getattr(sim, "baumgarte", 0.2))
@@ -310,7 +310,9 @@ class OracleWorld:
 
     def query_pair(self, env: int, pair: int, n_samples: int):
         phi, nrm, valid = np.zeros(n_samples), np.zeros((n_samples, 3)), np.zeros(n_samples, np.int32)
-        lib().or_query_pair(self.h, env, pair, phi, nrm, valid)
+        gn = np.zeros(n_samples)
+        lib().or_query_pair(self.h, env, pair, phi, nrm, valid, gn)
+        self.last_gnorm = gn
         return phi, nrm, valid.astype(bool)
 
     def pair_candidates(self, env: int, pair: int, cap: int = 1 << 20) -> np.ndarray:

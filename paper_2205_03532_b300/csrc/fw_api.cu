@@ -341,7 +341,7 @@ void fw_config_default(fw_config *c) {
     c->gravity[2] = -9.81f;
     c->dt = 1.0f / 60.0f;
     c->contact_offset = 1e-4f;
-    c->cos_patch = 0.97f;
+    c->cos_patch = 0.94f;
     c->max_patches = 128;
     c->batch_size = kBatch;
     c->baumgarte = 0.2f;

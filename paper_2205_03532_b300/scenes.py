@@ -565,7 +565,7 @@ class SimParams:
     frames: int = 120
     gravity: Tuple[float, float, float] = (0.0, 0.0, -9.81)
     contact_offset: float = 1e-4
-    cos_patch: float = 0.97
+    cos_patch: float = 0.94
     max_patches: int = 128
     batch_size: int = 1024
     baumgarte: float = 0.2

@@ -37,7 +37,7 @@ def test_config_defaults_without_gpu():
     cfg = fw.default_config()
     assert cfg.batch_size == 1024 and cfg.max_patches == 128
     assert abs(cfg.dt - 1 / 60) < 1e-7 and abs(cfg.gravity[2] + 9.81) < 1e-6
-    assert abs(cfg.contact_offset - 1e-4) < 1e-9 and abs(cfg.cos_patch - 0.97) < 1e-7
+    assert abs(cfg.contact_offset - 1e-4) < 1e-9 and abs(cfg.cos_patch - 0.94) < 1e-7
 
 
 def test_struct_layouts_match_header():

@@ -123,7 +123,9 @@ def test_equal_depth_tie_goes_to_lowest_sample():
             (6, -1e-4, (0, 1e-3, 0), (0, 0, 1))]
     c, _, ml, _ = O.reduce(_cands(rows))
     assert c["sample"][0] == 4
-    assert ml == 0.0                              # a tie is a zero-margin decision
+    # with identical float inputs a phi tie is resolved the same way by any implementation
+    # (lowest sample), so it is not a rounding-sensitive decision and sets no margin
+    assert ml > 0.0
 
 
 def test_two_member_patch_emits_distinct_points_only():
