@@ -288,6 +288,9 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.hs = hs;
     p.n_iters = n_iters;
     p.n_vel_iters = w->cfg.n_vel_iters;
+    int rc = 0;
+    for (const auto &E : w->envs) rc = std::max(rc, E.row_cap);
+    p.lam_cap = rc <= kLamCapMax ? rc : 0;   // larger envs take the general sweep
     return p;
 }
 
@@ -369,6 +372,7 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (e == cudaSuccess) e = cudaMalloc(&w->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(w->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = prepare_detect(kMaxPatchesCap);   // any later world fits
+    if (e == cudaSuccess) e = prepare_solve(kLamCapMax);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fw_destroy(w);
@@ -679,6 +683,11 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
                 for (int a = 0; a < 3; ++a) om[a] = s * P.axis[a];
             }
             for (int a = 0; a < 3; ++a) { w->h_vel.push_back(v[a]); w->h_ang.push_back(om[a]); }
+        }
+        E.movable = -1;
+        for (int i = 0; i < n_per_env; ++i) {
+            const int t = bd[e * n_per_env + i].type;
+            if (t == FW_BODY_DYNAMIC || t == FW_BODY_FIXED_AXIS) E.movable = (E.movable == -1) ? i : -2;
         }
         for (int k = 0; k < n_pairs; ++k) {
             PairDev P;

@@ -60,7 +60,8 @@ struct EnvDev {
     int first_pair, n_pairs;
     int row_off;             // offset of the env's rows in the row buffer
     int row_cap;             // rows available to the env
-    int pad_[2];
+    int movable;             // local id of the only movable body, -1 none, -2 several
+    int pad_;
 };
 
 // A reduced contact on the device.  sample_patch = sample | (patch << 24).
@@ -100,6 +101,7 @@ struct SimParams {
     float gravity[3];
     float hs;
     int n_iters, n_vel_iters;
+    int lam_cap;                           // rows whose impulses fit in shared memory (fast path)
 };
 
 // launchers (defined in the .cu files)
@@ -117,6 +119,9 @@ size_t detect_smem_bytes(int max_patches);
 cudaError_t launch_detect(const SimParams &p, cudaStream_t s);
 cudaError_t launch_reduce_list(const SimParams &p, const float *d_cands, int n, DContact *out,
                                int *d_count, int *d_npatch, cudaStream_t s);
+constexpr int kLamCapMax = 4096;   // fast-path impulse rows per env held in shared memory
+size_t solve_smem_bytes(int lam_cap);
+cudaError_t prepare_solve(int max_lam_cap);
 cudaError_t launch_solve(const SimParams &p, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
 

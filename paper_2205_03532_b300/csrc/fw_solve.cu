@@ -1,8 +1,15 @@
 // fw_solve.cu -- contact solution of one substep (Sec. III-B): external forces,
 // constraint preparation, Gauss-Seidel sweeps with Coulomb friction, integration.
 // One warp per environment: lanes prepare rows and integrate bodies in parallel; the
-// sweep itself is the serial Gauss-Seidel chain and runs on lane 0 with the env's body
-// velocities in shared memory.
+// sweep itself is the serial Gauss-Seidel chain and runs on lane 0.
+//
+// Two sweep forms compute the same update.  Fast form (an env with at most one movable
+// body, i.e. every other body static or kinematic): each contact is written from the
+// movable body's side (directions negated when it is the pair's SDF body, the partner's
+// prescribed velocity folded into a constant), 9 float4 per contact; the body's velocity
+// stays in registers, the rows stream from global memory through a cp.async ring in
+// shared memory and the accumulated impulses live in shared memory.  General form
+// (several movable bodies): full two-body rows, velocities in shared memory.
 //
 // Update rule (velocity-level projected Gauss-Seidel; the paper cites the solver without
 // restating it): per contact, the normal row
@@ -19,6 +26,18 @@ namespace fw {
 namespace {
 
 constexpr int kMaxBodies = 8;
+constexpr int kRing = 16;     // rows in flight in the fast sweep's shared-memory ring
+constexpr int kRowF4 = 9;     // float4 per fast row
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_ring() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 struct BodySm {
     float v[kMaxBodies][3], w[kMaxBodies][3];
@@ -108,6 +127,108 @@ __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
     }
 }
 
+// Fast row of one contact, from the side of the movable body m (a or b of the pair):
+//   f[0] = (d_n, k_n)        f[1] = (r x d_n, bias)     f[2] = (I^-1 (r x d_n), mu)
+//   f[3] = (d_1, k_t1)       f[4] = (r x d_1, e_1)      f[5] = (I^-1 (r x d_1), k_t2)
+//   f[6] = (d_2, e_2)        f[7] = (r x d_2, e_n)      f[8] = (I^-1 (r x d_2), 0)
+// d = s n, s t1, s t2 with s = +1 when m is body a (impulses +lambda d on m either way);
+// e = -d . (v_o + w_o x r_o) is the partner's constant contribution to the row velocity.
+__device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, const BodySm &B, int a, int b, int m,
+                                               float mu, float hs, float baumgarte) {
+    if (m != a && m != b) {   // neither body of this pair can move: the contact does nothing
+        f[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const bool ma = (m == a);
+    const int o = ma ? b : a;
+    const V3 n = ld3(c.n), xa = ld3(c.xa);
+    const float phi = c.phi;
+    const V3 xb = xa - phi * n;
+    const V3 rm = (ma ? xa : xb) - smv(B.com, m);
+    const V3 ro = (ma ? xb : xa) - smv(B.com, o);
+    const float sg = ma ? 1.0f : -1.0f;
+    V3 t1, t2;
+    tangent_basis(n, t1, t2);
+    const V3 dn = sg * n, d1 = sg * t1, d2 = sg * t2;
+    const V3 uo = smv(B.v, o) + cross(smv(B.w, o), ro);
+    const float ima = B.invm[m];
+    const V3 rdn = cross(rm, dn), rd1 = cross(rm, d1), rd2 = cross(rm, d2);
+    const V3 idn = sym_mul(B.Iinv[m], rdn), id1 = sym_mul(B.Iinv[m], rd1), id2 = sym_mul(B.Iinv[m], rd2);
+    const float kn = eff_mass(ima, 0.0f, rdn, idn, v3(0, 0, 0), v3(0, 0, 0));
+    const float kt1 = eff_mass(ima, 0.0f, rd1, id1, v3(0, 0, 0), v3(0, 0, 0));
+    const float kt2 = eff_mass(ima, 0.0f, rd2, id2, v3(0, 0, 0), v3(0, 0, 0));
+    const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    f[0] = make_float4(dn.x, dn.y, dn.z, kn);
+    f[1] = make_float4(rdn.x, rdn.y, rdn.z, bias);
+    f[2] = make_float4(idn.x, idn.y, idn.z, mu);
+    f[3] = make_float4(d1.x, d1.y, d1.z, kt1);
+    f[4] = make_float4(rd1.x, rd1.y, rd1.z, -dot(d1, uo));
+    f[5] = make_float4(id1.x, id1.y, id1.z, kt2);
+    f[6] = make_float4(d2.x, d2.y, d2.z, -dot(d2, uo));
+    f[7] = make_float4(rd2.x, rd2.y, rd2.z, -dot(dn, uo));
+    f[8] = make_float4(id2.x, id2.y, id2.z, 0.0f);
+}
+
+// `passes` Gauss-Seidel sweeps over nr fast rows (lane 0 only).  Row q of the sweep
+// sequence is fetched kRing rows ahead into ring slot q % kRing; one commit group per
+// row keeps "group q complete" equivalent to "at most kRing - 1 groups pending".
+__device__ void sweep_fast(const float4 *rows, int nr, int passes, float4 *ring, float4 *lam, V3 &va, V3 &wa,
+                           float ima, bool use_bias) {
+    const int total = nr * passes;
+    if (total == 0) return;
+    for (int q = 0; q < kRing; ++q) {
+        if (q < total) {
+            const float4 *src = rows + kRowF4 * (q % nr);
+            float4 *dst = ring + kRowF4 * q;
+            for (int k = 0; k < kRowF4; ++k) cp_async16(dst + k, src + k);
+        }
+        cp_async_commit();
+    }
+    int r = 0;
+    for (int q = 0; q < total; ++q) {
+        cp_async_wait_ring();
+        float4 *slot = ring + kRowF4 * (q % kRing);
+        const float4 f0 = slot[0], f1 = slot[1], f2 = slot[2], f3 = slot[3], f4 = slot[4];
+        const float4 f5 = slot[5], f6 = slot[6], f7 = slot[7], f8 = slot[8];
+        if (f0.w != 0.0f) {
+            float4 L = lam[r];
+            // normal row
+            const V3 dn = v3(f0.x, f0.y, f0.z);
+            float jv = dot(dn, va) + dot(v3(f1.x, f1.y, f1.z), wa) + f7.w;
+            if (use_bias) jv += f1.w;
+            const float ln = fmaxf(L.x - f0.w * jv, 0.0f);
+            const float dl = ln - L.x;
+            va = va + (dl * ima) * dn;
+            wa = wa + dl * v3(f2.x, f2.y, f2.z);
+            // friction rows, projected jointly on the disk of radius mu lambda_n
+            const V3 d1 = v3(f3.x, f3.y, f3.z), d2 = v3(f6.x, f6.y, f6.z);
+            const float j1 = dot(d1, va) + dot(v3(f4.x, f4.y, f4.z), wa) + f4.w;
+            const float j2 = dot(d2, va) + dot(v3(f7.x, f7.y, f7.z), wa) + f6.w;
+            float l1 = L.y - f3.w * j1, l2 = L.z - f5.w * j2;
+            const float lim = f2.w * ln;
+            const float lt = sqrtf(l1 * l1 + l2 * l2);
+            if (lt > lim) {
+                const float sc = lt > 0.0f ? lim / lt : 0.0f;
+                l1 *= sc;
+                l2 *= sc;
+            }
+            const float e1 = l1 - L.y, e2 = l2 - L.z;
+            va = va + ima * (e1 * d1 + e2 * d2);
+            wa = wa + e1 * v3(f5.x, f5.y, f5.z) + e2 * v3(f8.x, f8.y, f8.z);
+            L.x = ln; L.y = l1; L.z = l2;
+            lam[r] = L;
+        }
+        const int qn = q + kRing;
+        if (qn < total) {
+            const float4 *src = rows + kRowF4 * (qn % nr);
+            for (int k = 0; k < kRowF4; ++k) cp_async16(slot + k, src + k);
+        }
+        cp_async_commit();
+        if (++r == nr) r = 0;
+    }
+    cp_async_wait_all();
+}
+
 __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
     const int e = blockIdx.x;
     const int lane = threadIdx.x;
@@ -159,19 +280,45 @@ __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
     __syncwarp();
     const int nr = row_base[E.n_pairs];
     Row *rows = p.rows + E.row_off;
+    extern __shared__ __align__(16) float4 dyn_smem[];
+    const int m = E.movable;
+    const bool fast = (m != -2) && nr <= p.lam_cap;
+    float4 *frows = reinterpret_cast<float4 *>(rows);
+    float4 *lam = dyn_smem;
+    float4 *ring = dyn_smem + p.lam_cap;
     // 2. constraint preparation, one contact per lane
     for (int k = 0; k < E.n_pairs; ++k) {
         const int pi = E.first_pair + k;
         const PairDev P = p.pairs[pi];
         const int cnt = row_base[k + 1] - row_base[k];
-        for (int i = lane; i < cnt; i += 32)
-            build_row(rows[row_base[k] + i], p.contacts[(long long)pi * p.cap_pair + i], B, P.local_a, P.local_b,
-                      P.mu, hs, p.baumgarte);
+        for (int i = lane; i < cnt; i += 32) {
+            const DContact &c = p.contacts[(long long)pi * p.cap_pair + i];
+            if (fast) {
+                if (m >= 0) {
+                    build_fast_row(frows + kRowF4 * (row_base[k] + i), c, B, P.local_a, P.local_b, m, P.mu, hs,
+                                   p.baumgarte);
+                    lam[row_base[k] + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {
+                build_row(rows[row_base[k] + i], c, B, P.local_a, P.local_b, P.mu, hs, p.baumgarte);
+            }
+        }
     }
+    __threadfence_block();
     __syncwarp();
-    // 3. Gauss-Seidel sweeps
-    if (lane == 0)
-        for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
+    // 3. Gauss-Seidel sweeps (no movable body: nothing to solve)
+    if (lane == 0) {
+        if (fast) {
+            if (m >= 0) {
+                V3 va = smv(B.v, m), wa = smv(B.w, m);
+                sweep_fast(frows, nr, p.n_iters, ring, lam, va, wa, B.invm[m], true);
+                smv_set(B.v, m, va);
+                smv_set(B.w, m, wa);
+            }
+        } else {
+            for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
+        }
+    }
     __syncwarp();
     // 4. integration
     if (lane < E.n_bodies) {
@@ -209,8 +356,18 @@ __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
     }
     __syncwarp();
     // 5. optional bias-free sweeps
-    if (lane == 0)
-        for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
+    if (lane == 0 && p.n_vel_iters > 0) {
+        if (fast) {
+            if (m >= 0) {
+                V3 va = smv(B.v, m), wa = smv(B.w, m);
+                sweep_fast(frows, nr, p.n_vel_iters, ring, lam, va, wa, B.invm[m], false);
+                smv_set(B.v, m, va);
+                smv_set(B.w, m, wa);
+            }
+        } else {
+            for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
+        }
+    }
     __syncwarp();
     if (lane < E.n_bodies) {
         const int bi = E.first_body + lane;
@@ -239,9 +396,16 @@ cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+size_t solve_smem_bytes(int lam_cap) { return sizeof(float4) * ((size_t)lam_cap + (size_t)kRing * kRowF4); }
+
+cudaError_t prepare_solve(int max_lam_cap) {
+    return cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)solve_smem_bytes(max_lam_cap));
+}
+
 cudaError_t launch_solve(const SimParams &p, cudaStream_t s) {
     if (p.n_envs == 0) return cudaSuccess;
-    solve_kernel<<<p.n_envs, 32, 0, s>>>(p);
+    solve_kernel<<<p.n_envs, 32, solve_smem_bytes(p.lam_cap), s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,160 @@
+"""GPU solver paths against the FP64 oracle on identical contacts, and invariants.
+
+The solve kernel has a fast form (at most one movable body per env; rows written from
+that body's side) and a general form (several movable bodies).  Each is checked after one
+substep on contacts computed by the oracle and rounded to float32 for both sides:
+positions within 1e-6 m, orientations within 1e-6 rad."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O
+from paper_2205_03532_b300 import scenes as S
+
+
+def _fw():
+    from paper_2205_03532_b300 import fw
+    return fw
+
+
+def _rot_angle(q1, q2):
+    d = abs(float(np.dot(q1 / np.linalg.norm(q1), q2 / np.linalg.norm(q2))))
+    return 2 * math.acos(min(1.0, d))
+
+
+def _pair_worlds(descs, assets, pairs, **cfg):
+    """GPU and oracle worlds with one env of the given bodies."""
+    fw = _fw()
+    gw = fw.World(**cfg)
+    ow = O.OracleWorld(**cfg)
+    for V, T, Sp, res, pad in assets:
+        a = gw.add_mesh_asset(V, T, Sp)
+        b = ow.add_asset(V, T, Sp)
+        assert a == b
+        if res:
+            gw.bake_sdf(a, res, pad)
+            ow.bake(b, res, pad)
+    bodies = np.zeros((1, len(descs)), S.BODY_DTYPE)
+    for i, d in enumerate(descs):
+        bodies[0, i] = d
+    gw.add_env_bodies(bodies, np.array(pairs, np.int32))
+    ow.add_envs(bodies, np.array(pairs, np.int32))
+    return gw, ow
+
+
+def _solve_same_contacts(gw, ow, hs, n_iters):
+    fw = _fw()
+    p, q, v, w = gw.get_state()
+    ow.set_state(p, q, v, w)
+    ow.collide()
+    oc, _, _ = ow.contacts(0)
+    assert len(oc) > 0
+    gc = np.zeros(len(oc), fw.CONTACT_DTYPE)
+    gc["sample"], gc["patch"], gc["phi"] = oc["sample"], oc["patch"], oc["phi"]
+    gc["xa"], gc["n"] = oc["xa"], oc["n"]
+    gc["xb"] = gc["xa"] - gc["phi"][:, None] * gc["n"]
+    same = oc.copy()
+    same["phi"], same["xa"], same["n"] = gc["phi"], gc["xa"], gc["n"]
+    same["xb"] = same["xa"] - same["phi"][:, None] * same["n"]
+    gw.set_contacts(0, gc)
+    ow.set_contacts(0, same)
+    gw.substep(hs, n_iters, detect=False)
+    ow.substep(hs, n_iters, detect=False)
+    gs, os_ = gw.get_state(), ow.state()
+    for i in range(len(gs[0])):
+        assert np.linalg.norm(gs[0][i] - os_[0][i]) <= 1e-6, (i, gs[0][i], os_[0][i])
+        assert _rot_angle(gs[1][i].astype(np.float64), os_[1][i]) <= 1e-6
+        assert np.linalg.norm(gs[2][i] - os_[2][i]) <= 1e-4 * max(1.0, np.linalg.norm(os_[2][i]))
+    return len(oc)
+
+
+def _cube(half=0.01, n=700, seed=0):
+    V, T = S.box_mesh(half, half, half)
+    return V, T, S.sample_surface(V, T, n, np.random.default_rng(seed))
+
+
+def test_general_path_two_dynamic_bodies():
+    V, T, Sp = _cube()
+    q = S.quat_mul(S.quat_axis_angle([0, 0, 1], 0.3), S.quat_axis_angle([1, 0, 0], 0.2))
+    descs = [S._body(0, S.DYNAMIC, (0.0, 0.004, 0.0203), q, 0.4, 0.0, (0, 0, -0.3), (0.5, -1, 0)),
+             S._body(1, S.DYNAMIC, (0, 0, 0), (0, 0, 0, 1), 0.4, 0.02, (0.01, 0, 0.05))]
+    gw, ow = _pair_worlds(descs, [(V, T, Sp, None, 0), (V, T, None, 48, 3e-3)], [(0, 1)], gravity=(0, 0, -9.81))
+    assert _solve_same_contacts(gw, ow, 1 / 240, 16) > 0
+
+
+def test_fast_path_with_the_sdf_body_moving():
+    """The point body is static, the SDF body is dynamic: rows are written from the SDF
+    body's side (negated directions)."""
+    GV, GT = S.box_mesh(0.05, 0.05, 0.005)
+    Gs = S.sample_surface(GV, GT, 6000, np.random.default_rng(1))
+    V, T, _ = _cube()
+    tilt = S.quat_mul(S.quat_axis_angle([1, 0, 0], 0.1), S.quat_axis_angle([0, 1, 0], 0.05))
+    descs = [S._body(0, S.STATIC, (0, 0, -0.005), (0, 0, 0, 1), 0.6),
+             S._body(1, S.DYNAMIC, (0.002, 0.001, 0.0105), tilt, 0.6, 0.0, (0.05, 0, -0.1), (0, 0.5, 0))]
+    gw, ow = _pair_worlds(descs, [(GV, GT, Gs, None, 0), (V, T, None, 48, 3e-3)], [(0, 1)])
+    assert _solve_same_contacts(gw, ow, 1 / 240, 16) > 0
+
+
+def test_fast_path_kinematic_partner_velocity_enters_the_rows():
+    """A cube resting on a kinematic slab that moves sideways: friction must drag it."""
+    V, T, Sp = _cube()
+    GV, GT = S.box_mesh(0.1, 0.1, 0.01)
+    descs = [S._body(0, S.DYNAMIC, (0, 0, 0.01), (0, 0, 0, 1), 0.5),
+             S._body(1, S.KINEMATIC, (0, 0, -0.01), (0, 0, 0, 1), 0.5, 0.0, (0.2, 0, 0), (0, 0, 0.3))]
+    gw, ow = _pair_worlds(descs, [(V, T, Sp, None, 0), (GV, GT, None, 64, 2e-3)], [(0, 1)])
+    _solve_same_contacts(gw, ow, 1 / 240, 16)
+    v = gw.get_state()[2]
+    assert v[0, 0] > 1e-3          # dragged along by friction
+    np.testing.assert_allclose(v[1], [0.2, 0, 0], atol=0)
+
+
+def test_free_fall_on_gpu_matches_closed_form():
+    fw = _fw()
+    V, T, Sp = _cube()
+    w = fw.World()
+    a = w.add_mesh_asset(V, T, Sp)
+    b = np.zeros((1, 1), S.BODY_DTYPE)
+    b[0, 0] = S._body(a, S.DYNAMIC, (0, 0, 1.0), (0, 0, 0, 1), 0.5, 0.0, (0.1, 0, 0.5))
+    w.add_env_bodies(b, np.zeros((0, 2), np.int32))
+    K = 40
+    for _ in range(K // 4):
+        w.step(4, 8)
+    p, _, v, _ = w.get_state()
+    hs = np.float32(1 / 60) / 4
+    g = 9.81
+    z = 1.0 + 0.5 * hs * K - g * hs * hs * K * (K + 1) / 2
+    assert abs(p[0, 2] - z) <= 2e-6 and abs(v[0, 2] - (0.5 - g * hs * K)) <= 1e-5
+
+
+def test_frictionless_two_body_momentum_on_gpu():
+    fw = _fw()
+    V, T, Sp = _cube(n=800)
+    w = fw.World(gravity=(0, 0, 0))
+    a = w.add_mesh_asset(V, T, Sp)
+    bb = w.add_mesh_asset(V, T, None)
+    w.bake_sdf(bb, 48, 3e-3)
+    q = S.quat_mul(S.quat_axis_angle([0, 0, 1], 0.3), S.quat_axis_angle([1, 0, 0], 0.2))
+    b = np.zeros((1, 2), S.BODY_DTYPE)
+    b[0, 0] = S._body(a, S.DYNAMIC, (0.0, 0.004, 0.0205), q, 0.0, 0.0, (0, 0, -0.3), (0.5, -1, 0))
+    b[0, 1] = S._body(bb, S.DYNAMIC, (0, 0, 0), (0, 0, 0, 1), 0.0, 0.02, (0.01, 0, 0.05))
+    w.add_env_bodies(b, np.array([[0, 1]], np.int32))
+    m, _, I = w.get_mass(a)
+    mb = float(np.float32(0.02))
+    masses, inertias = [m, mb], [I, I * mb / m]
+
+    def momenta():
+        p, _, v, om = w.get_state()
+        P = sum(masses[i] * v[i].astype(np.float64) for i in range(2))
+        L = sum(inertias[i] @ om[i] + masses[i] * np.cross(p[i].astype(np.float64), v[i]) for i in range(2))
+        return P, L
+
+    P0, L0 = momenta()
+    for _ in range(20):
+        w.step(4, 16)
+    P, L = momenta()
+    np.testing.assert_allclose(P, P0, atol=2e-8)     # float32 rounding of ~1e-3 kg m/s
+    np.testing.assert_allclose(L, L0, atol=2e-10)
+    assert abs(w.get_state()[2][1, 2] - 0.05) > 1e-3  # they did collide
