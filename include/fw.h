@@ -240,6 +240,28 @@ FW_API fw_status fw_query_pair(fw_world *w, int env, int pair, float *phi, float
 FW_API fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_contact *out,
                            int cap, int *n_out, int *n_patches);
 
+/* Algorithm 1 on candidates already in device memory, without allocating anything.
+ * The paper has no counterpart to this call; it exists for callers that must not
+ * allocate device memory once they are running -- for example a control loop with a
+ * fixed latency budget (cudaMalloc and cudaFree can stall the whole device), or a host
+ * program whose memory pool owns the GPU (PyTorch's caching allocator) and lets no one
+ * else allocate.  Same reduction code and results as fw_reduce.
+ *   d_cands   device array of n candidates, samples strictly increasing and < 65536
+ *             (the limit of the call's fixed scratch), n <= 65536;
+ *   d_out     device array for up to cap contacts (fw_contact, pair = 0);
+ *   d_counts  device int[2]: number of contacts (may exceed cap; only cap are written)
+ *             and number of patches; (-1, 0) when the device finds the candidates
+ *             unsorted, repeated or out of range.
+ * Scratch: one 2.2 MB block of device memory that every GPU loading the library holds
+ * until the process exits, shared by all calls and keeping the last call's contents
+ * (nothing in it needs to start at zero).  Calls that overlap on the GPU (two streams, two
+ * worlds) race on it: order them on one stream.  The first call on a device looks the
+ * block's address up (no allocation); make that first call before any stream capture.
+ * Enqueued on the world's stream; does not synchronise.
+ * Errors: FW_ERR_ARG for NULL pointers or n > 65536 (a clear message in fw_last_error). */
+FW_API fw_status fw_reduce_noalloc(fw_world *w, const fw_candidate *d_cands, int n, fw_contact *d_out,
+                                   int cap, int *d_counts);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Waits for the world's stream and reports the device status word. */

@@ -954,6 +954,20 @@ fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_contact *o
     return k > cap ? fail(w, FW_ERR_OVERFLOW, "fw_reduce: cap too small") : FW_OK;
 }
 
+fw_status fw_reduce_noalloc(fw_world *w, const fw_candidate *d_cands, int n, fw_contact *d_out, int cap,
+                            int *d_counts) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n < 0 || cap < 0 || !d_counts || (n > 0 && !d_cands) || (cap > 0 && !d_out))
+        return fail(w, FW_ERR_ARG, "fw_reduce_noalloc: bad argument");
+    if (n > kNoAllocMaxSamples)
+        return fail(w, FW_ERR_ARG, "fw_reduce_noalloc: more than 65536 candidates (its fixed scratch holds "
+                                   "sample ids 0..65535)");
+    const SimParams p = sim_params(w, w->cfg.dt, 0);
+    CK(launch_reduce_noalloc(p, w->cfg.device, reinterpret_cast<const float *>(d_cands), n, d_out, cap, d_counts,
+                             w->stream));
+    return FW_OK;
+}
+
 fw_status fw_sync(fw_world *w) {
     if (!ready(w)) return FW_ERR_ARG;
     CK(cudaStreamSynchronize(w->stream));

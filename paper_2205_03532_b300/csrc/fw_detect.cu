@@ -447,7 +447,115 @@ __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free reduction (fw_reduce_noalloc).  Its scratch lives in g_noalloc below:
+// [0, 2*kNoAllocMaxSamples) the per-sample winner lines, then the staged contacts of one
+// call, then one float4 of counters.  The kernel first checks the caller's candidates
+// (strictly increasing samples below kNoAllocMaxSamples); on failure it only writes
+// counts = (-1, 0).
+constexpr int kStageF4 = 2 * kMaxPatchesCap * kSlots;   // DContact = 2 float4
+constexpr int kNoAllocF4 = 2 * kNoAllocMaxSamples + kStageF4 + 1;
+
+__global__ void __launch_bounds__(kT) reduce_noalloc_kernel(SimParams p, const float *cands, int n, float4 *scr,
+                                                            fw_contact *out, int cap, int *counts) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int *ci = reinterpret_cast<const int *>(cands);
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += kT) {
+        const int sm = ci[8 * i];
+        bad |= sm < 0 || sm >= kNoAllocMaxSamples || (i > 0 && ci[8 * (i - 1)] >= sm);
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) { counts[0] = -1; counts[1] = 0; }
+        return;
+    }
+    const int NP = p.max_patches + 1;
+    Smem S = carve(smem_raw, NP);
+    init_patches(S, NP);
+    __syncthreads();
+    DContact *stage = reinterpret_cast<DContact *>(scr + 2 * kNoAllocMaxSamples);
+    int *stage_count = reinterpret_cast<int *>(scr + 2 * kNoAllocMaxSamples + kStageF4);
+    int start = 0;
+    while (start < n) {
+        const int bidx = ci[8 * start] / kBatch;
+        int end = start;
+        while (end < n && ci[8 * end] / kBatch == bidx) ++end;
+        if (threadIdx.x == 0) S.misc[0] = 0;
+        __syncthreads();
+        for (int c0 = start; c0 < end; c0 += kT) {
+            const int c = c0 + threadIdx.x;
+            const bool ok = c < end;
+            V3 x = v3(0, 0, 0), nn = v3(0, 0, 0);
+            float phi = 0.f;
+            int sample = 0;
+            if (ok) {
+                const float *r = cands + 8 * c;
+                sample = ci[8 * c];
+                phi = r[1];
+                x = v3(r[2], r[3], r[4]);
+                nn = v3(r[5], r[6], r[7]);
+            }
+            compact_push(S, ok, x, nn, phi, sample);
+        }
+        reduce_batch(S, NP, p.max_patches, p.cos_patch, scr);
+        start = end;
+    }
+    if (threadIdx.x < 32) emit_contacts(S, NP, scr, stage, p.max_patches * kSlots, stage_count, p.status);
+    __syncthreads();
+    const int k = *stage_count;
+    for (int i = threadIdx.x; i < k && i < cap; i += kT) {
+        const DContact c = stage[i];
+        fw_contact o;
+        o.sample = c.sample_patch & 0xFFFFFF;
+        o.patch = (int)((unsigned)c.sample_patch >> 24);
+        o.pair = 0;
+        o.phi = c.phi;
+        for (int a = 0; a < 3; ++a) {
+            o.xa[a] = c.xa[a];
+            o.n[a] = c.n[a];
+            o.xb[a] = __fsub_rn(c.xa[a], __fmul_rn(c.phi, c.n[a]));   // rounded as fw_reduce's host code
+        }
+        out[i] = o;
+    }
+    if (threadIdx.x == 0) { counts[0] = k; counts[1] = S.misc[1]; }
+}
+
 }  // namespace
+
+// The scratch of fw_reduce_noalloc: a fixed 2.2 MB block in every device that loads the
+// library, shared by all calls.
+static __device__ __align__(256) float4 g_noalloc[kNoAllocF4];
+
+namespace {
+float4 *g_noalloc_dev[64];    // its device address per device ordinal (0 until set up)
+bool g_noalloc_ready[64];
+}  // namespace
+
+// First use on a device (that device current): look up the device address of g_noalloc
+// (the host-side name is only a stand-in) and raise the kernel's shared-memory limit.
+// Neither step allocates memory.
+cudaError_t noalloc_setup(int device) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_noalloc_ready[device]) return cudaSuccess;
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(reduce_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(kMaxPatchesCap + 1));
+    if (e != cudaSuccess) return e;
+    g_noalloc_dev[device] = static_cast<float4 *>(ptr);
+    g_noalloc_ready[device] = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d_cands, int n, fw_contact *d_out,
+                                  int cap, int *d_counts, cudaStream_t s) {
+    cudaError_t e = noalloc_setup(device);
+    if (e != cudaSuccess) return e;
+    reduce_noalloc_kernel<<<1, kT, smem_bytes(p.max_patches + 1), s>>>(p, d_cands, n, g_noalloc_dev[device], d_out,
+                                                                        cap, d_counts);
+    return cudaGetLastError();
+}
 
 size_t detect_smem_bytes(int max_patches) { return smem_bytes(max_patches + 1); }
 

@@ -117,6 +117,9 @@ cudaError_t launch_query_pair(const SimParams &p, int pair, float *phi, float *n
 cudaError_t prepare_detect(int max_patches);
 size_t detect_smem_bytes(int max_patches);
 cudaError_t launch_detect(const SimParams &p, cudaStream_t s);
+constexpr int kNoAllocMaxSamples = 65536;   // sample ids accepted by fw_reduce_noalloc
+cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d_cands, int n, fw_contact *d_out,
+                                  int cap, int *d_counts, cudaStream_t s);
 cudaError_t launch_reduce_list(const SimParams &p, const float *d_cands, int n, DContact *out,
                                int *d_count, int *d_npatch, cudaStream_t s);
 constexpr int kLamCapMax = 4096;   // fast-path impulse rows per env held in shared memory

@@ -25,7 +25,7 @@ STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_OOM", -3: "FW_ERR_CUDA", -4:
 ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_asset", "fw_bake_sdf",
                  "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
-                 "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_sync",
+                 "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "fw_query_sdf": (st, [vp, i, vp, i, vp, vp, i]),
         "fw_query_pair": (st, [vp, i, i, vp, vp, i]),
         "fw_reduce": (st, [vp, vp, i, vp, i, C.POINTER(i), C.POINTER(i)]),
+        "fw_reduce_noalloc": (st, [vp, vp, i, vp, i, vp]),
         "fw_sync": (st, [vp]),
         "fw_set_timing": (st, [vp, i]),
         "fw_get_timings": (st, [vp, vp, i]),
@@ -279,6 +280,11 @@ class World:
         self._check(self.lib.fw_reduce(self.h, c.ctypes.data if len(c) else None, len(c), out.ctypes.data,
                                        cap, C.byref(n), C.byref(npch)))
         return out[: n.value].copy(), npch.value
+
+    def reduce_noalloc(self, d_cands, n: int, d_out, cap: int, d_counts):
+        """fw_reduce_noalloc on device buffers (torch CUDA tensors or raw pointers)."""
+        ptr = lambda t: t if isinstance(t, int) else t.data_ptr()
+        self._check(self.lib.fw_reduce_noalloc(self.h, ptr(d_cands), n, ptr(d_out), cap, ptr(d_counts)))
 
     # -- diagnostics
     def set_timing(self, enable: bool):
