@@ -48,6 +48,7 @@ struct fw_world {
     DContact *d_contacts = nullptr;
     int *d_counts = nullptr;
     float4 *d_scratch = nullptr;
+    float4 *d_cand_ovf = nullptr;
     Row *d_rows = nullptr;
     unsigned *d_status = nullptr;
     int dev_bodies = 0;          // bodies whose state is on the device
@@ -222,7 +223,7 @@ fw_status ensure_device(fw_world *w) {
     }
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
-    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows);
+    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_cand_ovf);
     const int np = (int)w->pairs.size(), ne = (int)w->envs.size();
     const int cp = cap_pair(w);
     if (nb > 0) {
@@ -248,6 +249,7 @@ fw_status ensure_device(fw_world *w) {
             sl = std::max(sl, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
         w->scratch_len = std::max(sl, 2LL);
         CK(cudaMalloc(&w->d_scratch, sizeof(float4) * w->scratch_len));
+        CK(cudaMalloc(&w->d_cand_ovf, sizeof(float4) * (size_t)np * detect_spill_f4_per_pair()));
     }
     if (ne > 0) {
         CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
@@ -274,6 +276,7 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.contacts = w->d_contacts;
     p.counts = w->d_counts;
     p.scratch = w->d_scratch;
+    p.cand_ovf = w->d_cand_ovf;
     p.rows = w->d_rows;
     p.status = w->d_status;
     p.n_pairs = (int)w->pairs.size();
@@ -394,6 +397,7 @@ fw_status fw_destroy(fw_world *w) {
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
+    dfree(w->d_cand_ovf);
     for (auto e : w->ev_pool) cudaEventDestroy(e);
     for (auto e : w->ev_used) cudaEventDestroy(e);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);

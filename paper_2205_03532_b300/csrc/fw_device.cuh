@@ -75,36 +75,42 @@ __device__ __forceinline__ void tangent_basis(V3 n, V3 &t1, V3 &t2) {
 // 1/h), so the cell fraction is exact to float32 rounding of f itself instead of carrying
 // the ~N * 2^-24 voxel error of a plain float32 (x - lo) * inv_h.
 // ----------------------------------------------------------------------------------------
+// Returns whether x lies in [lo, lo + (dim-1) h]; c, f are always usable (clamped to a
+// cell of the grid), so callers can load the corners before knowing the answer.
 __device__ __forceinline__ bool grid_coord(float x, float lo, float inv_h, float inv_h_lo, int dim,
                                            int &c, float &f) {
-    float s = x - lo;
-    float bb = s - x;
-    float e = (x - (s - bb)) + (-lo - bb);       // s + e == x - lo exactly
-    float p = s * inv_h;
-    float pe = __fmaf_rn(s, inv_h, -p);          // s * inv_h - p exactly
-    float corr = pe + __fmaf_rn(s, inv_h_lo, e * inv_h);
-    if (!(p > -2.0f && p < (float)dim + 1.0f)) return false;   // also rejects NaN
-    float fl = floorf(p);
-    float fr = (p - fl) + corr;
+    const float s = x - lo;
+    const float bb = s - x;
+    const float e = (x - (s - bb)) + (-lo - bb);     // s + e == x - lo exactly
+    const float p = s * inv_h;
+    const float pe = __fmaf_rn(s, inv_h, -p);        // s * inv_h - p exactly
+    const float corr = pe + __fmaf_rn(s, inv_h_lo, e * inv_h);
+    bool ok = (p > -2.0f && p < (float)dim + 1.0f);  // also rejects NaN
+    const float pc = ok ? p : 0.0f;
+    float fl = floorf(pc);
+    float fr = (pc - fl) + (ok ? corr : 0.0f);
     if (fr < 0.0f) { fl -= 1.0f; fr += 1.0f; }
     else if (fr >= 1.0f) { fl += 1.0f; fr -= 1.0f; }
     int ci = (int)fl;
-    if (ci < 0 || ci > dim - 1 || (ci == dim - 1 && fr > 0.0f)) return false;
-    if (ci == dim - 1) { ci = dim - 2; fr = 1.0f; }
+    ok = ok && ci >= 0 && ci <= dim - 1 && !(ci == dim - 1 && fr > 0.0f);
+    if (ci >= dim - 1) { ci = dim - 2; fr = 1.0f; }
+    if (ci < 0) { ci = 0; fr = 0.0f; }
     c = ci;
     f = fr;
-    return true;
+    return ok;
 }
 
 __device__ __forceinline__ float lerp_(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
+// Trilinear value and gradient; the corner loads are always in bounds and issued before
+// the in-grid test is used, so several lookups can overlap their memory latency.
 template <bool kHalf>
 __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
     int ci, cj, ck;
     float fx, fy, fz;
-    if (!grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx)) return false;
-    if (!grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy)) return false;
-    if (!grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz)) return false;
+    const bool okx = grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx);
+    const bool oky = grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy);
+    const bool okz = grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz);
     const long long nx = g.dims[0], nxy = (long long)g.dims[0] * g.dims[1];
     const long long o = (long long)ck * nxy + (long long)cj * nx + ci;
     float v000, v100, v010, v110, v001, v101, v011, v111;
@@ -122,14 +128,14 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
         v011 = __ldg(b + nxy + nx); v111 = __ldg(b + nxy + nx + 1);
     }
     // value: lerp along x, then y, then z
-    float a00 = lerp_(v000, v100, fx), a10 = lerp_(v010, v110, fx);
-    float a01 = lerp_(v001, v101, fx), a11 = lerp_(v011, v111, fx);
-    float b0 = lerp_(a00, a10, fy), b1 = lerp_(a01, a11, fy);
-    float val = lerp_(b0, b1, fz);
+    const float a00 = lerp_(v000, v100, fx), a10 = lerp_(v010, v110, fx);
+    const float a01 = lerp_(v001, v101, fx), a11 = lerp_(v011, v111, fx);
+    const float b0 = lerp_(a00, a10, fy), b1 = lerp_(a01, a11, fy);
+    const float val = lerp_(b0, b1, fz);
     // gradient: bilinear blend of the node differences along each axis
-    float gx = lerp_(lerp_(v100 - v000, v110 - v010, fy), lerp_(v101 - v001, v111 - v011, fy), fz);
-    float gy = lerp_(lerp_(v010 - v000, v110 - v100, fx), lerp_(v011 - v001, v111 - v101, fx), fz);
-    float gz = lerp_(lerp_(v001 - v000, v101 - v100, fx), lerp_(v011 - v010, v111 - v110, fx), fy);
+    const float gx = lerp_(lerp_(v100 - v000, v110 - v010, fy), lerp_(v101 - v001, v111 - v011, fy), fz);
+    const float gy = lerp_(lerp_(v010 - v000, v110 - v100, fx), lerp_(v011 - v001, v111 - v101, fx), fz);
+    const float gz = lerp_(lerp_(v001 - v000, v101 - v100, fx), lerp_(v011 - v010, v111 - v110, fx), fy);
     if (kHalf) {   // nodes hold phi / h
         phi = val * g.h;
         grad = v3(gx, gy, gz);
@@ -137,7 +143,7 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
         phi = val;
         grad = g.inv_h * v3(gx, gy, gz);
     }
-    return true;
+    return okx && oky && okz;
 }
 
 __device__ __forceinline__ bool sdf_lookup_any(const AssetDev &g, V3 x, float &phi, V3 &grad) {

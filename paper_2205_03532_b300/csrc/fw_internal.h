@@ -102,6 +102,7 @@ struct SimParams {
     float hs;
     int n_iters, n_vel_iters;
     int lam_cap;                           // rows whose impulses fit in shared memory (fast path)
+    float4 *cand_ovf;                      // per pair: candidates of a batch beyond shared memory
 };
 
 // launchers (defined in the .cu files)
@@ -116,6 +117,7 @@ cudaError_t launch_query_sdf(const AssetDev &g, const float *pts, int n, float *
 cudaError_t launch_query_pair(const SimParams &p, int pair, float *phi, float *nrm, cudaStream_t s, int ns);
 cudaError_t prepare_detect(int max_patches);
 size_t detect_smem_bytes(int max_patches);
+long long detect_spill_f4_per_pair();
 cudaError_t launch_detect(const SimParams &p, cudaStream_t s);
 constexpr int kNoAllocMaxSamples = 65536;   // sample ids accepted by fw_reduce_noalloc
 cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d_cands, int n, fw_contact *d_out,

@@ -128,7 +128,7 @@ __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
 }
 
 // Fast row of one contact, from the side of the movable body m (a or b of the pair):
-//   f[0] = (d_n, k_n)        f[1] = (r x d_n, bias)     f[2] = (I^-1 (r x d_n), mu)
+//   f[0] = (d_n, k_n)        f[1] = (r x d_n, bias+e_n) f[2] = (I^-1 (r x d_n), mu)
 //   f[3] = (d_1, k_t1)       f[4] = (r x d_1, e_1)      f[5] = (I^-1 (r x d_1), k_t2)
 //   f[6] = (d_2, e_2)        f[7] = (r x d_2, e_n)      f[8] = (I^-1 (r x d_2), 0)
 // d = s n, s t1, s t2 with s = +1 when m is body a (impulses +lambda d on m either way);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, con
     const float kt2 = eff_mass(ima, 0.0f, rd2, id2, v3(0, 0, 0), v3(0, 0, 0));
     const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
     f[0] = make_float4(dn.x, dn.y, dn.z, kn);
-    f[1] = make_float4(rdn.x, rdn.y, rdn.z, bias);
+    f[1] = make_float4(rdn.x, rdn.y, rdn.z, bias - dot(dn, uo));
     f[2] = make_float4(idn.x, idn.y, idn.z, mu);
     f[3] = make_float4(d1.x, d1.y, d1.z, kt1);
     f[4] = make_float4(rd1.x, rd1.y, rd1.z, -dot(d1, uo));
@@ -169,64 +169,68 @@ __device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, con
     f[8] = make_float4(id2.x, id2.y, id2.z, 0.0f);
 }
 
-// `passes` Gauss-Seidel sweeps over nr fast rows (lane 0 only).  Row q of the sweep
-// sequence is fetched kRing rows ahead into ring slot q % kRing; one commit group per
-// row keeps "group q complete" equivalent to "at most kRing - 1 groups pending".
+// `passes` Gauss-Seidel sweeps over nr fast rows.  The whole warp runs the loop with
+// identical values in every lane (uniform control flow); lanes 0..8 copy one float4 each
+// of the row kRing positions ahead into the ring with one cp.async instruction, and lane
+// 0 stores the impulses.  One commit group per row keeps "row q has landed" equal to "at
+// most kRing - 1 groups pending"; __syncwarp makes the landed row visible to all lanes and
+// orders the reads of a slot before its refill.
 __device__ void sweep_fast(const float4 *rows, int nr, int passes, float4 *ring, float4 *lam, V3 &va, V3 &wa,
                            float ima, bool use_bias) {
+    const int lane = threadIdx.x & 31;
     const int total = nr * passes;
     if (total == 0) return;
+    int pf = 0;   // row index of the next prefetch
     for (int q = 0; q < kRing; ++q) {
-        if (q < total) {
-            const float4 *src = rows + kRowF4 * (q % nr);
-            float4 *dst = ring + kRowF4 * q;
-            for (int k = 0; k < kRowF4; ++k) cp_async16(dst + k, src + k);
-        }
+        if (q < total && lane < kRowF4) cp_async16(ring + kRowF4 * q + lane, rows + kRowF4 * pf + lane);
         cp_async_commit();
+        if (++pf == nr) pf = 0;
     }
-    int r = 0;
+    int r = 0, slot = 0;
     for (int q = 0; q < total; ++q) {
         cp_async_wait_ring();
-        float4 *slot = ring + kRowF4 * (q % kRing);
-        const float4 f0 = slot[0], f1 = slot[1], f2 = slot[2], f3 = slot[3], f4 = slot[4];
-        const float4 f5 = slot[5], f6 = slot[6], f7 = slot[7], f8 = slot[8];
+        __syncwarp();
+        float4 *sp = ring + kRowF4 * slot;
+        const float4 f0 = sp[0];
         if (f0.w != 0.0f) {
+            const float4 f1 = sp[1], f2 = sp[2], f3 = sp[3], f4 = sp[4], f5 = sp[5], f6 = sp[6], f7 = sp[7], f8 = sp[8];
             float4 L = lam[r];
-            // normal row
-            const V3 dn = v3(f0.x, f0.y, f0.z);
-            float jv = dot(dn, va) + dot(v3(f1.x, f1.y, f1.z), wa) + f7.w;
-            if (use_bias) jv += f1.w;
-            const float ln = fmaxf(L.x - f0.w * jv, 0.0f);
+            // normal row: two independent three-term chains
+            float jv = (f0.x * va.x + f0.y * va.y + f0.z * va.z) + (f1.x * wa.x + f1.y * wa.y + f1.z * wa.z);
+            jv += use_bias ? f1.w : f7.w;
+            const float ln = fmaxf(__fmaf_rn(-f0.w, jv, L.x), 0.0f);
             const float dl = ln - L.x;
-            va = va + (dl * ima) * dn;
-            wa = wa + dl * v3(f2.x, f2.y, f2.z);
+            const float dlm = dl * ima;
+            va = v3(__fmaf_rn(dlm, f0.x, va.x), __fmaf_rn(dlm, f0.y, va.y), __fmaf_rn(dlm, f0.z, va.z));
+            wa = v3(__fmaf_rn(dl, f2.x, wa.x), __fmaf_rn(dl, f2.y, wa.y), __fmaf_rn(dl, f2.z, wa.z));
             // friction rows, projected jointly on the disk of radius mu lambda_n
-            const V3 d1 = v3(f3.x, f3.y, f3.z), d2 = v3(f6.x, f6.y, f6.z);
-            const float j1 = dot(d1, va) + dot(v3(f4.x, f4.y, f4.z), wa) + f4.w;
-            const float j2 = dot(d2, va) + dot(v3(f7.x, f7.y, f7.z), wa) + f6.w;
-            float l1 = L.y - f3.w * j1, l2 = L.z - f5.w * j2;
+            const float j1 = (f3.x * va.x + f3.y * va.y + f3.z * va.z) + (f4.x * wa.x + f4.y * wa.y + f4.z * wa.z) + f4.w;
+            const float j2 = (f6.x * va.x + f6.y * va.y + f6.z * va.z) + (f7.x * wa.x + f7.y * wa.y + f7.z * wa.z) + f6.w;
+            float l1 = __fmaf_rn(-f3.w, j1, L.y), l2 = __fmaf_rn(-f5.w, j2, L.z);
             const float lim = f2.w * ln;
-            const float lt = sqrtf(l1 * l1 + l2 * l2);
-            if (lt > lim) {
-                const float sc = lt > 0.0f ? lim / lt : 0.0f;
+            const float lt2 = l1 * l1 + l2 * l2;
+            if (lt2 > lim * lim) {
+                const float sc = lim * rsqrtf(lt2);
                 l1 *= sc;
                 l2 *= sc;
             }
             const float e1 = l1 - L.y, e2 = l2 - L.z;
-            va = va + ima * (e1 * d1 + e2 * d2);
-            wa = wa + e1 * v3(f5.x, f5.y, f5.z) + e2 * v3(f8.x, f8.y, f8.z);
-            L.x = ln; L.y = l1; L.z = l2;
-            lam[r] = L;
+            const float e1m = e1 * ima, e2m = e2 * ima;
+            va = v3(__fmaf_rn(e2m, f6.x, __fmaf_rn(e1m, f3.x, va.x)), __fmaf_rn(e2m, f6.y, __fmaf_rn(e1m, f3.y, va.y)),
+                    __fmaf_rn(e2m, f6.z, __fmaf_rn(e1m, f3.z, va.z)));
+            wa = v3(__fmaf_rn(e2, f8.x, __fmaf_rn(e1, f5.x, wa.x)), __fmaf_rn(e2, f8.y, __fmaf_rn(e1, f5.y, wa.y)),
+                    __fmaf_rn(e2, f8.z, __fmaf_rn(e1, f5.z, wa.z)));
+            if (lane == 0) lam[r] = make_float4(ln, l1, l2, 0.0f);
         }
-        const int qn = q + kRing;
-        if (qn < total) {
-            const float4 *src = rows + kRowF4 * (qn % nr);
-            for (int k = 0; k < kRowF4; ++k) cp_async16(slot + k, src + k);
-        }
+        __syncwarp();
+        if (q + kRing < total && lane < kRowF4) cp_async16(sp + lane, rows + kRowF4 * pf + lane);
         cp_async_commit();
+        if (++pf == nr) pf = 0;
         if (++r == nr) r = 0;
+        slot = (slot + 1) & (kRing - 1);
     }
     cp_async_wait_all();
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
@@ -307,17 +311,14 @@ __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
     __threadfence_block();
     __syncwarp();
     // 3. Gauss-Seidel sweeps (no movable body: nothing to solve)
-    if (lane == 0) {
-        if (fast) {
-            if (m >= 0) {
-                V3 va = smv(B.v, m), wa = smv(B.w, m);
-                sweep_fast(frows, nr, p.n_iters, ring, lam, va, wa, B.invm[m], true);
-                smv_set(B.v, m, va);
-                smv_set(B.w, m, wa);
-            }
-        } else {
-            for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
+    if (fast) {
+        if (m >= 0) {
+            V3 va = smv(B.v, m), wa = smv(B.w, m);
+            sweep_fast(frows, nr, p.n_iters, ring, lam, va, wa, B.invm[m], true);
+            if (lane == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
         }
+    } else if (lane == 0) {
+        for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
     }
     __syncwarp();
     // 4. integration
@@ -356,15 +357,14 @@ __global__ void __launch_bounds__(32) solve_kernel(SimParams p) {
     }
     __syncwarp();
     // 5. optional bias-free sweeps
-    if (lane == 0 && p.n_vel_iters > 0) {
+    if (p.n_vel_iters > 0) {
         if (fast) {
             if (m >= 0) {
                 V3 va = smv(B.v, m), wa = smv(B.w, m);
                 sweep_fast(frows, nr, p.n_vel_iters, ring, lam, va, wa, B.invm[m], false);
-                smv_set(B.v, m, va);
-                smv_set(B.w, m, wa);
+                if (lane == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
             }
-        } else {
+        } else if (lane == 0) {
             for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
         }
     }
