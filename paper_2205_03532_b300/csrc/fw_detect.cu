@@ -24,7 +24,8 @@ __constant__ float c_sin6[6] = {0.0f, 0.8660254037844386f, 0.8660254037844386f, 
 // One warp's working set.  NP = max_patches + 1 (the last patch is the one being built).
 struct WarpSmem {
     unsigned long long *keys;     // kSlots x NP
-    float *pn, *pa, *pt1, *pt2;   // 3 x NP each, component-major
+    float4 *pn4;                  // NP patch normals (x, y, z, 0)
+    float *pa, *pt1, *pt2;        // 3 x NP each, component-major
     float *cx, *cy, *cz, *cnx, *cny, *cnz, *cphi;
     int *cidx;                    // C each
     short *cst;                   // kBatch: -1 unassigned, -2 joining, -3 consumed, >= 0 patch
@@ -34,16 +35,17 @@ struct WarpSmem {
 };
 
 __host__ __device__ inline size_t warp_smem_bytes(int NP, int C) {
-    const size_t b = (size_t)kSlots * NP * 8 + (size_t)12 * NP * 4 + (size_t)8 * C * 4 + (size_t)kBatch * 2 + 16;
+    const size_t b = (size_t)kSlots * NP * 8 + (size_t)13 * NP * 4 + (size_t)8 * C * 4 + (size_t)kBatch * 2 + 16;
     return (b + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ WarpSmem carve(unsigned char *base, int NP, int C, float4 *ovf) {
     WarpSmem s;
-    s.keys = reinterpret_cast<unsigned long long *>(base);
+    s.pn4 = reinterpret_cast<float4 *>(base);                      // the slice starts 16-byte aligned
+    s.keys = reinterpret_cast<unsigned long long *>(s.pn4 + NP);
     float *f = reinterpret_cast<float *>(s.keys + kSlots * NP);
-    s.pn = f; s.pa = f + 3 * NP; s.pt1 = f + 6 * NP; s.pt2 = f + 9 * NP;
-    f += 12 * NP;
+    s.pa = f; s.pt1 = f + 3 * NP; s.pt2 = f + 6 * NP;
+    f += 9 * NP;
     s.cx = f; s.cy = f + C; s.cz = f + 2 * C; s.cnx = f + 3 * C; s.cny = f + 4 * C; s.cnz = f + 5 * C;
     s.cphi = f + 6 * C;
     s.cidx = reinterpret_cast<int *>(f + 7 * C);
@@ -194,7 +196,8 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
         int best = -1;
         float bd = -3.0f;
         for (int j = 0; j < np0; ++j) {
-            const float d = dot(n, pvec(S.pn, NP, j));
+            const float4 q = S.pn4[j];
+            const float d = n.x * q.x + n.y * q.y + n.z * q.z;
             if (d > bd) { bd = d; best = j; }
         }
         short st = -1;
@@ -236,9 +239,10 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
         const V3 ab = cpos(S, cb);
         V3 t1, t2;
         tangent_basis(nb, t1, t2);
-        // BinReduce: the remaining candidates with a similar normal join
-        unsigned long long lk[kSlots];
-        for (int s = 0; s < kSlots; ++s) lk[s] = 0ull;
+        // BinReduce: the remaining candidates with a similar normal join; their slot keys
+        // go straight into patch T's keys with shared 64-bit atomics
+        for (int s = lane; s < kSlots; s += 32) S.keys[s * NP + T] = 0ull;
+        __syncwarp();
         for (int c = lane; c < nc; c += 32) {
             if (S.cst[c] != -1) continue;
             if (c == cb || dot(cnrm(S, c), nb) >= cos_patch) {
@@ -246,27 +250,24 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
                 const V3 x = cpos(S, c);
                 const float ph = cphi(S, c);
                 const int id = cidx(S, c);
-                for (int s = 0; s < kSlots; ++s) {
-                    const unsigned long long k = slot_key(slot_score(s, x, ph, ab, t1, t2), id);
-                    lk[s] = (k > lk[s]) ? k : lk[s];
-                }
+                for (int s = 0; s < kSlots; ++s)
+                    atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, x, ph, ab, t1, t2), id));
             }
         }
-        unsigned long long gk[kSlots];
-        for (int s = 0; s < kSlots; ++s) gk[s] = warp_max_u64(lk[s]);
+        __syncwarp();
         // the lane holding a winner publishes its data
         for (int c = lane; c < nc; c += 32) {
             if (S.cst[c] != -2) continue;
             const int id = cidx(S, c);
             bool won = false;
-            for (int s = 0; s < kSlots; ++s) won |= (key_sample(gk[s]) == id);
+            for (int s = 0; s < kSlots; ++s) won |= (key_sample(S.keys[s * NP + T]) == id);
             if (won) scratch_put(scr, id, cpos(S, c), cphi(S, c), cnrm(S, c));
             S.cst[c] = -3;   // consumed
         }
         if (lane == 0) {
-            set_pvec(S.pn, NP, T, nb); set_pvec(S.pa, NP, T, ab);
+            S.pn4[T] = make_float4(nb.x, nb.y, nb.z, 0.0f);
+            set_pvec(S.pa, NP, T, ab);
             set_pvec(S.pt1, NP, T, t1); set_pvec(S.pt2, NP, T, t2);
-            for (int s = 0; s < kSlots; ++s) S.keys[s * NP + T] = gk[s];
         }
         __syncwarp();
         // AddPatch: append below capacity, else replace the most similar patch if the new
@@ -278,7 +279,8 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
         } else {
             unsigned long long bk = 0ull;
             for (int j = lane; j < npat; j += 32) {
-                const unsigned long long k = ((unsigned long long)ord_f32(dot(nb, pvec(S.pn, NP, j))) << 32) |
+                const float4 q = S.pn4[j];
+                const unsigned long long k = ((unsigned long long)ord_f32(nb.x * q.x + nb.y * q.y + nb.z * q.z) << 32) |
                                              (unsigned)(0xFFFFFFFFu - (unsigned)j);
                 bk = (k > bk) ? k : bk;
             }
@@ -293,8 +295,9 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
             mold = __shfl_sync(0xffffffffu, mold, 0);
             if (mnew > mold) dst = ks;
         }
-        if (dst >= 0 && lane < 12) {
-            float *arr = (lane < 3) ? S.pn : (lane < 6) ? S.pa : (lane < 9) ? S.pt1 : S.pt2;
+        if (dst >= 0 && lane == 9) S.pn4[dst] = S.pn4[T];
+        if (dst >= 0 && lane < 9) {
+            float *arr = (lane < 3) ? S.pa : (lane < 6) ? S.pt1 : S.pt2;
             const int comp = lane % 3;
             arr[comp * NP + dst] = arr[comp * NP + T];
         }

@@ -136,7 +136,7 @@ __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
 __device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, const BodySm &B, int a, int b, int m,
                                                float mu, float hs, float baumgarte) {
     if (m != a && m != b) {   // neither body of this pair can move: the contact does nothing
-        f[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < kRowF4; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     const bool ma = (m == a);
@@ -158,6 +158,10 @@ __device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, con
     const float kt1 = eff_mass(ima, 0.0f, rd1, id1, v3(0, 0, 0), v3(0, 0, 0));
     const float kt2 = eff_mass(ima, 0.0f, rd2, id2, v3(0, 0, 0), v3(0, 0, 0));
     const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    if (kn == 0.0f) {   // the movable body cannot respond along n: the contact does nothing
+        for (int k = 0; k < kRowF4; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     f[0] = make_float4(dn.x, dn.y, dn.z, kn);
     f[1] = make_float4(rdn.x, rdn.y, rdn.z, bias - dot(dn, uo));
     f[2] = make_float4(idn.x, idn.y, idn.z, mu);
@@ -173,62 +177,87 @@ __device__ __forceinline__ void build_fast_row(float4 *f, const DContact &c, con
 // identical values in every lane (uniform control flow); lanes 0..8 copy one float4 each
 // of the row kRing positions ahead into the ring with one cp.async instruction, and lane
 // 0 stores the impulses.  One commit group per row keeps "row q has landed" equal to "at
-// most kRing - 1 groups pending"; __syncwarp makes the landed row visible to all lanes and
-// orders the reads of a slot before its refill.
+// most kRing - 1 groups pending"; __syncwarp makes a landed row visible to all lanes and
+// orders the reads of a slot before its refill.  Row q+1 is read into registers while
+// row q is solved, so the shared-memory latency stays off the Gauss-Seidel chain.  A row
+// written all-zero (a contact neither body can act on) leaves every value unchanged.
+__device__ __forceinline__ void ring_read(const float4 *sp, float4 f[kRowF4]) {
+#pragma unroll
+    for (int k = 0; k < kRowF4; ++k) f[k] = sp[k];
+}
+
+// One row of the fast sweep: solves the row held in f while the next row (slot nslot)
+// is read into g.
+struct SweepState {
+    V3 va, wa;
+    int r, slot, pf;
+};
+
+__device__ __forceinline__ void sweep_row(const float4 (&f)[kRowF4], float4 (&g)[kRowF4], SweepState &st,
+                                          const float4 *rows, int nr, float4 *ring, float4 *lam, float ima,
+                                          bool use_bias, int lane) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 2) : "memory");
+    __syncwarp();
+    const int nslot = (st.slot + 1) & (kRing - 1);
+    ring_read(ring + kRowF4 * nslot, g);
+    const float4 L = lam[st.r];
+    V3 va = st.va, wa = st.wa;
+    // normal row: two independent three-term chains
+    float jv = (f[0].x * va.x + f[0].y * va.y + f[0].z * va.z) + (f[1].x * wa.x + f[1].y * wa.y + f[1].z * wa.z);
+    jv += use_bias ? f[1].w : f[7].w;
+    const float ln = fmaxf(__fmaf_rn(-f[0].w, jv, L.x), 0.0f);
+    const float dl = ln - L.x;
+    const float dlm = dl * ima;
+    va = v3(__fmaf_rn(dlm, f[0].x, va.x), __fmaf_rn(dlm, f[0].y, va.y), __fmaf_rn(dlm, f[0].z, va.z));
+    wa = v3(__fmaf_rn(dl, f[2].x, wa.x), __fmaf_rn(dl, f[2].y, wa.y), __fmaf_rn(dl, f[2].z, wa.z));
+    // friction rows, projected jointly on the disk of radius mu lambda_n
+    const float j1 = (f[3].x * va.x + f[3].y * va.y + f[3].z * va.z) + (f[4].x * wa.x + f[4].y * wa.y + f[4].z * wa.z) + f[4].w;
+    const float j2 = (f[6].x * va.x + f[6].y * va.y + f[6].z * va.z) + (f[7].x * wa.x + f[7].y * wa.y + f[7].z * wa.z) + f[6].w;
+    const float t1 = __fmaf_rn(-f[3].w, j1, L.y), t2 = __fmaf_rn(-f[5].w, j2, L.z);
+    const float lim = f[2].w * ln;
+    const float lt2 = t1 * t1 + t2 * t2;
+    const float sc = (lt2 > lim * lim) ? lim * rsqrtf(lt2) : 1.0f;
+    const float l1 = t1 * sc, l2 = t2 * sc;
+    const float e1 = l1 - L.y, e2 = l2 - L.z;
+    const float e1m = e1 * ima, e2m = e2 * ima;
+    st.va = v3(__fmaf_rn(e2m, f[6].x, __fmaf_rn(e1m, f[3].x, va.x)), __fmaf_rn(e2m, f[6].y, __fmaf_rn(e1m, f[3].y, va.y)),
+               __fmaf_rn(e2m, f[6].z, __fmaf_rn(e1m, f[3].z, va.z)));
+    st.wa = v3(__fmaf_rn(e2, f[8].x, __fmaf_rn(e1, f[5].x, wa.x)), __fmaf_rn(e2, f[8].y, __fmaf_rn(e1, f[5].y, wa.y)),
+               __fmaf_rn(e2, f[8].z, __fmaf_rn(e1, f[5].z, wa.z)));
+    if (lane == 0) lam[st.r] = make_float4(ln, l1, l2, 0.0f);
+    __syncwarp();
+    // refill this slot with the row kRing positions ahead (past the end: an unused copy)
+    if (lane < kRowF4) cp_async16(ring + kRowF4 * st.slot + lane, rows + kRowF4 * st.pf + lane);
+    cp_async_commit();
+    if (++st.pf == nr) st.pf = 0;
+    if (++st.r == nr) st.r = 0;
+    st.slot = nslot;
+}
+
 __device__ void sweep_fast(const float4 *rows, int nr, int passes, float4 *ring, float4 *lam, V3 &va, V3 &wa,
                            float ima, bool use_bias) {
     const int lane = threadIdx.x & 31;
     const int total = nr * passes;
     if (total == 0) return;
-    int pf = 0;   // row index of the next prefetch
+    SweepState st;
+    st.va = va; st.wa = wa; st.r = 0; st.slot = 0; st.pf = 0;
     for (int q = 0; q < kRing; ++q) {
-        if (q < total && lane < kRowF4) cp_async16(ring + kRowF4 * q + lane, rows + kRowF4 * pf + lane);
+        if (lane < kRowF4) cp_async16(ring + kRowF4 * q + lane, rows + kRowF4 * st.pf + lane);
         cp_async_commit();
-        if (++pf == nr) pf = 0;
+        if (++st.pf == nr) st.pf = 0;
     }
-    int r = 0, slot = 0;
-    for (int q = 0; q < total; ++q) {
-        cp_async_wait_ring();
-        __syncwarp();
-        float4 *sp = ring + kRowF4 * slot;
-        const float4 f0 = sp[0];
-        if (f0.w != 0.0f) {
-            const float4 f1 = sp[1], f2 = sp[2], f3 = sp[3], f4 = sp[4], f5 = sp[5], f6 = sp[6], f7 = sp[7], f8 = sp[8];
-            float4 L = lam[r];
-            // normal row: two independent three-term chains
-            float jv = (f0.x * va.x + f0.y * va.y + f0.z * va.z) + (f1.x * wa.x + f1.y * wa.y + f1.z * wa.z);
-            jv += use_bias ? f1.w : f7.w;
-            const float ln = fmaxf(__fmaf_rn(-f0.w, jv, L.x), 0.0f);
-            const float dl = ln - L.x;
-            const float dlm = dl * ima;
-            va = v3(__fmaf_rn(dlm, f0.x, va.x), __fmaf_rn(dlm, f0.y, va.y), __fmaf_rn(dlm, f0.z, va.z));
-            wa = v3(__fmaf_rn(dl, f2.x, wa.x), __fmaf_rn(dl, f2.y, wa.y), __fmaf_rn(dl, f2.z, wa.z));
-            // friction rows, projected jointly on the disk of radius mu lambda_n
-            const float j1 = (f3.x * va.x + f3.y * va.y + f3.z * va.z) + (f4.x * wa.x + f4.y * wa.y + f4.z * wa.z) + f4.w;
-            const float j2 = (f6.x * va.x + f6.y * va.y + f6.z * va.z) + (f7.x * wa.x + f7.y * wa.y + f7.z * wa.z) + f6.w;
-            float l1 = __fmaf_rn(-f3.w, j1, L.y), l2 = __fmaf_rn(-f5.w, j2, L.z);
-            const float lim = f2.w * ln;
-            const float lt2 = l1 * l1 + l2 * l2;
-            if (lt2 > lim * lim) {
-                const float sc = lim * rsqrtf(lt2);
-                l1 *= sc;
-                l2 *= sc;
-            }
-            const float e1 = l1 - L.y, e2 = l2 - L.z;
-            const float e1m = e1 * ima, e2m = e2 * ima;
-            va = v3(__fmaf_rn(e2m, f6.x, __fmaf_rn(e1m, f3.x, va.x)), __fmaf_rn(e2m, f6.y, __fmaf_rn(e1m, f3.y, va.y)),
-                    __fmaf_rn(e2m, f6.z, __fmaf_rn(e1m, f3.z, va.z)));
-            wa = v3(__fmaf_rn(e2, f8.x, __fmaf_rn(e1, f5.x, wa.x)), __fmaf_rn(e2, f8.y, __fmaf_rn(e1, f5.y, wa.y)),
-                    __fmaf_rn(e2, f8.z, __fmaf_rn(e1, f5.z, wa.z)));
-            if (lane == 0) lam[r] = make_float4(ln, l1, l2, 0.0f);
-        }
-        __syncwarp();
-        if (q + kRing < total && lane < kRowF4) cp_async16(sp + lane, rows + kRowF4 * pf + lane);
-        cp_async_commit();
-        if (++pf == nr) pf = 0;
-        if (++r == nr) r = 0;
-        slot = (slot + 1) & (kRing - 1);
+    float4 f[kRowF4], g[kRowF4];
+    cp_async_wait_ring();
+    __syncwarp();
+    ring_read(ring, f);
+    int q = 0;
+    for (; q + 1 < total; q += 2) {   // two rows per trip, the register sets trade roles
+        sweep_row(f, g, st, rows, nr, ring, lam, ima, use_bias, lane);
+        sweep_row(g, f, st, rows, nr, ring, lam, ima, use_bias, lane);
     }
+    if (q < total) sweep_row(f, g, st, rows, nr, ring, lam, ima, use_bias, lane);
+    va = st.va;
+    wa = st.wa;
     cp_async_wait_all();
     __syncwarp();
 }
