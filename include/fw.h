@@ -275,6 +275,17 @@ FW_API fw_status fw_sync(fw_world *w);
 FW_API fw_status fw_set_timing(fw_world *w, int enable);
 FW_API fw_status fw_get_timings(fw_world *w, float *ms, int n);
 
+/* Launch shape of the solve kernel.  envs_per_warp in {1, 2, 4, 8}: that many environments
+ * share one warp, each on 32 / envs_per_warp lanes (fewer, longer-lived warps when the
+ * env count exceeds the device's schedulers); warps_per_block in 1..4.  0 for either
+ * lets the library choose from the env count and the device (the default).  A value that
+ * does not fit the device's shared memory for this world is lowered when launching.
+ * Results do not depend on the shape (each env runs the same arithmetic in any lane
+ * group).  Errors: FW_ERR_ARG for values outside those sets.  fw_get_solve_shape returns
+ * the shape the next fw_step will launch. */
+FW_API fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_per_block);
+FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block);
+
 /* Sizes: n_envs, n_bodies, n_pairs (any pointer may be NULL). */
 FW_API fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs);
 

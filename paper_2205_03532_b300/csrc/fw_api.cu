@@ -57,6 +57,9 @@ struct fw_world {
     // graph
     cudaGraphExec_t gexec = nullptr;
     int g_sub = -1, g_iters = -1;
+    // device limits and the solve's launch shape (0: chosen from the env count)
+    int n_sm = 0, max_dyn_smem[4] = {0, 0, 0, 0};
+    int solve_groups = 0, solve_warps = 0;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -297,6 +300,10 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     return p;
 }
 
+SolveShape current_solve_shape(const fw_world *w, const SimParams &p) {
+    return solve_shape(p.n_envs, p.lam_cap, w->solve_groups, w->solve_warps, w->max_dyn_smem, w->n_sm);
+}
+
 fw_status check_status(fw_world *w) {
     unsigned st = 0;
     CK(cudaMemcpy(&st, w->d_status, sizeof st, cudaMemcpyDeviceToHost));
@@ -324,11 +331,12 @@ cudaEvent_t take_event(fw_world *w) {
 fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs, int n_iters, bool detect,
                            bool timed) {
     SimParams p = sim_params(w, hs, n_iters);
+    const SolveShape sh = current_solve_shape(w, p);
     for (int k = 0; k < n_substeps; ++k) {
         if (timed) CK(cudaEventRecord(take_event(w), s));
         if (detect) CK(launch_detect(p, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
-        CK(launch_solve(p, s));
+        CK(launch_solve(p, sh, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
     }
     return FW_OK;
@@ -375,7 +383,11 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (e == cudaSuccess) e = cudaMalloc(&w->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(w->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = prepare_detect(kMaxPatchesCap);   // any later world fits
-    if (e == cudaSuccess) e = prepare_solve(kLamCapMax);
+    int optin = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
+    if (e == cudaSuccess) e = prepare_solve(optin, w->max_dyn_smem);
+    if (e == cudaSuccess && w->max_dyn_smem[0] < (int)solve_smem_bytes(kLamCapMax)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         cudaGetLastError();
         fw_destroy(w);
@@ -1002,6 +1014,26 @@ fw_status fw_get_timings(fw_world *w, float *ms, int n) {
     w->ev_used.clear();
     ms[0] = (float)det; ms[1] = (float)sol; ms[2] = (float)nd; ms[3] = (float)ns;
     for (int i = 4; i < n; ++i) ms[i] = 0.f;
+    return FW_OK;
+}
+
+fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_per_block) {
+    if (!w) return FW_ERR_ARG;
+    if (!(envs_per_warp == 0 || envs_per_warp == 1 || envs_per_warp == 2 || envs_per_warp == 4 || envs_per_warp == 8) ||
+        warps_per_block < 0 || warps_per_block > kSolveMaxWarps)
+        return fail(w, FW_ERR_ARG, "fw_set_solve_shape: envs_per_warp in {0,1,2,4,8}, warps_per_block in 0..4");
+    if (w->solve_groups != envs_per_warp || w->solve_warps != warps_per_block) drop_graph(w);
+    w->solve_groups = envs_per_warp;
+    w->solve_warps = warps_per_block;
+    return FW_OK;
+}
+
+fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block) {
+    if (!w) return FW_ERR_ARG;
+    const SimParams p = sim_params(w, 1.0f, 1);
+    const SolveShape sh = current_solve_shape(w, p);
+    if (envs_per_warp) *envs_per_warp = sh.groups;
+    if (warps_per_block) *warps_per_block = sh.warps;
     return FW_OK;
 }
 

@@ -125,9 +125,22 @@ cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d
 cudaError_t launch_reduce_list(const SimParams &p, const float *d_cands, int n, DContact *out,
                                int *d_count, int *d_npatch, cudaStream_t s);
 constexpr int kLamCapMax = 4096;   // fast-path impulse rows per env held in shared memory
+constexpr int kMaxPairsPerEnv = 63;
+constexpr int kSolveMaxWarps = 4;  // warps per solve block (one per scheduler of an SM)
+// Launch shape of the solve: `groups` envs per warp (32 / groups lanes each), `warps` warps
+// per block, `smem` dynamic shared memory per block.
+struct SolveShape {
+    int groups, warps;
+    size_t smem;
+};
 size_t solve_smem_bytes(int lam_cap);
-cudaError_t prepare_solve(int max_lam_cap);
-cudaError_t launch_solve(const SimParams &p, cudaStream_t s);
+// Allows each solve instance (1, 2, 4, 8 envs per warp) the largest dynamic shared memory
+// that fits beside its static part in `optin` bytes; returns those limits in max_dyn.
+cudaError_t prepare_solve(int optin, int max_dyn[4]);
+// groups / warps <= 0 choose automatically: as few envs per warp as still give every
+// scheduler of the device (n_sm x 4) at most about one warp.
+SolveShape solve_shape(int n_envs, int lam_cap, int groups, int warps, const int max_dyn[4], int n_sm);
+cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
 
 }  // namespace fw

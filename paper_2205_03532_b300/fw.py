@@ -26,7 +26,8 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
-                 "fw_set_timing", "fw_get_timings", "fw_get_counts", "fw_launches_per_step",
+                 "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_get_solve_shape",
+                 "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
 
 
@@ -87,6 +88,8 @@ def load_library(path: str = LIB_PATH):
         "fw_sync": (st, [vp]),
         "fw_set_timing": (st, [vp, i]),
         "fw_get_timings": (st, [vp, vp, i]),
+        "fw_set_solve_shape": (st, [vp, i, i]),
+        "fw_get_solve_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
         "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "fw_launches_per_step": (i, [vp, i]),
         "fw_last_error": (C.c_char_p, [vp]),
@@ -295,6 +298,14 @@ class World:
         self._check(self.lib.fw_get_timings(self.h, ms.ctypes.data, 4))
         return {"detect_ms": float(ms[0]), "solve_ms": float(ms[1]), "detect_launches": int(ms[2]),
                 "solve_launches": int(ms[3])}
+
+    def set_solve_shape(self, envs_per_warp: int = 0, warps_per_block: int = 0):
+        self._check(self.lib.fw_set_solve_shape(self.h, envs_per_warp, warps_per_block))
+
+    def solve_shape(self):
+        g, w = C.c_int(), C.c_int()
+        self._check(self.lib.fw_get_solve_shape(self.h, C.byref(g), C.byref(w)))
+        return g.value, w.value
 
     def launches_per_step(self, n_substeps: int) -> int:
         return self.lib.fw_launches_per_step(self.h, n_substeps)

@@ -158,3 +158,61 @@ def test_frictionless_two_body_momentum_on_gpu():
     np.testing.assert_allclose(P, P0, atol=2e-8)     # float32 rounding of ~1e-3 kg m/s
     np.testing.assert_allclose(L, L0, atol=2e-10)
     assert abs(w.get_state()[2][1, 2] - 0.05) > 1e-3  # they did collide
+
+
+def test_solve_shapes_give_bit_identical_results():
+    """Envs sharing a warp (2 or 4 per warp) and blocks of several warps run the same
+    arithmetic per env as one env per warp: states agree bit for bit.  Fast-form envs
+    (one dynamic cube on a static slab) and general-form envs (two dynamic cubes) are
+    interleaved so that warps hold both kinds, and the env count leaves ragged warps and
+    blocks."""
+    fw = _fw()
+    V, T, Sp = _cube(n=900)
+    GV, GT = S.box_mesh(0.05, 0.05, 0.005)
+    w = fw.World()
+    a = w.add_mesh_asset(V, T, Sp)
+    slab = w.add_mesh_asset(GV, GT, None)
+    w.bake_sdf(slab, 64, 2e-3)
+    cb = w.add_mesh_asset(V, T, None)
+    w.bake_sdf(cb, 48, 3e-3)
+    rng = np.random.default_rng(5)
+
+    def fast_group(n):
+        b = np.zeros((n, 2), S.BODY_DTYPE)
+        for e in range(n):
+            q = S.quat_mul(S.quat_axis_angle([1, 0, 0], rng.uniform(-0.2, 0.2)),
+                           S.quat_axis_angle([0, 0, 1], rng.uniform(0, 1)))
+            b[e, 0] = S._body(a, S.DYNAMIC, (rng.uniform(-0.01, 0.01), 0, 0.0148), q, 0.5, 0.0,
+                              (rng.uniform(-0.2, 0.2), 0, -0.1), (0, rng.uniform(-2, 2), 0))
+            b[e, 1] = S._body(slab, S.STATIC, (0, 0, 0), (0, 0, 0, 1), 0.5)
+        return b
+
+    def general_group(n):
+        b = np.zeros((n, 2), S.BODY_DTYPE)
+        for e in range(n):
+            q = S.quat_axis_angle([0, 0, 1], rng.uniform(0, 1))
+            b[e, 0] = S._body(a, S.DYNAMIC, (0.0, 0.002, 0.0203), q, 0.4, 0.0, (0, 0, -0.3), (0.5, -1, 0))
+            b[e, 1] = S._body(cb, S.DYNAMIC, (0, 0, 0), (0, 0, 0, 1), 0.4, 0.02, (0.01, 0, 0.05))
+        return b
+
+    for g in (fast_group(5), general_group(3), fast_group(4), general_group(1), fast_group(6)):
+        w.add_env_bodies(g, np.array([[0, 1]], np.int32))
+    s0 = [x.copy() for x in w.get_state()]
+    results = {}
+    for shape in [(1, 1), (1, 4), (2, 1), (2, 3), (4, 1), (4, 4), (8, 1), (8, 2)]:
+        w.set_solve_shape(*shape)
+        eff = w.solve_shape()               # lowered when the blocks would not fit in shared memory
+        assert eff[0] == shape[0] and 1 <= eff[1] <= shape[1]
+        w.set_state(*s0)
+        for _ in range(3):
+            w.step(4, 16)
+        results[shape] = w.get_state()
+    ref = results[(1, 1)]
+    assert np.abs(ref[0] - s0[0]).max() > 1e-5          # the bodies did move
+    for shape, st in results.items():
+        for x, y in zip(st, ref):
+            np.testing.assert_array_equal(x, y, err_msg=str(shape))
+    w.set_solve_shape(0, 0)
+    assert w.solve_shape() == (2, 1)                     # 19 envs: two per warp, one warp per block
+    with pytest.raises(fw.FwError):
+        w.set_solve_shape(3, 1)
