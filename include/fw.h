@@ -270,8 +270,9 @@ FW_API fw_status fw_sync(fw_world *w);
 /* Per-kernel timing.  enable = 1 makes later fw_step calls launch their kernels
  * directly (no graph) with a CUDA event pair around each launch; fw_get_timings then
  * synchronises and returns, summed over the launches since the previous call:
- * ms[0] detection + reduction kernel ms, ms[1] solve + integration kernel ms,
- * ms[2] number of detection launches, ms[3] number of solve launches (n >= 4). */
+ * ms[0] detection ms (query + reduction kernels), ms[1] solve + integration kernel ms,
+ * ms[2] number of detection passes, ms[3] number of solve launches (n >= 4), and when
+ * n > 4: ms[4] query kernel ms, ms[5] reduction kernel ms; further entries are 0. */
 FW_API fw_status fw_set_timing(fw_world *w, int enable);
 FW_API fw_status fw_get_timings(fw_world *w, float *ms, int n);
 

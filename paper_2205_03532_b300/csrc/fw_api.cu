@@ -48,7 +48,11 @@ struct fw_world {
     DContact *d_contacts = nullptr;
     int *d_counts = nullptr;
     float4 *d_scratch = nullptr;
-    float4 *d_cand_ovf = nullptr;
+    int2 *d_items = nullptr;     // detection work list (pair, batch)
+    int *d_pair_item0 = nullptr;
+    float4 *d_cand = nullptr;    // candidates of every item
+    int *d_cand_count = nullptr;
+    int n_items = 0;
     Row *d_rows = nullptr;
     unsigned *d_status = nullptr;
     int dev_bodies = 0;          // bodies whose state is on the device
@@ -226,7 +230,9 @@ fw_status ensure_device(fw_world *w) {
     }
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
-    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_cand_ovf);
+    dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows);
+    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count);
+    w->n_items = 0;
     const int np = (int)w->pairs.size(), ne = (int)w->envs.size();
     const int cp = cap_pair(w);
     if (nb > 0) {
@@ -252,7 +258,24 @@ fw_status ensure_device(fw_world *w) {
             sl = std::max(sl, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
         w->scratch_len = std::max(sl, 2LL);
         CK(cudaMalloc(&w->d_scratch, sizeof(float4) * w->scratch_len));
-        CK(cudaMalloc(&w->d_cand_ovf, sizeof(float4) * (size_t)np * detect_spill_f4_per_pair()));
+        // work list: one item per (pair, Generate batch)
+        std::vector<int2> items;
+        std::vector<int> item0(np + 1, 0);
+        for (int pi = 0; pi < np; ++pi) {
+            item0[pi] = (int)items.size();
+            const long long ns = (long long)(w->assets[w->pairs[pi].asset_a].S.size() / 3);
+            for (long long b = 0; b * kBatch < ns; ++b) items.push_back(make_int2(pi, (int)b));
+        }
+        item0[np] = (int)items.size();
+        w->n_items = (int)items.size();
+        CK(cudaMalloc(&w->d_pair_item0, sizeof(int) * (np + 1)));
+        CK(cudaMemcpy(w->d_pair_item0, item0.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice));
+        if (w->n_items > 0) {
+            CK(cudaMalloc(&w->d_items, sizeof(int2) * w->n_items));
+            CK(cudaMemcpy(w->d_items, items.data(), sizeof(int2) * w->n_items, cudaMemcpyHostToDevice));
+            CK(cudaMalloc(&w->d_cand, sizeof(float4) * 2 * (size_t)kBatch * w->n_items));
+            CK(cudaMalloc(&w->d_cand_count, sizeof(int) * w->n_items));
+        }
     }
     if (ne > 0) {
         CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
@@ -279,7 +302,11 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.contacts = w->d_contacts;
     p.counts = w->d_counts;
     p.scratch = w->d_scratch;
-    p.cand_ovf = w->d_cand_ovf;
+    p.items = w->d_items;
+    p.pair_item0 = w->d_pair_item0;
+    p.n_items = w->n_items;
+    p.cand = w->d_cand;
+    p.cand_count = w->d_cand_count;
     p.rows = w->d_rows;
     p.status = w->d_status;
     p.n_pairs = (int)w->pairs.size();
@@ -334,7 +361,9 @@ fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs
     const SolveShape sh = current_solve_shape(w, p);
     for (int k = 0; k < n_substeps; ++k) {
         if (timed) CK(cudaEventRecord(take_event(w), s));
-        if (detect) CK(launch_detect(p, s));
+        if (detect) CK(launch_query(p, s));
+        if (timed) CK(cudaEventRecord(take_event(w), s));
+        if (detect) CK(launch_reduce(p, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
         CK(launch_solve(p, sh, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
@@ -409,7 +438,7 @@ fw_status fw_destroy(fw_world *w) {
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
-    dfree(w->d_cand_ovf);
+    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count);
     for (auto e : w->ev_pool) cudaEventDestroy(e);
     for (auto e : w->ev_used) cudaEventDestroy(e);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
@@ -999,21 +1028,25 @@ fw_status fw_set_timing(fw_world *w, int enable) {
 fw_status fw_get_timings(fw_world *w, float *ms, int n) {
     if (!ready(w) || !ms || n < 4) return fail(w, FW_ERR_ARG, "fw_get_timings: need 4 outputs");
     CK(cudaStreamSynchronize(w->stream));
-    double det = 0, sol = 0;
+    double qry = 0, red = 0, sol = 0;
     int nd = 0, ns = 0;
-    for (size_t i = 0; i + 2 < w->ev_used.size(); i += 3) {
-        float a = 0, b = 0;
+    for (size_t i = 0; i + 3 < w->ev_used.size(); i += 4) {
+        float a = 0, b = 0, c = 0;
         CK(cudaEventElapsedTime(&a, w->ev_used[i], w->ev_used[i + 1]));
         CK(cudaEventElapsedTime(&b, w->ev_used[i + 1], w->ev_used[i + 2]));
-        det += a;
-        sol += b;
+        CK(cudaEventElapsedTime(&c, w->ev_used[i + 2], w->ev_used[i + 3]));
+        qry += a;
+        red += b;
+        sol += c;
         ++nd;
         ++ns;
     }
     for (auto e : w->ev_used) w->ev_pool.push_back(e);
     w->ev_used.clear();
-    ms[0] = (float)det; ms[1] = (float)sol; ms[2] = (float)nd; ms[3] = (float)ns;
-    for (int i = 4; i < n; ++i) ms[i] = 0.f;
+    ms[0] = (float)(qry + red); ms[1] = (float)sol; ms[2] = (float)nd; ms[3] = (float)ns;
+    if (n > 4) ms[4] = (float)qry;
+    if (n > 5) ms[5] = (float)red;
+    for (int i = 6; i < n; ++i) ms[i] = 0.f;
     return FW_OK;
 }
 
@@ -1047,7 +1080,7 @@ fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs) {
 
 int fw_launches_per_step(fw_world *w, int n_substeps) {
     if (!w || n_substeps < 1) return 0;
-    return 2 * n_substeps;
+    return 3 * n_substeps;   // query, reduction, solve
 }
 
 const char *fw_last_error(const fw_world *w) {

@@ -1,87 +1,84 @@
-// fw_detect.cu -- SDF narrow phase fused with contact reduction (Sec. III-A, III-C,
-// Algorithm 1).  One warp per shape pair, four pairs per CTA, no block-wide barrier: for
-// each Generate batch of 1024 samples the warp queries its 32 x 32 samples (four at a time
-// per lane so their grid gathers overlap), compacts the candidates in sample order with
-// ballots into its shared-memory slice (spilling past kCandSmem to a per-pair global
-// region), assigns them to existing patches (64-bit shared atomics pick slot winners),
-// and turns the rest into new patches (FindDeepest / BinReduce / AddPatch).  Patches stay
-// in shared memory for the whole pair; only the reduced contacts reach global memory,
-// plus the data of slot winners in a per-sample scratch line.
+// fw_detect.cu -- SDF narrow phase and contact reduction (Sec. III-A, III-C, Algorithm 1),
+// two kernels per substep.
+//
+// query_kernel: one CTA of 256 threads per work item (pair, Generate batch of 1024
+// samples).  Each thread queries 4 samples -- coalesced float4 sample loads, the 8-corner
+// gathers of all four in flight together -- and the CTA compacts the candidates
+// (phi < contact offset) in sample order into the item's slab of the candidate buffer:
+// per candidate the float4 pair (x_w, phi), (n_w, sample).
+//
+// reduce_kernel: one CTA of kReduceWarps warps per pair runs Algorithm 1 over the pair's
+// items in batch order.  It stages a batch's candidates in shared memory (read in place
+// from global memory when there are more than kStage), assigns them to the existing
+// patches (64-bit shared atomics pick each slot's winner), and turns the rest into new
+// patches one at a time (FindDeepest by a block-wide argmin, BinReduce, AddPatch).
+// Patches stay in shared memory for the whole pair; only the reduced contacts reach
+// global memory, plus the data of slot winners in a per-sample scratch line.
+//
+// The same reduction code, on one warp, serves fw_reduce_noalloc, and on kReduceWarps
+// warps serves fw_reduce (a caller's candidate list).
 #include "fw_device.cuh"
 
 namespace fw {
 
 namespace {
 
-constexpr int kWarps = 4;                  // pairs per CTA
-constexpr int kCandSmem = 256;             // candidates of a batch kept in shared memory
+constexpr int kQueryThreads = 256;
+constexpr int kQueryPerThread = kBatch / kQueryThreads;   // 4 samples per thread
+constexpr int kQueryWarps = kQueryThreads / 32;
+constexpr int kReduceWarps = 4;
+constexpr int kStage = 256;              // candidates of a batch staged in shared memory
+constexpr int kMaxW = 8;                 // warps of a reduction block, at most
 constexpr unsigned long long kNoKey = ~0ull;
 
 __constant__ float c_cos6[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
 __constant__ float c_sin6[6] = {0.0f, 0.8660254037844386f, 0.8660254037844386f, 0.0f,
                                 -0.8660254037844386f, -0.8660254037844386f};
 
-// One warp's working set.  NP = max_patches + 1 (the last patch is the one being built).
-struct WarpSmem {
-    unsigned long long *keys;     // kSlots x NP
+// Patch state of one pair in shared memory.  NP = max_patches + 1: the last patch is the
+// one being built.
+struct PatchSm {
     float4 *pn4;                  // NP patch normals (x, y, z, 0)
-    float *pa, *pt1, *pt2;        // 3 x NP each, component-major
-    float *cx, *cy, *cz, *cnx, *cny, *cnz, *cphi;
-    int *cidx;                    // C each
+    unsigned long long *keys;     // kSlots x NP
+    float *pa, *pt1, *pt2;        // 3 x NP each, component-major: anchor, tangent basis
     short *cst;                   // kBatch: -1 unassigned, -2 joining, -3 consumed, >= 0 patch
     int *npat;
-    float4 *ovf;                  // candidates C.. of a batch: 2 float4 each (global memory)
-    int C;
+    unsigned long long *red;      // kMaxW words for block reductions
+    float *bc;                    // 2 floats broadcast by thread 0
 };
 
-__host__ __device__ inline size_t warp_smem_bytes(int NP, int C) {
-    const size_t b = (size_t)kSlots * NP * 8 + (size_t)13 * NP * 4 + (size_t)8 * C * 4 + (size_t)kBatch * 2 + 16;
+__host__ __device__ inline size_t patch_smem_bytes(int NP) {
+    size_t b = (size_t)NP * 16 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    b = (b + 7) & ~(size_t)7;
+    b += (size_t)kBatch * 2;
+    b += 8;                                   // npat (+ pad)
+    b += (size_t)kMaxW * 8 + 8;               // red, bc
     return (b + 15) & ~(size_t)15;
 }
 
-__device__ __forceinline__ WarpSmem carve(unsigned char *base, int NP, int C, float4 *ovf) {
-    WarpSmem s;
-    s.pn4 = reinterpret_cast<float4 *>(base);                      // the slice starts 16-byte aligned
+__device__ __forceinline__ PatchSm carve_patch(unsigned char *base, int NP) {
+    PatchSm s;
+    s.pn4 = reinterpret_cast<float4 *>(base);                      // 16-byte aligned
     s.keys = reinterpret_cast<unsigned long long *>(s.pn4 + NP);
     float *f = reinterpret_cast<float *>(s.keys + kSlots * NP);
     s.pa = f; s.pt1 = f + 3 * NP; s.pt2 = f + 6 * NP;
-    f += 9 * NP;
-    s.cx = f; s.cy = f + C; s.cz = f + 2 * C; s.cnx = f + 3 * C; s.cny = f + 4 * C; s.cnz = f + 5 * C;
-    s.cphi = f + 6 * C;
-    s.cidx = reinterpret_cast<int *>(f + 7 * C);
-    s.cst = reinterpret_cast<short *>(f + 8 * C);
-    s.npat = reinterpret_cast<int *>(s.cst + kBatch);
-    s.ovf = ovf;
-    s.C = C;
+    size_t off = (size_t)NP * 16 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    off = (off + 7) & ~(size_t)7;
+    s.cst = reinterpret_cast<short *>(base + off);
+    off += (size_t)kBatch * 2;
+    s.npat = reinterpret_cast<int *>(base + off);
+    off += 8;
+    s.red = reinterpret_cast<unsigned long long *>(base + off);
+    off += (size_t)kMaxW * 8;
+    s.bc = reinterpret_cast<float *>(base + off);
     return s;
 }
 
-// candidate storage: the first C in shared memory, the rest in the global spill region
-__device__ __forceinline__ void cput(const WarpSmem &S, int k, V3 x, V3 n, float phi, int idx) {
-    if (k < S.C) {
-        S.cx[k] = x.x; S.cy[k] = x.y; S.cz[k] = x.z;
-        S.cnx[k] = n.x; S.cny[k] = n.y; S.cnz[k] = n.z;
-        S.cphi[k] = phi; S.cidx[k] = idx;
-    } else {
-        float4 *o = S.ovf + 2 * (k - S.C);
-        o[0] = make_float4(x.x, x.y, x.z, phi);
-        o[1] = make_float4(n.x, n.y, n.z, __int_as_float(idx));
-    }
-}
-__device__ __forceinline__ float cphi(const WarpSmem &S, int k) { return k < S.C ? S.cphi[k] : S.ovf[2 * (k - S.C)].w; }
-__device__ __forceinline__ int cidx(const WarpSmem &S, int k) {
-    return k < S.C ? S.cidx[k] : __float_as_int(S.ovf[2 * (k - S.C) + 1].w);
-}
-__device__ __forceinline__ V3 cpos(const WarpSmem &S, int k) {
-    if (k < S.C) return v3(S.cx[k], S.cy[k], S.cz[k]);
-    const float4 a = S.ovf[2 * (k - S.C)];
-    return v3(a.x, a.y, a.z);
-}
-__device__ __forceinline__ V3 cnrm(const WarpSmem &S, int k) {
-    if (k < S.C) return v3(S.cnx[k], S.cny[k], S.cnz[k]);
-    const float4 a = S.ovf[2 * (k - S.C) + 1];
-    return v3(a.x, a.y, a.z);
-}
+// candidate c of a batch: cd[2c] = (x_w, phi), cd[2c + 1] = (n_w, sample as int bits)
+__device__ __forceinline__ V3 cpos(const float4 *cd, int c) { const float4 a = cd[2 * c]; return v3(a.x, a.y, a.z); }
+__device__ __forceinline__ float cphi(const float4 *cd, int c) { return cd[2 * c].w; }
+__device__ __forceinline__ V3 cnrm(const float4 *cd, int c) { const float4 b = cd[2 * c + 1]; return v3(b.x, b.y, b.z); }
+__device__ __forceinline__ int cidx(const float4 *cd, int c) { return __float_as_int(cd[2 * c + 1].w); }
 
 // Per-pair transform.
 struct PairXf {
@@ -138,7 +135,7 @@ __device__ __forceinline__ void scratch_put(float4 *scr, int sample, V3 x, float
 
 // M = -phi_deepest + sqrt(area of the polygon through the distinct direction-slot
 // points, in slot order, in the patch plane).  Reads winners' data from scratch.
-__device__ float patch_measure(const WarpSmem &S, int NP, int j, const float4 *scr) {
+__device__ float patch_measure(const PatchSm &S, int NP, int j, const float4 *scr) {
     const int deep = key_sample(S.keys[j]);
     const float phid = scr[2 * deep].w;
     const V3 a = pvec(S.pa, NP, j), t1 = pvec(S.pt1, NP, j), t2 = pvec(S.pt2, NP, j);
@@ -178,21 +175,44 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-__device__ __forceinline__ void init_patches(const WarpSmem &S, int NP) {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < kSlots * NP; i += 32) S.keys[i] = 0ull;
-    if (lane == 0) *S.npat = 0;
-    __syncwarp();
+// Block-level helpers for a reduction block of kW warps (kW = 1: the warp alone).
+template <int kW>
+__device__ __forceinline__ void bsync() {
+    if (kW == 1) __syncwarp();
+    else __syncthreads();
+}
+template <int kW, bool kMin>
+__device__ __forceinline__ unsigned long long block_ext_u64(unsigned long long v, unsigned long long *red) {
+    v = kMin ? warp_min_u64(v) : warp_max_u64(v);
+    if (kW == 1) return v;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    unsigned long long m = red[0];
+#pragma unroll
+    for (int w = 1; w < kW; ++w) m = kMin ? (red[w] < m ? red[w] : m) : (red[w] > m ? red[w] : m);
+    __syncthreads();   // red is free again
+    return m;
 }
 
-// Algorithm 1 for one batch: nc candidates stored in sample order; patches persist in S.
-// Executed by one warp.
-__device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches, float cos_patch, float4 *scr) {
-    const int lane = threadIdx.x & 31;
+template <int kW>
+__device__ __forceinline__ void init_patches(const PatchSm &S, int NP) {
+    for (int i = threadIdx.x; i < kSlots * NP; i += 32 * kW) S.keys[i] = 0ull;
+    if (threadIdx.x == 0) *S.npat = 0;
+    bsync<kW>();
+}
+
+// Algorithm 1 for one batch: nc candidates in sample order at cd (shared or global
+// memory); patches persist in S.  Executed by all 32 * kW threads of the block.
+template <int kW>
+__device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc, int max_patches, float cos_patch,
+                             float4 *scr) {
+    constexpr int NT = 32 * kW;
+    const int tid = threadIdx.x;
     const int np0 = *S.npat;
     // ---- Assign: join the most similar existing patch if similar enough
-    for (int c = lane; c < nc; c += 32) {
-        const V3 n = cnrm(S, c);
+    for (int c = tid; c < nc; c += NT) {
+        const V3 n = cnrm(cd, c);
         int best = -1;
         float bd = -3.0f;
         for (int j = 0; j < np0; ++j) {
@@ -203,73 +223,72 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
         short st = -1;
         if (best >= 0 && bd >= cos_patch) {
             st = (short)best;
-            const V3 x = cpos(S, c);
-            const float ph = cphi(S, c);
-            const int id = cidx(S, c);
-            const V3 a = pvec(S.pa, NP, best), t1 = pvec(S.pt1, NP, best), t2 = pvec(S.pt2, NP, best);
+            const float4 a = cd[2 * c];
+            const V3 x = v3(a.x, a.y, a.z);
+            const int id = cidx(cd, c);
+            const V3 pa = pvec(S.pa, NP, best), t1 = pvec(S.pt1, NP, best), t2 = pvec(S.pt2, NP, best);
             for (int s = 0; s < kSlots; ++s)
-                atomicMax(&S.keys[s * NP + best], slot_key(slot_score(s, x, ph, a, t1, t2), id));
+                atomicMax(&S.keys[s * NP + best], slot_key(slot_score(s, x, a.w, pa, t1, t2), id));
         }
         S.cst[c] = st;
     }
-    __syncwarp();
+    bsync<kW>();
     // slot winners of this batch publish their data
-    for (int c = lane; c < nc; c += 32) {
+    for (int c = tid; c < nc; c += NT) {
         const int j = S.cst[c];
         if (j < 0) continue;
-        const int id = cidx(S, c);
+        const int id = cidx(cd, c);
         bool won = false;
         for (int s = 0; s < kSlots; ++s) won |= (key_sample(S.keys[s * NP + j]) == id);
-        if (won) scratch_put(scr, id, cpos(S, c), cphi(S, c), cnrm(S, c));
+        if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
     }
-    __syncwarp();
+    bsync<kW>();
     // ---- while candidates remain: FindDeepest, BinReduce, AddPatch
     const int T = NP - 1;   // the patch under construction
     for (;;) {
         unsigned long long mk = kNoKey;
-        for (int c = lane; c < nc; c += 32)
+        for (int c = tid; c < nc; c += NT)
             if (S.cst[c] == -1) {
-                const unsigned long long k = ((unsigned long long)ord_f32(cphi(S, c)) << 32) | (unsigned)c;
+                const unsigned long long k = ((unsigned long long)ord_f32(cphi(cd, c)) << 32) | (unsigned)c;
                 mk = (k < mk) ? k : mk;
             }
-        mk = warp_min_u64(mk);
+        mk = block_ext_u64<kW, true>(mk, S.red);
         if (mk == kNoKey) break;
         const int cb = (int)(mk & 0xFFFFFFFFull);
-        const V3 nb = cnrm(S, cb);
-        const V3 ab = cpos(S, cb);
+        const V3 nb = cnrm(cd, cb);
+        const V3 ab = cpos(cd, cb);
         V3 t1, t2;
         tangent_basis(nb, t1, t2);
         // BinReduce: the remaining candidates with a similar normal join; their slot keys
         // go straight into patch T's keys with shared 64-bit atomics
-        for (int s = lane; s < kSlots; s += 32) S.keys[s * NP + T] = 0ull;
-        __syncwarp();
-        for (int c = lane; c < nc; c += 32) {
+        if (tid < kSlots) S.keys[tid * NP + T] = 0ull;
+        bsync<kW>();
+        for (int c = tid; c < nc; c += NT) {
             if (S.cst[c] != -1) continue;
-            if (c == cb || dot(cnrm(S, c), nb) >= cos_patch) {
+            if (c == cb || dot(cnrm(cd, c), nb) >= cos_patch) {
                 S.cst[c] = -2;
-                const V3 x = cpos(S, c);
-                const float ph = cphi(S, c);
-                const int id = cidx(S, c);
+                const float4 a = cd[2 * c];
+                const int id = cidx(cd, c);
                 for (int s = 0; s < kSlots; ++s)
-                    atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, x, ph, ab, t1, t2), id));
+                    atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, v3(a.x, a.y, a.z), a.w, ab, t1, t2), id));
             }
         }
-        __syncwarp();
-        // the lane holding a winner publishes its data
-        for (int c = lane; c < nc; c += 32) {
+        bsync<kW>();
+        // the thread holding a winner publishes its data
+        for (int c = tid; c < nc; c += NT) {
             if (S.cst[c] != -2) continue;
-            const int id = cidx(S, c);
+            const int id = cidx(cd, c);
             bool won = false;
             for (int s = 0; s < kSlots; ++s) won |= (key_sample(S.keys[s * NP + T]) == id);
-            if (won) scratch_put(scr, id, cpos(S, c), cphi(S, c), cnrm(S, c));
+            if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
             S.cst[c] = -3;   // consumed
         }
-        if (lane == 0) {
+        if (tid == 0) {
             S.pn4[T] = make_float4(nb.x, nb.y, nb.z, 0.0f);
             set_pvec(S.pa, NP, T, ab);
             set_pvec(S.pt1, NP, T, t1); set_pvec(S.pt2, NP, T, t2);
         }
-        __syncwarp();
+        bsync<kW>();
         // AddPatch: append below capacity, else replace the most similar patch if the new
         // one measures higher, else drop it
         const int npat = *S.npat;
@@ -278,38 +297,37 @@ __device__ void reduce_batch(const WarpSmem &S, int NP, int nc, int max_patches,
             dst = npat;
         } else {
             unsigned long long bk = 0ull;
-            for (int j = lane; j < npat; j += 32) {
+            for (int j = tid; j < npat; j += NT) {
                 const float4 q = S.pn4[j];
                 const unsigned long long k = ((unsigned long long)ord_f32(nb.x * q.x + nb.y * q.y + nb.z * q.z) << 32) |
                                              (unsigned)(0xFFFFFFFFu - (unsigned)j);
                 bk = (k > bk) ? k : bk;
             }
-            bk = warp_max_u64(bk);
+            bk = block_ext_u64<kW, false>(bk, S.red);
             const int ks = key_sample(bk);
-            float mnew = 0.f, mold = 0.f;
-            if (lane == 0) {
-                mnew = patch_measure(S, NP, T, scr);
-                mold = patch_measure(S, NP, ks, scr);
+            if (tid == 0) {
+                S.bc[0] = patch_measure(S, NP, T, scr);
+                S.bc[1] = patch_measure(S, NP, ks, scr);
             }
-            mnew = __shfl_sync(0xffffffffu, mnew, 0);
-            mold = __shfl_sync(0xffffffffu, mold, 0);
-            if (mnew > mold) dst = ks;
+            bsync<kW>();
+            if (S.bc[0] > S.bc[1]) dst = ks;
         }
-        if (dst >= 0 && lane == 9) S.pn4[dst] = S.pn4[T];
-        if (dst >= 0 && lane < 9) {
-            float *arr = (lane < 3) ? S.pa : (lane < 6) ? S.pt1 : S.pt2;
-            const int comp = lane % 3;
+        if (dst >= 0 && tid == 9) S.pn4[dst] = S.pn4[T];
+        if (dst >= 0 && tid < 9) {
+            float *arr = (tid < 3) ? S.pa : (tid < 6) ? S.pt1 : S.pt2;
+            const int comp = tid % 3;
             arr[comp * NP + dst] = arr[comp * NP + T];
         }
-        if (dst >= 0 && lane < kSlots) S.keys[lane * NP + dst] = S.keys[lane * NP + T];
-        if (lane == 0 && dst == npat) *S.npat = npat + 1;
-        __syncwarp();
+        if (dst >= 0 && tid < kSlots) S.keys[tid * NP + dst] = S.keys[tid * NP + T];
+        if (tid == 0 && dst == npat) *S.npat = npat + 1;
+        bsync<kW>();
     }
+    bsync<kW>();
 }
 
 // Writes the reduced contacts of the pair: patches in order, distinct slot members in
 // slot order.  Executed by one warp.
-__device__ void emit_contacts(const WarpSmem &S, int NP, const float4 *scr, DContact *out, int cap, int *count,
+__device__ void emit_contacts(const PatchSm &S, int NP, const float4 *scr, DContact *out, int cap, int *count,
                               unsigned *status) {
     const int lane = threadIdx.x & 31;
     const int npat = *S.npat;
@@ -343,84 +361,119 @@ __device__ void emit_contacts(const WarpSmem &S, int NP, const float4 *scr, DCon
     }
 }
 
-// Loads candidates [start, end) of a caller's list (fw_candidate layout) into S.
-__device__ __forceinline__ void load_list(const WarpSmem &S, const float *cands, int start, int end) {
-    const int lane = threadIdx.x & 31;
+// Stages candidates [start, end) of a caller's list (fw_candidate layout: sample, phi,
+// x[3], n[3]) in the batch layout.
+template <int kW>
+__device__ __forceinline__ void load_list(float4 *stage, const float *cands, int start, int end) {
     const int *ci = reinterpret_cast<const int *>(cands);
-    for (int c = start + lane; c < end; c += 32) {
+    for (int c = start + (int)threadIdx.x; c < end; c += 32 * kW) {
         const float *r = cands + 8 * c;
-        cput(S, c - start, v3(r[2], r[3], r[4]), v3(r[5], r[6], r[7]), r[1], ci[8 * c]);
+        stage[2 * (c - start)] = make_float4(r[2], r[3], r[4], r[1]);
+        stage[2 * (c - start) + 1] = make_float4(r[5], r[6], r[7], __int_as_float(ci[8 * c]));
     }
-    __syncwarp();
+    bsync<kW>();
 }
 
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kWarps) detect_kernel(SimParams p, float4 *cand_ovf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pi = blockIdx.x * kWarps + warp;
-    if (pi >= p.n_pairs) return;   // whole warps leave; nothing below syncs across warps
-    const int NP = p.max_patches + 1;
-    const size_t wb = warp_smem_bytes(NP, kCandSmem);
-    const WarpSmem S = carve(smem_raw + warp * wb, NP, kCandSmem,
-                             cand_ovf + (long long)pi * 2 * (kBatch - kCandSmem));
+__global__ void __launch_bounds__(kQueryThreads) query_kernel(SimParams p) {
+    const int item = blockIdx.x;
+    const int2 it = p.items[item];
+    const int pi = it.x, base = it.y * kBatch;
     const PairDev P = p.pairs[pi];
     const AssetDev ga = p.assets[P.asset_a];
     const AssetDev gb = p.assets[P.asset_b];
     PairXf X;
     load_pose(p, P.a, X.RA, X.pA);
     load_pose(p, P.b, X.RB, X.pB);
-    init_patches(S, NP);
-    float4 *scr = p.scratch + P.scratch_off;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float cutoff = p.contact_offset;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int base = 0; base < ga.ns; base += kBatch) {
-        // Generate: query the batch's samples, 4 per lane at a time
-        int nc = 0;
-        for (int k0 = 0; k0 < kBatch / 32; k0 += 4) {
-            V3 xw[4], nw[4];
-            float ph[4];
-            bool ok[4];
+    V3 xw[kQueryPerThread], nw[kQueryPerThread];
+    float ph[kQueryPerThread];
+    bool ok[kQueryPerThread];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = base + (k0 + u) * 32 + lane;
-                const int ic = i < ga.ns ? i : ga.ns - 1;
-                const float4 s = __ldg(&ga.samples[ic]);
-                ok[u] = query_sample(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned m = __ballot_sync(0xffffffffu, ok[u]);
-                if (ok[u]) cput(S, nc + __popc(m & lt), xw[u], nw[u], ph[u], base + (k0 + u) * 32 + lane);
-                nc += __popc(m);
-            }
-        }
-        __syncwarp();
-        reduce_batch(S, NP, nc, p.max_patches, p.cos_patch, scr);
+    for (int u = 0; u < kQueryPerThread; ++u) {
+        const int i = base + u * kQueryThreads + tid;
+        const int ic = i < ga.ns ? i : ga.ns - 1;
+        const float4 s = __ldg(&ga.samples[ic]);
+        ok[u] = query_sample(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
     }
-    emit_contacts(S, NP, scr, p.contacts + (long long)pi * p.cap_pair, p.cap_pair, p.counts + pi, p.status);
+    // compaction in sample order: local sample u * 256 + warp * 32 + lane
+    __shared__ int cnt[kQueryPerThread * kQueryWarps];
+    unsigned m[kQueryPerThread];
+#pragma unroll
+    for (int u = 0; u < kQueryPerThread; ++u) {
+        m[u] = __ballot_sync(0xffffffffu, ok[u]);
+        if (lane == 0) cnt[u * kQueryWarps + warp] = __popc(m[u]);
+    }
+    __syncthreads();
+    int total = 0, off[kQueryPerThread];
+#pragma unroll
+    for (int u = 0; u < kQueryPerThread; ++u) {
+        for (int w = 0; w < kQueryWarps; ++w) {
+            if (w == warp) off[u] = total;
+            total += cnt[u * kQueryWarps + w];
+        }
+    }
+    float4 *out = p.cand + (size_t)item * 2 * kBatch;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < kQueryPerThread; ++u) {
+        if (ok[u]) {
+            const int k = off[u] + __popc(m[u] & lt);
+            out[2 * k] = make_float4(xw[u].x, xw[u].y, xw[u].z, ph[u]);
+            out[2 * k + 1] = make_float4(nw[u].x, nw[u].y, nw[u].z, __int_as_float(base + u * kQueryThreads + tid));
+        }
+    }
+    if (tid == 0) p.cand_count[item] = total;
+}
+
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) reduce_kernel(SimParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int pi = blockIdx.x;
+    const int NP = p.max_patches + 1;
+    const PatchSm S = carve_patch(smem_raw, NP);
+    float4 *stage = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
+    init_patches<kW>(S, NP);
+    float4 *scr = p.scratch + p.pairs[pi].scratch_off;
+    const int i0 = p.pair_item0[pi], i1 = p.pair_item0[pi + 1];
+    for (int it = i0; it < i1; ++it) {
+        const int nc = p.cand_count[it];
+        if (nc == 0) continue;
+        const float4 *cd = p.cand + (size_t)it * 2 * kBatch;
+        if (nc <= kStage) {
+            for (int k = threadIdx.x; k < 2 * nc; k += 32 * kW) stage[k] = cd[k];
+            bsync<kW>();
+            cd = stage;
+        }
+        reduce_batch<kW>(S, NP, cd, nc, p.max_patches, p.cos_patch, scr);
+    }
+    if (threadIdx.x < 32)
+        emit_contacts(S, NP, scr, p.contacts + (long long)pi * p.cap_pair, p.cap_pair, p.counts + pi, p.status);
 }
 
 // Algorithm 1 on a candidate list in global memory (fw_candidate layout, sorted by
-// sample) -- the same reduction code as detect_kernel, for parity tests.  One warp.
-__global__ void __launch_bounds__(32) reduce_list_kernel(SimParams p, const float *cands, int n, float4 *scr,
-                                                         DContact *out, int cap, int *count, int *npatch) {
+// sample) -- the same reduction code as reduce_kernel, for parity tests.
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) reduce_list_kernel(SimParams p, const float *cands, int n, float4 *scr,
+                                                              DContact *out, int cap, int *count, int *npatch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NP = p.max_patches + 1;
-    const WarpSmem S = carve(smem_raw, NP, kBatch, nullptr);
-    init_patches(S, NP);
+    const PatchSm S = carve_patch(smem_raw, NP);
+    float4 *stage = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
+    init_patches<kW>(S, NP);
     const int *ci = reinterpret_cast<const int *>(cands);
     int start = 0;
     while (start < n) {
         const int bidx = ci[8 * start] / kBatch;
         int end = start;
         while (end < n && ci[8 * end] / kBatch == bidx) ++end;
-        load_list(S, cands, start, end);
-        reduce_batch(S, NP, end - start, p.max_patches, p.cos_patch, scr);
+        load_list<kW>(stage, cands, start, end);
+        reduce_batch<kW>(S, NP, stage, end - start, p.max_patches, p.cos_patch, scr);
         start = end;
     }
-    emit_contacts(S, NP, scr, out, cap, count, p.status);
-    if ((threadIdx.x & 31) == 0) *npatch = *S.npat;
+    if (threadIdx.x < 32) emit_contacts(S, NP, scr, out, cap, count, p.status);
+    if (threadIdx.x == 0) *npatch = *S.npat;
 }
 
 __global__ void query_sdf_kernel(AssetDev g, const float *pts, int n, float *phi, float *grad) {
@@ -482,8 +535,9 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
         return;
     }
     const int NP = p.max_patches + 1;
-    const WarpSmem S = carve(smem_raw, NP, kBatch, nullptr);
-    init_patches(S, NP);
+    const PatchSm S = carve_patch(smem_raw, NP);
+    float4 *batch = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
+    init_patches<1>(S, NP);
     DContact *stage = reinterpret_cast<DContact *>(scr + 2 * kNoAllocMaxSamples);
     int *stage_count = reinterpret_cast<int *>(scr + 2 * kNoAllocMaxSamples + kStageF4);
     int start = 0;
@@ -491,8 +545,8 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
         const int bidx = ci[8 * start] / kBatch;
         int end = start;
         while (end < n && ci[8 * end] / kBatch == bidx) ++end;
-        load_list(S, cands, start, end);
-        reduce_batch(S, NP, end - start, p.max_patches, p.cos_patch, scr);
+        load_list<1>(batch, cands, start, end);
+        reduce_batch<1>(S, NP, batch, end - start, p.max_patches, p.cos_patch, scr);
         start = end;
     }
     emit_contacts(S, NP, scr, stage, p.max_patches * kSlots, stage_count, p.status);
@@ -513,6 +567,11 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
         out[i] = o;
     }
     if (lane == 0) { counts[0] = k; counts[1] = *S.npat; }
+}
+
+// shared memory of a reduction block that stages up to `stage` candidates
+size_t reduce_smem_bytes(int max_patches, int stage) {
+    return patch_smem_bytes(max_patches + 1) + (size_t)stage * 2 * sizeof(float4);
 }
 
 }  // namespace
@@ -536,7 +595,7 @@ cudaError_t noalloc_setup(int device) {
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(reduce_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)warp_smem_bytes(kMaxPatchesCap + 1, kBatch));
+                             (int)reduce_smem_bytes(kMaxPatchesCap, kBatch));
     if (e != cudaSuccess) return e;
     g_noalloc_dev[device] = static_cast<float4 *>(ptr);
     g_noalloc_ready[device] = true;
@@ -547,33 +606,41 @@ cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d
                                   int cap, int *d_counts, cudaStream_t s) {
     cudaError_t e = noalloc_setup(device);
     if (e != cudaSuccess) return e;
-    reduce_noalloc_kernel<<<1, 32, warp_smem_bytes(p.max_patches + 1, kBatch), s>>>(
+    reduce_noalloc_kernel<<<1, 32, reduce_smem_bytes(p.max_patches, kBatch), s>>>(
         p, d_cands, n, g_noalloc_dev[device], d_out, cap, d_counts);
     return cudaGetLastError();
 }
 
-size_t detect_smem_bytes(int max_patches) { return kWarps * warp_smem_bytes(max_patches + 1, kCandSmem); }
-long long detect_spill_f4_per_pair() { return 2LL * (kBatch - kCandSmem); }
-
 // Raises the kernels' dynamic shared-memory limit (outside any stream capture).
 cudaError_t prepare_detect(int max_patches) {
-    cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)detect_smem_bytes(max_patches));
+    cudaError_t e = cudaFuncSetAttribute(reduce_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)reduce_smem_bytes(max_patches, kStage));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(reduce_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)warp_smem_bytes(max_patches + 1, kBatch));
+    return cudaFuncSetAttribute(reduce_list_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)reduce_smem_bytes(max_patches, kBatch));
+}
+
+cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    query_kernel<<<p.n_items, kQueryThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const SimParams &p, cudaStream_t s) {
+    if (p.n_pairs == 0) return cudaSuccess;
+    reduce_kernel<kReduceWarps><<<p.n_pairs, 32 * kReduceWarps, reduce_smem_bytes(p.max_patches, kStage), s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_detect(const SimParams &p, cudaStream_t s) {
-    if (p.n_pairs == 0) return cudaSuccess;
-    detect_kernel<<<(p.n_pairs + kWarps - 1) / kWarps, 32 * kWarps, detect_smem_bytes(p.max_patches), s>>>(
-        p, p.cand_ovf);
-    return cudaGetLastError();
+    cudaError_t e = launch_query(p, s);
+    if (e != cudaSuccess) return e;
+    return launch_reduce(p, s);
 }
 
 cudaError_t launch_reduce_list(const SimParams &p, const float *d_cands, int n, DContact *out, int *d_count,
                                int *d_npatch, cudaStream_t s) {
-    reduce_list_kernel<<<1, 32, warp_smem_bytes(p.max_patches + 1, kBatch), s>>>(
+    reduce_list_kernel<kReduceWarps><<<1, 32 * kReduceWarps, reduce_smem_bytes(p.max_patches, kBatch), s>>>(
         p, d_cands, n, p.scratch, out, p.max_patches * kSlots, d_count, d_npatch);
     return cudaGetLastError();
 }

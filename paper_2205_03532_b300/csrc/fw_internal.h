@@ -12,7 +12,6 @@ namespace fw {
 
 constexpr int kBatch = 1024;        // Generate batch of Algorithm 1 (Sec. III-C)
 constexpr int kSlots = 7;           // per patch: deepest + 6 direction extremes
-constexpr int kDetectThreads = 256; // detection CTA size: 4 samples per thread per batch
 constexpr int kMaxPatchesCap = 256; // upper end of the paper's 128 <= N <= 256
 
 // device status word bits
@@ -102,7 +101,13 @@ struct SimParams {
     float hs;
     int n_iters, n_vel_iters;
     int lam_cap;                           // rows whose impulses fit in shared memory (fast path)
-    float4 *cand_ovf;                      // per pair: candidates of a batch beyond shared memory
+    // detection work list: item k = (pair, batch of kBatch samples); a pair's items are
+    // contiguous, pair_item0[pair] .. pair_item0[pair + 1] - 1, in batch order
+    const int2 *items;
+    const int *pair_item0;
+    int n_items;
+    float4 *cand;                          // n_items x kBatch x 2: (x_w, phi), (n_w, sample)
+    int *cand_count;                       // n_items
 };
 
 // launchers (defined in the .cu files)
@@ -116,9 +121,9 @@ cudaError_t launch_query_sdf(const AssetDev &g, const float *pts, int n, float *
                              cudaStream_t s);
 cudaError_t launch_query_pair(const SimParams &p, int pair, float *phi, float *nrm, cudaStream_t s, int ns);
 cudaError_t prepare_detect(int max_patches);
-size_t detect_smem_bytes(int max_patches);
-long long detect_spill_f4_per_pair();
-cudaError_t launch_detect(const SimParams &p, cudaStream_t s);
+cudaError_t launch_query(const SimParams &p, cudaStream_t s);    // narrow phase of every work item
+cudaError_t launch_reduce(const SimParams &p, cudaStream_t s);   // Algorithm 1 of every pair
+cudaError_t launch_detect(const SimParams &p, cudaStream_t s);   // both
 constexpr int kNoAllocMaxSamples = 65536;   // sample ids accepted by fw_reduce_noalloc
 cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d_cands, int n, fw_contact *d_out,
                                   int cap, int *d_counts, cudaStream_t s);

@@ -294,9 +294,10 @@ class World:
         self._check(self.lib.fw_set_timing(self.h, int(enable)))
 
     def get_timings(self):
-        ms = np.zeros(4, np.float32)
-        self._check(self.lib.fw_get_timings(self.h, ms.ctypes.data, 4))
+        ms = np.zeros(6, np.float32)
+        self._check(self.lib.fw_get_timings(self.h, ms.ctypes.data, 6))
         return {"detect_ms": float(ms[0]), "solve_ms": float(ms[1]), "detect_launches": int(ms[2]),
+                "query_ms": float(ms[4]), "reduce_ms": float(ms[5]),
                 "solve_launches": int(ms[3])}
 
     def set_solve_shape(self, envs_per_warp: int = 0, warps_per_block: int = 0):
