@@ -31,10 +31,12 @@ sys.path.insert(0, ROOT)
 NCU_TRAFFIC = {}
 
 FP32_LANES_PER_SM = 128
-SOLVE_FLOPS_PER_CONTACT_SWEEP = 150   # one normal row + the joint friction rows (generic two-body form)
-SOLVE_FLOPS_PER_CONTACT_PREP = 300    # rows, effective masses, bias
-DETECT_BYTES_PER_QUERY = 16 + 32      # float4 sample + 8 float32 corners
-DETECT_BYTES_PER_CONTACT = 32         # reduced contact written
+SOLVE_FLOPS_PER_CONTACT_SWEEP = 100   # normal row, joint friction rows and the 6-DoF velocity update of one body
+SOLVE_FLOPS_PER_CONTACT_PREP = 300    # rows, effective masses, couplings, bias
+QUERY_BYTES_PER_SAMPLE = 16           # float4 sample point
+QUERY_BYTES_PER_CORNER = {False: 4, True: 2}   # 8 grid corners per query, float32 / float16
+CANDIDATE_BYTES = 32                  # (x, phi), (n, sample) written by the query, read by the reduction
+CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
 def _src_hash() -> str:
@@ -187,6 +189,7 @@ def run_fw(args):
         w = fw.world_from_scene(sc, fp16=args.fp16, stream=stream.cuda_stream, device=dev)
         bake_s = time.perf_counter() - t_b
     n_env, n_body, n_pair = w.counts()
+    w.set_solve_shape(*[int(v) for v in args.solve_shape.split(",")])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
 
     def one_step():
@@ -230,31 +233,37 @@ def run_fw(args):
     tim = w.get_timings()
     w.set_timing(False)
     det_ms = tim["detect_ms"] / max(tim["detect_launches"], 1)
+    qry_ms = tim["query_ms"] / max(tim["detect_launches"], 1)
+    red_ms = tim["reduce_ms"] / max(tim["detect_launches"], 1)
     sol_ms = tim["solve_ms"] / max(tim["solve_launches"], 1)
-    # contacts per env (sample of envs) for the algorithmic counts
-    sample_envs = list(range(0, n_env, max(1, n_env // 50)))
-    cper = [len(w.get_contacts(e)) for e in sample_envs]
-    c_mean = float(np.mean(cper))
+    n_cand, n_cont = w.detect_stats()          # of the last substep
+    c_mean = n_cont / max(n_env, 1)
     ns = len(sc.assets[0].samples)
     hbm, sm_max, peak_kind = _peaks()
-    det_bytes = n_pair * ns * DETECT_BYTES_PER_QUERY + n_env * c_mean * DETECT_BYTES_PER_CONTACT
-    det_gbs = det_bytes / (det_ms * 1e-3) / 1e9
-    sol_flops = n_env * c_mean * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
+    q_bytes = n_pair * ns * (QUERY_BYTES_PER_SAMPLE + 8 * QUERY_BYTES_PER_CORNER[bool(args.fp16)]) + n_cand * CANDIDATE_BYTES
+    r_bytes = n_cand * CANDIDATE_BYTES + n_cont * CONTACT_BYTES
+    sol_flops = n_cont * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
     alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     src = _src_hash()
     traffic = NCU_TRAFFIC.get(src, {})
+
+    def hbm_entry(name, nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": traffic.get(name), "avg_launch_ms": ms, "algorithmic_bytes": nbytes,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+
+    sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     kernels = {
-        "detect_kernel": {"bound": "hbm", "achieved": det_gbs, "peak": hbm, "unit": "GB/s",
-                          "frac": det_gbs / hbm, "traffic": traffic.get("detect_kernel"),
-                          "avg_launch_ms": det_ms, "algorithmic_bytes": det_bytes,
-                          "peak_source": f"{peak_kind} hbm_gbs"},
+        "query_kernel": dict(hbm_entry("query_kernel", q_bytes, qry_ms),
+                             queries_per_s=n_pair * ns / (qry_ms * 1e-3)),
+        "reduce_kernel": hbm_entry("reduce_kernel", r_bytes, red_ms),
         "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": sol_tf / alu_peak, "traffic": traffic.get("solve_kernel"),
                          "avg_launch_ms": sol_ms, "algorithmic_flops": sol_flops,
                          "peak_source": "148 SMs x 128 FP32 lanes x 2 x max SM clock"},
     }
-    dominant = "solve_kernel" if tim["solve_ms"] >= tim["detect_ms"] else "detect_kernel"
+    dominant = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roof["kernel"] = dominant
     # ---- end to end through the public API with host buffers: state in, frame, state out
@@ -288,8 +297,10 @@ def run_fw(args):
                           "iters": sim.n_iters, "frame_dt": sim.dt, "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "kernels": kernels,
-               "phase_ms_per_frame": {"detect": det_ms * sim.n_substeps, "solve": sol_ms * sim.n_substeps},
-               "contacts_per_env": c_mean,
+               "phase_ms_per_frame": {"query": qry_ms * sim.n_substeps, "reduce": red_ms * sim.n_substeps,
+                                      "solve": sol_ms * sim.n_substeps},
+               "contacts_per_env": c_mean, "candidates_per_pair": n_cand / max(n_pair, 1),
+               "solve_shape": list(w.solve_shape()),
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),
                "e2e": {"value": e2e_value, "unit": "env-substeps/s", "h2d_bytes_per_step": state_bytes,
@@ -310,6 +321,7 @@ def main():
     ap.add_argument("--envs", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--solve-shape", default="0,0", help="envs per warp, warps per block (0,0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=4)
     ap.add_argument("--ref-envs", type=int, default=2)

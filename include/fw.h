@@ -287,6 +287,12 @@ FW_API fw_status fw_get_timings(fw_world *w, float *ms, int n);
 FW_API fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_per_block);
 FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block);
 
+/* Totals of the last detection pass (synchronises): candidates (samples with phi below
+ * the contact offset, Sec. III-A) summed over all pairs, and reduced contacts kept
+ * (Algorithm 1) summed over all pairs.  Either pointer may be NULL.  Counts are those of
+ * the most recent substep that ran detection (0 before any). */
+FW_API fw_status fw_get_detect_stats(fw_world *w, long long *n_candidates, long long *n_contacts);
+
 /* Sizes: n_envs, n_bodies, n_pairs (any pointer may be NULL). */
 FW_API fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs);
 

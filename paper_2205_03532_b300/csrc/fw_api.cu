@@ -1070,6 +1070,26 @@ fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_blo
     return FW_OK;
 }
 
+fw_status fw_get_detect_stats(fw_world *w, long long *n_candidates, long long *n_contacts) {
+    if (!ready(w)) return FW_ERR_ARG;
+    CK(cudaStreamSynchronize(w->stream));
+    long long nc = 0, nk = 0;
+    if (w->n_items > 0 && w->d_cand_count) {
+        std::vector<int> c(w->n_items);
+        CK(cudaMemcpy(c.data(), w->d_cand_count, sizeof(int) * w->n_items, cudaMemcpyDeviceToHost));
+        for (int v : c) nc += v;
+    }
+    const int np = (int)w->pairs.size();
+    if (np > 0 && w->d_counts) {
+        std::vector<int> c(np);
+        CK(cudaMemcpy(c.data(), w->d_counts, sizeof(int) * np, cudaMemcpyDeviceToHost));
+        for (int v : c) nk += v;
+    }
+    if (n_candidates) *n_candidates = nc;
+    if (n_contacts) *n_contacts = nk;
+    return FW_OK;
+}
+
 fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs) {
     if (!w) return FW_ERR_ARG;
     if (n_envs) *n_envs = (int)w->envs.size();

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_get_solve_shape",
-                 "fw_get_counts", "fw_launches_per_step",
+                 "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
 
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "fw_get_timings": (st, [vp, vp, i]),
         "fw_set_solve_shape": (st, [vp, i, i]),
         "fw_get_solve_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
+        "fw_get_detect_stats": (st, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "fw_launches_per_step": (i, [vp, i]),
         "fw_last_error": (C.c_char_p, [vp]),
@@ -307,6 +308,12 @@ class World:
         g, w = C.c_int(), C.c_int()
         self._check(self.lib.fw_get_solve_shape(self.h, C.byref(g), C.byref(w)))
         return g.value, w.value
+
+    def detect_stats(self):
+        """(candidates, reduced contacts) of the last detection pass, summed over pairs."""
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.fw_get_detect_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def launches_per_step(self, n_substeps: int) -> int:
         return self.lib.fw_launches_per_step(self.h, n_substeps)
