@@ -24,7 +24,8 @@ struct AssetHost {
     float lo[3] = {0, 0, 0}, h = 0;
     int dims[3] = {0, 0, 0};
     float *d_grid = nullptr;
-    __half *d_grid16 = nullptr;
+    float4 *d_cell32 = nullptr;   // cell-corner copies (AssetDev), one of them per the world's precision
+    uint4 *d_cell16 = nullptr;
 };
 
 }  // namespace
@@ -184,7 +185,8 @@ AssetDev asset_view(const AssetHost &A, bool fp16) {
     g.samples = A.d_samples;
     g.ns = (int)(A.S.size() / 3);
     g.grid = A.d_grid;
-    g.grid16 = fp16 ? A.d_grid16 : nullptr;
+    g.cell32 = fp16 ? nullptr : A.d_cell32;
+    g.cell16 = fp16 ? A.d_cell16 : nullptr;
     for (int a = 0; a < 3; ++a) { g.lo[a] = A.lo[a]; g.dims[a] = A.dims[a]; }
     g.h = A.h;
     const double ih = A.h > 0 ? 1.0 / (double)A.h : 0.0;
@@ -201,7 +203,7 @@ void drop_graph(fw_world *w) {
 fw_status upload_assets(fw_world *w) {
     if (!w->assets_dirty) return FW_OK;
     std::vector<AssetDev> v;
-    for (auto &A : w->assets) v.push_back(asset_view(A, w->cfg.sdf_fp16 != 0 && A.d_grid16));
+    for (auto &A : w->assets) v.push_back(asset_view(A, w->cfg.sdf_fp16 != 0));
     dfree(w->d_assets);
     if (!v.empty()) {
         CK(cudaMalloc(&w->d_assets, sizeof(AssetDev) * v.size()));
@@ -432,7 +434,7 @@ fw_status fw_destroy(fw_world *w) {
     if (w->stream) cudaStreamSynchronize(w->stream);
     drop_graph(w);
     for (auto &A : w->assets) {
-        dfree(A.d_samples); dfree(A.d_grid); dfree(A.d_grid16);
+        dfree(A.d_samples); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
     }
     dfree(w->d_assets);
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
@@ -484,10 +486,16 @@ fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3], do
 }
 
 static fw_status finish_grid(fw_world *w, AssetHost &A) {
-    const long long n = (long long)A.dims[0] * A.dims[1] * A.dims[2];
-    dfree(A.d_grid16);
-    CK(cudaMalloc(&A.d_grid16, sizeof(__half) * n));
-    CK(launch_to_half(A.d_grid, A.d_grid16, 1.0f / A.h, n, w->stream));
+    const long long nc = (long long)(A.dims[0] - 1) * (A.dims[1] - 1) * (A.dims[2] - 1);
+    dfree(A.d_cell32);
+    dfree(A.d_cell16);
+    if (w->cfg.sdf_fp16) {
+        CK(cudaMalloc(&A.d_cell16, sizeof(uint4) * nc));
+        CK(launch_cells(A.d_grid, A.dims, 1.0f / A.h, nullptr, A.d_cell16, w->stream));
+    } else {
+        CK(cudaMalloc(&A.d_cell32, sizeof(float4) * 2 * nc));
+        CK(launch_cells(A.d_grid, A.dims, 1.0f / A.h, A.d_cell32, nullptr, w->stream));
+    }
     CK(cudaStreamSynchronize(w->stream));
     A.has_sdf = true;
     w->assets_dirty = true;
@@ -590,7 +598,8 @@ fw_status fw_bake_sdf(fw_world *w, int asset_id, int resolution, float padding_m
     float *d_tri = nullptr, *d_pn = nullptr, *d_box = nullptr;
     int *d_flags = nullptr;
     dfree(A.d_grid);
-    dfree(A.d_grid16);
+    dfree(A.d_cell32);
+    dfree(A.d_cell16);
     CK(cudaMalloc(&A.d_grid, sizeof(float) * n_nodes));
     CK(cudaMalloc(&d_tri, sizeof(float) * tri.size()));
     CK(cudaMalloc(&d_pn, sizeof(float) * pn.size()));

@@ -208,10 +208,29 @@ __global__ void winding_fix_kernel(const float *tri, int nt, AssetDev g, float *
     }
 }
 
-__global__ void to_half_kernel(const float *src, __half *dst, float inv_h, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Cell-corner copy of a node grid (layout in AssetDev); float16 cells hold phi / h
+// rounded to nearest.
+__global__ void cells_kernel(const float *grid, int nx, int ny, int nz, float inv_h, float4 *c32, uint4 *c16) {
+    const long long cnx = nx - 1, cny = ny - 1, n = cnx * cny * (long long)(nz - 1);
+    const long long nxy = (long long)nx * ny;
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) dst[i] = __float2half_rn(src[i] * inv_h);
+    for (; c < n; c += stride) {
+        const long long i = c % cnx, j = (c / cnx) % cny, k = c / (cnx * cny);
+        const float *b = grid + k * nxy + j * nx + i;
+        const float v[8] = {b[0], b[1], b[nx], b[nx + 1], b[nxy], b[nxy + 1], b[nxy + nx], b[nxy + nx + 1]};
+        if (c16) {
+            unsigned u[4];
+            for (int q = 0; q < 4; ++q) {
+                const __half2 hh = __halves2half2(__float2half_rn(v[2 * q] * inv_h), __float2half_rn(v[2 * q + 1] * inv_h));
+                u[q] = *reinterpret_cast<const unsigned *>(&hh);
+            }
+            c16[c] = make_uint4(u[0], u[1], u[2], u[3]);
+        } else {
+            c32[2 * c] = make_float4(v[0], v[1], v[2], v[3]);
+            c32[2 * c + 1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+    }
 }
 
 }  // namespace
@@ -231,8 +250,9 @@ cudaError_t launch_bake_fix_sign(const float *d_tri, int n_tri, const AssetDev &
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_half(const float *src, __half *dst, float inv_h, long long n, cudaStream_t s) {
-    to_half_kernel<<<148 * 8, 256, 0, s>>>(src, dst, inv_h, n);
+cudaError_t launch_cells(const float *grid, const int dims[3], float inv_h, float4 *cell32, uint4 *cell16,
+                         cudaStream_t s) {
+    cells_kernel<<<148 * 8, 256, 0, s>>>(grid, dims[0], dims[1], dims[2], inv_h, cell32, cell16);
     return cudaGetLastError();
 }
 

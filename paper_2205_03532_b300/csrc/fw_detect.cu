@@ -375,7 +375,7 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 }
 
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kQueryThreads) query_kernel(SimParams p) {
+__global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const int item = blockIdx.x;
     const int2 it = p.items[item];
     const int pi = it.x, base = it.y * kBatch;

@@ -102,8 +102,9 @@ __device__ __forceinline__ bool grid_coord(float x, float lo, float inv_h, float
 
 __device__ __forceinline__ float lerp_(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// Trilinear value and gradient; the corner loads are always in bounds and issued before
-// the in-grid test is used, so several lookups can overlap their memory latency.
+// Trilinear value and gradient from the cell-corner copy; the corner loads (one or two
+// 16-byte loads) are always in bounds and issued before the in-grid test is used, so
+// several lookups can overlap their memory latency.
 template <bool kHalf>
 __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
     int ci, cj, ck;
@@ -111,21 +112,21 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
     const bool okx = grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx);
     const bool oky = grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy);
     const bool okz = grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz);
-    const long long nx = g.dims[0], nxy = (long long)g.dims[0] * g.dims[1];
-    const long long o = (long long)ck * nxy + (long long)cj * nx + ci;
+    const long long cnx = g.dims[0] - 1, cnxy = cnx * (long long)(g.dims[1] - 1);
+    const long long o = (long long)ck * cnxy + (long long)cj * cnx + ci;
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if (kHalf) {
-        const __half *b = g.grid16 + o;
-        v000 = __half2float(b[0]);        v100 = __half2float(b[1]);
-        v010 = __half2float(b[nx]);       v110 = __half2float(b[nx + 1]);
-        v001 = __half2float(b[nxy]);      v101 = __half2float(b[nxy + 1]);
-        v011 = __half2float(b[nxy + nx]); v111 = __half2float(b[nxy + nx + 1]);
+        const uint4 c = __ldg(g.cell16 + o);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&c.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&c.y));
+        const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&c.z));
+        const float2 e = __half22float2(*reinterpret_cast<const __half2 *>(&c.w));
+        v000 = a.x; v100 = a.y; v010 = b.x; v110 = b.y;
+        v001 = d.x; v101 = d.y; v011 = e.x; v111 = e.y;
     } else {
-        const float *b = g.grid + o;
-        v000 = __ldg(b);            v100 = __ldg(b + 1);
-        v010 = __ldg(b + nx);       v110 = __ldg(b + nx + 1);
-        v001 = __ldg(b + nxy);      v101 = __ldg(b + nxy + 1);
-        v011 = __ldg(b + nxy + nx); v111 = __ldg(b + nxy + nx + 1);
+        const float4 a = __ldg(g.cell32 + 2 * o), b = __ldg(g.cell32 + 2 * o + 1);
+        v000 = a.x; v100 = a.y; v010 = a.z; v110 = a.w;
+        v001 = b.x; v101 = b.y; v011 = b.z; v111 = b.w;
     }
     // value: lerp along x, then y, then z
     const float a00 = lerp_(v000, v100, fx), a10 = lerp_(v010, v110, fx);
@@ -136,7 +137,7 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
     const float gx = lerp_(lerp_(v100 - v000, v110 - v010, fy), lerp_(v101 - v001, v111 - v011, fy), fz);
     const float gy = lerp_(lerp_(v010 - v000, v110 - v100, fx), lerp_(v011 - v001, v111 - v101, fx), fz);
     const float gz = lerp_(lerp_(v001 - v000, v101 - v100, fx), lerp_(v011 - v010, v111 - v110, fx), fy);
-    if (kHalf) {   // nodes hold phi / h
+    if (kHalf) {   // cells hold phi / h
         phi = val * g.h;
         grad = v3(gx, gy, gz);
     } else {
@@ -147,7 +148,7 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
 }
 
 __device__ __forceinline__ bool sdf_lookup_any(const AssetDev &g, V3 x, float &phi, V3 &grad) {
-    return g.grid16 ? sdf_lookup<true>(g, x, phi, grad) : sdf_lookup<false>(g, x, phi, grad);
+    return g.cell16 ? sdf_lookup<true>(g, x, phi, grad) : sdf_lookup<false>(g, x, phi, grad);
 }
 
 // Order-preserving map of a float to uint32 (larger float -> larger integer).

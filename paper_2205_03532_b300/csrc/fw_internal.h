@@ -23,8 +23,13 @@ constexpr unsigned kStatusBounds = 4u;
 // grids store phi / h.
 struct AssetDev {
     const float4 *samples;   // asset-frame sample points (x, y, z, 0)
-    const float *grid;       // float32 nodes or nullptr
-    const __half *grid16;    // float16 nodes (phi / h) or nullptr
+    const float *grid;       // float32 nodes (bake output; fw_get_sdf)
+    // Cell-corner copy used by every query: cell (i, j, k), i < nx - 1 fastest, holds the
+    // values of its 8 corners in the order 000 100 010 110 001 101 011 111 (x fastest), so
+    // one query reads 32 contiguous bytes (float32, two float4) or 16 (float16 phi / h, one
+    // uint4).  Exactly one of the two is set, by the world's precision.
+    const float4 *cell32;
+    const uint4 *cell16;
     float lo[3];
     float h, inv_h, inv_h_lo; // inv_h + inv_h_lo = 1/h to ~1e-14 relative
     int dims[3];
@@ -115,7 +120,8 @@ cudaError_t launch_bake(const float *d_tri, int n_tri, const float *d_tri_pn, co
                         const AssetDev &g, float *d_out, int *d_flags, cudaStream_t s);
 cudaError_t launch_bake_fix_sign(const float *d_tri, int n_tri, const AssetDev &g, float *d_out,
                                  const int *d_idx, int n_idx, cudaStream_t s);
-cudaError_t launch_to_half(const float *src, __half *dst, float inv_h, long long n, cudaStream_t s);
+cudaError_t launch_cells(const float *grid, const int dims[3], float inv_h, float4 *cell32, uint4 *cell16,
+                         cudaStream_t s);   // one of cell32 / cell16 non-null
 int bake_tile_size();
 cudaError_t launch_query_sdf(const AssetDev &g, const float *pts, int n, float *phi, float *grad,
                              cudaStream_t s);
