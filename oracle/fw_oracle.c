@@ -381,7 +381,10 @@ struct or_world {
     double *env_mlen, *env_mdot;
     double **imp; int *imp_n;               /* per env friction record */
     double bake_seconds;                    /* wall time spent in lazy SDF bakes */
+    struct diff_tape *tape;                 /* decisions of the last recorded rollout */
 };
+
+static void diff_tape_free(or_world *w);
 
 or_world *or_create(const or_config *cfg) {
     or_world *w = (or_world *)calloc(1, sizeof(or_world));
@@ -397,6 +400,7 @@ void or_destroy(or_world *w) {
     }
     for (int i = 0; i < w->n_pairs; ++i) free(w->pc[i].c);
     free(w->assets); free(w->bodies); free(w->pairs); free(w->envs); free(w->pc);
+    diff_tape_free(w);
     for (int e = 0; e < w->n_envs; ++e) free(w->imp[e]);
     free(w->env_mlen); free(w->env_mdot); free(w->imp); free(w->imp_n);
     free(w);
@@ -1196,3 +1200,809 @@ int or_get_impulses(const or_world *w, int env, double *out, int cap, int *n_out
     *n_out = n;
     return n > cap ? -1 : 0;
 }
+
+/* ==================================================================================== */
+/* Differentiable rollout: reverse mode of substeps whose discrete decisions are held    */
+/* fixed by a tape.                                                                       */
+/* ==================================================================================== */
+/*
+ * Scope: an env is differentiable when exactly one of its bodies is dynamic and that body
+ * is the point-sampled body a of every pair of the env; its partners are static or
+ * kinematic (prescribed motion, no adjoint); n_vel_iters = 0.  Envs without a dynamic
+ * body are allowed and carry no adjoint.
+ *
+ * The tape of a rollout of S substeps over E envs with K sweeps each:
+ *   c_off[s*E + e] .. c_off[s*E + e + 1]: the contacts of env e in substep s, in solve
+ *     order, each 6 ints: sample, pair (global id), SDF cell i, j, k, flags (bit 0: t1
+ *     from n x e_x, bit 1: phi > 0, the speculative bias);
+ *   r_bits[K*c + it] for contact c (index into the records) and sweep it: bit 0 the
+ *     normal impulse is positive after the row, bit 1 the friction impulse was projected
+ *     onto the disk |lambda_t| <= mu lambda_n;
+ *   b_bits[s*E + e]: bit 0 the dynamic body's |omega| was clamped at integration.
+ * Recording takes each decision as the oracle's forward does (its own detection and
+ * Algorithm 1 each substep).  Replaying evaluates the same formulas with the taped
+ * decisions -- the trilinear polynomial of the taped cell is used even a little outside
+ * that cell -- so a replay is a smooth function of the initial state, of the dynamic
+ * bodies' masses (inertia scaled with mass at fixed geometry) and of the pairs' friction
+ * coefficients, equal to the plain forward at the recorded point.  The adjoint below is
+ * the exact reverse mode of a replay.
+ */
+struct diff_tape {
+    int S, E, K;
+    double hs;
+    int *c_off;
+    int *c_rec;
+    int n_c, cap_c;
+    unsigned char *r_bits;
+    unsigned char *b_bits;
+};
+
+static void diff_tape_free(or_world *w) {
+    if (!w->tape) return;
+    free(w->tape->c_off); free(w->tape->c_rec); free(w->tape->r_bits); free(w->tape->b_bits);
+    free(w->tape);
+    w->tape = NULL;
+}
+
+static struct diff_tape *diff_tape_new(int S, int E, int K, double hs) {
+    struct diff_tape *T = (struct diff_tape *)calloc(1, sizeof(struct diff_tape));
+    T->S = S; T->E = E; T->K = K; T->hs = hs;
+    T->c_off = (int *)calloc((size_t)S * E + 1, sizeof(int));
+    T->b_bits = (unsigned char *)calloc((size_t)S * E + 1, 1);
+    return T;
+}
+
+/* the dynamic body of env e (global id); -2 none; -1 the env is not differentiable */
+static int diff_env_body(const or_world *w, int e) {
+    const env_t *E = &w->envs[e];
+    int dyn = -2;
+    for (int i = 0; i < E->n_bodies; ++i) {
+        const int t = w->bodies[E->first_body + i].type;
+        if (t == 3) return -1;
+        if (t == 2) {
+            if (dyn >= 0) return -1;
+            dyn = E->first_body + i;
+        }
+    }
+    if (dyn >= 0)
+        for (int p = 0; p < E->n_pairs; ++p)
+            if (w->pairs[E->first_pair + p].a != dyn) return -1;
+    return dyn;
+}
+
+/* the 8 nodes of a cell, baked now if the grid is lazy */
+static void diff_cell_nodes(or_world *w, asset_t *ab, const int c[3], double v[2][2][2]) {
+    grid_t *g = &ab->grid;
+    for (int k = 0; k < 8; ++k) {
+        const long long id = gidx(g, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + ((k >> 2) & 1));
+        if (g->lazy && g->done[id] != 1) {
+            float lo[3] = {(float)g->lo[0], (float)g->lo[1], (float)g->lo[2]};
+            double val;
+            or_bake_nodes(ab->V, ab->T, ab->nt, lo, (float)g->h, g->dims, &id, 1, &val, 1);
+            g->val[id] = val;
+            g->done[id] = 1;
+        }
+        v[(k >> 2) & 1][(k >> 1) & 1][k & 1] = g->val[id];
+    }
+    (void)w;
+}
+
+/* value, gradient and Hessian of the trilinear polynomial of cell c at x (grid frame);
+ * f may fall slightly outside [0, 1] on a replay.  Within a cell the Hessian has a zero
+ * diagonal; its mixed terms are the bilinear blends of the cell's second differences. */
+static void diff_trilinear(or_world *w, asset_t *ab, const int c[3], const double x[3], double *phi,
+                           double grad[3], double H[9]) {
+    const grid_t *g = &ab->grid;
+    double f[3], v[2][2][2];
+    for (int a = 0; a < 3; ++a) f[a] = (x[a] - g->lo[a]) / g->h - (double)c[a];
+    diff_cell_nodes(w, ab, c, v);
+    const double wx[2] = {1 - f[0], f[0]}, wy[2] = {1 - f[1], f[1]}, wz[2] = {1 - f[2], f[2]};
+    double p = 0, gx = 0, gy = 0, gz = 0, hxy = 0, hxz = 0, hyz = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) p += wx[di] * wy[dj] * wz[dk] * v[dk][dj][di];
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj) gx += wy[dj] * wz[dk] * (v[dk][dj][1] - v[dk][dj][0]);
+    for (int dk = 0; dk < 2; ++dk)
+        for (int di = 0; di < 2; ++di) gy += wx[di] * wz[dk] * (v[dk][1][di] - v[dk][0][di]);
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) gz += wx[di] * wy[dj] * (v[1][dj][di] - v[0][dj][di]);
+    for (int dk = 0; dk < 2; ++dk) hxy += wz[dk] * (v[dk][1][1] - v[dk][1][0] - v[dk][0][1] + v[dk][0][0]);
+    for (int dj = 0; dj < 2; ++dj) hxz += wy[dj] * (v[1][dj][1] - v[1][dj][0] - v[0][dj][1] + v[0][dj][0]);
+    for (int di = 0; di < 2; ++di) hyz += wx[di] * (v[1][1][di] - v[1][0][di] - v[0][1][di] + v[0][0][di]);
+    *phi = p;
+    grad[0] = gx / g->h; grad[1] = gy / g->h; grad[2] = gz / g->h;
+    const double ih2 = 1.0 / (g->h * g->h);
+    H[0] = 0; H[1] = hxy * ih2; H[2] = hxz * ih2;
+    H[3] = hxy * ih2; H[4] = 0; H[5] = hyz * ih2;
+    H[6] = hxz * ih2; H[7] = hyz * ih2; H[8] = 0;
+}
+
+/* one contact row of the dynamic body (all quantities world frame) */
+typedef struct {
+    int pair, flags, cell[3], live;
+    double s[3];                       /* sample, body-a frame */
+    double xbl[3], phi, g[3], H[9], gn, nb[3];
+    double xa[3], xbw[3], n[3];
+    double ra[3], rb[3], uo[3], tr[3], tn;
+    double d[3][3], a[3][3], b[3][3], k[3];   /* directions n, t1, t2; r x d; I^-1 (r x d); 1/den */
+    double bias, e[3], mu;
+} drow_t;
+
+/* forward intermediates of one env substep */
+typedef struct {
+    int ia;                          /* dynamic body (global id) or < 0 */
+    double q0[4], R[9], com[3], Iw[9], Ii[9];
+    double v0[3], w0[3], v1[3], w1[3], Lw[3], tq[3];
+    drow_t *rows;
+    int nr, c0;                      /* rows and the index of the first tape record */
+    double *upd;                     /* per (sweep, row): v, w, lambda before the update (9) */
+    double vf[3], wf[3], wc[3];
+    double cp[3], qt[4], q1[4], R1[9];
+    int clamped;
+} dfwd_t;
+
+static void m_sandwich(const double R[9], const double S[9], double M[9]) {   /* R S R^T */
+    double Rt[9], t[9];
+    m_transpose(R, Rt);
+    m_mul(R, S, t);
+    m_mul(t, Rt, M);
+}
+
+/* geometry and row of one taped contact at the current state */
+static void diff_build_row(or_world *w, const body_t *A, const dfwd_t *F, drow_t *D, double hs) {
+    const pair_t *P = &w->pairs[D->pair];
+    const body_t *B = &w->bodies[P->b];
+    asset_t *ab = &w->assets[B->asset];
+    double RB[9], RBt[9], d[3], H[9];
+    q_to_m(B->q, RB);
+    m_transpose(RB, RBt);
+    m_vec(F->R, D->s, D->xa);
+    v_add(D->xa, A->p, D->xa);
+    v_sub(D->xa, B->p, d);
+    m_vec(RBt, d, D->xbl);
+    diff_trilinear(w, ab, D->cell, D->xbl, &D->phi, D->g, H);
+    memcpy(D->H, H, sizeof H);
+    D->gn = v_norm(D->g);
+    v_scale(D->g, 1.0 / D->gn, D->nb);
+    m_vec(RB, D->nb, D->n);
+    for (int i = 0; i < 3; ++i) D->xbw[i] = D->xa[i] - D->phi * D->n[i];
+    v_sub(D->xa, F->com, D->ra);
+    double comB[3], wr[3];
+    body_com_world(B, comB);
+    v_sub(D->xbw, comB, D->rb);
+    v_cross(B->w, D->rb, wr);
+    v_add(B->v, wr, D->uo);
+    /* tangent basis (R11) with the taped branch */
+    if (D->flags & 1) { D->tr[0] = 0; D->tr[1] = D->n[2]; D->tr[2] = -D->n[1]; }
+    else { D->tr[0] = -D->n[2]; D->tr[1] = 0; D->tr[2] = D->n[0]; }
+    D->tn = v_norm(D->tr);
+    memcpy(D->d[0], D->n, sizeof D->n);
+    v_scale(D->tr, 1.0 / D->tn, D->d[1]);
+    v_cross(D->n, D->d[1], D->d[2]);
+    D->live = 1;
+    for (int j = 0; j < 3; ++j) {
+        v_cross(D->ra, D->d[j], D->a[j]);
+        m_vec(F->Ii, D->a[j], D->b[j]);
+        const double den = A->invm + v_dot(D->a[j], D->b[j]);
+        D->k[j] = den > 0.0 ? 1.0 / den : 0.0;
+        D->e[j] = -v_dot(D->d[j], D->uo);
+    }
+    if (D->k[0] == 0.0) D->live = 0;
+    D->bias = (D->flags & 2) ? D->phi / hs : w->cfg.baumgarte * D->phi / hs;
+    D->mu = P->mu;
+}
+
+/* one row update of the sweep (R9) with the given decisions (record: bits computed) */
+static void diff_row_fwd(const drow_t *D, double invm, double v[3], double wv[3], double lam[3],
+                         unsigned char *bits, int replay) {
+    const double jv = v_dot(D->d[0], v) + v_dot(D->a[0], wv) + D->bias + D->e[0];
+    const double u = lam[0] - D->k[0] * jv;
+    int act;
+    if (replay) act = (*bits & 1) != 0; else act = u > 0.0;
+    const double ln = act ? u : 0.0;
+    const double dl = ln - lam[0];
+    double vm[3], wm[3];
+    for (int i = 0; i < 3; ++i) { vm[i] = v[i] + invm * dl * D->d[0][i]; wm[i] = wv[i] + dl * D->b[0][i]; }
+    const double j1 = v_dot(D->d[1], vm) + v_dot(D->a[1], wm) + D->e[1];
+    const double j2 = v_dot(D->d[2], vm) + v_dot(D->a[2], wm) + D->e[2];
+    const double t1 = lam[1] - D->k[1] * j1, t2 = lam[2] - D->k[2] * j2;
+    const double lim = D->mu * ln, tn = sqrt(t1 * t1 + t2 * t2);
+    int proj;
+    if (replay) proj = (*bits & 2) != 0; else proj = tn > lim;
+    const double s = proj ? lim / tn : 1.0;
+    const double l1 = s * t1, l2 = s * t2;
+    const double e1 = l1 - lam[1], e2 = l2 - lam[2];
+    for (int i = 0; i < 3; ++i) {
+        v[i] = vm[i] + invm * (e1 * D->d[1][i] + e2 * D->d[2][i]);
+        wv[i] = wm[i] + e1 * D->b[1][i] + e2 * D->b[2][i];
+    }
+    lam[0] = ln; lam[1] = l1; lam[2] = l2;
+    if (!replay) *bits = (unsigned char)((act ? 1 : 0) | (proj ? 2 : 0));
+}
+
+/* (omega, 0) (x) q */
+static void omega_q(const double wv[3], const double q[4], double dq[4]) {
+    dq[0] = q[3] * wv[0] + wv[1] * q[2] - wv[2] * q[1];
+    dq[1] = q[3] * wv[1] + wv[2] * q[0] - wv[0] * q[2];
+    dq[2] = q[3] * wv[2] + wv[0] * q[1] - wv[1] * q[0];
+    dq[3] = -(wv[0] * q[0] + wv[1] * q[1] + wv[2] * q[2]);
+}
+
+/* Forward of env e in substep si with tape T: record (contacts from the world's current
+ * detection, decisions computed) or replay (contacts and decisions from the tape).  The
+ * bodies' states advance.  F (optional) keeps what the adjoint needs. */
+static int diff_env_forward(or_world *w, int e, int si, int replay, dfwd_t *F, int keep_updates) {
+    struct diff_tape *T = w->tape;
+    const env_t *E = &w->envs[e];
+    const double hs = T->hs;
+    const int K = T->K;
+    memset(F, 0, sizeof *F);
+    F->ia = diff_env_body(w, e);
+    if (F->ia == -1) return -1;
+    const int slot = si * T->E + e;
+    if (F->ia >= 0) {
+        body_t *A = &w->bodies[F->ia];
+        /* 1. external forces at the substep's start */
+        memcpy(F->q0, A->q, sizeof F->q0);
+        q_to_m(A->q, F->R);
+        body_com_world(A, F->com);
+        m_sandwich(F->R, A->Ib, F->Iw);
+        m_sandwich(F->R, A->Ib_inv, F->Ii);
+        memcpy(F->v0, A->v, sizeof F->v0);
+        memcpy(F->w0, A->w, sizeof F->w0);
+        for (int k = 0; k < 3; ++k) F->v1[k] = A->v[k] + hs * (w->cfg.gravity[k] + A->force[k] / A->mass);
+        double gy[3], dw[3];
+        m_vec(F->Iw, A->w, F->Lw);
+        v_cross(A->w, F->Lw, gy);
+        v_sub(A->torque, gy, F->tq);
+        m_vec(F->Ii, F->tq, dw);
+        for (int k = 0; k < 3; ++k) F->w1[k] = A->w[k] + hs * dw[k];
+        /* 2. contacts (taped or recorded now) and their rows */
+        if (!replay) {
+            int n = 0;
+            for (int p = 0; p < E->n_pairs; ++p) n += w->pc[E->first_pair + p].n;
+            if (T->n_c + n > T->cap_c) {
+                T->cap_c = 2 * (T->n_c + n) + 64;
+                T->c_rec = (int *)realloc(T->c_rec, sizeof(int) * 6 * T->cap_c);
+                T->r_bits = (unsigned char *)realloc(T->r_bits, (size_t)K * T->cap_c);
+            }
+            T->c_off[slot] = T->n_c;
+            for (int p = 0; p < E->n_pairs; ++p) {
+                const int pi = E->first_pair + p;
+                const pair_contacts_t *pc = &w->pc[pi];
+                const body_t *B = &w->bodies[w->pairs[pi].b];
+                const grid_t *g = &w->assets[B->asset].grid;
+                for (int i = 0; i < pc->n; ++i) {
+                    int *rec = T->c_rec + 6 * T->n_c;
+                    rec[0] = pc->c[i].sample;
+                    rec[1] = pi;
+                    double RB[9], RBt[9], xw[3], d[3], xb[3], s3[3];
+                    load3(w->assets[A->asset].S + 3 * rec[0], s3);
+                    q_to_m(B->q, RB); m_transpose(RB, RBt);
+                    m_vec(F->R, s3, xw); v_add(xw, A->p, xw);
+                    v_sub(xw, B->p, d); m_vec(RBt, d, xb);
+                    for (int a = 0; a < 3; ++a) {
+                        int ci = (int)floor((xb[a] - g->lo[a]) / g->h);
+                        if (ci > g->dims[a] - 2) ci = g->dims[a] - 2;
+                        if (ci < 0) ci = 0;
+                        rec[2 + a] = ci;
+                    }
+                    rec[5] = (fabs(pc->c[i].n[0]) < 0.57735 ? 1 : 0) | (pc->c[i].phi > 0.0 ? 2 : 0);
+                    T->n_c++;
+                }
+            }
+            T->c_off[slot + 1] = T->n_c;
+        }
+        F->c0 = T->c_off[slot];
+        F->nr = T->c_off[slot + 1] - F->c0;
+        F->rows = (drow_t *)calloc(F->nr > 0 ? F->nr : 1, sizeof(drow_t));
+        for (int r = 0; r < F->nr; ++r) {
+            const int *rec = T->c_rec + 6 * (F->c0 + r);
+            drow_t *D = &F->rows[r];
+            D->pair = rec[1];
+            D->cell[0] = rec[2]; D->cell[1] = rec[3]; D->cell[2] = rec[4];
+            D->flags = rec[5];
+            load3(w->assets[A->asset].S + 3 * rec[0], D->s);
+            diff_build_row(w, A, F, D, hs);
+        }
+        /* 3. sweeps */
+        double *lam = (double *)calloc(3 * (F->nr > 0 ? F->nr : 1), sizeof(double));
+        double v[3], wv[3];
+        memcpy(v, F->v1, sizeof v);
+        memcpy(wv, F->w1, sizeof wv);
+        if (keep_updates) F->upd = (double *)malloc(sizeof(double) * 9 * (size_t)K * (F->nr > 0 ? F->nr : 1));
+        for (int it = 0; it < K; ++it)
+            for (int r = 0; r < F->nr; ++r) {
+                if (keep_updates) {
+                    double *u = F->upd + 9 * ((size_t)it * F->nr + r);
+                    memcpy(u, v, 3 * sizeof(double)); memcpy(u + 3, wv, 3 * sizeof(double));
+                    memcpy(u + 6, lam + 3 * r, 3 * sizeof(double));
+                }
+                if (!F->rows[r].live) continue;
+                diff_row_fwd(&F->rows[r], A->invm, v, wv, lam + 3 * r, T->r_bits + (size_t)K * (F->c0 + r) + it, replay);
+            }
+        free(lam);
+        memcpy(F->vf, v, sizeof v);
+        memcpy(F->wf, wv, sizeof wv);
+        /* 4. integration (R10) */
+        memcpy(F->wc, wv, sizeof wv);
+        const double wn = v_norm(wv);
+        if (!replay) T->b_bits[slot] = (w->cfg.max_angvel > 0.0 && wn > w->cfg.max_angvel) ? 1 : 0;
+        F->clamped = T->b_bits[slot] & 1;
+        if (F->clamped) v_scale(wv, w->cfg.max_angvel / wn, F->wc);
+        for (int k = 0; k < 3; ++k) F->cp[k] = F->com[k] + hs * F->vf[k];
+        double dq[4];
+        omega_q(F->wc, A->q, dq);
+        for (int k = 0; k < 4; ++k) F->qt[k] = A->q[k] + 0.5 * hs * dq[k];
+        memcpy(F->q1, F->qt, sizeof F->qt);
+        q_normalize(F->q1);
+        q_to_m(F->q1, F->R1);
+        double rc[3];
+        m_vec(F->R1, A->com_b, rc);
+        v_sub(F->cp, rc, A->p);
+        memcpy(A->q, F->q1, sizeof F->q1);
+        memcpy(A->v, F->vf, sizeof F->vf);
+        memcpy(A->w, F->wc, sizeof F->wc);
+    }
+    /* kinematic partners follow their prescribed velocity (R10) */
+    for (int i = 0; i < E->n_bodies; ++i) {
+        body_t *b = &w->bodies[E->first_body + i];
+        if (b->type != 1) continue;
+        double c[3], R[9], rc[3], dq[4];
+        body_com_world(b, c);
+        v_axpy(hs, b->v, c);
+        omega_q(b->w, b->q, dq);
+        for (int k = 0; k < 4; ++k) b->q[k] += 0.5 * hs * dq[k];
+        q_normalize(b->q);
+        q_to_m(b->q, R);
+        m_vec(R, b->com_b, rc);
+        v_sub(c, rc, b->p);
+    }
+    return 0;
+}
+
+static void dfwd_free(dfwd_t *F) { free(F->rows); free(F->upd); F->rows = NULL; F->upd = NULL; }
+
+/* adjoint of R = q_to_m(q) for the polynomial of q_to_m: qb += sum Rb_ij dR_ij/dq */
+static void q_to_m_vjp(const double q[4], const double Rb[9], double qb[4]) {
+    const double x = q[0], y = q[1], z = q[2], w = q[3];
+    qb[0] += 2 * y * Rb[1] + 2 * z * Rb[2] + 2 * y * Rb[3] - 4 * x * Rb[4] - 2 * w * Rb[5] + 2 * z * Rb[6] +
+             2 * w * Rb[7] - 4 * x * Rb[8];
+    qb[1] += -4 * y * Rb[0] + 2 * x * Rb[1] + 2 * w * Rb[2] + 2 * x * Rb[3] + 2 * z * Rb[5] - 2 * w * Rb[6] +
+             2 * z * Rb[7] - 4 * y * Rb[8];
+    qb[2] += -4 * z * Rb[0] - 2 * w * Rb[1] + 2 * x * Rb[2] + 2 * w * Rb[3] - 4 * z * Rb[4] + 2 * y * Rb[5] +
+             2 * x * Rb[6] + 2 * y * Rb[7];
+    qb[3] += -2 * z * Rb[1] + 2 * y * Rb[2] + 2 * z * Rb[3] - 2 * x * Rb[5] - 2 * y * Rb[6] + 2 * x * Rb[7];
+}
+
+/* y = M x:  xb += M^T yb,  Mb += yb x^T */
+static void mv_vjp(const double M[9], const double x[3], const double yb[3], double xb[3], double Mb[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (xb) xb[j] += M[3 * i + j] * yb[i];
+            if (Mb) Mb[3 * i + j] += yb[i] * x[j];
+        }
+}
+
+/* r = a x b:  ab += b x rb,  bb += rb x a */
+static void cross_vjp(const double a[3], const double b[3], const double rb[3], double ab[3], double bb[3]) {
+    double t[3];
+    if (ab) { v_cross(b, rb, t); v_add(ab, t, ab); }
+    if (bb) { v_cross(rb, a, t); v_add(bb, t, bb); }
+}
+
+/* M = R S R^T (S symmetric):  Rb += (Mb + Mb^T) R S,  Sb += R^T Mb R */
+static void sandwich_vjp(const double R[9], const double S[9], const double Mb[9], double Rb[9], double Sb[9]) {
+    double Ms[9], t[9], Rt[9], u[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Ms[3 * i + j] = Mb[3 * i + j] + Mb[3 * j + i];
+    m_mul(Ms, R, t);
+    m_mul(t, S, u);
+    for (int k = 0; k < 9; ++k) Rb[k] += u[k];
+    if (Sb) {
+        m_transpose(R, Rt);
+        m_mul(Rt, Mb, t);
+        m_mul(t, R, u);
+        for (int k = 0; k < 9; ++k) Sb[k] += u[k];
+    }
+}
+
+/* adjoints of one row's data, accumulated over the sweeps */
+typedef struct {
+    double d[3][3], a[3][3], b[3][3], k[3], bias, e[3], mu;
+} drow_bar_t;
+
+/* reverse of diff_row_fwd: (v, w, lam) before the update in u; vb, wb, lb hold the
+ * adjoints of the outputs and receive those of the inputs; row adjoints into RB */
+static void diff_row_rev(const drow_t *D, double invm, const double *u, unsigned char bits, double vb[3],
+                         double wb[3], double lb[3], drow_bar_t *RB, double *invm_b) {
+    const double *v = u, *wv = u + 3, *lam = u + 6;
+    /* recompute the forward of this update */
+    const double jv = v_dot(D->d[0], v) + v_dot(D->a[0], wv) + D->bias + D->e[0];
+    const double uu = lam[0] - D->k[0] * jv;
+    const int act = bits & 1, proj = (bits & 2) != 0;
+    const double ln = act ? uu : 0.0, dl = ln - lam[0];
+    double vm[3], wm[3];
+    for (int i = 0; i < 3; ++i) { vm[i] = v[i] + invm * dl * D->d[0][i]; wm[i] = wv[i] + dl * D->b[0][i]; }
+    const double j1 = v_dot(D->d[1], vm) + v_dot(D->a[1], wm) + D->e[1];
+    const double j2 = v_dot(D->d[2], vm) + v_dot(D->a[2], wm) + D->e[2];
+    const double t1 = lam[1] - D->k[1] * j1, t2 = lam[2] - D->k[2] * j2;
+    const double lim = D->mu * ln, tn = sqrt(t1 * t1 + t2 * t2);
+    const double s = proj ? lim / tn : 1.0;
+    const double l1 = s * t1, l2 = s * t2, e1 = l1 - lam[1], e2 = l2 - lam[2];
+    /* v' = vm + invm (e1 d1 + e2 d2),  w' = wm + e1 b1 + e2 b2 */
+    double vmb[3], wmb[3];
+    memcpy(vmb, vb, sizeof vmb);
+    memcpy(wmb, wb, sizeof wmb);
+    const double e1b = invm * v_dot(D->d[1], vb) + v_dot(D->b[1], wb);
+    const double e2b = invm * v_dot(D->d[2], vb) + v_dot(D->b[2], wb);
+    for (int i = 0; i < 3; ++i) {
+        RB->d[1][i] += invm * e1 * vb[i];
+        RB->d[2][i] += invm * e2 * vb[i];
+        RB->b[1][i] += e1 * wb[i];
+        RB->b[2][i] += e2 * wb[i];
+    }
+    *invm_b += v_dot(vb, D->d[1]) * e1 + v_dot(vb, D->d[2]) * e2;
+    /* e_k = l_k' - l_k */
+    double l1b = lb[1] + e1b, l2b = lb[2] + e2b;
+    double lam_b1 = -e1b, lam_b2 = -e2b;
+    /* l_k' = s t_k */
+    double t1b = s * l1b, t2b = s * l2b;
+    double lnb = lb[0];
+    if (proj) {
+        const double sb = t1 * l1b + t2 * l2b;
+        const double limb = sb / tn;
+        const double tnb = -sb * lim / (tn * tn);
+        t1b += tnb * t1 / tn;
+        t2b += tnb * t2 / tn;
+        RB->mu += ln * limb;
+        lnb += D->mu * limb;
+    }
+    /* t_k = l_k - k_tk j_k */
+    lam_b1 += t1b;
+    lam_b2 += t2b;
+    RB->k[1] -= j1 * t1b;
+    RB->k[2] -= j2 * t2b;
+    const double j1b = -D->k[1] * t1b, j2b = -D->k[2] * t2b;
+    /* j_k = d_k . vm + a_k . wm + e_k */
+    for (int i = 0; i < 3; ++i) {
+        vmb[i] += j1b * D->d[1][i] + j2b * D->d[2][i];
+        wmb[i] += j1b * D->a[1][i] + j2b * D->a[2][i];
+        RB->d[1][i] += j1b * vm[i];
+        RB->d[2][i] += j2b * vm[i];
+        RB->a[1][i] += j1b * wm[i];
+        RB->a[2][i] += j2b * wm[i];
+    }
+    RB->e[1] += j1b;
+    RB->e[2] += j2b;
+    /* vm = v + invm dl dn,  wm = w + dl bn */
+    const double dlb = invm * v_dot(D->d[0], vmb) + v_dot(D->b[0], wmb);
+    for (int i = 0; i < 3; ++i) {
+        RB->d[0][i] += invm * dl * vmb[i];
+        RB->b[0][i] += dl * wmb[i];
+    }
+    *invm_b += dl * v_dot(D->d[0], vmb);
+    /* dl = ln - lam_n */
+    lnb += dlb;
+    double lam_b0 = -dlb;
+    /* ln = max(0, u) with the taped branch */
+    const double ub = act ? lnb : 0.0;
+    /* u = lam_n - k_n jv */
+    lam_b0 += ub;
+    RB->k[0] -= jv * ub;
+    const double jvb = -D->k[0] * ub;
+    /* jv = dn . v + an . w + bias + e_n */
+    for (int i = 0; i < 3; ++i) {
+        vb[i] = vmb[i] + jvb * D->d[0][i];
+        wb[i] = wmb[i] + jvb * D->a[0][i];
+        RB->d[0][i] += jvb * v[i];
+        RB->a[0][i] += jvb * wv[i];
+    }
+    RB->bias += jvb;
+    RB->e[0] += jvb;
+    lb[0] = lam_b0; lb[1] = lam_b1; lb[2] = lam_b2;
+}
+
+/* Reverse of one env substep.  xb = adjoint of the dynamic body's state after the
+ * substep (p 3, q 4, v 3, w 3), replaced by the adjoint before it; mass_b and mu_b
+ * (per global pair) accumulate.  F holds the forward intermediates (keep_updates). */
+static void diff_env_reverse(or_world *w, const dfwd_t *F, double xb[13], double *mass_b, double *mu_b) {
+    const body_t *A = &w->bodies[F->ia];
+    const struct diff_tape *T = w->tape;
+    const double hs = T->hs;
+    const int K = T->K;
+    const double m = A->mass;
+    double qb1[4], wcb[3], vb[3], wb[3];
+    memcpy(qb1, xb + 3, sizeof qb1);
+    memcpy(vb, xb + 7, sizeof vb);         /* final velocities are the state's */
+    memcpy(wcb, xb + 10, sizeof wcb);
+    double pbt[3] = {0, 0, 0}, comb[3], Rb[9] = {0}, qb[4] = {0, 0, 0, 0};
+    /* ---- integration: p' = c' - R(q') com_b, q' = qt/|qt|, qt = q + hs/2 (w,0)(x)q,
+     * c' = com + hs vf, w' = wc */
+    memcpy(comb, xb, 3 * sizeof(double));  /* dp'/dc' = I */
+    double R1b[9] = {0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R1b[3 * i + j] -= xb[i] * A->com_b[j];
+    q_to_m_vjp(F->q1, R1b, qb1);
+    const double qn = sqrt(F->qt[0] * F->qt[0] + F->qt[1] * F->qt[1] + F->qt[2] * F->qt[2] + F->qt[3] * F->qt[3]);
+    const double dq1 = F->q1[0] * qb1[0] + F->q1[1] * qb1[1] + F->q1[2] * qb1[2] + F->q1[3] * qb1[3];
+    double tb[4];
+    for (int k = 0; k < 4; ++k) tb[k] = (qb1[k] - F->q1[k] * dq1) / qn;
+    const double hh = 0.5 * hs;
+    const double *q = F->q0, *wc = F->wc;
+    for (int k = 0; k < 4; ++k) qb[k] += tb[k];
+    qb[0] += hh * (wc[2] * tb[1] - wc[1] * tb[2] - wc[0] * tb[3]);
+    qb[1] += hh * (-wc[2] * tb[0] + wc[0] * tb[2] - wc[1] * tb[3]);
+    qb[2] += hh * (wc[1] * tb[0] - wc[0] * tb[1] - wc[2] * tb[3]);
+    qb[3] += hh * (wc[0] * tb[0] + wc[1] * tb[1] + wc[2] * tb[2]);
+    wcb[0] += hh * (q[3] * tb[0] - q[2] * tb[1] + q[1] * tb[2] - q[0] * tb[3]);
+    wcb[1] += hh * (q[2] * tb[0] + q[3] * tb[1] - q[0] * tb[2] - q[1] * tb[3]);
+    wcb[2] += hh * (-q[1] * tb[0] + q[0] * tb[1] + q[3] * tb[2] - q[2] * tb[3]);
+    for (int i = 0; i < 3; ++i) vb[i] += hs * xb[i];     /* c' = com + hs vf */
+    if (F->clamped) {                                    /* wc = wf max / |wf| */
+        const double wn = v_norm(F->wf), s = w->cfg.max_angvel / wn;
+        double u[3], d;
+        v_scale(F->wf, 1.0 / wn, u);
+        d = v_dot(u, wcb);
+        for (int i = 0; i < 3; ++i) wb[i] = s * (wcb[i] - u[i] * d);
+    } else {
+        memcpy(wb, wcb, sizeof wb);
+    }
+    /* ---- sweeps, last update first; the final impulses carry no adjoint */
+    const int nr = F->nr;
+    double *lb = (double *)calloc(3 * (nr > 0 ? nr : 1), sizeof(double));
+    drow_bar_t *RBr = (drow_bar_t *)calloc(nr > 0 ? nr : 1, sizeof(drow_bar_t));
+    double invm_b = 0.0;
+    for (int it = K - 1; it >= 0; --it)
+        for (int r = nr - 1; r >= 0; --r) {
+            if (!F->rows[r].live) continue;
+            diff_row_rev(&F->rows[r], A->invm, F->upd + 9 * ((size_t)it * nr + r),
+                         T->r_bits[(size_t)K * (F->c0 + r) + it], vb, wb, lb + 3 * r, &RBr[r], &invm_b);
+        }
+    /* vb, wb: adjoints of v1, w1 */
+    /* ---- rows from the contacts */
+    double Iib[9] = {0};
+    for (int r = 0; r < nr; ++r) {
+        const drow_t *D = &F->rows[r];
+        if (!D->live) continue;
+        drow_bar_t *X = &RBr[r];
+        const body_t *B = &w->bodies[w->pairs[D->pair].b];
+        double ab_[3][3], bb_[3][3], db_[3][3];
+        memcpy(ab_, X->a, sizeof ab_);
+        memcpy(bb_, X->b, sizeof bb_);
+        memcpy(db_, X->d, sizeof db_);
+        double rab[3] = {0, 0, 0}, uob[3] = {0, 0, 0}, rbb[3] = {0, 0, 0};
+        for (int j = 0; j < 3; ++j) {
+            const double denb = -D->k[j] * D->k[j] * X->k[j];      /* k = 1/den */
+            invm_b += denb;
+            for (int i = 0; i < 3; ++i) { ab_[j][i] += denb * D->b[j][i]; bb_[j][i] += denb * D->a[j][i]; }
+            mv_vjp(F->Ii, D->a[j], bb_[j], ab_[j], Iib);           /* b = Ii a */
+            for (int i = 0; i < 3; ++i) { uob[i] -= X->e[j] * D->d[j][i]; db_[j][i] -= X->e[j] * D->uo[i]; }
+            cross_vjp(D->ra, D->d[j], ab_[j], rab, db_[j]);       /* a = ra x d */
+        }
+        mu_b[D->pair] += X->mu;
+        double phib = X->bias * ((D->flags & 2) ? 1.0 / hs : w->cfg.baumgarte / hs);
+        cross_vjp(B->w, D->rb, uob, NULL, rbb);                   /* uo = vB + wB x rb */
+        double xbwb[3], xab[3], nbv[3];
+        memcpy(xbwb, rbb, sizeof xbwb);                          /* rb = xbw - comB */
+        memcpy(xab, rab, sizeof xab);                            /* ra = xa - com */
+        for (int i = 0; i < 3; ++i) comb[i] -= rab[i];
+        /* d0 = n, d1 = tr / |tr|, d2 = n x d1 */
+        memcpy(nbv, db_[0], sizeof nbv);
+        double d1b[3];
+        memcpy(d1b, db_[1], sizeof d1b);
+        cross_vjp(D->n, D->d[1], db_[2], nbv, d1b);
+        const double dd = v_dot(D->d[1], d1b);
+        double trb[3];
+        for (int i = 0; i < 3; ++i) trb[i] = (d1b[i] - D->d[1][i] * dd) / D->tn;
+        if (D->flags & 1) { nbv[2] += trb[1]; nbv[1] -= trb[2]; }
+        else { nbv[2] -= trb[0]; nbv[0] += trb[2]; }
+        /* xbw = xa - phi n */
+        for (int i = 0; i < 3; ++i) { xab[i] += xbwb[i]; nbv[i] -= D->phi * xbwb[i]; }
+        phib -= v_dot(D->n, xbwb);
+        /* n = RB nb, nb = g / |g| */
+        double RBm[9], RBt[9], nbb[3], gb[3], xblb[3], xwb[3];
+        q_to_m(B->q, RBm);
+        m_transpose(RBm, RBt);
+        m_vec(RBt, nbv, nbb);
+        const double gd = v_dot(D->nb, nbb);
+        for (int i = 0; i < 3; ++i) gb[i] = (nbb[i] - D->nb[i] * gd) / D->gn;
+        /* (phi, g) of the taped cell's trilinear polynomial at xbl */
+        m_vec(D->H, gb, xblb);
+        for (int i = 0; i < 3; ++i) xblb[i] += D->g[i] * phib;
+        /* xbl = RB^T (xw - pB), xa = xw = R s + p */
+        m_vec(RBm, xblb, xwb);
+        v_add(xwb, xab, xwb);
+        for (int i = 0; i < 3; ++i) {
+            pbt[i] += xwb[i];
+            for (int j = 0; j < 3; ++j) Rb[3 * i + j] += xwb[i] * D->s[j];
+        }
+    }
+    free(lb);
+    free(RBr);
+    /* ---- external forces: v1 = v + hs (g + F/m), w1 = w + hs Ii (tau - w x Iw w) */
+    *mass_b += -hs * v_dot(A->force, vb) / (m * m);
+    double tqb[3], gyb[3], Lwb[3] = {0, 0, 0}, Iwb[9] = {0}, w0b[3];
+    memcpy(w0b, wb, sizeof w0b);
+    m_vec(F->Ii, wb, tqb);
+    v_scale(tqb, hs, tqb);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Iib[3 * i + j] += hs * wb[i] * F->tq[j];
+    v_scale(tqb, -1.0, gyb);
+    cross_vjp(F->w0, F->Lw, gyb, w0b, Lwb);
+    mv_vjp(F->Iw, F->w0, Lwb, w0b, Iwb);
+    /* com = R com_b + p */
+    for (int i = 0; i < 3; ++i) {
+        pbt[i] += comb[i];
+        for (int j = 0; j < 3; ++j) Rb[3 * i + j] += comb[i] * A->com_b[j];
+    }
+    /* Iw = R Ib R^T, Ii = R Ib^-1 R^T; Ib = m I_1, Ib^-1 = I_1^-1 / m, invm = 1/m */
+    double Ibb[9] = {0}, Ibib[9] = {0};
+    sandwich_vjp(F->R, A->Ib, Iwb, Rb, Ibb);
+    sandwich_vjp(F->R, A->Ib_inv, Iib, Rb, Ibib);
+    double s1 = 0, s2 = 0;
+    for (int k = 0; k < 9; ++k) { s1 += Ibb[k] * A->Ib[k]; s2 += Ibib[k] * A->Ib_inv[k]; }
+    *mass_b += s1 / m - s2 / m - invm_b / (m * m);
+    q_to_m_vjp(F->q0, Rb, qb);
+    memcpy(xb, pbt, 3 * sizeof(double));
+    memcpy(xb + 3, qb, 4 * sizeof(double));
+    memcpy(xb + 7, vb, 3 * sizeof(double));
+    memcpy(xb + 10, w0b, 3 * sizeof(double));
+}
+
+/* ---- public entry points ---- */
+
+int or_diff_record(or_world *w, int n_substeps, int n_iters) {
+    if (w->cfg.n_vel_iters != 0 || n_substeps < 1 || n_iters < 0) return -1;
+    for (int e = 0; e < w->n_envs; ++e)
+        if (diff_env_body(w, e) == -1) return -1;
+    diff_tape_free(w);
+    const double hs = w->cfg.dt / (double)n_substeps;
+    w->tape = diff_tape_new(n_substeps, w->n_envs, n_iters, hs);
+    for (int si = 0; si < n_substeps; ++si) {
+        or_collide(w);
+        for (int e = 0; e < w->n_envs; ++e) {
+            dfwd_t F;
+            diff_env_forward(w, e, si, 0, &F, 0);
+            dfwd_free(&F);
+        }
+    }
+    return 0;
+}
+
+int or_diff_replay(or_world *w) {
+    if (!w->tape) return -1;
+    for (int si = 0; si < w->tape->S; ++si)
+        for (int e = 0; e < w->n_envs; ++e) {
+            dfwd_t F;
+            if (diff_env_forward(w, e, si, 1, &F, 0)) return -1;
+            dfwd_free(&F);
+        }
+    return 0;
+}
+
+/* Gradient of a replay from the current state (which is left unchanged).  g_* are the
+ * adjoints of the final state (n_bodies entries each); d_* receive those of the initial
+ * state; d_mass (n_bodies) and d_mu (n_pairs) those of the parameters.  Bodies without
+ * dynamics get zero. */
+int or_diff_adjoint(or_world *w, const double *g_pos, const double *g_quat, const double *g_lin,
+                    const double *g_ang, double *d_pos, double *d_quat, double *d_lin, double *d_ang,
+                    double *d_mass, double *d_mu) {
+    struct diff_tape *T = w->tape;
+    if (!T) return -1;
+    const int nb = w->n_bodies;
+    double *x0 = (double *)malloc(sizeof(double) * 13 * nb);
+    for (int i = 0; i < nb; ++i) {
+        const body_t *b = &w->bodies[i];
+        memcpy(x0 + 13 * i, b->p, 3 * sizeof(double)); memcpy(x0 + 13 * i + 3, b->q, 4 * sizeof(double));
+        memcpy(x0 + 13 * i + 7, b->v, 3 * sizeof(double)); memcpy(x0 + 13 * i + 10, b->w, 3 * sizeof(double));
+    }
+    /* checkpoints: the state at each substep's start */
+    double *ck = (double *)malloc(sizeof(double) * 13 * nb * (size_t)T->S);
+    for (int si = 0; si < T->S; ++si) {
+        for (int i = 0; i < nb; ++i) {
+            const body_t *b = &w->bodies[i];
+            double *c = ck + 13 * ((size_t)si * nb + i);
+            memcpy(c, b->p, 3 * sizeof(double)); memcpy(c + 3, b->q, 4 * sizeof(double));
+            memcpy(c + 7, b->v, 3 * sizeof(double)); memcpy(c + 10, b->w, 3 * sizeof(double));
+        }
+        for (int e = 0; e < w->n_envs; ++e) {
+            dfwd_t F;
+            diff_env_forward(w, e, si, 1, &F, 0);
+            dfwd_free(&F);
+        }
+    }
+    double *xb = (double *)calloc(13 * (size_t)nb, sizeof(double));
+    for (int i = 0; i < nb; ++i) {
+        memcpy(xb + 13 * i, g_pos + 3 * i, 3 * sizeof(double)); memcpy(xb + 13 * i + 3, g_quat + 4 * i, 4 * sizeof(double));
+        memcpy(xb + 13 * i + 7, g_lin + 3 * i, 3 * sizeof(double)); memcpy(xb + 13 * i + 10, g_ang + 3 * i, 3 * sizeof(double));
+    }
+    for (int i = 0; i < nb; ++i) d_mass[i] = 0.0;
+    for (int p = 0; p < w->n_pairs; ++p) d_mu[p] = 0.0;
+    for (int si = T->S - 1; si >= 0; --si) {
+        for (int i = 0; i < nb; ++i) {      /* recompute from the checkpoint */
+            body_t *b = &w->bodies[i];
+            const double *c = ck + 13 * ((size_t)si * nb + i);
+            memcpy(b->p, c, 3 * sizeof(double)); memcpy(b->q, c + 3, 4 * sizeof(double));
+            memcpy(b->v, c + 7, 3 * sizeof(double)); memcpy(b->w, c + 10, 3 * sizeof(double));
+        }
+        for (int e = 0; e < w->n_envs; ++e) {
+            dfwd_t F;
+            diff_env_forward(w, e, si, 1, &F, 1);
+            if (F.ia >= 0) diff_env_reverse(w, &F, xb + 13 * F.ia, &d_mass[F.ia], d_mu);
+            dfwd_free(&F);
+        }
+    }
+    for (int i = 0; i < nb; ++i) {
+        const int dyn = w->bodies[i].type == 2;
+        for (int k = 0; k < 3; ++k) {
+            d_pos[3 * i + k] = dyn ? xb[13 * i + k] : 0.0;
+            d_lin[3 * i + k] = dyn ? xb[13 * i + 7 + k] : 0.0;
+            d_ang[3 * i + k] = dyn ? xb[13 * i + 10 + k] : 0.0;
+        }
+        for (int k = 0; k < 4; ++k) d_quat[4 * i + k] = dyn ? xb[13 * i + 3 + k] : 0.0;
+        body_t *b = &w->bodies[i];
+        memcpy(b->p, x0 + 13 * i, 3 * sizeof(double)); memcpy(b->q, x0 + 13 * i + 3, 4 * sizeof(double));
+        memcpy(b->v, x0 + 13 * i + 7, 3 * sizeof(double)); memcpy(b->w, x0 + 13 * i + 10, 3 * sizeof(double));
+    }
+    free(x0); free(ck); free(xb);
+    return 0;
+}
+
+/* Tape exchange: sizes, then arrays in the layout described above. */
+int or_diff_tape_info(const or_world *w, int *S, int *E, int *K, double *hs, int *n_contacts) {
+    if (!w->tape) return -1;
+    *S = w->tape->S; *E = w->tape->E; *K = w->tape->K; *hs = w->tape->hs; *n_contacts = w->tape->n_c;
+    return 0;
+}
+
+int or_diff_get_tape(const or_world *w, int *c_off, int *c_rec, unsigned char *r_bits, unsigned char *b_bits) {
+    const struct diff_tape *T = w->tape;
+    if (!T) return -1;
+    memcpy(c_off, T->c_off, sizeof(int) * ((size_t)T->S * T->E + 1));
+    memcpy(c_rec, T->c_rec, sizeof(int) * 6 * (size_t)T->n_c);
+    memcpy(r_bits, T->r_bits, (size_t)T->K * T->n_c);
+    memcpy(b_bits, T->b_bits, (size_t)T->S * T->E);
+    return 0;
+}
+
+int or_diff_set_tape(or_world *w, int S, int K, double hs, const int *c_off, const int *c_rec,
+                     const unsigned char *r_bits, const unsigned char *b_bits) {
+    if (S < 1 || K < 0 || w->cfg.n_vel_iters != 0) return -1;
+    for (int e = 0; e < w->n_envs; ++e)
+        if (diff_env_body(w, e) == -1) return -1;
+    diff_tape_free(w);
+    struct diff_tape *T = diff_tape_new(S, w->n_envs, K, hs);
+    memcpy(T->c_off, c_off, sizeof(int) * ((size_t)S * w->n_envs + 1));
+    T->n_c = T->cap_c = c_off[(size_t)S * w->n_envs];
+    T->c_rec = (int *)malloc(sizeof(int) * 6 * (size_t)(T->n_c > 0 ? T->n_c : 1));
+    T->r_bits = (unsigned char *)malloc((size_t)K * (T->n_c > 0 ? T->n_c : 1) + 1);
+    memcpy(T->c_rec, c_rec, sizeof(int) * 6 * (size_t)T->n_c);
+    memcpy(T->r_bits, r_bits, (size_t)K * T->n_c);
+    memcpy(T->b_bits, b_bits, (size_t)S * w->n_envs);
+    w->tape = T;
+    return 0;
+}
+
+/* Parameters of the differentiable rollout: a dynamic body's mass (inertia scaled at
+ * fixed geometry) and a pair's friction coefficient. */
+int or_set_body_mass(or_world *w, int body, double mass) {
+    if (body < 0 || body >= w->n_bodies || !(mass > 0.0)) return -1;
+    body_t *b = &w->bodies[body];
+    const double s = mass / b->mass;
+    for (int k = 0; k < 9; ++k) { b->Ib[k] *= s; b->Ib_inv[k] /= s; }
+    b->mass = mass;
+    b->invm = (b->type == 2) ? 1.0 / mass : 0.0;
+    return 0;
+}
+
+int or_set_pair_mu(or_world *w, int pair, double mu) {
+    if (pair < 0 || pair >= w->n_pairs || !(mu >= 0.0)) return -1;
+    w->pairs[pair].mu = mu;
+    return 0;
+}
+
+int or_n_pairs(const or_world *w) { return w->n_pairs; }
+double or_get_body_mass(const or_world *w, int body) { return w->bodies[body].mass; }
+double or_get_pair_mu(const or_world *w, int pair) { return w->pairs[pair].mu; }

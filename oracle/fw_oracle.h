@@ -153,6 +153,30 @@ double or_bake_seconds(const or_world *w);
 /* Friction-cone record of the last solve: per contact row of env, (lambda_n, |lambda_t|, mu). */
 int or_get_impulses(const or_world *w, int env, double *out, int cap, int *n_out);
 
+/* ---- differentiable rollout (reverse mode with the discrete decisions held fixed) ----
+ * Envs must have at most one dynamic body, the point body a of each of their pairs, with
+ * static or kinematic partners, and n_vel_iters = 0.  See fw_oracle.c for the tape. */
+/* One frame (dt) of n_substeps substeps with n_iters sweeps from the current state,
+ * detection and decisions as in or_step, recording the tape; the state advances. */
+int or_diff_record(or_world *w, int n_substeps, int n_iters);
+/* The taped rollout from the current state with every decision taken from the tape. */
+int or_diff_replay(or_world *w);
+/* Reverse mode of or_diff_replay at the current state (left unchanged): adjoints of the
+ * final state in, adjoints of the initial state, of each body's mass and of each pair's
+ * friction coefficient out. */
+int or_diff_adjoint(or_world *w, const double *g_pos, const double *g_quat, const double *g_lin,
+                    const double *g_ang, double *d_pos, double *d_quat, double *d_lin, double *d_ang,
+                    double *d_mass, double *d_mu);
+int or_diff_tape_info(const or_world *w, int *S, int *E, int *K, double *hs, int *n_contacts);
+int or_diff_get_tape(const or_world *w, int *c_off, int *c_rec, unsigned char *r_bits, unsigned char *b_bits);
+int or_diff_set_tape(or_world *w, int S, int K, double hs, const int *c_off, const int *c_rec,
+                     const unsigned char *r_bits, const unsigned char *b_bits);
+int or_set_body_mass(or_world *w, int body, double mass);
+int or_set_pair_mu(or_world *w, int pair, double mu);
+int or_n_pairs(const or_world *w);
+double or_get_body_mass(const or_world *w, int body);
+double or_get_pair_mu(const or_world *w, int pair);
+
 /* Algorithm 1 on a given candidate list (sorted by sample index is not required). */
 int or_reduce(const or_candidate *cand, int n, double cos_patch, int max_patches,
               int batch_size, or_contact *out, int cap, int *n_out, int *n_patches,

@@ -49,6 +49,7 @@ _P = np.ctypeslib.ndpointer
 _f32 = _P(dtype=np.float32, flags="C_CONTIGUOUS")
 _f64 = _P(dtype=np.float64, flags="C_CONTIGUOUS")
 _i32 = _P(dtype=np.int32, flags="C_CONTIGUOUS")
+_u8 = _P(dtype=np.uint8, flags="C_CONTIGUOUS")
 _i64 = _P(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
@@ -99,6 +100,20 @@ def lib():
             L.or_bake_seconds.restype = C.c_double
             L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32, _f64]
             L.or_pair_candidates.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
+            L.or_diff_record.argtypes = [vp, C.c_int, C.c_int]
+            L.or_diff_replay.argtypes = [vp]
+            L.or_diff_adjoint.argtypes = [vp] + [_f64] * 10
+            L.or_diff_tape_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_int)]
+            L.or_diff_get_tape.argtypes = [vp, _i32, _i32, _u8, _u8]
+            L.or_diff_set_tape.argtypes = [vp, C.c_int, C.c_int, C.c_double, _i32, _i32, _u8, _u8]
+            L.or_set_body_mass.argtypes = [vp, C.c_int, C.c_double]
+            L.or_set_pair_mu.argtypes = [vp, C.c_int, C.c_double]
+            L.or_n_pairs.argtypes = [vp]
+            L.or_get_body_mass.argtypes = [vp, C.c_int]
+            L.or_get_body_mass.restype = C.c_double
+            L.or_get_pair_mu.argtypes = [vp, C.c_int]
+            L.or_get_pair_mu.restype = C.c_double
             L.or_reduce.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, vp, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]
@@ -307,6 +322,63 @@ class OracleWorld:
 
     def bake_seconds(self) -> float:
         return lib().or_bake_seconds(self.h)
+
+    # ---- differentiable rollout (decisions held fixed by a tape; see fw_oracle.c)
+    def diff_record(self, n_substeps: int, n_iters: int):
+        if lib().or_diff_record(self.h, n_substeps, n_iters) != 0:
+            raise ValueError("or_diff_record: world not differentiable")
+
+    def diff_replay(self):
+        if lib().or_diff_replay(self.h) != 0:
+            raise ValueError("or_diff_replay: no tape")
+
+    def diff_adjoint(self, g_pos, g_quat, g_lin, g_ang):
+        """Adjoints of the initial state and parameters of a replay from the current state:
+        dict(pos, quat, linvel, angvel (n_bodies x k), mass (n_bodies), mu (n_pairs))."""
+        n, npair = self.n_bodies, lib().or_n_pairs(self.h)
+        f = lambda a, k: np.ascontiguousarray(np.asarray(a, np.float64).reshape(n, k))
+        out = dict(pos=np.zeros((n, 3)), quat=np.zeros((n, 4)), linvel=np.zeros((n, 3)),
+                   angvel=np.zeros((n, 3)), mass=np.zeros(n), mu=np.zeros(npair))
+        st = lib().or_diff_adjoint(self.h, f(g_pos, 3), f(g_quat, 4), f(g_lin, 3), f(g_ang, 3), out["pos"],
+                                   out["quat"], out["linvel"], out["angvel"], out["mass"], out["mu"])
+        if st != 0:
+            raise ValueError("or_diff_adjoint: no tape")
+        return out
+
+    def get_tape(self):
+        S, E, K, n = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        hs = C.c_double()
+        if lib().or_diff_tape_info(self.h, C.byref(S), C.byref(E), C.byref(K), C.byref(hs), C.byref(n)) != 0:
+            raise ValueError("no tape")
+        t = dict(S=S.value, K=K.value, hs=hs.value, c_off=np.zeros(S.value * E.value + 1, np.int32),
+                 c_rec=np.zeros((max(n.value, 1), 6), np.int32), r_bits=np.zeros(max(K.value * n.value, 1), np.uint8),
+                 b_bits=np.zeros(S.value * E.value + 1, np.uint8))
+        lib().or_diff_get_tape(self.h, t["c_off"], t["c_rec"].reshape(-1), t["r_bits"], t["b_bits"])
+        t["c_rec"], t["r_bits"] = t["c_rec"][: n.value], t["r_bits"][: K.value * n.value]
+        return t
+
+    def set_tape(self, t):
+        st = lib().or_diff_set_tape(self.h, int(t["S"]), int(t["K"]), float(t["hs"]),
+                                    np.ascontiguousarray(t["c_off"], np.int32),
+                                    np.ascontiguousarray(np.asarray(t["c_rec"], np.int32).reshape(-1)),
+                                    np.ascontiguousarray(t["r_bits"], np.uint8),
+                                    np.ascontiguousarray(t["b_bits"], np.uint8))
+        if st != 0:
+            raise ValueError("or_diff_set_tape refused the tape")
+
+    def set_body_mass(self, body: int, mass: float):
+        if lib().or_set_body_mass(self.h, body, float(mass)) != 0:
+            raise ValueError("bad body or mass")
+
+    def body_mass(self, body: int) -> float:
+        return lib().or_get_body_mass(self.h, body)
+
+    def pair_mu(self, pair: int) -> float:
+        return lib().or_get_pair_mu(self.h, pair)
+
+    def set_pair_mu(self, pair: int, mu: float):
+        if lib().or_set_pair_mu(self.h, pair, float(mu)) != 0:
+            raise ValueError("bad pair or mu")
 
     def query_pair(self, env: int, pair: int, n_samples: int):
         phi, nrm, valid = np.zeros(n_samples), np.zeros((n_samples, 3)), np.zeros(n_samples, np.int32)
