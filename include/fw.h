@@ -262,6 +262,49 @@ FW_API fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_con
 FW_API fw_status fw_reduce_noalloc(fw_world *w, const fw_candidate *d_cands, int n, fw_contact *d_out,
                                    int cap, int *d_counts);
 
+/* ------------------------------------------------ differentiable rollout */
+/* Reverse mode of the substep with its discrete decisions held fixed (no counterpart in
+ * the paper, which simulates forward only).  Envs taking part have at most one dynamic
+ * body, the point-sampled body a of each of their pairs, with static or kinematic
+ * partners (no fixed-axis bodies), and the world has n_vel_iters = 0.
+ *
+ * fw_record_rollout: one frame (dt) of n_substeps substeps with n_iters Gauss-Seidel
+ * sweeps from the current state, each substep running detection (Sec. III-A, III-C) and
+ * then the differentiable solve (Sec. III-B: normal row with lambda_n >= 0, friction rows
+ * projected jointly on the disk, semi-implicit integration), recording a tape of every
+ * discrete decision: the contacts (sample, pair, SDF cell), the tangent and bias
+ * branches, per contact and sweep the normal clamp and friction projection, and the
+ * |omega| clamp; and a checkpoint of the state at each substep's start.  The state
+ * advances.  FW_ERR_ARG when an env does not qualify.  Device memory for the tape and
+ * the checkpoints is allocated here (freed by the next record or fw_destroy).
+ * fw_replay_rollout: the recorded rollout again from the current state with every
+ * decision taken from the tape (the taped cell's trilinear polynomial is used even a
+ * little outside it): a smooth function of the initial state, the dynamic bodies'
+ * masses and the pairs' friction coefficients, equal to the recorded forward at the
+ * recorded point.  Writes new checkpoints.  FW_ERR_STATE without a record.
+ * fw_adjoint_rollout: the reverse mode of that function at the initial state of the
+ * last record or replay: given the adjoints of the final state (g_*, n_bodies entries
+ * of 3/4/3/3 floats), returns the adjoints of the initial state (d_*), of each body's
+ * mass (d_mass, n_bodies; inertia scales with mass at fixed geometry) and of each
+ * pair's friction coefficient (d_mu, n_pairs).  Bodies that are not dynamic get zero.
+ * Each substep is recomputed from its checkpoint, last first.  device_ptrs selects host
+ * (0) or device (1) arrays.  Synchronises.
+ * fw_get_tape: info = (substeps, envs, sweeps, contacts); with non-NULL arrays also the
+ * tape: c_off (substeps*envs + 1 offsets, env-major within each substep), c_rec (6 ints
+ * per contact: sample, pair, cell i, j, k, flags bit 0 t1 from n x e_x, bit 1 phi > 0),
+ * r_bits (sweeps per contact: bit 0 lambda_n > 0 after the row, bit 1 projected),
+ * b_bits (substeps*envs: bit 0 |omega| clamped).  Synchronises.
+ * fw_set_body_params: mass (n_bodies, <= 0 keeps; inertia rescaled with the mass) and
+ * mu (n_pairs, < 0 keeps), host arrays, either may be NULL.  Synchronises. */
+FW_API fw_status fw_record_rollout(fw_world *w, int n_substeps, int n_iters);
+FW_API fw_status fw_replay_rollout(fw_world *w);
+FW_API fw_status fw_adjoint_rollout(fw_world *w, const float *g_pos, const float *g_quat, const float *g_linvel,
+                                   const float *g_angvel, float *d_pos, float *d_quat, float *d_linvel,
+                                   float *d_angvel, float *d_mass, float *d_mu, int device_ptrs);
+FW_API fw_status fw_get_tape(fw_world *w, int info[4], int *c_off, int *c_rec, unsigned char *r_bits,
+                             unsigned char *b_bits);
+FW_API fw_status fw_set_body_params(fw_world *w, const float *mass, const float *mu);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Waits for the world's stream and reports the device status word. */

@@ -65,6 +65,9 @@ struct fw_world {
     // device limits and the solve's launch shape (0: chosen from the env count)
     int n_sm = 0, max_dyn_smem[4] = {0, 0, 0, 0};
     int solve_groups = 0, solve_warps = 0;
+    // differentiable rollout (fw_record_rollout .. fw_adjoint_rollout)
+    DiffState diff;
+    bool diff_valid = false;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -254,7 +257,7 @@ fw_status ensure_device(fw_world *w) {
         CK(cudaMemcpy(w->d_pairs, w->pairs.data(), sizeof(PairDev) * np, cudaMemcpyHostToDevice));
         CK(cudaMalloc(&w->d_contacts, sizeof(DContact) * (size_t)np * cp));
         CK(cudaMalloc(&w->d_counts, sizeof(int) * np));
-        CK(cudaMemset(w->d_counts, 0, sizeof(int) * np));
+        CK(cudaMemsetAsync(w->d_counts, 0, sizeof(int) * np, w->stream));
         long long sl = 0;
         for (auto &P : w->pairs)
             sl = std::max(sl, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
@@ -337,7 +340,7 @@ fw_status check_status(fw_world *w) {
     unsigned st = 0;
     CK(cudaMemcpy(&st, w->d_status, sizeof st, cudaMemcpyDeviceToHost));
     if (st) {
-        CK(cudaMemset(w->d_status, 0, sizeof st));
+        CK(cudaMemsetAsync(w->d_status, 0, sizeof st, w->stream));
         if (st & kStatusNonFinite) return fail(w, FW_ERR_NONFINITE, "a body state became non-finite");
         if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts than fit");
         if (st & kStatusBounds) return fail(w, FW_ERR_DEVICE_BOUNDS, "device index check failed");
@@ -374,6 +377,75 @@ fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs
 }
 
 bool ready(fw_world *w) { return w && cudaSetDevice(w->cfg.device) == cudaSuccess; }
+
+void diff_free(fw_world *w) {
+    DiffState &d = w->diff;
+    dfree(d.dyn); dfree(d.tape_c); dfree(d.tape_n); dfree(d.tape_r); dfree(d.tape_b); dfree(d.ck);
+    dfree(d.scratch); dfree(d.rows); dfree(d.rbar); dfree(d.upd); dfree(d.lam); dfree(d.xb); dfree(d.mass_b);
+    dfree(d.mu_row); dfree(d.mu_b);
+    d = DiffState();
+    w->diff_valid = false;
+}
+
+// Checks that every env is differentiable (at most one dynamic body, the point body a of
+// each of its pairs; no fixed-axis bodies) and returns each env's dynamic body.
+fw_status diff_envs(fw_world *w, std::vector<int> &dyn) {
+    dyn.assign(w->envs.size(), -1);
+    for (size_t e = 0; e < w->envs.size(); ++e) {
+        const EnvDev &E = w->envs[e];
+        for (int i = 0; i < E.n_bodies; ++i) {
+            const int t = w->props[E.first_body + i].type;
+            if (t == FW_BODY_FIXED_AXIS)
+                return fail(w, FW_ERR_ARG, "differentiable rollout: fixed-axis bodies are not supported");
+            if (t == FW_BODY_DYNAMIC) {
+                if (dyn[e] >= 0) return fail(w, FW_ERR_ARG, "differentiable rollout: more than one dynamic body in an env");
+                dyn[e] = E.first_body + i;
+            }
+        }
+        for (int k = 0; k < E.n_pairs; ++k)
+            if (dyn[e] >= 0 && w->pairs[E.first_pair + k].a != dyn[e])
+                return fail(w, FW_ERR_ARG, "differentiable rollout: the dynamic body must be the point body of every pair");
+    }
+    return FW_OK;
+}
+
+template <class T>
+fw_status dalloc(fw_world *w, T *&ptr, size_t bytes) {
+    dfree(ptr);
+    CK(cudaMalloc(reinterpret_cast<void **>(&ptr), bytes > 0 ? bytes : 16));
+    return FW_OK;
+}
+
+fw_status diff_alloc(fw_world *w, int S, int K) {
+    diff_free(w);
+    DiffState &d = w->diff;
+    const size_t E = w->envs.size(), nb = w->props.size(), np = w->pairs.size();
+    int rc = 1;
+    for (const auto &en : w->envs) rc = std::max(rc, en.row_cap);
+    d.S = S; d.K = K; d.row_cap = rc;
+    d.hs = w->cfg.dt / (float)S;
+    const size_t slots = (size_t)S * E, rows = E * (size_t)rc;
+    fw_status st = FW_OK;
+#define DA(ptr, bytes) if ((st = dalloc(w, ptr, bytes)) != FW_OK) return st
+    DA(d.dyn, sizeof(int) * E);
+    DA(d.tape_c, diff_tape_record_bytes() * slots * rc);
+    DA(d.tape_n, sizeof(int) * slots);
+    DA(d.tape_r, slots * rc * (size_t)std::max(K, 1));
+    DA(d.tape_b, slots);
+    DA(d.ck, sizeof(float) * 13 * nb * (size_t)S);
+    DA(d.scratch, sizeof(float) * 13 * nb);
+    DA(d.rows, diff_row_bytes() * rows);
+    DA(d.rbar, diff_row_bar_bytes() * rows);
+    DA(d.upd, sizeof(float) * 9 * rows * (size_t)std::max(K, 1));
+    DA(d.lam, sizeof(float) * 3 * rows);
+    DA(d.xb, sizeof(float) * 13 * nb);
+    DA(d.mass_b, sizeof(float) * nb);
+    DA(d.mu_row, sizeof(float) * rows);
+    DA(d.mu_b, sizeof(float) * std::max(np, (size_t)1));
+#undef DA
+    CK(cudaMemsetAsync(d.tape_n, 0, sizeof(int) * slots, w->stream));
+    return FW_OK;
+}
 
 }  // namespace
 
@@ -433,6 +505,7 @@ fw_status fw_destroy(fw_world *w) {
     cudaSetDevice(w->cfg.device);
     if (w->stream) cudaStreamSynchronize(w->stream);
     drop_graph(w);
+    diff_free(w);
     for (auto &A : w->assets) {
         dfree(A.d_samples); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
     }
@@ -978,7 +1051,7 @@ fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_contact *o
     CK(cudaMalloc(&d_out, sizeof(DContact) * cp));
     CK(cudaMalloc(&d_cnt, sizeof(int) * 2));
     if (n > 0) CK(cudaMemcpy(d_c, c.data(), sizeof(fw_candidate) * n, cudaMemcpyHostToDevice));
-    CK(cudaMemset(d_cnt, 0, sizeof(int) * 2));
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * 2, w->stream));
     SimParams p = sim_params(w, w->cfg.dt, 0);
     p.scratch = d_scr;
     CK(launch_reduce_list(p, d_c, n, d_out, d_cnt, d_cnt + 1, w->stream));
@@ -1076,6 +1149,143 @@ fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_blo
     const SolveShape sh = current_solve_shape(w, p);
     if (envs_per_warp) *envs_per_warp = sh.groups;
     if (warps_per_block) *warps_per_block = sh.warps;
+    return FW_OK;
+}
+
+fw_status fw_set_body_params(fw_world *w, const float *mass, const float *mu) {
+    if (!ready(w)) return FW_ERR_ARG;
+    CK(cudaStreamSynchronize(w->stream));
+    const int nb = (int)w->props.size(), np = (int)w->pairs.size();
+    if (mass)
+        for (int i = 0; i < nb; ++i) {
+            if (!(mass[i] > 0.0f)) continue;
+            BodyProps &P = w->props[i];
+            if (!(P.mass > 0.0f)) return fail(w, FW_ERR_ARG, "fw_set_body_params: body has no mass to rescale");
+            const float sc = mass[i] / P.mass;
+            for (int k = 0; k < 6; ++k) { P.Ib[k] *= sc; P.Ib_inv[k] /= sc; }
+            P.mass = mass[i];
+            if (P.type == FW_BODY_DYNAMIC) P.invm = 1.0f / mass[i];
+        }
+    if (mu)
+        for (int i = 0; i < np; ++i)
+            if (mu[i] >= 0.0f) w->pairs[i].mu = mu[i];
+    if (w->d_props && nb > 0) CK(cudaMemcpy(w->d_props, w->props.data(), sizeof(BodyProps) * nb, cudaMemcpyHostToDevice));
+    if (w->d_pairs && np > 0) CK(cudaMemcpy(w->d_pairs, w->pairs.data(), sizeof(PairDev) * np, cudaMemcpyHostToDevice));
+    return FW_OK;
+}
+
+fw_status fw_record_rollout(fw_world *w, int n_substeps, int n_iters) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n_substeps < 1 || n_iters < 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: bad substeps/iterations");
+    if (w->cfg.n_vel_iters != 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: needs n_vel_iters = 0");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    std::vector<int> dyn;
+    if ((st = diff_envs(w, dyn)) != FW_OK) return st;
+    if ((st = diff_alloc(w, n_substeps, n_iters)) != FW_OK) return st;
+    if (!dyn.empty()) {
+        CK(cudaMemcpyAsync(w->diff.dyn, dyn.data(), sizeof(int) * dyn.size(), cudaMemcpyHostToDevice, w->stream));
+        CK(cudaStreamSynchronize(w->stream));   // dyn is a local vector
+    }
+    const SimParams p = sim_params(w, w->diff.hs, n_iters);
+    const int nb = (int)w->props.size();
+    for (int si = 0; si < n_substeps; ++si) {
+        CK(launch_detect(p, w->stream));
+        CK(launch_diff_forward(p, w->diff, si, nb, false, w->stream));
+    }
+    w->diff_valid = true;
+    return FW_OK;
+}
+
+fw_status fw_replay_rollout(fw_world *w) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (!w->diff_valid) return fail(w, FW_ERR_STATE, "fw_replay_rollout: no recorded rollout");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const SimParams p = sim_params(w, w->diff.hs, w->diff.K);
+    for (int si = 0; si < w->diff.S; ++si) CK(launch_diff_forward(p, w->diff, si, (int)w->props.size(), true, w->stream));
+    return FW_OK;
+}
+
+fw_status fw_adjoint_rollout(fw_world *w, const float *g_pos, const float *g_quat, const float *g_linvel,
+                             const float *g_angvel, float *d_pos, float *d_quat, float *d_linvel, float *d_angvel,
+                             float *d_mass, float *d_mu, int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (!w->diff_valid) return fail(w, FW_ERR_STATE, "fw_adjoint_rollout: no recorded rollout");
+    if (!g_pos || !g_quat || !g_linvel || !g_angvel || !d_pos || !d_quat || !d_linvel || !d_angvel || !d_mass || !d_mu)
+        return fail(w, FW_ERR_ARG, "fw_adjoint_rollout: NULL pointer");
+    const int nb = (int)w->props.size(), np = (int)w->pairs.size();
+    const cudaMemcpyKind in_kind = device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    std::vector<float> g(4 * 13 * (size_t)nb), xb(13 * (size_t)nb);
+    float *gp = g.data(), *gq = gp + 3 * nb, *gv = gq + 4 * nb, *gw = gv + 3 * nb;
+    CK(cudaStreamSynchronize(w->stream));
+    CK(cudaMemcpy(gp, g_pos, sizeof(float) * 3 * nb, in_kind));
+    CK(cudaMemcpy(gq, g_quat, sizeof(float) * 4 * nb, in_kind));
+    CK(cudaMemcpy(gv, g_linvel, sizeof(float) * 3 * nb, in_kind));
+    CK(cudaMemcpy(gw, g_angvel, sizeof(float) * 3 * nb, in_kind));
+    for (int i = 0; i < nb; ++i) {
+        for (int k = 0; k < 3; ++k) { xb[13 * i + k] = gp[3 * i + k]; xb[13 * i + 7 + k] = gv[3 * i + k]; xb[13 * i + 10 + k] = gw[3 * i + k]; }
+        for (int k = 0; k < 4; ++k) xb[13 * i + 3 + k] = gq[4 * i + k];
+    }
+    DiffState &d = w->diff;
+    // everything in stream order on the world's stream (it does not synchronise with the
+    // legacy default stream), then one wait before reading back
+    CK(cudaMemcpyAsync(d.xb, xb.data(), sizeof(float) * 13 * nb, cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemsetAsync(d.mass_b, 0, sizeof(float) * nb, w->stream));
+    CK(cudaMemsetAsync(d.mu_b, 0, sizeof(float) * std::max(np, 1), w->stream));
+    const SimParams p = sim_params(w, d.hs, d.K);
+    for (int si = d.S - 1; si >= 0; --si) CK(launch_diff_reverse(p, d, si, nb, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    std::vector<float> mb(nb), mub(std::max(np, 1));
+    CK(cudaMemcpy(xb.data(), d.xb, sizeof(float) * 13 * nb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mb.data(), d.mass_b, sizeof(float) * nb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mub.data(), d.mu_b, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    std::vector<float> out(13 * (size_t)nb, 0.0f);
+    float *op = out.data(), *oq = op + 3 * nb, *ov = oq + 4 * nb, *ow = ov + 3 * nb;
+    for (int i = 0; i < nb; ++i) {
+        if (w->props[i].type != FW_BODY_DYNAMIC) { mb[i] = 0.0f; continue; }
+        for (int k = 0; k < 3; ++k) { op[3 * i + k] = xb[13 * i + k]; ov[3 * i + k] = xb[13 * i + 7 + k]; ow[3 * i + k] = xb[13 * i + 10 + k]; }
+        for (int k = 0; k < 4; ++k) oq[4 * i + k] = xb[13 * i + 3 + k];
+    }
+    const cudaMemcpyKind out_kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    CK(cudaMemcpy(d_pos, op, sizeof(float) * 3 * nb, out_kind));
+    CK(cudaMemcpy(d_quat, oq, sizeof(float) * 4 * nb, out_kind));
+    CK(cudaMemcpy(d_linvel, ov, sizeof(float) * 3 * nb, out_kind));
+    CK(cudaMemcpy(d_angvel, ow, sizeof(float) * 3 * nb, out_kind));
+    CK(cudaMemcpy(d_mass, mb.data(), sizeof(float) * nb, out_kind));
+    if (np > 0) CK(cudaMemcpy(d_mu, mub.data(), sizeof(float) * np, out_kind));
+    return FW_OK;
+}
+
+fw_status fw_get_tape(fw_world *w, int info[4], int *c_off, int *c_rec, unsigned char *r_bits, unsigned char *b_bits) {
+    if (!ready(w) || !info) return FW_ERR_ARG;
+    if (!w->diff_valid) return fail(w, FW_ERR_STATE, "fw_get_tape: no recorded rollout");
+    DiffState &d = w->diff;
+    const int E = (int)w->envs.size();
+    const size_t slots = (size_t)d.S * E;
+    CK(cudaStreamSynchronize(w->stream));
+    std::vector<int> tn(slots);
+    CK(cudaMemcpy(tn.data(), d.tape_n, sizeof(int) * slots, cudaMemcpyDeviceToHost));
+    long long total = 0;
+    for (int v : tn) total += v;
+    info[0] = d.S; info[1] = E; info[2] = d.K; info[3] = (int)total;
+    if (!c_off || !c_rec || !r_bits || !b_bits) return FW_OK;
+    const size_t rec_ints = diff_tape_record_bytes() / sizeof(int);
+    std::vector<int> tc(slots * d.row_cap * rec_ints);
+    std::vector<unsigned char> tr(slots * d.row_cap * (size_t)d.K), tb(slots);
+    CK(cudaMemcpy(tc.data(), d.tape_c, sizeof(int) * tc.size(), cudaMemcpyDeviceToHost));
+    if (!tr.empty()) CK(cudaMemcpy(tr.data(), d.tape_r, tr.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tb.data(), d.tape_b, slots, cudaMemcpyDeviceToHost));
+    int c = 0;
+    for (size_t sl = 0; sl < slots; ++sl) {
+        c_off[sl] = c;
+        for (int r = 0; r < tn[sl]; ++r, ++c) {
+            for (size_t k = 0; k < 6; ++k) c_rec[6 * (size_t)c + k] = tc[(sl * d.row_cap + r) * rec_ints + k];
+            for (int it = 0; it < d.K; ++it) r_bits[(size_t)d.K * c + it] = tr[(sl * d.row_cap + r) * d.K + it];
+        }
+        b_bits[sl] = tb[sl];
+    }
+    c_off[slots] = c;
     return FW_OK;
 }
 

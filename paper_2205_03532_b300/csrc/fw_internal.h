@@ -145,6 +145,27 @@ struct SolveShape {
     size_t smem;
 };
 size_t solve_smem_bytes(int lam_cap);
+// Differentiable rollout (fw_diff.cu owns the layouts behind the void pointers).
+struct DiffState {
+    int S = 0, K = 0, row_cap = 0;
+    float hs = 0.f;
+    int *dyn = nullptr;               // per env: the dynamic body (global id) or -1
+    void *tape_c = nullptr;           // S * n_envs * row_cap contact records (sample, pair, cell, flags)
+    int *tape_n = nullptr;            // S * n_envs
+    unsigned char *tape_r = nullptr;  // S * n_envs * row_cap * K decision bits
+    unsigned char *tape_b = nullptr;  // S * n_envs clamp bits
+    float *ck = nullptr;              // S checkpoints: pos | quat | lin | ang blocks of S * n_bodies
+    float *scratch = nullptr;         // 13 * n_bodies
+    void *rows = nullptr, *rbar = nullptr;   // n_envs * row_cap each
+    float *upd = nullptr, *lam = nullptr, *xb = nullptr, *mass_b = nullptr, *mu_row = nullptr, *mu_b = nullptr;
+};
+size_t diff_tape_record_bytes();
+size_t diff_row_bytes();
+size_t diff_row_bar_bytes();
+cudaError_t launch_diff_forward(const SimParams &p, const DiffState &d, int si, int n_bodies, bool replay,
+                                cudaStream_t s);
+cudaError_t launch_diff_reverse(const SimParams &p, const DiffState &d, int si, int n_bodies, cudaStream_t s);
+
 // Allows each solve instance (1, 2, 4, 8 envs per warp) the largest dynamic shared memory
 // that fits beside its static part in `optin` bytes; returns those limits in max_dyn.
 cudaError_t prepare_solve(int optin, int max_dyn[4]);

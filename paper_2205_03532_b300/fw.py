@@ -27,7 +27,8 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_get_solve_shape",
-                 "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
+                 "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_get_tape",
+                 "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
 
 
@@ -90,6 +91,11 @@ def load_library(path: str = LIB_PATH):
         "fw_get_timings": (st, [vp, vp, i]),
         "fw_set_solve_shape": (st, [vp, i, i]),
         "fw_get_solve_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
+        "fw_record_rollout": (st, [vp, i, i]),
+        "fw_replay_rollout": (st, [vp]),
+        "fw_adjoint_rollout": (st, [vp] + [vp] * 10 + [i]),
+        "fw_get_tape": (st, [vp, vp, vp, vp, vp, vp]),
+        "fw_set_body_params": (st, [vp, vp, vp]),
         "fw_get_detect_stats": (st, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "fw_launches_per_step": (i, [vp, i]),
@@ -318,6 +324,49 @@ class World:
     def launches_per_step(self, n_substeps: int) -> int:
         return self.lib.fw_launches_per_step(self.h, n_substeps)
 
+    # -- differentiable rollout
+    def record_rollout(self, n_substeps: int, n_iters: int):
+        self._check(self.lib.fw_record_rollout(self.h, n_substeps, n_iters))
+
+    def replay_rollout(self):
+        self._check(self.lib.fw_replay_rollout(self.h))
+
+    def adjoint_rollout(self, g_pos, g_quat, g_linvel, g_angvel):
+        """Adjoints of the initial state and parameters of the last record/replay, given
+        those of its final state.  numpy in -> numpy out, CUDA tensors in -> CUDA tensors
+        out: (pos, quat, linvel, angvel, mass, mu)."""
+        nb, npair = self.counts()[1], self.counts()[2]
+        dev = hasattr(g_pos, "data_ptr") and g_pos.is_cuda
+        if dev:
+            import torch
+            mk = lambda *shape: torch.zeros(shape, dtype=torch.float32, device=g_pos.device)
+            gs = [t.detach().contiguous().float() for t in (g_pos, g_quat, g_linvel, g_angvel)]
+        else:
+            mk = lambda *shape: np.zeros(shape, np.float32)
+            gs = [np.ascontiguousarray(a, np.float32) for a in (g_pos, g_quat, g_linvel, g_angvel)]
+        outs = [mk(nb, 3), mk(nb, 4), mk(nb, 3), mk(nb, 3), mk(nb), mk(max(npair, 1))]
+        self._check(self.lib.fw_adjoint_rollout(self.h, *[_ptr(a)[0] for a in gs], *[_ptr(a)[0] for a in outs],
+                                                int(dev)))
+        outs[5] = outs[5][:npair]
+        return tuple(outs)
+
+    def get_tape(self):
+        info = np.zeros(4, np.int32)
+        self._check(self.lib.fw_get_tape(self.h, info.ctypes.data, None, None, None, None))
+        S, E, K, n = (int(v) for v in info)
+        t = dict(S=S, K=K, c_off=np.zeros(S * E + 1, np.int32), c_rec=np.zeros((max(n, 1), 6), np.int32),
+                 r_bits=np.zeros(max(K * n, 1), np.uint8), b_bits=np.zeros(max(S * E, 1), np.uint8))
+        self._check(self.lib.fw_get_tape(self.h, info.ctypes.data, t["c_off"].ctypes.data, t["c_rec"].ctypes.data,
+                                         t["r_bits"].ctypes.data, t["b_bits"].ctypes.data))
+        t["c_rec"], t["r_bits"], t["b_bits"] = t["c_rec"][:n], t["r_bits"][: K * n], t["b_bits"][: S * E]
+        return t
+
+    def set_body_params(self, mass=None, mu=None):
+        m = None if mass is None else np.ascontiguousarray(mass, np.float32)
+        u = None if mu is None else np.ascontiguousarray(mu, np.float32)
+        self._check(self.lib.fw_set_body_params(self.h, None if m is None else m.ctypes.data,
+                                                None if u is None else u.ctypes.data))
+
 
 def world_from_scene(scene, fp16: bool = False, stream=None, **over) -> World:
     """Builds a World from a scenes.Scene: assets, SDF bakes, env groups."""
@@ -341,3 +390,37 @@ def world_from_scene(scene, fp16: bool = False, stream=None, **over) -> World:
     for g in scene.groups:
         w.add_env_bodies(g.bodies, g.pairs)
     return w
+
+
+def rollout_function():
+    """torch.autograd.Function over a recorded rollout: forward(world, n_substeps, n_iters,
+    pos0, quat0, linvel0, angvel0, mass, mu) sets the initial state (n_bodies x 3/4/3/3
+    CUDA tensors) and the parameters (mass per body, mu per pair), records the rollout and
+    returns the final (pos, quat, linvel, angvel); backward runs fw_adjoint_rollout with the
+    incoming gradients and returns those of the initial state, the masses and the mus."""
+    import torch
+
+    class Rollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, world, n_substeps, n_iters, pos0, quat0, linvel0, angvel0, mass, mu):
+            torch.cuda.synchronize(pos0.device)     # the world copies on its own stream
+            world.set_body_params(mass.detach().cpu().numpy(), mu.detach().cpu().numpy())
+            world.set_state(*[t.detach().contiguous().float() for t in (pos0, quat0, linvel0, angvel0)])
+            world.record_rollout(n_substeps, n_iters)
+            nb = world.counts()[1]
+            out = [torch.empty((nb, k), dtype=torch.float32, device=pos0.device) for k in (3, 4, 3, 3)]
+            world.get_state(out=out)
+            torch.cuda.synchronize(pos0.device)
+            ctx.world = world
+            return tuple(out)
+
+        @staticmethod
+        def backward(ctx, gp, gq, gv, gw):
+            dev = gp.device if gp is not None else gq.device
+            z = lambda t, k: t if t is not None else torch.zeros((ctx.world.counts()[1], k), device=dev)
+            torch.cuda.synchronize(dev)
+            dp, dq, dv, dw, dm, dmu = ctx.world.adjoint_rollout(z(gp, 3), z(gq, 4), z(gv, 3), z(gw, 3))
+            return None, None, None, dp, dq, dv, dw, dm, dmu
+
+    return Rollout
+

@@ -624,6 +624,37 @@ def peg_in_hole_scene(n_envs: int = 1, seed: int = 0, clearance_mm: float = 0.1,
     return Scene("peg_in_hole", [peg, hole], [EnvGroup(bodies, pairs)], sim)
 
 
+def diff_peg_scene(n_envs: int = 256, seed: int = 0, n_substeps: int = 32, n_iters: int = 8,
+                   mass_range_g: Tuple[float, float] = (5.0, 50.0),
+                   mu_range: Tuple[float, float] = (0.2, 0.8)) -> Tuple[Scene, np.ndarray, np.ndarray]:
+    """Differentiable peg-in-hole: the peg-in-hole geometry with 0.1 mm clearance, one
+    frame of 32 substeps x 8 sweeps, peg mass ~U(5, 50) g and friction ~U(0.2, 0.8) per
+    env.  Each peg starts 1-3 mm into the hole (the rollout is in contact throughout),
+    offset up to 0.08 mm sideways, tilted up to 0.3 deg, moving down at 2 cm/s with a
+    small sideways velocity and spin, pressed down by a constant 0.5 N (a gripper pushing
+    it in: without an applied force the motion under gravity and rigid contacts does not
+    depend on the mass, whose gradient would then be zero).  Returns the scene and
+    per-env target poses (peg bottom 6 mm into the hole, upright, centred) for a
+    squared-distance loss.""" 
+    sc = peg_in_hole_scene(n_envs=n_envs, seed=seed, clearance_mm=0.1, n_substeps=n_substeps,
+                           n_iters=n_iters, frames=1, mass_range_g=mass_range_g, mu_range=mu_range)
+    b = sc.groups[0].bodies
+    rng = np.random.default_rng(seed + 1)
+    b["pos"][:, 0, 2] = 12.5e-3 - rng.uniform(1e-3, 3e-3, n_envs)
+    b["pos"][:, 0, :2] = rng.uniform(-0.08e-3, 0.08e-3, (n_envs, 2))
+    b["linvel"][:, 0] = np.stack([rng.uniform(-5e-3, 5e-3, n_envs), rng.uniform(-5e-3, 5e-3, n_envs),
+                                  np.full(n_envs, -0.02)], axis=1)
+    b["angvel"][:, 0] = rng.uniform(-0.5, 0.5, (n_envs, 3))
+    b["force"][:, 0] = [0.0, 0.0, -0.5]
+    for e in range(n_envs):
+        t = np.deg2rad(rng.uniform(-0.3, 0.3, 2))
+        b["quat"][e, 0] = quat_mul(quat_axis_angle([1, 0, 0], t[0]), quat_axis_angle([0, 1, 0], t[1]))
+    target_pos = np.zeros((n_envs, 3))
+    target_pos[:, 2] = 12.5e-3 - 6e-3
+    target_quat = np.tile([0.0, 0.0, 0.0, 1.0], (n_envs, 1))
+    return sc, target_pos, target_quat
+
+
 def nut_bolt_assets(d: int = 16, n_samples: int = 10000, sdf_res: int = 256,
                     rng: Optional[np.random.Generator] = None, clearance_mm: float = 0.05,
                     bolt_n_ang: int = 42, nut_n_ang: int = 84):
