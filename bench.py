@@ -182,14 +182,21 @@ def run_fw(args):
     dev = local
     stream = torch.cuda.Stream(device=dev)
     t_setup = time.perf_counter()
-    sc = S.nut_bolt_scene(n_envs=args.envs, seed=args.seed + 1000 * rank)
+    if args.workload == "mixed":
+        sc = S.mixed_nut_bolt_scene(n_envs=args.envs if args.envs != 1000 else 4096, seed=args.seed + 1000 * rank)
+    else:
+        sc = S.nut_bolt_scene(n_envs=args.envs, seed=args.seed + 1000 * rank)
     sim = sc.sim
     with torch.cuda.stream(stream):
         t_b = time.perf_counter()
         w = fw.world_from_scene(sc, fp16=args.fp16, stream=stream.cuda_stream, device=dev)
         bake_s = time.perf_counter() - t_b
     n_env, n_body, n_pair = w.counts()
-    w.set_solve_shape(*[int(v) for v in args.solve_shape.split(",")])
+    shape = [int(v) for v in args.solve_shape.split(",")]
+    w.set_solve_shape(*shape)
+    tuned = None
+    if shape == [0, 0] and not args.no_autotune:   # untimed set-up: pick the fastest solve shape
+        tuned = w.autotune_solve(sim.n_substeps, sim.n_iters, trials=3)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
 
     def one_step():
@@ -238,9 +245,10 @@ def run_fw(args):
     sol_ms = tim["solve_ms"] / max(tim["solve_launches"], 1)
     n_cand, n_cont = w.detect_stats()          # of the last substep
     c_mean = n_cont / max(n_env, 1)
-    ns = len(sc.assets[0].samples)
+    queries = sum(len(g.bodies) * len(sc.assets[int(g.bodies["asset"][0, 0])].samples) for g in sc.groups)
+    ns = queries / max(n_pair, 1)
     hbm, sm_max, peak_kind = _peaks()
-    q_bytes = n_pair * ns * (QUERY_BYTES_PER_SAMPLE + 8 * QUERY_BYTES_PER_CORNER[bool(args.fp16)]) + n_cand * CANDIDATE_BYTES
+    q_bytes = queries * (QUERY_BYTES_PER_SAMPLE + 8 * QUERY_BYTES_PER_CORNER[bool(args.fp16)]) + n_cand * CANDIDATE_BYTES
     r_bytes = n_cand * CANDIDATE_BYTES + n_cont * CONTACT_BYTES
     sol_flops = n_cont * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
     alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -256,7 +264,7 @@ def run_fw(args):
     sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     kernels = {
         "query_kernel": dict(hbm_entry("query_kernel", q_bytes, qry_ms),
-                             queries_per_s=n_pair * ns / (qry_ms * 1e-3)),
+                             queries_per_s=queries / (qry_ms * 1e-3)),
         "reduce_kernel": hbm_entry("reduce_kernel", r_bytes, red_ms),
         "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": sol_tf / alu_peak, "traffic": traffic.get("solve_kernel"),
@@ -292,15 +300,17 @@ def run_fw(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)",
-               "config": {"workload": "nut_bolt_m16", "n_envs": n_env, "samples_per_nut": ns,
-                          "sdf": "256^3 " + ("fp16" if args.fp16 else "fp32"), "substeps": sim.n_substeps,
+               "config": {"workload": "mixed_nut_bolt_m8_m20" if args.workload == "mixed" else "nut_bolt_m16",
+                          "n_envs": n_env, "samples_per_nut": ns,
+                          "sdf": ("128^3-256^3 " if args.workload == "mixed" else "256^3 ") + ("fp16" if args.fp16 else "fp32"),
+                          "substeps": sim.n_substeps,
                           "iters": sim.n_iters, "frame_dt": sim.dt, "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "kernels": kernels,
                "phase_ms_per_frame": {"query": qry_ms * sim.n_substeps, "reduce": red_ms * sim.n_substeps,
                                       "solve": sol_ms * sim.n_substeps},
                "contacts_per_env": c_mean, "candidates_per_pair": n_cand / max(n_pair, 1),
-               "solve_shape": list(w.solve_shape()),
+               "solve_shape": list(w.solve_shape()), "autotuned": tuned is not None,
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),
                "e2e": {"value": e2e_value, "unit": "env-substeps/s", "h2d_bytes_per_step": state_bytes,
@@ -310,6 +320,57 @@ def run_fw(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_diff_peg(args):
+    """Gradient throughput on the differentiable peg workload (256 envs, one frame of 32
+    substeps x 8 sweeps): each step records the rollout from the same initial state and
+    runs its adjoint for a squared-distance pose loss.  Reported separately from the
+    headline (nut-bolt) line."""
+    import torch
+    from paper_2205_03532_b300 import fw, scenes as S
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    sc, tp, tq = S.diff_peg_scene(n_envs=args.envs if args.envs != 1000 else 256, seed=args.seed)
+    w = fw.world_from_scene(sc, device=local)
+    n_env, nb, npair = w.counts()
+    x0 = [torch.tensor(a, device="cuda") for a in w.get_state()]
+    pegs = torch.arange(0, nb, 2, device="cuda")
+    tpos = torch.tensor(tp, dtype=torch.float32, device="cuda")
+    S_, K = sc.sim.n_substeps, sc.sim.n_iters
+
+    def step():
+        w.set_state(*x0)
+        w.record_rollout(S_, K)
+        out = [torch.empty((nb, k), device="cuda") for k in (3, 4, 3, 3)]
+        w.get_state(out=out)
+        w.sync()
+        gp = torch.zeros(nb, 3, device="cuda")
+        gp[pegs] = 2 * (out[0][pegs] - tpos)
+        z3, z4 = torch.zeros(nb, 3, device="cuda"), torch.zeros(nb, 4, device="cuda")
+        t0 = time.perf_counter()
+        w.adjoint_rollout(gp, z4, z3, z3)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t_rec, t_adj = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ta = step()
+        t_rec.append(time.perf_counter() - t0 - ta)
+        t_adj.append(ta)
+    tot = sum(t_rec) + sum(t_adj)
+    units = n_env * S_ * args.steps
+    if rank == 0:
+        print(json.dumps({"metric": "gradient env-substeps/s", "value": units / tot, "unit": "env-substeps/s",
+                          "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic (procedural peg in hole, seeded)",
+                          "config": {"workload": "diff_peg", "n_envs": n_env, "substeps": S_, "iters": K},
+                          "record_ms": 1e3 * sum(t_rec) / args.steps, "adjoint_ms": 1e3 * sum(t_adj) / args.steps,
+                          "timing": "host wall clock around calls that synchronise"}), flush=True)
 
 
 def main():
@@ -325,11 +386,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=4)
     ap.add_argument("--ref-envs", type=int, default=2)
+    ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "diff_peg"],
+                    help="nut_bolt: the headline substep benchmark (1000 M16 envs); mixed: 4096 envs of "
+                         "M8-M20 pairs; diff_peg: gradient throughput of the differentiable peg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default solve shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "diff_peg":
+        run_diff_peg(args)
     else:
         run_fw(args)
 

@@ -328,6 +328,14 @@ FW_API fw_status fw_get_timings(fw_world *w, float *ms, int n);
  * group).  Errors: FW_ERR_ARG for values outside those sets.  fw_get_solve_shape returns
  * the shape the next fw_step will launch. */
 FW_API fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_per_block);
+/* Autotuner of that shape: at the current state, runs detection once for n_substeps /
+ * n_iters, then times `trials` solve launches for every shape that fits (envs per warp
+ * 1, 2, 4, 8 x warps per block 1..4), restoring the body state before each, and keeps
+ * the fastest (as fw_set_solve_shape would).  The state is left as it was.  Returns the
+ * chosen shape and its time per solve launch (ms); any output pointer may be NULL.
+ * Allocates and frees one state-sized device buffer; synchronises. */
+FW_API fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials, int *envs_per_warp,
+                                   int *warps_per_block, float *best_ms);
 FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block);
 
 /* Totals of the last detection pass (synchronises): candidates (samples with phi below

@@ -1143,6 +1143,72 @@ fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_per_block
     return FW_OK;
 }
 
+fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials, int *envs_per_warp,
+                            int *warps_per_block, float *best_ms) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (n_substeps < 1 || n_iters < 0 || trials < 1) return fail(w, FW_ERR_ARG, "fw_autotune_solve: bad arguments");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const int nb = (int)w->props.size();
+    if (nb == 0 || w->envs.empty()) return FW_OK;
+    // the state is saved and put back around every candidate, so tuning does not advance it
+    float *save = nullptr;
+    CK(cudaMalloc(&save, sizeof(float) * 13 * nb));
+    float *const src[4] = {w->d_pos, w->d_quat, w->d_vel, w->d_ang};
+    const size_t len[4] = {3, 4, 3, 3};
+    auto copy_state = [&](bool to_save) -> cudaError_t {
+        size_t off = 0;
+        for (int k = 0; k < 4; ++k) {
+            const size_t bytes = sizeof(float) * len[k] * nb;
+            cudaError_t e = to_save ? cudaMemcpyAsync(save + off, src[k], bytes, cudaMemcpyDeviceToDevice, w->stream)
+                                    : cudaMemcpyAsync(src[k], save + off, bytes, cudaMemcpyDeviceToDevice, w->stream);
+            if (e != cudaSuccess) return e;
+            off += len[k] * nb;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = copy_state(true);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const SimParams p = sim_params(w, w->cfg.dt / (float)n_substeps, n_iters);
+    if (e == cudaSuccess) e = launch_detect(p, w->stream);   // contacts of the current state
+    int bg = 0, bw = 0;
+    float best = 1e30f;
+    const int gs[4] = {1, 2, 4, 8};
+    for (int gi = 0; gi < 4 && e == cudaSuccess; ++gi)
+        for (int wp = 1; wp <= kSolveMaxWarps && e == cudaSuccess; ++wp) {
+            const SolveShape sh = solve_shape(p.n_envs, p.lam_cap, gs[gi], wp, w->max_dyn_smem, w->n_sm);
+            if (sh.groups != gs[gi] || sh.warps != wp) continue;   // does not fit: lowered to another candidate
+            e = copy_state(false);
+            if (e == cudaSuccess) e = launch_solve(p, sh, w->stream);   // warm
+            if (e == cudaSuccess) e = copy_state(false);
+            if (e == cudaSuccess) e = cudaEventRecord(a, w->stream);
+            for (int t = 0; t < trials && e == cudaSuccess; ++t) e = launch_solve(p, sh, w->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(b, w->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            ms /= (float)trials;
+            if (e == cudaSuccess && ms < best) { best = ms; bg = gs[gi]; bw = wp; }
+        }
+    if (e == cudaSuccess) e = copy_state(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(save);
+    if (e != cudaSuccess) return cuda_fail(w, e, "fw_autotune_solve");
+    if (bg > 0) {
+        if (w->solve_groups != bg || w->solve_warps != bw) drop_graph(w);
+        w->solve_groups = bg;
+        w->solve_warps = bw;
+    }
+    if (envs_per_warp) *envs_per_warp = bg;
+    if (warps_per_block) *warps_per_block = bw;
+    if (best_ms) *best_ms = best;
+    return FW_OK;
+}
+
 fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block) {
     if (!w) return FW_ERR_ARG;
     const SimParams p = sim_params(w, 1.0f, 1);

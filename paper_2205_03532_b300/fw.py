@@ -26,7 +26,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
-                 "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_get_solve_shape",
+                 "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "fw_get_timings": (st, [vp, vp, i]),
         "fw_set_solve_shape": (st, [vp, i, i]),
         "fw_get_solve_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
+        "fw_autotune_solve": (st, [vp, i, i, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_float)]),
         "fw_record_rollout": (st, [vp, i, i]),
         "fw_replay_rollout": (st, [vp]),
         "fw_adjoint_rollout": (st, [vp] + [vp] * 10 + [i]),
@@ -309,6 +310,14 @@ class World:
 
     def set_solve_shape(self, envs_per_warp: int = 0, warps_per_block: int = 0):
         self._check(self.lib.fw_set_solve_shape(self.h, envs_per_warp, warps_per_block))
+
+    def autotune_solve(self, n_substeps: int, n_iters: int, trials: int = 3):
+        """times every solve shape on the current state and keeps the fastest:
+        (envs_per_warp, warps_per_block, ms per solve launch)"""
+        g, w, ms = C.c_int(), C.c_int(), C.c_float()
+        self._check(self.lib.fw_autotune_solve(self.h, n_substeps, n_iters, trials, C.byref(g), C.byref(w),
+                                               C.byref(ms)))
+        return g.value, w.value, ms.value
 
     def solve_shape(self):
         g, w = C.c_int(), C.c_int()

@@ -672,7 +672,8 @@ def nut_bolt_assets(d: int = 16, n_samples: int = 10000, sdf_res: int = 256,
 
 def nut_bolt_scene(n_envs: int = 1000, seed: int = 0, d: int = 16, n_samples: int = 10000,
                    sdf_res: int = 256, n_substeps: int = 8, n_iters: int = 32,
-                   frames: int = 600, torque: float = 0.1, mu: float = 0.05) -> Scene:
+                   frames: int = 600, torque: float = 0.1, mu: float = 0.05,
+                   bolt_n_ang: int = 42, nut_n_ang: int = 84) -> Scene:
     """Procedural ISO M16 nut on bolt (pitch 2 mm, 60-degree thread, 0.05 mm radial
     clearance); one SDF per bolt shared by all envs; 10k samples on the nut.  The nut
     starts engaged (its lower face about two pitches below the bolt tip, about one
@@ -680,7 +681,7 @@ def nut_bolt_scene(n_envs: int = 1000, seed: int = 0, d: int = 16, n_samples: in
     psi ~U(0, 60) deg and z = kP + P psi / 2pi so that the threads mesh without
     overlap; a tightening torque (-torque about +z, right-hand thread) is applied."""
     rng = np.random.default_rng(seed)
-    nut, bolt, P, thick, L = nut_bolt_assets(d, n_samples, sdf_res, rng)
+    nut, bolt, P, thick, L = nut_bolt_assets(d, n_samples, sdf_res, rng, bolt_n_ang=bolt_n_ang, nut_n_ang=nut_n_ang)
     bodies = np.zeros((n_envs, 2), dtype=BODY_DTYPE)
     k = int(math.floor((L - 2 * P + thick / 2) / P))
     for e in range(n_envs):
@@ -691,3 +692,39 @@ def nut_bolt_scene(n_envs: int = 1000, seed: int = 0, d: int = 16, n_samples: in
         bodies[e, 1] = _body(1, STATIC, (0, 0, 0), (0, 0, 0, 1), mu)
     sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, frames=frames, max_angvel=100.0)
     return Scene("nut_bolt", [nut, bolt], [EnvGroup(bodies, np.array([[0, 1]], np.int32))], sim)
+
+
+# per size: SDF resolution (voxels on the longest axis) and samples on the nut
+MIXED_NUT_BOLT = {8: (128, 5000), 12: (176, 10000), 16: (224, 20000), 20: (256, 40000)}
+
+
+def mixed_nut_bolt_scene(n_envs: int = 4096, seed: int = 0, n_substeps: int = 8, n_iters: int = 32,
+                         frames: int = 1) -> Scene:
+    """Batched uneven environments: M8 / M12 / M16 / M20 nut-on-bolt pairs drawn uniformly
+    by seed, SDF resolutions 128^3 - 256^3 and 5k - 40k samples per nut
+    (MIXED_NUT_BOLT); angular segments of the threads scale with the diameter (multiples
+    of 6 for the hex: 24/48 for M8 ... 54/108 for M20) so the chord error stays near half
+    the clearance.  The drive torque scales with the nut's size, 0.1 N m (d/16)^3, so that
+    every size turns at a comparable rate.  Envs of one size are contiguous (one group per
+    size)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(sorted(MIXED_NUT_BOLT), n_envs)
+    assets: List[Asset] = []
+    groups: List[EnvGroup] = []
+    sim = None
+    for d in sorted(MIXED_NUT_BOLT):
+        n_d = int((sizes == d).sum())
+        if n_d == 0:
+            continue
+        res, ns = MIXED_NUT_BOLT[d]
+        sub = nut_bolt_scene(n_envs=n_d, seed=seed + d, d=d, n_samples=ns, sdf_res=res, n_substeps=n_substeps,
+                             n_iters=n_iters, frames=frames, torque=0.1 * (d / 16.0) ** 3,
+                             bolt_n_ang=6 * max(4, round(7 * d / 16)),
+                             nut_n_ang=6 * max(7, round(14 * d / 16)))
+        b = sub.groups[0].bodies.copy()
+        b["asset"] += len(assets)
+        assets += sub.assets
+        groups.append(EnvGroup(b, sub.groups[0].pairs))
+        sim = sub.sim
+    return Scene("mixed_nut_bolt", assets, groups, sim)
+

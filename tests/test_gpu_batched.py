@@ -1,0 +1,121 @@
+"""Batched uneven environments: M8 / M12 / M16 / M20 nut-bolt pairs with different SDF
+resolutions (128^3 - 256^3) and sample counts (5k - 40k) in one world, one detection
+launch over the (pair, batch) work list; and the solve-shape autotuner.
+
+* narrow phase per sample, one env of every size, against the FP64 oracle (same
+  tolerances as the single-size scenes);
+* detection of every env: contact sets agree with the oracle's in bulk (full-size pairs
+  have ~1000 near-tie decisions each, so identical sets are rare there);
+* one substep of every env on identical contacts: poses within 1e-6 m and 1e-6 rad
+  (a whole frame is not compared: a light nut under the drive torque spins up within a
+  frame, and one near-tie contact choice then changes its rotation by tenths of a
+  radian);
+* the autotuner leaves the state untouched, picks a shape that fits, and the step it
+  tunes gives the same states as that shape set by hand.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O
+from paper_2205_03532_b300 import scenes as S
+
+
+def _fw():
+    from paper_2205_03532_b300 import fw
+    return fw
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    fw = _fw()
+    sc = S.mixed_nut_bolt_scene(n_envs=12, seed=3)
+    assert len(sc.groups) == 4
+    gw = fw.world_from_scene(sc)
+    ow = O.world_from_scene(sc, lazy_bake=True)
+    return sc, gw, ow
+
+
+def _rot_angle(q1, q2):
+    d = abs(float(np.dot(q1 / np.linalg.norm(q1), q2 / np.linalg.norm(q2))))
+    return 2 * math.acos(min(1.0, d))
+
+
+def test_narrow_phase_every_size(mixed):
+    sc, gw, ow = mixed
+    env = 0
+    for g in sc.groups:
+        nut = sc.assets[int(g.bodies["asset"][0, 0])]
+        bolt_asset = int(g.bodies["asset"][0, 1])
+        ns = len(nut.samples)
+        h = float(gw.get_sdf(bolt_asset, values=False)[1])
+        phi, nrm = gw.query_pair(env, 0, ns)
+        ophi, onrm, ovalid = ow.query_pair(env, 0, ns)
+        assert np.array_equal(np.isfinite(phi), ovalid)
+        assert np.all(np.abs(phi[ovalid] - ophi[ovalid]) <= 5e-5 * h)
+        dn = np.max(np.abs(nrm[ovalid] - onrm[ovalid]), axis=1)
+        assert np.all(dn <= 1e-5 / np.minimum(1.0, ow.last_gnorm[ovalid]))
+        env += len(g.bodies)
+
+
+def test_detection_every_env_agrees_in_bulk(mixed):
+    sc, gw, ow = mixed
+    p, q, v, w = gw.get_state()
+    ow.set_state(p, q, v, w)
+    gw.collide()
+    ow.collide()
+    for env in range(sc.n_envs):
+        gc = gw.get_contacts(env)
+        oc, _, _ = ow.contacts(env)
+        assert len(oc) > 0
+        common = len(set(gc["sample"]) & set(oc["sample"]))
+        assert common >= 0.8 * max(len(gc), len(oc)), (env, common, len(gc), len(oc))
+        assert abs(len(gc) - len(oc)) <= max(3, 0.15 * len(oc)), (env, len(gc), len(oc))
+
+
+def test_one_substep_on_identical_contacts_every_env(mixed):
+    fw = _fw()
+    sc, gw, ow = mixed
+    hs = sc.sim.dt / sc.sim.n_substeps
+    p, q, v, w = gw.get_state()
+    ow.set_state(p, q, v, w)
+    ow.collide()
+    for env in range(sc.n_envs):
+        oc, _, _ = ow.contacts(env)
+        gc = np.zeros(len(oc), fw.CONTACT_DTYPE)
+        gc["sample"], gc["patch"], gc["phi"] = oc["sample"], oc["patch"], oc["phi"]
+        gc["xa"], gc["n"] = oc["xa"], oc["n"]
+        gc["xb"] = gc["xa"] - gc["phi"][:, None] * gc["n"]
+        same = oc.copy()
+        same["phi"], same["xa"], same["n"] = gc["phi"], gc["xa"], gc["n"]
+        same["xb"] = same["xa"] - same["phi"][:, None] * same["n"]
+        gw.set_contacts(env, gc)
+        ow.set_contacts(env, same)
+    gw.substep(hs, sc.sim.n_iters, detect=False)
+    ow.substep(hs, sc.sim.n_iters, detect=False)
+    gs, os_ = gw.get_state(), ow.state()
+    for i in range(0, len(gs[0]), 2):
+        assert np.linalg.norm(gs[0][i] - os_[0][i]) <= 1e-6, (i, gs[0][i], os_[0][i])
+        assert _rot_angle(gs[1][i].astype(np.float64), os_[1][i]) <= 1e-6, i
+
+
+def test_autotuner_keeps_state_and_matches_manual_shape():
+    fw = _fw()
+    sc = S.mixed_nut_bolt_scene(n_envs=40, seed=5)
+    w = fw.world_from_scene(sc)
+    x0 = [a.copy() for a in w.get_state()]
+    g, wpb, ms = w.autotune_solve(sc.sim.n_substeps, sc.sim.n_iters, trials=2)
+    assert g in (1, 2, 4, 8) and 1 <= wpb <= 4 and ms > 0
+    assert w.solve_shape() == (g, wpb)
+    for a, b in zip(w.get_state(), x0):
+        np.testing.assert_array_equal(a, b)
+    w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    tuned = w.get_state()
+    w2 = fw.world_from_scene(sc)
+    w2.set_solve_shape(g, wpb)
+    w2.step(sc.sim.n_substeps, sc.sim.n_iters)
+    for a, b in zip(tuned, w2.get_state()):
+        np.testing.assert_array_equal(a, b)
