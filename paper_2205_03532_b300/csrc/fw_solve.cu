@@ -28,8 +28,7 @@ namespace {
 
 constexpr int kMaxBodies = 8;
 constexpr int kRing = 16;     // rows in flight in the fast sweep's shared-memory ring
-constexpr int kRowF4 = 9;     // float4 per fast row
-constexpr int kRowBlock = 2;  // fast rows solved between two warp barriers
+constexpr int kRowF4 = 13;    // float4 per fast row
 
 
 
@@ -140,23 +139,33 @@ __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
     }
 }
 
-// Fast row of one contact, from the side of the movable body m (a or b of the pair):
-//   f[0] = (d_n, k_n)        f[1] = (r x d_n, bias+e_n) f[2] = (I^-1 (r x d_n), mu)
-//   f[3] = (d_1, k_t1)       f[4] = (r x d_1, e_1)      f[5] = (I^-1 (r x d_1), k_t2)
-//   f[6] = (d_2, e_2)        f[7] = (r x d_2, e_n)      f[8] = (I^-1 (r x d_2), c_n1)
-// and the row's impulse word (lambda_n, lambda_t1, lambda_t2, c_n2) in shared memory.
-// d = s n, s t1, s t2 with s = +1 when m is body a (impulses +lambda d on m either way);
-// e = -d . (v_o + w_o x r_o) is the partner's constant contribution to the row velocity;
-// c_nk = ima d_k . d_n + (r x d_k) . I^-1 (r x d_n) is the change of friction row k's
-// velocity per unit normal impulse of the same contact (an entry of J M^-1 J^T), so the
-// friction rows need not wait for the velocity update of the normal row.
+// Fast row of one contact, from the side of the movable body m (a or b of the pair).
+// For each row direction j in (n, 1, 2) = (d_n, d_1, d_2) = s (n, t1, t2), s = +1 when m
+// is body a: the Jacobian J_j = (d_j, r x d_j) acting on m's velocity u = (v, w), the
+// update vector W_j = M^-1 J_j^T = (ima d_j, I^-1 (r x d_j)) (an impulse lambda along j
+// changes u by lambda W_j), the effective mass k_j = 1 / (J_j . W_j) and the partner's
+// constant e_j = -d_j . (v_o + w_o x r_o).  Stored scaled by -k_j, so that a row's
+// "scaled velocity" S_j = -k_j (J_j . u + e_j [+ bias for n]) gives the impulse change
+// directly (lambda_n' = max(0, lambda_n + S_n)):
+//   f[0]  = (-k_n d_n,          -k_n (e_n + bias))  f[1]  = (-k_n (r x d_n), -k_n e_n)
+//   f[2]  = (-k_1 d_1,          -k_1 e_1)           f[3]  = (-k_1 (r x d_1), K_1)
+//   f[4]  = (-k_2 d_2,          -k_2 e_2)           f[5]  = (-k_2 (r x d_2), K_2)
+//   f[6]  = (W_n linear,  mu)   f[7]  = (W_n angular, C_n0)
+//   f[8]  = (W_1 linear,  C_n1) f[9]  = (W_1 angular, C_n2)
+//   f[10] = (W_2 linear,  C_10) f[11] = (W_2 angular, C_11)
+//   f[12] = (C_12, C_20, C_21, C_22)
+// K_k = -k_k J_k . W_n is the change of friction row k's scaled velocity per unit normal
+// impulse of the same contact; C_jk = -k'_j J'_j . W_k (J'_j, k'_j of the NEXT row, r+1,
+// wrapping from the last row to the first) the change of the next row's scaled velocity
+// j per unit impulse along this row's direction k -- the entries of J M^-1 J^T between
+// neighbouring rows.  They let the sweep carry the next row's three scaled velocities
+// from one row to the next with two dependent FMAs, instead of rebuilding them from the
+// updated body velocity.  A contact neither body can act on is an all-zero row.
 __device__ __forceinline__ void build_fast_row(float4 *f, float4 &lam0, const DContact &c, const BodySm &B, int a,
                                                int b, int m, float mu, float hs, float baumgarte) {
     lam0 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (m != a && m != b) {   // neither body of this pair can move: the contact does nothing
-        for (int k = 0; k < kRowF4; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
+    for (int k = 0; k < kRowF4; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m != a && m != b) return;   // neither body of this pair can move
     const bool ma = (m == a);
     const int o = ma ? b : a;
     const V3 n = ld3(c.n), xa = ld3(c.xa);
@@ -167,44 +176,71 @@ __device__ __forceinline__ void build_fast_row(float4 *f, float4 &lam0, const DC
     const float sg = ma ? 1.0f : -1.0f;
     V3 t1, t2;
     tangent_basis(n, t1, t2);
-    const V3 dn = sg * n, d1 = sg * t1, d2 = sg * t2;
+    const V3 d[3] = {sg * n, sg * t1, sg * t2};
     const V3 uo = smv(B.v, o) + cross(smv(B.w, o), ro);
     const float ima = B.invm[m];
-    const V3 rdn = cross(rm, dn), rd1 = cross(rm, d1), rd2 = cross(rm, d2);
-    const V3 idn = sym_mul(B.Iinv[m], rdn), id1 = sym_mul(B.Iinv[m], rd1), id2 = sym_mul(B.Iinv[m], rd2);
-    const float kn = eff_mass(ima, 0.0f, rdn, idn, v3(0, 0, 0), v3(0, 0, 0));
-    const float kt1 = eff_mass(ima, 0.0f, rd1, id1, v3(0, 0, 0), v3(0, 0, 0));
-    const float kt2 = eff_mass(ima, 0.0f, rd2, id2, v3(0, 0, 0), v3(0, 0, 0));
-    const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
-    if (kn == 0.0f) {   // the movable body cannot respond along n: the contact does nothing
-        for (int k = 0; k < kRowF4; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    V3 a3[3], i3[3];
+    float k[3], e[3];
+    for (int j = 0; j < 3; ++j) {
+        a3[j] = cross(rm, d[j]);
+        i3[j] = sym_mul(B.Iinv[m], a3[j]);
+        k[j] = eff_mass(ima, 0.0f, a3[j], i3[j], v3(0, 0, 0), v3(0, 0, 0));
+        e[j] = -dot(d[j], uo);
     }
-    f[0] = make_float4(dn.x, dn.y, dn.z, kn);
-    f[1] = make_float4(rdn.x, rdn.y, rdn.z, bias - dot(dn, uo));
-    f[2] = make_float4(idn.x, idn.y, idn.z, mu);
-    f[3] = make_float4(d1.x, d1.y, d1.z, kt1);
-    f[4] = make_float4(rd1.x, rd1.y, rd1.z, -dot(d1, uo));
-    f[5] = make_float4(id1.x, id1.y, id1.z, kt2);
-    f[6] = make_float4(d2.x, d2.y, d2.z, -dot(d2, uo));
-    f[7] = make_float4(rd2.x, rd2.y, rd2.z, -dot(dn, uo));
-    f[8] = make_float4(id2.x, id2.y, id2.z, ima * dot(d1, dn) + dot(rd1, idn));
-    lam0.w = ima * dot(d2, dn) + dot(rd2, idn);
+    if (k[0] == 0.0f) return;   // the movable body cannot respond along n
+    const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    const V3 wnl = ima * d[0];
+    // K_k = -k_k (ima d_k . d_n + (r x d_k) . I^-1 (r x d_n))
+    const float K1 = -k[1] * (dot(d[1], wnl) + dot(a3[1], i3[0]));
+    const float K2 = -k[2] * (dot(d[2], wnl) + dot(a3[2], i3[0]));
+    const V3 jn = -k[0] * d[0], jan = -k[0] * a3[0];
+    const V3 j1 = -k[1] * d[1], ja1 = -k[1] * a3[1];
+    const V3 j2 = -k[2] * d[2], ja2 = -k[2] * a3[2];
+    f[0] = make_float4(jn.x, jn.y, jn.z, -k[0] * (e[0] + bias));
+    f[1] = make_float4(jan.x, jan.y, jan.z, -k[0] * e[0]);
+    f[2] = make_float4(j1.x, j1.y, j1.z, -k[1] * e[1]);
+    f[3] = make_float4(ja1.x, ja1.y, ja1.z, K1);
+    f[4] = make_float4(j2.x, j2.y, j2.z, -k[2] * e[2]);
+    f[5] = make_float4(ja2.x, ja2.y, ja2.z, K2);
+    f[6] = make_float4(wnl.x, wnl.y, wnl.z, mu);
+    f[7] = make_float4(i3[0].x, i3[0].y, i3[0].z, 0.f);
+    const V3 w1l = ima * d[1], w2l = ima * d[2];
+    f[8] = make_float4(w1l.x, w1l.y, w1l.z, 0.f);
+    f[9] = make_float4(i3[1].x, i3[1].y, i3[1].z, 0.f);
+    f[10] = make_float4(w2l.x, w2l.y, w2l.z, 0.f);
+    f[11] = make_float4(i3[2].x, i3[2].y, i3[2].z, 0.f);
 }
 
-// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env),
-// kRowBlock rows at a time.  All lanes of the warp run the same number of blocks (enough
-// for the largest total of its groups; rows past a group's own total are computed and
+// C_jk of row r against its next row (see build_fast_row): scaled next-row Jacobian j
+// dotted with this row's update vector k.
+__device__ __forceinline__ void couple_fast_row(float4 *fr, const float4 *fn) {
+    const V3 J[3][2] = {{v3(fn[0].x, fn[0].y, fn[0].z), v3(fn[1].x, fn[1].y, fn[1].z)},
+                        {v3(fn[2].x, fn[2].y, fn[2].z), v3(fn[3].x, fn[3].y, fn[3].z)},
+                        {v3(fn[4].x, fn[4].y, fn[4].z), v3(fn[5].x, fn[5].y, fn[5].z)}};
+    const V3 W[3][2] = {{v3(fr[6].x, fr[6].y, fr[6].z), v3(fr[7].x, fr[7].y, fr[7].z)},
+                        {v3(fr[8].x, fr[8].y, fr[8].z), v3(fr[9].x, fr[9].y, fr[9].z)},
+                        {v3(fr[10].x, fr[10].y, fr[10].z), v3(fr[11].x, fr[11].y, fr[11].z)}};
+    float C[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int kk = 0; kk < 3; ++kk) C[j][kk] = dot(J[j][0], W[kk][0]) + dot(J[j][1], W[kk][1]);
+    fr[7].w = C[0][0]; fr[8].w = C[0][1]; fr[9].w = C[0][2];
+    fr[10].w = C[1][0]; fr[11].w = C[1][1];
+    fr[12] = make_float4(C[1][2], C[2][0], C[2][1], C[2][2]);
+}
+
+// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env), one
+// row per step.  All lanes of the warp run the same number of steps (enough for the
+// largest total of its groups; rows past a group's own total are computed and
 // discarded), so every __syncwarp is reached by the whole warp.  Lanes of a group hold
-// identical values.  Per block: wait for its rows' copy group, read the rows and their
-// impulse words into registers, let the group's lanes refill those ring slots with the
-// rows kRing positions ahead (one cp.async per float4, one commit group per block), then
-// solve the rows with no barrier in between, so the compiler can overlap one row's
-// velocity update with the next row's independent work.  Lane 0 of the group stores the
-// impulses; the next block's __syncwarp orders those stores before any later read.  An
-// impulse word read for a row that repeats inside the block (nr smaller than the block)
-// is replaced by the value just computed.  A row written all-zero (a contact neither body
-// can act on) leaves every value unchanged.
+// identical values.  A step: wait for the next row's copy group, read the next row and
+// its impulse word into registers, let the group's lanes refill that ring slot with the
+// row kRing positions ahead (one cp.async per float4, one commit group per step), then
+// solve the current row from its carried scaled velocities (S_n, S_1, S_2): only
+// S -> impulse changes -> next row's S (through C) is serial; the next row's velocities
+// at the current body velocity and the body velocity update run beside it.  Lane 0 of
+// the group stores the impulses; the next step's __syncwarp orders those stores before a
+// later read.  With a single row the next row is the current one, and its impulse word
+// is the value just computed.
 __device__ __forceinline__ void ring_read(const float4 *sp, float4 (&f)[kRowF4]) {
 #pragma unroll
     for (int k = 0; k < kRowF4; ++k) f[k] = sp[k];
@@ -218,80 +254,102 @@ __device__ __forceinline__ void ring_fill(float4 *ring, int slot, const float4 *
     }
 }
 
+struct SweepState {
+    V3 va, wa;                 // body velocity before the current row
+    float sn, s1, s2;          // current row's scaled velocities at (va, wa), incl. couplings
+    int r, pf, slot, q;
+};
+
+// scaled velocities of a row at (va, wa), without couplings
+template <bool kBias>
+__device__ __forceinline__ void row_base(const float4 (&g)[kRowF4], V3 va, V3 wa, float &bn, float &b1, float &b2) {
+    bn = __fmaf_rn(g[0].z, va.z, __fmaf_rn(g[0].y, va.y, __fmaf_rn(g[0].x, va.x, kBias ? g[0].w : g[1].w))) +
+         __fmaf_rn(g[1].z, wa.z, __fmaf_rn(g[1].y, wa.y, g[1].x * wa.x));
+    b1 = __fmaf_rn(g[2].z, va.z, __fmaf_rn(g[2].y, va.y, __fmaf_rn(g[2].x, va.x, g[2].w))) +
+         __fmaf_rn(g[3].z, wa.z, __fmaf_rn(g[3].y, wa.y, g[3].x * wa.x));
+    b2 = __fmaf_rn(g[4].z, va.z, __fmaf_rn(g[4].y, va.y, __fmaf_rn(g[4].x, va.x, g[4].w))) +
+         __fmaf_rn(g[5].z, wa.z, __fmaf_rn(g[5].y, wa.y, g[5].x * wa.x));
+}
+
+template <int G, bool kBias>
+__device__ __forceinline__ void sweep_step(const float4 (&f)[kRowF4], float4 &Lf, float4 (&g)[kRowF4], float4 &Lg,
+                                           SweepState &st, const float4 *rows, int nr, int total, float4 *ring,
+                                           float4 *lam, int gl) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+    __syncwarp();
+    ring_read(ring + kRowF4 * st.slot, g);
+    const int rn = (st.r + 1 >= nr) ? 0 : st.r + 1;
+    Lg = lam[rn];
+    __syncwarp();
+    ring_fill<G>(ring, st.slot, rows, st.pf, nr, gl);
+    cp_async_commit();
+    if (++st.pf >= nr) st.pf = 0;
+    st.slot = (st.slot + 1) & (kRing - 1);
+    // the current row, from its carried scaled velocities
+    const float4 L = Lf;
+    const float dl = fmaxf(st.sn, -L.x);                  // lambda_n' - lambda_n
+    const float ln = L.x + dl;
+    const float t1 = __fmaf_rn(f[3].w, dl, st.s1 + L.y);
+    const float t2 = __fmaf_rn(f[5].w, dl, st.s2 + L.z);
+    const float sc = fminf(1.0f, (f[6].w * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
+    const float e1 = __fmaf_rn(t1, sc, -L.y), e2 = __fmaf_rn(t2, sc, -L.z);
+    // the next row's scaled velocities: at the current body velocity, plus the couplings
+    float bn, b1, b2;
+    row_base<kBias>(g, st.va, st.wa, bn, b1, b2);
+    const float sn = __fmaf_rn(f[9].w, e2, __fmaf_rn(f[8].w, e1, __fmaf_rn(f[7].w, dl, bn)));
+    const float s1 = __fmaf_rn(f[12].x, e2, __fmaf_rn(f[11].w, e1, __fmaf_rn(f[10].w, dl, b1)));
+    const float s2 = __fmaf_rn(f[12].w, e2, __fmaf_rn(f[12].z, e1, __fmaf_rn(f[12].y, dl, b2)));
+    // the body velocity after this row
+    const bool act = st.q < total;
+    const float da = act ? dl : 0.0f, e1a = act ? e1 : 0.0f, e2a = act ? e2 : 0.0f;
+    const V3 va = st.va, wa = st.wa;
+    st.va = v3(__fmaf_rn(e2a, f[10].x, __fmaf_rn(e1a, f[8].x, __fmaf_rn(da, f[6].x, va.x))),
+               __fmaf_rn(e2a, f[10].y, __fmaf_rn(e1a, f[8].y, __fmaf_rn(da, f[6].y, va.y))),
+               __fmaf_rn(e2a, f[10].z, __fmaf_rn(e1a, f[8].z, __fmaf_rn(da, f[6].z, va.z))));
+    st.wa = v3(__fmaf_rn(e2a, f[11].x, __fmaf_rn(e1a, f[9].x, __fmaf_rn(da, f[7].x, wa.x))),
+               __fmaf_rn(e2a, f[11].y, __fmaf_rn(e1a, f[9].y, __fmaf_rn(da, f[7].y, wa.y))),
+               __fmaf_rn(e2a, f[11].z, __fmaf_rn(e1a, f[9].z, __fmaf_rn(da, f[7].z, wa.z))));
+    const float4 nl = make_float4(ln, L.y + e1, L.z + e2, 0.0f);
+    if (act && gl == 0) lam[st.r] = nl;
+    if (rn == st.r) Lg = nl;
+    st.sn = sn; st.s1 = s1; st.s2 = s2;
+    st.r = rn;
+    ++st.q;
+}
+
 template <int G, bool kBias>
 __device__ void sweep_fast(const float4 *rows, int nr, int total, int trips, float4 *ring, float4 *lam, V3 &va,
-                           V3 &wa, float ima, int gl) {
-    constexpr int RB = kRowBlock;
+                           V3 &wa, int gl) {
     if (trips == 0) return;   // warp-uniform
-    int r = 0, pf = 0;
-    for (int s = 0; s < kRing; s += RB) {
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            ring_fill<G>(ring, s + b, rows, pf, nr, gl);
-            if (++pf >= nr) pf = 0;
-        }
+    SweepState st;
+    st.va = va; st.wa = wa; st.r = 0; st.pf = 0; st.q = 0;
+    for (int s = 0; s < kRing; ++s) {
+        ring_fill<G>(ring, s, rows, st.pf, nr, gl);
         cp_async_commit();
+        if (++st.pf >= nr) st.pf = 0;
     }
-    for (int q0 = 0; q0 < trips; q0 += RB) {
-        const int slot0 = q0 & (kRing - 1);
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing / RB - 1) : "memory");
-        __syncwarp();
-        float4 f[RB][kRowF4], L[RB];
-        int rr[RB];
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            ring_read(ring + kRowF4 * (slot0 + b), f[b]);
-            rr[b] = r;
-            L[b] = lam[r];
-            if (++r >= nr) r = 0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            ring_fill<G>(ring, slot0 + b, rows, pf, nr, gl);
-            if (++pf >= nr) pf = 0;
-        }
-        cp_async_commit();
-        float4 nl[RB];
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            float4 Lb = L[b];
-#pragma unroll
-            for (int bp = 0; bp < b; ++bp)
-                if (b - bp == nr) Lb = nl[bp];   // this row already ran in the block
-            const float4 *F = f[b];
-            const float jv = __fmaf_rn(F[0].z, va.z, __fmaf_rn(F[0].y, va.y, __fmaf_rn(F[0].x, va.x, kBias ? F[1].w : F[7].w))) +
-                             __fmaf_rn(F[1].z, wa.z, __fmaf_rn(F[1].y, wa.y, F[1].x * wa.x));
-            const float j1b = __fmaf_rn(F[3].z, va.z, __fmaf_rn(F[3].y, va.y, __fmaf_rn(F[3].x, va.x, F[4].w))) +
-                              __fmaf_rn(F[4].z, wa.z, __fmaf_rn(F[4].y, wa.y, F[4].x * wa.x));
-            const float j2b = __fmaf_rn(F[6].z, va.z, __fmaf_rn(F[6].y, va.y, __fmaf_rn(F[6].x, va.x, F[6].w))) +
-                              __fmaf_rn(F[7].z, wa.z, __fmaf_rn(F[7].y, wa.y, F[7].x * wa.x));
-            // normal row
-            const float ln = fmaxf(__fmaf_rn(-F[0].w, jv, Lb.x), 0.0f);
-            float dl = ln - Lb.x;
-            // friction rows after the normal change, projected jointly on |lambda_t| <= mu lambda_n
-            const float t1 = __fmaf_rn(-F[3].w, __fmaf_rn(dl, F[8].w, j1b), Lb.y);
-            const float t2 = __fmaf_rn(-F[5].w, __fmaf_rn(dl, Lb.w, j2b), Lb.z);
-            const float sc = fminf(1.0f, (F[2].w * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
-            const float l1 = t1 * sc, l2 = t2 * sc;
-            float e1 = l1 - Lb.y, e2 = l2 - Lb.z;
-            nl[b] = make_float4(ln, l1, l2, Lb.w);
-            const bool act = q0 + b < total;
-            if (!act) { dl = 0.0f; e1 = 0.0f; e2 = 0.0f; }
-            if (act && gl == 0) lam[rr[b]] = nl[b];
-            const float dlm = dl * ima, e1m = e1 * ima, e2m = e2 * ima;
-            va = v3(__fmaf_rn(e2m, F[6].x, __fmaf_rn(e1m, F[3].x, __fmaf_rn(dlm, F[0].x, va.x))),
-                    __fmaf_rn(e2m, F[6].y, __fmaf_rn(e1m, F[3].y, __fmaf_rn(dlm, F[0].y, va.y))),
-                    __fmaf_rn(e2m, F[6].z, __fmaf_rn(e1m, F[3].z, __fmaf_rn(dlm, F[0].z, va.z))));
-            wa = v3(__fmaf_rn(e2, F[8].x, __fmaf_rn(e1, F[5].x, __fmaf_rn(dl, F[2].x, wa.x))),
-                    __fmaf_rn(e2, F[8].y, __fmaf_rn(e1, F[5].y, __fmaf_rn(dl, F[2].y, wa.y))),
-                    __fmaf_rn(e2, F[8].z, __fmaf_rn(e1, F[5].z, __fmaf_rn(dl, F[2].z, wa.z))));
-        }
+    float4 A[kRowF4], B[kRowF4], LA, LB;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+    __syncwarp();
+    ring_read(ring, A);
+    LA = lam[0];
+    __syncwarp();
+    ring_fill<G>(ring, 0, rows, st.pf, nr, gl);
+    cp_async_commit();
+    if (++st.pf >= nr) st.pf = 0;
+    st.slot = 1;
+    row_base<kBias>(A, st.va, st.wa, st.sn, st.s1, st.s2);
+    int q = 0;
+    for (; q + 1 < trips; q += 2) {   // two rows per trip, the register sets trade roles
+        sweep_step<G, kBias>(A, LA, B, LB, st, rows, nr, total, ring, lam, gl);
+        sweep_step<G, kBias>(B, LB, A, LA, st, rows, nr, total, ring, lam, gl);
     }
+    if (q < trips) sweep_step<G, kBias>(A, LA, B, LB, st, rows, nr, total, ring, lam, gl);
+    va = st.va;
+    wa = st.wa;
     cp_async_wait_all();
     __syncwarp();
 }
-
 
 template <int G>
 __device__ __forceinline__ int warp_max(int v) {
@@ -303,7 +361,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // One substep's solve for kGroups envs per warp (G = 32 / kGroups lanes each) and
 // blockDim.x / 32 warps per block.  No block-wide barrier: every warp is independent.
 template <int kGroups>
-__global__ void __launch_bounds__(kSolveMaxWarps * 32) solve_kernel(SimParams p) {
+__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams p) {
     constexpr int G = 32 / kGroups;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
@@ -392,15 +450,19 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32) solve_kernel(SimParams p)
     }
     __threadfence_block();
     __syncwarp();
+    if (fast && m >= 0) {
+        for (int r = gl; r < nr; r += G) couple_fast_row(frows + kRowF4 * r, frows + kRowF4 * (r + 1 < nr ? r + 1 : 0));
+    }
+    __threadfence_block();
+    __syncwarp();
     // 3. Gauss-Seidel sweeps (no movable body: nothing to solve)
     const bool run_fast = valid && fast && m >= 0;
     {
         const int total = run_fast ? nr * p.n_iters : 0;
         const int trips = warp_max<G>(total);
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
-        float ima = 0.0f;
-        if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); ima = B.invm[m]; }
-        sweep_fast<G, true>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, ima, gl);
+        if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
+        sweep_fast<G, true>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
     }
     if (valid && !fast && gl == 0) {
@@ -447,9 +509,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32) solve_kernel(SimParams p)
         const int total = run_fast ? nr * p.n_vel_iters : 0;
         const int trips = warp_max<G>(total);
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
-        float ima = 0.0f;
-        if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); ima = B.invm[m]; }
-        sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, ima, gl);
+        if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
+        sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
         if (valid && !fast && gl == 0) {
             for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
