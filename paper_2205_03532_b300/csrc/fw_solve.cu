@@ -7,9 +7,10 @@
 // Two sweep forms compute the same update.  Fast form (an env with at most one movable
 // body, i.e. every other body static or kinematic): each contact is written from the
 // movable body's side (directions negated when it is the pair's SDF body, the partner's
-// prescribed velocity folded into a constant), 9 float4 per contact; the body's velocity
-// stays in registers, the rows stream from global memory through a cp.async ring in
-// shared memory and the accumulated impulses live in shared memory.  General form
+// prescribed velocity folded into a constant), 15 float4 per contact; the body's velocity
+// stays in registers, split between the group's even lanes (linear part) and odd lanes
+// (angular part), the rows stream from global memory through a cp.async ring in shared
+// memory and the accumulated impulses live in shared memory.  General form
 // (several movable bodies): full two-body rows, velocities in shared memory, one lane.
 //
 // Update rule (velocity-level projected Gauss-Seidel; the paper cites the solver without
@@ -28,7 +29,8 @@ namespace {
 
 constexpr int kMaxBodies = 8;
 constexpr int kRing = 16;     // rows in flight in the fast sweep's shared-memory ring
-constexpr int kRowF4 = 13;    // float4 per fast row
+constexpr int kRowF4 = 15;    // float4 per fast row
+constexpr int kHalfF4 = 6;    // float4 of a row's linear (even lanes) or angular (odd lanes) half
 
 
 
@@ -56,6 +58,7 @@ struct EnvSm {
 // 1 mod 8 so that the envs of a warp, which read the same ring slot at the same time, start
 // in different shared-memory banks.  The slot's bodies and row offsets (EnvSm) are in a
 // static array of the kernel.
+static_assert(sizeof(Row) >= kRowF4 * sizeof(float4), "a fast row lives in a general row's storage");
 __host__ __device__ inline int env_stride_f4(int lam_cap) { return ((lam_cap + kRing * kRowF4 + 7) & ~7) + 1; }
 
 __device__ __forceinline__ V3 smv(const float (*a)[3], int i) { return v3(a[i][0], a[i][1], a[i][2]); }
@@ -147,13 +150,17 @@ __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
 // constant e_j = -d_j . (v_o + w_o x r_o).  Stored scaled by -k_j, so that a row's
 // "scaled velocity" S_j = -k_j (J_j . u + e_j [+ bias for n]) gives the impulse change
 // directly (lambda_n' = max(0, lambda_n + S_n)):
-//   f[0]  = (-k_n d_n,          -k_n (e_n + bias))  f[1]  = (-k_n (r x d_n), -k_n e_n)
-//   f[2]  = (-k_1 d_1,          -k_1 e_1)           f[3]  = (-k_1 (r x d_1), K_1)
-//   f[4]  = (-k_2 d_2,          -k_2 e_2)           f[5]  = (-k_2 (r x d_2), K_2)
-//   f[6]  = (W_n linear,  mu)   f[7]  = (W_n angular, C_n0)
-//   f[8]  = (W_1 linear,  C_n1) f[9]  = (W_1 angular, C_n2)
-//   f[10] = (W_2 linear,  C_10) f[11] = (W_2 angular, C_11)
-//   f[12] = (C_12, C_20, C_21, C_22)
+// directly (lambda_n' = max(0, lambda_n + S_n)).  Two halves of six float4, one per
+// velocity part, then three of coefficients every lane needs:
+//   linear half   f[0] = (-k_n d_n, -k_n (e_n + bias))   f[3] = (W_n linear, -k_n e_n)
+//                 f[1] = (-k_1 d_1, -k_1 e_1)            f[4] = (W_1 linear, 0)
+//                 f[2] = (-k_2 d_2, -k_2 e_2)            f[5] = (W_2 linear, 0)
+//   angular half  f[6] = (-k_n (r x d_n), 0)             f[9]  = (W_n angular, 0)
+//                 f[7] = (-k_1 (r x d_1), 0)             f[10] = (W_1 angular, 0)
+//                 f[8] = (-k_2 (r x d_2), 0)             f[11] = (W_2 angular, 0)
+//   f[12] = (K_1, K_2, mu, C_n0)  f[13] = (C_n1, C_n2, C_10, C_11)  f[14] = (C_12, C_20, C_21, C_22)
+// so that a half's j-th Jacobian part is its float4 j and its update-vector part float4 3 + j,
+// and its constant terms (zero in the angular half) sit in the .w words.
 // K_k = -k_k J_k . W_n is the change of friction row k's scaled velocity per unit normal
 // impulse of the same contact; C_jk = -k'_j J'_j . W_k (J'_j, k'_j of the NEXT row, r+1,
 // wrapping from the last row to the first) the change of the next row's scaled velocity
@@ -196,54 +203,59 @@ __device__ __forceinline__ void build_fast_row(float4 *f, float4 &lam0, const DC
     const V3 jn = -k[0] * d[0], jan = -k[0] * a3[0];
     const V3 j1 = -k[1] * d[1], ja1 = -k[1] * a3[1];
     const V3 j2 = -k[2] * d[2], ja2 = -k[2] * a3[2];
-    f[0] = make_float4(jn.x, jn.y, jn.z, -k[0] * (e[0] + bias));
-    f[1] = make_float4(jan.x, jan.y, jan.z, -k[0] * e[0]);
-    f[2] = make_float4(j1.x, j1.y, j1.z, -k[1] * e[1]);
-    f[3] = make_float4(ja1.x, ja1.y, ja1.z, K1);
-    f[4] = make_float4(j2.x, j2.y, j2.z, -k[2] * e[2]);
-    f[5] = make_float4(ja2.x, ja2.y, ja2.z, K2);
-    f[6] = make_float4(wnl.x, wnl.y, wnl.z, mu);
-    f[7] = make_float4(i3[0].x, i3[0].y, i3[0].z, 0.f);
     const V3 w1l = ima * d[1], w2l = ima * d[2];
-    f[8] = make_float4(w1l.x, w1l.y, w1l.z, 0.f);
-    f[9] = make_float4(i3[1].x, i3[1].y, i3[1].z, 0.f);
-    f[10] = make_float4(w2l.x, w2l.y, w2l.z, 0.f);
+    f[0] = make_float4(jn.x, jn.y, jn.z, -k[0] * (e[0] + bias));
+    f[1] = make_float4(j1.x, j1.y, j1.z, -k[1] * e[1]);
+    f[2] = make_float4(j2.x, j2.y, j2.z, -k[2] * e[2]);
+    f[3] = make_float4(wnl.x, wnl.y, wnl.z, -k[0] * e[0]);
+    f[4] = make_float4(w1l.x, w1l.y, w1l.z, 0.f);
+    f[5] = make_float4(w2l.x, w2l.y, w2l.z, 0.f);
+    f[6] = make_float4(jan.x, jan.y, jan.z, 0.f);
+    f[7] = make_float4(ja1.x, ja1.y, ja1.z, 0.f);
+    f[8] = make_float4(ja2.x, ja2.y, ja2.z, 0.f);
+    f[9] = make_float4(i3[0].x, i3[0].y, i3[0].z, 0.f);
+    f[10] = make_float4(i3[1].x, i3[1].y, i3[1].z, 0.f);
     f[11] = make_float4(i3[2].x, i3[2].y, i3[2].z, 0.f);
+    f[12] = make_float4(K1, K2, mu, 0.f);
 }
 
 // C_jk of row r against its next row (see build_fast_row): scaled next-row Jacobian j
 // dotted with this row's update vector k.
 __device__ __forceinline__ void couple_fast_row(float4 *fr, const float4 *fn) {
-    const V3 J[3][2] = {{v3(fn[0].x, fn[0].y, fn[0].z), v3(fn[1].x, fn[1].y, fn[1].z)},
-                        {v3(fn[2].x, fn[2].y, fn[2].z), v3(fn[3].x, fn[3].y, fn[3].z)},
-                        {v3(fn[4].x, fn[4].y, fn[4].z), v3(fn[5].x, fn[5].y, fn[5].z)}};
-    const V3 W[3][2] = {{v3(fr[6].x, fr[6].y, fr[6].z), v3(fr[7].x, fr[7].y, fr[7].z)},
-                        {v3(fr[8].x, fr[8].y, fr[8].z), v3(fr[9].x, fr[9].y, fr[9].z)},
-                        {v3(fr[10].x, fr[10].y, fr[10].z), v3(fr[11].x, fr[11].y, fr[11].z)}};
+    V3 J[3][2], W[3][2];
+    for (int j = 0; j < 3; ++j) {
+        J[j][0] = v3(fn[j].x, fn[j].y, fn[j].z);
+        J[j][1] = v3(fn[kHalfF4 + j].x, fn[kHalfF4 + j].y, fn[kHalfF4 + j].z);
+        W[j][0] = v3(fr[3 + j].x, fr[3 + j].y, fr[3 + j].z);
+        W[j][1] = v3(fr[kHalfF4 + 3 + j].x, fr[kHalfF4 + 3 + j].y, fr[kHalfF4 + 3 + j].z);
+    }
     float C[3][3];
     for (int j = 0; j < 3; ++j)
         for (int kk = 0; kk < 3; ++kk) C[j][kk] = dot(J[j][0], W[kk][0]) + dot(J[j][1], W[kk][1]);
-    fr[7].w = C[0][0]; fr[8].w = C[0][1]; fr[9].w = C[0][2];
-    fr[10].w = C[1][0]; fr[11].w = C[1][1];
-    fr[12] = make_float4(C[1][2], C[2][0], C[2][1], C[2][2]);
+    fr[12].w = C[0][0];
+    fr[13] = make_float4(C[0][1], C[0][2], C[1][0], C[1][1]);
+    fr[14] = make_float4(C[1][2], C[2][0], C[2][1], C[2][2]);
 }
 
-// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env), one
-// row per step.  All lanes of the warp run the same number of steps (enough for the
-// largest total of its groups; rows past a group's own total are computed and
-// discarded), so every __syncwarp is reached by the whole warp.  Lanes of a group hold
-// identical values.  A step: wait for the next row's copy group, read the next row and
-// its impulse word into registers, let the group's lanes refill that ring slot with the
-// row kRing positions ahead (one cp.async per float4, one commit group per step), then
-// solve the current row from its carried scaled velocities (S_n, S_1, S_2): only
-// S -> impulse changes -> next row's S (through C) is serial; the next row's velocities
-// at the current body velocity and the body velocity update run beside it.  Lane 0 of
-// the group stores the impulses; the next step's __syncwarp orders those stores before a
-// later read.  With a single row the next row is the current one, and its impulse word
-// is the value just computed.
-__device__ __forceinline__ void ring_read(const float4 *sp, float4 (&f)[kRowF4]) {
+// smallest v over the warp's groups (lanes of a group hold the same v)
+template <int G>
+__device__ __forceinline__ int warp_min(int v) {
 #pragma unroll
-    for (int k = 0; k < kRowF4; ++k) f[k] = sp[k];
+    for (int off = G; off < 32; off <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// A row as one lane holds it: its half (linear or angular) and the shared coefficients.
+struct HalfRow {
+    float4 h[kHalfF4];
+    float4 c[3];
+};
+
+__device__ __forceinline__ void ring_read(const float4 *sp, int ho, HalfRow &f) {
+#pragma unroll
+    for (int k = 0; k < kHalfF4; ++k) f.h[k] = sp[ho + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f.c[k] = sp[2 * kHalfF4 + k];
 }
 
 template <int G>
@@ -255,29 +267,44 @@ __device__ __forceinline__ void ring_fill(float4 *ring, int slot, const float4 *
 }
 
 struct SweepState {
-    V3 va, wa;                 // body velocity before the current row
-    float sn, s1, s2;          // current row's scaled velocities at (va, wa), incl. couplings
+    V3 u;                      // the lane's half of the body velocity before the current row
+    float sn, s1, s2;          // current row's scaled velocities at that velocity, incl. couplings
     int r, pf, slot, q;
 };
 
-// scaled velocities of a row at (va, wa), without couplings
+// scaled velocities of a row at the body velocity (u and its partner lane's half), without
+// couplings: each lane dots its half, the pair adds the two parts (the same sum on both)
 template <bool kBias>
-__device__ __forceinline__ void row_base(const float4 (&g)[kRowF4], V3 va, V3 wa, float &bn, float &b1, float &b2) {
-    bn = __fmaf_rn(g[0].z, va.z, __fmaf_rn(g[0].y, va.y, __fmaf_rn(g[0].x, va.x, kBias ? g[0].w : g[1].w))) +
-         __fmaf_rn(g[1].z, wa.z, __fmaf_rn(g[1].y, wa.y, g[1].x * wa.x));
-    b1 = __fmaf_rn(g[2].z, va.z, __fmaf_rn(g[2].y, va.y, __fmaf_rn(g[2].x, va.x, g[2].w))) +
-         __fmaf_rn(g[3].z, wa.z, __fmaf_rn(g[3].y, wa.y, g[3].x * wa.x));
-    b2 = __fmaf_rn(g[4].z, va.z, __fmaf_rn(g[4].y, va.y, __fmaf_rn(g[4].x, va.x, g[4].w))) +
-         __fmaf_rn(g[5].z, wa.z, __fmaf_rn(g[5].y, wa.y, g[5].x * wa.x));
+__device__ __forceinline__ void row_base(const HalfRow &g, V3 u, float &bn, float &b1, float &b2) {
+    const float pn = __fmaf_rn(g.h[0].z, u.z, __fmaf_rn(g.h[0].y, u.y, __fmaf_rn(g.h[0].x, u.x, kBias ? g.h[0].w : g.h[3].w)));
+    const float p1 = __fmaf_rn(g.h[1].z, u.z, __fmaf_rn(g.h[1].y, u.y, __fmaf_rn(g.h[1].x, u.x, g.h[1].w)));
+    const float p2 = __fmaf_rn(g.h[2].z, u.z, __fmaf_rn(g.h[2].y, u.y, __fmaf_rn(g.h[2].x, u.x, g.h[2].w)));
+    bn = pn + __shfl_xor_sync(0xffffffffu, pn, 1);
+    b1 = p1 + __shfl_xor_sync(0xffffffffu, p1, 1);
+    b2 = p2 + __shfl_xor_sync(0xffffffffu, p2, 1);
 }
 
-template <int G, bool kBias>
-__device__ __forceinline__ void sweep_step(const float4 (&f)[kRowF4], float4 &Lf, float4 (&g)[kRowF4], float4 &Lg,
-                                           SweepState &st, const float4 *rows, int nr, int total, float4 *ring,
-                                           float4 *lam, int gl) {
+// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env), one
+// row per step.  All lanes of the warp run the same number of steps (enough for the
+// largest total of its groups; rows past a group's own total are computed and
+// discarded), so every __syncwarp and shuffle is reached by the whole warp.  The even
+// lanes of a group keep the body's linear velocity, the odd lanes its angular velocity;
+// scaled velocities and impulses are identical on all of them.  A step: wait for the next
+// row's copy group, read the lane's half of the next row and its impulse word into
+// registers, let the group's lanes refill that ring slot with the row kRing positions
+// ahead (one cp.async per float4, one commit group per step), then solve the current row
+// from its carried scaled velocities (S_n, S_1, S_2): only S -> impulse changes -> next
+// row's S (through C) is serial; the next row's velocities at the current body velocity
+// and the velocity update run beside it.  Lane 0 of the group stores the impulses; the
+// next step's __syncwarp orders those stores before a later read.  With a single row the
+// next row is the current one, and its impulse word is the value just computed.
+template <int G, bool kBias, bool kMasked>
+__device__ __forceinline__ void sweep_step(const HalfRow &f, float4 &Lf, HalfRow &g, float4 &Lg, SweepState &st,
+                                           const float4 *rows, int nr, int total, bool single, int ho,
+                                           float4 *ring, float4 *lam, int gl) {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
     __syncwarp();
-    ring_read(ring + kRowF4 * st.slot, g);
+    ring_read(ring + kRowF4 * st.slot, ho, g);
     const int rn = (st.r + 1 >= nr) ? 0 : st.r + 1;
     Lg = lam[rn];
     __syncwarp();
@@ -289,29 +316,26 @@ __device__ __forceinline__ void sweep_step(const float4 (&f)[kRowF4], float4 &Lf
     const float4 L = Lf;
     const float dl = fmaxf(st.sn, -L.x);                  // lambda_n' - lambda_n
     const float ln = L.x + dl;
-    const float t1 = __fmaf_rn(f[3].w, dl, st.s1 + L.y);
-    const float t2 = __fmaf_rn(f[5].w, dl, st.s2 + L.z);
-    const float sc = fminf(1.0f, (f[6].w * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
+    const float t1 = __fmaf_rn(f.c[0].x, dl, st.s1 + L.y);
+    const float t2 = __fmaf_rn(f.c[0].y, dl, st.s2 + L.z);
+    const float sc = fminf(1.0f, (f.c[0].z * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
     const float e1 = __fmaf_rn(t1, sc, -L.y), e2 = __fmaf_rn(t2, sc, -L.z);
     // the next row's scaled velocities: at the current body velocity, plus the couplings
     float bn, b1, b2;
-    row_base<kBias>(g, st.va, st.wa, bn, b1, b2);
-    const float sn = __fmaf_rn(f[9].w, e2, __fmaf_rn(f[8].w, e1, __fmaf_rn(f[7].w, dl, bn)));
-    const float s1 = __fmaf_rn(f[12].x, e2, __fmaf_rn(f[11].w, e1, __fmaf_rn(f[10].w, dl, b1)));
-    const float s2 = __fmaf_rn(f[12].w, e2, __fmaf_rn(f[12].z, e1, __fmaf_rn(f[12].y, dl, b2)));
-    // the body velocity after this row
-    const bool act = st.q < total;
+    row_base<kBias>(g, st.u, bn, b1, b2);
+    const float sn = __fmaf_rn(f.c[1].y, e2, __fmaf_rn(f.c[1].x, e1, __fmaf_rn(f.c[0].w, dl, bn)));
+    const float s1 = __fmaf_rn(f.c[2].x, e2, __fmaf_rn(f.c[1].w, e1, __fmaf_rn(f.c[1].z, dl, b1)));
+    const float s2 = __fmaf_rn(f.c[2].w, e2, __fmaf_rn(f.c[2].z, e1, __fmaf_rn(f.c[2].y, dl, b2)));
+    // the lane's half of the body velocity after this row
+    const bool act = !kMasked || st.q < total;   // unmasked steps: every group still has rows
     const float da = act ? dl : 0.0f, e1a = act ? e1 : 0.0f, e2a = act ? e2 : 0.0f;
-    const V3 va = st.va, wa = st.wa;
-    st.va = v3(__fmaf_rn(e2a, f[10].x, __fmaf_rn(e1a, f[8].x, __fmaf_rn(da, f[6].x, va.x))),
-               __fmaf_rn(e2a, f[10].y, __fmaf_rn(e1a, f[8].y, __fmaf_rn(da, f[6].y, va.y))),
-               __fmaf_rn(e2a, f[10].z, __fmaf_rn(e1a, f[8].z, __fmaf_rn(da, f[6].z, va.z))));
-    st.wa = v3(__fmaf_rn(e2a, f[11].x, __fmaf_rn(e1a, f[9].x, __fmaf_rn(da, f[7].x, wa.x))),
-               __fmaf_rn(e2a, f[11].y, __fmaf_rn(e1a, f[9].y, __fmaf_rn(da, f[7].y, wa.y))),
-               __fmaf_rn(e2a, f[11].z, __fmaf_rn(e1a, f[9].z, __fmaf_rn(da, f[7].z, wa.z))));
+    const V3 u = st.u;
+    st.u = v3(__fmaf_rn(e2a, f.h[5].x, __fmaf_rn(e1a, f.h[4].x, __fmaf_rn(da, f.h[3].x, u.x))),
+              __fmaf_rn(e2a, f.h[5].y, __fmaf_rn(e1a, f.h[4].y, __fmaf_rn(da, f.h[3].y, u.y))),
+              __fmaf_rn(e2a, f.h[5].z, __fmaf_rn(e1a, f.h[4].z, __fmaf_rn(da, f.h[3].z, u.z))));
     const float4 nl = make_float4(ln, L.y + e1, L.z + e2, 0.0f);
     if (act && gl == 0) lam[st.r] = nl;
-    if (rn == st.r) Lg = nl;
+    if (single) Lg = nl;
     st.sn = sn; st.s1 = s1; st.s2 = s2;
     st.r = rn;
     ++st.q;
@@ -321,32 +345,45 @@ template <int G, bool kBias>
 __device__ void sweep_fast(const float4 *rows, int nr, int total, int trips, float4 *ring, float4 *lam, V3 &va,
                            V3 &wa, int gl) {
     if (trips == 0) return;   // warp-uniform
+    const bool odd = gl & 1;
+    const int ho = odd ? kHalfF4 : 0;
     SweepState st;
-    st.va = va; st.wa = wa; st.r = 0; st.pf = 0; st.q = 0;
+    st.u = odd ? wa : va; st.r = 0; st.pf = 0; st.q = 0;
     for (int s = 0; s < kRing; ++s) {
         ring_fill<G>(ring, s, rows, st.pf, nr, gl);
         cp_async_commit();
         if (++st.pf >= nr) st.pf = 0;
     }
-    float4 A[kRowF4], B[kRowF4], LA, LB;
+    HalfRow A, B;
+    float4 LA, LB;
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
     __syncwarp();
-    ring_read(ring, A);
+    ring_read(ring, ho, A);
     LA = lam[0];
     __syncwarp();
     ring_fill<G>(ring, 0, rows, st.pf, nr, gl);
     cp_async_commit();
     if (++st.pf >= nr) st.pf = 0;
     st.slot = 1;
-    row_base<kBias>(A, st.va, st.wa, st.sn, st.s1, st.s2);
+    row_base<kBias>(A, st.u, st.sn, st.s1, st.s2);
+    const bool single = nr == 1;
+    // steps every group of the warp still needs run unmasked, two per trip (the register
+    // sets trade roles); the rest, and an odd last step, masked
+    const int common = warp_min<G>(total) & ~1;
     int q = 0;
-    for (; q + 1 < trips; q += 2) {   // two rows per trip, the register sets trade roles
-        sweep_step<G, kBias>(A, LA, B, LB, st, rows, nr, total, ring, lam, gl);
-        sweep_step<G, kBias>(B, LB, A, LA, st, rows, nr, total, ring, lam, gl);
+    for (; q < common; q += 2) {
+        sweep_step<G, kBias, false>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
+        sweep_step<G, kBias, false>(B, LB, A, LA, st, rows, nr, total, single, ho, ring, lam, gl);
     }
-    if (q < trips) sweep_step<G, kBias>(A, LA, B, LB, st, rows, nr, total, ring, lam, gl);
-    va = st.va;
-    wa = st.wa;
+    for (; q + 1 < trips; q += 2) {
+        sweep_step<G, kBias, true>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
+        sweep_step<G, kBias, true>(B, LB, A, LA, st, rows, nr, total, single, ho, ring, lam, gl);
+    }
+    if (q < trips) sweep_step<G, kBias, true>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
+    const V3 other = v3(__shfl_xor_sync(0xffffffffu, st.u.x, 1), __shfl_xor_sync(0xffffffffu, st.u.y, 1),
+                        __shfl_xor_sync(0xffffffffu, st.u.z, 1));
+    va = odd ? other : st.u;
+    wa = odd ? st.u : other;
     cp_async_wait_all();
     __syncwarp();
 }
