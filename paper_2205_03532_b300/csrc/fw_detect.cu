@@ -10,10 +10,17 @@
 // reduce_kernel: one CTA of kReduceWarps warps per pair runs Algorithm 1 over the pair's
 // items in batch order.  It stages a batch's candidates in shared memory (read in place
 // from global memory when there are more than kStage), assigns them to the existing
-// patches (64-bit shared atomics pick each slot's winner), and turns the rest into new
-// patches one at a time (FindDeepest by a block-wide argmin, BinReduce, AddPatch).
-// Patches stay in shared memory for the whole pair; only the reduced contacts reach
-// global memory, plus the data of slot winners in a per-sample scratch line.
+// patches (64-bit shared atomics pick each slot's winner), ranks the rest by depth, and
+// turns them into new patches in rounds: one warp takes the kWin deepest unassigned
+// candidates and finds, with ballots, which of them FindDeepest would pick as patch seeds
+// one after another (a member is a seed unless an earlier seed's normal is similar
+// enough); then every thread runs BinReduce for all of the round's seeds at once (each
+// remaining candidate joins the first seed, in depth order, whose normal is similar), and
+// AddPatch takes the new patches in seed order.  The patches and contacts are those of
+// the one-patch-at-a-time loop: within a round no later seed can change an earlier
+// seed's members.  Patches stay in shared memory for the whole pair; only the reduced
+// contacts reach global memory, plus the data of slot winners in a per-sample scratch
+// line.
 //
 // The same reduction code, on one warp, serves fw_reduce_noalloc, and on kReduceWarps
 // warps serves fw_reduce (a caller's candidate list).
@@ -28,49 +35,49 @@ constexpr int kQueryPerThread = kBatch / kQueryThreads;   // 4 samples per threa
 constexpr int kQueryWarps = kQueryThreads / 32;
 constexpr int kReduceWarps = 4;
 constexpr int kStage = 256;              // candidates of a batch staged in shared memory
-constexpr int kMaxW = 8;                 // warps of a reduction block, at most
-constexpr unsigned long long kNoKey = ~0ull;
+constexpr int kWin = 32;                 // deepest unassigned candidates examined per round
 
 __constant__ float c_cos6[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
 __constant__ float c_sin6[6] = {0.0f, 0.8660254037844386f, 0.8660254037844386f, 0.0f,
                                 -0.8660254037844386f, -0.8660254037844386f};
 
-// Patch state of one pair in shared memory.  NP = max_patches + 1: the last patch is the
-// one being built.
+// Patch state of one pair in shared memory.  NP = max_patches + kWin: the patches kept,
+// then the kWin slots of a round's new patches.
 struct PatchSm {
     float4 *pn4;                  // NP patch normals (x, y, z, 0)
+    unsigned *kord;               // kBatch: depth keys of the unassigned candidates, then their order
     unsigned long long *keys;     // kSlots x NP
     float *pa, *pt1, *pt2;        // 3 x NP each, component-major: anchor, tangent basis
-    short *cst;                   // kBatch: -1 unassigned, -2 joining, -3 consumed, >= 0 patch
-    int *npat;
-    unsigned long long *red;      // kMaxW words for block reductions
-    float *bc;                    // 2 floats broadcast by thread 0
+    short *cst;                   // kBatch: -1 unassigned, -3 consumed, >= 0 existing patch,
+                                  // -4 - t joining the round's new patch t
+    int *npat;                    // patches kept
+    int *nun;                     // unassigned candidates of the batch
+    int *nseed;                   // new patches of the round
+    int *win;                     // kWin: the round's candidates, then its seeds
 };
 
 __host__ __device__ inline size_t patch_smem_bytes(int NP) {
-    size_t b = (size_t)NP * 16 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    size_t b = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
     b = (b + 7) & ~(size_t)7;
     b += (size_t)kBatch * 2;
-    b += 8;                                   // npat (+ pad)
-    b += (size_t)kMaxW * 8 + 8;               // red, bc
+    b += 16 + (size_t)kWin * 4;               // npat, nun, nseed (+ pad), win
     return (b + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ PatchSm carve_patch(unsigned char *base, int NP) {
     PatchSm s;
     s.pn4 = reinterpret_cast<float4 *>(base);                      // 16-byte aligned
-    s.keys = reinterpret_cast<unsigned long long *>(s.pn4 + NP);
+    s.kord = reinterpret_cast<unsigned *>(s.pn4 + NP);             // 16-byte aligned
+    s.keys = reinterpret_cast<unsigned long long *>(s.kord + kBatch);
     float *f = reinterpret_cast<float *>(s.keys + kSlots * NP);
     s.pa = f; s.pt1 = f + 3 * NP; s.pt2 = f + 6 * NP;
-    size_t off = (size_t)NP * 16 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    size_t off = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
     off = (off + 7) & ~(size_t)7;
     s.cst = reinterpret_cast<short *>(base + off);
     off += (size_t)kBatch * 2;
-    s.npat = reinterpret_cast<int *>(base + off);
-    off += 8;
-    s.red = reinterpret_cast<unsigned long long *>(base + off);
-    off += (size_t)kMaxW * 8;
-    s.bc = reinterpret_cast<float *>(base + off);
+    int *ip = reinterpret_cast<int *>(base + off);
+    s.npat = ip; s.nun = ip + 1; s.nseed = ip + 2;
+    s.win = ip + 4;
     return s;
 }
 
@@ -79,6 +86,11 @@ __device__ __forceinline__ V3 cpos(const float4 *cd, int c) { const float4 a = c
 __device__ __forceinline__ float cphi(const float4 *cd, int c) { return cd[2 * c].w; }
 __device__ __forceinline__ V3 cnrm(const float4 *cd, int c) { const float4 b = cd[2 * c + 1]; return v3(b.x, b.y, b.z); }
 __device__ __forceinline__ int cidx(const float4 *cd, int c) { return __float_as_int(cd[2 * c + 1].w); }
+
+// normal similarity n . m, rounded the same way wherever a decision compares it (and
+// symmetric: ndot(a, b) == ndot(b, a) bit for bit)
+__device__ __forceinline__ float ndot(V3 a, V3 b) { return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, a.x * b.x)); }
+__device__ __forceinline__ float ndot(V3 a, float4 b) { return ndot(a, v3(b.x, b.y, b.z)); }
 
 // Per-pair transform.
 struct PairXf {
@@ -160,13 +172,6 @@ __device__ float patch_measure(const PatchSm &S, int NP, int j, const float4 *sc
     return -phid + sqrtf(0.5f * fabsf(area2));
 }
 
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = (w < v) ? w : v;
-    }
-    return v;
-}
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
@@ -175,31 +180,137 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Block-level helpers for a reduction block of kW warps (kW = 1: the warp alone).
+// Barrier of a reduction block of kW warps (kW = 1: the warp alone).
 template <int kW>
 __device__ __forceinline__ void bsync() {
     if (kW == 1) __syncwarp();
     else __syncthreads();
 }
-template <int kW, bool kMin>
-__device__ __forceinline__ unsigned long long block_ext_u64(unsigned long long v, unsigned long long *red) {
-    v = kMin ? warp_min_u64(v) : warp_max_u64(v);
-    if (kW == 1) return v;
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) red[warp] = v;
-    __syncthreads();
-    unsigned long long m = red[0];
-#pragma unroll
-    for (int w = 1; w < kW; ++w) m = kMin ? (red[w] < m ? red[w] : m) : (red[w] > m ? red[w] : m);
-    __syncthreads();   // red is free again
-    return m;
-}
 
 template <int kW>
 __device__ __forceinline__ void init_patches(const PatchSm &S, int NP) {
     for (int i = threadIdx.x; i < kSlots * NP; i += 32 * kW) S.keys[i] = 0ull;
-    if (threadIdx.x == 0) *S.npat = 0;
+    if (threadIdx.x == 0) { *S.npat = 0; *S.nun = 0; }
     bsync<kW>();
+}
+
+// Position of unassigned candidate c in the depth order of the batch (phi ascending, ties
+// to the lower candidate): kord holds ord(phi) of the unassigned, all ones elsewhere,
+// padded with all ones to a multiple of four.
+__device__ __forceinline__ int depth_rank(const unsigned *kord, int nc, int c) {
+    const unsigned kc = kord[c];
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(kord);
+    const int n4 = (nc + 3) >> 2, c4 = c >> 2;
+    int r = 0;
+    for (int i = 0; i < c4; ++i) {   // candidates before c: equal depth counts
+        const uint4 q = k4[i];
+        r += (q.x <= kc) + (q.y <= kc) + (q.z <= kc) + (q.w <= kc);
+    }
+    {
+        const uint4 q = k4[c4];
+        const unsigned v[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = 4 * c4 + j;
+            r += (i < c) ? (v[j] <= kc) : (i > c) ? (v[j] < kc) : 0;
+        }
+    }
+    for (int i = c4 + 1; i < n4; ++i) {   // candidates after c: only strictly deeper count
+        const uint4 q = k4[i];
+        r += (q.x < kc) + (q.y < kc) + (q.z < kc) + (q.w < kc);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void copy_patch(const PatchSm &S, int NP, int from, int to) {
+    S.pn4[to] = S.pn4[from];
+    for (int k = 0; k < 3; ++k) {
+        S.pa[k * NP + to] = S.pa[k * NP + from];
+        S.pt1[k * NP + to] = S.pt1[k * NP + from];
+        S.pt2[k * NP + to] = S.pt2[k * NP + from];
+    }
+    for (int k = 0; k < kSlots; ++k) S.keys[k * NP + to] = S.keys[k * NP + from];
+}
+
+// AddPatch for the ns new patches of a round (slots T0 .. T0 + ns - 1, seed order): append
+// below capacity, else replace the most similar kept patch if the new one measures
+// higher, else drop it.  Executed by one warp.
+__device__ void add_patches(const PatchSm &S, int NP, int T0, int ns, int max_patches, const float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    int npat = *S.npat;
+    const int fit = min(ns, max(0, max_patches - npat));
+    if (lane < fit) copy_patch(S, NP, T0 + lane, npat + lane);
+    npat += fit;
+    for (int t = fit; t < ns; ++t) {
+        const int T = T0 + t;
+        const V3 nb = v3(S.pn4[T].x, S.pn4[T].y, S.pn4[T].z);
+        unsigned long long bk = 0ull;
+        for (int j = lane; j < npat; j += 32) {
+            const unsigned long long k = ((unsigned long long)ord_f32(ndot(nb, S.pn4[j])) << 32) |
+                                         (unsigned)(0xFFFFFFFFu - (unsigned)j);
+            bk = (k > bk) ? k : bk;
+        }
+        bk = warp_max_u64(bk);
+        const int ks = key_sample(bk);
+        if (lane == 0 && patch_measure(S, NP, T, scr) > patch_measure(S, NP, ks, scr)) copy_patch(S, NP, T, ks);
+        __syncwarp();
+    }
+    if (lane == 0) *S.npat = npat;
+    __syncwarp();
+}
+
+// One round's seeds, by one warp: the first kWin unassigned entries of the depth order
+// from position pos on; member i is a seed unless an earlier seed's normal is similar
+// enough (n_i . n_seed >= cos_patch), which is the order FindDeepest + BinReduce would
+// create them in.  Writes the seeds' patch frames into slots T0.. and their count to
+// *S.nseed; returns the next scan position.
+__device__ int next_seeds(const PatchSm &S, int NP, int T0, const float4 *cd, const int *order, int m, int pos,
+                          float cos_patch) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int k = 0;
+    while (k < kWin && pos < m) {
+        const int i = pos + lane;
+        const int c = i < m ? order[i] : -1;
+        const bool un = c >= 0 && S.cst[c] == -1;
+        const unsigned b = __ballot_sync(0xffffffffu, un);
+        const int nb = __popc(b), take = min(nb, kWin - k);
+        const int r = __popc(b & lt);
+        if (un && r < take) S.win[k + r] = c;
+        const unsigned last = __ballot_sync(0xffffffffu, un && r == take - 1);
+        pos = (take == nb) ? pos + 32 : pos + __ffs(last);
+        k += take;
+    }
+    __syncwarp();
+    const int c = lane < k ? S.win[lane] : -1;
+    const V3 n = c >= 0 ? cnrm(cd, c) : v3(0.0f, 0.0f, 0.0f);
+    unsigned cov = 0;   // bit j: earlier member j's normal is similar to this one's
+    for (int j = 0; j < k; ++j) {
+        const V3 nj = v3(__shfl_sync(0xffffffffu, n.x, j), __shfl_sync(0xffffffffu, n.y, j),
+                         __shfl_sync(0xffffffffu, n.z, j));
+        if (j < lane && ndot(n, nj) >= cos_patch) cov |= 1u << j;
+    }
+    unsigned rem = (k == 32) ? 0xffffffffu : ((1u << k) - 1u), seeds = 0u;
+    while (rem) {   // the deepest remaining member is the next seed; the members it covers are not
+        const int i = __ffs(rem) - 1;
+        seeds |= 1u << i;
+        rem &= ~((1u << i) | __ballot_sync(0xffffffffu, (cov >> i) & 1u));
+    }
+    __syncwarp();   // every lane has read S.win
+    if ((seeds >> lane) & 1u) {
+        const int t = __popc(seeds & lt), T = T0 + t;
+        const V3 a = cpos(cd, c);
+        V3 t1, t2;
+        tangent_basis(n, t1, t2);
+        S.win[t] = c;
+        S.pn4[T] = make_float4(n.x, n.y, n.z, 0.0f);
+        set_pvec(S.pa, NP, T, a);
+        set_pvec(S.pt1, NP, T, t1);
+        set_pvec(S.pt2, NP, T, t2);
+        for (int q = 0; q < kSlots; ++q) S.keys[q * NP + T] = 0ull;
+    }
+    if (lane == 0) *S.nseed = __popc(seeds);
+    return pos;
 }
 
 // Algorithm 1 for one batch: nc candidates in sample order at cd (shared or global
@@ -208,16 +319,17 @@ template <int kW>
 __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc, int max_patches, float cos_patch,
                              float4 *scr) {
     constexpr int NT = 32 * kW;
+    constexpr int kPer = kBatch / NT;
     const int tid = threadIdx.x;
     const int np0 = *S.npat;
+    const int T0 = NP - kWin;
     // ---- Assign: join the most similar existing patch if similar enough
     for (int c = tid; c < nc; c += NT) {
         const V3 n = cnrm(cd, c);
         int best = -1;
         float bd = -3.0f;
         for (int j = 0; j < np0; ++j) {
-            const float4 q = S.pn4[j];
-            const float d = n.x * q.x + n.y * q.y + n.z * q.z;
+            const float d = ndot(n, S.pn4[j]);
             if (d > bd) { bd = d; best = j; }
         }
         short st = -1;
@@ -229,11 +341,15 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
             const V3 pa = pvec(S.pa, NP, best), t1 = pvec(S.pt1, NP, best), t2 = pvec(S.pt2, NP, best);
             for (int s = 0; s < kSlots; ++s)
                 atomicMax(&S.keys[s * NP + best], slot_key(slot_score(s, x, a.w, pa, t1, t2), id));
+        } else {
+            atomicAdd(S.nun, 1);
         }
         S.cst[c] = st;
+        S.kord[c] = st < 0 ? ord_f32(cphi(cd, c)) : 0xFFFFFFFFu;
     }
+    if (tid < 3 && nc + tid < ((nc + 3) & ~3)) S.kord[nc + tid] = 0xFFFFFFFFu;
     bsync<kW>();
-    // slot winners of this batch publish their data
+    // slot winners of this batch publish their data; the unassigned find their depth rank
     for (int c = tid; c < nc; c += NT) {
         const int j = S.cst[c];
         if (j < 0) continue;
@@ -242,86 +358,63 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
         for (int s = 0; s < kSlots; ++s) won |= (key_sample(S.keys[s * NP + j]) == id);
         if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
     }
+    const int m = *S.nun;
+    int rk[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int c = tid + u * NT;
+        rk[u] = (c < nc && S.cst[c] == -1) ? depth_rank(S.kord, nc, c) : -1;
+    }
     bsync<kW>();
-    // ---- while candidates remain: FindDeepest, BinReduce, AddPatch
-    const int T = NP - 1;   // the patch under construction
+    int *order = reinterpret_cast<int *>(S.kord);   // the depth order replaces the keys
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+        if (rk[u] >= 0) order[rk[u]] = tid + u * NT;
+    bsync<kW>();
+    // ---- rounds of FindDeepest, BinReduce, AddPatch
+    int pos = 0, ns_prev = 0;
     for (;;) {
-        unsigned long long mk = kNoKey;
-        for (int c = tid; c < nc; c += NT)
-            if (S.cst[c] == -1) {
-                const unsigned long long k = ((unsigned long long)ord_f32(cphi(cd, c)) << 32) | (unsigned)c;
-                mk = (k < mk) ? k : mk;
-            }
-        mk = block_ext_u64<kW, true>(mk, S.red);
-        if (mk == kNoKey) break;
-        const int cb = (int)(mk & 0xFFFFFFFFull);
-        const V3 nb = cnrm(cd, cb);
-        const V3 ab = cpos(cd, cb);
-        V3 t1, t2;
-        tangent_basis(nb, t1, t2);
-        // BinReduce: the remaining candidates with a similar normal join; their slot keys
-        // go straight into patch T's keys with shared 64-bit atomics
-        if (tid < kSlots) S.keys[tid * NP + T] = 0ull;
+        if (tid < 32) {
+            add_patches(S, NP, T0, ns_prev, max_patches, scr);
+            pos = next_seeds(S, NP, T0, cd, order, m, pos, cos_patch);
+        }
         bsync<kW>();
+        const int ns = *S.nseed;
+        if (ns == 0) break;
+        // BinReduce: every unassigned candidate joins the first seed (in depth order) whose
+        // normal is similar enough; slot keys go straight into that patch's keys
         for (int c = tid; c < nc; c += NT) {
             if (S.cst[c] != -1) continue;
-            if (c == cb || dot(cnrm(cd, c), nb) >= cos_patch) {
-                S.cst[c] = -2;
-                const float4 a = cd[2 * c];
-                const int id = cidx(cd, c);
-                for (int s = 0; s < kSlots; ++s)
-                    atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, v3(a.x, a.y, a.z), a.w, ab, t1, t2), id));
+            const V3 n = cnrm(cd, c);
+            int t = -1;
+            for (int u = 0; u < ns; ++u) {
+                if (c == S.win[u] || ndot(n, S.pn4[T0 + u]) >= cos_patch) { t = u; break; }
             }
+            if (t < 0) continue;
+            S.cst[c] = (short)(-4 - t);
+            const int T = T0 + t;
+            const float4 a = cd[2 * c];
+            const int id = cidx(cd, c);
+            const V3 pa = pvec(S.pa, NP, T), t1 = pvec(S.pt1, NP, T), t2 = pvec(S.pt2, NP, T);
+            for (int s = 0; s < kSlots; ++s)
+                atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, v3(a.x, a.y, a.z), a.w, pa, t1, t2), id));
         }
         bsync<kW>();
         // the thread holding a winner publishes its data
         for (int c = tid; c < nc; c += NT) {
-            if (S.cst[c] != -2) continue;
+            const int st = S.cst[c];
+            if (st > -4) continue;
+            const int T = T0 + (-4 - st);
             const int id = cidx(cd, c);
             bool won = false;
             for (int s = 0; s < kSlots; ++s) won |= (key_sample(S.keys[s * NP + T]) == id);
             if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
             S.cst[c] = -3;   // consumed
         }
-        if (tid == 0) {
-            S.pn4[T] = make_float4(nb.x, nb.y, nb.z, 0.0f);
-            set_pvec(S.pa, NP, T, ab);
-            set_pvec(S.pt1, NP, T, t1); set_pvec(S.pt2, NP, T, t2);
-        }
         bsync<kW>();
-        // AddPatch: append below capacity, else replace the most similar patch if the new
-        // one measures higher, else drop it
-        const int npat = *S.npat;
-        int dst = -1;
-        if (npat < max_patches) {
-            dst = npat;
-        } else {
-            unsigned long long bk = 0ull;
-            for (int j = tid; j < npat; j += NT) {
-                const float4 q = S.pn4[j];
-                const unsigned long long k = ((unsigned long long)ord_f32(nb.x * q.x + nb.y * q.y + nb.z * q.z) << 32) |
-                                             (unsigned)(0xFFFFFFFFu - (unsigned)j);
-                bk = (k > bk) ? k : bk;
-            }
-            bk = block_ext_u64<kW, false>(bk, S.red);
-            const int ks = key_sample(bk);
-            if (tid == 0) {
-                S.bc[0] = patch_measure(S, NP, T, scr);
-                S.bc[1] = patch_measure(S, NP, ks, scr);
-            }
-            bsync<kW>();
-            if (S.bc[0] > S.bc[1]) dst = ks;
-        }
-        if (dst >= 0 && tid == 9) S.pn4[dst] = S.pn4[T];
-        if (dst >= 0 && tid < 9) {
-            float *arr = (tid < 3) ? S.pa : (tid < 6) ? S.pt1 : S.pt2;
-            const int comp = tid % 3;
-            arr[comp * NP + dst] = arr[comp * NP + T];
-        }
-        if (dst >= 0 && tid < kSlots) S.keys[tid * NP + dst] = S.keys[tid * NP + T];
-        if (tid == 0 && dst == npat) *S.npat = npat + 1;
-        bsync<kW>();
+        ns_prev = ns;
     }
+    if (tid == 0) *S.nun = 0;
     bsync<kW>();
 }
 
@@ -428,10 +521,10 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
 }
 
 template <int kW>
-__global__ void __launch_bounds__(32 * kW) reduce_kernel(SimParams p) {
+__global__ void __launch_bounds__(32 * kW, 8) reduce_kernel(SimParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pi = blockIdx.x;
-    const int NP = p.max_patches + 1;
+    const int NP = p.max_patches + kWin;
     const PatchSm S = carve_patch(smem_raw, NP);
     float4 *stage = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
     init_patches<kW>(S, NP);
@@ -458,7 +551,7 @@ template <int kW>
 __global__ void __launch_bounds__(32 * kW) reduce_list_kernel(SimParams p, const float *cands, int n, float4 *scr,
                                                               DContact *out, int cap, int *count, int *npatch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int NP = p.max_patches + 1;
+    const int NP = p.max_patches + kWin;
     const PatchSm S = carve_patch(smem_raw, NP);
     float4 *stage = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
     init_patches<kW>(S, NP);
@@ -534,7 +627,7 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
         if (lane == 0) { counts[0] = -1; counts[1] = 0; }
         return;
     }
-    const int NP = p.max_patches + 1;
+    const int NP = p.max_patches + kWin;
     const PatchSm S = carve_patch(smem_raw, NP);
     float4 *batch = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
     init_patches<1>(S, NP);
@@ -571,7 +664,7 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
 
 // shared memory of a reduction block that stages up to `stage` candidates
 size_t reduce_smem_bytes(int max_patches, int stage) {
-    return patch_smem_bytes(max_patches + 1) + (size_t)stage * 2 * sizeof(float4);
+    return patch_smem_bytes(max_patches + kWin) + (size_t)stage * 2 * sizeof(float4);
 }
 
 }  // namespace
@@ -615,6 +708,11 @@ cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d
 cudaError_t prepare_detect(int max_patches) {
     cudaError_t e = cudaFuncSetAttribute(reduce_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)reduce_smem_bytes(max_patches, kStage));
+    if (e != cudaSuccess) return e;
+    // one reduction block per pair, all resident at once: ask for the largest shared-memory
+    // share of the SM's on-chip memory
+    e = cudaFuncSetAttribute(reduce_kernel<kReduceWarps>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reduce_list_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)reduce_smem_bytes(max_patches, kBatch));

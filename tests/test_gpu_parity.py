@@ -259,6 +259,37 @@ def test_reduce_synthetic_batches_and_capacity(max_patches):
         pytest.skip(f"seeded input has a near-tie decision (margins {ml}, {md})")
 
 
+@pytest.mark.parametrize("max_patches", [40, 128])
+def test_reduce_many_new_patches_per_batch(max_patches):
+    """Normals spread over the whole sphere: a batch opens far more than 32 new patches,
+    with seeds and covered candidates interleaved in depth order, and with max_patches = 40
+    the capacity is reached in the middle of a batch (AddPatch replacements follow appends).
+    Seeds whose input has a near-tie decision are skipped; at least two must compare."""
+    fw = _fw()
+    checked = 0
+    for seed in range(6):
+        rng = np.random.default_rng(100 + seed)
+        n = 2500
+        samples = np.sort(rng.choice(4096, n, replace=False))
+        nn = rng.normal(size=(n, 3))
+        nn /= np.linalg.norm(nn, axis=1)[:, None]
+        c = np.zeros(n, O.CANDIDATE_DTYPE)
+        c["sample"] = samples
+        c["phi"] = rng.uniform(-3e-4, 1e-4, n)
+        c["phi"][rng.integers(0, n, 40)] = -1e-4          # equal depths: ties go to the lower sample
+        c["x"] = rng.uniform(-0.01, 0.01, (n, 3))
+        c["n"] = nn
+        w = fw.World(max_patches=max_patches)
+        oc, onp, ml, md = O.reduce(c, cos_patch=w.cfg.cos_patch, max_patches=max_patches)
+        gc, gnp = w.reduce(c)
+        w.close()
+        if ml >= MARGIN_LEN and md >= MARGIN_DOT:
+            assert gnp == onp
+            _compare_contacts(gc, oc)
+            checked += 1
+    assert checked >= 2, checked
+
+
 # ------------------------------------------------------------------------- fused collide
 @pytest.mark.parametrize("scene", ["peg", "nut"])
 def test_collide_matches_where_decisions_have_margin(scene, request):
