@@ -202,6 +202,7 @@ __device__ __forceinline__ int depth_rank(const unsigned *kord, int nc, int c) {
     const uint4 *k4 = reinterpret_cast<const uint4 *>(kord);
     const int n4 = (nc + 3) >> 2, c4 = c >> 2;
     int r = 0;
+#pragma unroll 4
     for (int i = 0; i < c4; ++i) {   // candidates before c: equal depth counts
         const uint4 q = k4[i];
         r += (q.x <= kc) + (q.y <= kc) + (q.z <= kc) + (q.w <= kc);
@@ -215,6 +216,7 @@ __device__ __forceinline__ int depth_rank(const unsigned *kord, int nc, int c) {
             r += (i < c) ? (v[j] <= kc) : (i > c) ? (v[j] < kc) : 0;
         }
     }
+#pragma unroll 4
     for (int i = c4 + 1; i < n4; ++i) {   // candidates after c: only strictly deeper count
         const uint4 q = k4[i];
         r += (q.x < kc) + (q.y < kc) + (q.z < kc) + (q.w < kc);
@@ -285,6 +287,7 @@ __device__ int next_seeds(const PatchSm &S, int NP, int T0, const float4 *cd, co
     const int c = lane < k ? S.win[lane] : -1;
     const V3 n = c >= 0 ? cnrm(cd, c) : v3(0.0f, 0.0f, 0.0f);
     unsigned cov = 0;   // bit j: earlier member j's normal is similar to this one's
+#pragma unroll 8
     for (int j = 0; j < k; ++j) {
         const V3 nj = v3(__shfl_sync(0xffffffffu, n.x, j), __shfl_sync(0xffffffffu, n.y, j),
                          __shfl_sync(0xffffffffu, n.z, j));
@@ -328,6 +331,7 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
         const V3 n = cnrm(cd, c);
         int best = -1;
         float bd = -3.0f;
+#pragma unroll 4
         for (int j = 0; j < np0; ++j) {
             const float d = ndot(n, S.pn4[j]);
             if (d > bd) { bd = d; best = j; }
@@ -386,11 +390,12 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
         for (int c = tid; c < nc; c += NT) {
             if (S.cst[c] != -1) continue;
             const V3 n = cnrm(cd, c);
-            int t = -1;
-            for (int u = 0; u < ns; ++u) {
-                if (c == S.win[u] || ndot(n, S.pn4[T0 + u]) >= cos_patch) { t = u; break; }
-            }
-            if (t < 0) continue;
+            unsigned hit = 0u;   // seeds whose patch c may join
+#pragma unroll 4
+            for (int u = 0; u < ns; ++u)
+                hit |= (unsigned)(c == S.win[u] || ndot(n, S.pn4[T0 + u]) >= cos_patch) << u;
+            if (hit == 0u) continue;
+            const int t = __ffs(hit) - 1;
             S.cst[c] = (short)(-4 - t);
             const int T = T0 + t;
             const float4 a = cd[2 * c];
@@ -419,25 +424,55 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
 }
 
 // Writes the reduced contacts of the pair: patches in order, distinct slot members in
-// slot order.  Executed by one warp.
+// slot order.  Executed by all 32 * kW threads, one patch per thread: each finds its
+// patch's distinct members, a block-wide prefix sum over the patches places them.
+template <int kW>
 __device__ void emit_contacts(const PatchSm &S, int NP, const float4 *scr, DContact *out, int cap, int *count,
                               unsigned *status) {
-    const int lane = threadIdx.x & 31;
+    constexpr int NT = 32 * kW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int npat = *S.npat;
-    int n = 0;
-    for (int j = 0; j < npat; ++j) {
-        int id = -1;
-        if (lane < kSlots) id = key_sample(S.keys[lane * NP + j]);
-        bool dup = false;
-        for (int s = 0; s < kSlots; ++s) {
-            const int o = __shfl_sync(0xffffffffu, id, s);
-            if (s < lane && o == id) dup = true;
+    int base = 0;   // contacts of the patches before this chunk
+    for (int j0 = 0; j0 < npat; j0 += NT) {
+        const int j = j0 + tid;
+        int ids[kSlots];
+        unsigned dm = 0u;   // slots holding a member not held by an earlier slot
+        if (j < npat) {
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                ids[q] = key_sample(S.keys[q * NP + j]);
+                bool dup = false;
+#pragma unroll
+                for (int t = 0; t < q; ++t) dup |= (ids[t] == ids[q]);
+                if (!dup) dm |= 1u << q;
+            }
         }
-        const bool emit = (lane < kSlots) && !dup;
-        const unsigned m = __ballot_sync(0xffffffffu, emit);
-        if (emit) {
-            const int k = n + __popc(m & ((1u << lane) - 1u));
+        const int d = __popc(dm);
+        int incl = d;   // inclusive prefix sum over the block's patches
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int before = 0, total = 0;
+        if (kW > 1) {
+            if (lane == 31) S.win[warp] = incl;
+            bsync<kW>();
+            for (int w = 0; w < kW; ++w) {
+                const int v = S.win[w];
+                before += (w < warp) ? v : 0;
+                total += v;
+            }
+            bsync<kW>();
+        } else {
+            total = __shfl_sync(0xffffffffu, incl, 31);
+        }
+        int k = base + before + incl - d;
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            if (!((dm >> q) & 1u)) continue;
             if (k < cap) {
+                const int id = ids[q];
                 const float4 a = scr[2 * id], b = scr[2 * id + 1];
                 DContact c;
                 c.xa[0] = a.x; c.xa[1] = a.y; c.xa[2] = a.z; c.phi = a.w;
@@ -445,12 +480,13 @@ __device__ void emit_contacts(const PatchSm &S, int NP, const float4 *scr, DCont
                 c.sample_patch = id | (j << 24);
                 out[k] = c;
             }
+            ++k;
         }
-        n += __popc(m);
+        base += total;
     }
-    if (lane == 0) {
-        if (n > cap) atomicOr(status, kStatusOverflow);
-        *count = n < cap ? n : cap;
+    if (tid == 0) {
+        if (base > cap) atomicOr(status, kStatusOverflow);
+        *count = base < cap ? base : cap;
     }
 }
 
@@ -541,8 +577,7 @@ __global__ void __launch_bounds__(32 * kW, 8) reduce_kernel(SimParams p) {
         }
         reduce_batch<kW>(S, NP, cd, nc, p.max_patches, p.cos_patch, scr);
     }
-    if (threadIdx.x < 32)
-        emit_contacts(S, NP, scr, p.contacts + (long long)pi * p.cap_pair, p.cap_pair, p.counts + pi, p.status);
+    emit_contacts<kW>(S, NP, scr, p.contacts + (long long)pi * p.cap_pair, p.cap_pair, p.counts + pi, p.status);
 }
 
 // Algorithm 1 on a candidate list in global memory (fw_candidate layout, sorted by
@@ -565,7 +600,7 @@ __global__ void __launch_bounds__(32 * kW) reduce_list_kernel(SimParams p, const
         reduce_batch<kW>(S, NP, stage, end - start, p.max_patches, p.cos_patch, scr);
         start = end;
     }
-    if (threadIdx.x < 32) emit_contacts(S, NP, scr, out, cap, count, p.status);
+    emit_contacts<kW>(S, NP, scr, out, cap, count, p.status);
     if (threadIdx.x == 0) *npatch = *S.npat;
 }
 
@@ -642,7 +677,7 @@ __global__ void __launch_bounds__(32) reduce_noalloc_kernel(SimParams p, const f
         reduce_batch<1>(S, NP, batch, end - start, p.max_patches, p.cos_patch, scr);
         start = end;
     }
-    emit_contacts(S, NP, scr, stage, p.max_patches * kSlots, stage_count, p.status);
+    emit_contacts<1>(S, NP, scr, stage, p.max_patches * kSlots, stage_count, p.status);
     __syncwarp();
     const int k = *stage_count;
     for (int i = lane; i < k && i < cap; i += 32) {
