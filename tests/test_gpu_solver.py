@@ -45,13 +45,15 @@ def _pair_worlds(descs, assets, pairs, **cfg):
     return gw, ow
 
 
-def _solve_same_contacts(gw, ow, hs, n_iters):
+def _solve_same_contacts(gw, ow, hs, n_iters, keep=None):
     fw = _fw()
     p, q, v, w = gw.get_state()
     ow.set_state(p, q, v, w)
     ow.collide()
     oc, _, _ = ow.contacts(0)
     assert len(oc) > 0
+    if keep is not None:      # the deepest `keep` contacts only
+        oc = oc[np.argsort(oc["phi"], kind="stable")[:keep]]
     gc = np.zeros(len(oc), fw.CONTACT_DTYPE)
     gc["sample"], gc["patch"], gc["phi"] = oc["sample"], oc["patch"], oc["phi"]
     gc["xa"], gc["n"] = oc["xa"], oc["n"]
@@ -109,6 +111,19 @@ def test_fast_path_kinematic_partner_velocity_enters_the_rows():
     v = gw.get_state()[2]
     assert v[0, 0] > 1e-3          # dragged along by friction
     np.testing.assert_allclose(v[1], [0.2, 0, 0], atol=0)
+
+
+@pytest.mark.parametrize("keep", [1, 2, 3])
+def test_fast_path_with_one_two_three_contacts(keep):
+    """Fewest rows: one contact (the fast sweep pads it with an all-zero row), two (each
+    row's neighbour is the other), three.  A tilted cube pressed onto a kinematic slab."""
+    V, T, Sp = _cube()
+    GV, GT = S.box_mesh(0.1, 0.1, 0.01)
+    tilt = S.quat_mul(S.quat_axis_angle([1, 0, 0], 0.15), S.quat_axis_angle([0, 1, 0], 0.1))
+    descs = [S._body(0, S.DYNAMIC, (0, 0, 0.0117), tilt, 0.5, 0.0, (0.05, 0.02, -0.2), (0.3, -0.2, 0.4)),
+             S._body(1, S.KINEMATIC, (0, 0, -0.01), (0, 0, 0, 1), 0.5, 0.0, (0.1, 0, 0), (0, 0, 0.3))]
+    gw, ow = _pair_worlds(descs, [(V, T, Sp, None, 0), (GV, GT, None, 64, 2e-3)], [(0, 1)])
+    assert _solve_same_contacts(gw, ow, 1 / 240, 16, keep=keep) == keep
 
 
 def test_free_fall_on_gpu_matches_closed_form():
