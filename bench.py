@@ -46,7 +46,7 @@ def _src_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_03532_b300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) or f == "build.py":   # sources and their flags
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -349,6 +349,11 @@ __device__ void sweep_fast(const float4 *rows, int nr, int total, int trips, flo
     const int ho = odd ? kHalfF4 : 0;
     SweepState st;
     st.u = odd ? wa : va; st.r = 0; st.pf = 0; st.q = 0;
+    // A group without rows runs only discarded steps, which scale its ring words by zero:
+    // make them zeros (shared memory may hold any bits, NaN patterns included).
+    if (nr == 0) {
+        for (int k = gl; k < kRing * kRowF4; k += G) ring[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (int s = 0; s < kRing; ++s) {
         ring_fill<G>(ring, s, rows, st.pf, nr, gl);
         cp_async_commit();

@@ -126,6 +126,35 @@ def test_fast_path_with_one_two_three_contacts(keep):
     assert _solve_same_contacts(gw, ow, 1 / 240, 16, keep=keep) == keep
 
 
+def test_envs_without_contacts_beside_envs_in_contact():
+    """Envs with no contact share warps with envs in contact (every solve shape); the
+    solve's masked steps for them must leave their free flight exact, frame after frame,
+    whatever the shared memory held before (the reduction kernel leaves all-ones words)."""
+    fw = _fw()
+    sc = S.peg_in_hole_scene(n_envs=64, seed=11)
+    b = sc.groups[0].bodies
+    b["pos"][:, 0, 2] = 12.5e-3 - 1e-3              # partly inserted: in contact
+    b["pos"][1::2, 0, 2] = 1.0                        # far above the box: free flight
+    b["linvel"][1::2, 0] = [0.01, -0.02, 0.3]
+    b["angvel"][1::2, 0] = [0.5, -1.0, 2.0]
+    hs = np.float32(np.float32(sc.sim.dt) / sc.sim.n_substeps)
+    for shape in [(1, 1), (2, 1), (4, 2), (8, 4)]:
+        w = fw.world_from_scene(sc)
+        w.set_solve_shape(*shape)
+        v0 = w.get_state()[2].copy()
+        K = 3 * sc.sim.n_substeps
+        for _ in range(3):
+            w.step(sc.sim.n_substeps, sc.sim.n_iters)
+        p, q, v, om = w.get_state()
+        assert np.all(np.isfinite(p)) and np.all(np.isfinite(q)), shape
+        free = np.arange(2, len(p), 4)                # the pegs of the odd envs
+        g = np.float32(9.81)
+        assert np.allclose(v[free, 2], v0[free, 2] - g * hs * K, atol=1e-5), shape
+        assert np.array_equal(v[free, :2], v0[free, :2]), shape
+        assert np.all(np.isfinite(om)), shape
+        w.close()
+
+
 def test_free_fall_on_gpu_matches_closed_form():
     fw = _fw()
     V, T, Sp = _cube()
