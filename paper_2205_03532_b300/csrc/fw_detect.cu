@@ -42,14 +42,18 @@ __constant__ float c_sin6[6] = {0.0f, 0.8660254037844386f, 0.8660254037844386f, 
                                 -0.8660254037844386f, -0.8660254037844386f};
 
 // Patch state of one pair in shared memory.  NP = max_patches + kWin: the patches kept,
-// then the kWin slots of a round's new patches.
+// then the kWin slots of a round's new patches.  Of a patch's tangent basis only t1 is
+// stored; t2 = n x t1 is formed again where needed (patch_t2, explicitly rounded, so it is
+// the same vector at every use).
 struct PatchSm {
     float4 *pn4;                  // NP patch normals (x, y, z, 0)
-    unsigned *kord;               // kBatch: depth keys of the unassigned candidates, then their order
+    unsigned *kord;               // kBatch: depth keys ord(phi) of the unassigned candidates
+                                  // (in cl's order), then the depth order itself
     unsigned long long *keys;     // kSlots x NP
-    float *pa, *pt1, *pt2;        // 3 x NP each, component-major: anchor, tangent basis
+    float *pa, *pt1;              // 3 x NP each, component-major: anchor, tangent t1
     short *cst;                   // kBatch: -1 unassigned, -3 consumed, >= 0 existing patch,
                                   // -4 - t joining the round's new patch t
+    short *cl;                    // kBatch: the unassigned candidates of the batch
     int *npat;                    // patches kept
     int *nun;                     // unassigned candidates of the batch
     int *nseed;                   // new patches of the round
@@ -57,9 +61,9 @@ struct PatchSm {
 };
 
 __host__ __device__ inline size_t patch_smem_bytes(int NP) {
-    size_t b = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    size_t b = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)6 * NP * 4;
     b = (b + 7) & ~(size_t)7;
-    b += (size_t)kBatch * 2;
+    b += (size_t)kBatch * 4;                  // cst, cl
     b += 16 + (size_t)kWin * 4;               // npat, nun, nseed (+ pad), win
     return (b + 15) & ~(size_t)15;
 }
@@ -69,12 +73,13 @@ __device__ __forceinline__ PatchSm carve_patch(unsigned char *base, int NP) {
     s.pn4 = reinterpret_cast<float4 *>(base);                      // 16-byte aligned
     s.kord = reinterpret_cast<unsigned *>(s.pn4 + NP);             // 16-byte aligned
     s.keys = reinterpret_cast<unsigned long long *>(s.kord + kBatch);
-    float *f = reinterpret_cast<float *>(s.keys + kSlots * NP);
-    s.pa = f; s.pt1 = f + 3 * NP; s.pt2 = f + 6 * NP;
-    size_t off = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)9 * NP * 4;
+    s.pa = reinterpret_cast<float *>(s.keys + kSlots * NP);
+    s.pt1 = s.pa + 3 * NP;
+    size_t off = (size_t)NP * 16 + (size_t)kBatch * 4 + (size_t)kSlots * NP * 8 + (size_t)6 * NP * 4;
     off = (off + 7) & ~(size_t)7;
     s.cst = reinterpret_cast<short *>(base + off);
-    off += (size_t)kBatch * 2;
+    s.cl = s.cst + kBatch;
+    off += (size_t)kBatch * 4;
     int *ip = reinterpret_cast<int *>(base + off);
     s.npat = ip; s.nun = ip + 1; s.nseed = ip + 2;
     s.win = ip + 4;
@@ -91,6 +96,12 @@ __device__ __forceinline__ int cidx(const float4 *cd, int c) { return __float_as
 // symmetric: ndot(a, b) == ndot(b, a) bit for bit)
 __device__ __forceinline__ float ndot(V3 a, V3 b) { return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, a.x * b.x)); }
 __device__ __forceinline__ float ndot(V3 a, float4 b) { return ndot(a, v3(b.x, b.y, b.z)); }
+
+// second tangent of a patch: n x t1, each component rounded in one fixed way
+__device__ __forceinline__ V3 patch_t2(V3 n, V3 t1) {
+    return v3(__fmaf_rn(n.y, t1.z, -__fmul_rn(n.z, t1.y)), __fmaf_rn(n.z, t1.x, -__fmul_rn(n.x, t1.z)),
+              __fmaf_rn(n.x, t1.y, -__fmul_rn(n.y, t1.x)));
+}
 
 // Per-pair transform.
 struct PairXf {
@@ -150,7 +161,8 @@ __device__ __forceinline__ void scratch_put(float4 *scr, int sample, V3 x, float
 __device__ float patch_measure(const PatchSm &S, int NP, int j, const float4 *scr) {
     const int deep = key_sample(S.keys[j]);
     const float phid = scr[2 * deep].w;
-    const V3 a = pvec(S.pa, NP, j), t1 = pvec(S.pt1, NP, j), t2 = pvec(S.pt2, NP, j);
+    const V3 a = pvec(S.pa, NP, j), t1 = pvec(S.pt1, NP, j);
+    const V3 t2 = patch_t2(v3(S.pn4[j].x, S.pn4[j].y, S.pn4[j].z), t1);
     float xs[6], ys[6];
     int seen[6], n = 0;
     for (int s = 1; s < kSlots; ++s) {
@@ -194,34 +206,28 @@ __device__ __forceinline__ void init_patches(const PatchSm &S, int NP) {
     bsync<kW>();
 }
 
-// Position of unassigned candidate c in the depth order of the batch (phi ascending, ties
-// to the lower candidate): kord holds ord(phi) of the unassigned, all ones elsewhere,
-// padded with all ones to a multiple of four.
-__device__ __forceinline__ int depth_rank(const unsigned *kord, int nc, int c) {
-    const unsigned kc = kord[c];
+// Position of the i-th unassigned candidate in the depth order of the batch (phi
+// ascending, ties to the lower candidate): kord[0..m) holds ord(phi) of the m unassigned
+// candidates, cl[0..m) the candidates themselves, in no particular order.
+__device__ __forceinline__ int depth_rank(const unsigned *kord, const short *cl, int m, int i) {
+    const unsigned ki = kord[i];
     const uint4 *k4 = reinterpret_cast<const uint4 *>(kord);
-    const int n4 = (nc + 3) >> 2, c4 = c >> 2;
-    int r = 0;
+    int lt = 0, eq = 0;
 #pragma unroll 4
-    for (int i = 0; i < c4; ++i) {   // candidates before c: equal depth counts
-        const uint4 q = k4[i];
-        r += (q.x <= kc) + (q.y <= kc) + (q.z <= kc) + (q.w <= kc);
+    for (int j = 0; j < (m >> 2); ++j) {
+        const uint4 q = k4[j];
+        lt += (q.x < ki) + (q.y < ki) + (q.z < ki) + (q.w < ki);
+        eq += (q.x == ki) + (q.y == ki) + (q.z == ki) + (q.w == ki);
     }
-    {
-        const uint4 q = k4[c4];
-        const unsigned v[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = 4 * c4 + j;
-            r += (i < c) ? (v[j] <= kc) : (i > c) ? (v[j] < kc) : 0;
-        }
+    for (int j = m & ~3; j < m; ++j) {
+        lt += kord[j] < ki;
+        eq += kord[j] == ki;
     }
-#pragma unroll 4
-    for (int i = c4 + 1; i < n4; ++i) {   // candidates after c: only strictly deeper count
-        const uint4 q = k4[i];
-        r += (q.x < kc) + (q.y < kc) + (q.z < kc) + (q.w < kc);
+    if (eq > 1) {   // equal depths (rare): the lower candidate comes first
+        const int ci = cl[i];
+        for (int j = 0; j < m; ++j) lt += (kord[j] == ki) && (cl[j] < ci);
     }
-    return r;
+    return lt;
 }
 
 __device__ __forceinline__ void copy_patch(const PatchSm &S, int NP, int from, int to) {
@@ -229,7 +235,6 @@ __device__ __forceinline__ void copy_patch(const PatchSm &S, int NP, int from, i
     for (int k = 0; k < 3; ++k) {
         S.pa[k * NP + to] = S.pa[k * NP + from];
         S.pt1[k * NP + to] = S.pt1[k * NP + from];
-        S.pt2[k * NP + to] = S.pt2[k * NP + from];
     }
     for (int k = 0; k < kSlots; ++k) S.keys[k * NP + to] = S.keys[k * NP + from];
 }
@@ -302,14 +307,12 @@ __device__ int next_seeds(const PatchSm &S, int NP, int T0, const float4 *cd, co
     __syncwarp();   // every lane has read S.win
     if ((seeds >> lane) & 1u) {
         const int t = __popc(seeds & lt), T = T0 + t;
-        const V3 a = cpos(cd, c);
         V3 t1, t2;
         tangent_basis(n, t1, t2);
         S.win[t] = c;
         S.pn4[T] = make_float4(n.x, n.y, n.z, 0.0f);
-        set_pvec(S.pa, NP, T, a);
+        set_pvec(S.pa, NP, T, cpos(cd, c));
         set_pvec(S.pt1, NP, T, t1);
-        set_pvec(S.pt2, NP, T, t2);
         for (int q = 0; q < kSlots; ++q) S.keys[q * NP + T] = 0ull;
     }
     if (lane == 0) *S.nseed = __popc(seeds);
@@ -327,31 +330,43 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
     const int np0 = *S.npat;
     const int T0 = NP - kWin;
     // ---- Assign: join the most similar existing patch if similar enough
-    for (int c = tid; c < nc; c += NT) {
-        const V3 n = cnrm(cd, c);
+    const int lane = tid & 31;
+    for (int c0 = 0; c0 < nc; c0 += NT) {   // same trip count on every lane (ballot below)
+        const int c = c0 + tid;
         int best = -1;
         float bd = -3.0f;
+        if (c < nc) {
+            const V3 n = cnrm(cd, c);
 #pragma unroll 4
-        for (int j = 0; j < np0; ++j) {
-            const float d = ndot(n, S.pn4[j]);
-            if (d > bd) { bd = d; best = j; }
+            for (int j = 0; j < np0; ++j) {
+                const float d = ndot(n, S.pn4[j]);
+                if (d > bd) { bd = d; best = j; }
+            }
         }
+        // the warp's unassigned candidates take consecutive list entries
+        const bool un = c < nc && !(best >= 0 && bd >= cos_patch);
+        const unsigned um = __ballot_sync(0xffffffffu, un);
+        int i0 = 0;
+        if (lane == 0 && um) i0 = atomicAdd(S.nun, __popc(um));
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if (c >= nc) continue;
         short st = -1;
-        if (best >= 0 && bd >= cos_patch) {
+        if (!un) {
             st = (short)best;
             const float4 a = cd[2 * c];
             const V3 x = v3(a.x, a.y, a.z);
             const int id = cidx(cd, c);
-            const V3 pa = pvec(S.pa, NP, best), t1 = pvec(S.pt1, NP, best), t2 = pvec(S.pt2, NP, best);
+            const V3 pa = pvec(S.pa, NP, best), t1 = pvec(S.pt1, NP, best);
+            const V3 t2 = patch_t2(v3(S.pn4[best].x, S.pn4[best].y, S.pn4[best].z), t1);
             for (int s = 0; s < kSlots; ++s)
                 atomicMax(&S.keys[s * NP + best], slot_key(slot_score(s, x, a.w, pa, t1, t2), id));
         } else {
-            atomicAdd(S.nun, 1);
+            const int i = i0 + __popc(um & ((1u << lane) - 1u));
+            S.kord[i] = ord_f32(cphi(cd, c));
+            S.cl[i] = (short)c;
         }
         S.cst[c] = st;
-        S.kord[c] = st < 0 ? ord_f32(cphi(cd, c)) : 0xFFFFFFFFu;
     }
-    if (tid < 3 && nc + tid < ((nc + 3) & ~3)) S.kord[nc + tid] = 0xFFFFFFFFu;
     bsync<kW>();
     // slot winners of this batch publish their data; the unassigned find their depth rank
     for (int c = tid; c < nc; c += NT) {
@@ -363,17 +378,18 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
         if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
     }
     const int m = *S.nun;
-    int rk[kPer];
+    int rk[kPer], rc[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-        const int c = tid + u * NT;
-        rk[u] = (c < nc && S.cst[c] == -1) ? depth_rank(S.kord, nc, c) : -1;
+        const int i = tid + u * NT;
+        rk[u] = i < m ? depth_rank(S.kord, S.cl, m, i) : -1;
+        rc[u] = i < m ? S.cl[i] : 0;
     }
     bsync<kW>();
     int *order = reinterpret_cast<int *>(S.kord);   // the depth order replaces the keys
 #pragma unroll
     for (int u = 0; u < kPer; ++u)
-        if (rk[u] >= 0) order[rk[u]] = tid + u * NT;
+        if (rk[u] >= 0) order[rk[u]] = rc[u];
     bsync<kW>();
     // ---- rounds of FindDeepest, BinReduce, AddPatch
     int pos = 0, ns_prev = 0;
@@ -400,7 +416,8 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
             const int T = T0 + t;
             const float4 a = cd[2 * c];
             const int id = cidx(cd, c);
-            const V3 pa = pvec(S.pa, NP, T), t1 = pvec(S.pt1, NP, T), t2 = pvec(S.pt2, NP, T);
+            const V3 pa = pvec(S.pa, NP, T), t1 = pvec(S.pt1, NP, T);
+            const V3 t2 = patch_t2(v3(S.pn4[T].x, S.pn4[T].y, S.pn4[T].z), t1);
             for (int s = 0; s < kSlots; ++s)
                 atomicMax(&S.keys[s * NP + T], slot_key(slot_score(s, v3(a.x, a.y, a.z), a.w, pa, t1, t2), id));
         }
