@@ -124,7 +124,7 @@ __device__ __forceinline__ bool query_sample(const PairXf &X, const AssetDev &gb
     V3 g;
     const bool in = sdf_lookup_any(gb, xb, phi, g);
     const float gg = dot(g, g);
-    const V3 nb = (1.0f / sqrtf(fmaxf(gg, 1e-30f))) * g;
+    const V3 nb = rsqrtf(fmaxf(gg, 1e-30f)) * g;   // unit to a few ulp; the decisions on it have margins
     nw = mul(X.RB, nb);
     return in && (gg >= 1e-24f);
 }
