@@ -67,6 +67,7 @@ typedef struct {
     float contact_offset;       /* candidate iff phi < contact_offset; default 1e-4 m */
     float cos_patch;            /* normal similarity for Assign/BinReduce; default 0.94 */
     int max_patches;            /* N of Sec. III-C (128 <= N <= 256); default 128 */
+    int patch_dirs;             /* direction slots per patch (beside the deepest); must be 6 */
     int batch_size;             /* samples per Generate batch; must be 1024 (Sec. III-C) */
     float baumgarte;            /* bias factor for penetrating contacts; default 0.2 */
     int n_vel_iters;            /* bias-free sweeps after integration; default 0 */
@@ -116,7 +117,8 @@ typedef struct {
 FW_API void fw_config_default(fw_config *cfg);
 
 /* Creates a world on cfg->device.  *out receives the handle (NULL on failure).
- * Errors: FW_ERR_ARG for batch_size != 1024, max_patches outside 1..256, dt <= 0. */
+ * Errors: FW_ERR_ARG for batch_size != 1024, patch_dirs != 6, max_patches outside 1..256,
+ * dt <= 0. */
 FW_API fw_status fw_create(const fw_config *cfg, fw_world **out);
 
 /* Frees every device and host resource of the world.  NULL is accepted. */
@@ -301,6 +303,14 @@ FW_API fw_status fw_replay_rollout(fw_world *w);
 FW_API fw_status fw_adjoint_rollout(fw_world *w, const float *g_pos, const float *g_quat, const float *g_linvel,
                                    const float *g_angvel, float *d_pos, float *d_quat, float *d_linvel,
                                    float *d_angvel, float *d_mass, float *d_mu, int device_ptrs);
+/* The same two operations under the names of the frame-step interface:
+ * fw_step_fwd_ckpt(w, n_substeps, n_iters) is fw_record_rollout: one frame forward with
+ * its tape and per-substep checkpoints; fw_step_bwd(w, ...) is fw_adjoint_rollout of the
+ * frame last recorded (or replayed).  Arguments, ownership and errors as there. */
+FW_API fw_status fw_step_fwd_ckpt(fw_world *w, int n_substeps, int n_iters);
+FW_API fw_status fw_step_bwd(fw_world *w, const float *g_pos, const float *g_quat, const float *g_linvel,
+                             const float *g_angvel, float *d_pos, float *d_quat, float *d_linvel, float *d_angvel,
+                             float *d_mass, float *d_mu, int device_ptrs);
 FW_API fw_status fw_get_tape(fw_world *w, int info[4], int *c_off, int *c_rec, unsigned char *r_bits,
                              unsigned char *b_bits);
 FW_API fw_status fw_set_body_params(fw_world *w, const float *mass, const float *mu);

@@ -460,6 +460,7 @@ void fw_config_default(fw_config *c) {
     c->contact_offset = 1e-4f;
     c->cos_patch = 0.94f;
     c->max_patches = 128;
+    c->patch_dirs = kSlots - 1;
     c->batch_size = kBatch;
     c->baumgarte = 0.2f;
     c->n_vel_iters = 0;
@@ -472,7 +473,8 @@ void fw_config_default(fw_config *c) {
 fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (!cfg || !out) return FW_ERR_ARG;
     *out = nullptr;
-    if (cfg->batch_size != kBatch || cfg->max_patches < 1 || cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0))
+    if (cfg->batch_size != kBatch || cfg->patch_dirs != kSlots - 1 || cfg->max_patches < 1 ||
+        cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0))
         return FW_ERR_ARG;
     fw_world *w = new fw_world();
     w->cfg = *cfg;
@@ -1321,6 +1323,17 @@ fw_status fw_adjoint_rollout(fw_world *w, const float *g_pos, const float *g_qua
     CK(cudaMemcpy(d_mass, mb.data(), sizeof(float) * nb, out_kind));
     if (np > 0) CK(cudaMemcpy(d_mu, mub.data(), sizeof(float) * np, out_kind));
     return FW_OK;
+}
+
+fw_status fw_step_fwd_ckpt(fw_world *w, int n_substeps, int n_iters) {
+    return fw_record_rollout(w, n_substeps, n_iters);
+}
+
+fw_status fw_step_bwd(fw_world *w, const float *g_pos, const float *g_quat, const float *g_linvel,
+                      const float *g_angvel, float *d_pos, float *d_quat, float *d_linvel, float *d_angvel,
+                      float *d_mass, float *d_mu, int device_ptrs) {
+    return fw_adjoint_rollout(w, g_pos, g_quat, g_linvel, g_angvel, d_pos, d_quat, d_linvel, d_angvel, d_mass, d_mu,
+                              device_ptrs);
 }
 
 fw_status fw_get_tape(fw_world *w, int info[4], int *c_off, int *c_rec, unsigned char *r_bits, unsigned char *b_bits) {

@@ -27,7 +27,8 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
-                 "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_get_tape",
+                 "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
+                 "fw_step_bwd", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
                  "fw_last_error"]
 
@@ -40,7 +41,8 @@ class FwError(RuntimeError):
 
 class FwConfig(C.Structure):
     _fields_ = [("gravity", C.c_float * 3), ("dt", C.c_float), ("contact_offset", C.c_float),
-                ("cos_patch", C.c_float), ("max_patches", C.c_int), ("batch_size", C.c_int),
+                ("cos_patch", C.c_float), ("max_patches", C.c_int), ("patch_dirs", C.c_int),
+                ("batch_size", C.c_int),
                 ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
                 ("sdf_fp16", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p)]
 
@@ -95,6 +97,8 @@ def load_library(path: str = LIB_PATH):
         "fw_record_rollout": (st, [vp, i, i]),
         "fw_replay_rollout": (st, [vp]),
         "fw_adjoint_rollout": (st, [vp] + [vp] * 10 + [i]),
+        "fw_step_fwd_ckpt": (st, [vp, i, i]),
+        "fw_step_bwd": (st, [vp] + [vp] * 10 + [i]),
         "fw_get_tape": (st, [vp, vp, vp, vp, vp, vp]),
         "fw_set_body_params": (st, [vp, vp, vp]),
         "fw_get_detect_stats": (st, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
@@ -337,10 +341,18 @@ class World:
     def record_rollout(self, n_substeps: int, n_iters: int):
         self._check(self.lib.fw_record_rollout(self.h, n_substeps, n_iters))
 
+    def step_fwd_ckpt(self, n_substeps: int, n_iters: int):
+        """One frame forward with its tape and checkpoints (fw_step_fwd_ckpt)."""
+        self._check(self.lib.fw_step_fwd_ckpt(self.h, n_substeps, n_iters))
+
     def replay_rollout(self):
         self._check(self.lib.fw_replay_rollout(self.h))
 
-    def adjoint_rollout(self, g_pos, g_quat, g_linvel, g_angvel):
+    def step_bwd(self, g_pos, g_quat, g_linvel, g_angvel):
+        """The adjoint of the frame last stepped by step_fwd_ckpt (fw_step_bwd)."""
+        return self.adjoint_rollout(g_pos, g_quat, g_linvel, g_angvel, _entry="fw_step_bwd")
+
+    def adjoint_rollout(self, g_pos, g_quat, g_linvel, g_angvel, _entry="fw_adjoint_rollout"):
         """Adjoints of the initial state and parameters of the last record/replay, given
         those of its final state.  numpy in -> numpy out, CUDA tensors in -> CUDA tensors
         out: (pos, quat, linvel, angvel, mass, mu)."""
@@ -354,8 +366,8 @@ class World:
             mk = lambda *shape: np.zeros(shape, np.float32)
             gs = [np.ascontiguousarray(a, np.float32) for a in (g_pos, g_quat, g_linvel, g_angvel)]
         outs = [mk(nb, 3), mk(nb, 4), mk(nb, 3), mk(nb, 3), mk(nb), mk(max(npair, 1))]
-        self._check(self.lib.fw_adjoint_rollout(self.h, *[_ptr(a)[0] for a in gs], *[_ptr(a)[0] for a in outs],
-                                                int(dev)))
+        self._check(getattr(self.lib, _entry)(self.h, *[_ptr(a)[0] for a in gs], *[_ptr(a)[0] for a in outs],
+                                              int(dev)))
         outs[5] = outs[5][:npair]
         return tuple(outs)
 

@@ -35,11 +35,34 @@ def test_library_exports_nothing_else():
 
 def test_config_defaults_without_gpu():
     cfg = fw.default_config()
-    assert cfg.batch_size == 1024 and cfg.max_patches == 128
+    assert cfg.batch_size == 1024 and cfg.max_patches == 128 and cfg.patch_dirs == 6
     assert abs(cfg.dt - 1 / 60) < 1e-7 and abs(cfg.gravity[2] + 9.81) < 1e-6
     assert abs(cfg.contact_offset - 1e-4) < 1e-9 and abs(cfg.cos_patch - 0.94) < 1e-7
 
 
-def test_struct_layouts_match_header():
-    assert ctypes.sizeof(fw.FwConfig) == 64   # 11 four-byte fields, pad, pointer
+def test_struct_layouts_match_header(tmp_path):
+    assert ctypes.sizeof(fw.FwConfig) == 64   # 14 four-byte values (gravity has 3), then a pointer
+    # every field offset of the binding's fw_config against the C compiler's, from the header
+    names = [f[0] for f in fw.FwConfig._fields_]
+    src = tmp_path / "offsets.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"fw.h\"\nint main(void) {\n" +
+                   "".join(f'  printf("%zu\\n", offsetof(fw_config, {n}));\n' for n in names) +
+                   '  printf("%zu\\n", sizeof(fw_config));\n  return 0;\n}\n')
+    exe = tmp_path / "offsets"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [getattr(fw.FwConfig, n).offset for n in names] + [ctypes.sizeof(fw.FwConfig)]
+    assert got == want, (got, want)
+    # the numpy record types the binding passes as arrays of fw_body_desc / fw_contact / fw_candidate
+    from paper_2205_03532_b300 import scenes
+    for ctype, dt in (("fw_body_desc", scenes.BODY_DTYPE), ("fw_contact", fw.CONTACT_DTYPE),
+                      ("fw_candidate", fw.CANDIDATE_DTYPE)):
+        src = tmp_path / f"{ctype}.c"
+        src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"fw.h\"\nint main(void) {\n" +
+                       "".join(f'  printf("%zu\\n", offsetof({ctype}, {n}));\n' for n in dt.names) +
+                       f'  printf("%zu\\n", sizeof({ctype}));\n  return 0;\n}}\n')
+        exe = tmp_path / ctype
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+        got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+        assert got == [dt.fields[n][1] for n in dt.names] + [dt.itemsize], (ctype, got)
     assert fw.CONTACT_DTYPE.itemsize == 52 and fw.CANDIDATE_DTYPE.itemsize == 32

@@ -109,6 +109,26 @@ def test_gpu_adjoint_matches_oracle_on_the_same_tape(diff_world):
         assert np.quantile(e, 0.95) <= 1e-3 and e.max() <= 5e-3, (name, float(e.max()))
 
 
+def test_step_fwd_ckpt_and_step_bwd_are_record_and_adjoint(diff_world):
+    """The frame-step names of the interface run the same operations: same final state,
+    same adjoints, bit for bit."""
+    sc, w, x0 = diff_world
+    nb = len(x0[0])
+    g = _rand_g(nb, 5)
+    w.set_state(*x0)
+    w.record_rollout(sc.sim.n_substeps, sc.sim.n_iters)
+    s1 = [a.copy() for a in w.get_state()]
+    a1 = w.adjoint_rollout(*g)
+    w.set_state(*x0)
+    w.step_fwd_ckpt(sc.sim.n_substeps, sc.sim.n_iters)
+    s2 = w.get_state()
+    a2 = w.step_bwd(*g)
+    for x, y in zip(s1, s2):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(a1, a2):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_full_frame_adjoint_within_the_problems_conditioning(frame_world):
     sc, w, x0 = frame_world
     w.set_state(*x0)
