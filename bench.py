@@ -32,6 +32,9 @@ NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32)
     "3e73388cbb3265bf": {"query_kernel": 10.54e6, "reduce_kernel": 31.89e6, "solve_kernel": 28.23e6},
 }
+# per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
+NCU_L2 = {
+}
 
 FP32_LANES_PER_SM = 128
 SOLVE_FLOPS_PER_CONTACT_SWEEP = 100   # normal row, joint friction rows and the 6-DoF velocity update of one body
@@ -121,23 +124,32 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(n_envs: int, seed: int, frames: int = 1):
+def cpu_baseline(n_envs: int, seed: int, frames: int = 2):
     """The FP64 oracle as it stands, on host cores, on a bounded sample of the workload:
-    n_envs nut-bolt envs for `frames` frames after one warm-up detection; the oracle's lazy
-    SDF bake (set-up work on both sides) is excluded."""
+    n_envs nut-bolt envs (0: one per core, the oracle parallelises over envs) for `frames`
+    frames after one warm-up detection, then one frame of the same world on one core; the
+    oracle's lazy SDF bake (set-up work on both sides) is excluded from both times."""
     from oracle import oracle as O
     from paper_2205_03532_b300 import scenes as S
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    n_envs = n_envs if n_envs > 0 else cores
     sc = S.nut_bolt_scene(n_envs=n_envs, seed=seed)
     w = O.world_from_scene(sc, lazy_bake=True)
     w.collide()
-    b0 = w.bake_seconds()
-    t0 = time.perf_counter()
-    for _ in range(frames):
-        w.step(sc.sim.n_substeps, sc.sim.n_iters)
-    el = time.perf_counter() - t0 - (w.bake_seconds() - b0)
-    units = n_envs * sc.sim.n_substeps * frames
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return units / el, cores, f"{n_envs} envs x {frames} frame(s) of {sc.sim.n_substeps} substeps x {sc.sim.n_iters} sweeps"
+
+    def timed(k):
+        b0 = w.bake_seconds()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            w.step(sc.sim.n_substeps, sc.sim.n_iters)
+        return time.perf_counter() - t0 - (w.bake_seconds() - b0)
+    el = timed(frames)
+    w.set_threads(1)
+    el1 = timed(1)
+    units = n_envs * sc.sim.n_substeps
+    return (units * frames / el, units / el1, cores,
+            f"{n_envs} envs x {frames} frame(s) of {sc.sim.n_substeps} substeps x {sc.sim.n_iters} sweeps on "
+            f"{cores} threads, then 1 frame on 1 thread")
 
 
 def run_reference(args):
@@ -195,6 +207,14 @@ def run_fw(args):
         w = fw.world_from_scene(sc, fp16=args.fp16, stream=stream.cuda_stream, device=dev)
         bake_s = time.perf_counter() - t_b
     n_env, n_body, n_pair = w.counts()
+    nodes = tests = 0
+    for ai, a in enumerate(sc.assets):
+        if a.sdf_res:
+            d = w.get_sdf(ai, values=False)[2]
+            nodes += int(d[0]) * int(d[1]) * int(d[2])
+            tests += int(d[0]) * int(d[1]) * int(d[2]) * len(a.tris)
+    bake_info = {"s": bake_s, "grid_nodes": nodes, "nodes_per_s": nodes / bake_s,
+                 "brute_force_point_triangle_tests_per_s": tests / bake_s}
     shape = [int(v) for v in args.solve_shape.split(",")]
     w.set_solve_shape(*shape)
     tuned = None
@@ -259,12 +279,20 @@ def run_fw(args):
     # the table was taken on the default workload only (1000 M16 envs, FP32)
     default_run = args.workload == "nut_bolt" and not args.fp16 and args.envs == 1000
     traffic = NCU_TRAFFIC.get(src, {}) if default_run else {}
+    l2_traffic = NCU_L2.get(src, {}) if default_run else {}
+    l2_gbs = fw.measure_l2_read(dev)   # untimed: the L2 roofline's denominator on this device
+
+    def l2_entry(name, ms):
+        t = l2_traffic.get(name)
+        a = None if t is None else t / (ms * 1e-3) / 1e9
+        return {"achieved": a, "peak": l2_gbs, "unit": "GB/s", "frac": None if a is None else a / l2_gbs,
+                "traffic": t, "peak_source": "measured L2 read bandwidth (fw_measure_l2_read, 48 MB, L1 bypassed)"}
 
     def hbm_entry(name, nbytes, ms):
         gbs = nbytes / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": traffic.get(name), "avg_launch_ms": ms, "algorithmic_bytes": nbytes,
-                "peak_source": f"{peak_kind} hbm_gbs"}
+                "peak_source": f"{peak_kind} hbm_gbs", "l2": l2_entry(name, ms)}
 
     sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     kernels = {
@@ -274,7 +302,9 @@ def run_fw(args):
         "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": sol_tf / alu_peak, "traffic": traffic.get("solve_kernel"),
                          "avg_launch_ms": sol_ms, "algorithmic_flops": sol_flops,
-                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x max SM clock"},
+                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x max SM clock",
+                         "cycles_per_row_update": sol_ms * 1e-3 * sm_max * 1e6 / max(c_mean * sim.n_iters, 1),
+                         "l2": l2_entry("solve_kernel", sol_ms)},
     }
     dominant = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
@@ -298,8 +328,9 @@ def run_fw(args):
     state_bytes = n_body * (3 + 4 + 3 + 3) * 4
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline(args.cpu_envs, args.seed)
-        cpu = {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle", "sample": sample}
+        v, v1, cores, sample = cpu_baseline(args.cpu_envs, args.seed)
+        cpu = {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "value_1core": v1}
     if rank == 0:
         out = {"metric": "env-substeps/s", "value": value, "unit": "env-substeps/s", "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -321,7 +352,7 @@ def run_fw(args):
                "e2e": {"value": e2e_value, "unit": "env-substeps/s", "h2d_bytes_per_step": state_bytes,
                        "d2h_bytes_per_step": state_bytes},
                "gpu_launches": args.steps * w.launches_per_step(sim.n_substeps),
-               "bake_s": bake_s, "setup_s": time.perf_counter() - t_setup, "src": src}
+               "bake_s": bake_s, "bake": bake_info, "setup_s": time.perf_counter() - t_setup, "src": src}
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -382,14 +413,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fw", choices=["fw", "reference"])
     ap.add_argument("--envs", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp16", action="store_true")
     ap.add_argument("--solve-shape", default="0,0", help="envs per warp, warps per block (0,0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-envs", type=int, default=4)
+    ap.add_argument("--cpu-envs", type=int, default=0, help="envs of the oracle sample (0: one per core)")
     ap.add_argument("--ref-envs", type=int, default=2)
     ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "diff_peg"],
                     help="nut_bolt: the headline substep benchmark (1000 M16 envs); mixed: 4096 envs of "

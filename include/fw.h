@@ -363,6 +363,17 @@ FW_API int fw_launches_per_step(fw_world *w, int n_substeps);
 /* Message of the last failed call on this world (never NULL). */
 FW_API const char *fw_last_error(const fw_world *w);
 
+/* ---------------------------------------------------------------- measurement */
+/* L2 read bandwidth of a device, the denominator of the L2 roofline of kernels whose
+ * working set stays in L2 (not on the substep path; no counterpart in the paper).
+ * Allocates a device buffer of `bytes` (a multiple of 16, far below the L2 size), fills
+ * it, reads it once to bring it into L2, then times `iters` full reads by SM-count x 8
+ * blocks of 16-byte loads that bypass L1, and frees it.  *gbs = iters x bytes / time
+ * (GB/s, 1e9 bytes).  Synchronises; runs on a stream of its own.
+ * Errors: FW_ERR_ARG for bytes < 1 MiB, bytes not a multiple of 16, iters < 1 or a NULL
+ * gbs; FW_ERR_CUDA if a CUDA call fails. */
+FW_API fw_status fw_measure_l2_read(int device, long long bytes, int iters, float *gbs);
+
 #ifdef __cplusplus
 }
 #endif

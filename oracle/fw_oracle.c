@@ -392,6 +392,10 @@ or_world *or_create(const or_config *cfg) {
     return w;
 }
 
+void or_set_threads(or_world *w, int n_threads) {
+    if (w) w->cfg.n_threads = n_threads;
+}
+
 void or_destroy(or_world *w) {
     if (!w) return;
     for (int i = 0; i < w->n_assets; ++i) {

@@ -115,6 +115,8 @@ typedef struct or_world or_world;
 
 or_world *or_create(const or_config *cfg);
 void or_destroy(or_world *w);
+/* OpenMP threads of the world's later calls (0 = the OpenMP default); test/timing use */
+void or_set_threads(or_world *w, int n_threads);
 int or_add_asset(or_world *w, const float *V, int nv, const int *T, int nt,
                  const float *samples, int ns, double density);
 /* lazy = 1 bakes nodes only when a query first needs them. */

@@ -77,6 +77,7 @@ def lib():
             L.or_create.argtypes = [C.POINTER(OrConfig)]
             L.or_create.restype = vp
             L.or_destroy.argtypes = [vp]
+            L.or_set_threads.argtypes = [vp, C.c_int]
             L.or_add_asset.argtypes = [vp, _f32, C.c_int, _i32, C.c_int, vp, C.c_int, C.c_double]
             L.or_asset_bake.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.c_int, C.c_int]
             L.or_asset_set_grid.argtypes = [vp, C.c_int, _f32, C.c_float, _i32, _f32]
@@ -224,6 +225,10 @@ class OracleWorld:
         self.cfg = cfg
         self.h = lib().or_create(C.byref(cfg))
         self.n_assets = 0
+
+    def set_threads(self, n_threads: int):
+        """OpenMP threads for this world's later calls (0: the OpenMP default)."""
+        lib().or_set_threads(self.h, n_threads)
 
     def close(self):
         if self.h:

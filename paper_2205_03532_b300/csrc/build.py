@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
-SOURCES = ["fw_api.cu", "fw_bake.cu", "fw_detect.cu", "fw_solve.cu", "fw_diff.cu"]
+SOURCES = ["fw_api.cu", "fw_bake.cu", "fw_detect.cu", "fw_solve.cu", "fw_diff.cu", "fw_probe.cu"]
 HEADERS = ["fw_internal.h", "fw_device.cuh"]
 LIB = os.path.join(PKG, "libfw.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -1406,4 +1406,9 @@ const char *fw_last_error(const fw_world *w) {
     return w->err.c_str();
 }
 
+fw_status fw_measure_l2_read(int device, long long bytes, int iters, float *gbs) {
+    if (!gbs || bytes < (1LL << 20) || bytes % 16 != 0 || iters < 1) return FW_ERR_ARG;
+    return fw::measure_l2_read(device, bytes, iters, gbs) == cudaSuccess ? FW_OK : FW_ERR_CUDA;
+}
+
 }  // extern "C"

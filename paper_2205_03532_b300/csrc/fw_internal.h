@@ -174,5 +174,6 @@ cudaError_t prepare_solve(int optin, int max_dyn[4]);
 SolveShape solve_shape(int n_envs, int lam_cap, int groups, int warps, const int max_dyn[4], int n_sm);
 cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
+cudaError_t measure_l2_read(int device, long long bytes, int iters, float *gbs);
 
 }  // namespace fw

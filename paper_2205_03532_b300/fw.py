@@ -30,7 +30,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
-                 "fw_last_error"]
+                 "fw_last_error", "fw_measure_l2_read"]
 
 
 class FwError(RuntimeError):
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "fw_launches_per_step": (i, [vp, i]),
         "fw_last_error": (C.c_char_p, [vp]),
+        "fw_measure_l2_read": (st, [i, C.c_longlong, i, C.POINTER(f)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -112,6 +113,16 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = L
     return L
+
+
+def measure_l2_read(device: int = 0, nbytes: int = 48 << 20, iters: int = 200) -> float:
+    """L2 read bandwidth of a device in GB/s (fw_measure_l2_read)."""
+    L = load_library()
+    g = C.c_float(0.0)
+    st = L.fw_measure_l2_read(device, nbytes, iters, C.byref(g))
+    if st != 0:
+        raise FwError(st, "fw_measure_l2_read failed")
+    return float(g.value)
 
 
 def default_config(**over) -> FwConfig:
