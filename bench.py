@@ -159,7 +159,8 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2205_03532_b300 import scenes as S
-    n = args.ref_envs
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    n = args.ref_envs if args.ref_envs > 0 else cores   # one env per core: the oracle parallelises over envs
     sc = S.nut_bolt_scene(n_envs=n, seed=args.seed)
     w = O.world_from_scene(sc, lazy_bake=True)
     w.collide()
@@ -172,7 +173,6 @@ def run_reference(args):
     el = time.perf_counter() - t0 - (w.bake_seconds() - b0)
     units = n * sc.sim.n_substeps * args.steps
     v = units / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out = {"impl": "reference", "metric": "env-substeps/s", "value": v, "unit": "env-substeps/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -421,7 +421,7 @@ def main():
     ap.add_argument("--solve-shape", default="0,0", help="envs per warp, warps per block (0,0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=0, help="envs of the oracle sample (0: one per core)")
-    ap.add_argument("--ref-envs", type=int, default=2)
+    ap.add_argument("--ref-envs", type=int, default=0, help="envs of the reference arm's sample (0: one per core)")
     ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "diff_peg"],
                     help="nut_bolt: the headline substep benchmark (1000 M16 envs); mixed: 4096 envs of "
                          "M8-M20 pairs; diff_peg: gradient throughput of the differentiable peg")
