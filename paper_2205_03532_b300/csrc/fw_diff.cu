@@ -21,6 +21,10 @@
 // One warp per env, four envs per block.  Lane 0 runs the serial parts (sweeps,
 // integration, their reverse); the lanes share the contacts for geometry and rows and
 // their reverse, whose body-level sums are reduced in a fixed order (deterministic).
+// For an env of at most kDiffSmemRows contacts the serial sweeps read the rows' solve
+// coefficients, the impulses and the row adjoints from shared memory (the lanes stage
+// them), and fetch the next update's recorded inputs and decision bits one step ahead;
+// larger envs use the same code on the global copies.
 #include "fw_device.cuh"
 
 namespace fw {
@@ -28,6 +32,7 @@ namespace fw {
 namespace {
 
 constexpr int kDiffWarps = 4;
+constexpr int kDiffSmemRows = 128;  // contacts of an env whose sweeps run from shared memory
 
 
 // (omega, 0) (x) q for q = (x, y, z, w)
@@ -113,8 +118,21 @@ struct DRow {   // one contact row of the dynamic body, world frame
     float bias, e[3], mu;
 };
 
-struct DRowBar {
+struct __align__(16) DRowBar {   // 144 bytes: nine float4
     float d[3][3], a[3][3], b[3][3], k[3], bias, e[3], mu;
+};
+
+// the fields of a DRow that one row update reads (160 bytes: ten float4)
+struct __align__(16) SRow {
+    float d[3][3], a[3][3], b[3][3], k[3], bias, e[3], mu;
+    int live, pad_[2];
+};
+
+// shared memory of one env (one warp)
+struct EnvSmem {
+    SRow row[kDiffSmemRows];
+    float lam[3 * kDiffSmemRows];      // impulses (forward), their adjoints (reverse)
+    DRowBar bar[kDiffSmemRows];        // row adjoints (reverse)
 };
 
 struct St {
@@ -198,11 +216,14 @@ __device__ void build_drow(const DiffParams &dp, const St &in, const DBody &F, c
     D.mu = P.mu;
 }
 
-// one row update with the given decisions (record: computed and written to *bits)
-__device__ void drow_fwd(const DRow &D, float invm, V3 &v, V3 &w, float lam[3], unsigned char *bits, bool replay) {
+// one row update with the given decisions (replay: taken from `taped`; record: computed
+// and written to *bits)
+template <class R>
+__device__ __forceinline__ void drow_fwd(const R &D, float invm, V3 &v, V3 &w, float *lam, unsigned char taped,
+                                         unsigned char *bits, bool replay) {
     const float jv = dot(ld3(D.d[0]), v) + dot(ld3(D.a[0]), w) + D.bias + D.e[0];
     const float u = lam[0] - D.k[0] * jv;
-    const bool act = replay ? ((*bits & 1) != 0) : (u > 0.0f);
+    const bool act = replay ? ((taped & 1) != 0) : (u > 0.0f);
     const float ln = act ? u : 0.0f;
     const float dl = ln - lam[0];
     const V3 vm = v + (invm * dl) * ld3(D.d[0]);
@@ -211,7 +232,7 @@ __device__ void drow_fwd(const DRow &D, float invm, V3 &v, V3 &w, float lam[3], 
     const float j2 = dot(ld3(D.d[2]), vm) + dot(ld3(D.a[2]), wm) + D.e[2];
     const float t1 = lam[1] - D.k[1] * j1, t2 = lam[2] - D.k[2] * j2;
     const float lim = D.mu * ln, tn = sqrtf(t1 * t1 + t2 * t2);
-    const bool proj = replay ? ((*bits & 2) != 0) : (tn > lim);
+    const bool proj = replay ? ((taped & 2) != 0) : (tn > lim);
     const float s = proj ? lim / tn : 1.0f;
     const float l1 = s * t1, l2 = s * t2;
     const float e1 = l1 - lam[1], e2 = l2 - lam[2];
@@ -221,10 +242,36 @@ __device__ void drow_fwd(const DRow &D, float invm, V3 &v, V3 &w, float lam[3], 
     if (!replay) *bits = (unsigned char)((act ? 1 : 0) | (proj ? 2 : 0));
 }
 
+// K sweeps over nr rows, as lane 0 runs them: the taped decision bit of the next row is
+// loaded a step ahead (replay); upd, when not NULL, receives each update's inputs.
+template <class R>
+__device__ void sweeps_fwd(const R *rows, int nr, int K, float invm, V3 &v, V3 &w, float *L, unsigned char *bits,
+                           bool replay, float *upd) {
+    if (nr == 0) return;
+    unsigned char next = replay ? bits[0] : 0;
+    for (int it = 0; it < K; ++it)
+        for (int r = 0; r < nr; ++r) {
+            const unsigned char taped = next;
+            if (replay) {
+                const int rn = (r + 1 < nr) ? r + 1 : 0, itn = (r + 1 < nr) ? it : it + 1;
+                if (itn < K) next = bits[(size_t)rn * K + itn];
+            }
+            if (upd) {
+                float *u = upd + ((size_t)r * K + it) * 9;
+                u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = w.x; u[4] = w.y; u[5] = w.z;
+                u[6] = L[3 * r]; u[7] = L[3 * r + 1]; u[8] = L[3 * r + 2];
+            }
+            if (!rows[r].live) continue;
+            const R D = rows[r];
+            drow_fwd(D, invm, v, w, L + 3 * r, taped, bits + (size_t)r * K + it, replay);
+        }
+}
+
 // Forward of env e in substep dp.si from state `in`; writes the new state to `out` (which
 // may be `in`: every input is read first).  keep: store each update's inputs in dp.upd.
+// sm: the warp's shared memory (NULL: rows, impulses from global memory).
 __device__ void env_forward(const DiffParams &dp, int e, int lane, const St &in, const St &out, bool replay,
-                            bool keep, DBody &F) {
+                            bool keep, DBody &F, EnvSmem *sm) {
     const SimParams &p = dp.p;
     const EnvDev E = p.envs[e];
     const int ia = dp.dyn[e];
@@ -299,22 +346,31 @@ __device__ void env_forward(const DiffParams &dp, int e, int lane, const St &in,
         }
         __threadfence_block();
         __syncwarp();
+        const bool staged = sm && nr <= kDiffSmemRows;
+        if (staged) {   // the rows' solve coefficients and zero impulses into shared memory
+            for (int r = lane; r < nr; r += 32) {
+                const DRow &D = rows[r];
+                SRow &Sr = sm->row[r];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) { Sr.d[i][j] = D.d[i][j]; Sr.a[i][j] = D.a[i][j]; Sr.b[i][j] = D.b[i][j]; }
+                for (int i = 0; i < 3; ++i) { Sr.k[i] = D.k[i]; Sr.e[i] = D.e[i]; }
+                Sr.bias = D.bias; Sr.mu = D.mu; Sr.live = D.live;
+                sm->lam[3 * r] = 0.f; sm->lam[3 * r + 1] = 0.f; sm->lam[3 * r + 2] = 0.f;
+            }
+            __syncwarp();
+        }
         // sweeps and integration on lane 0
         if (lane == 0) {
             V3 v = F.v1, w = F.w1;
-            float *L = dp.lam + (size_t)e * dp.row_cap * 3;   // impulses, no warm start
-            for (int r = 0; r < nr; ++r) { L[3 * r] = 0.f; L[3 * r + 1] = 0.f; L[3 * r + 2] = 0.f; }
+            float *L = staged ? sm->lam : dp.lam + (size_t)e * dp.row_cap * 3;   // impulses, no warm start
+            if (!staged)
+                for (int r = 0; r < nr; ++r) { L[3 * r] = 0.f; L[3 * r + 1] = 0.f; L[3 * r + 2] = 0.f; }
             unsigned char *bits = dp.tape_r + (size_t)slot * dp.row_cap * dp.K;
-            for (int it = 0; it < dp.K; ++it)
-                for (int r = 0; r < nr; ++r) {
-                    if (keep) {
-                        float *u = dp.upd + (((size_t)e * dp.row_cap + r) * dp.K + it) * 9;
-                        u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = w.x; u[4] = w.y; u[5] = w.z;
-                        u[6] = L[3 * r]; u[7] = L[3 * r + 1]; u[8] = L[3 * r + 2];
-                    }
-                    if (!rows[r].live) continue;
-                    drow_fwd(rows[r], PA.invm, v, w, L + 3 * r, bits + (size_t)r * dp.K + it, replay);
-                }
+            float *upd = keep ? dp.upd + (size_t)e * dp.row_cap * dp.K * 9 : nullptr;
+            if (staged)
+                sweeps_fwd(sm->row, nr, dp.K, PA.invm, v, w, L, bits, replay, upd);
+            else
+                sweeps_fwd(rows, nr, dp.K, PA.invm, v, w, L, bits, replay, upd);
             F.vf = v;
             F.wf = w;
             const float wn = sqrtf(dot(w, w));
@@ -382,8 +438,9 @@ __device__ __forceinline__ void add3(float *a, V3 b) { a[0] += b.x; a[1] += b.y;
 
 // reverse of drow_fwd: u = (v, w, lambda) before the update; vb, wb, lb: adjoints of the
 // outputs in, of the inputs out; the row's data adjoints accumulate in X
-__device__ void drow_rev(const DRow &D, float invm, const float *u, unsigned char bits, V3 &vb, V3 &wb, float lb[3],
-                         DRowBar &X, float &invm_b) {
+template <class R>
+__device__ __forceinline__ void drow_rev(const R &D, float invm, const float *u, unsigned char bits, V3 &vb, V3 &wb,
+                                         float *lb, DRowBar &X, float &invm_b) {
     const V3 v = v3(u[0], u[1], u[2]), w = v3(u[3], u[4], u[5]);
     const float lam0 = u[6], lam1 = u[7], lam2 = u[8];
     const V3 d0 = ld3(D.d[0]), d1 = ld3(D.d[1]), d2 = ld3(D.d[2]);
@@ -519,15 +576,47 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Reverse of one env substep; the forward (with keep) has just run from `in`.
-__device__ void env_reverse(const DiffParams &dp, int e, int lane, const St &in, const DBody &F) {
+// The sweeps of one env in reverse, as lane 0 runs them: last update first, the next
+// update's recorded inputs and decision bits loaded a step ahead.
+template <class R>
+__device__ void sweeps_rev(const R *rows, DRowBar *X, int nr, int K, float invm, const float *upd,
+                           const unsigned char *bits, V3 &vb, V3 &wb, float *lb, float &invm_b) {
+    if (nr == 0 || K == 0) return;
+    int it = K - 1, r = nr - 1;
+    float un[9];
+    unsigned char bn = bits[(size_t)r * K + it];
+    for (int k = 0; k < 9; ++k) un[k] = upd[((size_t)r * K + it) * 9 + k];
+    for (;;) {
+        float u[9];
+        for (int k = 0; k < 9; ++k) u[k] = un[k];
+        const unsigned char b = bn;
+        const int rc = r;
+        if (--r < 0) { r = nr - 1; --it; }
+        if (it >= 0) {
+            bn = bits[(size_t)r * K + it];
+            for (int k = 0; k < 9; ++k) un[k] = upd[((size_t)r * K + it) * 9 + k];
+        }
+        if (rows[rc].live) {   // the row and its adjoints in registers for the update
+            const R D = rows[rc];
+            DRowBar Xr = X[rc];
+            drow_rev(D, invm, u, b, vb, wb, lb + 3 * rc, Xr, invm_b);
+            X[rc] = Xr;
+        }
+        if (it < 0) break;
+    }
+}
+
+__device__ void env_reverse(const DiffParams &dp, int e, int lane, const St &in, const DBody &F, EnvSmem *sm) {
     const SimParams &p = dp.p;
     const int ia = dp.dyn[e];
     const BodyProps PA = p.props[ia];
     const int slot = dp.si * p.n_envs + e;
     const int nr = dp.tape_n[slot];
     DRow *rows = dp.rows + (size_t)e * dp.row_cap;
-    DRowBar *rbar = dp.rbar + (size_t)e * dp.row_cap;
-    float *lb = dp.lam + (size_t)e * dp.row_cap * 3;
+    // the forward just ran (env_forward with keep) and staged the rows when this holds
+    const bool staged = sm && nr <= kDiffSmemRows;
+    DRowBar *rbar = staged ? sm->bar : dp.rbar + (size_t)e * dp.row_cap;
+    float *lb = staged ? sm->lam : dp.lam + (size_t)e * dp.row_cap * 3;
     float *xb = dp.xb + 13 * ia;
     const float hs = dp.hs;
     for (int r = lane; r < nr; r += 32) {
@@ -579,12 +668,11 @@ __device__ void env_reverse(const DiffParams &dp, int e, int lane, const St &in,
         }
         // sweeps, last update first
         const unsigned char *bits = dp.tape_r + (size_t)slot * dp.row_cap * dp.K;
-        for (int it = dp.K - 1; it >= 0; --it)
-            for (int r = nr - 1; r >= 0; --r) {
-                if (!rows[r].live) continue;
-                drow_rev(rows[r], PA.invm, dp.upd + (((size_t)e * dp.row_cap + r) * dp.K + it) * 9,
-                         bits[(size_t)r * dp.K + it], vb, wb, lb + 3 * r, rbar[r], invm_b0);
-            }
+        const float *upd = dp.upd + (size_t)e * dp.row_cap * dp.K * 9;
+        if (staged)
+            sweeps_rev(sm->row, rbar, nr, dp.K, PA.invm, upd, bits, vb, wb, lb, invm_b0);
+        else
+            sweeps_rev(rows, rbar, nr, dp.K, PA.invm, upd, bits, vb, wb, lb, invm_b0);
         v1b = vb;
         w1b = wb;
     }
@@ -680,8 +768,9 @@ __global__ void __launch_bounds__(32 * kDiffWarps) diff_forward_kernel(DiffParam
         for (int k = 0; k < 4; ++k) ck.quat[4 * bi + k] = p.quat[4 * bi + k];
     }
     __syncwarp();
+    extern __shared__ EnvSmem diff_smem[];
     DBody F;
-    env_forward(dp, e, lane, world, world, replay != 0, false, F);
+    env_forward(dp, e, lane, world, world, replay != 0, false, F, diff_smem + (threadIdx.x >> 5));
 }
 
 __global__ void __launch_bounds__(32 * kDiffWarps) diff_reverse_kernel(DiffParams dp, int n_bodies) {
@@ -689,9 +778,28 @@ __global__ void __launch_bounds__(32 * kDiffWarps) diff_reverse_kernel(DiffParam
     const int lane = threadIdx.x & 31;
     if (e >= dp.p.n_envs) return;
     const St ck = ck_at(dp, dp.si, n_bodies);
+    extern __shared__ EnvSmem diff_smem[];
+    EnvSmem *sm = diff_smem + (threadIdx.x >> 5);
     DBody F;
-    env_forward(dp, e, lane, ck, dp.scratch, true, true, F);
-    if (dp.dyn[e] >= 0) env_reverse(dp, e, lane, ck, F);
+    env_forward(dp, e, lane, ck, dp.scratch, true, true, F, sm);
+    if (dp.dyn[e] >= 0) env_reverse(dp, e, lane, ck, F, sm);
+}
+
+constexpr size_t kDiffSmemBytes = sizeof(EnvSmem) * kDiffWarps;
+
+// raise the kernels' dynamic shared-memory limit once per device (the block needs more
+// than the default 48 KB)
+cudaError_t prepare_diff_kernels() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(diff_reverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSmemBytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
 }
 
 DiffParams make_params(const SimParams &p, const DiffState &d, int si, int n_bodies) {
@@ -723,14 +831,19 @@ cudaError_t launch_diff_forward(const SimParams &p, const DiffState &d, int si, 
                                 cudaStream_t s) {
     if (p.n_envs == 0) return cudaSuccess;
     const DiffParams dp = make_params(p, d, si, n_bodies);
-    diff_forward_kernel<<<(p.n_envs + kDiffWarps - 1) / kDiffWarps, 32 * kDiffWarps, 0, s>>>(dp, n_bodies, replay ? 1 : 0);
+    cudaError_t e = prepare_diff_kernels();
+    if (e != cudaSuccess) return e;
+    diff_forward_kernel<<<(p.n_envs + kDiffWarps - 1) / kDiffWarps, 32 * kDiffWarps, kDiffSmemBytes, s>>>(
+        dp, n_bodies, replay ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diff_reverse(const SimParams &p, const DiffState &d, int si, int n_bodies, cudaStream_t s) {
     if (p.n_envs == 0) return cudaSuccess;
     const DiffParams dp = make_params(p, d, si, n_bodies);
-    diff_reverse_kernel<<<(p.n_envs + kDiffWarps - 1) / kDiffWarps, 32 * kDiffWarps, 0, s>>>(dp, n_bodies);
+    cudaError_t e = prepare_diff_kernels();
+    if (e != cudaSuccess) return e;
+    diff_reverse_kernel<<<(p.n_envs + kDiffWarps - 1) / kDiffWarps, 32 * kDiffWarps, kDiffSmemBytes, s>>>(dp, n_bodies);
     return cudaGetLastError();
 }
 
