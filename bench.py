@@ -117,6 +117,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def env_seed(seed: int, rank: int) -> int:
+    """Scene seed of a rank: every rank simulates its own envs (weak scaling, no exchange)."""
+    return seed + 1000 * rank
+
+
+def job_rate(local_ms: float, local_units: int, ws: int, device=None):
+    """Whole-job rate of a weak-scaled run.  Each rank processed local_units in a timed
+    region of local_ms; the job's time is the longest rank's and its units are the sum over
+    ranks.  Returns (units per second, job ms, job units); collective only when ws > 1."""
+    job_ms, units = float(local_ms), int(local_units)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([job_ms], dtype=torch.float64, device=device)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        job_ms, units = float(t.item()), int(round(u.item()))
+    return units / (job_ms * 1e-3), job_ms, units
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -198,9 +219,9 @@ def run_fw(args):
     stream = torch.cuda.Stream(device=dev)
     t_setup = time.perf_counter()
     if args.workload == "mixed":
-        sc = S.mixed_nut_bolt_scene(n_envs=args.envs if args.envs != 1000 else 4096, seed=args.seed + 1000 * rank)
+        sc = S.mixed_nut_bolt_scene(n_envs=args.envs if args.envs != 1000 else 4096, seed=env_seed(args.seed, rank))
     else:
-        sc = S.nut_bolt_scene(n_envs=args.envs, seed=args.seed + 1000 * rank)
+        sc = S.nut_bolt_scene(n_envs=args.envs, seed=env_seed(args.seed, rank))
     sim = sc.sim
     with torch.cuda.stream(stream):
         t_b = time.perf_counter()
@@ -247,13 +268,7 @@ def run_fw(args):
         dist.barrier()
     w.sync()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = ws * n_env * sim.n_substeps * args.steps
-    value = units / (total_ms * 1e-3)
+    value, total_ms, units = job_rate(sum(step_ms), n_env * sim.n_substeps * args.steps, ws, device=dev)
     # ---- per-kernel durations (direct launches with events on the world stream)
     w.set_timing(True)
     with torch.cuda.stream(stream):
@@ -366,8 +381,11 @@ def run_diff_peg(args):
     import torch
     from paper_2205_03532_b300 import fw, scenes as S
     ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    sc, tp, tq = S.diff_peg_scene(n_envs=args.envs if args.envs != 1000 else 256, seed=args.seed)
+    sc, tp, tq = S.diff_peg_scene(n_envs=args.envs if args.envs != 1000 else 256, seed=env_seed(args.seed, rank))
     w = fw.world_from_scene(sc, device=local)
     n_env, nb, npair = w.counts()
     x0 = [torch.tensor(a, device="cuda") for a in w.get_state()]
@@ -391,6 +409,8 @@ def run_diff_peg(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     t_rec, t_adj = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -398,15 +418,17 @@ def run_diff_peg(args):
         t_rec.append(time.perf_counter() - t0 - ta)
         t_adj.append(ta)
     tot = sum(t_rec) + sum(t_adj)
-    units = n_env * S_ * args.steps
+    value, job_ms, units = job_rate(1e3 * tot, n_env * S_ * args.steps, ws, device=local)
     if rank == 0:
-        print(json.dumps({"metric": "gradient env-substeps/s", "value": units / tot, "unit": "env-substeps/s",
+        print(json.dumps({"metric": "gradient env-substeps/s", "value": value, "unit": "env-substeps/s",
                           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-                          "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "ms_per_step": job_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f32", "data": "synthetic (procedural peg in hole, seeded)",
                           "config": {"workload": "diff_peg", "n_envs": n_env, "substeps": S_, "iters": K},
                           "record_ms": 1e3 * sum(t_rec) / args.steps, "adjoint_ms": 1e3 * sum(t_adj) / args.steps,
                           "timing": "host wall clock around calls that synchronise"}), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def main():
