@@ -26,14 +26,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Per-launch DRAM traffic (read + write bytes) of the substep kernels from a one-pass ncu
-# capture of the default workload, keyed by the sha256 of the CUDA sources it was taken
-# on; reported only while the sources are unchanged (profiles/ holds the capture).
+# capture of the default workload, keyed by the sha256 of the substep kernels' sources
+# (SUBSTEP_SOURCES) it was taken on; reported only while they are unchanged (profiles/
+# holds the capture).
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32)
-    "3e73388cbb3265bf": {"query_kernel": 10.54e6, "reduce_kernel": 31.89e6, "solve_kernel": 28.23e6},
+    "cf230361e2f01c81": {"query_kernel": 10.54e6, "reduce_kernel": 32.03e6, "solve_kernel": 28.04e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
+    "cf230361e2f01c81": {"query_kernel": 456.1e6, "reduce_kernel": 97.3e6, "solve_kernel": 3330.0e6},
 }
 
 FP32_LANES_PER_SM = 128
@@ -45,12 +47,16 @@ CANDIDATE_BYTES = 32                  # (x, phi), (n, sample) written by the que
 CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
+# the files that make up the substep kernels (query, reduction, solve), their launches and
+# their compile flags; the traffic tables are keyed by their hash
+SUBSTEP_SOURCES = ("fw_api.cu", "fw_detect.cu", "fw_solve.cu", "fw_device.cuh", "fw_internal.h", "build.py")
+
+
 def _src_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_03532_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")) or f == "build.py":   # sources and their flags
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in SUBSTEP_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
