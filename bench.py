@@ -31,11 +31,11 @@ sys.path.insert(0, ROOT)
 # holds the capture).
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32)
-    "cf230361e2f01c81": {"query_kernel": 10.54e6, "reduce_kernel": 32.03e6, "solve_kernel": 28.04e6},
+    "f071360575c9fc31": {"query_kernel": 10.54e6, "reduce_kernel": 32.03e6, "solve_kernel": 28.04e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "cf230361e2f01c81": {"query_kernel": 456.1e6, "reduce_kernel": 97.3e6, "solve_kernel": 3330.0e6},
+    "f071360575c9fc31": {"query_kernel": 456.1e6, "reduce_kernel": 97.3e6, "solve_kernel": 3330.0e6},
 }
 
 FP32_LANES_PER_SM = 128
@@ -47,16 +47,18 @@ CANDIDATE_BYTES = 32                  # (x, phi), (n, sample) written by the que
 CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
-# the files that make up the substep kernels (query, reduction, solve), their launches and
-# their compile flags; the traffic tables are keyed by their hash
-SUBSTEP_SOURCES = ("fw_api.cu", "fw_detect.cu", "fw_solve.cu", "fw_device.cuh", "fw_internal.h", "build.py")
+# the files that make up the substep kernels (query, reduction, solve) and their launches;
+# the traffic tables are keyed by the hash of these files and of their compile flags
+SUBSTEP_SOURCES = ("fw_api.cu", "fw_detect.cu", "fw_solve.cu", "fw_device.cuh", "fw_internal.h")
 
 
 def _src_hash() -> str:
+    from paper_2205_03532_b300.csrc import build as B
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_03532_b300", "csrc")
     for f in SUBSTEP_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
+        h.update(repr((B.ARCH, B.FLAGS, B.FILE_FLAGS.get(f, []))).encode())
     return h.hexdigest()[:16]
 
 

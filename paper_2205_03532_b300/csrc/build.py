@@ -18,14 +18,20 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # The solve flushes subnormal float32 values to zero: its reciprocal square root then needs no
 # subnormal handling on the serial per-row chain.  Values that small (< 1.2e-38) carry no
 # physical meaning in any of its quantities (velocities, impulses, effective masses).
-FILE_FLAGS = {"fw_solve.cu": ["--ftz=true"]}
+# The adjoint's serial sweeps divide and take square roots on their dependency chain (the
+# friction-disk projection and its reverse): the approximate forms (a few ulp) replace the
+# correctly rounded library sequences there, which made up about half of the adjoint's
+# time; the adjoint is checked against FP64 finite differences and the FP64 oracle with
+# tolerances far above that.
+FILE_FLAGS = {"fw_solve.cu": ["--ftz=true"], "fw_diff.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(HERE, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "fw.h")]
+    deps = [os.path.join(HERE, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "fw.h"),
+                                                                 os.path.abspath(__file__)]   # flags
     return any(os.path.getmtime(d) > t for d in deps)
 
 
