@@ -313,6 +313,39 @@ def test_collide_matches_where_decisions_have_margin(scene, request):
     assert comparable >= (0 if scene == "nut" else 4), comparable
 
 
+@pytest.mark.parametrize("max_patches", [4, 12])
+def test_collide_at_patch_capacity(max_patches):
+    """The substep's own reduction with a patch capacity far below the pairs' patch count:
+    AddPatch replaces patches (the measure M decides) inside the per-pair kernel, in rounds
+    that mix appends and replacements."""
+    fw = _fw()
+    sc = S.peg_in_hole_scene(n_envs=64, seed=9)
+    b = sc.groups[0].bodies
+    rng = np.random.default_rng(9)
+    b["pos"][:, 0, 2] = 12.5e-3 + rng.uniform(-4e-3, 0.3e-3, len(b))
+    b["pos"][:, 0, :2] = rng.uniform(-0.09e-3, 0.09e-3, (len(b), 2))
+    gw = fw.world_from_scene(sc, max_patches=max_patches)
+    ow = O.world_from_scene(sc, max_patches=max_patches, margin_len=MARGIN_LEN, margin_dot=MARGIN_DOT)
+    p, q, v, w = gw.get_state()
+    ow.set_state(p, q, v, w)
+    gw.collide()
+    ow.reset_margins()
+    ow.collide()
+    comparable = replaced = 0
+    for env in range(sc.n_envs):
+        gc = gw.get_contacts(env)
+        oc, ml, md = ow.contacts(env)
+        assert len(set(gc["patch"])) <= max_patches
+        if ml >= MARGIN_LEN and md >= MARGIN_DOT:
+            _compare_contacts(gc, oc)
+            comparable += 1
+        else:
+            _bulk_agree(gc, oc, shared=0.8, count=0.15)
+        replaced += int(len(ow.pair_candidates(env, 0)) > 0 and len(set(oc["patch"])) == max_patches)
+    assert comparable >= 4 and replaced >= 4, (comparable, replaced)
+    gw.close()
+
+
 # ------------------------------------------------------------------------- solve (a4-a7)
 def _state_close(gs, os_, pos_tol, rot_tol, bodies=None):
     p, q, v, w = gs
