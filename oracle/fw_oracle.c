@@ -34,6 +34,16 @@
  *      q <- normalize(q + hs/2 (omega,0) q); |omega| clamped to max_angvel if set.
  *   R11 tangent basis: t1 = normalize(n x e_x) if |n_x| < 0.57735 else
  *      normalize(n x e_y); t2 = n x t1.
+ *   R15 per-triangle generator (contact_gen = 1; Sec. III-A: one contact per face of the
+ *      point body's mesh by local minimisation with projected gradient descent and
+ *      adaptive steps): in body B's frame, start at the face centroid with step length
+ *      s = half the longest edge; each of tri_iters steps moves against the gradient's
+ *      in-plane part by s, projects onto the face (closest point), and is accepted when
+ *      phi decreases (then s *= 1.5), else rejected (s *= 0.5); the descent stops when
+ *      the in-plane gradient is below 1e-9.  A face whose centroid is outside the grid,
+ *      or whose final gradient vanishes, makes no candidate; trial points outside the
+ *      grid are rejected.  The candidate index is the triangle index, Generate batches
+ *      are batch_size triangles.
  */
 #include "fw_oracle.h"
 
@@ -789,7 +799,79 @@ int or_reduce(const or_candidate *cand, int n, double cos_patch, int max_patches
 /* ------------------------------------------------------------------------------------ */
 static void ensure_nodes(or_world *w);
 
+/* R15: local minimisation of phi over the face (a, b, c), all in the SDF's frame.
+ * Returns 1 with the minimiser x, phi and gradient there; 0 when the centroid is outside
+ * the grid.  *margin: smallest |phi_trial - phi| over the step decisions. */
+static int tri_minimise(const grid_t *g, const double a[3], const double b[3], const double c[3], int iters,
+                        double x[3], double *phi, double grad[3], double *margin) {
+    double e1[3], e2[3], e3[3], nt[3];
+    v_sub(b, a, e1); v_sub(c, a, e2); v_sub(c, b, e3);
+    v_cross(e1, e2, nt);
+    double ntn = v_norm(nt);
+    for (int k = 0; k < 3; ++k) x[k] = (a[k] + b[k] + c[k]) / 3.0;
+    *margin = INFINITY;
+    if (!trilinear(g, x, phi, grad, NULL)) return 0;
+    if (ntn > 0.0) v_scale(nt, 1.0 / ntn, nt);
+    double s = 0.5 * fmax(v_norm(e1), fmax(v_norm(e2), v_norm(e3)));
+    for (int it = 0; it < iters; ++it) {
+        /* the gradient's part in the face's plane */
+        double d[3], gn = v_dot(grad, nt);
+        for (int k = 0; k < 3; ++k) d[k] = grad[k] - gn * nt[k];
+        double dn = v_norm(d);
+        if (!(dn > 1e-9)) break;
+        double p[3], xt[3], pt, gt[3];
+        for (int k = 0; k < 3; ++k) p[k] = x[k] - (s / dn) * d[k];
+        or_closest_point_triangle(p, a, b, c, xt);
+        int ok = trilinear(g, xt, &pt, gt, NULL);
+        if (ok && fabs(pt - *phi) < *margin) *margin = fabs(pt - *phi);
+        if (ok && pt < *phi) {
+            memcpy(x, xt, sizeof xt); *phi = pt; memcpy(grad, gt, sizeof gt);
+            s *= 1.5;
+        } else {
+            s *= 0.5;
+        }
+    }
+    return 1;
+}
+
+/* the face of body a's mesh, in body b's (SDF) frame */
+static void tri_in_b(const asset_t *aa, int t, const double RA[9], const double pA[3], const double RBt[9],
+                     const double pB[3], double v[3][3]) {
+    for (int k = 0; k < 3; ++k) {
+        double s[3], xw[3], d[3];
+        load3(aa->V + 3 * aa->T[3 * t + k], s);
+        m_vec(RA, s, xw); v_add(xw, pA, xw);
+        v_sub(xw, pB, d); m_vec(RBt, d, v[k]);
+    }
+}
+
+static int generate_tri_candidates(const or_world *w, const pair_t *P, cand_t *out, margin_t *m) {
+    const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
+    const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
+    double RA[9], RB[9], RBt[9];
+    q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+    int n = 0;
+    for (int t = 0; t < aa->nt; ++t) {
+        double v[3][3], x[3], phi, g[3], mg;
+        tri_in_b(aa, t, RA, A->p, RBt, B->p, v);
+        if (!tri_minimise(&ab->grid, v[0], v[1], v[2], w->cfg.tri_iters, x, &phi, g, &mg)) continue;
+        mark_len(m, mg);
+        double gn = v_norm(g);
+        if (gn < 1e-12) continue;
+        mark_len(m, phi - w->cfg.contact_offset);
+        if (!(phi < w->cfg.contact_offset)) continue;
+        double nb[3];
+        v_scale(g, 1.0 / gn, nb);
+        cand_t *c = &out[n++];
+        c->idx = t; c->phi = phi;
+        m_vec(RB, x, c->x); v_add(c->x, B->p, c->x);
+        m_vec(RB, nb, c->n);
+    }
+    return n;
+}
+
 static int generate_candidates(const or_world *w, const pair_t *P, cand_t *out, margin_t *m) {
+    if (w->cfg.contact_gen == 1) return generate_tri_candidates(w, P, out, m);
     const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
     const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
     double RA[9], RB[9], RBt[9];
@@ -820,7 +902,8 @@ static int generate_candidates(const or_world *w, const pair_t *P, cand_t *out, 
 static void detect_pair(or_world *w, int pi) {
     const pair_t *P = &w->pairs[pi];
     const asset_t *aa = &w->assets[w->bodies[P->a].asset];
-    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (aa->ns > 0 ? aa->ns : 1));
+    const int n_src = w->cfg.contact_gen == 1 ? aa->nt : aa->ns;
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (n_src > 0 ? n_src : 1));
     margin_t m = {INFINITY, INFINITY};
     int nc = generate_candidates(w, P, c, &m);
     pair_contacts_t *pc = &w->pc[pi];
@@ -854,6 +937,30 @@ static void ensure_nodes(or_world *w) {
             const asset_t *aa = &w->assets[A->asset];
             double RA[9], RB[9], RBt[9];
             q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+            if (w->cfg.contact_gen == 1) {   /* every cell a face's bounding box touches */
+                for (int t = 0; t < aa->nt; ++t) {
+                    double v[3][3];
+                    tri_in_b(aa, t, RA, A->p, RBt, B->p, v);
+                    int c0[3], c1[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double lo = fmin(v[0][a], fmin(v[1][a], v[2][a])), hi = fmax(v[0][a], fmax(v[1][a], v[2][a]));
+                        c0[a] = (int)floor((lo - g->lo[a]) / g->h); c1[a] = (int)floor((hi - g->lo[a]) / g->h);
+                        if (c0[a] < 0) c0[a] = 0;
+                        if (c1[a] > g->dims[a] - 2) c1[a] = g->dims[a] - 2;
+                    }
+                    for (int k = c0[2]; k <= c1[2]; ++k)
+                        for (int j = c0[1]; j <= c1[1]; ++j)
+                            for (int i = c0[0]; i <= c1[0]; ++i)
+                                for (int q = 0; q < 8; ++q) {
+                                    long long id = gidx(g, i + (q & 1), j + ((q >> 1) & 1), k + ((q >> 2) & 1));
+                                    if (g->done[id]) continue;
+                                    g->done[id] = 2;
+                                    if (nn == cap) { cap *= 2; need = (long long *)realloc(need, sizeof(long long) * cap); }
+                                    need[nn++] = id;
+                                }
+                }
+                continue;
+            }
             for (int i = 0; i < aa->ns; ++i) {
                 double s[3], xw[3], xb[3], d[3];
                 load3(aa->S + 3 * i, s);
@@ -926,7 +1033,8 @@ int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int ca
     ensure_nodes(w);
     const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
     const asset_t *aa = &w->assets[w->bodies[P->a].asset];
-    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (aa->ns > 0 ? aa->ns : 1));
+    const int n_src = w->cfg.contact_gen == 1 ? aa->nt : aa->ns;
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (n_src > 0 ? n_src : 1));
     margin_t m = {INFINITY, INFINITY};
     int n = generate_candidates(w, P, c, &m);
     for (int i = 0; i < n && i < cap; ++i) {
@@ -937,6 +1045,30 @@ int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int ca
     *n_out = n;
     free(c);
     return n > cap ? -1 : 0;
+}
+
+int or_tri_contacts(or_world *w, int env, int pair, double *x, double *phi, double *n, int *valid,
+                    double *margin) {
+    ensure_nodes(w);
+    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
+    const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
+    double RA[9], RB[9], RBt[9];
+    q_to_m(A->q, RA); q_to_m(B->q, RB); m_transpose(RB, RBt);
+    for (int t = 0; t < aa->nt; ++t) {
+        double v[3][3], xb[3], p, g[3], mg;
+        tri_in_b(aa, t, RA, A->p, RBt, B->p, v);
+        int ok = tri_minimise(&ab->grid, v[0], v[1], v[2], w->cfg.tri_iters, xb, &p, g, &mg);
+        double gn = ok ? v_norm(g) : 0.0;
+        valid[t] = ok && gn >= 1e-12;
+        phi[t] = ok ? p : 0.0;
+        margin[t] = mg;
+        m_vec(RB, xb, x + 3 * t); v_add(x + 3 * t, B->p, x + 3 * t);
+        double nb[3] = {0, 0, 0};
+        if (valid[t]) v_scale(g, 1.0 / gn, nb);
+        m_vec(RB, nb, n + 3 * t);
+    }
+    return 0;
 }
 
 int or_collide(or_world *w) {

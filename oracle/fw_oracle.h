@@ -79,6 +79,9 @@ typedef struct {
     double margin_len;       /* decision margin (m) below which a pair is not comparable */
     double margin_dot;       /* decision margin (dimensionless) */
     int n_threads;           /* OpenMP threads (0 = default) */
+    int contact_gen;         /* 0: one candidate per surface sample; 1: one per triangle of
+                                the point body's mesh, by local minimisation (R15) */
+    int tri_iters;           /* steps of that minimisation */
 } or_config;
 
 typedef struct {             /* same layout as the ABI's fw_body_desc (104 bytes) */
@@ -138,6 +141,12 @@ int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int 
                   double *gnorm);
 /* The pair's candidates (phi < contact_offset) rounded to float, in sample order. */
 int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int cap, int *n_out);
+/* Per triangle of the point body's mesh (R15), at the current poses: the minimiser on the
+ * face (world), phi there, the world normal, valid (0: outside the grid or vanishing
+ * gradient) and the smallest |phi_trial - phi| of the step decisions taken (the margin of
+ * the result against rounding).  Arrays of n_tris (x3 for x, n). */
+int or_tri_contacts(or_world *w, int env, int pair, double *x, double *phi, double *n, int *valid,
+                    double *margin);
 /* Contact detection + reduction at the current state. */
 int or_collide(or_world *w);
 int or_get_contacts(const or_world *w, int env, or_contact *out, int cap, int *n_out,

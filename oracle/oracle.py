@@ -36,7 +36,8 @@ class OrConfig(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("dt", C.c_double), ("contact_offset", C.c_double),
                 ("cos_patch", C.c_double), ("max_patches", C.c_int), ("batch_size", C.c_int),
                 ("baumgarte", C.c_double), ("n_vel_iters", C.c_int), ("max_angvel", C.c_double),
-                ("margin_len", C.c_double), ("margin_dot", C.c_double), ("n_threads", C.c_int)]
+                ("margin_len", C.c_double), ("margin_dot", C.c_double), ("n_threads", C.c_int),
+                ("contact_gen", C.c_int), ("tri_iters", C.c_int)]
 
 
 CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("phi", np.float64),
@@ -101,6 +102,7 @@ def lib():
             L.or_bake_seconds.restype = C.c_double
             L.or_query_pair.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _i32, _f64]
             L.or_pair_candidates.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
+            L.or_tri_contacts.argtypes = [vp, C.c_int, C.c_int, _f64, _f64, _f64, _i32, _f64]
             L.or_diff_record.argtypes = [vp, C.c_int, C.c_int]
             L.or_diff_replay.argtypes = [vp]
             L.or_diff_adjoint.argtypes = [vp] + [_f64] * 10
@@ -219,6 +221,8 @@ class OracleWorld:
         cfg.baumgarte = over.get("baumgarte", getattr(sim, "baumgarte", 0.2))
         cfg.n_vel_iters = over.get("n_vel_iters", getattr(sim, "n_vel_iters", 0))
         cfg.max_angvel = over.get("max_angvel", getattr(sim, "max_angvel", 0.0))
+        cfg.contact_gen = over.get("contact_gen", 0)
+        cfg.tri_iters = over.get("tri_iters", 16)
         cfg.margin_len = margin_len
         cfg.margin_dot = margin_dot
         cfg.n_threads = n_threads
@@ -391,6 +395,15 @@ class OracleWorld:
         lib().or_query_pair(self.h, env, pair, phi, nrm, valid, gn)
         self.last_gnorm = gn
         return phi, nrm, valid.astype(bool)
+
+    def tri_contacts(self, env: int, pair: int, n_tris: int):
+        """Per triangle of the point body's mesh (R15): minimiser (world), phi, world normal,
+        valid, and the smallest phi gap among the descent's accept/reject decisions."""
+        x, n = np.zeros((n_tris, 3)), np.zeros((n_tris, 3))
+        phi, margin = np.zeros(n_tris), np.zeros(n_tris)
+        valid = np.zeros(n_tris, np.int32)
+        lib().or_tri_contacts(self.h, env, pair, x, phi, n, valid, margin)
+        return x, phi, n, valid.astype(bool), margin
 
     def pair_candidates(self, env: int, pair: int, cap: int = 1 << 20) -> np.ndarray:
         out = np.zeros(cap, CANDIDATE_DTYPE)
