@@ -73,6 +73,13 @@ typedef struct {
     int n_vel_iters;            /* bias-free sweeps after integration; default 0 */
     float max_angvel;           /* |omega| clamp at integration, 0 = off; default 0 */
     int sdf_fp16;               /* 1: look up FP16 copies of the grids (phi/h); default 0 */
+    int contact_gen;            /* 0: one candidate per surface sample of the point body
+                                   (default); 1: one per triangle of its mesh, the minimiser
+                                   of the SDF over the face by projected gradient descent
+                                   with adaptive steps (Sec. III-A); Generate batches are
+                                   then 1024 triangles and a contact's `sample` is the
+                                   triangle index */
+    int tri_iters;              /* descent steps per triangle (contact_gen = 1); default 16 */
     int device;                 /* CUDA device ordinal, default 0 */
     void *cuda_stream;          /* cudaStream_t to enqueue on, NULL: the world's own */
 } fw_config;
@@ -229,6 +236,18 @@ FW_API fw_status fw_set_state(fw_world *w, const float *pos, const float *quat,
  * grad = 0.  Synchronises when device_ptrs = 0. */
 FW_API fw_status fw_query_sdf(fw_world *w, int asset_id, const float *pts, int n, float *phi,
                               float *grad, int device_ptrs);
+
+/* Per-triangle contact generation of one pair at the current poses (contact_gen = 1's
+ * Generate step, whatever the world's contact_gen): for each triangle of the point body's
+ * mesh, the minimiser of body B's SDF over the face by projected gradient descent with
+ * adaptive steps, tri_iters steps (Sec. III-A; centroid start, first step half the
+ * longest edge, accepted steps grow by 1.5, rejected ones halve, closest-point
+ * projection onto the face).  Outputs per triangle (n_tris entries): x (3 floats, world)
+ * the minimiser on the face, phi there (+inf when the centroid lies outside B's grid or
+ * the gradient vanishes), normal (3 floats, world, the unit SDF gradient).  Host or
+ * device arrays per device_ptrs; synchronises for host arrays. */
+FW_API fw_status fw_tri_contacts(fw_world *w, int env, int pair, float *x, float *phi, float *normal,
+                                 int device_ptrs);
 
 /* The narrow phase of one pair at the current poses, for every sample point of body a:
  * phi (n_samples) and the world normal (n_samples x 3); phi = +inf where the point is

@@ -20,6 +20,7 @@ struct AssetHost {
     std::vector<float> S;   // samples, 3 per point
     double density = 0, mass = 0, com[3] = {0, 0, 0}, I[9] = {0};
     float4 *d_samples = nullptr;
+    float4 *d_tri = nullptr;      // 3 per triangle, asset frame
     bool has_sdf = false;
     float lo[3] = {0, 0, 0}, h = 0;
     int dims[3] = {0, 0, 0};
@@ -187,6 +188,8 @@ AssetDev asset_view(const AssetHost &A, bool fp16) {
     memset(&g, 0, sizeof g);
     g.samples = A.d_samples;
     g.ns = (int)(A.S.size() / 3);
+    g.tri = A.d_tri;
+    g.nt = (int)(A.T.size() / 3);
     g.grid = A.d_grid;
     g.cell32 = fp16 ? nullptr : A.d_cell32;
     g.cell16 = fp16 ? A.d_cell16 : nullptr;
@@ -218,6 +221,12 @@ fw_status upload_assets(fw_world *w) {
 }
 
 int cap_pair(const fw_world *w) { return w->cfg.max_patches * kSlots; }
+
+// candidate sources of a pair's point body: its samples, or its triangles
+long long pair_sources(const fw_world *w, int asset_a) {
+    const AssetHost &A = w->assets[asset_a];
+    return (long long)(w->cfg.contact_gen == 1 ? A.T.size() / 3 : A.S.size() / 3);
+}
 
 // (Re)builds the device copies of the topology, keeping the device state of bodies that
 // are already there.
@@ -259,8 +268,7 @@ fw_status ensure_device(fw_world *w) {
         CK(cudaMalloc(&w->d_counts, sizeof(int) * np));
         CK(cudaMemsetAsync(w->d_counts, 0, sizeof(int) * np, w->stream));
         long long sl = 0;
-        for (auto &P : w->pairs)
-            sl = std::max(sl, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
+        for (auto &P : w->pairs) sl = std::max(sl, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
         w->scratch_len = std::max(sl, 2LL);
         CK(cudaMalloc(&w->d_scratch, sizeof(float4) * w->scratch_len));
         // work list: one item per (pair, Generate batch)
@@ -268,7 +276,7 @@ fw_status ensure_device(fw_world *w) {
         std::vector<int> item0(np + 1, 0);
         for (int pi = 0; pi < np; ++pi) {
             item0[pi] = (int)items.size();
-            const long long ns = (long long)(w->assets[w->pairs[pi].asset_a].S.size() / 3);
+            const long long ns = pair_sources(w, w->pairs[pi].asset_a);
             for (long long b = 0; b * kBatch < ns; ++b) items.push_back(make_int2(pi, (int)b));
         }
         item0[np] = (int)items.size();
@@ -308,6 +316,8 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.counts = w->d_counts;
     p.scratch = w->d_scratch;
     p.items = w->d_items;
+    p.contact_gen = w->cfg.contact_gen;
+    p.tri_iters = w->cfg.tri_iters;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;
     p.cand = w->d_cand;
@@ -466,6 +476,8 @@ void fw_config_default(fw_config *c) {
     c->n_vel_iters = 0;
     c->max_angvel = 0.0f;
     c->sdf_fp16 = 0;
+    c->contact_gen = 0;
+    c->tri_iters = 16;
     c->device = 0;
     c->cuda_stream = nullptr;
 }
@@ -474,7 +486,8 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (!cfg || !out) return FW_ERR_ARG;
     *out = nullptr;
     if (cfg->batch_size != kBatch || cfg->patch_dirs != kSlots - 1 || cfg->max_patches < 1 ||
-        cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0))
+        cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0) || cfg->contact_gen < 0 || cfg->contact_gen > 1 ||
+        cfg->tri_iters < 0 || cfg->tri_iters > 1024)
         return FW_ERR_ARG;
     fw_world *w = new fw_world();
     w->cfg = *cfg;
@@ -509,7 +522,7 @@ fw_status fw_destroy(fw_world *w) {
     drop_graph(w);
     diff_free(w);
     for (auto &A : w->assets) {
-        dfree(A.d_samples); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
+        dfree(A.d_samples); dfree(A.d_tri); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
     }
     dfree(w->d_assets);
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
@@ -527,7 +540,7 @@ fw_status fw_destroy(fw_world *w) {
 fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const int *tris, int n_tris,
                             const float *sample_pts, int n_samples, float density, int *asset_id_out) {
     if (!ready(w)) return FW_ERR_ARG;
-    if (!verts || !tris || n_verts < 3 || n_tris < 1 || n_samples < 0 || n_samples > (1 << 24) ||
+    if (!verts || !tris || n_verts < 3 || n_tris < 1 || n_tris > (1 << 24) || n_samples < 0 || n_samples > (1 << 24) ||
         (n_samples > 0 && !sample_pts) || !(density > 0))
         return fail(w, FW_ERR_ARG, "fw_add_mesh_asset: bad argument");
     for (int i = 0; i < 3 * n_tris; ++i)
@@ -544,6 +557,13 @@ fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const 
         for (int i = 0; i < n_samples; ++i) s4[i] = make_float4(A.S[3 * i], A.S[3 * i + 1], A.S[3 * i + 2], 0.f);
         CK(cudaMalloc(&A.d_samples, sizeof(float4) * n_samples));
         CK(cudaMemcpy(A.d_samples, s4.data(), sizeof(float4) * n_samples, cudaMemcpyHostToDevice));
+    }
+    {   // the faces, for the per-triangle contact generator
+        std::vector<float4> t4(3 * (size_t)n_tris);
+        for (size_t k = 0; k < t4.size(); ++k)
+            t4[k] = make_float4(A.V[3 * A.T[k]], A.V[3 * A.T[k] + 1], A.V[3 * A.T[k] + 2], 0.f);
+        CK(cudaMalloc(&A.d_tri, sizeof(float4) * t4.size()));
+        CK(cudaMemcpy(A.d_tri, t4.data(), sizeof(float4) * t4.size(), cudaMemcpyHostToDevice));
     }
     w->assets.push_back(std::move(A));
     w->assets_dirty = true;
@@ -744,7 +764,8 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
         for (int k = 0; k < n_pairs; ++k) {
             const AssetHost &Aa = w->assets[bd[e * n_per_env + pairs[2 * k]].asset];
             const AssetHost &Ab = w->assets[bd[e * n_per_env + pairs[2 * k + 1]].asset];
-            if (Aa.S.empty()) return fail(w, FW_ERR_STATE, "fw_add_env_bodies: point body has no sample points");
+            if (Aa.S.empty() && w->cfg.contact_gen == 0)   // per-triangle generation needs only the mesh
+                return fail(w, FW_ERR_STATE, "fw_add_env_bodies: point body has no sample points");
             if (!Ab.has_sdf) return fail(w, FW_ERR_STATE, "fw_add_env_bodies: SDF body has no baked SDF");
         }
     // validate everything before appending anything
@@ -758,8 +779,7 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
     }
     const int e0 = (int)w->envs.size();
     long long scratch = 0, rows = 0;
-    for (auto &P : w->pairs)
-        scratch = std::max(scratch, (long long)P.scratch_off + 2LL * (long long)(w->assets[P.asset_a].S.size() / 3));
+    for (auto &P : w->pairs) scratch = std::max(scratch, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
     for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap);
     for (int e = 0; e < n_envs; ++e) {
         EnvDev E;
@@ -830,7 +850,7 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
             P.env = e0 + e;
             P.mu = (float)std::sqrt((double)w->props[P.a].mu * (double)w->props[P.b].mu);
             P.scratch_off = (int)scratch;
-            scratch += 2LL * (long long)(w->assets[P.asset_a].S.size() / 3);
+            scratch += 2LL * pair_sources(w, P.asset_a);
             if (scratch > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many samples in total");
             w->pairs.push_back(P);
         }
@@ -1026,6 +1046,30 @@ fw_status fw_query_pair(fw_world *w, int env, int pair, float *phi, float *norma
     CK(launch_query_pair(p, pi, d, d + ns, w->stream, ns));
     CK(cudaMemcpyAsync(phi, d, sizeof(float) * ns, cudaMemcpyDeviceToHost, w->stream));
     CK(cudaMemcpyAsync(normal, d + ns, sizeof(float) * 3 * (size_t)ns, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    cudaFree(d);
+    return FW_OK;
+}
+
+fw_status fw_tri_contacts(fw_world *w, int env, int pair, float *x, float *phi, float *normal, int device_ptrs) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size() || pair < 0 || pair >= w->envs[env].n_pairs || !x || !phi || !normal)
+        return fail(w, FW_ERR_ARG, "fw_tri_contacts: bad argument");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const int pi = w->envs[env].first_pair + pair;
+    const int nt = (int)(w->assets[w->pairs[pi].asset_a].T.size() / 3);
+    const SimParams p = sim_params(w, w->cfg.dt, 0);
+    if (device_ptrs) {
+        CK(launch_tri_pair(p, pi, x, phi, normal, w->stream, nt));
+        return FW_OK;
+    }
+    float *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(float) * 7 * (size_t)nt));
+    CK(launch_tri_pair(p, pi, d, d + 3 * (size_t)nt, d + 4 * (size_t)nt, w->stream, nt));
+    CK(cudaMemcpyAsync(x, d, sizeof(float) * 3 * (size_t)nt, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemcpyAsync(phi, d + 3 * (size_t)nt, sizeof(float) * nt, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemcpyAsync(normal, d + 4 * (size_t)nt, sizeof(float) * 3 * (size_t)nt, cudaMemcpyDeviceToHost, w->stream));
     CK(cudaStreamSynchronize(w->stream));
     cudaFree(d);
     return FW_OK;

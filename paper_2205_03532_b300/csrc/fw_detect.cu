@@ -129,6 +129,81 @@ __device__ __forceinline__ bool query_sample(const PairXf &X, const AssetDev &gb
     return in && (gg >= 1e-24f);
 }
 
+// Closest point of the triangle (a, b, c) to p: p's Voronoi region among the vertices,
+// the edges and the face, then the point of that feature (the standard construction of
+// real-time collision detection; Ericson, Sec. 5.1.5).
+__device__ V3 tri_closest(V3 p, V3 a, V3 b, V3 c) {
+    const V3 ab = b - a, ac = c - a, ap = p - a;
+    const float d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= 0.0f && d2 <= 0.0f) return a;
+    const V3 bp = p - b;
+    const float d3 = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3 >= 0.0f && d4 <= d3) return b;
+    const V3 cp = p - c;
+    const float d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= 0.0f && d5 <= d6) return c;
+    const float vc = d1 * d4 - d3 * d2;                       // weight of c
+    if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) return a + (d1 / (d1 - d3)) * ab;
+    const float vb = d5 * d2 - d1 * d6;                       // weight of b
+    if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) return a + (d2 / (d2 - d6)) * ac;
+    const float va = d3 * d6 - d5 * d4;                       // weight of a
+    if (va <= 0.0f && d4 - d3 >= 0.0f && d5 - d6 >= 0.0f)
+        return b + ((d4 - d3) / ((d4 - d3) + (d5 - d6))) * (c - b);
+    const float den = 1.0f / (va + vb + vc);
+    return a + (vb * den) * ab + (vc * den) * ac;
+}
+
+// Per-triangle Generate (Sec. III-A): the minimiser of the SDF over the face (a, b, c),
+// all in the SDF's frame, by projected gradient descent with adaptive steps -- start at
+// the centroid with step length half the longest edge; each step moves against the
+// gradient's in-plane part, projects onto the face and is accepted if phi decreases (step
+// x 1.5), else rejected (step x 0.5); it ends after `iters` steps or when the in-plane
+// gradient falls below 1e-9.  False when the centroid lies outside the grid; trial points
+// outside the grid are rejected.
+__device__ bool tri_minimise(const AssetDev &gb, V3 a, V3 b, V3 c, int iters, V3 &x, float &phi, V3 &g) {
+    const V3 e1 = b - a, e2 = c - a, e3 = c - b;
+    V3 nt = cross(e1, e2);
+    const float nn = dot(nt, nt);
+    nt = nn > 0.0f ? rsqrtf(nn) * nt : v3(0.0f, 0.0f, 0.0f);
+    x = (1.0f / 3.0f) * ((a + b) + c);
+    if (!sdf_lookup_any(gb, x, phi, g)) return false;
+    float s = 0.5f * sqrtf(fmaxf(dot(e1, e1), fmaxf(dot(e2, e2), dot(e3, e3))));
+    for (int it = 0; it < iters; ++it) {
+        const V3 d = g - dot(g, nt) * nt;
+        const float dd = dot(d, d);
+        if (!(dd > 1e-18f)) break;
+        const V3 xt = tri_closest(x - (s * rsqrtf(dd)) * d, a, b, c);
+        float pt;
+        V3 gt;
+        if (sdf_lookup_any(gb, xt, pt, gt) && pt < phi) {
+            x = xt; phi = pt; g = gt;
+            s *= 1.5f;
+        } else {
+            s *= 0.5f;
+        }
+    }
+    return true;
+}
+
+// Triangle t of body a's mesh, minimised against body b's SDF: world point on the face,
+// world normal, phi.  False when there is no candidate point (centroid outside the grid,
+// vanishing gradient).
+__device__ __forceinline__ bool tri_sample(const PairXf &X, const AssetDev &ga, const AssetDev &gb, int t, int iters,
+                                           V3 &xw, V3 &nw, float &phi) {
+    V3 v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 s = __ldg(&ga.tri[3 * t + k]);
+        v[k] = mul_t(X.RB, mul(X.RA, v3(s.x, s.y, s.z)) + X.pA - X.pB);
+    }
+    V3 x, g;
+    const bool in = tri_minimise(gb, v[0], v[1], v[2], iters, x, phi, g);
+    const float gg = dot(g, g);
+    nw = mul(X.RB, rsqrtf(fmaxf(gg, 1e-30f)) * g);
+    xw = mul(X.RB, x) + X.pB;
+    return in && (gg >= 1e-24f);
+}
+
 __device__ __forceinline__ unsigned long long slot_key(float score, int sample) {
     return ((unsigned long long)ord_f32(score) << 32) | (unsigned)(0xFFFFFFFFu - (unsigned)sample);
 }
@@ -521,6 +596,7 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 }
 
 // ---------------------------------------------------------------------------------------
+template <bool kTri>
 __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const int item = blockIdx.x;
     const int2 it = p.items[item];
@@ -539,9 +615,14 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
 #pragma unroll
     for (int u = 0; u < kQueryPerThread; ++u) {
         const int i = base + u * kQueryThreads + tid;
-        const int ic = i < ga.ns ? i : ga.ns - 1;
-        const float4 s = __ldg(&ga.samples[ic]);
-        ok[u] = query_sample(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
+        if (kTri) {   // one candidate per triangle of the mesh
+            const int ic = i < ga.nt ? i : ga.nt - 1;
+            ok[u] = tri_sample(X, ga, gb, ic, p.tri_iters, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.nt);
+        } else {      // one per surface sample
+            const int ic = i < ga.ns ? i : ga.ns - 1;
+            const float4 s = __ldg(&ga.samples[ic]);
+            ok[u] = query_sample(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
+        }
     }
     // compaction in sample order: local sample u * 256 + warp * 32 + lane
     __shared__ int cnt[kQueryPerThread * kQueryWarps];
@@ -634,6 +715,23 @@ __global__ void query_sdf_kernel(AssetDev g, const float *pts, int n, float *phi
         phi[i] = __int_as_float(0x7f800000);
         grad[3 * i] = 0.f; grad[3 * i + 1] = 0.f; grad[3 * i + 2] = 0.f;
     }
+}
+
+__global__ void tri_pair_kernel(SimParams p, int pi, float *x, float *phi, float *nrm) {
+    const PairDev P = p.pairs[pi];
+    const AssetDev ga = p.assets[P.asset_a];
+    const AssetDev gb = p.assets[P.asset_b];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ga.nt) return;
+    PairXf X;
+    load_pose(p, P.a, X.RA, X.pA);
+    load_pose(p, P.b, X.RB, X.pB);
+    V3 xw, nw;
+    float f;
+    const bool ok = tri_sample(X, ga, gb, t, p.tri_iters, xw, nw, f);
+    x[3 * t] = xw.x; x[3 * t + 1] = xw.y; x[3 * t + 2] = xw.z;
+    phi[t] = ok ? f : __int_as_float(0x7f800000);
+    nrm[3 * t] = ok ? nw.x : 0.f; nrm[3 * t + 1] = ok ? nw.y : 0.f; nrm[3 * t + 2] = ok ? nw.z : 0.f;
 }
 
 __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
@@ -772,7 +870,16 @@ cudaError_t prepare_detect(int max_patches) {
 
 cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    query_kernel<<<p.n_items, kQueryThreads, 0, s>>>(p);
+    if (p.contact_gen == 1)
+        query_kernel<true><<<p.n_items, kQueryThreads, 0, s>>>(p);
+    else
+        query_kernel<false><<<p.n_items, kQueryThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt) {
+    if (nt <= 0) return cudaSuccess;
+    tri_pair_kernel<<<(nt + 255) / 256, 256, 0, s>>>(p, pair, x, phi, nrm);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,8 @@ struct AssetDev {
     float h, inv_h, inv_h_lo; // inv_h + inv_h_lo = 1/h to ~1e-14 relative
     int dims[3];
     int ns;
-    int pad_;
+    int nt;                  // triangles of the mesh
+    const float4 *tri;       // 3 per triangle: asset-frame vertices (x, y, z, 0)
 };
 
 struct BodyProps {           // constant per body
@@ -113,6 +114,8 @@ struct SimParams {
     int n_items;
     float4 *cand;                          // n_items x kBatch x 2: (x_w, phi), (n_w, sample)
     int *cand_count;                       // n_items
+    int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
+    int tri_iters;                         // descent steps per triangle
 };
 
 // launchers (defined in the .cu files)
@@ -174,6 +177,7 @@ cudaError_t prepare_solve(int optin, int max_dyn[4]);
 SolveShape solve_shape(int n_envs, int lam_cap, int groups, int warps, const int max_dyn[4], int n_sm);
 cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
+cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt);
 cudaError_t measure_l2_read(int device, long long bytes, int iters, float *gbs);
 
 }  // namespace fw

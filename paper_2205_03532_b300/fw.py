@@ -25,7 +25,7 @@ STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_OOM", -3: "FW_ERR_CUDA", -4:
 ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_asset", "fw_bake_sdf",
                  "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
-                 "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
+                 "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_tri_contacts", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
@@ -44,7 +44,8 @@ class FwConfig(C.Structure):
                 ("cos_patch", C.c_float), ("max_patches", C.c_int), ("patch_dirs", C.c_int),
                 ("batch_size", C.c_int),
                 ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
-                ("sdf_fp16", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("sdf_fp16", C.c_int), ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("device", C.c_int),
+                ("cuda_stream", C.c_void_p)]
 
 
 CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("pair", np.int32),
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "fw_set_state": (st, [vp, vp, vp, vp, vp, i]),
         "fw_query_sdf": (st, [vp, i, vp, i, vp, vp, i]),
         "fw_query_pair": (st, [vp, i, i, vp, vp, i]),
+        "fw_tri_contacts": (st, [vp, i, i, vp, vp, vp, i]),
         "fw_reduce": (st, [vp, vp, i, vp, i, C.POINTER(i), C.POINTER(i)]),
         "fw_reduce_noalloc": (st, [vp, vp, i, vp, i, vp]),
         "fw_sync": (st, [vp]),
@@ -297,6 +299,14 @@ class World:
         phi, nrm = np.zeros(n_samples, np.float32), np.zeros((n_samples, 3), np.float32)
         self._check(self.lib.fw_query_pair(self.h, env, pair, phi.ctypes.data, nrm.ctypes.data, 0))
         return phi, nrm
+
+    def tri_contacts(self, env: int, pair: int, n_tris: int):
+        """Per triangle of the pair's point body: minimiser on the face (world), phi (+inf:
+        no candidate point), world normal (fw_tri_contacts)."""
+        x, nrm = np.zeros((n_tris, 3), np.float32), np.zeros((n_tris, 3), np.float32)
+        phi = np.zeros(n_tris, np.float32)
+        self._check(self.lib.fw_tri_contacts(self.h, env, pair, x.ctypes.data, phi.ctypes.data, nrm.ctypes.data, 0))
+        return x, phi, nrm
 
     def reduce(self, cands: np.ndarray):
         c = np.ascontiguousarray(cands).view(CANDIDATE_DTYPE)
