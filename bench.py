@@ -44,6 +44,7 @@ SOLVE_FLOPS_PER_CONTACT_PREP = 300    # rows, effective masses, couplings, bias
 QUERY_BYTES_PER_SAMPLE = 16           # float4 sample point
 QUERY_BYTES_PER_CORNER = {False: 4, True: 2}   # 8 grid corners per query, float32 / float16
 CANDIDATE_BYTES = 32                  # (x, phi), (n, sample) written by the query, read by the reduction
+FACE_BYTES = 48                       # three float4 vertices of a face (per-triangle contact generation)
 CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
@@ -125,6 +126,33 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# workload -> (scene builder (n_envs, seed), default envs, name, SDF description, data description)
+WORKLOADS = {
+    "nut_bolt": ("nut_bolt_scene", 1000, "nut_bolt_m16", "256^3",
+                 "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)"),
+    "mixed": ("mixed_nut_bolt_scene", 4096, "mixed_nut_bolt_m8_m20", "128^3-256^3",
+              "synthetic (procedural ISO M8-M20 nut/bolt meshes, sizes and poses seeded)"),
+    "gears": ("gear_scene", 2048, "gear_train_z20_z30_z40", "256^3",
+              "synthetic (procedural involute spur gears, seeded phases)"),
+}
+
+
+def make_scene(workload: str, n_envs: int, seed: int):
+    from paper_2205_03532_b300 import scenes as S
+    return getattr(S, WORKLOADS[workload][0])(n_envs=n_envs, seed=seed)
+
+
+def pair_sources(sc, per_triangle: bool) -> int:
+    """Candidate sources of one substep over all envs: per pair, the samples (or faces) of
+    its point body's asset."""
+    n = 0
+    for g in sc.groups:
+        for a, _ in g.pairs:
+            A = sc.assets[int(g.bodies["asset"][0, a])]
+            n += len(g.bodies) * (len(A.tris) if per_triangle else len(A.samples))
+    return n
+
+
 def env_seed(seed: int, rank: int) -> int:
     """Scene seed of a rank: every rank simulates its own envs (weak scaling, no exchange)."""
     return seed + 1000 * rank
@@ -153,16 +181,15 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(n_envs: int, seed: int, frames: int = 2):
+def cpu_baseline(n_envs: int, seed: int, frames: int = 2, workload: str = "nut_bolt"):
     """The FP64 oracle as it stands, on host cores, on a bounded sample of the workload:
-    n_envs nut-bolt envs (0: one per core, the oracle parallelises over envs) for `frames`
+    n_envs envs of it (0: one per core, the oracle parallelises over envs) for `frames`
     frames after one warm-up detection, then one frame of the same world on one core; the
     oracle's lazy SDF bake (set-up work on both sides) is excluded from both times."""
     from oracle import oracle as O
-    from paper_2205_03532_b300 import scenes as S
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     n_envs = n_envs if n_envs > 0 else cores
-    sc = S.nut_bolt_scene(n_envs=n_envs, seed=seed)
+    sc = make_scene(workload, n_envs, seed)
     w = O.world_from_scene(sc, lazy_bake=True)
     w.collide()
 
@@ -187,10 +214,11 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    from paper_2205_03532_b300 import scenes as S
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     n = args.ref_envs if args.ref_envs > 0 else cores   # one env per core: the oracle parallelises over envs
-    sc = S.nut_bolt_scene(n_envs=n, seed=args.seed)
+    wl = args.workload if args.workload in WORKLOADS else "nut_bolt"
+    _, n_full, wl_name, sdf_desc, data_desc = WORKLOADS[wl]
+    sc = make_scene(wl, n, args.seed)
     w = O.world_from_scene(sc, lazy_bake=True)
     w.collide()
     for _ in range(args.warmup):
@@ -205,13 +233,39 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "env-substeps/s", "value": v, "unit": "env-substeps/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)",
-           "config": {"workload": "nut_bolt_m16", "n_envs": n, "sample_of_envs": 1000, "sdf": "256^3 lazy",
-                      "substeps": 8, "iters": 32},
+           "data": data_desc,
+           "config": {"workload": wl_name, "n_envs": n, "sample_of_envs": n_full, "sdf": sdf_desc + " fp64 lazy",
+                      "substeps": sc.sim.n_substeps, "iters": sc.sim.n_iters},
            "cpu_baseline": {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle",
                             "sample": f"{n} envs per step, lazy SDF bake excluded"},
            "e2e": {"value": v, "unit": "env-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def single_pair_generate(sc, gen_cfg, fp16, dev, frames=5):
+    """Per-triangle contact generation for ONE nut-bolt pair (the first env of the scene):
+    the average query launch time over `frames` frames, after one warm-up frame.  This is
+    the latency of generating one pair's contacts, the figure the paper gives for its own
+    generator (Sec. III-A)."""
+    import torch
+    from paper_2205_03532_b300 import fw, scenes as S
+    g = sc.groups[0]
+    one = S.Scene(name=sc.name, assets=sc.assets, groups=[S.EnvGroup(bodies=g.bodies[:1].copy(), pairs=g.pairs)],
+                  sim=sc.sim)
+    w = fw.world_from_scene(one, fp16=fp16, device=dev, **gen_cfg)
+    w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    w.sync()
+    w.set_timing(True)
+    for _ in range(frames):
+        w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    tim = w.get_timings()
+    w.set_timing(False)
+    n_cand, n_cont = w.detect_stats()
+    faces = len(sc.assets[int(g.bodies["asset"][0, 0])].tris)
+    w.close()
+    return {"faces": faces, "generate_ms": tim["query_ms"] / max(tim["detect_launches"], 1),
+            "reduce_ms": tim["reduce_ms"] / max(tim["detect_launches"], 1),
+            "candidates": n_cand, "contacts": n_cont}
 
 
 def run_fw(args):
@@ -226,14 +280,16 @@ def run_fw(args):
     dev = local
     stream = torch.cuda.Stream(device=dev)
     t_setup = time.perf_counter()
-    if args.workload == "mixed":
-        sc = S.mixed_nut_bolt_scene(n_envs=args.envs if args.envs != 1000 else 4096, seed=env_seed(args.seed, rank))
-    else:
-        sc = S.nut_bolt_scene(n_envs=args.envs, seed=env_seed(args.seed, rank))
+    _, n_default, wl_name, sdf_desc, data_desc = WORKLOADS[args.workload]
+    sc = make_scene(args.workload, args.envs if args.envs > 0 else n_default, env_seed(args.seed, rank))
+    # the gear train's SDFs are stored in FP16 (FP32 interpolation and solve) unless --fp32
+    fp16 = bool(args.fp16 or (args.workload == "gears" and not args.fp32))
     sim = sc.sim
+    tri_mode = args.contact_gen == "triangles"
+    gen_cfg = {"contact_gen": 1, "tri_iters": args.tri_iters} if tri_mode else {}
     with torch.cuda.stream(stream):
         t_b = time.perf_counter()
-        w = fw.world_from_scene(sc, fp16=args.fp16, stream=stream.cuda_stream, device=dev)
+        w = fw.world_from_scene(sc, fp16=fp16, stream=stream.cuda_stream, device=dev, **gen_cfg)
         bake_s = time.perf_counter() - t_b
     n_env, n_body, n_pair = w.counts()
     nodes = tests = 0
@@ -291,16 +347,22 @@ def run_fw(args):
     sol_ms = tim["solve_ms"] / max(tim["solve_launches"], 1)
     n_cand, n_cont = w.detect_stats()          # of the last substep
     c_mean = n_cont / max(n_env, 1)
-    queries = sum(len(g.bodies) * len(sc.assets[int(g.bodies["asset"][0, 0])].samples) for g in sc.groups)
+    corner = QUERY_BYTES_PER_CORNER[fp16]
+    queries = pair_sources(sc, tri_mode)
+    if tri_mode:
+        # one candidate source per face of the point body's mesh: its three vertices and
+        # one SDF cell (the descent's further lookups stay in the cell's neighbourhood)
+        q_bytes = queries * (FACE_BYTES + 8 * corner) + n_cand * CANDIDATE_BYTES
+    else:
+        q_bytes = queries * (QUERY_BYTES_PER_SAMPLE + 8 * corner) + n_cand * CANDIDATE_BYTES
     ns = queries / max(n_pair, 1)
     hbm, sm_max, peak_kind = _peaks()
-    q_bytes = queries * (QUERY_BYTES_PER_SAMPLE + 8 * QUERY_BYTES_PER_CORNER[bool(args.fp16)]) + n_cand * CANDIDATE_BYTES
     r_bytes = n_cand * CANDIDATE_BYTES + n_cont * CONTACT_BYTES
     sol_flops = n_cont * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
     alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     src = _src_hash()
     # the table was taken on the default workload only (1000 M16 envs, FP32)
-    default_run = args.workload == "nut_bolt" and not args.fp16 and args.envs == 1000
+    default_run = args.workload == "nut_bolt" and not fp16 and sc.n_envs == 1000 and not tri_mode
     traffic = NCU_TRAFFIC.get(src, {}) if default_run else {}
     l2_traffic = NCU_L2.get(src, {}) if default_run else {}
     l2_gbs = fw.measure_l2_read(dev)   # untimed: the L2 roofline's denominator on this device
@@ -320,7 +382,7 @@ def run_fw(args):
     sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     kernels = {
         "query_kernel": dict(hbm_entry("query_kernel", q_bytes, qry_ms),
-                             queries_per_s=queries / (qry_ms * 1e-3)),
+                             **{("faces_per_s" if tri_mode else "queries_per_s"): queries / (qry_ms * 1e-3)}),
         "reduce_kernel": hbm_entry("reduce_kernel", r_bytes, red_ms),
         "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": sol_tf / alu_peak, "traffic": traffic.get("solve_kernel"),
@@ -332,6 +394,9 @@ def run_fw(args):
     dominant = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roof["kernel"] = dominant
+    single = None
+    if tri_mode:
+        single = single_pair_generate(sc, gen_cfg, fp16, dev)
     # ---- end to end through the public API with host buffers: state in, frame, state out
     pin = [torch.empty((n_body, k), dtype=torch.float32).pin_memory() for k in (3, 4, 3, 3)]
     w.get_state(out=pin)
@@ -351,17 +416,20 @@ def run_fw(args):
     state_bytes = n_body * (3 + 4 + 3 + 3) * 4
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, v1, cores, sample = cpu_baseline(args.cpu_envs, args.seed)
+        v, v1, cores, sample = cpu_baseline(args.cpu_envs, args.seed, workload=args.workload)
         cpu = {"value": v, "unit": "env-substeps/s", "cores": cores, "kind": "oracle", "sample": sample,
                "value_1core": v1}
     if rank == 0:
         out = {"metric": "env-substeps/s", "value": value, "unit": "env-substeps/s", "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic (procedural ISO M16 nut/bolt meshes, seeded poses)",
-               "config": {"workload": "mixed_nut_bolt_m8_m20" if args.workload == "mixed" else "nut_bolt_m16",
-                          "n_envs": n_env, "samples_per_nut": ns,
-                          "sdf": ("128^3-256^3 " if args.workload == "mixed" else "256^3 ") + ("fp16" if args.fp16 else "fp32"),
+               "data": data_desc,
+               "config": {"workload": wl_name + ("_per_triangle" if tri_mode else ""),
+                          "n_envs": n_env, "pairs_per_env": n_pair / max(n_env, 1),
+                          ("faces_per_pair" if tri_mode else "samples_per_pair"): ns,
+                          "contact_gen": args.contact_gen,
+                          **({"tri_iters": args.tri_iters} if tri_mode else {}),
+                          "sdf": sdf_desc + (" fp16" if fp16 else " fp32"),
                           "substeps": sim.n_substeps,
                           "iters": sim.n_iters, "frame_dt": sim.dt, "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{ws}"},
@@ -372,6 +440,7 @@ def run_fw(args):
                "solve_shape": list(w.solve_shape()), "autotuned": tuned is not None,
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),
+               **({"single_pair_generate": single} if single else {}),
                "e2e": {"value": e2e_value, "unit": "env-substeps/s", "h2d_bytes_per_step": state_bytes,
                        "d2h_bytes_per_step": state_bytes},
                "gpu_launches": args.steps * w.launches_per_step(sim.n_substeps),
@@ -393,7 +462,7 @@ def run_diff_peg(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    sc, tp, tq = S.diff_peg_scene(n_envs=args.envs if args.envs != 1000 else 256, seed=env_seed(args.seed, rank))
+    sc, tp, tq = S.diff_peg_scene(n_envs=args.envs if args.envs > 0 else 256, seed=env_seed(args.seed, rank))
     w = fw.world_from_scene(sc, device=local)
     n_env, nb, npair = w.counts()
     x0 = [torch.tensor(a, device="cuda") for a in w.get_state()]
@@ -445,17 +514,23 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fw", choices=["fw", "reference"])
-    ap.add_argument("--envs", type=int, default=1000)
+    ap.add_argument("--envs", type=int, default=0, help="envs (0: the workload's own count)")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--fp16", action="store_true", help="store the SDFs in FP16 (FP32 interpolation and solve)")
+    ap.add_argument("--fp32", action="store_true", help="gears: keep the SDFs in FP32 (its configuration stores FP16)")
     ap.add_argument("--solve-shape", default="0,0", help="envs per warp, warps per block (0,0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=0, help="envs of the oracle sample (0: one per core)")
     ap.add_argument("--ref-envs", type=int, default=0, help="envs of the reference arm's sample (0: one per core)")
-    ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "diff_peg"],
+    ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "gears", "diff_peg"],
                     help="nut_bolt: the headline substep benchmark (1000 M16 envs); mixed: 4096 envs of "
-                         "M8-M20 pairs; diff_peg: gradient throughput of the differentiable peg")
+                         "M8-M20 pairs; gears: 2048 three-gear trains (FP16 SDFs); diff_peg: gradient "
+                         "throughput of the differentiable peg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default solve shape")
+    ap.add_argument("--contact-gen", default="samples", choices=["samples", "triangles"],
+                    help="samples: SDF query of the nut's surface samples; triangles: one contact per "
+                         "face of the nut's mesh by local minimisation over the face")
+    ap.add_argument("--tri-iters", type=int, default=16, help="descent steps per face (triangles)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

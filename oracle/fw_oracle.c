@@ -1120,6 +1120,23 @@ int or_set_contacts(or_world *w, int env, const or_contact *in, int n) {
     return 0;
 }
 
+int or_get_pair_contacts(const or_world *w, int env, int pair, or_contact *out, int cap, int *n_out) {
+    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= w->envs[env].n_pairs) return -1;
+    const pair_contacts_t *pc = &w->pc[w->envs[env].first_pair + pair];
+    for (int i = 0; i < pc->n && i < cap; ++i) out[i] = pc->c[i];
+    *n_out = pc->n;
+    return pc->n > cap ? -1 : 0;
+}
+
+int or_set_pair_contacts(or_world *w, int env, int pair, const or_contact *in, int n) {
+    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= w->envs[env].n_pairs || n < 0) return -1;
+    pair_contacts_t *pc = &w->pc[w->envs[env].first_pair + pair];
+    if (pc->cap < n) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * (n > 0 ? n : 1)); pc->cap = n; }
+    if (n > 0) memcpy(pc->c, in, sizeof(or_contact) * n);
+    pc->n = n;
+    return 0;
+}
+
 int or_env_margins(const or_world *w, int env, double *len, double *dot) {
     *len = w->env_mlen[env]; *dot = w->env_mdot[env];
     return 0;

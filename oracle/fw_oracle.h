@@ -152,6 +152,10 @@ int or_collide(or_world *w);
 int or_get_contacts(const or_world *w, int env, or_contact *out, int cap, int *n_out,
                     double *min_margin_len, double *min_margin_dot);
 int or_set_contacts(or_world *w, int env, const or_contact *in, int n);
+/* Contacts of one pair of an env (its list in sweep order), and a replacement of that
+ * list alone (the env's other pairs keep theirs).  `pair` is the env-local pair index. */
+int or_get_pair_contacts(const or_world *w, int env, int pair, or_contact *out, int cap, int *n_out);
+int or_set_pair_contacts(or_world *w, int env, int pair, const or_contact *in, int n);
 /* Per-env minimum decision margins over everything since the last reset. */
 int or_env_margins(const or_world *w, int env, double *len, double *dot);
 void or_reset_margins(or_world *w);

@@ -93,6 +93,8 @@ def lib():
             L.or_get_contacts.argtypes = [vp, C.c_int, vp, C.c_int, C.POINTER(C.c_int),
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_set_contacts.argtypes = [vp, C.c_int, vp, C.c_int]
+            L.or_get_pair_contacts.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_int)]
+            L.or_set_pair_contacts.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
             L.or_env_margins.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_reset_margins.argtypes = [vp]
             L.or_get_state.argtypes = [vp, _f64, _f64, _f64, _f64]
@@ -310,6 +312,23 @@ class OracleWorld:
     def set_contacts(self, env: int, contacts: np.ndarray):
         c = np.ascontiguousarray(contacts, dtype=CONTACT_DTYPE)
         lib().or_set_contacts(self.h, env, c.ctypes.data, len(c))
+
+    def pair_contacts(self, env: int, pair: int):
+        """the contacts of one pair of the env (env-local pair index), in sweep order"""
+        cap = 4096
+        while True:
+            out = np.zeros(cap, CONTACT_DTYPE)
+            n = C.c_int()
+            if lib().or_get_pair_contacts(self.h, env, pair, out.ctypes.data, cap, C.byref(n)) == 0:
+                return out[: n.value].copy()
+            if n.value <= cap:
+                raise ValueError(f"or_get_pair_contacts: bad env {env} or pair {pair}")
+            cap = n.value
+
+    def set_pair_contacts(self, env: int, pair: int, contacts: np.ndarray):
+        c = np.ascontiguousarray(contacts, dtype=CONTACT_DTYPE)
+        if lib().or_set_pair_contacts(self.h, env, pair, c.ctypes.data, len(c)) != 0:
+            raise ValueError(f"or_set_pair_contacts: bad env {env} or pair {pair}")
 
     def margins(self, env: int):
         ml, md = C.c_double(), C.c_double()

@@ -427,11 +427,15 @@ def gear_outline(module_mm: float, teeth: int, backlash_mm: float, n_flank: int 
         root_a = root_a[1:-1]
         root = np.stack([np.full_like(root_a, rf), root_a], 1)
         seg = [left, tip, right]
+        # below the base circle the flank drops to the root circle along a line turned a
+        # quarter of a root step off the radius (a radial drop would put two outline
+        # points on one ray, and the caps are triangulated along rays)
+        dr = 0.25 * (nxt - c - 2 * off[0]) / (n_root + 1)
         if rf < r_start - 1e-12:
-            seg.append(np.array([[rf, c + off[0]]]))
+            seg.append(np.array([[rf, c + off[0] + dr]]))
         seg.append(root)
         if rf < r_start - 1e-12:
-            seg.append(np.array([[rf, nxt - off[0]]]))
+            seg.append(np.array([[rf, nxt - off[0] - dr]]))
         pts.append(np.concatenate(seg))
     polar = np.concatenate(pts)
     return np.stack([polar[:, 0] * np.cos(polar[:, 1]), polar[:, 0] * np.sin(polar[:, 1])], 1)
@@ -728,3 +732,66 @@ def mixed_nut_bolt_scene(n_envs: int = 4096, seed: int = 0, n_substeps: int = 8,
         sim = sub.sim
     return Scene("mixed_nut_bolt", assets, groups, sim)
 
+
+
+GEAR_TEETH = (20, 30, 40)
+
+
+def gear_assets(module_mm: float = 1.0, teeth: Sequence[int] = GEAR_TEETH, thick_mm: float = 10.0,
+                backlash_mm: float = 0.1, tri_target: int = 30000, n_samples: int = 15000,
+                sdf_res: int = 256, rng: Optional[np.random.Generator] = None) -> List[Asset]:
+    """One asset per gear of the train: extruded in as many layers as bring it near
+    tri_target triangles, n_samples surface samples on every gear that is a pair's point
+    body (all but the last) and an SDF on every gear that is a pair's SDF body (all but
+    the first)."""
+    rng = rng or np.random.default_rng(0)
+    assets = []
+    for i, z in enumerate(teeth):
+        n_out = len(gear_outline(module_mm, z, backlash_mm))
+        layers = max(1, int(round(tri_target / (4.0 * n_out))) - 1)
+        V, T = gear_mesh(module_mm, z, thick_mm, backlash_mm, n_layers=layers)
+        samples = sample_surface(V, T, n_samples, rng) if i < len(teeth) - 1 else None
+        assets.append(Asset(f"gear_z{z}", V, T, samples, 7800.0,
+                            sdf_res=sdf_res if i > 0 else None, sdf_pad=1e-3))
+    return assets
+
+
+def gear_scene(n_envs: int = 2048, seed: int = 0, module_mm: float = 1.0, backlash_mm: float = 0.1,
+               tri_target: int = 30000, n_samples: int = 15000, sdf_res: int = 256,
+               drive_rate: float = 2.0, load_torque: float = 0.02, mu: float = 0.1,
+               n_substeps: int = 8, n_iters: int = 32, frames: int = 300) -> Scene:
+    """Gear train: involute spur gears of 20, 30 and 40 teeth (module 1 mm, 10 mm thick,
+    0.1 mm backlash per mesh) on fixed parallel shafts along +z, in a row along +x at the
+    standard centre distances m (z1 + z2) / 2.  The 20-tooth gear is kinematic, driven at
+    drive_rate rad/s about +z; the 30- and 40-tooth gears are fixed-axis bodies free to
+    spin about their shafts, the last one loaded by a constant torque against its turning
+    direction (so that the flanks stay in contact).  Pairs: the samples of the smaller
+    gear against the SDF of the larger one, (20 -> 30) and (30 -> 40).
+
+    Initial angles (seeded per env): the train starts in exact conjugate mesh -- a tooth of
+    one gear centred in a gap of the next on the line of centres -- turned by a common
+    phase theta ~U(0, one pitch of the driver) through the gear ratios, then the two
+    driven gears are each turned by an independent jitter of at most a fifth of the
+    backlash (arc length on their pitch circles)."""
+    rng = np.random.default_rng(seed)
+    z1, z2, z3 = GEAR_TEETH
+    m = module_mm * 1e-3
+    assets = gear_assets(module_mm, GEAR_TEETH, 10.0, backlash_mm, tri_target, n_samples, sdf_res, rng)
+    c12 = m * (z1 + z2) / 2
+    c23 = m * (z2 + z3) / 2
+    centres = [(0.0, 0.0, 0.0), (c12, 0.0, 0.0), (c12 + c23, 0.0, 0.0)]
+    bodies = np.zeros((n_envs, 3), dtype=BODY_DTYPE)
+    jit = 0.2 * backlash_mm * 1e-3
+    for e in range(n_envs):
+        th = rng.uniform(0.0, 2 * np.pi / z1)
+        a2 = np.pi / z2 - th * z1 / z2 + rng.uniform(-jit, jit) / (m * z2 / 2)
+        a3 = th * z1 / z3 + rng.uniform(-jit, jit) / (m * z3 / 2)
+        z_axis = [0, 0, 1]
+        bodies[e, 0] = _body(0, KINEMATIC, centres[0], quat_axis_angle(z_axis, th), mu,
+                             angvel=(0, 0, drive_rate))
+        bodies[e, 1] = _body(1, FIXED_AXIS, centres[1], quat_axis_angle(z_axis, a2), mu, axis=(0, 0, 1))
+        bodies[e, 2] = _body(2, FIXED_AXIS, centres[2], quat_axis_angle(z_axis, a3), mu, axis=(0, 0, 1),
+                             torque=(0, 0, -load_torque))
+    pairs = np.array([[0, 1], [1, 2]], dtype=np.int32)
+    sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, frames=frames)
+    return Scene("gears", assets, [EnvGroup(bodies, pairs)], sim)

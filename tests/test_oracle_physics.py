@@ -83,7 +83,7 @@ def test_kinematic_body_follows_prescribed_velocity():
 
 
 def test_fixed_axis_body_spins_about_its_axis_only():
-    V, T = S.gear_mesh(teeth=20, n_flank=6, n_tip=2, n_root=2) if False else S.cylinder_mesh(0.01, 0.005, 24)
+    V, T = S.cylinder_mesh(0.01, 0.005, 24)
     w = O.OracleWorld(gravity=(0, 0, -9.81))
     a = w.add_asset(V, T, S.sample_surface(V, T, 100, np.random.default_rng(1)))
     ax = np.array([0.0, 0.6, 0.8])
