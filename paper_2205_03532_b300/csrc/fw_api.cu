@@ -66,6 +66,7 @@ struct fw_world {
     // device limits and the solve's launch shape (0: chosen from the env count)
     int n_sm = 0, max_dyn_smem[4] = {0, 0, 0, 0};
     int solve_groups = 0, solve_warps = 0;
+    int lam_rows = 0;   // rows per env whose impulses the solve keeps in shared memory (0: every row)
     // differentiable rollout (fw_record_rollout .. fw_adjoint_rollout)
     DiffState diff;
     bool diff_valid = false;
@@ -317,6 +318,8 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.scratch = w->d_scratch;
     p.items = w->d_items;
     p.contact_gen = w->cfg.contact_gen;
+    p.multi_movable = 0;
+    for (const auto &E : w->envs) p.multi_movable |= (E.movable == -2);
     p.tri_iters = w->cfg.tri_iters;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;
@@ -338,6 +341,7 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.n_vel_iters = w->cfg.n_vel_iters;
     int rc = 0;
     for (const auto &E : w->envs) rc = std::max(rc, E.row_cap);
+    if (w->lam_rows > 0 && w->lam_rows < rc) rc = w->lam_rows;   // envs with more rows: global impulses
     p.lam_cap = rc <= kLamCapMax ? rc : 0;   // larger envs take the general sweep
     return p;
 }
@@ -1217,8 +1221,32 @@ fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials
     cudaError_t e = copy_state(true);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    const SimParams p = sim_params(w, w->cfg.dt / (float)n_substeps, n_iters);
+    SimParams p = sim_params(w, w->cfg.dt / (float)n_substeps, n_iters);
     if (e == cudaSuccess) e = launch_detect(p, w->stream);   // contacts of the current state
+    // Shared memory per env: room for twice the largest row count seen now (a power of two,
+    // at least 64 rows) when that is below the envs' row capacity.  Fewer bytes per env let
+    // more envs run at once; an env that later outgrows it keeps its impulses in global
+    // memory (same update, slower).
+    if (e == cudaSuccess) {
+        std::vector<int> cnt(w->pairs.size());
+        e = cudaMemcpyAsync(cnt.data(), w->d_counts, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+        if (e == cudaSuccess) {
+            const int cp = cap_pair(w);
+            int max_nr = 0, rc = 0;
+            for (const auto &E : w->envs) {
+                int nr = 0;
+                for (int k = 0; k < E.n_pairs; ++k) nr += std::min(cnt[E.first_pair + k], cp);
+                max_nr = std::max(max_nr, nr);
+                rc = std::max(rc, E.row_cap);
+            }
+            int lam = 64;
+            while (lam < 2 * max_nr) lam *= 2;
+            const int rows = lam < rc ? lam : 0;
+            if (rows != w->lam_rows) { w->lam_rows = rows; drop_graph(w); }
+            p = sim_params(w, w->cfg.dt / (float)n_substeps, n_iters);
+        }
+    }
     int bg = 0, bw = 0;
     float best = 1e30f;
     const int gs[4] = {1, 2, 4, 8};

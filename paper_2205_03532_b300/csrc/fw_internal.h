@@ -115,6 +115,7 @@ struct SimParams {
     float4 *cand;                          // n_items x kBatch x 2: (x_w, phi), (n_w, sample)
     int *cand_count;                       // n_items
     int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
+    int multi_movable;                     // some env has several movable bodies (general sweep form)
     int tri_iters;                         // descent steps per triangle
 };
 

@@ -11,7 +11,8 @@
 // stays in registers, split between the group's even lanes (linear part) and odd lanes
 // (angular part), the rows stream from global memory through a cp.async ring in shared
 // memory and the accumulated impulses live in shared memory.  General form
-// (several movable bodies): full two-body rows, velocities in shared memory, one lane.
+// (several movable bodies): full two-body rows streamed through the same ring by one lane,
+// impulses and velocities in shared memory.
 //
 // Update rule (velocity-level projected Gauss-Seidel; the paper cites the solver without
 // restating it): per contact, the normal row
@@ -97,49 +98,94 @@ __device__ __forceinline__ void build_row(Row &R, const DContact &c, const BodyS
     R.a = a; R.b = b;
 }
 
-// One Gauss-Seidel sweep over the env's rows (lane 0 only).
+// One contact's Gauss-Seidel update in the general form: the normal row, then the two
+// friction rows projected jointly on the disk; L = (lambda_n, lambda_t1, lambda_t2, -).
+__device__ __forceinline__ void gs_row(const Row &R, float4 &L, BodySm &B, bool use_bias) {
+    if (R.kn == 0.0f) return;
+    const int a = R.a, b = R.b;
+    V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
+    const float ima = B.invm[a], imb = B.invm[b];
+    // normal row
+    const V3 n = ld3(R.n);
+    float jv = dot(n, va - vb) + dot(ld3(R.ra_n), wa) - dot(ld3(R.rb_n), wb);
+    if (use_bias) jv += R.bias;
+    const float ln = fmaxf(L.x - R.kn * jv, 0.0f);
+    const float dl = ln - L.x;
+    L.x = ln;
+    va = va + (dl * ima) * n;
+    wa = wa + dl * ld3(R.ia_n);
+    vb = vb - (dl * imb) * n;
+    wb = wb - dl * ld3(R.ib_n);
+    // friction rows, projected jointly on the disk of radius mu lambda_n
+    const V3 t1 = ld3(R.t1), t2 = ld3(R.t2);
+    const V3 dv = va - vb;
+    const float j1 = dot(t1, dv) + dot(ld3(R.ra_t1), wa) - dot(ld3(R.rb_t1), wb);
+    const float j2 = dot(t2, dv) + dot(ld3(R.ra_t2), wa) - dot(ld3(R.rb_t2), wb);
+    float l1 = L.y - R.kt1 * j1, l2 = L.z - R.kt2 * j2;
+    const float lim = R.mu * ln;
+    const float lt = sqrtf(l1 * l1 + l2 * l2);
+    if (lt > lim) {
+        const float s = lt > 0.0f ? lim / lt : 0.0f;
+        l1 *= s;
+        l2 *= s;
+    }
+    const float d1 = l1 - L.y, d2 = l2 - L.z;
+    L.y = l1;
+    L.z = l2;
+    const V3 pt = d1 * t1 + d2 * t2;
+    va = va + ima * pt;
+    wa = wa + d1 * ld3(R.ia_t1) + d2 * ld3(R.ia_t2);
+    vb = vb - imb * pt;
+    wb = wb - (d1 * ld3(R.ib_t1) + d2 * ld3(R.ib_t2));
+    smv_set(B.v, a, va); smv_set(B.w, a, wa);
+    smv_set(B.v, b, vb); smv_set(B.w, b, wb);
+}
+
+// One Gauss-Seidel sweep over the env's rows in global memory, impulses in the rows (lane
+// 0 only; the form for envs whose rows exceed the shared-memory impulse capacity).
 __device__ void sweep(Row *rows, int nr, BodySm &B, bool use_bias) {
     for (int r = 0; r < nr; ++r) {
         Row &R = rows[r];
-        if (R.kn == 0.0f) continue;
-        const int a = R.a, b = R.b;
-        V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
-        const float ima = B.invm[a], imb = B.invm[b];
-        // normal row
-        const V3 n = ld3(R.n);
-        float jv = dot(n, va - vb) + dot(ld3(R.ra_n), wa) - dot(ld3(R.rb_n), wb);
-        if (use_bias) jv += R.bias;
-        const float ln = fmaxf(R.ln - R.kn * jv, 0.0f);
-        const float dl = ln - R.ln;
-        R.ln = ln;
-        va = va + (dl * ima) * n;
-        wa = wa + dl * ld3(R.ia_n);
-        vb = vb - (dl * imb) * n;
-        wb = wb - dl * ld3(R.ib_n);
-        // friction rows, projected jointly on the disk of radius mu lambda_n
-        const V3 t1 = ld3(R.t1), t2 = ld3(R.t2);
-        const V3 dv = va - vb;
-        const float j1 = dot(t1, dv) + dot(ld3(R.ra_t1), wa) - dot(ld3(R.rb_t1), wb);
-        const float j2 = dot(t2, dv) + dot(ld3(R.ra_t2), wa) - dot(ld3(R.rb_t2), wb);
-        float l1 = R.lt1 - R.kt1 * j1, l2 = R.lt2 - R.kt2 * j2;
-        const float lim = R.mu * ln;
-        const float lt = sqrtf(l1 * l1 + l2 * l2);
-        if (lt > lim) {
-            const float s = lt > 0.0f ? lim / lt : 0.0f;
-            l1 *= s;
-            l2 *= s;
-        }
-        const float d1 = l1 - R.lt1, d2 = l2 - R.lt2;
-        R.lt1 = l1;
-        R.lt2 = l2;
-        const V3 pt = d1 * t1 + d2 * t2;
-        va = va + ima * pt;
-        wa = wa + d1 * ld3(R.ia_t1) + d2 * ld3(R.ia_t2);
-        vb = vb - imb * pt;
-        wb = wb - (d1 * ld3(R.ib_t1) + d2 * ld3(R.ib_t2));
-        smv_set(B.v, a, va); smv_set(B.w, a, wa);
-        smv_set(B.v, b, vb); smv_set(B.w, b, wb);
+        float4 L = make_float4(R.ln, R.lt1, R.lt2, 0.0f);
+        gs_row(R, L, B, use_bias);
+        R.ln = L.x; R.lt1 = L.y; R.lt2 = L.z;
     }
+}
+
+// n_sweeps Gauss-Seidel sweeps in the general form (lane 0 only), the same updates as
+// sweep(): the rows, read-only here, stream through the env's shared-memory ring with
+// cp.async kRing - 1 steps ahead, so that no step waits on a global load; the impulses live
+// in lam (one float4 per row, shared memory).
+__device__ __noinline__ void sweep_general(const Row *rows, int nr, int n_sweeps, float4 *ring, float4 *lam,
+                                           BodySm &B, bool use_bias) {
+    const int total = nr * n_sweeps;
+    if (total == 0) return;
+    const float4 *src = reinterpret_cast<const float4 *>(rows);
+    int pf = 0;   // row of the next step to prefetch
+    for (int s = 0; s < kRing - 1; ++s) {
+        if (s < total) {
+            for (int k = 0; k < kRowF4; ++k) cp_async16(ring + s * kRowF4 + k, src + (size_t)pf * kRowF4 + k);
+            if (++pf == nr) pf = 0;
+        }
+        cp_async_commit();
+    }
+    int r = 0;
+    for (int s = 0; s < total; ++s) {
+        const int sp = s + kRing - 1;   // its slot held step s - 1, already consumed
+        if (sp < total) {
+            float4 *dst = ring + (sp % kRing) * kRowF4;
+            for (int k = 0; k < kRowF4; ++k) cp_async16(dst + k, src + (size_t)pf * kRowF4 + k);
+            if (++pf == nr) pf = 0;
+        }
+        cp_async_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+        const Row &R = *reinterpret_cast<const Row *>(ring + (s % kRing) * kRowF4);
+        float4 L = lam[r];
+        gs_row(R, L, B, use_bias);
+        lam[r] = L;
+        if (++r == nr) r = 0;
+    }
+    cp_async_wait_all();
 }
 
 // Fast row of one contact, from the side of the movable body m (a or b of the pair).
@@ -402,7 +448,9 @@ __device__ __forceinline__ int warp_max(int v) {
 
 // One substep's solve for kGroups envs per warp (G = 32 / kGroups lanes each) and
 // blockDim.x / 32 warps per block.  No block-wide barrier: every warp is independent.
-template <int kGroups>
+// kMulti: the world has envs with several movable bodies, whose general-form sweeps keep
+// their impulses in shared memory (sweep_general); without it that code is compiled out.
+template <int kGroups, bool kMulti>
 __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams p) {
     constexpr int G = 32 / kGroups;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -473,6 +521,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     float4 *ring = lam + p.lam_cap;
     const int m = E.movable;
     const bool fast = (m != -2) && nr <= p.lam_cap;
+    // several movable bodies: general rows, impulses in shared memory when they fit
+    const bool general_sm = kMulti && (m == -2) && nr <= p.lam_cap;
     float4 *frows = reinterpret_cast<float4 *>(rows);
     // 2. constraint preparation, one contact per lane, then the couplings between neighbours
     for (int k = 0; k < E.n_pairs; ++k) {
@@ -487,6 +537,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
                                    P.local_b, m, P.mu, hs, p.baumgarte);
             } else {
                 build_row(rows[S.row_base[k] + i], c, B, P.local_a, P.local_b, P.mu, hs, p.baumgarte);
+                if (kMulti && general_sm) lam[S.row_base[k] + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
     }
@@ -508,7 +559,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
     }
     if (valid && !fast && gl == 0) {
-        for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
+        if (kMulti && general_sm) sweep_general(rows, nr, p.n_iters, ring, lam, B, true);
+        else for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
     }
     __syncwarp();
     // 4. integration
@@ -555,7 +607,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
         if (valid && !fast && gl == 0) {
-            for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
+            if (kMulti && general_sm) sweep_general(rows, nr, p.n_vel_iters, ring, lam, B, false);
+            else for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
         }
     }
     __syncwarp();
@@ -590,11 +643,15 @@ size_t solve_smem_bytes(int lam_cap) { return sizeof(float4) * (size_t)env_strid
 
 template <int kGroups>
 static cudaError_t prepare_one(int optin, int *max_dyn) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, solve_kernel<kGroups>);
+    cudaFuncAttributes a, b;
+    cudaError_t e = cudaFuncGetAttributes(&a, solve_kernel<kGroups, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, solve_kernel<kGroups, true>);
     if (e != cudaSuccess) return e;
-    *max_dyn = optin - (int)a.sharedSizeBytes;
-    return cudaFuncSetAttribute(solve_kernel<kGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+    *max_dyn = optin - (int)(a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes);
+    e = cudaFuncSetAttribute(solve_kernel<kGroups, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<kGroups, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+    return e;
 }
 
 cudaError_t prepare_solve(int optin, int max_dyn[4]) {
@@ -633,10 +690,18 @@ cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t 
     if (p.n_envs == 0) return cudaSuccess;
     const int per_block = sh.groups * sh.warps;
     const int blocks = (p.n_envs + per_block - 1) / per_block;
-    if (sh.groups == 1) solve_kernel<1><<<blocks, 32 * sh.warps, sh.smem, s>>>(p);
-    else if (sh.groups == 2) solve_kernel<2><<<blocks, 32 * sh.warps, sh.smem, s>>>(p);
-    else if (sh.groups == 4) solve_kernel<4><<<blocks, 32 * sh.warps, sh.smem, s>>>(p);
-    else solve_kernel<8><<<blocks, 32 * sh.warps, sh.smem, s>>>(p);
+    const dim3 grid(blocks), block(32 * sh.warps);
+    if (p.multi_movable) {
+        if (sh.groups == 1) solve_kernel<1, true><<<grid, block, sh.smem, s>>>(p);
+        else if (sh.groups == 2) solve_kernel<2, true><<<grid, block, sh.smem, s>>>(p);
+        else if (sh.groups == 4) solve_kernel<4, true><<<grid, block, sh.smem, s>>>(p);
+        else solve_kernel<8, true><<<grid, block, sh.smem, s>>>(p);
+    } else {
+        if (sh.groups == 1) solve_kernel<1, false><<<grid, block, sh.smem, s>>>(p);
+        else if (sh.groups == 2) solve_kernel<2, false><<<grid, block, sh.smem, s>>>(p);
+        else if (sh.groups == 4) solve_kernel<4, false><<<grid, block, sh.smem, s>>>(p);
+        else solve_kernel<8, false><<<grid, block, sh.smem, s>>>(p);
+    }
     return cudaGetLastError();
 }
 

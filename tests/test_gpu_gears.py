@@ -3,7 +3,14 @@ a 256^3 SDF each, 15k samples on the point gears, two pairs per env and two mova
 fixed-axis bodies, so the solve takes its general form) against the FP64 oracle, and
 against the gear ratios that involute geometry fixes.
 
-Tolerances as for the other scenes: narrow phase 5e-5 h in phi; reduced contacts identical
+Tolerances as for the other scenes: narrow phase 5e-5 h in phi; normals to (2e-5 +
+2^-20 |phi| / h) / |grad| -- each side bakes its own grid and the bakes agree per node to
+1e-5 h + 2^-22 |phi|, a gradient component blends node differences over h, so the
+gradients differ by up to twice that over h -- except where a sample lies within the pose transform's float32 rounding (1e-4 voxel)
+of a cell face: the trilinear gradient jumps across cell faces, and there the two sides may
+take either cell (both gears' SDF bodies are rotated and translated, so the transform
+rounds at the 1e-5 voxel level); such a flip must stay rare (at most 0.1% of the samples);
+reduced contacts identical
 where every decision has margin, else agreeing in bulk; identical contacts solved for one
 substep to 1e-6 rad; one frame through the whole path to 2e-3 rad (a near-tie resolved
 the other way changes a flank contact); the ratios w2/w1 = -z1/z2 and w3/w1 = z1/z3 to 3%
@@ -41,23 +48,52 @@ def gears():
     return sc, gw, ow
 
 
+def _rot(q):
+    x, y, z, w = np.asarray(q, np.float64) / np.linalg.norm(np.asarray(q, np.float64))
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def _near_cell_face(gw, sc, env, pair, sdf_asset, tol=1e-4):
+    """samples whose grid coordinate (FP64 pose transform of the float32 state) lies within
+    tol voxel of a cell face on some axis; bodies of env e are 3e .. 3e + 2 and pair k joins
+    bodies k and k + 1"""
+    p, q = gw.get_state()[:2]
+    a, b = 3 * env + pair, 3 * env + pair + 1
+    s = sc.assets[pair].samples.astype(np.float64)
+    xw = s @ _rot(q[a]).T + p[a].astype(np.float64)
+    xb = (xw - p[b].astype(np.float64)) @ _rot(q[b])
+    lo, h = gw.get_sdf(sdf_asset, values=False)[:2]
+    u = (xb - lo.astype(np.float64)) / np.float64(h)
+    return np.any(np.abs(u - np.round(u)) < tol, axis=1)
+
+
 def test_narrow_phase_both_pairs(gears):
     sc, gw, ow = gears
     for pair, sdf_asset in ((0, 1), (1, 2)):
         ns = len(sc.assets[pair].samples)
         h = float(gw.get_sdf(sdf_asset, values=False)[1])
-        inside = 0
+        inside = flipped = 0
         for env in range(sc.n_envs):
             phi, nrm = gw.query_pair(env, pair, ns)
             ophi, onrm, ovalid = ow.query_pair(env, pair, ns)
             assert np.array_equal(np.isfinite(phi), ovalid), (env, pair)
             d = np.abs(phi[ovalid] - ophi[ovalid])
             assert np.all(d <= 5e-5 * h), (env, pair, float(d.max() / h))
-            dn = np.max(np.abs(nrm[ovalid] - onrm[ovalid]), axis=1)
-            tol = 1e-5 / np.minimum(1.0, ow.last_gnorm[ovalid])
-            assert np.all(dn <= tol), (env, pair, float((dn / tol).max()))
+            near = _near_cell_face(gw, sc, env, pair, sdf_asset)
+            dn = np.where(ovalid, np.max(np.abs(nrm - onrm), axis=1), 0.0)
+            gtol = 2e-5 + 2.0 ** -20 * np.abs(np.where(ovalid, ophi, 0.0)) / h
+            bad = ovalid & (dn > gtol / np.minimum(1.0, np.maximum(ow.last_gnorm, 1e-30)))
+            if np.any(bad & ~near):
+                i = int(np.flatnonzero(bad & ~near)[0])
+                raise AssertionError((env, pair, i, float(dn[i]), float(ow.last_gnorm[i]), float(ophi[i] / h),
+                                      nrm[i].tolist(), onrm[i].tolist()))
+            assert np.all(np.abs(np.linalg.norm(nrm[ovalid], axis=1) - 1) <= 1e-5)
             inside += int(ovalid.sum())
+            flipped += int((bad & near).sum())
         assert inside > 1000, (pair, inside)     # part of the point gear lies in the grid
+        assert flipped <= max(2, 1e-3 * inside), (pair, flipped, inside)
 
 
 def test_collide_per_pair(gears):
