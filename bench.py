@@ -30,12 +30,13 @@ sys.path.insert(0, ROOT)
 # (SUBSTEP_SOURCES) it was taken on; reported only while they are unchanged (profiles/
 # holds the capture).
 NCU_TRAFFIC = {
-    # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32)
-    "f071360575c9fc31": {"query_kernel": 10.54e6, "reduce_kernel": 32.03e6, "solve_kernel": 28.04e6},
+    # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the bench's own
+    # timing-pass state: 332 contacts per env, 3,358 candidates per pair)
+    "5fa3d7814e7350f0": {"query_kernel": 54.30e6, "reduce_kernel": 108.24e6, "solve_kernel": 140.03e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "f071360575c9fc31": {"query_kernel": 456.1e6, "reduce_kernel": 97.3e6, "solve_kernel": 3330.0e6},
+    "5fa3d7814e7350f0": {"query_kernel": 656.6e6, "reduce_kernel": 356.3e6, "solve_kernel": 4510.0e6},
 }
 
 FP32_LANES_PER_SM = 128
