@@ -44,6 +44,15 @@
  *      or whose final gradient vanishes, makes no candidate; trial points outside the
  *      grid are rejected.  The candidate index is the triangle index, Generate batches
  *      are batch_size triangles.
+ *   R17 narrow-band bricked storage (sdf_band > 0; the paper names sparse storage as the
+ *      remedy for the grid's memory footprint without fixing a scheme): cells are grouped
+ *      in bricks of 8^3; a brick is stored iff one node of its cells has |phi| <= band
+ *      (band = sdf_band voxels, in float32: sdf_band * h) or its nodes change sign, the
+ *      decision taken on the float32 node values.  A query in a cell of a brick that is
+ *      not stored returns phi = +band (all its nodes positive) or -band (all negative)
+ *      with a zero gradient, so it makes no candidate (R4).  Since a trilinear value is a
+ *      convex combination of its cell's corners, every point with |phi| <= band lies in
+ *      a stored brick and reads the dense value there.
  */
 #include "fw_oracle.h"
 
@@ -279,16 +288,71 @@ void or_bake_nodes(const float *V, const int *T, int nt, const float lo[3], floa
 /* ------------------------------------------------------------------------------------ */
 /* trilinear value and gradient (Sec. III-A; R3, R4)                                     */
 /* ------------------------------------------------------------------------------------ */
+#define BRICK 8                       /* cells per brick edge (R17) */
+#define BRICK_UNKNOWN (-3)
+
 typedef struct {
     double lo[3], h;
     int dims[3];
     double *val;          /* nx*ny*nz */
     unsigned char *done;  /* lazy bake: 1 when val is set */
     int lazy;
+    float band;           /* R17: narrow band (m, float32); 0 = dense storage */
+    int bdims[3];         /* bricks per axis */
+    signed char *bstate;  /* per brick: 1 stored, -1 out of band outside, -2 inside, unknown */
 } grid_t;
 
 static long long gidx(const grid_t *g, int i, int j, int k) {
     return ((long long)k * g->dims[1] + j) * g->dims[0] + i;
+}
+
+static long long brick_index(const grid_t *g, int ci, int cj, int ck) {
+    return ((long long)(ck / BRICK) * g->bdims[1] + cj / BRICK) * g->bdims[0] + ci / BRICK;
+}
+
+/* R17: the state of brick (bi, bj, bk) from its nodes (those of its cells), or unknown
+ * while a lazy grid has not baked all of them */
+static signed char brick_state(const grid_t *g, int bi, int bj, int bk) {
+    const int b[3] = {bi, bj, bk};
+    int n0[3], n1[3];
+    for (int a = 0; a < 3; ++a) {
+        n0[a] = b[a] * BRICK;
+        n1[a] = n0[a] + BRICK;                                   /* last node of its last cell */
+        if (n1[a] > g->dims[a] - 1) n1[a] = g->dims[a] - 1;
+    }
+    int near = 0, pos = 0, neg = 0;
+    for (int k = n0[2]; k <= n1[2]; ++k)
+        for (int j = n0[1]; j <= n1[1]; ++j)
+            for (int i = n0[0]; i <= n1[0]; ++i) {
+                const long long id = gidx(g, i, j, k);
+                if (g->lazy && g->done[id] != 1) return BRICK_UNKNOWN;
+                const float v = (float)g->val[id];
+                if (fabsf(v) <= g->band) near = 1;
+                if (v < 0.0f) neg = 1; else pos = 1;
+            }
+    if (near || (pos && neg)) return 1;
+    return neg ? -2 : -1;
+}
+
+/* R17: set up the brick table of a grid (band in voxels); states of bricks whose nodes are
+ * all known are computed now, the rest when a lazy bake completes them */
+static void grid_set_band(grid_t *g, float band_voxels) {
+    free(g->bstate);
+    g->bstate = NULL;
+    g->band = 0.0f;
+    if (!(band_voxels > 0.0f)) return;
+    g->band = band_voxels * (float)g->h;
+    long long nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        g->bdims[a] = (g->dims[a] - 1 + BRICK - 1) / BRICK;
+        nb *= g->bdims[a];
+    }
+    g->bstate = (signed char *)malloc((size_t)nb);
+    for (long long b = 0; b < nb; ++b) g->bstate[b] = BRICK_UNKNOWN;
+    for (int bk = 0; bk < g->bdims[2]; ++bk)
+        for (int bj = 0; bj < g->bdims[1]; ++bj)
+            for (int bi = 0; bi < g->bdims[0]; ++bi)
+                g->bstate[brick_index(g, bi * BRICK, bj * BRICK, bk * BRICK)] = brick_state(g, bi, bj, bk);
 }
 
 /* returns 0 when the point is outside the grid box; *margin = distance (m) to the box */
@@ -310,6 +374,14 @@ static int trilinear(const grid_t *g, const double x[3], double *phi, double gra
         if (ci < 0) ci = 0;
         c[a] = ci;
         f[a] = u[a] - ci;
+    }
+    if (g->band > 0.0f) {   /* R17: a brick out of the band answers +-band, no gradient */
+        const signed char st = g->bstate[brick_index(g, c[0], c[1], c[2])];
+        if (st == -1 || st == -2) {
+            *phi = st == -1 ? (double)g->band : -(double)g->band;
+            grad[0] = grad[1] = grad[2] = 0.0;
+            return 1;
+        }
     }
     double v[2][2][2];
     for (int dk = 0; dk < 2; ++dk)
@@ -348,6 +420,33 @@ void or_query(const double *grid, const float lo[3], float h, const int dims[3],
         phi[i] = ok ? p : 0.0;
         for (int a = 0; a < 3; ++a) grad[3 * i + a] = ok ? gr[a] : 0.0;
     }
+}
+
+/* or_query on a grid held in bricked storage (R17); *n_stored, *n_bricks: the bricks kept */
+void or_query_band(const double *grid, const float lo[3], float h, const int dims[3], float band_voxels,
+                   const float *pts, int n, double *phi, double *grad, int *valid, int *n_stored, int *n_bricks) {
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    for (int a = 0; a < 3; ++a) { g.lo[a] = lo[a]; g.dims[a] = dims[a]; }
+    g.h = h;
+    g.val = (double *)grid;
+    grid_set_band(&g, band_voxels);
+    for (int i = 0; i < n; ++i) {
+        double x[3], gr[3], p;
+        load3(pts + 3 * i, x);
+        int ok = trilinear(&g, x, &p, gr, NULL);
+        valid[i] = ok;
+        phi[i] = ok ? p : 0.0;
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = ok ? gr[a] : 0.0;
+    }
+    int ns = 0, nb = 0;
+    if (g.bstate) {
+        nb = g.bdims[0] * g.bdims[1] * g.bdims[2];
+        for (int b = 0; b < nb; ++b) ns += g.bstate[b] == 1;
+    }
+    if (n_stored) *n_stored = ns;
+    if (n_bricks) *n_bricks = nb;
+    free(g.bstate);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -410,7 +509,7 @@ void or_destroy(or_world *w) {
     if (!w) return;
     for (int i = 0; i < w->n_assets; ++i) {
         asset_t *a = &w->assets[i];
-        free(a->V); free(a->T); free(a->S); free(a->grid.val); free(a->grid.done);
+        free(a->V); free(a->T); free(a->S); free(a->grid.val); free(a->grid.done); free(a->grid.bstate);
     }
     for (int i = 0; i < w->n_pairs; ++i) free(w->pc[i].c);
     free(w->assets); free(w->bodies); free(w->pairs); free(w->envs); free(w->pc);
@@ -444,10 +543,12 @@ static void grid_alloc(grid_t *g, const float lo[3], float h, const int dims[3],
     for (int a = 0; a < 3; ++a) { g->lo[a] = lo[a]; g->dims[a] = dims[a]; }
     g->h = h;
     long long n = (long long)dims[0] * dims[1] * dims[2];
-    free(g->val); free(g->done);
+    free(g->val); free(g->done); free(g->bstate);
     g->val = (double *)calloc(n, sizeof(double));
     g->done = lazy ? (unsigned char *)calloc(n, 1) : NULL;
     g->lazy = lazy;
+    g->bstate = NULL;
+    g->band = 0.0f;
 }
 
 int or_asset_bake(or_world *w, int asset, int res, float pad, int cubic, int lazy) {
@@ -456,6 +557,7 @@ int or_asset_bake(or_world *w, int asset, int res, float pad, int cubic, int laz
     or_grid_params(a->V, a->nv, res, pad, cubic, lo, &h, dims);
     grid_alloc(&a->grid, lo, h, dims, lazy);
     if (!lazy) or_bake_nodes(a->V, a->T, a->nt, lo, h, dims, NULL, 0, a->grid.val, w->cfg.n_threads);
+    grid_set_band(&a->grid, w->cfg.sdf_band);
     a->has_grid = 1;
     return 0;
 }
@@ -466,6 +568,7 @@ int or_asset_set_grid(or_world *w, int asset, const float lo[3], float h, const 
     grid_alloc(&a->grid, lo, h, dims, 0);
     long long n = (long long)dims[0] * dims[1] * dims[2];
     for (long long i = 0; i < n; ++i) a->grid.val[i] = values[i];
+    grid_set_band(&a->grid, w->cfg.sdf_band);
     a->has_grid = 1;
     return 0;
 }
@@ -915,6 +1018,32 @@ static void detect_pair(or_world *w, int pi) {
     free(c);
 }
 
+/* lazy bake: queue the nodes a lookup in cell c reads -- its 8 corners, or with bricked
+ * storage (R17) every node of its brick, which the brick's state depends on */
+static void queue_cell(grid_t *g, const int c[3], long long **need, long long *nn, long long *cap) {
+    int n0[3], n1[3];
+    for (int a = 0; a < 3; ++a) {
+        if (g->band > 0.0f) {
+            n0[a] = (c[a] / BRICK) * BRICK;
+            n1[a] = n0[a] + BRICK;
+            if (n1[a] > g->dims[a] - 1) n1[a] = g->dims[a] - 1;
+        } else {
+            n0[a] = c[a];
+            n1[a] = c[a] + 1;
+        }
+    }
+    if (g->band > 0.0f && g->bstate[brick_index(g, c[0], c[1], c[2])] != BRICK_UNKNOWN) return;
+    for (int k = n0[2]; k <= n1[2]; ++k)
+        for (int j = n0[1]; j <= n1[1]; ++j)
+            for (int i = n0[0]; i <= n1[0]; ++i) {
+                const long long id = gidx(g, i, j, k);
+                if (g->done[id]) continue;
+                g->done[id] = 2;    /* queued */
+                if (*nn == *cap) { *cap *= 2; *need = (long long *)realloc(*need, sizeof(long long) * *cap); }
+                (*need)[(*nn)++] = id;
+            }
+}
+
 /* lazy bake: compute every grid node the next detection will read */
 static double wall_seconds(void) {
     struct timespec ts;
@@ -950,14 +1079,10 @@ static void ensure_nodes(or_world *w) {
                     }
                     for (int k = c0[2]; k <= c1[2]; ++k)
                         for (int j = c0[1]; j <= c1[1]; ++j)
-                            for (int i = c0[0]; i <= c1[0]; ++i)
-                                for (int q = 0; q < 8; ++q) {
-                                    long long id = gidx(g, i + (q & 1), j + ((q >> 1) & 1), k + ((q >> 2) & 1));
-                                    if (g->done[id]) continue;
-                                    g->done[id] = 2;
-                                    if (nn == cap) { cap *= 2; need = (long long *)realloc(need, sizeof(long long) * cap); }
-                                    need[nn++] = id;
-                                }
+                            for (int i = c0[0]; i <= c1[0]; ++i) {
+                                const int c[3] = {i, j, k};
+                                queue_cell(g, c, &need, &nn, &cap);
+                            }
                 }
                 continue;
             }
@@ -976,13 +1101,7 @@ static void ensure_nodes(or_world *w) {
                     c[a] = ci;
                 }
                 if (!inside) continue;
-                for (int k = 0; k < 8; ++k) {
-                    long long id = gidx(g, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + ((k >> 2) & 1));
-                    if (g->done[id]) continue;
-                    g->done[id] = 2;    /* queued */
-                    if (nn == cap) { cap *= 2; need = (long long *)realloc(need, sizeof(long long) * cap); }
-                    need[nn++] = id;
-                }
+                queue_cell(g, c, &need, &nn, &cap);
             }
         }
         if (nn > 0) {
@@ -993,6 +1112,13 @@ static void ensure_nodes(or_world *w) {
             free(vals);
         }
         free(need);
+        if (g->band > 0.0f)   /* R17: states of the bricks whose nodes are now all baked */
+            for (int bk = 0; bk < g->bdims[2]; ++bk)
+                for (int bj = 0; bj < g->bdims[1]; ++bj)
+                    for (int bi = 0; bi < g->bdims[0]; ++bi) {
+                        signed char *st = &g->bstate[brick_index(g, bi * BRICK, bj * BRICK, bk * BRICK)];
+                        if (*st == BRICK_UNKNOWN) *st = brick_state(g, bi, bj, bk);
+                    }
     }
     w->bake_seconds += wall_seconds() - t0;
 }

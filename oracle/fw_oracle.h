@@ -62,6 +62,8 @@ void or_bake_nodes(const float *V, const int *T, int nt, const float lo[3], floa
                    double *phi, int n_threads);
 /* Trilinear value and analytic gradient (grid frame).  valid[i] = 0 when the point is
  * outside the grid box (phi/grad then 0). */
+void or_query_band(const double *grid, const float lo[3], float h, const int dims[3], float band_voxels,
+                   const float *pts, int n, double *phi, double *grad, int *valid, int *n_stored, int *n_bricks);
 void or_query(const double *grid, const float lo[3], float h, const int dims[3],
               const float *pts, int n, double *phi, double *grad, int *valid);
 
@@ -82,6 +84,7 @@ typedef struct {
     int contact_gen;         /* 0: one candidate per surface sample; 1: one per triangle of
                                 the point body's mesh, by local minimisation (R15) */
     int tri_iters;           /* steps of that minimisation */
+    float sdf_band;          /* R17 narrow band in voxels (bricks of 8^3 cells); 0 = dense */
 } or_config;
 
 typedef struct {             /* same layout as the ABI's fw_body_desc (104 bytes) */

@@ -37,7 +37,7 @@ class OrConfig(C.Structure):
                 ("cos_patch", C.c_double), ("max_patches", C.c_int), ("batch_size", C.c_int),
                 ("baumgarte", C.c_double), ("n_vel_iters", C.c_int), ("max_angvel", C.c_double),
                 ("margin_len", C.c_double), ("margin_dot", C.c_double), ("n_threads", C.c_int),
-                ("contact_gen", C.c_int), ("tri_iters", C.c_int)]
+                ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float)]
 
 
 CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("phi", np.float64),
@@ -75,6 +75,8 @@ def lib():
             L.or_bake_nodes.argtypes = [_f32, _i32, C.c_int, _f32, C.c_float, _i32, vp,
                                         C.c_longlong, _f64, C.c_int]
             L.or_query.argtypes = [_f64, _f32, C.c_float, _i32, _f32, C.c_int, _f64, _f64, _i32]
+            L.or_query_band.argtypes = [_f64, _f32, C.c_float, _i32, C.c_float, _f32, C.c_int, _f64, _f64, _i32,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.or_create.argtypes = [C.POINTER(OrConfig)]
             L.or_create.restype = vp
             L.or_destroy.argtypes = [vp]
@@ -194,6 +196,19 @@ def query(grid: np.ndarray, lo, h, dims, pts):
     return phi, grad, valid.astype(bool)
 
 
+def query_band(grid: np.ndarray, lo, h, dims, band_voxels: float, pts):
+    """query() with the grid held in narrow-band bricks (R17): (phi, grad, valid, bricks
+    stored, bricks in all)."""
+    g = np.ascontiguousarray(grid, dtype=np.float64).reshape(-1)
+    pts = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 3)
+    n = len(pts)
+    phi, grad, valid = np.zeros(n), np.zeros((n, 3)), np.zeros(n, np.int32)
+    ns, nb = C.c_int(), C.c_int()
+    lib().or_query_band(g, np.ascontiguousarray(lo, np.float32), h, np.ascontiguousarray(dims, np.int32),
+                        band_voxels, pts, n, phi, grad, valid, C.byref(ns), C.byref(nb))
+    return phi, grad, valid.astype(bool), ns.value, nb.value
+
+
 def reduce(cands: np.ndarray, cos_patch: float = 0.94, max_patches: int = 128,
            batch_size: int = 1024):
     """Algorithm 1 on a CANDIDATE_DTYPE array -> (contacts, n_patches, margin_len, margin_dot)."""
@@ -225,6 +240,7 @@ class OracleWorld:
         cfg.max_angvel = over.get("max_angvel", getattr(sim, "max_angvel", 0.0))
         cfg.contact_gen = over.get("contact_gen", 0)
         cfg.tri_iters = over.get("tri_iters", 16)
+        cfg.sdf_band = over.get("sdf_band", 0.0)
         cfg.margin_len = margin_len
         cfg.margin_dot = margin_dot
         cfg.n_threads = n_threads
