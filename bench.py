@@ -46,6 +46,7 @@ QUERY_BYTES_PER_SAMPLE = 16           # float4 sample point
 QUERY_BYTES_PER_CORNER = {False: 4, True: 2}   # 8 grid corners per query, float32 / float16
 CANDIDATE_BYTES = 32                  # (x, phi), (n, sample) written by the query, read by the reduction
 FACE_BYTES = 48                       # three float4 vertices of a face (per-triangle contact generation)
+BRICK_ENTRY_BYTES = 4                 # brick-table entry read per lookup (narrow-band bricked SDF)
 CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
@@ -288,6 +289,8 @@ def run_fw(args):
     sim = sc.sim
     tri_mode = args.contact_gen == "triangles"
     gen_cfg = {"contact_gen": 1, "tri_iters": args.tri_iters} if tri_mode else {}
+    if args.sdf_band > 0:
+        gen_cfg["sdf_band"] = args.sdf_band
     with torch.cuda.stream(stream):
         t_b = time.perf_counter()
         w = fw.world_from_scene(sc, fp16=fp16, stream=stream.cuda_stream, device=dev, **gen_cfg)
@@ -301,6 +304,13 @@ def run_fw(args):
             tests += int(d[0]) * int(d[1]) * int(d[2]) * len(a.tris)
     bake_info = {"s": bake_s, "grid_nodes": nodes, "nodes_per_s": nodes / bake_s,
                  "brute_force_point_triangle_tests_per_s": tests / bake_s}
+    storage = {"band_voxels": args.sdf_band, "lookup_bytes": 0, "bricks_stored": 0, "bricks_total": 0}
+    for ai, a in enumerate(sc.assets):
+        if a.sdf_res:
+            nbytes, ns_b, nb_b = w.sdf_storage(ai)
+            storage["lookup_bytes"] += nbytes
+            storage["bricks_stored"] += ns_b
+            storage["bricks_total"] += nb_b
     shape = [int(v) for v in args.solve_shape.split(",")]
     w.set_solve_shape(*shape)
     tuned = None
@@ -356,6 +366,8 @@ def run_fw(args):
         q_bytes = queries * (FACE_BYTES + 8 * corner) + n_cand * CANDIDATE_BYTES
     else:
         q_bytes = queries * (QUERY_BYTES_PER_SAMPLE + 8 * corner) + n_cand * CANDIDATE_BYTES
+    if args.sdf_band > 0:
+        q_bytes += queries * BRICK_ENTRY_BYTES
     ns = queries / max(n_pair, 1)
     hbm, sm_max, peak_kind = _peaks()
     r_bytes = n_cand * CANDIDATE_BYTES + n_cont * CONTACT_BYTES
@@ -363,7 +375,8 @@ def run_fw(args):
     alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     src = _src_hash()
     # the table was taken on the default workload only (1000 M16 envs, FP32)
-    default_run = args.workload == "nut_bolt" and not fp16 and sc.n_envs == 1000 and not tri_mode
+    default_run = (args.workload == "nut_bolt" and not fp16 and sc.n_envs == 1000 and not tri_mode
+                   and args.sdf_band == 0)
     traffic = NCU_TRAFFIC.get(src, {}) if default_run else {}
     l2_traffic = NCU_L2.get(src, {}) if default_run else {}
     l2_gbs = fw.measure_l2_read(dev)   # untimed: the L2 roofline's denominator on this device
@@ -430,7 +443,9 @@ def run_fw(args):
                           ("faces_per_pair" if tri_mode else "samples_per_pair"): ns,
                           "contact_gen": args.contact_gen,
                           **({"tri_iters": args.tri_iters} if tri_mode else {}),
-                          "sdf": sdf_desc + (" fp16" if fp16 else " fp32"),
+                          "sdf": sdf_desc + (" fp16" if fp16 else " fp32")
+                                 + (f" narrow-band bricks ({args.sdf_band:g} voxels)" if args.sdf_band > 0 else ""),
+                          "sdf_storage": storage,
                           "substeps": sim.n_substeps,
                           "iters": sim.n_iters, "frame_dt": sim.dt, "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{ws}"},
@@ -532,6 +547,8 @@ def main():
                     help="samples: SDF query of the nut's surface samples; triangles: one contact per "
                          "face of the nut's mesh by local minimisation over the face")
     ap.add_argument("--tri-iters", type=int, default=16, help="descent steps per face (triangles)")
+    ap.add_argument("--sdf-band", type=float, default=0.0,
+                    help="narrow-band bricked SDF storage, band half-width in voxels (0: dense)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -80,6 +80,15 @@ typedef struct {
                                    then 1024 triangles and a contact's `sample` is the
                                    triangle index */
     int tri_iters;              /* descent steps per triangle (contact_gen = 1); default 16 */
+    float sdf_band;             /* narrow-band bricked SDF storage, band half-width in voxels;
+                                   0 (default): dense cell-corner copies.  Cells are grouped in
+                                   bricks of 8^3; a brick is kept when a node of its cells has
+                                   |phi| <= sdf_band * h or its nodes change sign, and a lookup
+                                   in a brick left out answers phi = +band (-band inside) with a
+                                   zero gradient, i.e. no candidate.  Every point with |phi| <=
+                                   band reads exactly the dense value (sparse SDF storage,
+                                   which the paper's Limitations section plans against the
+                                   grids' memory footprint) */
     int device;                 /* CUDA device ordinal, default 0 */
     void *cuda_stream;          /* cudaStream_t to enqueue on, NULL: the world's own */
 } fw_config;
@@ -169,6 +178,12 @@ FW_API fw_status fw_get_sdf(fw_world *w, int asset_id, float lo[3], float *h, in
 
 /* Mass properties used for the asset (density based): mass, centre of mass (asset
  * frame) and inertia about it (row-major 3x3), host arrays. */
+/* Device bytes of an asset's SDF lookup copy (the cell-corner copy, dense or bricked,
+ * plus the brick table) and, with narrow-band storage, the bricks kept and the bricks of
+ * the grid (both 0 when dense).  FW_ERR_STATE when the asset has no SDF.  Any pointer may
+ * be NULL. */
+FW_API fw_status fw_get_sdf_storage(fw_world *w, int asset_id, long long *cell_bytes, int *bricks_stored,
+                                    int *bricks_total);
 FW_API fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3],
                              double inertia[9]);
 

@@ -44,8 +44,8 @@
  *      or whose final gradient vanishes, makes no candidate; trial points outside the
  *      grid are rejected.  The candidate index is the triangle index, Generate batches
  *      are batch_size triangles.
- *   R17 narrow-band bricked storage (sdf_band > 0; the paper names sparse storage as the
- *      remedy for the grid's memory footprint without fixing a scheme): cells are grouped
+ *   R17 narrow-band bricked storage (sdf_band > 0; the Limitations section plans sparse
+ *      SDF storage against the grids' memory footprint without fixing a scheme): cells are grouped
  *      in bricks of 8^3; a brick is stored iff one node of its cells has |phi| <= band
  *      (band = sdf_band voxels, in float32: sdf_band * h) or its nodes change sign, the
  *      decision taken on the float32 node values.  A query in a cell of a brick that is

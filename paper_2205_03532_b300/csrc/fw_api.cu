@@ -27,6 +27,11 @@ struct AssetHost {
     float *d_grid = nullptr;
     float4 *d_cell32 = nullptr;   // cell-corner copies (AssetDev), one of them per the world's precision
     uint4 *d_cell16 = nullptr;
+    int *d_brick = nullptr;       // narrow-band brick table (AssetDev::brick), null when dense
+    int bdims[3] = {0, 0, 0};
+    int n_stored = 0;             // bricks kept
+    float band = 0;               // metres
+    long long cell_bytes = 0;     // bytes of the cell-corner copy
 };
 
 }  // namespace
@@ -194,6 +199,9 @@ AssetDev asset_view(const AssetHost &A, bool fp16) {
     g.grid = A.d_grid;
     g.cell32 = fp16 ? nullptr : A.d_cell32;
     g.cell16 = fp16 ? A.d_cell16 : nullptr;
+    g.brick = A.d_brick;
+    for (int a = 0; a < 3; ++a) g.bdims[a] = A.bdims[a];
+    g.band = A.band;
     for (int a = 0; a < 3; ++a) { g.lo[a] = A.lo[a]; g.dims[a] = A.dims[a]; }
     g.h = A.h;
     const double ih = A.h > 0 ? 1.0 / (double)A.h : 0.0;
@@ -318,6 +326,7 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.scratch = w->d_scratch;
     p.items = w->d_items;
     p.contact_gen = w->cfg.contact_gen;
+    p.sdf_bricks = w->cfg.sdf_band > 0.0f;
     p.multi_movable = 0;
     for (const auto &E : w->envs) p.multi_movable |= (E.movable == -2);
     p.tri_iters = w->cfg.tri_iters;
@@ -482,6 +491,7 @@ void fw_config_default(fw_config *c) {
     c->sdf_fp16 = 0;
     c->contact_gen = 0;
     c->tri_iters = 16;
+    c->sdf_band = 0.0f;
     c->device = 0;
     c->cuda_stream = nullptr;
 }
@@ -491,7 +501,7 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     *out = nullptr;
     if (cfg->batch_size != kBatch || cfg->patch_dirs != kSlots - 1 || cfg->max_patches < 1 ||
         cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0) || cfg->contact_gen < 0 || cfg->contact_gen > 1 ||
-        cfg->tri_iters < 0 || cfg->tri_iters > 1024)
+        cfg->tri_iters < 0 || cfg->tri_iters > 1024 || !(cfg->sdf_band >= 0.0f && cfg->sdf_band <= 1e6f))
         return FW_ERR_ARG;
     fw_world *w = new fw_world();
     w->cfg = *cfg;
@@ -527,6 +537,7 @@ fw_status fw_destroy(fw_world *w) {
     diff_free(w);
     for (auto &A : w->assets) {
         dfree(A.d_samples); dfree(A.d_tri); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
+        dfree(A.d_brick);
     }
     dfree(w->d_assets);
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
@@ -575,6 +586,16 @@ fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const 
     return FW_OK;
 }
 
+fw_status fw_get_sdf_storage(fw_world *w, int asset_id, long long *cell_bytes, int *bricks_stored, int *bricks_total) {
+    if (!w || asset_id < 0 || asset_id >= (int)w->assets.size()) return fail(w, FW_ERR_ARG, "bad asset");
+    const AssetHost &A = w->assets[asset_id];
+    if (!A.has_sdf) return fail(w, FW_ERR_STATE, "fw_get_sdf_storage: asset has no SDF");
+    if (cell_bytes) *cell_bytes = A.cell_bytes;
+    if (bricks_stored) *bricks_stored = A.d_brick ? A.n_stored : 0;
+    if (bricks_total) *bricks_total = A.d_brick ? A.bdims[0] * A.bdims[1] * A.bdims[2] : 0;
+    return FW_OK;
+}
+
 fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3], double inertia[9]) {
     if (!w || asset_id < 0 || asset_id >= (int)w->assets.size()) return fail(w, FW_ERR_ARG, "bad asset");
     const AssetHost &A = w->assets[asset_id];
@@ -586,14 +607,65 @@ fw_status fw_get_mass(fw_world *w, int asset_id, double *mass, double com[3], do
 
 static fw_status finish_grid(fw_world *w, AssetHost &A) {
     const long long nc = (long long)(A.dims[0] - 1) * (A.dims[1] - 1) * (A.dims[2] - 1);
+    const size_t cell = w->cfg.sdf_fp16 ? sizeof(uint4) : 2 * sizeof(float4);
     dfree(A.d_cell32);
     dfree(A.d_cell16);
-    if (w->cfg.sdf_fp16) {
+    dfree(A.d_brick);
+    A.n_stored = 0;
+    A.band = 0.0f;
+    for (int a = 0; a < 3; ++a) A.bdims[a] = 0;
+    if (w->cfg.sdf_band > 0.0f) {
+        // narrow-band bricks: flag every brick on the device, number the stored ones here,
+        // then copy their cells (the dense cell copy is never made)
+        A.band = w->cfg.sdf_band * A.h;
+        long long nb = 1;
+        for (int a = 0; a < 3; ++a) {
+            A.bdims[a] = (A.dims[a] - 1 + kBrick - 1) / kBrick;
+            nb *= A.bdims[a];
+        }
+        if (nb > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "narrow-band bricks: grid too large");
+        std::vector<int> flag((size_t)nb), of_slot;
+        CK(cudaMalloc(&A.d_brick, sizeof(int) * nb));
+        CK(launch_brick_flags(A.d_grid, A.dims, A.band, A.bdims, A.d_brick, w->stream));
+        CK(cudaMemcpyAsync(flag.data(), A.d_brick, sizeof(int) * nb, cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        for (long long b = 0; b < nb; ++b)
+            if (flag[b] == 1) { flag[b] = (int)of_slot.size(); of_slot.push_back((int)b); }
+        A.n_stored = (int)of_slot.size();
+        CK(cudaMemcpyAsync(A.d_brick, flag.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, w->stream));
+        const long long ncs = (long long)(A.n_stored > 0 ? A.n_stored : 1) * kBrickCells;   // >= 1 brick: a valid dummy
+        int *d_of_slot = nullptr;
+        if (A.n_stored > 0) {
+            CK(cudaMalloc(&d_of_slot, sizeof(int) * of_slot.size()));
+            CK(cudaMemcpyAsync(d_of_slot, of_slot.data(), sizeof(int) * of_slot.size(), cudaMemcpyHostToDevice,
+                               w->stream));
+        }
+        cudaError_t e;
+        if (w->cfg.sdf_fp16) {
+            e = cudaMalloc(&A.d_cell16, sizeof(uint4) * ncs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(A.d_cell16, 0, sizeof(uint4) * ncs, w->stream);
+            if (e == cudaSuccess)
+                e = launch_brick_cells(A.d_grid, A.dims, 1.0f / A.h, A.bdims, d_of_slot, A.n_stored, nullptr,
+                                       A.d_cell16, w->stream);
+        } else {
+            e = cudaMalloc(&A.d_cell32, sizeof(float4) * 2 * ncs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(A.d_cell32, 0, sizeof(float4) * 2 * ncs, w->stream);
+            if (e == cudaSuccess)
+                e = launch_brick_cells(A.d_grid, A.dims, 1.0f / A.h, A.bdims, d_of_slot, A.n_stored, A.d_cell32,
+                                       nullptr, w->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+        dfree(d_of_slot);
+        CK(e);
+        A.cell_bytes = (long long)cell * ncs + (long long)sizeof(int) * nb;
+    } else if (w->cfg.sdf_fp16) {
         CK(cudaMalloc(&A.d_cell16, sizeof(uint4) * nc));
         CK(launch_cells(A.d_grid, A.dims, 1.0f / A.h, nullptr, A.d_cell16, w->stream));
+        A.cell_bytes = (long long)cell * nc;
     } else {
         CK(cudaMalloc(&A.d_cell32, sizeof(float4) * 2 * nc));
         CK(launch_cells(A.d_grid, A.dims, 1.0f / A.h, A.d_cell32, nullptr, w->stream));
+        A.cell_bytes = (long long)cell * nc;
     }
     CK(cudaStreamSynchronize(w->stream));
     A.has_sdf = true;
@@ -699,6 +771,7 @@ fw_status fw_bake_sdf(fw_world *w, int asset_id, int resolution, float padding_m
     dfree(A.d_grid);
     dfree(A.d_cell32);
     dfree(A.d_cell16);
+    dfree(A.d_brick);
     CK(cudaMalloc(&A.d_grid, sizeof(float) * n_nodes));
     CK(cudaMalloc(&d_tri, sizeof(float) * tri.size()));
     CK(cudaMalloc(&d_pn, sizeof(float) * pn.size()));

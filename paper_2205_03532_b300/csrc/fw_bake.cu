@@ -208,8 +208,26 @@ __global__ void winding_fix_kernel(const float *tri, int nt, AssetDev g, float *
     }
 }
 
-// Cell-corner copy of a node grid (layout in AssetDev); float16 cells hold phi / h
-// rounded to nearest.
+// Corners of cell (i, j, k) of a node grid written as entry `dst` of a cell-corner copy
+// (layout in AssetDev); float16 cells hold phi / h rounded to nearest.
+__device__ __forceinline__ void write_cell(const float *grid, long long nx, long long nxy, long long i, long long j,
+                                           long long k, float inv_h, float4 *c32, uint4 *c16, long long dst) {
+    const float *b = grid + k * nxy + j * nx + i;
+    const float v[8] = {b[0], b[1], b[nx], b[nx + 1], b[nxy], b[nxy + 1], b[nxy + nx], b[nxy + nx + 1]};
+    if (c16) {
+        unsigned u[4];
+        for (int q = 0; q < 4; ++q) {
+            const __half2 hh = __halves2half2(__float2half_rn(v[2 * q] * inv_h), __float2half_rn(v[2 * q + 1] * inv_h));
+            u[q] = *reinterpret_cast<const unsigned *>(&hh);
+        }
+        c16[dst] = make_uint4(u[0], u[1], u[2], u[3]);
+    } else {
+        c32[2 * dst] = make_float4(v[0], v[1], v[2], v[3]);
+        c32[2 * dst + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+// Dense cell-corner copy of a node grid: cell (i, j, k), i fastest.
 __global__ void cells_kernel(const float *grid, int nx, int ny, int nz, float inv_h, float4 *c32, uint4 *c16) {
     const long long cnx = nx - 1, cny = ny - 1, n = cnx * cny * (long long)(nz - 1);
     const long long nxy = (long long)nx * ny;
@@ -217,19 +235,59 @@ __global__ void cells_kernel(const float *grid, int nx, int ny, int nz, float in
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (; c < n; c += stride) {
         const long long i = c % cnx, j = (c / cnx) % cny, k = c / (cnx * cny);
-        const float *b = grid + k * nxy + j * nx + i;
-        const float v[8] = {b[0], b[1], b[nx], b[nx + 1], b[nxy], b[nxy + 1], b[nxy + nx], b[nxy + nx + 1]};
-        if (c16) {
-            unsigned u[4];
-            for (int q = 0; q < 4; ++q) {
-                const __half2 hh = __halves2half2(__float2half_rn(v[2 * q] * inv_h), __float2half_rn(v[2 * q + 1] * inv_h));
-                u[q] = *reinterpret_cast<const unsigned *>(&hh);
-            }
-            c16[c] = make_uint4(u[0], u[1], u[2], u[3]);
-        } else {
-            c32[2 * c] = make_float4(v[0], v[1], v[2], v[3]);
-            c32[2 * c + 1] = make_float4(v[4], v[5], v[6], v[7]);
+        write_cell(grid, nx, nxy, i, j, k, inv_h, c32, c16, c);
+    }
+}
+
+// Narrow band: one warp per brick reads the nodes of its cells (those of a partial brick
+// at the grid's far faces stop at the last node) and flags it 1 if a node has |phi| <=
+// band or the nodes change sign, else -1 (all above +band) or -2 (all below -band).
+__global__ void brick_flags_kernel(const float *grid, int nx, int ny, int nz, float band, int bx, int by, int bz,
+                                   int *flag) {
+    const int lane = threadIdx.x & 31;
+    const long long nb = (long long)bx * by * bz;
+    const long long wpb = blockDim.x >> 5;
+    const long long stride = (long long)gridDim.x * wpb;
+    for (long long b = blockIdx.x * wpb + (threadIdx.x >> 5); b < nb; b += stride) {   // warp-uniform
+        const int bi = (int)(b % bx), bj = (int)((b / bx) % by), bk = (int)(b / ((long long)bx * by));
+        const int i0 = bi * kBrick, j0 = bj * kBrick, k0 = bk * kBrick;
+        const int ni = min(i0 + kBrick, nx - 1) - i0 + 1, nj = min(j0 + kBrick, ny - 1) - j0 + 1;
+        const int nk = min(k0 + kBrick, nz - 1) - k0 + 1;
+        const int n = ni * nj * nk;
+        bool near = false, pos = false, neg = false;
+        for (int q = lane; q < n; q += 32) {
+            const int i = i0 + q % ni, j = j0 + (q / ni) % nj, k = k0 + q / (ni * nj);
+            const float v = grid[((long long)k * ny + j) * nx + i];
+            near |= fabsf(v) <= band;
+            if (v < 0.0f) neg = true; else pos = true;
         }
+        near = __any_sync(0xffffffffu, near);
+        pos = __any_sync(0xffffffffu, pos);
+        neg = __any_sync(0xffffffffu, neg);
+        if (lane == 0) flag[b] = (near || (pos && neg)) ? 1 : (neg ? -2 : -1);
+    }
+}
+
+// Cell-corner copies of the stored bricks: cell (li, lj, lk) of slot s is entry
+// s * kBrickCells + (lk * kBrick + lj) * kBrick + li; cells past the grid's last cell (a
+// partial brick) are zero and never read.
+__global__ void brick_cells_kernel(const float *grid, int nx, int ny, int nz, float inv_h, int bx, int by,
+                                   const int *brick_of_slot, int n_stored, float4 *c32, uint4 *c16) {
+    const long long n = (long long)n_stored * kBrickCells;
+    const long long nxy = (long long)nx * ny;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const int b = brick_of_slot[t / kBrickCells];
+        const int l = (int)(t % kBrickCells);
+        const long long i = (long long)(b % bx) * kBrick + (l & (kBrick - 1));
+        const long long j = (long long)((b / bx) % by) * kBrick + ((l >> kBrickLog) & (kBrick - 1));
+        const long long k = (long long)(b / (bx * by)) * kBrick + (l >> (2 * kBrickLog));
+        if (i >= nx - 1 || j >= ny - 1 || k >= nz - 1) {
+            if (c16) c16[t] = make_uint4(0u, 0u, 0u, 0u);
+            else { c32[2 * t] = make_float4(0.f, 0.f, 0.f, 0.f); c32[2 * t + 1] = make_float4(0.f, 0.f, 0.f, 0.f); }
+            continue;
+        }
+        write_cell(grid, nx, nxy, i, j, k, inv_h, c32, c16, t);
     }
 }
 
@@ -253,6 +311,21 @@ cudaError_t launch_bake_fix_sign(const float *d_tri, int n_tri, const AssetDev &
 cudaError_t launch_cells(const float *grid, const int dims[3], float inv_h, float4 *cell32, uint4 *cell16,
                          cudaStream_t s) {
     cells_kernel<<<148 * 8, 256, 0, s>>>(grid, dims[0], dims[1], dims[2], inv_h, cell32, cell16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_flags(const float *grid, const int dims[3], float band, const int bdims[3], int *flags,
+                               cudaStream_t s) {
+    brick_flags_kernel<<<148 * 8, 256, 0, s>>>(grid, dims[0], dims[1], dims[2], band, bdims[0], bdims[1], bdims[2],
+                                               flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_cells(const float *grid, const int dims[3], float inv_h, const int bdims[3],
+                               const int *brick_of_slot, int n_stored, float4 *cell32, uint4 *cell16, cudaStream_t s) {
+    if (n_stored <= 0) return cudaSuccess;
+    brick_cells_kernel<<<148 * 8, 256, 0, s>>>(grid, dims[0], dims[1], dims[2], inv_h, bdims[0], bdims[1],
+                                               brick_of_slot, n_stored, cell32, cell16);
     return cudaGetLastError();
 }
 

@@ -117,12 +117,13 @@ __device__ __forceinline__ void load_pose(const SimParams &p, int body, M3 &R, V
 
 // The narrow phase of one sample: world point, world normal and signed distance.  False
 // when the point is outside the SDF grid or the gradient vanishes (|grad| < 1e-12).
+template <int kStore = kStoreAny>
 __device__ __forceinline__ bool query_sample(const PairXf &X, const AssetDev &gb, float4 s, V3 &xw, V3 &nw,
                                              float &phi) {
     xw = mul(X.RA, v3(s.x, s.y, s.z)) + X.pA;
     const V3 xb = mul_t(X.RB, xw - X.pB);
     V3 g;
-    const bool in = sdf_lookup_any(gb, xb, phi, g);
+    const bool in = sdf_lookup_any<kStore>(gb, xb, phi, g);
     const float gg = dot(g, g);
     const V3 nb = rsqrtf(fmaxf(gg, 1e-30f)) * g;   // unit to a few ulp; the decisions on it have margins
     nw = mul(X.RB, nb);
@@ -160,13 +161,14 @@ __device__ V3 tri_closest(V3 p, V3 a, V3 b, V3 c) {
 // x 1.5), else rejected (step x 0.5); it ends after `iters` steps or when the in-plane
 // gradient falls below 1e-9.  False when the centroid lies outside the grid; trial points
 // outside the grid are rejected.
+template <int kStore = kStoreAny>
 __device__ bool tri_minimise(const AssetDev &gb, V3 a, V3 b, V3 c, int iters, V3 &x, float &phi, V3 &g) {
     const V3 e1 = b - a, e2 = c - a, e3 = c - b;
     V3 nt = cross(e1, e2);
     const float nn = dot(nt, nt);
     nt = nn > 0.0f ? rsqrtf(nn) * nt : v3(0.0f, 0.0f, 0.0f);
     x = (1.0f / 3.0f) * ((a + b) + c);
-    if (!sdf_lookup_any(gb, x, phi, g)) return false;
+    if (!sdf_lookup_any<kStore>(gb, x, phi, g)) return false;
     float s = 0.5f * sqrtf(fmaxf(dot(e1, e1), fmaxf(dot(e2, e2), dot(e3, e3))));
     for (int it = 0; it < iters; ++it) {
         const V3 d = g - dot(g, nt) * nt;
@@ -175,7 +177,7 @@ __device__ bool tri_minimise(const AssetDev &gb, V3 a, V3 b, V3 c, int iters, V3
         const V3 xt = tri_closest(x - (s * rsqrtf(dd)) * d, a, b, c);
         float pt;
         V3 gt;
-        if (sdf_lookup_any(gb, xt, pt, gt) && pt < phi) {
+        if (sdf_lookup_any<kStore>(gb, xt, pt, gt) && pt < phi) {
             x = xt; phi = pt; g = gt;
             s *= 1.5f;
         } else {
@@ -188,6 +190,7 @@ __device__ bool tri_minimise(const AssetDev &gb, V3 a, V3 b, V3 c, int iters, V3
 // Triangle t of body a's mesh, minimised against body b's SDF: world point on the face,
 // world normal, phi.  False when there is no candidate point (centroid outside the grid,
 // vanishing gradient).
+template <int kStore = kStoreAny>
 __device__ __forceinline__ bool tri_sample(const PairXf &X, const AssetDev &ga, const AssetDev &gb, int t, int iters,
                                            V3 &xw, V3 &nw, float &phi) {
     V3 v[3];
@@ -197,7 +200,7 @@ __device__ __forceinline__ bool tri_sample(const PairXf &X, const AssetDev &ga, 
         v[k] = mul_t(X.RB, mul(X.RA, v3(s.x, s.y, s.z)) + X.pA - X.pB);
     }
     V3 x, g;
-    const bool in = tri_minimise(gb, v[0], v[1], v[2], iters, x, phi, g);
+    const bool in = tri_minimise<kStore>(gb, v[0], v[1], v[2], iters, x, phi, g);
     const float gg = dot(g, g);
     nw = mul(X.RB, rsqrtf(fmaxf(gg, 1e-30f)) * g);
     xw = mul(X.RB, x) + X.pB;
@@ -596,7 +599,7 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 }
 
 // ---------------------------------------------------------------------------------------
-template <bool kTri>
+template <bool kTri, int kStore>
 __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const int item = blockIdx.x;
     const int2 it = p.items[item];
@@ -617,11 +620,12 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
         const int i = base + u * kQueryThreads + tid;
         if (kTri) {   // one candidate per triangle of the mesh
             const int ic = i < ga.nt ? i : ga.nt - 1;
-            ok[u] = tri_sample(X, ga, gb, ic, p.tri_iters, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.nt);
+            ok[u] = tri_sample<kStore>(X, ga, gb, ic, p.tri_iters, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) &&
+                    (i < ga.nt);
         } else {      // one per surface sample
             const int ic = i < ga.ns ? i : ga.ns - 1;
             const float4 s = __ldg(&ga.samples[ic]);
-            ok[u] = query_sample(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
+            ok[u] = query_sample<kStore>(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
         }
     }
     // compaction in sample order: local sample u * 256 + warp * 32 + lane
@@ -870,10 +874,13 @@ cudaError_t prepare_detect(int max_patches) {
 
 cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    if (p.contact_gen == 1)
-        query_kernel<true><<<p.n_items, kQueryThreads, 0, s>>>(p);
-    else
-        query_kernel<false><<<p.n_items, kQueryThreads, 0, s>>>(p);
+    if (p.sdf_bricks) {
+        if (p.contact_gen == 1) query_kernel<true, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        else query_kernel<false, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);
+    } else {
+        if (p.contact_gen == 1) query_kernel<true, kStoreDense><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        else query_kernel<false, kStoreDense><<<p.n_items, kQueryThreads, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -102,18 +102,39 @@ __device__ __forceinline__ bool grid_coord(float x, float lo, float inv_h, float
 
 __device__ __forceinline__ float lerp_(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
+// Storage of the cell-corner copies a lookup is compiled for: dense, narrow-band bricks,
+// or either, decided per asset at run time.
+enum : int { kStoreDense = 0, kStoreBricks = 1, kStoreAny = 2 };
+
+// Entry of cell (ci, cj, ck) in the asset's cell-corner copy: dense (x fastest), or with
+// narrow-band bricks the cell's place in its brick's slot.  st: the brick's table entry
+// (0 when dense); st < 0 means the brick is not stored, and the entry returned is then a
+// valid dummy (0) so that the load can still be issued unconditionally.
+template <int kStore = kStoreAny>
+__device__ __forceinline__ long long cell_offset(const AssetDev &g, int ci, int cj, int ck, int &st) {
+    if (kStore == kStoreDense || (kStore == kStoreAny && !g.brick)) {
+        st = 0;
+        const long long cnx = g.dims[0] - 1, cnxy = cnx * (long long)(g.dims[1] - 1);
+        return (long long)ck * cnxy + (long long)cj * cnx + ci;
+    }
+    st = __ldg(g.brick + ((ck >> kBrickLog) * g.bdims[1] + (cj >> kBrickLog)) * g.bdims[0] + (ci >> kBrickLog));
+    const int l = ((ck & (kBrick - 1)) << (2 * kBrickLog)) | ((cj & (kBrick - 1)) << kBrickLog) | (ci & (kBrick - 1));
+    return st >= 0 ? (long long)st * kBrickCells + l : 0;
+}
+
 // Trilinear value and gradient from the cell-corner copy; the corner loads (one or two
 // 16-byte loads) are always in bounds and issued before the in-grid test is used, so
-// several lookups can overlap their memory latency.
-template <bool kHalf>
+// several lookups can overlap their memory latency.  A cell of a brick left out of the
+// narrow band answers phi = +band (or -band inside) with a zero gradient.
+template <bool kHalf, int kStore = kStoreAny>
 __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
     int ci, cj, ck;
     float fx, fy, fz;
     const bool okx = grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx);
     const bool oky = grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy);
     const bool okz = grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz);
-    const long long cnx = g.dims[0] - 1, cnxy = cnx * (long long)(g.dims[1] - 1);
-    const long long o = (long long)ck * cnxy + (long long)cj * cnx + ci;
+    int st;
+    const long long o = cell_offset<kStore>(g, ci, cj, ck, st);
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if (kHalf) {
         const uint4 c = __ldg(g.cell16 + o);
@@ -144,11 +165,16 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
         phi = val;
         grad = g.inv_h * v3(gx, gy, gz);
     }
+    if (st < 0) {
+        phi = st == -1 ? g.band : -g.band;
+        grad = v3(0.0f, 0.0f, 0.0f);
+    }
     return okx && oky && okz;
 }
 
+template <int kStore = kStoreAny>
 __device__ __forceinline__ bool sdf_lookup_any(const AssetDev &g, V3 x, float &phi, V3 &grad) {
-    return g.cell16 ? sdf_lookup<true>(g, x, phi, grad) : sdf_lookup<false>(g, x, phi, grad);
+    return g.cell16 ? sdf_lookup<true, kStore>(g, x, phi, grad) : sdf_lookup<false, kStore>(g, x, phi, grad);
 }
 
 // Order-preserving map of a float to uint32 (larger float -> larger integer).

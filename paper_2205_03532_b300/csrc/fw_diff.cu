@@ -73,8 +73,8 @@ __device__ void cell_eval(const AssetDev &g, const int c[3], V3 x, float &phi, V
     const float fx = grid_frac(x.x, g.lo[0], g.inv_h, g.inv_h_lo, c[0]);
     const float fy = grid_frac(x.y, g.lo[1], g.inv_h, g.inv_h_lo, c[1]);
     const float fz = grid_frac(x.z, g.lo[2], g.inv_h, g.inv_h_lo, c[2]);
-    const long long cnx = g.dims[0] - 1, cnxy = cnx * (long long)(g.dims[1] - 1);
-    const long long o = (long long)c[2] * cnxy + (long long)c[1] * cnx + c[0];
+    int st;   // a taped cell made a candidate, so with narrow-band bricks its brick is stored
+    const long long o = cell_offset<kStoreAny>(g, c[0], c[1], c[2], st);
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if (g.cell16) {
         const uint4 q = g.cell16[o];

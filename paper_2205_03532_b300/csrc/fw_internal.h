@@ -36,6 +36,13 @@ struct AssetDev {
     int ns;
     int nt;                  // triangles of the mesh
     const float4 *tri;       // 3 per triangle: asset-frame vertices (x, y, z, 0)
+    // Narrow-band bricked storage (world option sdf_band > 0): cells grouped in bricks of
+    // kBrick^3; brick[b] is the slot of a stored brick in cell32/cell16 (kBrickCells cells
+    // each, x fastest inside the brick), or -1 / -2 for a brick left out because all its
+    // nodes are above +band / below -band.  NULL: dense cell-corner copy.
+    const int *brick;
+    int bdims[3];            // bricks per axis
+    float band;              // metres
 };
 
 struct BodyProps {           // constant per body
@@ -116,8 +123,13 @@ struct SimParams {
     int *cand_count;                       // n_items
     int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
     int multi_movable;                     // some env has several movable bodies (general sweep form)
+    int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks
     int tri_iters;                         // descent steps per triangle
 };
+
+constexpr int kBrickLog = 3;                          // narrow-band bricks of 8^3 cells
+constexpr int kBrick = 1 << kBrickLog;
+constexpr int kBrickCells = kBrick * kBrick * kBrick;
 
 // launchers (defined in the .cu files)
 cudaError_t launch_bake(const float *d_tri, int n_tri, const float *d_tri_pn, const float *d_tile_box,
@@ -127,6 +139,12 @@ cudaError_t launch_bake_fix_sign(const float *d_tri, int n_tri, const AssetDev &
 cudaError_t launch_cells(const float *grid, const int dims[3], float inv_h, float4 *cell32, uint4 *cell16,
                          cudaStream_t s);   // one of cell32 / cell16 non-null
 int bake_tile_size();
+// narrow-band bricks: per brick 1 (stored), -1 or -2 (out of band outside / inside)
+cudaError_t launch_brick_flags(const float *grid, const int dims[3], float band, const int bdims[3], int *flags,
+                               cudaStream_t s);
+// cell-corner copies of the stored bricks (one of cell32 / cell16 non-null)
+cudaError_t launch_brick_cells(const float *grid, const int dims[3], float inv_h, const int bdims[3],
+                               const int *brick_of_slot, int n_stored, float4 *cell32, uint4 *cell16, cudaStream_t s);
 cudaError_t launch_query_sdf(const AssetDev &g, const float *pts, int n, float *phi, float *grad,
                              cudaStream_t s);
 cudaError_t launch_query_pair(const SimParams &p, int pair, float *phi, float *nrm, cudaStream_t s, int ns);

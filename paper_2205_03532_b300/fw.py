@@ -23,7 +23,7 @@ STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_OOM", -3: "FW_ERR_CUDA", -4:
 
 # every function include/fw.h declares
 ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_asset", "fw_bake_sdf",
-                 "fw_set_sdf", "fw_get_sdf", "fw_get_mass", "fw_add_env_bodies", "fw_step",
+                 "fw_set_sdf", "fw_get_sdf", "fw_get_sdf_storage", "fw_get_mass", "fw_add_env_bodies", "fw_step",
                  "fw_substep", "fw_collide", "fw_get_contacts", "fw_set_contacts", "fw_get_state",
                  "fw_set_state", "fw_query_sdf", "fw_query_pair", "fw_tri_contacts", "fw_reduce", "fw_reduce_noalloc", "fw_sync",
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
@@ -44,7 +44,8 @@ class FwConfig(C.Structure):
                 ("cos_patch", C.c_float), ("max_patches", C.c_int), ("patch_dirs", C.c_int),
                 ("batch_size", C.c_int),
                 ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
-                ("sdf_fp16", C.c_int), ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("device", C.c_int),
+                ("sdf_fp16", C.c_int), ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float),
+                ("device", C.c_int),
                 ("cuda_stream", C.c_void_p)]
 
 
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "fw_set_sdf": (st, [vp, i, vp, f, vp, vp]),
         "fw_get_sdf": (st, [vp, i, vp, C.POINTER(f), vp, vp]),
         "fw_get_mass": (st, [vp, i, vp, vp, vp]),
+        "fw_get_sdf_storage": (st, [vp, i, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
         "fw_add_env_bodies": (st, [vp, i, vp, i, vp, i, C.POINTER(i)]),
         "fw_step": (st, [vp, i, i]),
         "fw_substep": (st, [vp, f, i, i]),
@@ -207,6 +209,13 @@ class World:
             vals = np.zeros((dims[2], dims[1], dims[0]), np.float32)
             self._check(self.lib.fw_get_sdf(self.h, asset, None, None, None, vals.ctypes.data))
         return lo, np.float32(h.value), dims, vals
+
+    def sdf_storage(self, asset: int):
+        """(bytes of the SDF lookup copy, bricks kept, bricks in all) (fw_get_sdf_storage;
+        the brick counts are 0 for dense storage)"""
+        b, ns, nb = C.c_longlong(), C.c_int(), C.c_int()
+        self._check(self.lib.fw_get_sdf_storage(self.h, asset, C.byref(b), C.byref(ns), C.byref(nb)))
+        return int(b.value), int(ns.value), int(nb.value)
 
     def get_mass(self, asset: int):
         m, com, I = np.zeros(1), np.zeros(3), np.zeros(9)
