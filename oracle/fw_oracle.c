@@ -53,6 +53,13 @@
  *      with a zero gradient, so it makes no candidate (R4).  Since a trilinear value is a
  *      convex combination of its cell's corners, every point with |phi| <= band lies in
  *      a stored brick and reads the dense value there.
+ *   R18 Jacobi solver (solver = 1; the paper's solver comparison sizes a Jacobi solver at
+ *      8 substeps x 64 iterations without stating its update): a sweep computes every
+ *      contact's block update -- the normal row, then the friction rows with that
+ *      contact's own normal change applied, projected on the disk -- from the velocities
+ *      at the sweep's start, then takes all of them with the weight omega = 1 / (number
+ *      of contacts that can act), impulses and velocities alike (a convex step towards
+ *      each block's answer, so impulses stay in the friction cone).
  */
 #include "fw_oracle.h"
 
@@ -1340,6 +1347,49 @@ static void sweep(body_t *bodies, row_t *rows, int nr, double (*Iinv)[9], int us
     }
 }
 
+/* R18: one Jacobi sweep over the env's rows */
+static void sweep_jacobi(body_t *bodies, row_t *rows, int nr, double (*Iinv)[9], int use_bias) {
+    int na = 0;
+    for (int r = 0; r < nr; ++r) na += rows[r].kn != 0.0;
+    if (na == 0) return;
+    const double om = 1.0 / (double)na;
+    double *d = (double *)malloc(sizeof(double) * 3 * nr);
+    for (int r = 0; r < nr; ++r) {   /* block updates at the sweep's start velocities */
+        const row_t *R = &rows[r];
+        d[3 * r] = d[3 * r + 1] = d[3 * r + 2] = 0.0;
+        if (R->kn == 0.0) continue;
+        body_t A = bodies[R->a], B = bodies[R->b];   /* copies: the sweep-start state */
+        double vr[3], p[3];
+        rel_vel(&A, &B, R->ra, R->rb, vr);
+        double vn = v_dot(R->n, vr) + (use_bias ? R->bias : 0.0);
+        double ln = R->ln - R->kn * vn;
+        if (ln < 0.0) ln = 0.0;
+        const double dl = ln - R->ln;
+        v_scale(R->n, dl, p);
+        apply_impulse(&A, &B, Iinv[R->a], Iinv[R->b], R->ra, R->rb, p);
+        rel_vel(&A, &B, R->ra, R->rb, vr);
+        double l1 = R->lt1 - R->kt1 * v_dot(R->t1, vr);
+        double l2 = R->lt2 - R->kt2 * v_dot(R->t2, vr);
+        const double lim = R->mu * ln;
+        const double lt = sqrt(l1 * l1 + l2 * l2);
+        if (lt > lim) {
+            const double s = lt > 0.0 ? lim / lt : 0.0;
+            l1 *= s; l2 *= s;
+        }
+        d[3 * r] = dl; d[3 * r + 1] = l1 - R->lt1; d[3 * r + 2] = l2 - R->lt2;
+    }
+    for (int r = 0; r < nr; ++r) {   /* all of them, weighted */
+        row_t *R = &rows[r];
+        if (R->kn == 0.0) continue;
+        const double dl = om * d[3 * r], d1 = om * d[3 * r + 1], d2 = om * d[3 * r + 2];
+        R->ln += dl; R->lt1 += d1; R->lt2 += d2;
+        double p[3];
+        for (int i = 0; i < 3; ++i) p[i] = dl * R->n[i] + d1 * R->t1[i] + d2 * R->t2[i];
+        apply_impulse(&bodies[R->a], &bodies[R->b], Iinv[R->a], Iinv[R->b], R->ra, R->rb, p);
+    }
+    free(d);
+}
+
 static void env_substep(or_world *w, int e, double hs, int n_iters) {
     const env_t *E = &w->envs[e];
     body_t *bodies = &w->bodies[E->first_body];
@@ -1393,8 +1443,11 @@ static void env_substep(or_world *w, int e, double hs, int n_iters) {
             R->mu = P->mu;
         }
     }
-    /* 4. Gauss-Seidel sweeps */
-    for (int it = 0; it < n_iters; ++it) sweep(bodies, rows, nr, Iinv, 1);
+    /* 4. Gauss-Seidel sweeps (R9), or Jacobi sweeps (R18) */
+    for (int it = 0; it < n_iters; ++it) {
+        if (w->cfg.solver == 1) sweep_jacobi(bodies, rows, nr, Iinv, 1);
+        else sweep(bodies, rows, nr, Iinv, 1);
+    }
     /* 5. integrate */
     for (int i = 0; i < nb; ++i) {
         body_t *b = &bodies[i];
@@ -1419,7 +1472,10 @@ static void env_substep(or_world *w, int e, double hs, int n_iters) {
         v_sub(c, rc, b->p);
     }
     /* 6. optional bias-free sweeps */
-    for (int it = 0; it < w->cfg.n_vel_iters; ++it) sweep(bodies, rows, nr, Iinv, 0);
+    for (int it = 0; it < w->cfg.n_vel_iters; ++it) {
+        if (w->cfg.solver == 1) sweep_jacobi(bodies, rows, nr, Iinv, 0);
+        else sweep(bodies, rows, nr, Iinv, 0);
+    }
     /* friction-cone record of this solve: (lambda_n, |lambda_t|, mu) per row */
     double *rec = (double *)malloc(sizeof(double) * 3 * (nr > 0 ? nr : 1));
     for (int k = 0; k < nr; ++k) {
@@ -2133,7 +2189,7 @@ static void diff_env_reverse(or_world *w, const dfwd_t *F, double xb[13], double
 /* ---- public entry points ---- */
 
 int or_diff_record(or_world *w, int n_substeps, int n_iters) {
-    if (w->cfg.n_vel_iters != 0 || n_substeps < 1 || n_iters < 0) return -1;
+    if (w->cfg.n_vel_iters != 0 || w->cfg.solver != 0 || n_substeps < 1 || n_iters < 0) return -1;
     for (int e = 0; e < w->n_envs; ++e)
         if (diff_env_body(w, e) == -1) return -1;
     diff_tape_free(w);

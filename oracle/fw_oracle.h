@@ -85,6 +85,7 @@ typedef struct {
                                 the point body's mesh, by local minimisation (R15) */
     int tri_iters;           /* steps of that minimisation */
     float sdf_band;          /* R17 narrow band in voxels (bricks of 8^3 cells); 0 = dense */
+    int solver;              /* 0: Gauss-Seidel (R9); 1: weighted Jacobi (R18) */
 } or_config;
 
 typedef struct {             /* same layout as the ABI's fw_body_desc (104 bytes) */

@@ -37,7 +37,8 @@ class OrConfig(C.Structure):
                 ("cos_patch", C.c_double), ("max_patches", C.c_int), ("batch_size", C.c_int),
                 ("baumgarte", C.c_double), ("n_vel_iters", C.c_int), ("max_angvel", C.c_double),
                 ("margin_len", C.c_double), ("margin_dot", C.c_double), ("n_threads", C.c_int),
-                ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float)]
+                ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float),
+                ("solver", C.c_int)]
 
 
 CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("phi", np.float64),
@@ -241,6 +242,7 @@ class OracleWorld:
         cfg.contact_gen = over.get("contact_gen", 0)
         cfg.tri_iters = over.get("tri_iters", 16)
         cfg.sdf_band = over.get("sdf_band", 0.0)
+        cfg.solver = over.get("solver", 0)
         cfg.margin_len = margin_len
         cfg.margin_dot = margin_dot
         cfg.n_threads = n_threads
