@@ -291,6 +291,12 @@ def run_fw(args):
     gen_cfg = {"contact_gen": 1, "tri_iters": args.tri_iters} if tri_mode else {}
     if args.sdf_band > 0:
         gen_cfg["sdf_band"] = args.sdf_band
+    if args.solver == "jacobi":
+        gen_cfg["solver"] = 1
+    if args.substeps > 0:
+        sim.n_substeps = args.substeps
+    if args.iters > 0:
+        sim.n_iters = args.iters
     with torch.cuda.stream(stream):
         t_b = time.perf_counter()
         w = fw.world_from_scene(sc, fp16=fp16, stream=stream.cuda_stream, device=dev, **gen_cfg)
@@ -376,7 +382,7 @@ def run_fw(args):
     src = _src_hash()
     # the table was taken on the default workload only (1000 M16 envs, FP32)
     default_run = (args.workload == "nut_bolt" and not fp16 and sc.n_envs == 1000 and not tri_mode
-                   and args.sdf_band == 0)
+                   and args.sdf_band == 0 and args.solver == "gs" and args.substeps == 0 and args.iters == 0)
     traffic = NCU_TRAFFIC.get(src, {}) if default_run else {}
     l2_traffic = NCU_L2.get(src, {}) if default_run else {}
     l2_gbs = fw.measure_l2_read(dev)   # untimed: the L2 roofline's denominator on this device
@@ -408,6 +414,8 @@ def run_fw(args):
     dominant = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roof["kernel"] = dominant
+    # deepest contact over a sample of envs at the end of the run (a stability indicator)
+    deepest = min([float(w.get_contacts(e)["phi"].min(initial=np.inf)) for e in range(0, n_env, max(1, n_env // 64))])
     single = None
     if tri_mode:
         single = single_pair_generate(sc, gen_cfg, fp16, dev)
@@ -441,7 +449,7 @@ def run_fw(args):
                "config": {"workload": wl_name + ("_per_triangle" if tri_mode else ""),
                           "n_envs": n_env, "pairs_per_env": n_pair / max(n_env, 1),
                           ("faces_per_pair" if tri_mode else "samples_per_pair"): ns,
-                          "contact_gen": args.contact_gen,
+                          "contact_gen": args.contact_gen, "solver": args.solver,
                           **({"tri_iters": args.tri_iters} if tri_mode else {}),
                           "sdf": sdf_desc + (" fp16" if fp16 else " fp32")
                                  + (f" narrow-band bricks ({args.sdf_band:g} voxels)" if args.sdf_band > 0 else ""),
@@ -452,7 +460,7 @@ def run_fw(args):
                "roofline": roof, "kernels": kernels,
                "phase_ms_per_frame": {"query": qry_ms * sim.n_substeps, "reduce": red_ms * sim.n_substeps,
                                       "solve": sol_ms * sim.n_substeps},
-               "contacts_per_env": c_mean, "candidates_per_pair": n_cand / max(n_pair, 1),
+               "contacts_per_env": c_mean, "deepest_contact_m": deepest, "candidates_per_pair": n_cand / max(n_pair, 1),
                "solve_shape": list(w.solve_shape()), "autotuned": tuned is not None,
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),
@@ -547,6 +555,10 @@ def main():
                     help="samples: SDF query of the nut's surface samples; triangles: one contact per "
                          "face of the nut's mesh by local minimisation over the face")
     ap.add_argument("--tri-iters", type=int, default=16, help="descent steps per face (triangles)")
+    ap.add_argument("--solver", default="gs", choices=["gs", "jacobi"],
+                    help="gs: projected Gauss-Seidel; jacobi: weighted Jacobi (one movable body per env)")
+    ap.add_argument("--substeps", type=int, default=0, help="substeps per frame (0: the workload's)")
+    ap.add_argument("--iters", type=int, default=0, help="solver sweeps per substep (0: the workload's)")
     ap.add_argument("--sdf-band", type=float, default=0.0,
                     help="narrow-band bricked SDF storage, band half-width in voxels (0: dense)")
     args = ap.parse_args()

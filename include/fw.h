@@ -89,6 +89,13 @@ typedef struct {
                                    band reads exactly the dense value (sparse SDF storage,
                                    which the paper's Limitations section plans against the
                                    grids' memory footprint) */
+    int solver;                 /* 0 (default): projected Gauss-Seidel; 1: weighted Jacobi --
+                                   per sweep every contact's block update (normal row, then
+                                   friction rows with its own normal change, disk projection)
+                                   from the sweep-start velocities, all taken with weight
+                                   1 / (contacts that can act); envs with at most one movable
+                                   body; no adjoint (the solver the paper's solver comparison
+                                   sizes at 8 substeps x 64 iterations) */
     int device;                 /* CUDA device ordinal, default 0 */
     void *cuda_stream;          /* cudaStream_t to enqueue on, NULL: the world's own */
 } fw_config;

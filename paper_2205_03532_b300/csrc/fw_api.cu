@@ -352,6 +352,8 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     for (const auto &E : w->envs) rc = std::max(rc, E.row_cap);
     if (w->lam_rows > 0 && w->lam_rows < rc) rc = w->lam_rows;   // envs with more rows: global impulses
     p.lam_cap = rc <= kLamCapMax ? rc : 0;   // larger envs take the general sweep
+    p.solver = w->cfg.solver;
+    if (p.solver == 1) p.lam_cap = 0;         // Jacobi keeps its impulses in the rows
     return p;
 }
 
@@ -492,6 +494,7 @@ void fw_config_default(fw_config *c) {
     c->contact_gen = 0;
     c->tri_iters = 16;
     c->sdf_band = 0.0f;
+    c->solver = 0;
     c->device = 0;
     c->cuda_stream = nullptr;
 }
@@ -501,7 +504,8 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     *out = nullptr;
     if (cfg->batch_size != kBatch || cfg->patch_dirs != kSlots - 1 || cfg->max_patches < 1 ||
         cfg->max_patches > kMaxPatchesCap || !(cfg->dt > 0) || cfg->contact_gen < 0 || cfg->contact_gen > 1 ||
-        cfg->tri_iters < 0 || cfg->tri_iters > 1024 || !(cfg->sdf_band >= 0.0f && cfg->sdf_band <= 1e6f))
+        cfg->tri_iters < 0 || cfg->tri_iters > 1024 || !(cfg->sdf_band >= 0.0f && cfg->sdf_band <= 1e6f) ||
+        cfg->solver < 0 || cfg->solver > 1)
         return FW_ERR_ARG;
     fw_world *w = new fw_world();
     w->cfg = *cfg;
@@ -915,6 +919,8 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
             const int t = bd[e * n_per_env + i].type;
             if (t == FW_BODY_DYNAMIC || t == FW_BODY_FIXED_AXIS) E.movable = (E.movable == -1) ? i : -2;
         }
+        if (E.movable == -2 && w->cfg.solver == 1)
+            return fail(w, FW_ERR_ARG, "fw_add_env_bodies: the Jacobi solver takes envs with one movable body");
         for (int k = 0; k < n_pairs; ++k) {
             PairDev P;
             memset(&P, 0, sizeof P);
@@ -1391,6 +1397,7 @@ fw_status fw_record_rollout(fw_world *w, int n_substeps, int n_iters) {
     if (!ready(w)) return FW_ERR_ARG;
     if (n_substeps < 1 || n_iters < 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: bad substeps/iterations");
     if (w->cfg.n_vel_iters != 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: needs n_vel_iters = 0");
+    if (w->cfg.solver != 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: needs the Gauss-Seidel solver");
     fw_status st = ensure_device(w);
     if (st != FW_OK) return st;
     std::vector<int> dyn;

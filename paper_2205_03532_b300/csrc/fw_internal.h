@@ -124,6 +124,7 @@ struct SimParams {
     int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
     int multi_movable;                     // some env has several movable bodies (general sweep form)
     int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks
+    int solver;                            // 0: Gauss-Seidel; 1: weighted Jacobi
     int tri_iters;                         // descent steps per triangle
 };
 

@@ -448,10 +448,78 @@ __device__ __forceinline__ int warp_max(int v) {
 
 // One substep's solve for kGroups envs per warp (G = 32 / kGroups lanes each) and
 // blockDim.x / 32 warps per block.  No block-wide barrier: every warp is independent.
-// kMulti: the world has envs with several movable bodies, whose general-form sweeps keep
-// their impulses in shared memory (sweep_general); without it that code is compiled out.
-template <int kGroups, bool kMulti>
+// n_sweeps weighted Jacobi sweeps (solver = 1) over an env's nr fast rows by its group of
+// G lanes.  Every lane holds the whole body velocity u = (v, w).  Per sweep each lane takes
+// rows gl, gl + G, ...: the contact's block update from the sweep-start velocity -- S_n from
+// the scaled Jacobian, the normal clamp, S_1 and S_2 with the contact's own normal change
+// (K_1, K_2), the projection on the disk -- and sums its velocity changes; the group adds
+// the lanes' sums, and all impulses and the velocity move by omega = 1 / (rows that can
+// act, those with a nonzero normal Jacobian).  The impulses live in the row's float4 13
+// (a Jacobi row has no neighbour couplings), so no shared memory is needed.
+template <int G, bool kBias>
+__device__ void sweep_jacobi(float4 *rows_, int nr, int n_sweeps, V3 &va, V3 &wa, int gl) {
+    // the sweep reads a row's coefficients (float4 0-12) and reads and writes its impulses
+    // (float4 13) through separate pointers, so the next rows' loads may move ahead of the
+    // impulse stores
+    const float4 *__restrict__ rows = rows_;
+    float4 *__restrict__ imp = rows_ + 13;
+    int na = 0;
+    for (int r = gl; r < nr; r += G) {
+        const float4 f0 = rows[kRowF4 * r];
+        na += (f0.x != 0.0f || f0.y != 0.0f || f0.z != 0.0f);
+    }
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) na += __shfl_xor_sync(0xffffffffu, na, off);
+    const float om = na > 0 ? 1.0f / (float)na : 0.0f;
+    for (int it = 0; it < n_sweeps; ++it) {
+        V3 dv = v3(0.0f, 0.0f, 0.0f), dw = v3(0.0f, 0.0f, 0.0f);
+#pragma unroll 2
+        for (int r = gl; r < nr; r += G) {
+            const float4 *f = rows + kRowF4 * r;
+            const float4 f0 = f[0], f1 = f[1], f2 = f[2], f3 = f[3], f4 = f[4], f5 = f[5];
+            const float4 f6 = f[6], f7 = f[7], f8 = f[8], f9 = f[9], f10 = f[10], f11 = f[11];
+            const float4 f12 = f[12], L = imp[kRowF4 * r];
+            const float sn = dot(v3(f0.x, f0.y, f0.z), va) + (kBias ? f0.w : f3.w) + dot(v3(f6.x, f6.y, f6.z), wa);
+            const float ln = fmaxf(L.x + sn, 0.0f);
+            const float dn = ln - L.x;
+            const float s1 = dot(v3(f1.x, f1.y, f1.z), va) + f1.w + dot(v3(f7.x, f7.y, f7.z), wa) + f12.x * dn;
+            const float s2 = dot(v3(f2.x, f2.y, f2.z), va) + f2.w + dot(v3(f8.x, f8.y, f8.z), wa) + f12.y * dn;
+            float l1 = L.y + s1, l2 = L.z + s2;
+            const float lim = f12.z * ln;
+            const float lt = sqrtf(l1 * l1 + l2 * l2);
+            if (lt > lim) {
+                const float sc = lt > 0.0f ? lim / lt : 0.0f;
+                l1 *= sc;
+                l2 *= sc;
+            }
+            const float d1 = l1 - L.y, d2 = l2 - L.z;
+            dv = dv + dn * v3(f3.x, f3.y, f3.z) + d1 * v3(f4.x, f4.y, f4.z) + d2 * v3(f5.x, f5.y, f5.z);
+            dw = dw + dn * v3(f9.x, f9.y, f9.z) + d1 * v3(f10.x, f10.y, f10.z) + d2 * v3(f11.x, f11.y, f11.z);
+            imp[kRowF4 * r] = make_float4(L.x + om * dn, L.y + om * d1, L.z + om * d2, 0.0f);
+        }
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+            dv.x += __shfl_xor_sync(0xffffffffu, dv.x, off);
+            dv.y += __shfl_xor_sync(0xffffffffu, dv.y, off);
+            dv.z += __shfl_xor_sync(0xffffffffu, dv.z, off);
+            dw.x += __shfl_xor_sync(0xffffffffu, dw.x, off);
+            dw.y += __shfl_xor_sync(0xffffffffu, dw.y, off);
+            dw.z += __shfl_xor_sync(0xffffffffu, dw.z, off);
+        }
+        va = va + om * dv;
+        wa = wa + om * dw;
+    }
+}
+
+// Solve variants: Gauss-Seidel for worlds whose envs have at most one movable body, the
+// same with the general form for several movable bodies (sweep_general: impulses in
+// shared memory), and the weighted Jacobi solver; each is compiled only into its own
+// kernel so the others keep their code and registers.
+enum : int { kVarGS = 0, kVarMulti = 1, kVarJacobi = 2 };
+
+template <int kGroups, int kVar>
 __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams p) {
+    constexpr bool kMulti = kVar == kVarMulti, kJacobi = kVar == kVarJacobi;
     constexpr int G = 32 / kGroups;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
@@ -520,7 +588,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     float4 *lam = env_base;
     float4 *ring = lam + p.lam_cap;
     const int m = E.movable;
-    const bool fast = (m != -2) && nr <= p.lam_cap;
+    const bool fast = (m != -2) && (kJacobi || nr <= p.lam_cap);
     // several movable bodies: general rows, impulses in shared memory when they fit
     const bool general_sm = kMulti && (m == -2) && nr <= p.lam_cap;
     float4 *frows = reinterpret_cast<float4 *>(rows);
@@ -532,9 +600,12 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         for (int i = gl; i < cnt; i += G) {
             const DContact &c = p.contacts[(long long)pi * p.cap_pair + i];
             if (fast) {
+                // Jacobi keeps its impulses in the row (float4 13, zeroed here) and has no
+                // shared-memory impulse words: its lam region is empty (lam_cap = 0)
+                float4 unused;
                 if (m >= 0)
-                    build_fast_row(frows + kRowF4 * (S.row_base[k] + i), lam[S.row_base[k] + i], c, B, P.local_a,
-                                   P.local_b, m, P.mu, hs, p.baumgarte);
+                    build_fast_row(frows + kRowF4 * (S.row_base[k] + i), kJacobi ? unused : lam[S.row_base[k] + i], c,
+                                   B, P.local_a, P.local_b, m, P.mu, hs, p.baumgarte);
             } else {
                 build_row(rows[S.row_base[k] + i], c, B, P.local_a, P.local_b, P.mu, hs, p.baumgarte);
                 if (kMulti && general_sm) lam[S.row_base[k] + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -543,7 +614,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     }
     __threadfence_block();
     __syncwarp();
-    if (fast && m >= 0) {
+    if (!kJacobi && fast && m >= 0) {
         for (int r = gl; r < nr; r += G) couple_fast_row(frows + kRowF4 * r, frows + kRowF4 * (r + 1 < nr ? r + 1 : 0));
     }
     __threadfence_block();
@@ -555,7 +626,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         const int trips = warp_max<G>(total);
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
         if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
-        sweep_fast<G, true>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
+        if (kJacobi) sweep_jacobi<G, true>(frows, run_fast ? nr : 0, p.n_iters, va, wa, gl);
+        else sweep_fast<G, true>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
     }
     if (valid && !fast && gl == 0) {
@@ -604,7 +676,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         const int trips = warp_max<G>(total);
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
         if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
-        sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
+        if (kJacobi) sweep_jacobi<G, false>(frows, run_fast ? nr : 0, p.n_vel_iters, va, wa, gl);
+        else sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
         if (valid && !fast && gl == 0) {
             if (kMulti && general_sm) sweep_general(rows, nr, p.n_vel_iters, ring, lam, B, false);
@@ -643,15 +716,28 @@ size_t solve_smem_bytes(int lam_cap) { return sizeof(float4) * (size_t)env_strid
 
 template <int kGroups>
 static cudaError_t prepare_one(int optin, int *max_dyn) {
-    cudaFuncAttributes a, b;
-    cudaError_t e = cudaFuncGetAttributes(&a, solve_kernel<kGroups, false>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, solve_kernel<kGroups, true>);
-    if (e != cudaSuccess) return e;
-    *max_dyn = optin - (int)(a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes);
-    e = cudaFuncSetAttribute(solve_kernel<kGroups, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_kernel<kGroups, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
-    return e;
+    void (*const k[3])(SimParams) = {solve_kernel<kGroups, kVarGS>, solve_kernel<kGroups, kVarMulti>,
+                                     solve_kernel<kGroups, kVarJacobi>};
+    size_t stat = 0;
+    for (int v = 0; v < 3; ++v) {
+        cudaFuncAttributes a;
+        cudaError_t e = cudaFuncGetAttributes(&a, k[v]);
+        if (e != cudaSuccess) return e;
+        if (a.sharedSizeBytes > stat) stat = a.sharedSizeBytes;
+    }
+    *max_dyn = optin - (int)stat;
+    for (int v = 0; v < 3; ++v) {
+        cudaError_t e = cudaFuncSetAttribute(k[v], cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int kGroups>
+static void launch_variant(const SimParams &p, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (p.solver == 1) solve_kernel<kGroups, kVarJacobi><<<grid, block, smem, s>>>(p);
+    else if (p.multi_movable) solve_kernel<kGroups, kVarMulti><<<grid, block, smem, s>>>(p);
+    else solve_kernel<kGroups, kVarGS><<<grid, block, smem, s>>>(p);
 }
 
 cudaError_t prepare_solve(int optin, int max_dyn[4]) {
@@ -691,17 +777,10 @@ cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t 
     const int per_block = sh.groups * sh.warps;
     const int blocks = (p.n_envs + per_block - 1) / per_block;
     const dim3 grid(blocks), block(32 * sh.warps);
-    if (p.multi_movable) {
-        if (sh.groups == 1) solve_kernel<1, true><<<grid, block, sh.smem, s>>>(p);
-        else if (sh.groups == 2) solve_kernel<2, true><<<grid, block, sh.smem, s>>>(p);
-        else if (sh.groups == 4) solve_kernel<4, true><<<grid, block, sh.smem, s>>>(p);
-        else solve_kernel<8, true><<<grid, block, sh.smem, s>>>(p);
-    } else {
-        if (sh.groups == 1) solve_kernel<1, false><<<grid, block, sh.smem, s>>>(p);
-        else if (sh.groups == 2) solve_kernel<2, false><<<grid, block, sh.smem, s>>>(p);
-        else if (sh.groups == 4) solve_kernel<4, false><<<grid, block, sh.smem, s>>>(p);
-        else solve_kernel<8, false><<<grid, block, sh.smem, s>>>(p);
-    }
+    if (sh.groups == 1) launch_variant<1>(p, grid, block, sh.smem, s);
+    else if (sh.groups == 2) launch_variant<2>(p, grid, block, sh.smem, s);
+    else if (sh.groups == 4) launch_variant<4>(p, grid, block, sh.smem, s);
+    else launch_variant<8>(p, grid, block, sh.smem, s);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ class FwConfig(C.Structure):
                 ("batch_size", C.c_int),
                 ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
                 ("sdf_fp16", C.c_int), ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float),
-                ("device", C.c_int),
+                ("solver", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p)]
 
 

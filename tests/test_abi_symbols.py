@@ -36,13 +36,13 @@ def test_library_exports_nothing_else():
 def test_config_defaults_without_gpu():
     cfg = fw.default_config()
     assert cfg.batch_size == 1024 and cfg.max_patches == 128 and cfg.patch_dirs == 6
-    assert cfg.contact_gen == 0 and cfg.tri_iters == 16 and cfg.sdf_band == 0.0
+    assert cfg.contact_gen == 0 and cfg.tri_iters == 16 and cfg.sdf_band == 0.0 and cfg.solver == 0
     assert abs(cfg.dt - 1 / 60) < 1e-7 and abs(cfg.gravity[2] + 9.81) < 1e-6
     assert abs(cfg.contact_offset - 1e-4) < 1e-9 and abs(cfg.cos_patch - 0.94) < 1e-7
 
 
 def test_struct_layouts_match_header(tmp_path):
-    assert ctypes.sizeof(fw.FwConfig) == 80   # 17 four-byte values (gravity has 3), padding, a pointer
+    assert ctypes.sizeof(fw.FwConfig) == 80   # 18 four-byte values (gravity has 3), then a pointer
     # every field offset of the binding's fw_config against the C compiler's, from the header
     names = [f[0] for f in fw.FwConfig._fields_]
     src = tmp_path / "offsets.c"
