@@ -207,6 +207,87 @@ __device__ __forceinline__ bool tri_sample(const PairXf &X, const AssetDev &ga, 
     return in && (gg >= 1e-24f);
 }
 
+// Per-triangle Generate of one work item, one descent step per loop trip.  A thread takes
+// its faces u * kQueryThreads + tid (u = 0 .. kQueryPerThread - 1) one after another and
+// starts the next face as soon as one ends, so a warp's lanes stay busy while their faces
+// need different numbers of steps; the steps of a face are exactly those of tri_minimise
+// (centroid lookup, then up to `iters` projected steps while the in-plane gradient is
+// above 1e-9), and every trip makes at most one SDF lookup from one place in the code.
+// The pose X is read from shared memory.  Face u's candidate goes to
+// res[2 (u kQueryThreads + tid)] = (x_w, phi), res[... + 1] = (n_w, 0); bit u of the
+// result is set when it is one.
+template <int kStore>
+__device__ unsigned tri_batch(const PairXf &X, const AssetDev &ga, const AssetDev &gb, int base, int tid, int iters,
+                              float cutoff, float4 *res) {
+    unsigned okb = 0;
+    int u = 0, it = 0;
+    bool start = true;
+    V3 a = v3(0.f, 0.f, 0.f), b = a, c = a, nt = a, x = a, g = a;
+    float phi = 0.0f, s = 0.0f;
+    while (u < kQueryPerThread) {
+        const int i = base + u * kQueryThreads + tid;
+        V3 q;
+        bool look = true;
+        if (start) {
+            const int t = i < ga.nt ? i : ga.nt - 1;
+            V3 v[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 w4 = __ldg(&ga.tri[3 * t + k]);
+                v[k] = mul_t(X.RB, mul(X.RA, v3(w4.x, w4.y, w4.z)) + X.pA - X.pB);
+            }
+            a = v[0]; b = v[1]; c = v[2];
+            const V3 e1 = b - a, e2 = c - a, e3 = c - b;
+            nt = cross(e1, e2);
+            const float nn = dot(nt, nt);
+            nt = nn > 0.0f ? rsqrtf(nn) * nt : v3(0.0f, 0.0f, 0.0f);
+            q = (1.0f / 3.0f) * ((a + b) + c);
+            s = 0.5f * sqrtf(fmaxf(dot(e1, e1), fmaxf(dot(e2, e2), dot(e3, e3))));
+        } else {
+            const V3 d = g - dot(g, nt) * nt;
+            const float dd = dot(d, d);
+            look = it < iters && dd > 1e-18f;
+            q = look ? tri_closest(x - (s * rsqrtf(dd)) * d, a, b, c) : x;
+        }
+        float pt = 0.0f;
+        V3 gt = v3(0.0f, 0.0f, 0.0f);
+        bool in = false;
+        if (look) in = sdf_lookup_any<kStore>(gb, q, pt, gt);
+        bool done = false, cand = false;
+        if (start) {
+            x = q; phi = pt; g = gt; it = 0;
+            start = false;
+            done = !in;                       // centroid outside the grid: no candidate
+        } else if (look) {
+            if (in && pt < phi) {
+                x = q; phi = pt; g = gt;
+                s *= 1.5f;
+            } else {
+                s *= 0.5f;
+            }
+            ++it;
+        } else {
+            done = true;
+            cand = true;
+        }
+        if (done) {
+            const float gg = dot(g, g);
+            cand = cand && gg >= 1e-24f && phi < cutoff && i < ga.nt;
+            if (cand) {
+                const V3 nw = mul(X.RB, rsqrtf(fmaxf(gg, 1e-30f)) * g);
+                const V3 xw = mul(X.RB, x) + X.pB;
+                const int o = 2 * (u * kQueryThreads + tid);
+                res[o] = make_float4(xw.x, xw.y, xw.z, phi);
+                res[o + 1] = make_float4(nw.x, nw.y, nw.z, 0.0f);
+                okb |= 1u << u;
+            }
+            ++u;
+            start = true;
+        }
+    }
+    return okb;
+}
+
 __device__ __forceinline__ unsigned long long slot_key(float score, int sample) {
     return ((unsigned long long)ord_f32(score) << 32) | (unsigned)(0xFFFFFFFFu - (unsigned)sample);
 }
@@ -607,22 +688,35 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const PairDev P = p.pairs[pi];
     const AssetDev ga = p.assets[P.asset_a];
     const AssetDev gb = p.assets[P.asset_b];
-    PairXf X;
-    load_pose(p, P.a, X.RA, X.pA);
-    load_pose(p, P.b, X.RB, X.pB);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float cutoff = p.contact_offset;
     V3 xw[kQueryPerThread], nw[kQueryPerThread];
     float ph[kQueryPerThread];
     bool ok[kQueryPerThread];
+    if (kTri) {   // one candidate per triangle of the mesh, the pose shared in shared memory
+        __shared__ PairXf Xs;
+        __shared__ float4 tres[2 * kBatch];
+        if (tid == 0) {
+            load_pose(p, P.a, Xs.RA, Xs.pA);
+            load_pose(p, P.b, Xs.RB, Xs.pB);
+        }
+        __syncthreads();
+        const unsigned okb = tri_batch<kStore>(Xs, ga, gb, base, tid, p.tri_iters, cutoff, tres);
 #pragma unroll
-    for (int u = 0; u < kQueryPerThread; ++u) {
-        const int i = base + u * kQueryThreads + tid;
-        if (kTri) {   // one candidate per triangle of the mesh
-            const int ic = i < ga.nt ? i : ga.nt - 1;
-            ok[u] = tri_sample<kStore>(X, ga, gb, ic, p.tri_iters, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) &&
-                    (i < ga.nt);
-        } else {      // one per surface sample
+        for (int u = 0; u < kQueryPerThread; ++u) {   // the thread's own results
+            ok[u] = (okb >> u) & 1u;
+            const float4 r0 = tres[2 * (u * kQueryThreads + tid)], r1 = tres[2 * (u * kQueryThreads + tid) + 1];
+            xw[u] = v3(r0.x, r0.y, r0.z);
+            ph[u] = r0.w;
+            nw[u] = v3(r1.x, r1.y, r1.z);
+        }
+    } else {      // one per surface sample
+        PairXf X;
+        load_pose(p, P.a, X.RA, X.pA);
+        load_pose(p, P.b, X.RB, X.pB);
+#pragma unroll
+        for (int u = 0; u < kQueryPerThread; ++u) {
+            const int i = base + u * kQueryThreads + tid;
             const int ic = i < ga.ns ? i : ga.ns - 1;
             const float4 s = __ldg(&ga.samples[ic]);
             ok[u] = query_sample<kStore>(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);

@@ -153,3 +153,23 @@ def test_one_frame_with_per_triangle_contacts():
     rot = np.array(rot)
     assert np.all(rot <= 1e-2) and np.mean(rot <= 2e-3) >= 0.75, rot
     gw.close()
+
+
+def test_substep_generate_equals_the_per_face_hook(tri_pair):
+    """The substep's Generate (each thread streams the descent steps of its four faces)
+    and the per-face hook (one face per thread) take the same steps: every contact's
+    point and phi equal the hook's for its face bit for bit; the normal, the same
+    expression compiled in two places, to a couple of float32 ulps."""
+    sc, gw, ow = tri_pair
+    nt = len(sc.assets[0].tris)
+    gw.collide()
+    checked = 0
+    for env in range(sc.n_envs):
+        c = gw.get_contacts(env)
+        x, phi, nrm = gw.tri_contacts(env, 0, nt)
+        f = c["sample"]
+        np.testing.assert_array_equal(c["xa"], x[f])
+        np.testing.assert_array_equal(c["phi"], phi[f])
+        np.testing.assert_allclose(c["n"], nrm[f], rtol=0, atol=2.5e-7)
+        checked += len(c)
+    assert checked > 50
