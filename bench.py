@@ -136,6 +136,8 @@ WORKLOADS = {
               "synthetic (procedural ISO M8-M20 nut/bolt meshes, sizes and poses seeded)"),
     "gears": ("gear_scene", 2048, "gear_train_z20_z30_z40", "256^3",
               "synthetic (procedural involute spur gears, seeded phases)"),
+    "pile": ("pile_scene", 256, "nut_pile_7xM16", "128^3",
+             "synthetic (procedural M16 nuts dropped on a plate, seeded poses)"),
 }
 
 
@@ -546,10 +548,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=0, help="envs of the oracle sample (0: one per core)")
     ap.add_argument("--ref-envs", type=int, default=0, help="envs of the reference arm's sample (0: one per core)")
-    ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "gears", "diff_peg"],
+    ap.add_argument("--workload", default="nut_bolt", choices=["nut_bolt", "mixed", "gears", "pile", "diff_peg"],
                     help="nut_bolt: the headline substep benchmark (1000 M16 envs); mixed: 4096 envs of "
-                         "M8-M20 pairs; gears: 2048 three-gear trains (FP16 SDFs); diff_peg: gradient "
-                         "throughput of the differentiable peg")
+                         "M8-M20 pairs; gears: 2048 three-gear trains (FP16 SDFs); pile: 256 envs of 7 M16 "
+                         "nuts dropped on a plate; diff_peg: gradient throughput of the differentiable peg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default solve shape")
     ap.add_argument("--contact-gen", default="samples", choices=["samples", "triangles"],
                     help="samples: SDF query of the nut's surface samples; triangles: one contact per "

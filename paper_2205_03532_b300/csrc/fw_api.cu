@@ -32,6 +32,7 @@ struct AssetHost {
     int n_stored = 0;             // bricks kept
     float band = 0;               // metres
     long long cell_bytes = 0;     // bytes of the cell-corner copy
+    float radius = 0;             // bounding sphere about the asset origin (vertices and samples)
 };
 
 }  // namespace
@@ -202,6 +203,7 @@ AssetDev asset_view(const AssetHost &A, bool fp16) {
     g.brick = A.d_brick;
     for (int a = 0; a < 3; ++a) g.bdims[a] = A.bdims[a];
     g.band = A.band;
+    g.radius = A.radius;
     for (int a = 0; a < 3; ++a) { g.lo[a] = A.lo[a]; g.dims[a] = A.dims[a]; }
     g.h = A.h;
     const double ih = A.h > 0 ? 1.0 / (double)A.h : 0.0;
@@ -569,6 +571,14 @@ fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const 
     A.T.assign(tris, tris + 3 * n_tris);
     if (n_samples > 0) A.S.assign(sample_pts, sample_pts + 3 * n_samples);
     A.density = density;
+    {   // bounding radius, rounded up to float
+        double r2 = 0.0;
+        for (size_t k = 0; k + 2 < A.V.size(); k += 3)
+            r2 = std::max(r2, (double)A.V[k] * A.V[k] + (double)A.V[k + 1] * A.V[k + 1] + (double)A.V[k + 2] * A.V[k + 2]);
+        for (size_t k = 0; k + 2 < A.S.size(); k += 3)
+            r2 = std::max(r2, (double)A.S[k] * A.S[k] + (double)A.S[k + 1] * A.S[k + 1] + (double)A.S[k + 2] * A.S[k + 2]);
+        A.radius = std::nextafter((float)std::sqrt(r2), INFINITY);
+    }
     mass_props(A.V, A.T, density, A.mass, A.com, A.I);
     if (!(A.mass > 0)) return fail(w, FW_ERR_ARG, "fw_add_mesh_asset: mesh encloses no volume (winding?)");
     if (n_samples > 0) {

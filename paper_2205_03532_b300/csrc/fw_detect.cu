@@ -688,6 +688,18 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const PairDev P = p.pairs[pi];
     const AssetDev ga = p.assets[P.asset_a];
     const AssetDev gb = p.assets[P.asset_b];
+    // Broad phase: when the bodies' bounding spheres (about their origins, over every vertex
+    // and sample) are farther apart than the contact offset plus two voxels of the SDF, no
+    // point of A can come closer than that to B's surface, and the interpolated SDF is
+    // within sqrt(3) voxels of the distance: the item has no candidate.
+    {
+        const V3 dp = ld3(p.pos + 3 * P.a) - ld3(p.pos + 3 * P.b);
+        const float lim = ga.radius + gb.radius + p.contact_offset + 2.0f * gb.h;
+        if (dot(dp, dp) > lim * lim) {   // the same for every thread of the block
+            if (threadIdx.x == 0) p.cand_count[item] = 0;
+            return;
+        }
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float cutoff = p.contact_offset;
     V3 xw[kQueryPerThread], nw[kQueryPerThread];

@@ -43,6 +43,7 @@ struct AssetDev {
     const int *brick;
     int bdims[3];            // bricks per axis
     float band;              // metres
+    float radius;            // bounding sphere about the asset origin: every vertex and sample
 };
 
 struct BodyProps {           // constant per body

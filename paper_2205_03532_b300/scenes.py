@@ -795,3 +795,74 @@ def gear_scene(n_envs: int = 2048, seed: int = 0, module_mm: float = 1.0, backla
     pairs = np.array([[0, 1], [1, 2]], dtype=np.int32)
     sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, frames=frames)
     return Scene("gears", assets, [EnvGroup(bodies, pairs)], sim)
+
+
+# --------------------------------------------------------------------------------------
+# piles of nuts: several free bodies per env, coupled through their contacts
+# --------------------------------------------------------------------------------------
+def _random_quat(rng: np.random.Generator) -> np.ndarray:
+    """uniform random rotation (normalised Gaussian quaternion), w >= 0"""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    return q if q[3] >= 0 else -q
+
+
+def pile_scene(n_envs: int = 256, seed: int = 0, n_nuts: int = 7, mode: str = "drop", n_samples: int = 5000,
+               sdf_res: int = 128, mu: float = 0.3, n_substeps: int = 8, n_iters: int = 32,
+               frames: int = 120, sink_mm: float = 0.02) -> Scene:
+    """Piles of ISO M16 nuts (the M16 nut of nut_bolt_scene, 18,136 triangles, n_samples
+    samples and its own 128^3 SDF) on a static 120 x 120 x 10 mm plate whose top face is
+    z = 0.  Every nut is a free body; the pairs are nut -> plate for every nut and nut i ->
+    nut j (samples of i against the SDF of j) for every i < j, so an env couples up to
+    n_nuts + 1 <= 8 bodies through up to 28 pairs.
+
+    mode "drop": the nuts start at random orientations and positions (xy within +-25 mm,
+    heights 10-100 mm) with their bounding spheres 1 mm apart or more, and fall into a pile.
+    mode "stacks": resting stacks of one to three nuts lying flat (random yaw, xy offsets
+    of a stack's nuts within 1 mm), each nut sunk sink_mm into the one below (or the
+    plate), the stacks' bounding spheres apart: contacts from the first substep."""
+    if not 1 <= n_nuts <= 7:
+        raise ValueError("n_nuts must be 1..7 (8 bodies per env at most)")
+    rng = np.random.default_rng(seed)
+    P, af, _ = ISO_COARSE[16]
+    thick = 13.0e-3
+    nV, nT = nut_mesh(16, P, 13.0, af, 0.05, n_ang=84)
+    nut = Asset("nut_m16", nV, nT, sample_surface(nV, nT, n_samples, rng), 7800.0, sdf_res=sdf_res, sdf_pad=1e-3)
+    PV, PT = box_mesh(0.06, 0.06, 0.005)
+    plate = Asset("plate", PV, PT, None, 7800.0, sdf_res=sdf_res, sdf_pad=1e-3)
+    r = float(np.linalg.norm(nV, axis=1).max())
+    bodies = np.zeros((n_envs, n_nuts + 1), dtype=BODY_DTYPE)
+    for e in range(n_envs):
+        if mode == "drop":
+            pos = []
+            while len(pos) < n_nuts:
+                c = np.array([rng.uniform(-0.025, 0.025), rng.uniform(-0.025, 0.025), rng.uniform(0.010, 0.100)])
+                if c[2] - r < 0.0005:
+                    continue
+                if all(np.linalg.norm(c - o) >= 2 * r + 1e-3 for o in pos):
+                    pos.append(c)
+            for k, c in enumerate(pos):
+                bodies[e, k] = _body(0, DYNAMIC, tuple(c), _random_quat(rng), mu)
+        elif mode == "stacks":
+            heights = []
+            while sum(heights) < n_nuts:
+                heights.append(int(rng.integers(1, min(3, n_nuts - sum(heights)) + 1)))
+            centres = []
+            while len(centres) < len(heights):
+                c = rng.uniform(-0.045, 0.045, 2)
+                if all(np.linalg.norm(c - o) >= 2 * r + 1e-3 for o in centres):
+                    centres.append(c)
+            k = 0
+            for c, hgt in zip(centres, heights):
+                for level in range(hgt):
+                    z = thick / 2 + level * thick - (level + 1) * sink_mm * 1e-3
+                    xy = c + rng.uniform(-1e-3, 1e-3, 2)
+                    bodies[e, k] = _body(0, DYNAMIC, (xy[0], xy[1], z),
+                                         quat_axis_angle([0, 0, 1], rng.uniform(0, np.pi / 3)), mu)
+                    k += 1
+        else:
+            raise ValueError(f"unknown pile mode {mode!r}")
+        bodies[e, n_nuts] = _body(1, STATIC, (0.0, 0.0, -0.005), (0, 0, 0, 1), mu)
+    pairs = [(k, n_nuts) for k in range(n_nuts)] + [(i, j) for i in range(n_nuts) for j in range(i + 1, n_nuts)]
+    sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, frames=frames)
+    return Scene("pile", [nut, plate], [EnvGroup(bodies, np.array(pairs, np.int32))], sim)
