@@ -32,11 +32,11 @@ sys.path.insert(0, ROOT)
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the bench's own
     # timing-pass state: 332 contacts per env, 3,358 candidates per pair)
-    "6a01c476b71dc041": {"query_kernel": 54.26e6, "reduce_kernel": 108.20e6, "solve_kernel": 139.09e6},
+    "63ed1060a0af91fb": {"query_kernel": 54.40e6, "reduce_kernel": 108.15e6, "solve_kernel": 127.76e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "6a01c476b71dc041": {"query_kernel": 656.5e6, "reduce_kernel": 356.0e6, "solve_kernel": 4510.0e6},
+    "63ed1060a0af91fb": {"query_kernel": 655.8e6, "reduce_kernel": 356.4e6, "solve_kernel": 4495.0e6},
 }
 
 FP32_LANES_PER_SM = 128

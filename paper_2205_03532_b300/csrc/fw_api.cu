@@ -330,7 +330,11 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.contact_gen = w->cfg.contact_gen;
     p.sdf_bricks = w->cfg.sdf_band > 0.0f;
     p.multi_movable = 0;
-    for (const auto &E : w->envs) p.multi_movable |= (E.movable == -2);
+    p.broad_phase = 0;
+    for (const auto &E : w->envs) {
+        p.multi_movable |= (E.movable == -2);
+        p.broad_phase |= (E.n_pairs > 1);
+    }
     p.tri_iters = w->cfg.tri_iters;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;

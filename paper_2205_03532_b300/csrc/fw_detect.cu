@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     // and sample) are farther apart than the contact offset plus two voxels of the SDF, no
     // point of A can come closer than that to B's surface, and the interpolated SDF is
     // within sqrt(3) voxels of the distance: the item has no candidate.
-    {
+    if (p.broad_phase) {   // worlds whose envs hold several pairs
         const V3 dp = ld3(p.pos + 3 * P.a) - ld3(p.pos + 3 * P.b);
         const float lim = ga.radius + gb.radius + p.contact_offset + 2.0f * gb.h;
         if (dot(dp, dp) > lim * lim) {   // the same for every thread of the block

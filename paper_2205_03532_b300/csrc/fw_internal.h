@@ -126,6 +126,7 @@ struct SimParams {
     int multi_movable;                     // some env has several movable bodies (general sweep form)
     int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks
     int solver;                            // 0: Gauss-Seidel; 1: weighted Jacobi
+    int broad_phase;                       // some env has several pairs: skip pairs far apart
     int tri_iters;                         // descent steps per triangle
 };
 
