@@ -1,11 +1,15 @@
 // fw_detect.cu -- SDF narrow phase and contact reduction (Sec. III-A, III-C, Algorithm 1),
 // two kernels per substep.
 //
-// query_kernel: one CTA of 256 threads per work item (pair, Generate batch of 1024
-// samples).  Each thread queries 4 samples -- coalesced float4 sample loads, the 8-corner
-// gathers of all four in flight together -- and the CTA compacts the candidates
-// (phi < contact offset) in sample order into the item's slab of the candidate buffer:
-// per candidate the float4 pair (x_w, phi), (n_w, sample).
+// query_kernel<kTri, kStore>: one CTA of 256 threads per work item (pair, Generate batch
+// of 1024 samples or faces).  Per sample (kTri false) each thread queries 4 samples --
+// coalesced float4 sample loads, the 8-corner gathers of all four in flight together; per
+// face (kTri true, contact_gen = 1) each thread streams the descent steps of its 4 faces
+// (tri_batch).  The CTA compacts the candidates (phi < contact offset) in sample or face
+// order into the item's slab of the candidate buffer: per candidate the float4 pair
+// (x_w, phi), (n_w, index).  kStore selects dense or narrow-band bricked SDF storage.  In
+// worlds whose envs hold several pairs, an item whose bodies' bounding spheres are too
+// far apart to touch is skipped (broad phase).
 //
 // reduce_kernel: one CTA of kReduceWarps warps per pair runs Algorithm 1 over the pair's
 // items in batch order.  It stages a batch's candidates in shared memory (read in place

@@ -22,6 +22,11 @@
 // both bodies at once.  b = phi/hs for phi > 0 (speculative contact), baumgarte*phi/hs
 // otherwise.  Integration: semi-implicit Euler of the centre of mass and
 // q <- normalize(q + hs/2 (omega, 0) q).
+//
+// The weighted Jacobi solver (solver = 1, sweep_jacobi) is the alternative the paper's
+// solver comparison sizes: per sweep every contact's block update from the sweep-start
+// velocity, all taken with the weight 1 / (contacts that can act); it runs on fast rows,
+// an env's contacts in parallel on its lanes.
 #include "fw_device.cuh"
 
 namespace fw {
