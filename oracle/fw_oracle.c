@@ -275,13 +275,23 @@ static double node_phi(const double x[3], const float *V, const int *T, int nt) 
     return (w > 0.5) ? -d : d;        /* R1 */
 }
 
+/* threads of one parallel region: n_threads, or the OpenMP default when n_threads <= 0
+ * (set per region, never process-wide, so one world's setting cannot slow another's) */
+static int team_size(int n_threads) {
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
 void or_bake_nodes(const float *V, const int *T, int nt, const float lo[3], float h,
                    const int dims[3], const long long *nodes, long long n_nodes,
                    double *phi, int n_threads) {
     long long total = nodes ? n_nodes : (long long)dims[0] * dims[1] * dims[2];
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 64) num_threads(team_size(n_threads))
 #endif
     for (long long q = 0; q < total; ++q) {
         long long id = nodes ? nodes[q] : q;
@@ -1207,8 +1217,7 @@ int or_tri_contacts(or_world *w, int env, int pair, double *x, double *phi, doub
 int or_collide(or_world *w) {
     ensure_nodes(w);
 #ifdef _OPENMP
-    if (w->cfg.n_threads > 0) omp_set_num_threads(w->cfg.n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(team_size(w->cfg.n_threads))
 #endif
     for (int pi = 0; pi < w->n_pairs; ++pi) detect_pair(w, pi);
     for (int e = 0; e < w->n_envs; ++e) {
@@ -1492,8 +1501,7 @@ static void env_substep(or_world *w, int e, double hs, int n_iters) {
 int or_substep(or_world *w, double hs, int n_iters, int detect) {
     if (detect) or_collide(w);
 #ifdef _OPENMP
-    if (w->cfg.n_threads > 0) omp_set_num_threads(w->cfg.n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(team_size(w->cfg.n_threads))
 #endif
     for (int e = 0; e < w->n_envs; ++e) env_substep(w, e, hs, n_iters);
     return 0;
