@@ -32,7 +32,7 @@ def _fw():
 @pytest.fixture(scope="module")
 def mixed():
     fw = _fw()
-    sc = S.mixed_nut_bolt_scene(n_envs=6, seed=1)   # every size: 2 x M8, M12, M16, 2 x M20
+    sc = S.mixed_nut_bolt_scene(n_envs=12, seed=3)
     assert len(sc.groups) == 4
     gw = fw.world_from_scene(sc)
     ow = O.world_from_scene(sc, lazy_bake=True)

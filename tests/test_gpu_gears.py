@@ -42,7 +42,7 @@ def _rot_angle(q1, q2):
 @pytest.fixture(scope="module")
 def gears():
     fw = _fw()
-    sc = S.gear_scene(n_envs=2, seed=2)
+    sc = S.gear_scene(n_envs=4, seed=2)
     gw = fw.world_from_scene(sc)
     ow = O.world_from_scene(sc, lazy_bake=True, margin_len=MARGIN_LEN, margin_dot=MARGIN_DOT)
     return sc, gw, ow

@@ -49,7 +49,7 @@ def _close(gs, os_, pos_tol, rot_tol, bodies):
 @pytest.mark.parametrize("scene", ["peg", "nut"])
 def test_identical_contacts_one_substep(scene):
     fw = _fw()
-    sc = _peg() if scene == "peg" else S.nut_bolt_scene(n_envs=2, seed=1)
+    sc = _peg() if scene == "peg" else S.nut_bolt_scene(n_envs=4, seed=1)
     gw = fw.world_from_scene(sc, solver=1)
     ow = O.world_from_scene(sc, lazy_bake=True, solver=1)
     hs = sc.sim.dt / sc.sim.n_substeps
