@@ -65,6 +65,11 @@ struct EnvSm {
 // in different shared-memory banks.  The slot's bodies and row offsets (EnvSm) are in a
 // static array of the kernel.
 static_assert(sizeof(Row) >= kRowF4 * sizeof(float4), "a fast row lives in a general row's storage");
+static_assert(offsetof(Row, t1) == 3 * 4 && offsetof(Row, ra_n) == 9 * 4 && offsetof(Row, rb_n) == 18 * 4 &&
+                  offsetof(Row, ia_n) == 27 * 4 && offsetof(Row, ib_n) == 36 * 4 && offsetof(Row, kn) == 45 * 4 &&
+                  offsetof(Row, bias) == 48 * 4 && offsetof(Row, mu) == 49 * 4 && offsetof(Row, a) == 53 * 4 &&
+                  offsetof(Row, b) == 54 * 4 && sizeof(Row) == kRowF4 * sizeof(float4),
+              "gs_row reads Row fields by these word offsets");
 __host__ __device__ inline int env_stride_f4(int lam_cap) { return ((lam_cap + kRing * kRowF4 + 7) & ~7) + 1; }
 
 __device__ __forceinline__ V3 smv(const float (*a)[3], int i) { return v3(a[i][0], a[i][1], a[i][2]); }
@@ -105,43 +110,54 @@ __device__ __forceinline__ void build_row(Row &R, const DContact &c, const BodyS
 
 // One contact's Gauss-Seidel update in the general form: the normal row, then the two
 // friction rows projected jointly on the disk; L = (lambda_n, lambda_t1, lambda_t2, -).
+// The row is read as its 15 float4 (fields by constant word offsets, see Row), and the
+// disk projection scales by min(1, mu lambda_n / |lambda_t|) through a reciprocal square
+// root, as the fast form does.
 __device__ __forceinline__ void gs_row(const Row &R, float4 &L, BodySm &B, bool use_bias) {
-    if (R.kn == 0.0f) return;
-    const int a = R.a, b = R.b;
+    const float4 *q = reinterpret_cast<const float4 *>(&R);
+    float f[4 * kRowF4];
+#pragma unroll
+    for (int k = 0; k < kRowF4; ++k) {
+        const float4 v = q[k];
+        f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+    }
+    // word offsets of the Row fields
+    enum { N = 0, T1 = 3, T2 = 6, RAN = 9, RAT1 = 12, RAT2 = 15, RBN = 18, RBT1 = 21, RBT2 = 24,
+           IAN = 27, IAT1 = 30, IAT2 = 33, IBN = 36, IBT1 = 39, IBT2 = 42, KN = 45, KT1 = 46, KT2 = 47,
+           BIAS = 48, MU = 49, A = 53, B_ = 54 };
+    auto w3 = [&](int o) { return v3(f[o], f[o + 1], f[o + 2]); };
+    if (f[KN] == 0.0f) return;
+    const int a = __float_as_int(f[A]), b = __float_as_int(f[B_]);
     V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
     const float ima = B.invm[a], imb = B.invm[b];
     // normal row
-    const V3 n = ld3(R.n);
-    float jv = dot(n, va - vb) + dot(ld3(R.ra_n), wa) - dot(ld3(R.rb_n), wb);
-    if (use_bias) jv += R.bias;
-    const float ln = fmaxf(L.x - R.kn * jv, 0.0f);
+    const V3 n = w3(N);
+    float jv = dot(n, va - vb) + dot(w3(RAN), wa) - dot(w3(RBN), wb);
+    if (use_bias) jv += f[BIAS];
+    const float ln = fmaxf(L.x - f[KN] * jv, 0.0f);
     const float dl = ln - L.x;
     L.x = ln;
     va = va + (dl * ima) * n;
-    wa = wa + dl * ld3(R.ia_n);
+    wa = wa + dl * w3(IAN);
     vb = vb - (dl * imb) * n;
-    wb = wb - dl * ld3(R.ib_n);
+    wb = wb - dl * w3(IBN);
     // friction rows, projected jointly on the disk of radius mu lambda_n
-    const V3 t1 = ld3(R.t1), t2 = ld3(R.t2);
+    const V3 t1 = w3(T1), t2 = w3(T2);
     const V3 dv = va - vb;
-    const float j1 = dot(t1, dv) + dot(ld3(R.ra_t1), wa) - dot(ld3(R.rb_t1), wb);
-    const float j2 = dot(t2, dv) + dot(ld3(R.ra_t2), wa) - dot(ld3(R.rb_t2), wb);
-    float l1 = L.y - R.kt1 * j1, l2 = L.z - R.kt2 * j2;
-    const float lim = R.mu * ln;
-    const float lt = sqrtf(l1 * l1 + l2 * l2);
-    if (lt > lim) {
-        const float s = lt > 0.0f ? lim / lt : 0.0f;
-        l1 *= s;
-        l2 *= s;
-    }
+    const float j1 = dot(t1, dv) + dot(w3(RAT1), wa) - dot(w3(RBT1), wb);
+    const float j2 = dot(t2, dv) + dot(w3(RAT2), wa) - dot(w3(RBT2), wb);
+    float l1 = L.y - f[KT1] * j1, l2 = L.z - f[KT2] * j2;
+    const float sc = fminf(1.0f, (f[MU] * ln) * rsqrtf(__fmaf_rn(l1, l1, l2 * l2)));
+    l1 *= sc;
+    l2 *= sc;
     const float d1 = l1 - L.y, d2 = l2 - L.z;
     L.y = l1;
     L.z = l2;
     const V3 pt = d1 * t1 + d2 * t2;
     va = va + ima * pt;
-    wa = wa + d1 * ld3(R.ia_t1) + d2 * ld3(R.ia_t2);
+    wa = wa + d1 * w3(IAT1) + d2 * w3(IAT2);
     vb = vb - imb * pt;
-    wb = wb - (d1 * ld3(R.ib_t1) + d2 * ld3(R.ib_t2));
+    wb = wb - (d1 * w3(IBT1) + d2 * w3(IBT2));
     smv_set(B.v, a, va); smv_set(B.w, a, wa);
     smv_set(B.v, b, vb); smv_set(B.w, b, wb);
 }
