@@ -32,11 +32,11 @@ sys.path.insert(0, ROOT)
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the middle of the
     # bench's timed frames, replayed by its per-kernel timing pass)
-    "c37a85f1818595dc": {"query_kernel": 32.03e6, "reduce_kernel": 81.20e6, "solve_kernel": 105.69e6},
+    "dd188ec0f8ae773d": {"query_kernel": 31.96e6, "reduce_kernel": 81.31e6, "solve_kernel": 104.44e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "c37a85f1818595dc": {"query_kernel": 593.9e6, "reduce_kernel": 293.4e6, "solve_kernel": 4325.0e6},
+    "dd188ec0f8ae773d": {"query_kernel": 594.2e6, "reduce_kernel": 293.2e6, "solve_kernel": 4320.0e6},
 }
 
 FP32_LANES_PER_SM = 128
