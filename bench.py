@@ -32,11 +32,11 @@ sys.path.insert(0, ROOT)
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the middle of the
     # bench's timed frames, replayed by its per-kernel timing pass)
-    "dd188ec0f8ae773d": {"query_kernel": 31.96e6, "reduce_kernel": 81.31e6, "solve_kernel": 104.44e6},
+    "c5ebc7c9e1f4c82d": {"query_kernel": 32.08e6, "reduce_kernel": 81.44e6, "solve_kernel": 94.53e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "dd188ec0f8ae773d": {"query_kernel": 594.2e6, "reduce_kernel": 293.2e6, "solve_kernel": 4320.0e6},
+    "c5ebc7c9e1f4c82d": {"query_kernel": 593.7e6, "reduce_kernel": 293.9e6, "solve_kernel": 4305.0e6},
 }
 
 FP32_LANES_PER_SM = 128

@@ -506,13 +506,9 @@ __device__ void sweep_jacobi(float4 *rows_, int nr, int n_sweeps, V3 &va, V3 &wa
             const float s1 = dot(v3(f1.x, f1.y, f1.z), va) + f1.w + dot(v3(f7.x, f7.y, f7.z), wa) + f12.x * dn;
             const float s2 = dot(v3(f2.x, f2.y, f2.z), va) + f2.w + dot(v3(f8.x, f8.y, f8.z), wa) + f12.y * dn;
             float l1 = L.y + s1, l2 = L.z + s2;
-            const float lim = f12.z * ln;
-            const float lt = sqrtf(l1 * l1 + l2 * l2);
-            if (lt > lim) {
-                const float sc = lt > 0.0f ? lim / lt : 0.0f;
-                l1 *= sc;
-                l2 *= sc;
-            }
+            const float sc = fminf(1.0f, (f12.z * ln) * rsqrtf(__fmaf_rn(l1, l1, l2 * l2)));   // disk
+            l1 *= sc;
+            l2 *= sc;
             const float d1 = l1 - L.y, d2 = l2 - L.z;
             dv = dv + dn * v3(f3.x, f3.y, f3.z) + d1 * v3(f4.x, f4.y, f4.z) + d2 * v3(f5.x, f5.y, f5.z);
             dw = dw + dn * v3(f9.x, f9.y, f9.z) + d1 * v3(f10.x, f10.y, f10.z) + d2 * v3(f11.x, f11.y, f11.z);
