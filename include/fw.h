@@ -288,19 +288,27 @@ FW_API fw_status fw_reduce(fw_world *w, const fw_candidate *cands, int n, fw_con
  * allocate device memory once they are running -- for example a control loop with a
  * fixed latency budget (cudaMalloc and cudaFree can stall the whole device), or a host
  * program whose memory pool owns the GPU (PyTorch's caching allocator) and lets no one
- * else allocate.  Same reduction code and results as fw_reduce.
+ * else allocate.  On candidates sorted by sample it runs the same reduction code as
+ * fw_reduce and returns the same contacts and patch count; it differs in how it reports
+ * problems: an overflow (more contacts than cap) is reported through d_counts[0] > cap,
+ * not through a status, and the input must already be sorted (fw_reduce sorts a copy).
  *   d_cands   device array of n candidates, samples strictly increasing and < 65536
  *             (the limit of the call's fixed scratch), n <= 65536;
- *   d_out     device array for up to cap contacts (fw_contact, pair = 0);
+ *   d_out     device array for up to cap contacts (fw_contact, pair = 0); nothing is
+ *             written past entry cap - 1;
  *   d_counts  device int[2]: number of contacts (may exceed cap; only cap are written)
  *             and number of patches; (-1, 0) when the device finds the candidates
  *             unsorted, repeated or out of range.
  * Scratch: one 2.2 MB block of device memory that every GPU loading the library holds
  * until the process exits, shared by all calls and keeping the last call's contents
  * (nothing in it needs to start at zero).  Calls that overlap on the GPU (two streams, two
- * worlds) race on it: order them on one stream.  The first call on a device looks the
- * block's address up (no allocation); make that first call before any stream capture.
- * Enqueued on the world's stream; does not synchronise.
+ * worlds) race on it: order them on one stream.  The first call on a device (from any
+ * host thread; concurrent first calls are serialised) looks the block's address up, with
+ * no allocation; make that first call before any stream capture.  The address is kept for
+ * the life of the process: a program that resets the device (cudaDeviceReset) must not
+ * call this function afterwards.
+ * Enqueued on the world's stream, which must be ordered after the writes of d_cands and
+ * d_counts' previous readers; does not synchronise.
  * Errors: FW_ERR_ARG for NULL pointers or n > 65536 (a clear message in fw_last_error). */
 FW_API fw_status fw_reduce_noalloc(fw_world *w, const fw_candidate *d_cands, int n, fw_contact *d_out,
                                    int cap, int *d_counts);
@@ -309,7 +317,10 @@ FW_API fw_status fw_reduce_noalloc(fw_world *w, const fw_candidate *d_cands, int
 /* Reverse mode of the substep with its discrete decisions held fixed (no counterpart in
  * the paper, which simulates forward only).  Envs taking part have at most one dynamic
  * body, the point-sampled body a of each of their pairs, with static or kinematic
- * partners (no fixed-axis bodies), and the world has n_vel_iters = 0.
+ * partners (no fixed-axis bodies), and the world has n_vel_iters = 0 and contact_gen = 0
+ * (per-sample contacts: the tape rebuilds every contact from its surface sample, which a
+ * per-triangle contact does not have; such worlds are refused with FW_ERR_ARG before
+ * anything is enqueued).
  *
  * fw_record_rollout: one frame (dt) of n_substeps substeps with n_iters Gauss-Seidel
  * sweeps from the current state, each substep running detection (Sec. III-A, III-C) and

@@ -305,7 +305,7 @@ fw_status ensure_device(fw_world *w) {
         CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
         CK(cudaMemcpy(w->d_envs, w->envs.data(), sizeof(EnvDev) * ne, cudaMemcpyHostToDevice));
         long long rl = 0;
-        for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + E.row_cap);
+        for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + E.row_cap + kRowPad);
         w->rows_len = std::max(rl, 1LL);
         CK(cudaMalloc(&w->d_rows, sizeof(Row) * w->rows_len));
     }
@@ -375,6 +375,7 @@ fw_status check_status(fw_world *w) {
         if (st & kStatusNonFinite) return fail(w, FW_ERR_NONFINITE, "a body state became non-finite");
         if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts than fit");
         if (st & kStatusBounds) return fail(w, FW_ERR_DEVICE_BOUNDS, "device index check failed");
+        if (st & kStatusTimeout) return fail(w, FW_ERR_TIMEOUT, "a bounded device wait gave up");
     }
     return FW_OK;
 }
@@ -875,7 +876,7 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
     const int e0 = (int)w->envs.size();
     long long scratch = 0, rows = 0;
     for (auto &P : w->pairs) scratch = std::max(scratch, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
-    for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap);
+    for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap + kRowPad);
     for (int e = 0; e < n_envs; ++e) {
         EnvDev E;
         memset(&E, 0, sizeof E);
@@ -885,7 +886,7 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
         E.n_pairs = n_pairs;
         E.row_off = (int)rows;
         E.row_cap = n_pairs * cap_pair(w);
-        rows += E.row_cap;
+        rows += E.row_cap + kRowPad;
         for (int i = 0; i < n_per_env; ++i) {
             const fw_body_desc &d = bd[e * n_per_env + i];
             const AssetHost &A = w->assets[d.asset];
@@ -1412,6 +1413,9 @@ fw_status fw_record_rollout(fw_world *w, int n_substeps, int n_iters) {
     if (n_substeps < 1 || n_iters < 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: bad substeps/iterations");
     if (w->cfg.n_vel_iters != 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: needs n_vel_iters = 0");
     if (w->cfg.solver != 0) return fail(w, FW_ERR_ARG, "fw_record_rollout: needs the Gauss-Seidel solver");
+    // the tape rebuilds a contact from its surface sample; per-triangle contacts have none
+    if (w->cfg.contact_gen != 0)
+        return fail(w, FW_ERR_ARG, "fw_record_rollout: needs contact_gen = 0 (per-sample contacts)");
     fw_status st = ensure_device(w);
     if (st != FW_OK) return st;
     std::vector<int> dyn;

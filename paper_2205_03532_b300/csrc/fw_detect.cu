@@ -28,6 +28,9 @@
 //
 // The same reduction code, on one warp, serves fw_reduce_noalloc, and on kReduceWarps
 // warps serves fw_reduce (a caller's candidate list).
+#include <atomic>
+#include <mutex>
+
 #include "fw_device.cuh"
 
 namespace fw {
@@ -938,16 +941,20 @@ size_t reduce_smem_bytes(int max_patches, int stage) {
 static __device__ __align__(256) float4 g_noalloc[kNoAllocF4];
 
 namespace {
-float4 *g_noalloc_dev[64];    // its device address per device ordinal (0 until set up)
-bool g_noalloc_ready[64];
+float4 *g_noalloc_dev[64];                   // its device address per device ordinal
+std::atomic<bool> g_noalloc_ready[64];       // set (release) once g_noalloc_dev[d] is valid
+std::mutex g_noalloc_mutex;                  // serialises first calls from several host threads
 }  // namespace
 
 // First use on a device (that device current): look up the device address of g_noalloc
 // (the host-side name is only a stand-in) and raise the kernel's shared-memory limit.
-// Neither step allocates memory.
+// Neither step allocates memory.  The address is kept for the process's lifetime (a device
+// reset would invalidate it; the header tells callers not to reset).
 cudaError_t noalloc_setup(int device) {
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (g_noalloc_ready[device]) return cudaSuccess;
+    if (g_noalloc_ready[device].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ready[device].load(std::memory_order_relaxed)) return cudaSuccess;
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc);
     if (e != cudaSuccess) return e;
@@ -955,7 +962,7 @@ cudaError_t noalloc_setup(int device) {
                              (int)reduce_smem_bytes(kMaxPatchesCap, kBatch));
     if (e != cudaSuccess) return e;
     g_noalloc_dev[device] = static_cast<float4 *>(ptr);
-    g_noalloc_ready[device] = true;
+    g_noalloc_ready[device].store(true, std::memory_order_release);
     return cudaSuccess;
 }
 

@@ -105,3 +105,20 @@ def test_contact_buffer_too_small_reports_the_size():
     st = w.lib.fw_get_contacts(w.h, 0, out.ctypes.data, 2, C.byref(n))
     assert st == ERR_OVERFLOW and n.value == n_all
     w.close()
+
+
+def test_rollout_recording_refuses_per_triangle_contacts():
+    """The adjoint's tape rebuilds each contact from its surface sample; a per-triangle
+    contact (contact_gen = 1) has none, so recording is refused on the host before anything
+    is enqueued.  Only the refusal is exercised: no kernel runs with such a world."""
+    fw = _fw()
+    sc = _peg(n_envs=2)
+    w = fw.world_from_scene(sc, contact_gen=1)
+    for call in (lambda: w.record_rollout(4, 8), lambda: w.step_fwd_ckpt(4, 8)):
+        with pytest.raises(fw.FwError) as e:
+            call()
+        assert _status(e) == ERR_ARG and "contact_gen" in str(e.value)
+    with pytest.raises(fw.FwError) as e:
+        w.replay_rollout()                                             # nothing was recorded
+    assert _status(e) == ERR_STATE
+    w.close()

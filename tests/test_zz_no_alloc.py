@@ -31,17 +31,24 @@ def _candidates(seed, n, max_sample, clusters=9):
     return c
 
 
-def _noalloc(w, cands, cap):
+def _noalloc(w, cands, cap, spare=0):
+    """fw_reduce_noalloc on device copies of cands; the output buffer holds `spare` more
+    contacts than cap, filled with a 0xA5 byte pattern; returns (contacts, count, patches,
+    the spare bytes after the call)."""
     import torch
     from paper_2205_03532_b300 import fw
     raw = torch.from_numpy(cands.view(np.uint8).copy()).cuda()
-    out = torch.zeros(cap * fw.CONTACT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    out = torch.zeros((cap + spare) * fw.CONTACT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    out[cap * fw.CONTACT_DTYPE.itemsize:] = 0xA5
     counts = torch.full((2,), 7, dtype=torch.int32, device="cuda")
+    # the inputs were written on torch's stream; the call runs on the world's own stream
+    torch.cuda.current_stream().synchronize()
     w.reduce_noalloc(raw, len(cands), out, cap, counts)
     w.sync()
     k, npatch = counts.cpu().tolist()
-    res = out.cpu().numpy().view(fw.CONTACT_DTYPE)
-    return res[: max(0, min(k, cap))].copy(), k, npatch
+    host = out.cpu().numpy()
+    res = host[: cap * fw.CONTACT_DTYPE.itemsize].view(fw.CONTACT_DTYPE)
+    return res[: max(0, min(k, cap))].copy(), k, npatch, host[cap * fw.CONTACT_DTYPE.itemsize:]
 
 
 def _same(a, b):
@@ -57,9 +64,25 @@ def test_noalloc_matches_fw_reduce_on_two_calls_in_a_row():
     inputs = [_candidates(1, 3000, 5000), _candidates(2, 2500, 60000, clusters=14)]
     for c in inputs:
         ref, ref_np = w.reduce(c)
-        got, k, npatch = _noalloc(w, c, cap=7 * 256)
+        got, k, npatch, _ = _noalloc(w, c, cap=7 * 256)
         assert k == len(ref) and npatch == ref_np
         _same(got, ref)
+
+
+def test_noalloc_reports_overflow_through_the_count():
+    """With cap below the number of contacts the call writes the first cap contacts (the
+    same as fw_reduce's first cap), reports the full count in counts[0] and writes nothing
+    past entry cap - 1."""
+    from paper_2205_03532_b300 import fw
+    w = fw.World(max_patches=128)
+    c = _candidates(4, 3000, 5000)
+    ref, ref_np = w.reduce(c)
+    cap = len(ref) // 3
+    assert cap > 0
+    got, k, npatch, spare = _noalloc(w, c, cap=cap, spare=64)
+    assert k == len(ref) and npatch == ref_np
+    _same(got, ref[:cap])
+    assert np.all(spare == 0xA5)
 
 
 def test_noalloc_rejects_bad_input():
@@ -67,7 +90,7 @@ def test_noalloc_rejects_bad_input():
     w = fw.World()
     c = _candidates(3, 100, 1000)
     c["sample"][[10, 11]] = c["sample"][[11, 10]]          # out of order: rejected on the device
-    _, k, npatch = _noalloc(w, c, cap=64)
+    _, k, npatch, _ = _noalloc(w, c, cap=64)
     assert (k, npatch) == (-1, 0)
     big = np.zeros(70000, fw.CANDIDATE_DTYPE)                # beyond the fixed scratch: rejected on the host
     with pytest.raises(fw.FwError) as e:
