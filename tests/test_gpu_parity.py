@@ -25,6 +25,14 @@ from oracle import oracle as O
 from paper_2205_03532_b300 import scenes as S
 
 MARGIN_LEN, MARGIN_DOT = 1e-7, 1e-6
+# Length margin for decisions of the fused narrow phase + reduction on the full-size nut
+# (h = 0.17 mm): the per-sample |d phi| bound is 5e-5 h = 8.5e-9 m (test_narrow_phase_per_sample
+# holds every sample to it), so two phi values compared by FindDeepest differ by at most
+# 1.7e-8 m between the two sides; world positions near 5 cm carry float32 rounding of a few
+# 4e-9 m ulps, so slot-score differences of two candidates stay below ~3e-8 m.  5e-8 m is
+# above both; the SURVEY's 1e-7 m would leave almost no nut pair comparable (~2,700
+# candidates per pair put consecutive depths ~0.1 um apart).
+MARGIN_LEN_FUSED = 5e-8
 
 
 def _fw():
@@ -300,17 +308,19 @@ def test_collide_matches_where_decisions_have_margin(scene, request):
     ow.reset_margins()
     ow.collide()
     comparable = 0
+    m_len = MARGIN_LEN_FUSED if scene == "nut" else MARGIN_LEN
     for env in range(sc.n_envs):
         gc = gw.get_contacts(env)
         oc, ml, md = ow.contacts(env)
-        if ml >= MARGIN_LEN and md >= MARGIN_DOT:
+        if ml >= m_len and md >= MARGIN_DOT:
             _compare_contacts(gc, oc)
             assert np.all(np.abs(gc["phi"] - oc["phi"]) <= 5e-5 * _h_of(gw, 1))
             comparable += 1
         else:
             _bulk_agree(gc, oc, shared=0.8, count=0.15)
-    # full-size nut pairs have ~1000 phi decisions each; a clean pair is rare there
-    assert comparable >= (0 if scene == "nut" else 4), comparable
+    print(f"{scene}: {comparable} of {sc.n_envs} pairs compared exactly")
+    # the 4 seeded nut pairs: 2 have every decision's margin above MARGIN_LEN_FUSED
+    assert comparable >= (2 if scene == "nut" else 4), comparable
 
 
 @pytest.mark.parametrize("max_patches", [4, 12])
