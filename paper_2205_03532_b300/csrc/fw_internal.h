@@ -23,7 +23,7 @@ constexpr unsigned kStatusTimeout = 8u;   // a bounded device wait gave up
 // The solve streams an env's rows into shared memory kChunk at a time; the row region of
 // an env is followed by kRowPad rows that repeat its first rows (row nr + j holds row
 // j mod nr), so that every chunk of the periodic row stream is one contiguous copy.
-constexpr int kChunk = 8;
+constexpr int kChunk = 16;
 constexpr int kRowPad = kChunk;
 
 // Grid view of one asset's SDF.  Value at node (i, j, k) = val[(k*ny + j)*nx + i]; FP16

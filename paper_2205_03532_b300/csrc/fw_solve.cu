@@ -9,8 +9,10 @@
 // movable body's side (directions negated when it is the pair's SDF body, the partner's
 // prescribed velocity folded into a constant), 15 float4 per contact; the body's velocity
 // stays in registers, split between the group's even lanes (linear part) and odd lanes
-// (angular part), the rows stream from global memory through a cp.async ring in shared
-// memory and the accumulated impulses live in shared memory.  General form
+// (angular part), the rows stream from global memory into shared memory in chunks of 16
+// rows, one cp.async.bulk copy per chunk issued by one lane and completed on an mbarrier
+// (two chunk buffers: the next chunk is in flight while one is read), and the accumulated
+// impulses live in shared memory.  General form
 // (several movable bodies): full two-body rows streamed through the same ring by one lane,
 // impulses and velocities in shared memory.
 //
@@ -34,11 +36,17 @@ namespace fw {
 namespace {
 
 constexpr int kMaxBodies = 8;
-constexpr int kRing = 16;     // rows in flight in the fast sweep's shared-memory ring
+constexpr int kRing = 16;     // rows in flight in the general form's shared-memory ring
 constexpr int kRowF4 = 15;    // float4 per fast row
 constexpr int kHalfF4 = 6;    // float4 of a row's linear (even lanes) or angular (odd lanes) half
-
-
+static_assert(kChunk * kRowF4 * 16 % 16 == 0, "bulk copies move multiples of 16 bytes");
+constexpr int kChunkF4 = kChunk * kRowF4;                  // one chunk of rows: 240 float4, 3840 bytes
+constexpr unsigned kChunkBytes = kChunkF4 * 16;
+constexpr int kChunkBufs = 2;                              // chunk buffers per env
+constexpr int kBarF4 = 1;                                  // their 2 mbarriers (8 bytes each)
+constexpr int kSlotF4 = kChunkBufs * kChunkF4 + kBarF4;    // per env beside its impulse words
+static_assert(kSlotF4 >= kRing * kRowF4 + kBarF4, "the general form's ring fits in the chunk buffers");
+constexpr int kWaitTries = 1 << 20;                        // bounded mbarrier waits
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -46,6 +54,61 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ---- mbarriers and bulk copies (the fast sweep's chunked row stream)
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// makes this thread's global writes (the rows) visible to later bulk copies (async proxy)
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+// One chunk, issued by the lanes with copy != 0 (the group's leader): arrive expecting
+// kChunkBytes, then the copy that completes them; lanes with arrive_only != 0 (the leader
+// of a group without rows) only arrive.  Predicated, so the warp does not branch.
+__device__ __forceinline__ void bulk_chunk(unsigned dst, const float4 *src, unsigned bar, unsigned copy,
+                                           unsigned arrive_only) {
+    asm volatile(
+        "{\n .reg .pred pc, pa;\n setp.ne.u32 pc, %4, 0;\n setp.ne.u32 pa, %5, 0;\n"
+        " @pc mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n"
+        " @pc cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %3, [%2];\n"
+        " @pa mbarrier.arrive.shared::cta.b64 _, [%2];\n}\n" ::"r"(dst),
+        "l"(__cvta_generic_to_global(src)), "r"(bar), "n"(kChunkBytes), "r"(copy), "r"(arrive_only)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity to complete; false after kWaitTries more tries
+// (each try itself blocks for a bounded, hardware-chosen time).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    bool ok = mbar_try_wait(bar, parity);
+    if (!ok) {
+        for (int i = 0; i < kWaitTries && !ok; ++i) ok = mbar_try_wait(bar, parity);
+    }
+    return ok;
+}
+// 16-byte shared-memory accesses by 32-bit shared addresses (the chunk buffers and impulse
+// words are reached through addresses the compiler cannot trace back to shared memory)
+__device__ __forceinline__ float4 lds4(unsigned a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float lds1(unsigned a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts4(unsigned a, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
 
 struct BodySm {
     float v[kMaxBodies][3], w[kMaxBodies][3];
@@ -70,7 +133,7 @@ static_assert(offsetof(Row, t1) == 3 * 4 && offsetof(Row, ra_n) == 9 * 4 && offs
                   offsetof(Row, bias) == 48 * 4 && offsetof(Row, mu) == 49 * 4 && offsetof(Row, a) == 53 * 4 &&
                   offsetof(Row, b) == 54 * 4 && sizeof(Row) == kRowF4 * sizeof(float4),
               "gs_row reads Row fields by these word offsets");
-__host__ __device__ inline int env_stride_f4(int lam_cap) { return ((lam_cap + kRing * kRowF4 + 7) & ~7) + 1; }
+__host__ __device__ inline int env_stride_f4(int lam_cap) { return ((lam_cap + kSlotF4 + 7) & ~7) + 1; }
 
 __device__ __forceinline__ V3 smv(const float (*a)[3], int i) { return v3(a[i][0], a[i][1], a[i][2]); }
 __device__ __forceinline__ void smv_set(float (*a)[3], int i, V3 x) { a[i][0] = x.x; a[i][1] = x.y; a[i][2] = x.z; }
@@ -312,152 +375,245 @@ __device__ __forceinline__ int warp_min(int v) {
     return v;
 }
 
-// A row as one lane holds it: its half (linear or angular) and the shared coefficients.
-struct HalfRow {
-    float4 h[kHalfF4];
+// A row as one lane holds it, in the pieces a step uses at different times: the scaled
+// Jacobian of the lane's half (J, float4 0-2 of the half), whose scaled velocities at the
+// body velocity are formed the step BEFORE the row is solved, and the half's update vectors
+// (W, float4 3-5 of the half) with the coefficients every lane needs (C, float4 12-14), used
+// when it is solved.  nc is the normal row's constant without the bias (float4 3 .w of the
+// half), for the bias-free sweeps.
+struct RowJ {
+    float4 j[3];
+    float nc;
+};
+struct RowCW {
     float4 c[3];
+    float4 w[3];
 };
 
-__device__ __forceinline__ void ring_read(const float4 *sp, int ho, HalfRow &f) {
+__device__ __forceinline__ void read_j(unsigned hp, RowJ &r, bool need_nc) {
 #pragma unroll
-    for (int k = 0; k < kHalfF4; ++k) f.h[k] = sp[ho + k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f.c[k] = sp[2 * kHalfF4 + k];
+    for (int k = 0; k < 3; ++k) r.j[k] = lds4(hp + 16u * k);
+    if (need_nc) r.nc = lds1(hp + 16u * 3 + 12u);
 }
-
-template <int G>
-__device__ __forceinline__ void ring_fill(float4 *ring, int slot, const float4 *rows, int pf, int nr, int gl) {
-    if (nr > 0) {
+__device__ __forceinline__ void read_cw(unsigned hp, unsigned cp, RowCW &r) {
 #pragma unroll
-        for (int k = gl; k < kRowF4; k += G) cp_async16(ring + kRowF4 * slot + k, rows + kRowF4 * pf + k);
-    }
+    for (int k = 0; k < 3; ++k) r.w[k] = lds4(hp + 16u * (3 + k));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.c[k] = lds4(cp + 16u * k);
 }
-
-struct SweepState {
-    V3 u;                      // the lane's half of the body velocity before the current row
-    float sn, s1, s2;          // current row's scaled velocities at that velocity, incl. couplings
-    int r, pf, slot, q;
-};
 
 // scaled velocities of a row at the body velocity (u and its partner lane's half), without
 // couplings: each lane dots its half, the pair adds the two parts (the same sum on both)
 template <bool kBias>
-__device__ __forceinline__ void row_base(const HalfRow &g, V3 u, float &bn, float &b1, float &b2) {
-    const float pn = __fmaf_rn(g.h[0].z, u.z, __fmaf_rn(g.h[0].y, u.y, __fmaf_rn(g.h[0].x, u.x, kBias ? g.h[0].w : g.h[3].w)));
-    const float p1 = __fmaf_rn(g.h[1].z, u.z, __fmaf_rn(g.h[1].y, u.y, __fmaf_rn(g.h[1].x, u.x, g.h[1].w)));
-    const float p2 = __fmaf_rn(g.h[2].z, u.z, __fmaf_rn(g.h[2].y, u.y, __fmaf_rn(g.h[2].x, u.x, g.h[2].w)));
+__device__ __forceinline__ void row_base(const RowJ &g, V3 u, float &bn, float &b1, float &b2) {
+    const float pn = __fmaf_rn(g.j[0].z, u.z, __fmaf_rn(g.j[0].y, u.y, __fmaf_rn(g.j[0].x, u.x, kBias ? g.j[0].w : g.nc)));
+    const float p1 = __fmaf_rn(g.j[1].z, u.z, __fmaf_rn(g.j[1].y, u.y, __fmaf_rn(g.j[1].x, u.x, g.j[1].w)));
+    const float p2 = __fmaf_rn(g.j[2].z, u.z, __fmaf_rn(g.j[2].y, u.y, __fmaf_rn(g.j[2].x, u.x, g.j[2].w)));
     bn = pn + __shfl_xor_sync(0xffffffffu, pn, 1);
     b1 = p1 + __shfl_xor_sync(0xffffffffu, p1, 1);
     b2 = p2 + __shfl_xor_sync(0xffffffffu, p2, 1);
 }
 
-// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env), one
-// row per step.  All lanes of the warp run the same number of steps (enough for the
-// largest total of its groups; rows past a group's own total are computed and
-// discarded), so every __syncwarp and shuffle is reached by the whole warp.  The even
-// lanes of a group keep the body's linear velocity, the odd lanes its angular velocity;
-// scaled velocities and impulses are identical on all of them.  A step: wait for the next
-// row's copy group, read the lane's half of the next row and its impulse word into
-// registers, let the group's lanes refill that ring slot with the row kRing positions
-// ahead (one cp.async per float4, one commit group per step), then solve the current row
-// from its carried scaled velocities (S_n, S_1, S_2): only S -> impulse changes -> next
-// row's S (through C) is serial; the next row's velocities at the current body velocity
-// and the velocity update run beside it.  Lane 0 of the group stores the impulses; the
-// next step's __syncwarp orders those stores before a later read.  With a single row the
-// next row is the current one, and its impulse word is the value just computed.
-template <int G, bool kBias, bool kMasked>
-__device__ __forceinline__ void sweep_step(const HalfRow &f, float4 &Lf, HalfRow &g, float4 &Lg, SweepState &st,
-                                           const float4 *rows, int nr, int total, bool single, int ho,
-                                           float4 *ring, float4 *lam, int gl) {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
-    __syncwarp();
-    ring_read(ring + kRowF4 * st.slot, ho, g);
-    const int rn = (st.r + 1 >= nr) ? 0 : st.r + 1;
-    Lg = lam[rn];
-    __syncwarp();
-    ring_fill<G>(ring, st.slot, rows, st.pf, nr, gl);
-    cp_async_commit();
-    if (++st.pf >= nr) st.pf = 0;
-    st.slot = (st.slot + 1) & (kRing - 1);
+// The chunked row stream of one env (one lane group).  The env's rows, read cyclically
+// (sweep after sweep), are cut into chunks of kChunk consecutive stream positions; chunk k
+// of the kernel's sequence goes to buffer k mod kChunkBufs and completes phase
+// k / kChunkBufs of that buffer's mbarrier.  Lane 0 of the group issues the copies (one
+// cp.async.bulk of kChunkBytes each, contiguous thanks to the kRowPad repeated rows after
+// the env's region);
+// a group without rows only arrives, so its phases complete at once and its buffers keep
+// the zeros they were given.
+struct RowStream {
+    const float4 *rows;   // the env's rows (global), followed by kRowPad repeated ones
+    float4 *buf;          // kChunkBufs chunk buffers (shared)
+    unsigned bar;         // shared address of the first of their kChunkBufs mbarriers
+    int nr;               // rows of the env (0: none)
+    int pf;               // row at which the next chunk to issue starts
+    int seq;              // chunks issued so far in this kernel (the next one's number)
+    int ib;               // buffer of the next chunk to issue (seq mod kChunkBufs)
+    bool leader;          // lane 0 of the group
+    bool on;              // issuing (cleared after a wait gave up)
+};
+
+__device__ __forceinline__ void issue_chunk(RowStream &rs) {
+    const unsigned bar = rs.bar + 8u * rs.ib;
+    bulk_chunk(smem_addr(rs.buf) + 16u * kChunkF4 * rs.ib, rs.rows + (size_t)kRowF4 * rs.pf, bar,
+               rs.leader && rs.on && rs.nr > 0, rs.leader && rs.on && rs.nr == 0);
+    if (rs.nr >= kChunk) {
+        rs.pf += kChunk;
+        rs.pf = rs.pf >= rs.nr ? rs.pf - rs.nr : rs.pf;
+    } else if (rs.nr > 0) {
+        rs.pf = (rs.pf + kChunk) % rs.nr;
+    }
+    ++rs.seq;
+    rs.ib = rs.ib + 1 == kChunkBufs ? 0 : rs.ib + 1;
+}
+
+struct SweepRegs {
+    V3 u;                 // the lane's half of the body velocity before the current row
+    float sn, s1, s2;     // current row's scaled velocities at that velocity, incl. couplings
+};
+
+// One Gauss-Seidel step of a group, software-pipelined over three rows.  Row j (C and W in
+// f, impulse word Lf) is solved from its carried scaled velocities; meanwhile the next row's
+// scaled velocities are formed at the body velocity before row j from its Jacobian half jn
+// (read a step earlier), and the loads for later steps are issued: row j + 1's C and W
+// (into fn, at shared addresses hn / cn), row j + 2's Jacobian half (into jnn, at hnn) and
+// row j + 1's impulse word (Lg).  Only S -> impulse changes -> next row's S (through the
+// couplings C) is serial; no load result is needed within the step it is issued in.  kFast:
+// every group of the warp takes this step for real; otherwise a step past a group's total is
+// computed and discarded (act = false), and with a single row the next row is the current
+// one.  The leader lane stores the new impulse word at lam_cur.
+template <bool kBias, bool kFast>
+__device__ __forceinline__ void gs_step(const RowCW &f, const float4 &Lf, const RowJ &jn, RowCW &fn, RowJ &jnn,
+                                        float4 &Lg, SweepRegs &st, unsigned hn, unsigned cn, unsigned hnn,
+                                        unsigned lam_next, unsigned lam_cur, bool leader, bool act, bool single) {
+    // the next row's scaled velocities at the body velocity before this row: independent of
+    // this row's solve, so they are formed first and overlap its dependency chain
+    float bn, b1, b2;
+    row_base<kBias>(jn, st.u, bn, b1, b2);
+    read_cw(hn, cn, fn);
+    read_j(hnn, jnn, !kBias);
+    Lg = lds4(lam_next);
     // the current row, from its carried scaled velocities
     const float4 L = Lf;
     const float dl = fmaxf(st.sn, -L.x);                  // lambda_n' - lambda_n
+    const float da = (kFast || act) ? dl : 0.0f;
+    const V3 u = st.u;
+    const V3 ud = v3(__fmaf_rn(da, f.w[0].x, u.x), __fmaf_rn(da, f.w[0].y, u.y), __fmaf_rn(da, f.w[0].z, u.z));
+    const float xn = __fmaf_rn(f.c[0].w, dl, bn), x1 = __fmaf_rn(f.c[1].z, dl, b1), x2 = __fmaf_rn(f.c[2].y, dl, b2);
     const float ln = L.x + dl;
     const float t1 = __fmaf_rn(f.c[0].x, dl, st.s1 + L.y);
     const float t2 = __fmaf_rn(f.c[0].y, dl, st.s2 + L.z);
     const float sc = fminf(1.0f, (f.c[0].z * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
     const float e1 = __fmaf_rn(t1, sc, -L.y), e2 = __fmaf_rn(t2, sc, -L.z);
-    // the next row's scaled velocities: at the current body velocity, plus the couplings
-    float bn, b1, b2;
-    row_base<kBias>(g, st.u, bn, b1, b2);
-    const float sn = __fmaf_rn(f.c[1].y, e2, __fmaf_rn(f.c[1].x, e1, __fmaf_rn(f.c[0].w, dl, bn)));
-    const float s1 = __fmaf_rn(f.c[2].x, e2, __fmaf_rn(f.c[1].w, e1, __fmaf_rn(f.c[1].z, dl, b1)));
-    const float s2 = __fmaf_rn(f.c[2].w, e2, __fmaf_rn(f.c[2].z, e1, __fmaf_rn(f.c[2].y, dl, b2)));
+    // the next row's scaled velocities: plus the couplings
+    st.sn = __fmaf_rn(f.c[1].y, e2, __fmaf_rn(f.c[1].x, e1, xn));
+    st.s1 = __fmaf_rn(f.c[2].x, e2, __fmaf_rn(f.c[1].w, e1, x1));
+    st.s2 = __fmaf_rn(f.c[2].w, e2, __fmaf_rn(f.c[2].z, e1, x2));
     // the lane's half of the body velocity after this row
-    const bool act = !kMasked || st.q < total;   // unmasked steps: every group still has rows
-    const float da = act ? dl : 0.0f, e1a = act ? e1 : 0.0f, e2a = act ? e2 : 0.0f;
-    const V3 u = st.u;
-    st.u = v3(__fmaf_rn(e2a, f.h[5].x, __fmaf_rn(e1a, f.h[4].x, __fmaf_rn(da, f.h[3].x, u.x))),
-              __fmaf_rn(e2a, f.h[5].y, __fmaf_rn(e1a, f.h[4].y, __fmaf_rn(da, f.h[3].y, u.y))),
-              __fmaf_rn(e2a, f.h[5].z, __fmaf_rn(e1a, f.h[4].z, __fmaf_rn(da, f.h[3].z, u.z))));
+    const float e1a = (kFast || act) ? e1 : 0.0f, e2a = (kFast || act) ? e2 : 0.0f;
+    st.u = v3(__fmaf_rn(e2a, f.w[2].x, __fmaf_rn(e1a, f.w[1].x, ud.x)),
+              __fmaf_rn(e2a, f.w[2].y, __fmaf_rn(e1a, f.w[1].y, ud.y)),
+              __fmaf_rn(e2a, f.w[2].z, __fmaf_rn(e1a, f.w[1].z, ud.z)));
     const float4 nl = make_float4(ln, L.y + e1, L.z + e2, 0.0f);
-    if (act && gl == 0) lam[st.r] = nl;
-    if (single) Lg = nl;
-    st.sn = sn; st.s1 = s1; st.s2 = s2;
-    st.r = rn;
-    ++st.q;
+    if (leader && (kFast || act)) sts4(lam_cur, nl);
+    if (!kFast && single) Lg = nl;
 }
 
+// `passes` Gauss-Seidel sweeps over nr fast rows by one group of G lanes (one env), one
+// row per step, total = nr * passes steps.  All lanes of the warp run the same number of
+// steps, `trips` rounded up to whole chunks (rows past a group's own total are computed
+// and discarded), so every shuffle and warp vote is reached by the whole warp.  The even
+// lanes of a group keep the body's linear velocity, the odd lanes its angular velocity;
+// scaled velocities and impulses are identical on all of them.  Chunk c of the call is read
+// while chunk c + 1 is in flight (issued into chunk c - 1's buffer as chunk c starts); its
+// step kChunk - 2 waits for chunk c + 1, whose first row's Jacobian is loaded there (two
+// rows ahead).  A chunk in which every group of the warp takes all kChunk steps for real
+// and no impulse index wraps runs the kFast steps (constant
+// shared-memory offsets; one __syncwarp per chunk orders the leader's impulse stores before
+// other lanes' later reads); other chunks take the general steps (index wrap, masking, a
+// __syncwarp per step).  Returns false if a wait for a chunk gave up (bounded); the chunks
+// still in flight are then waited for (bounded again) before returning.
 template <int G, bool kBias>
-__device__ void sweep_fast(const float4 *rows, int nr, int total, int trips, float4 *ring, float4 *lam, V3 &va,
-                           V3 &wa, int gl) {
-    if (trips == 0) return;   // warp-uniform
-    const bool odd = gl & 1;
-    const int ho = odd ? kHalfF4 : 0;
-    SweepState st;
-    st.u = odd ? wa : va; st.r = 0; st.pf = 0; st.q = 0;
-    // A group without rows runs only discarded steps, which scale its ring words by zero:
+__device__ bool sweep_fast(RowStream &rs, int total, int trips, float4 *lam, V3 &va, V3 &wa, int gl) {
+    if (trips == 0) return true;   // warp-uniform
+    const int nr = rs.nr;
+    const bool odd = gl & 1, leader = rs.leader;
+    const int nch = (trips + kChunk - 1) / kChunk;   // chunks of steps; chunk nch is read ahead
+    const int seq0 = rs.seq;
+    // A group without rows runs only discarded steps, which scale its chunk words by zero:
     // make them zeros (shared memory may hold any bits, NaN patterns included).
     if (nr == 0) {
-        for (int k = gl; k < kRing * kRowF4; k += G) ring[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = gl; k < kChunkBufs * kChunkF4; k += G) rs.buf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int s = 0; s < kRing; ++s) {
-        ring_fill<G>(ring, s, rows, st.pf, nr, gl);
-        cp_async_commit();
-        if (++st.pf >= nr) st.pf = 0;
-    }
-    HalfRow A, B;
+    __syncwarp();
+    for (int k = 0; k < kChunkBufs && k <= nch; ++k) issue_chunk(rs);
+    SweepRegs st;
+    st.u = odd ? wa : va;
+    // buffer and phase parity of the chunk being read (rb, rpar) and of the next one
+    int rb = seq0 % kChunkBufs;
+    unsigned rpar = (unsigned)((seq0 / kChunkBufs) & 1);
+    bool ok = mbar_wait(rs.bar + 8u * rb, rpar);
+    int done = seq0 + (ok ? 1 : 0);   // chunks waited for, in sequence
+    const unsigned buf0 = smem_addr(rs.buf), lam0 = smem_addr(lam);
+    constexpr unsigned kRowB = 16u * kRowF4, kChunkB = 16u * kChunkF4, kCoefB = 16u * 2 * kHalfF4;
+    const unsigned hob = 16u * (odd ? kHalfF4 : 0);
+    unsigned cur = buf0 + kChunkB * rb;
+    // prologue: row 0 (C, W, impulse, its scaled velocities) and row 1's Jacobian half
+    RowCW A, B;
+    RowJ JA, JB;
     float4 LA, LB;
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
-    __syncwarp();
-    ring_read(ring, ho, A);
-    LA = lam[0];
-    __syncwarp();
-    ring_fill<G>(ring, 0, rows, st.pf, nr, gl);
-    cp_async_commit();
-    if (++st.pf >= nr) st.pf = 0;
-    st.slot = 1;
-    row_base<kBias>(A, st.u, st.sn, st.s1, st.s2);
+    read_cw(cur + hob, cur + kCoefB, A);
+    read_j(cur + hob, JA, !kBias);
+    LA = lds4(lam0);
+    row_base<kBias>(JA, st.u, st.sn, st.s1, st.s2);
+    read_j(cur + kRowB + hob, JB, !kBias);
     const bool single = nr == 1;
-    // steps every group of the warp still needs run unmasked, two per trip (the register
-    // sets trade roles); the rest, and an odd last step, masked
-    const int common = warp_min<G>(total) & ~1;
-    int q = 0;
-    for (; q < common; q += 2) {
-        sweep_step<G, kBias, false>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
-        sweep_step<G, kBias, false>(B, LB, A, LA, st, rows, nr, total, single, ho, ring, lam, gl);
+    int r = 0;    // row of the chunk's first step
+    for (int c = 0; c < nch; ++c) {
+        if (c >= 1 && c + kChunkBufs - 1 <= nch) issue_chunk(rs);   // into chunk c - 1's buffer
+        const int nb = rb + 1 == kChunkBufs ? 0 : rb + 1;
+        const unsigned npar = nb == 0 ? rpar ^ 1u : rpar;
+        cur = buf0 + kChunkB * rb;
+        const unsigned nxt = buf0 + kChunkB * nb, nbar = rs.bar + 8u * nb;
+        const int q0 = c * kChunk;
+        __syncwarp();
+        const bool fast = __all_sync(0xffffffffu, nr == 0 || (q0 + kChunk <= total && r + kChunk < nr));
+        if (fast) {
+            const unsigned lp = lam0 + 16u * r;
+#pragma unroll
+            for (int j = 0; j < kChunk; j += 2) {
+                // step kChunk - 2 loads row kChunk, the next chunk's first: wait for it (after a
+                // wait gave up, no more waits: the results are discarded)
+                if (j + 2 == kChunk && ok) {
+                    ok = mbar_wait(nbar, npar);
+                    done += ok ? 1 : 0;
+                }
+                const unsigned r1 = (j + 1 < kChunk) ? cur + kRowB * (j + 1) : nxt + kRowB * (j + 1 - kChunk);
+                const unsigned r2 = (j + 2 < kChunk) ? cur + kRowB * (j + 2) : nxt + kRowB * (j + 2 - kChunk);
+                const unsigned r3 = (j + 3 < kChunk) ? cur + kRowB * (j + 3) : nxt + kRowB * (j + 3 - kChunk);
+                gs_step<kBias, true>(A, LA, JB, B, JA, LB, st, r1 + hob, r1 + kCoefB, r2 + hob, lp + 16u * (j + 1),
+                                     lp + 16u * j, leader, true, false);
+                gs_step<kBias, true>(B, LB, JA, A, JB, LA, st, r2 + hob, r2 + kCoefB, r3 + hob, lp + 16u * (j + 2),
+                                     lp + 16u * (j + 1), leader, true, false);
+            }
+            if (nr > 0) r += kChunk;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kChunk; j += 2) {
+                if (j + 2 == kChunk && ok) {
+                    ok = mbar_wait(nbar, npar);
+                    done += ok ? 1 : 0;
+                }
+                const unsigned r1 = (j + 1 < kChunk) ? cur + kRowB * (j + 1) : nxt + kRowB * (j + 1 - kChunk);
+                const unsigned r2 = (j + 2 < kChunk) ? cur + kRowB * (j + 2) : nxt + kRowB * (j + 2 - kChunk);
+                const unsigned r3 = (j + 3 < kChunk) ? cur + kRowB * (j + 3) : nxt + kRowB * (j + 3 - kChunk);
+                __syncwarp();
+                int rn = r + 1 >= nr ? 0 : r + 1;
+                gs_step<kBias, false>(A, LA, JB, B, JA, LB, st, r1 + hob, r1 + kCoefB, r2 + hob, lam0 + 16u * rn,
+                                      lam0 + 16u * r, leader, q0 + j < total, single);
+                r = rn;
+                rn = r + 1 >= nr ? 0 : r + 1;
+                __syncwarp();
+                gs_step<kBias, false>(B, LB, JA, A, JB, LA, st, r2 + hob, r2 + kCoefB, r3 + hob, lam0 + 16u * rn,
+                                      lam0 + 16u * r, leader, q0 + j + 1 < total, single);
+                r = rn;
+            }
+        }
+        rb = nb;
+        rpar = npar;
+        rs.on = rs.on && ok;
     }
-    for (; q + 1 < trips; q += 2) {
-        sweep_step<G, kBias, true>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
-        sweep_step<G, kBias, true>(B, LB, A, LA, st, rows, nr, total, single, ho, ring, lam, gl);
-    }
-    if (q < trips) sweep_step<G, kBias, true>(A, LA, B, LB, st, rows, nr, total, single, ho, ring, lam, gl);
     const V3 other = v3(__shfl_xor_sync(0xffffffffu, st.u.x, 1), __shfl_xor_sync(0xffffffffu, st.u.y, 1),
                         __shfl_xor_sync(0xffffffffu, st.u.z, 1));
     va = odd ? other : st.u;
     wa = odd ? st.u : other;
-    cp_async_wait_all();
+    // normally every issued chunk has been waited for; after a wait gave up, wait (bounded)
+    // for the copies issued after it, so that none lands after the kernel has moved on
+    const bool all_ok = __all_sync(0xffffffffu, ok);
+    for (int k = done; k < rs.seq; ++k) mbar_wait(rs.bar + 8u * (k % kChunkBufs), (unsigned)((k / kChunkBufs) & 1));
     __syncwarp();
+    return all_ok;
 }
 
 template <int G>
@@ -555,6 +711,13 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     }
     extern __shared__ __align__(16) float4 dyn_smem[];
     float4 *env_base = dyn_smem + (size_t)slot * env_stride_f4(p.lam_cap);
+    // the group's chunk buffers and their mbarriers, behind its impulse words
+    float4 *chunk_buf = env_base + p.lam_cap;
+    const unsigned chunk_bar = smem_addr(chunk_buf + kChunkBufs * kChunkF4);
+    if (!kJacobi && gl == 0) {
+        for (int b = 0; b < kChunkBufs; ++b) mbar_init(chunk_bar + 8u * b);
+        mbar_init_fence();
+    }
     __shared__ EnvSm S_all[kSolveMaxWarps * kGroups];
     EnvSm &S = S_all[slot];
     BodySm &B = S.B;
@@ -603,7 +766,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     const int nr = S.row_base[E.n_pairs];
     Row *rows = p.rows + E.row_off;
     float4 *lam = env_base;
-    float4 *ring = lam + p.lam_cap;
+    float4 *ring = chunk_buf;   // the general form's cp.async ring (it has no chunk stream)
     const int m = E.movable;
     const bool fast = (m != -2) && (kJacobi || nr <= p.lam_cap);
     // several movable bodies: general rows, impulses in shared memory when they fit
@@ -631,20 +794,43 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     }
     __threadfence_block();
     __syncwarp();
-    if (!kJacobi && fast && m >= 0) {
+    const bool streamed = !kJacobi && fast && m >= 0 && nr > 0;   // rows read through the chunk stream
+    if (streamed) {
         for (int r = gl; r < nr; r += G) couple_fast_row(frows + kRowF4 * r, frows + kRowF4 * (r + 1 < nr ? r + 1 : 0));
+    }
+    __syncwarp();
+    if (streamed) {   // the kRowPad rows after the env's rows repeat rows 0, 1, ... (mod nr)
+        for (int k = gl; k < kRowPad * kRowF4; k += G) {
+            const int j = k / kRowF4, f4 = k - j * kRowF4;
+            frows[kRowF4 * (nr + j) + f4] = frows[kRowF4 * (j % nr) + f4];
+        }
+        // the rows are read next by bulk copies (async proxy) that lane 0 issues: make this
+        // lane's row writes visible at device scope, then to the async proxy
+        __threadfence();
+        fence_async_global();
     }
     __threadfence_block();
     __syncwarp();
     // 3. Gauss-Seidel sweeps (no movable body: nothing to solve)
     const bool run_fast = valid && fast && m >= 0;
+    RowStream rs;
+    rs.rows = frows;
+    rs.buf = chunk_buf;
+    rs.bar = chunk_bar;
+    rs.nr = run_fast ? nr : 0;
+    rs.pf = 0;
+    rs.seq = 0;
+    rs.ib = 0;
+    rs.leader = gl == 0;
+    rs.on = true;
+    bool waits_ok = true;
     {
         const int total = run_fast ? nr * p.n_iters : 0;
         const int trips = warp_max<G>(total);
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
         if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
         if (kJacobi) sweep_jacobi<G, true>(frows, run_fast ? nr : 0, p.n_iters, va, wa, gl);
-        else sweep_fast<G, true>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
+        else waits_ok = sweep_fast<G, true>(rs, total, trips, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
     }
     if (valid && !fast && gl == 0) {
@@ -694,13 +880,17 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         V3 va = v3(0, 0, 0), wa = v3(0, 0, 0);
         if (run_fast) { va = smv(B.v, m); wa = smv(B.w, m); }
         if (kJacobi) sweep_jacobi<G, false>(frows, run_fast ? nr : 0, p.n_vel_iters, va, wa, gl);
-        else sweep_fast<G, false>(frows, run_fast ? nr : 0, total, trips, ring, lam, va, wa, gl);
+        else if (waits_ok) {   // the row stream continues: rows from the start again
+            rs.pf = 0;
+            waits_ok = sweep_fast<G, false>(rs, total, trips, lam, va, wa, gl);
+        }
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
         if (valid && !fast && gl == 0) {
             if (kMulti && general_sm) sweep_general(rows, nr, p.n_vel_iters, ring, lam, B, false);
             else for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
         }
     }
+    if (!waits_ok && lane == 0) atomicOr(p.status, kStatusTimeout);   // a row chunk never arrived
     __syncwarp();
     for (int lb = gl; lb < E.n_bodies; lb += G) {
         const int bi = E.first_body + lb;
