@@ -15,10 +15,11 @@
 // items in batch order.  It stages a batch's candidates in shared memory (read in place
 // from global memory when there are more than kStage), assigns them to the existing
 // patches (64-bit shared atomics pick each slot's winner), ranks the rest by depth, and
-// turns them into new patches in rounds: one warp takes the kWin deepest unassigned
-// candidates and finds, with ballots, which of them FindDeepest would pick as patch seeds
-// one after another (a member is a seed unless an earlier seed's normal is similar
-// enough); then every thread runs BinReduce for all of the round's seeds at once (each
+// turns them into new patches in rounds: one warp takes the kWinR deepest unassigned
+// candidates and finds, with one ballot per seed and 32 members, which of them FindDeepest
+// would pick as patch seeds one after another (a member is a seed unless an earlier seed's
+// normal is similar enough; at most kWin per round); then every thread runs BinReduce for
+// all of the round's seeds at once (each
 // remaining candidate joins the first seed, in depth order, whose normal is similar), and
 // AddPatch takes the new patches in seed order.  The patches and contacts are those of
 // the one-patch-at-a-time loop: within a round no later seed can change an earlier
@@ -42,7 +43,9 @@ constexpr int kQueryPerThread = kBatch / kQueryThreads;   // 4 samples per threa
 constexpr int kQueryWarps = kQueryThreads / 32;
 constexpr int kReduceWarps = 4;
 constexpr int kStage = 256;              // candidates of a batch staged in shared memory
-constexpr int kWin = 32;                 // deepest unassigned candidates examined per round
+constexpr int kWin = 32;                 // new patches (seeds) per round at most
+constexpr int kWinR = 128;               // deepest unassigned candidates examined per round
+static_assert(kWinR <= kBatch, "the round's window reuses the batch's candidate list");
 
 __constant__ float c_cos6[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
 __constant__ float c_sin6[6] = {0.0f, 0.8660254037844386f, 0.8660254037844386f, 0.0f,
@@ -64,7 +67,9 @@ struct PatchSm {
     int *npat;                    // patches kept
     int *nun;                     // unassigned candidates of the batch
     int *nseed;                   // new patches of the round
-    int *win;                     // kWin: the round's candidates, then its seeds
+    int *win;                     // kWin: the round's seeds (candidate ids, seed order)
+    short *wcand;                 // kWinR: the round's window (candidate ids, depth order); it
+                                  // reuses cl, dead once the depth order is built
 };
 
 __host__ __device__ inline size_t patch_smem_bytes(int NP) {
@@ -90,6 +95,7 @@ __device__ __forceinline__ PatchSm carve_patch(unsigned char *base, int NP) {
     int *ip = reinterpret_cast<int *>(base + off);
     s.npat = ip; s.nun = ip + 1; s.nseed = ip + 2;
     s.win = ip + 4;
+    s.wcand = s.cl;
     return s;
 }
 
@@ -432,57 +438,89 @@ __device__ void add_patches(const PatchSm &S, int NP, int T0, int ns, int max_pa
     __syncwarp();
 }
 
-// One round's seeds, by one warp: the first kWin unassigned entries of the depth order
-// from position pos on; member i is a seed unless an earlier seed's normal is similar
-// enough (n_i . n_seed >= cos_patch), which is the order FindDeepest + BinReduce would
-// create them in.  Writes the seeds' patch frames into slots T0.. and their count to
-// *S.nseed; returns the next scan position.
+// One round's seeds, by one warp.  The window is the first kWinR unassigned entries of the
+// depth order from position pos on (lane l holds members l, l + 32, l + 64, l + 96).  The
+// seeds are the members FindDeepest would pick one after another: the first remaining
+// member is a seed, and every later member whose normal is similar enough to it
+// (n . n_seed >= cos_patch) is covered and can no longer be one; at most kWin seeds per
+// round, the window's uncovered rest staying for the next round.  Each seed costs one
+// broadcast of its normal and one ballot per 32 members.  Writes the seeds' patch frames
+// into slots T0.., their candidates into S.win and their count into *S.nseed; returns the
+// position from which the next round scans (entries consumed meanwhile are skipped).
 __device__ int next_seeds(const PatchSm &S, int NP, int T0, const float4 *cd, const int *order, int m, int pos,
                           float cos_patch) {
+    constexpr int kQ = kWinR / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int k = 0;
-    while (k < kWin && pos < m) {
+    const int start = pos;
+    while (k < kWinR && pos < m) {
         const int i = pos + lane;
         const int c = i < m ? order[i] : -1;
         const bool un = c >= 0 && S.cst[c] == -1;
         const unsigned b = __ballot_sync(0xffffffffu, un);
-        const int nb = __popc(b), take = min(nb, kWin - k);
+        const int nb = __popc(b), take = min(nb, kWinR - k);
         const int r = __popc(b & lt);
-        if (un && r < take) S.win[k + r] = c;
+        if (un && r < take) S.wcand[k + r] = (short)c;
         const unsigned last = __ballot_sync(0xffffffffu, un && r == take - 1);
         pos = (take == nb) ? pos + 32 : pos + __ffs(last);
         k += take;
     }
     __syncwarp();
-    const int c = lane < k ? S.win[lane] : -1;
-    const V3 n = c >= 0 ? cnrm(cd, c) : v3(0.0f, 0.0f, 0.0f);
-    unsigned cov = 0;   // bit j: earlier member j's normal is similar to this one's
-#pragma unroll 8
-    for (int j = 0; j < k; ++j) {
-        const V3 nj = v3(__shfl_sync(0xffffffffu, n.x, j), __shfl_sync(0xffffffffu, n.y, j),
-                         __shfl_sync(0xffffffffu, n.z, j));
-        if (j < lane && ndot(n, nj) >= cos_patch) cov |= 1u << j;
+    V3 n[kQ];
+    unsigned rem[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const int idx = 32 * q + lane;
+        const bool v = idx < k;
+        n[q] = v ? cnrm(cd, S.wcand[idx]) : v3(0.0f, 0.0f, 0.0f);
+        rem[q] = __ballot_sync(0xffffffffu, v);
     }
-    unsigned rem = (k == 32) ? 0xffffffffu : ((1u << k) - 1u), seeds = 0u;
-    while (rem) {   // the deepest remaining member is the next seed; the members it covers are not
-        const int i = __ffs(rem) - 1;
-        seeds |= 1u << i;
-        rem &= ~((1u << i) | __ballot_sync(0xffffffffu, (cov >> i) & 1u));
+    int ns = 0;
+    while (ns < kWin) {
+        int q0 = kQ;   // first word with a remaining member (the same on every lane)
+#pragma unroll
+        for (int q = kQ - 1; q >= 0; --q) q0 = rem[q] ? q : q0;
+        if (q0 == kQ) break;
+        int l = 0;
+        V3 nq = n[0];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q == q0) { l = __ffs(rem[q]) - 1; nq = n[q]; }
+        }
+        const V3 sd = v3(__shfl_sync(0xffffffffu, nq.x, l), __shfl_sync(0xffffffffu, nq.y, l),
+                         __shfl_sync(0xffffffffu, nq.z, l));
+        const int i = 32 * q0 + l;   // the seed's window index
+        if (lane == 0) S.win[ns] = S.wcand[i];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const bool later = 32 * q + lane > i;
+            const unsigned cov = __ballot_sync(0xffffffffu, later && ndot(n[q], sd) >= cos_patch);
+            rem[q] &= ~cov;
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            if (q == q0) rem[q] &= ~(1u << l);
+        ++ns;
     }
-    __syncwarp();   // every lane has read S.win
-    if ((seeds >> lane) & 1u) {
-        const int t = __popc(seeds & lt), T = T0 + t;
+    __syncwarp();   // S.win written
+    if (lane < ns) {
+        const int c = S.win[lane], T = T0 + lane;
+        const V3 nn = cnrm(cd, c);
         V3 t1, t2;
-        tangent_basis(n, t1, t2);
-        S.win[t] = c;
-        S.pn4[T] = make_float4(n.x, n.y, n.z, 0.0f);
+        tangent_basis(nn, t1, t2);
+        S.pn4[T] = make_float4(nn.x, nn.y, nn.z, 0.0f);
         set_pvec(S.pa, NP, T, cpos(cd, c));
         set_pvec(S.pt1, NP, T, t1);
         for (int q = 0; q < kSlots; ++q) S.keys[q * NP + T] = 0ull;
     }
-    if (lane == 0) *S.nseed = __popc(seeds);
-    return pos;
+    if (lane == 0) *S.nseed = ns;
+    // every window member is now a seed or covered by one (BinReduce consumes them all): the
+    // next round scans on from the window's end; otherwise (kWin seeds reached) from its start
+    unsigned left = 0u;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) left |= rem[q];
+    return left ? start : pos;
 }
 
 // Algorithm 1 for one batch: nc candidates in sample order at cd (shared or global
