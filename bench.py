@@ -425,9 +425,21 @@ def run_fw(args):
                 "traffic": traffic.get(name), "avg_launch_ms": ms, "algorithmic_bytes": nbytes,
                 "peak_source": f"{peak_kind} hbm_gbs", "l2": l2_entry(name, ms)}
 
+    def l2_bound_entry(name, nbytes, ms):
+        # a kernel whose working set (grid cells, samples) is shared by every env and stays
+        # in the 126 MB L2: its algorithmic bytes are served by L2, so L2 bounds it; the HBM
+        # figure is kept beside it
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "l2", "achieved": gbs, "peak": l2_gbs, "unit": "GB/s", "frac": gbs / l2_gbs,
+                "traffic": traffic.get(name), "avg_launch_ms": ms, "algorithmic_bytes": nbytes,
+                "peak_source": "measured L2 read bandwidth (fw_measure_l2_read, 48 MB, L1 bypassed)",
+                "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                        "peak_source": f"{peak_kind} hbm_gbs"},
+                "l2": l2_entry(name, ms)}
+
     sol_tf = sol_flops / (sol_ms * 1e-3) / 1e12
     kernels = {
-        "query_kernel": dict(hbm_entry("query_kernel", q_bytes, qry_ms),
+        "query_kernel": dict(l2_bound_entry("query_kernel", q_bytes, qry_ms),
                              **{("faces_per_s" if tri_mode else "queries_per_s"): queries / (qry_ms * 1e-3)}),
         "reduce_kernel": hbm_entry("reduce_kernel", r_bytes, red_ms),
         "solve_kernel": {"bound": "alu", "achieved": sol_tf, "peak": alu_peak, "unit": "TFLOP/s",

@@ -313,3 +313,103 @@ def test_autograd_function_through_a_pose_loss(diff_world):
         assert torch.allclose(got, want, rtol=1e-6, atol=1e-12)
     assert torch.isfinite(mass.grad).all() and mass.grad[pegs].abs().max() > 0
     assert mu.grad.abs().max() > 0
+
+
+# ------------------------------------------------------------- config-3 size, untaped differences
+def _env_tapes(t, n_envs):
+    """per env, per substep: (contact records, row bits, clamp bit) of a tape"""
+    S_, K = t["S"], t["K"]
+    off, rec, rb, bb = t["c_off"], t["c_rec"], t["r_bits"], t["b_bits"]
+    out = []
+    for e in range(n_envs):
+        parts = []
+        for s in range(S_):
+            a, b = off[s * n_envs + e], off[s * n_envs + e + 1]
+            parts.append((rec[a:b].tobytes(), rb[K * a:K * b].tobytes(), int(bb[s * n_envs + e])))
+        out.append(parts)
+    return out
+
+
+def test_config3_adjoint_against_untaped_central_differences():
+    """The differentiable peg at its configured size (256 envs, one frame of 32 substeps x 8
+    sweeps) against central differences of the FP64 oracle's own forward -- not a replay of
+    a tape.  Each env is moved along its own random direction over all 14 inputs (position,
+    rotation, linear and angular velocity, mass, friction; scaled by 1 mm, 0.01 rad, 1 cm/s,
+    1 rad/s, the mass and 1) by +-h with h = 1e-6, and the oracle records its own decisions
+    at x0 and at both ends.  Envs whose decisions (contacts with their SDF cells and branch
+    bits, per-sweep clamp bits, |omega| clamp) are the same at all three points are kept:
+    there the frame is one smooth function and its central difference is exact to O(h^2).
+    On every kept env whose GPU tape also equals the oracle's, the GPU adjoint's
+    directional derivative agrees to 1e-3 relative.  The kept and agreeing fractions are
+    printed and floored.  (h = 1e-4 keeps no env of this workload: a jammed peg carries
+    ~1,300 taped contacts and ~10,000 clamp bits per env, and a step of 0.1 um in position
+    already moves some sample across an SDF cell or a reduction slot's winner.)"""
+    fw = _fw()
+    sc, tp, tq = S.diff_peg_scene(n_envs=256, seed=4)
+    E, K, Sn = sc.n_envs, sc.sim.n_iters, sc.sim.n_substeps
+    b0 = sc.groups[0].bodies
+    x0 = [np.ascontiguousarray(b0[k].reshape(-1, b0[k].shape[-1]), np.float32) for k in ("pos", "quat", "linvel", "angvel")]
+    nb = len(x0[0])
+    pegs = np.arange(0, nb, 2)
+    gw = fw.world_from_scene(sc)
+    gw.set_state(*x0)
+    gw.record_rollout(Sn, K)
+    tg = _env_tapes(gw.get_tape(), E)
+    rng = np.random.default_rng(11)
+    g = [rng.normal(size=(nb, k)).astype(np.float32) for k in (3, 4, 3, 3)]
+    g[0] *= 1e3
+    for a in g:
+        a[1::2] = 0.0
+    adj = gw.adjoint_rollout(*g)
+    ow = O.world_from_scene(sc, lazy_bake=True)
+    mass0 = np.array([ow.body_mass(int(b)) for b in pegs])
+    mu0 = np.array([ow.pair_mu(e) for e in range(E)])
+    x64 = [a.astype(np.float64) for a in x0]
+
+    def record(xs, mass, mu):
+        ow.set_state(*xs)
+        for e, b in enumerate(pegs):
+            ow.set_body_mass(int(b), float(mass[e]))
+        for e in range(E):
+            ow.set_pair_mu(e, float(mu[e]))
+        ow.diff_record(Sn, K)
+        return _env_tapes(ow.get_tape(), E), [a.copy() for a in ow.state()]
+
+    h = 1e-6
+    scale = dict(pos=1e-3, rot=1e-2, lin=1e-2, ang=1.0)
+    d = {k: rng.normal(size=(E, 3)) for k in scale}
+    dm, dmu = rng.normal(size=E), rng.normal(size=E)
+
+    def perturbed(sign):
+        xs = [a.copy() for a in x64]
+        for e, bdy in enumerate(pegs):
+            xs[0][bdy] += sign * h * scale["pos"] * d["pos"][e]
+            xs[2][bdy] += sign * h * scale["lin"] * d["lin"][e]
+            xs[3][bdy] += sign * h * scale["ang"] * d["ang"][e]
+            th = sign * h * scale["rot"] * d["rot"][e]
+            xs[1][bdy] = S.quat_mul(S.quat_axis_angle(th / np.linalg.norm(th), np.linalg.norm(th)), x64[1][bdy])
+        return xs, mass0 * (1.0 + sign * h * dm), mu0 + sign * h * dmu
+
+    to, _ = record(x64, mass0, mu0)
+    tpl, xp = record(*perturbed(+1.0))
+    tmi, xm = record(*perturbed(-1.0))
+    kept = np.array([to[e] == tpl[e] == tmi[e] for e in range(E)])
+    agree = np.array([tg[e] == to[e] for e in range(E)])
+    g64 = [a.astype(np.float64) for a in g]
+    loss = lambda X: sum((gi * xi).sum(axis=1) for gi, xi in zip(g64, X))[pegs]
+    fd = (loss(xp) - loss(xm)) / 2.0
+    an = np.zeros(E)
+    for e, bdy in enumerate(pegs):
+        an[e] += adj[0][bdy] @ (h * scale["pos"] * d["pos"][e]) + adj[2][bdy] @ (h * scale["lin"] * d["lin"][e])
+        an[e] += adj[3][bdy] @ (h * scale["ang"] * d["ang"][e])
+        th = h * scale["rot"] * d["rot"][e]
+        an[e] += adj[1][bdy].astype(np.float64) @ (0.5 * S.quat_mul(np.array([th[0], th[1], th[2], 0.0]), x64[1][bdy]))
+        an[e] += adj[4][bdy] * mass0[e] * h * dm[e] + adj[5][e] * h * dmu[e]
+    err = np.abs(an - fd) / np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max())
+    both = kept & agree
+    print(f"\nconfig-3 adjoint: {kept.sum()} of {E} envs keep every decision within +-h, the GPU tape equals the "
+          f"oracle's in {agree.sum()}, both in {both.sum()}; GPU directional derivative vs untaped FP64 central "
+          f"differences there: median {np.median(err[both]):.1e}, max {err[both].max():.1e}; "
+          f"over the other envs median {np.median(err[~both]):.1e}")
+    assert kept.sum() >= 0.5 * E and both.sum() >= 0.3 * E, (kept.sum(), both.sum())
+    assert np.all(err[both] <= 1e-3), float(err[both].max())
