@@ -139,12 +139,17 @@ typedef struct {
 /* Fills *cfg with the defaults listed in fw_config. */
 FW_API void fw_config_default(fw_config *cfg);
 
-/* Creates a world on cfg->device.  *out receives the handle (NULL on failure).
+/* Creates a world on cfg->device: the container of many independent environments that are
+ * stepped in parallel on one GPU (Sec. III-D runs 1,024 of them), with the simulation
+ * constants of fw_config (frame time 1/60 s and substeps per frame: the caption of Table
+ * "performance statistics"; Generate batches of 1024 and N patches per pair: Sec. III-C).
+ * *out receives the handle (NULL on failure).
  * Errors: FW_ERR_ARG for batch_size != 1024, patch_dirs != 6, max_patches outside 1..256,
  * dt <= 0. */
 FW_API fw_status fw_create(const fw_config *cfg, fw_world **out);
 
-/* Frees every device and host resource of the world.  NULL is accepted. */
+/* Frees every device and host resource of the world (no counterpart in the paper).  NULL
+ * is accepted. */
 FW_API fw_status fw_destroy(fw_world *w);
 
 /* ---------------------------------------------------------------- assets */
@@ -211,7 +216,9 @@ FW_API fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *
 /* ---------------------------------------------------------------- stepping */
 
 /* Advances every environment by one frame dt as n_substeps substeps of
- * hs = dt / n_substeps.  Each substep: external forces (gravity, applied force and
+ * hs = dt / n_substeps (substeps and solver iterations per frame: Sec. III-B and Table
+ * "performance statistics"; the substep itself: Sec. III-A SDF collisions, Sec. III-C
+ * contact reduction, Sec. III-B solve).  Each substep: external forces (gravity, applied force and
  * torque, gyroscopic term); contact detection and reduction at the current poses;
  * constraint rows per contact (normal, two tangents, effective masses, bias
  * phi/hs if phi > 0 else baumgarte*phi/hs); n_iters Gauss-Seidel sweeps, each contact's
@@ -241,13 +248,16 @@ FW_API fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int
 
 /* ---------------------------------------------------------------- state */
 
-/* Body state of all bodies (global body order = env order, then body order):
- * pos n x 3, quat n x 4, linvel n x 3, angvel n x 3 (float32).  Any pointer may be NULL
+/* Body state of all bodies (global body order = env order, then body order; see
+ * fw_get_env_info): pos n x 3, quat n x 4, linvel n x 3, angvel n x 3 (float32) -- the
+ * state the integration of Sec. III-B advances, and all a frame needs to resume (contacts
+ * are detected again every substep and impulses start at zero).  Any pointer may be NULL
  * to skip it.  device_ptrs = 0 synchronises. */
 FW_API fw_status fw_get_state(fw_world *w, float *pos, float *quat, float *linvel,
                               float *angvel, int device_ptrs);
-/* Sets the state; quaternions are normalised on the device.  device_ptrs = 0 synchronises
- * before returning so host buffers may be reused. */
+/* Sets the state of Sec. III-B's integration (the layout of fw_get_state); quaternions are
+ * normalised on the device.  device_ptrs = 0 synchronises before returning so host buffers
+ * may be reused. */
 FW_API fw_status fw_set_state(fw_world *w, const float *pos, const float *quat,
                               const float *linvel, const float *angvel, int device_ptrs);
 
@@ -408,6 +418,14 @@ FW_API fw_status fw_get_detect_stats(fw_world *w, long long *n_candidates, long 
 
 /* Sizes: n_envs, n_bodies, n_pairs (any pointer may be NULL). */
 FW_API fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs);
+
+/* Where one environment's bodies and pairs sit in the world's global order (the index of its
+ * first body in fw_get_state's arrays, its body count, the index of its first pair in
+ * fw_adjoint_rollout's d_mu and its pair count); any pointer may be NULL.  With several
+ * fw_add_env_bodies calls of different structures, this is how a caller finds a body.
+ * Errors: FW_ERR_ARG for env outside 0..n_envs-1. */
+FW_API fw_status fw_get_env_info(fw_world *w, int env, int *first_body, int *n_bodies, int *first_pair,
+                                 int *n_pairs);
 
 /* Number of kernel launches one fw_step(n_substeps, ...) enqueues. */
 FW_API int fw_launches_per_step(fw_world *w, int n_substeps);

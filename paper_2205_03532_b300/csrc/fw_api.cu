@@ -60,6 +60,7 @@ struct fw_world {
     int *d_pair_item0 = nullptr;
     float4 *d_cand = nullptr;    // candidates of every item
     int *d_cand_count = nullptr;
+    PairMap *d_maps = nullptr;   // each pair's composed map into its SDF grid
     int n_items = 0;
     Row *d_rows = nullptr;
     unsigned *d_status = nullptr;
@@ -256,7 +257,7 @@ fw_status ensure_device(fw_world *w) {
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows);
-    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count);
+    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count); dfree(w->d_maps);
     w->n_items = 0;
     const int np = (int)w->pairs.size(), ne = (int)w->envs.size();
     const int cp = cap_pair(w);
@@ -277,6 +278,7 @@ fw_status ensure_device(fw_world *w) {
         CK(cudaMemcpy(w->d_pairs, w->pairs.data(), sizeof(PairDev) * np, cudaMemcpyHostToDevice));
         CK(cudaMalloc(&w->d_contacts, sizeof(DContact) * (size_t)np * cp));
         CK(cudaMalloc(&w->d_counts, sizeof(int) * np));
+        CK(cudaMalloc(&w->d_maps, sizeof(PairMap) * np));
         CK(cudaMemsetAsync(w->d_counts, 0, sizeof(int) * np, w->stream));
         long long sl = 0;
         for (auto &P : w->pairs) sl = std::max(sl, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
@@ -340,6 +342,7 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.n_items = w->n_items;
     p.cand = w->d_cand;
     p.cand_count = w->d_cand_count;
+    p.maps = w->d_maps;
     p.rows = w->d_rows;
     p.status = w->d_status;
     p.n_pairs = (int)w->pairs.size();
@@ -554,7 +557,7 @@ fw_status fw_destroy(fw_world *w) {
     dfree(w->d_props); dfree(w->d_pairs); dfree(w->d_envs);
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
-    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count);
+    dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count); dfree(w->d_maps);
     for (auto e : w->ev_pool) cudaEventDestroy(e);
     for (auto e : w->ev_used) cudaEventDestroy(e);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
@@ -1566,9 +1569,21 @@ fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_pairs) {
     return FW_OK;
 }
 
+fw_status fw_get_env_info(fw_world *w, int env, int *first_body, int *n_bodies, int *first_pair, int *n_pairs) {
+    if (!w) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size()) return fail(w, FW_ERR_ARG, "fw_get_env_info: env out of range");
+    const EnvDev &E = w->envs[env];
+    if (first_body) *first_body = E.first_body;
+    if (n_bodies) *n_bodies = E.n_bodies;
+    if (first_pair) *first_pair = E.first_pair;
+    if (n_pairs) *n_pairs = E.n_pairs;
+    return FW_OK;
+}
+
 int fw_launches_per_step(fw_world *w, int n_substeps) {
     if (!w || n_substeps < 1) return 0;
-    return 3 * n_substeps;   // query, reduction, solve
+    // per substep: the pairs' maps (per-sample generation only), query, reduction, solve
+    return (w->cfg.contact_gen == 0 ? 4 : 3) * n_substeps;
 }
 
 const char *fw_last_error(const fw_world *w) {

@@ -128,19 +128,71 @@ __device__ __forceinline__ void load_pose(const SimParams &p, int body, M3 &R, V
     t = ld3(p.pos + 3 * body);
 }
 
-// The narrow phase of one sample: world point, world normal and signed distance.  False
-// when the point is outside the SDF grid or the gradient vanishes (|grad| < 1e-12).
+// Column i of the rotation of q = (x, y, z, w) (row i of its transpose), in FP64.
+__device__ __forceinline__ void rot_col(const float *q, int i, double r[3]) {
+    const double x = q[0], y = q[1], z = q[2], w = q[3];
+    if (i == 0) { r[0] = 1.0 - 2.0 * (y * y + z * z); r[1] = 2.0 * (x * y + z * w); r[2] = 2.0 * (x * z - y * w); }
+    else if (i == 1) { r[0] = 2.0 * (x * y - z * w); r[1] = 1.0 - 2.0 * (x * x + z * z); r[2] = 2.0 * (y * z + x * w); }
+    else { r[0] = 2.0 * (x * z + y * w); r[1] = 2.0 * (y * z - x * w); r[2] = 1.0 - 2.0 * (x * x + y * y); }
+}
+
+// The map of pair P into body B's grid (PairMap), by one thread in FP64 from the float32
+// quaternions and positions; 1/h is the stored float pair inv_h + inv_h_lo (1/h to ~1e-14).
+// Formed once per pair and substep (map_kernel) and the same way, by this one function, for
+// the per-pair test hook.  A point whose translation is not finite gets a cell far outside.
+__device__ __noinline__ void pair_map(const SimParams &p, const PairDev &P, const AssetDev &gb, PairMap &M) {
+    const float *qa = p.quat + 4 * P.a, *qb = p.quat + 4 * P.b;
+    const double inv_h = (double)gb.inv_h + (double)gb.inv_h_lo;
+    const double d[3] = {(double)p.pos[3 * P.a] - p.pos[3 * P.b], (double)p.pos[3 * P.a + 1] - p.pos[3 * P.b + 1],
+                         (double)p.pos[3 * P.a + 2] - p.pos[3 * P.b + 2]};
+    double ra[3][3];
+    for (int j = 0; j < 3; ++j) rot_col(qa, j, ra[j]);
+    for (int i = 0; i < 3; ++i) {
+        double rb[3];
+        rot_col(qb, i, rb);
+        for (int j = 0; j < 3; ++j)
+            M.A[3 * i + j] = (float)((rb[0] * ra[j][0] + rb[1] * ra[j][1] + rb[2] * ra[j][2]) * inv_h);
+        const double u = ((rb[0] * d[0] + rb[1] * d[1] + rb[2] * d[2]) - (double)gb.lo[i]) * inv_h;
+        const double fl = floor(u);
+        const bool finite = fl == fl && fabs(fl) < 1.0e6;
+        M.c[i] = finite ? (int)fl : -(1 << 28);
+        M.f[i] = finite ? (float)(u - fl) : 0.0f;
+    }
+    M.pad_ = 0;
+}
+
+// Every pair's map for the coming query (one thread per pair).
+__global__ void map_kernel(SimParams p) {
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= p.n_pairs) return;
+    const PairDev P = p.pairs[pi];
+    PairMap M;
+    pair_map(p, P, p.assets[P.asset_b], M);
+    p.maps[pi] = M;
+}
+
+// The narrow phase of one sample through the pair's map: signed distance, and the world
+// normal (R_B g / |g|, float32) and world point (R_A s + p_A) for a candidate.  False when the
+// point is outside the SDF grid or the gradient vanishes (|grad| < 1e-12).
 template <int kStore = kStoreAny>
-__device__ __forceinline__ bool query_sample(const PairXf &X, const AssetDev &gb, float4 s, V3 &xw, V3 &nw,
-                                             float &phi) {
-    xw = mul(X.RA, v3(s.x, s.y, s.z)) + X.pA;
-    const V3 xb = mul_t(X.RB, xw - X.pB);
+__device__ __forceinline__ bool query_sample(const PairMap &M, const PairXf &X, const AssetDev &gb, float4 s,
+                                             V3 &xw, V3 &nw, float &phi) {
+    const float ux = __fmaf_rn(M.A[2], s.z, __fmaf_rn(M.A[1], s.y, __fmaf_rn(M.A[0], s.x, M.f[0])));
+    const float uy = __fmaf_rn(M.A[5], s.z, __fmaf_rn(M.A[4], s.y, __fmaf_rn(M.A[3], s.x, M.f[1])));
+    const float uz = __fmaf_rn(M.A[8], s.z, __fmaf_rn(M.A[7], s.y, __fmaf_rn(M.A[6], s.x, M.f[2])));
+    int ci, cj, ck;
+    float fx, fy, fz;
+    const bool okx = cell_of(ux, M.c[0], gb.dims[0], ci, fx);
+    const bool oky = cell_of(uy, M.c[1], gb.dims[1], cj, fy);
+    const bool okz = cell_of(uz, M.c[2], gb.dims[2], ck, fz);
     V3 g;
-    const bool in = sdf_lookup_any<kStore>(gb, xb, phi, g);
+    if (gb.cell16) sdf_cell_eval<true, kStore>(gb, ci, cj, ck, fx, fy, fz, phi, g);
+    else sdf_cell_eval<false, kStore>(gb, ci, cj, ck, fx, fy, fz, phi, g);
     const float gg = dot(g, g);
     const V3 nb = rsqrtf(fmaxf(gg, 1e-30f)) * g;   // unit to a few ulp; the decisions on it have margins
     nw = mul(X.RB, nb);
-    return in && (gg >= 1e-24f);
+    xw = mul(X.RA, v3(s.x, s.y, s.z)) + X.pA;
+    return okx && oky && okz && (gg >= 1e-24f);
 }
 
 // Closest point of the triangle (a, b, c) to p: p's Voronoi region among the vertices,
@@ -767,16 +819,16 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
             ph[u] = r0.w;
             nw[u] = v3(r1.x, r1.y, r1.z);
         }
-    } else {      // one per surface sample
+    } else {      // one per surface sample, through the pair's map (map_kernel)
+        const PairMap M = p.maps[pi];
         PairXf X;
         load_pose(p, P.a, X.RA, X.pA);
         load_pose(p, P.b, X.RB, X.pB);
 #pragma unroll
         for (int u = 0; u < kQueryPerThread; ++u) {
             const int i = base + u * kQueryThreads + tid;
-            const int ic = i < ga.ns ? i : ga.ns - 1;
-            const float4 s = __ldg(&ga.samples[ic]);
-            ok[u] = query_sample<kStore>(X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
+            const float4 s = __ldg(&ga.samples[i < ga.ns ? i : ga.ns - 1]);
+            ok[u] = query_sample<kStore>(M, X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
         }
     }
     // compaction in sample order: local sample u * 256 + warp * 32 + lane
@@ -893,6 +945,9 @@ __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
     const PairDev P = p.pairs[pi];
     const AssetDev ga = p.assets[P.asset_a];
     const AssetDev gb = p.assets[P.asset_b];
+    __shared__ PairMap Ms;
+    if (threadIdx.x == 0) pair_map(p, P, gb, Ms);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ga.ns) return;
     PairXf X;
@@ -900,7 +955,7 @@ __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
     load_pose(p, P.b, X.RB, X.pB);
     V3 xw, nw;
     float f;
-    if (query_sample(X, gb, ga.samples[i], xw, nw, f)) {
+    if (query_sample(Ms, X, gb, ga.samples[i], xw, nw, f)) {
         phi[i] = f;
         nrm[3 * i] = nw.x; nrm[3 * i + 1] = nw.y; nrm[3 * i + 2] = nw.z;
     } else {
@@ -1029,6 +1084,11 @@ cudaError_t prepare_detect(int max_patches) {
 
 cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
+    if (p.contact_gen == 0) {
+        map_kernel<<<(p.n_pairs + 127) / 128, 128, 0, s>>>(p);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (p.sdf_bricks) {
         if (p.contact_gen == 1) query_kernel<true, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);
         else query_kernel<false, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);

@@ -122,17 +122,13 @@ __device__ __forceinline__ long long cell_offset(const AssetDev &g, int ci, int 
     return st >= 0 ? (long long)st * kBrickCells + l : 0;
 }
 
-// Trilinear value and gradient from the cell-corner copy; the corner loads (one or two
-// 16-byte loads) are always in bounds and issued before the in-grid test is used, so
-// several lookups can overlap their memory latency.  A cell of a brick left out of the
-// narrow band answers phi = +band (or -band inside) with a zero gradient.
+// Trilinear value and gradient in cell (ci, cj, ck) at fractions (fx, fy, fz) from the
+// cell-corner copy (the cell must be a valid cell of the grid: its one or two 16-byte loads
+// are in bounds).  A cell of a brick left out of the narrow band answers phi = +band (or
+// -band inside) with a zero gradient.
 template <bool kHalf, int kStore = kStoreAny>
-__device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
-    int ci, cj, ck;
-    float fx, fy, fz;
-    const bool okx = grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx);
-    const bool oky = grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy);
-    const bool okz = grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz);
+__device__ __forceinline__ void sdf_cell_eval(const AssetDev &g, int ci, int cj, int ck, float fx, float fy, float fz,
+                                              float &phi, V3 &grad) {
     int st;
     const long long o = cell_offset<kStore>(g, ci, cj, ck, st);
     float v000, v100, v010, v110, v001, v101, v011, v111;
@@ -169,7 +165,36 @@ __device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, 
         phi = st == -1 ? g.band : -g.band;
         grad = v3(0.0f, 0.0f, 0.0f);
     }
+}
+
+// Trilinear value and gradient of the asset's SDF at x (grid frame); the corner loads are
+// always in bounds and issued before the in-grid test is used, so several lookups can
+// overlap their memory latency.  Returns whether x lies in the grid box.
+template <bool kHalf, int kStore = kStoreAny>
+__device__ __forceinline__ bool sdf_lookup(const AssetDev &g, V3 x, float &phi, V3 &grad) {
+    int ci, cj, ck;
+    float fx, fy, fz;
+    const bool okx = grid_coord(x.x, g.lo[0], g.inv_h, g.inv_h_lo, g.dims[0], ci, fx);
+    const bool oky = grid_coord(x.y, g.lo[1], g.inv_h, g.inv_h_lo, g.dims[1], cj, fy);
+    const bool okz = grid_coord(x.z, g.lo[2], g.inv_h, g.inv_h_lo, g.dims[2], ck, fz);
+    sdf_cell_eval<kHalf, kStore>(g, ci, cj, ck, fx, fy, fz, phi, grad);
     return okx && oky && okz;
+}
+
+// Cell index and fraction along one axis from a grid coordinate given as an integer part
+// (exact) plus a float32 remainder u (|u| a few hundred at most): the cell holding the point
+// clamped to the grid, and whether the point lies in [0, dim - 1].  NaN gives false.
+__device__ __forceinline__ bool cell_of(float u, int base, int dim, int &c, float &f) {
+    const float fl = floorf(u);
+    float fr = u - fl;                                   // exact
+    const bool finite = fl == fl && fabsf(fl) < 1.0e6f;
+    int ci = finite ? (int)fl + base : -1;
+    bool ok = finite && ci >= 0 && ci <= dim - 1 && !(ci == dim - 1 && fr > 0.0f);
+    if (ci >= dim - 1) { ci = dim - 2; fr = 1.0f; }
+    if (ci < 0) { ci = 0; fr = 0.0f; }
+    c = ci;
+    f = fr;
+    return ok;
 }
 
 template <int kStore = kStoreAny>

@@ -75,6 +75,17 @@ struct PairDev {
     int pad_[3];
 };
 
+// The pose of one pair as a single affine map from body A's frame into body B's grid
+// coordinates: u = A s + f + c for a sample s, A = R_B^T R_A / h (row-major), and the
+// translation (R_B^T (p_A - p_B) - lo) / h split into an integer part c (exact) and a
+// remainder f in [0, 1).  Formed in FP64 once per pair and substep, rounded once.
+struct __align__(16) PairMap {
+    float A[9];
+    float f[3];
+    int c[3];
+    int pad_;
+};
+
 struct EnvDev {
     int first_body, n_bodies;
     int first_pair, n_pairs;
@@ -129,6 +140,7 @@ struct SimParams {
     int n_items;
     float4 *cand;                          // n_items x kBatch x 2: (x_w, phi), (n_w, sample)
     int *cand_count;                       // n_items
+    PairMap *maps;                         // n_pairs: each pair's map into its SDF grid
     int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
     int multi_movable;                     // some env has several movable bodies (general sweep form)
     int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks

@@ -29,7 +29,8 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
-                 "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_launches_per_step",
+                 "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info",
+                 "fw_launches_per_step",
                  "fw_last_error", "fw_measure_l2_read"]
 
 
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "fw_set_body_params": (st, [vp, vp, vp]),
         "fw_get_detect_stats": (st, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fw_get_counts": (st, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "fw_get_env_info": (st, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "fw_launches_per_step": (i, [vp, i]),
         "fw_last_error": (C.c_char_p, [vp]),
         "fw_measure_l2_read": (st, [i, C.c_longlong, i, C.POINTER(f)]),
@@ -235,6 +237,12 @@ class World:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         self._check(self.lib.fw_get_counts(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
+
+    def env_info(self, env: int) -> Tuple[int, int, int, int]:
+        """(first body, bodies, first pair, pairs) of an env in the world's global order."""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.fw_get_env_info(self.h, env, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return a.value, b.value, c.value, d.value
 
     # -- stepping
     def step(self, n_substeps: int, n_iters: int):

@@ -122,3 +122,30 @@ def test_rollout_recording_refuses_per_triangle_contacts():
         w.replay_rollout()                                             # nothing was recorded
     assert _status(e) == ERR_STATE
     w.close()
+
+
+def test_env_info_locates_bodies_of_uneven_env_groups():
+    """Envs added by several calls with different structures: fw_get_env_info gives each
+    env's first body and pair in the global order of fw_get_state and the pair adjoints."""
+    fw = _fw()
+    w = fw.World()
+    V, T = S.box_mesh(0.01, 0.01, 0.01)
+    a = w.add_mesh_asset(V, T, S.sample_surface(V, T, 100, np.random.default_rng(0)))
+    b = w.add_mesh_asset(V, T, None)
+    w.bake_sdf(b, 32, 2e-3)
+    one = np.zeros((3, 1), S.BODY_DTYPE)
+    for e in range(3):
+        one[e, 0] = S._body(a, S.DYNAMIC, (0.1 * e, 0, 0.5), (0, 0, 0, 1), 0.5)
+    two = np.zeros((2, 2), S.BODY_DTYPE)
+    for e in range(2):
+        two[e, 0] = S._body(a, S.DYNAMIC, (0, 0.1 * e, 0.03), (0, 0, 0, 1), 0.5)
+        two[e, 1] = S._body(b, S.STATIC, (0, 0.1 * e, 0), (0, 0, 0, 1), 0.5)
+    assert w.add_env_bodies(one, np.zeros((0, 2), np.int32)) == 0
+    assert w.add_env_bodies(two, np.array([[0, 1]], np.int32)) == 3
+    assert [w.env_info(e) for e in range(5)] == [(0, 1, 0, 0), (1, 1, 0, 0), (2, 1, 0, 0), (3, 2, 0, 1), (5, 2, 1, 1)]
+    p = w.get_state()[0]
+    np.testing.assert_array_equal(p[5], two[1, 0]["pos"])
+    with pytest.raises(fw.FwError) as e:
+        w.env_info(5)
+    assert _status(e) == ERR_ARG
+    w.close()
