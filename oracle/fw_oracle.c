@@ -473,6 +473,7 @@ typedef struct {
     float *V; int nv; int *T; int nt;
     float *S; int ns;
     double density, mass, com[3], I[9];
+    double radius;              /* bounding sphere about the asset origin (vertices, samples) */
     int has_grid;
     grid_t grid;
 } asset_t;
@@ -485,17 +486,20 @@ typedef struct {
     double p[3], q[4], v[3], w[3];
 } body_t;
 
-typedef struct { int a, b; double mu; } pair_t;   /* global body ids */
-
-typedef struct {
-    int first_body, n_bodies, first_pair, n_pairs;
-} env_t;
+typedef struct { int a, b; double mu; int color; } pair_t;   /* global body ids; colour (piles) */
 
 typedef struct {
     or_contact *c; int n, cap;
     double m_len, m_dot;        /* margins of the last detection of this pair */
     int n_patches;
 } pair_contacts_t;
+
+typedef struct {
+    int first_body, n_bodies, first_pair, n_pairs;
+    /* piles (R20): the pairs come from a broad phase at every detection */
+    int pile;
+    pair_t *dp; pair_contacts_t *dpc; int ndp, cap_dp;
+} env_t;
 
 struct or_world {
     or_config cfg;
@@ -529,6 +533,10 @@ void or_destroy(or_world *w) {
         free(a->V); free(a->T); free(a->S); free(a->grid.val); free(a->grid.done); free(a->grid.bstate);
     }
     for (int i = 0; i < w->n_pairs; ++i) free(w->pc[i].c);
+    for (int e = 0; e < w->n_envs; ++e) {
+        for (int i = 0; i < w->envs[e].cap_dp; ++i) free(w->envs[e].dpc[i].c);
+        free(w->envs[e].dp); free(w->envs[e].dpc);
+    }
     free(w->assets); free(w->bodies); free(w->pairs); free(w->envs); free(w->pc);
     diff_tape_free(w);
     for (int e = 0; e < w->n_envs; ++e) free(w->imp[e]);
@@ -553,6 +561,16 @@ int or_add_asset(or_world *w, const float *V, int nv, const int *T, int nt,
     }
     a->density = density;
     or_mass_properties(V, T, nt, density, &a->mass, a->com, a->I);
+    double r2 = 0.0;
+    for (int i = 0; i < nv; ++i) {
+        const double x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+        if (x * x + y * y + z * z > r2) r2 = x * x + y * y + z * z;
+    }
+    for (int i = 0; i < a->ns; ++i) {
+        const double x = a->S[3 * i], y = a->S[3 * i + 1], z = a->S[3 * i + 2];
+        if (x * x + y * y + z * z > r2) r2 = x * x + y * y + z * z;
+    }
+    a->radius = sqrt(r2);
     return w->n_assets++;
 }
 
@@ -638,6 +656,8 @@ static void body_com_world(const body_t *b, double c[3]) {
 
 int or_add_envs(or_world *w, int n_envs, const or_body_desc *bd, int n_per_env,
                 const int *pairs, int n_pairs) {
+    const int pile = n_pairs < 0;   /* R20: pairs from the broad phase at every detection */
+    if (pile) n_pairs = 0;
     int nb0 = w->n_bodies, np0 = w->n_pairs, ne0 = w->n_envs;
     w->bodies = (body_t *)realloc(w->bodies, sizeof(body_t) * (nb0 + n_envs * n_per_env));
     w->pairs = (pair_t *)realloc(w->pairs, sizeof(pair_t) * (np0 + n_envs * n_pairs));
@@ -654,6 +674,8 @@ int or_add_envs(or_world *w, int n_envs, const or_body_desc *bd, int n_per_env,
         E->n_bodies = n_per_env;
         E->first_pair = np0 + e * n_pairs;
         E->n_pairs = n_pairs;
+        E->pile = pile;
+        E->dp = NULL; E->dpc = NULL; E->ndp = 0; E->cap_dp = 0;
         w->env_mlen[ne0 + e] = INFINITY;
         w->env_mdot[ne0 + e] = INFINITY;
         for (int i = 0; i < n_per_env; ++i) {
@@ -687,6 +709,7 @@ int or_add_envs(or_world *w, int n_envs, const or_body_desc *bd, int n_per_env,
             P->a = E->first_body + pairs[2 * p];
             P->b = E->first_body + pairs[2 * p + 1];
             P->mu = sqrt((double)w->bodies[P->a].mu * (double)w->bodies[P->b].mu);
+            P->color = 0;
             pair_contacts_t *pc = &w->pc[E->first_pair + p];
             memset(pc, 0, sizeof *pc);
             pc->m_len = INFINITY; pc->m_dot = INFINITY;
@@ -1019,14 +1042,70 @@ static int generate_candidates(const or_world *w, const pair_t *P, cand_t *out, 
     return n;
 }
 
-static void detect_pair(or_world *w, int pi) {
-    const pair_t *P = &w->pairs[pi];
+/* The pairs of an env and their contacts: the listed pairs, or a pile's current list. */
+static pair_t *env_pairs(const or_world *w, int e) {
+    const env_t *E = &w->envs[e];
+    return E->pile ? E->dp : &w->pairs[E->first_pair];
+}
+static pair_contacts_t *env_pcs(const or_world *w, int e) {
+    const env_t *E = &w->envs[e];
+    return E->pile ? E->dpc : &w->pc[E->first_pair];
+}
+static int env_np(const or_world *w, int e) {
+    const env_t *E = &w->envs[e];
+    return E->pile ? E->ndp : E->n_pairs;
+}
+
+static int movable(const body_t *b) { return b->type == 2 || b->type == 3; }
+
+/* R20: the pairs of a pile env, rebuilt at every detection.  For bodies i < j (env order),
+ * at least one of them movable: body i's samples against body j's SDF when i has samples
+ * and j a grid, else body j's samples against body i's SDF when j has samples and i a grid,
+ * else no pair.  A pair whose bounding spheres (about the asset origins) are farther apart
+ * than the contact offset plus two voxels of the SDF body is left out: no sample can have
+ * a candidate there (R19), so leaving it out changes no contact.  Pairs in (i, j) order. */
+static void pile_pairs(or_world *w, int e) {
+    env_t *E = &w->envs[e];
+    int n = 0;
+    for (int i = 0; i < E->n_bodies; ++i)
+        for (int j = i + 1; j < E->n_bodies; ++j) {
+            const body_t *Bi = &w->bodies[E->first_body + i], *Bj = &w->bodies[E->first_body + j];
+            if (!movable(Bi) && !movable(Bj)) continue;
+            const asset_t *Ai = &w->assets[Bi->asset], *Aj = &w->assets[Bj->asset];
+            int a, b;
+            if (Ai->ns > 0 && Aj->has_grid) { a = i; b = j; }
+            else if (Aj->ns > 0 && Ai->has_grid) { a = j; b = i; }
+            else continue;
+            const body_t *BA = &w->bodies[E->first_body + a], *BB = &w->bodies[E->first_body + b];
+            const asset_t *AA = &w->assets[BA->asset], *AB = &w->assets[BB->asset];
+            double d[3];
+            v_sub(BA->p, BB->p, d);
+            const double lim = AA->radius + AB->radius + w->cfg.contact_offset + 2.0 * AB->grid.h;
+            if (v_dot(d, d) > lim * lim) continue;
+            if (n == E->cap_dp) {
+                const int cap = E->cap_dp ? 2 * E->cap_dp : 64;
+                E->dp = (pair_t *)realloc(E->dp, sizeof(pair_t) * cap);
+                E->dpc = (pair_contacts_t *)realloc(E->dpc, sizeof(pair_contacts_t) * cap);
+                memset(E->dpc + E->cap_dp, 0, sizeof(pair_contacts_t) * (cap - E->cap_dp));
+                E->cap_dp = cap;
+            }
+            pair_t *P = &E->dp[n];
+            P->a = E->first_body + a;
+            P->b = E->first_body + b;
+            P->mu = sqrt((double)BA->mu * (double)BB->mu);
+            E->dpc[n].n = 0;
+            E->dpc[n].m_len = INFINITY; E->dpc[n].m_dot = INFINITY;
+            ++n;
+        }
+    E->ndp = n;
+}
+
+static void detect_pair(or_world *w, const pair_t *P, pair_contacts_t *pc) {
     const asset_t *aa = &w->assets[w->bodies[P->a].asset];
     const int n_src = w->cfg.contact_gen == 1 ? aa->nt : aa->ns;
     cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (n_src > 0 ? n_src : 1));
     margin_t m = {INFINITY, INFINITY};
     int nc = generate_candidates(w, P, c, &m);
-    pair_contacts_t *pc = &w->pc[pi];
     int cap = w->cfg.max_patches * NSLOT;
     if (pc->cap < cap) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * cap); pc->cap = cap; }
     pc->n = reduce_pair(c, nc, w->cfg.cos_patch, w->cfg.max_patches, w->cfg.batch_size,
@@ -1076,8 +1155,19 @@ static void ensure_nodes(or_world *w) {
         grid_t *g = &ab->grid;
         long long cap = 1024, nn = 0;
         long long *need = (long long *)malloc(sizeof(long long) * cap);
-        for (int pi = 0; pi < w->n_pairs; ++pi) {
-            const pair_t *P = &w->pairs[pi];
+        int n_all = w->n_pairs;
+        for (int e = 0; e < w->n_envs; ++e) n_all += w->envs[e].pile ? w->envs[e].ndp : 0;
+        for (int pi = 0; pi < n_all; ++pi) {
+            const pair_t *P = NULL;
+            if (pi < w->n_pairs) P = &w->pairs[pi];
+            else {   /* the pile envs' current pairs, env after env */
+                int k = pi - w->n_pairs;
+                for (int e = 0; e < w->n_envs && !P; ++e) {
+                    if (!w->envs[e].pile) continue;
+                    if (k < w->envs[e].ndp) P = &w->envs[e].dp[k];
+                    else k -= w->envs[e].ndp;
+                }
+            }
             const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
             if (B->asset != ai) continue;
             const asset_t *aa = &w->assets[A->asset];
@@ -1146,7 +1236,7 @@ double or_bake_seconds(const or_world *w) { return w->bake_seconds; }
  * sample is outside the grid or the gradient vanishes) */
 int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int *valid, double *gnorm) {
     ensure_nodes(w);
-    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const pair_t *P = &env_pairs(w, env)[pair];
     const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
     const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
     double RA[9], RB[9], RBt[9];
@@ -1174,7 +1264,7 @@ int or_query_pair(or_world *w, int env, int pair, double *phi, double *nrm, int 
 /* the candidates of one pair (Generate of Algorithm 1), rounded to float */
 int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int cap, int *n_out) {
     ensure_nodes(w);
-    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const pair_t *P = &env_pairs(w, env)[pair];
     const asset_t *aa = &w->assets[w->bodies[P->a].asset];
     const int n_src = w->cfg.contact_gen == 1 ? aa->nt : aa->ns;
     cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (n_src > 0 ? n_src : 1));
@@ -1193,7 +1283,7 @@ int or_pair_candidates(or_world *w, int env, int pair, or_candidate *out, int ca
 int or_tri_contacts(or_world *w, int env, int pair, double *x, double *phi, double *n, int *valid,
                     double *margin) {
     ensure_nodes(w);
-    const pair_t *P = &w->pairs[w->envs[env].first_pair + pair];
+    const pair_t *P = &env_pairs(w, env)[pair];
     const body_t *A = &w->bodies[P->a], *B = &w->bodies[P->b];
     const asset_t *aa = &w->assets[A->asset], *ab = &w->assets[B->asset];
     double RA[9], RB[9], RBt[9];
@@ -1215,15 +1305,27 @@ int or_tri_contacts(or_world *w, int env, int pair, double *x, double *phi, doub
 }
 
 int or_collide(or_world *w) {
+    for (int e = 0; e < w->n_envs; ++e)
+        if (w->envs[e].pile) pile_pairs(w, e);
     ensure_nodes(w);
+    int n_all = w->n_pairs;
+    for (int e = 0; e < w->n_envs; ++e) n_all += w->envs[e].pile ? w->envs[e].ndp : 0;
+    const pair_t **lp = (const pair_t **)malloc(sizeof(pair_t *) * (n_all > 0 ? n_all : 1));
+    pair_contacts_t **lc = (pair_contacts_t **)malloc(sizeof(pair_contacts_t *) * (n_all > 0 ? n_all : 1));
+    int k = 0;
+    for (int pi = 0; pi < w->n_pairs; ++pi, ++k) { lp[k] = &w->pairs[pi]; lc[k] = &w->pc[pi]; }
+    for (int e = 0; e < w->n_envs; ++e)
+        if (w->envs[e].pile)
+            for (int p = 0; p < w->envs[e].ndp; ++p, ++k) { lp[k] = &w->envs[e].dp[p]; lc[k] = &w->envs[e].dpc[p]; }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(team_size(w->cfg.n_threads))
 #endif
-    for (int pi = 0; pi < w->n_pairs; ++pi) detect_pair(w, pi);
+    for (int q = 0; q < n_all; ++q) detect_pair(w, lp[q], lc[q]);
+    free(lp); free(lc);
     for (int e = 0; e < w->n_envs; ++e) {
-        const env_t *E = &w->envs[e];
-        for (int p = 0; p < E->n_pairs; ++p) {
-            const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+        const pair_contacts_t *pcs = env_pcs(w, e);
+        for (int p = 0; p < env_np(w, e); ++p) {
+            const pair_contacts_t *pc = &pcs[p];
             if (pc->m_len < w->env_mlen[e]) w->env_mlen[e] = pc->m_len;
             if (pc->m_dot < w->env_mdot[e]) w->env_mdot[e] = pc->m_dot;
         }
@@ -1233,11 +1335,11 @@ int or_collide(or_world *w) {
 
 int or_get_contacts(const or_world *w, int env, or_contact *out, int cap, int *n_out,
                     double *min_margin_len, double *min_margin_dot) {
-    const env_t *E = &w->envs[env];
     int n = 0;
     double ml = INFINITY, md = INFINITY;
-    for (int p = 0; p < E->n_pairs; ++p) {
-        const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+    const pair_contacts_t *pcs = env_pcs(w, env);
+    for (int p = 0; p < env_np(w, env); ++p) {
+        const pair_contacts_t *pc = &pcs[p];
         for (int i = 0; i < pc->n; ++i) {
             if (n < cap) out[n] = pc->c[i];
             ++n;
@@ -1251,9 +1353,11 @@ int or_get_contacts(const or_world *w, int env, or_contact *out, int cap, int *n
     return n > cap ? -1 : 0;
 }
 
-/* contacts of an env go to its first pair (the solve only needs them in order) */
+/* contacts of an env go to its first pair (the solve only needs them in order); a pile
+ * env's contacts are set pair by pair (or_set_pair_contacts) */
 int or_set_contacts(or_world *w, int env, const or_contact *in, int n) {
     const env_t *E = &w->envs[env];
+    if (E->pile) return -1;
     for (int p = 0; p < E->n_pairs; ++p) w->pc[E->first_pair + p].n = 0;
     pair_contacts_t *pc = &w->pc[E->first_pair];
     if (pc->cap < n) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * n); pc->cap = n; }
@@ -1263,20 +1367,34 @@ int or_set_contacts(or_world *w, int env, const or_contact *in, int n) {
 }
 
 int or_get_pair_contacts(const or_world *w, int env, int pair, or_contact *out, int cap, int *n_out) {
-    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= w->envs[env].n_pairs) return -1;
-    const pair_contacts_t *pc = &w->pc[w->envs[env].first_pair + pair];
+    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= env_np(w, env)) return -1;
+    const pair_contacts_t *pc = &env_pcs(w, env)[pair];
     for (int i = 0; i < pc->n && i < cap; ++i) out[i] = pc->c[i];
     *n_out = pc->n;
     return pc->n > cap ? -1 : 0;
 }
 
 int or_set_pair_contacts(or_world *w, int env, int pair, const or_contact *in, int n) {
-    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= w->envs[env].n_pairs || n < 0) return -1;
-    pair_contacts_t *pc = &w->pc[w->envs[env].first_pair + pair];
+    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= env_np(w, env) || n < 0) return -1;
+    pair_contacts_t *pc = &env_pcs(w, env)[pair];
     if (pc->cap < n) { pc->c = (or_contact *)realloc(pc->c, sizeof(or_contact) * (n > 0 ? n : 1)); pc->cap = n; }
     if (n > 0) memcpy(pc->c, in, sizeof(or_contact) * n);
     pc->n = n;
     return 0;
+}
+
+/* A pile env's current pairs (from its last detection): (point body, SDF body) as local
+ * body ids, in pair order; the pair's colour in the last solve (-1: no contacts). */
+int or_get_pile_pairs(const or_world *w, int env, int *ab, int *color, int cap, int *n_out) {
+    if (env < 0 || env >= w->n_envs || !w->envs[env].pile) return -1;
+    const env_t *E = &w->envs[env];
+    for (int p = 0; p < E->ndp && p < cap; ++p) {
+        ab[2 * p] = E->dp[p].a - E->first_body;
+        ab[2 * p + 1] = E->dp[p].b - E->first_body;
+        if (color) color[p] = E->dp[p].color;
+    }
+    *n_out = E->ndp;
+    return E->ndp > cap ? -1 : 0;
 }
 
 int or_env_margins(const or_world *w, int env, double *len, double *dot) {
@@ -1426,14 +1544,48 @@ static void env_substep(or_world *w, int e, double hs, int n_iters) {
             v_axpy(hs * v_dot(b->axis, b->torque) / Iaa, b->axis, b->w);
         }
     }
-    /* 3. prep: rows from the contacts of every pair of the env, in pair order */
+    /* 3. prep: rows from the contacts of every pair of the env, in pair order -- in a pile
+       env, in colour order (R20): the pairs with contacts are coloured greedily in pair
+       order, each taking the lowest colour no earlier pair sharing one of its movable bodies
+       took (64 colours at most; the last one gathers every pair left over), and their rows
+       follow colour by colour, in pair order within a colour.  Pairs of one colour share no
+       movable body, so solving them in any order, or at once, gives these same updates. */
+    const int np_e = env_np(w, e);
+    pair_t *pairs_e = env_pairs(w, e);
+    const pair_contacts_t *pcs_e = env_pcs(w, e);
+    int *order = (int *)malloc(sizeof(int) * (np_e > 0 ? np_e : 1));
+    int n_order = 0;
+    if (E->pile) {
+        unsigned long long *used = (unsigned long long *)calloc(nb > 0 ? nb : 1, sizeof(unsigned long long));
+        int n_colors = 0;
+        for (int p = 0; p < np_e; ++p) {
+            pairs_e[p].color = -1;
+            if (pcs_e[p].n == 0) continue;
+            const int la = pairs_e[p].a - E->first_body, lb = pairs_e[p].b - E->first_body;
+            const int ma = movable(&bodies[la]), mb = movable(&bodies[lb]);
+            const unsigned long long taken = (ma ? used[la] : 0ull) | (mb ? used[lb] : 0ull);
+            int c = 0;
+            while (c < 63 && ((taken >> c) & 1ull)) ++c;
+            pairs_e[p].color = c;
+            if (ma) used[la] |= 1ull << c;
+            if (mb) used[lb] |= 1ull << c;
+            if (c + 1 > n_colors) n_colors = c + 1;
+        }
+        for (int c = 0; c < n_colors; ++c)
+            for (int p = 0; p < np_e; ++p)
+                if (pairs_e[p].color == c) order[n_order++] = p;
+        free(used);
+    } else {
+        for (int p = 0; p < np_e; ++p) order[n_order++] = p;
+    }
     int nr = 0;
-    for (int p = 0; p < E->n_pairs; ++p) nr += w->pc[E->first_pair + p].n;
+    for (int p = 0; p < np_e; ++p) nr += pcs_e[p].n;
     row_t *rows = (row_t *)calloc(nr > 0 ? nr : 1, sizeof(row_t));
     int r = 0;
-    for (int p = 0; p < E->n_pairs; ++p) {
-        const pair_t *P = &w->pairs[E->first_pair + p];
-        const pair_contacts_t *pc = &w->pc[E->first_pair + p];
+    for (int q = 0; q < n_order; ++q) {
+        const int p = order[q];
+        const pair_t *P = &pairs_e[p];
+        const pair_contacts_t *pc = &pcs_e[p];
         int la = P->a - E->first_body, lb = P->b - E->first_body;
         for (int i = 0; i < pc->n; ++i, ++r) {
             const or_contact *c = &pc->c[i];
@@ -1495,7 +1647,7 @@ static void env_substep(or_world *w, int e, double hs, int n_iters) {
     free(w->imp[e]);
     w->imp[e] = rec;
     w->imp_n[e] = nr;
-    free(rows); free(Iw); free(Iinv); free(com);
+    free(rows); free(Iw); free(Iinv); free(com); free(order);
 }
 
 int or_substep(or_world *w, double hs, int n_iters, int detect) {
@@ -1607,6 +1759,7 @@ static int diff_env_body(const or_world *w, int e) {
             dyn = E->first_body + i;
         }
     }
+    if (dyn >= 0 && E->pile) return -1;   /* piles are not differentiable */
     if (dyn >= 0)
         for (int p = 0; p < E->n_pairs; ++p)
             if (w->pairs[E->first_pair + p].a != dyn) return -1;

@@ -132,6 +132,7 @@ int or_asset_set_grid(or_world *w, int asset, const float lo[3], float h, const 
                       const float *values);
 int or_asset_get_grid(const or_world *w, int asset, float lo[3], float *h, int dims[3]);
 int or_asset_mass(const or_world *w, int asset, double *mass, double com[3], double inertia[9]);
+/* n_pairs < 0: pile envs (R20), whose pairs a broad phase finds at every detection. */
 int or_add_envs(or_world *w, int n_envs, const or_body_desc *bodies, int n_per_env,
                 const int *pairs, int n_pairs);
 int or_n_envs(const or_world *w);
@@ -162,6 +163,9 @@ int or_get_pair_contacts(const or_world *w, int env, int pair, or_contact *out, 
 int or_set_pair_contacts(or_world *w, int env, int pair, const or_contact *in, int n);
 /* Per-env minimum decision margins over everything since the last reset. */
 int or_env_margins(const or_world *w, int env, double *len, double *dot);
+/* A pile env's current pairs (R20; from its last detection): (point body, SDF body) as
+ * local body ids, in pair order, and each pair's colour in the last solve (-1: no contacts). */
+int or_get_pile_pairs(const or_world *w, int env, int *ab, int *color, int cap, int *n_out);
 void or_reset_margins(or_world *w);
 /* State arrays, n_bodies entries: pos 3, quat 4, linvel 3, angvel 3. */
 int or_get_state(const or_world *w, double *pos, double *quat, double *linvel, double *angvel);

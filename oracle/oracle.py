@@ -88,6 +88,7 @@ def lib():
             L.or_asset_get_grid.argtypes = [vp, C.c_int, _f32, C.POINTER(C.c_float), _i32]
             L.or_asset_mass.argtypes = [vp, C.c_int, C.POINTER(C.c_double), _f64, _f64]
             L.or_add_envs.argtypes = [vp, C.c_int, vp, C.c_int, _i32, C.c_int]
+            L.or_get_pile_pairs.argtypes = [vp, C.c_int, _i32, _i32, C.c_int, C.POINTER(C.c_int)]
             L.or_n_envs.argtypes = [vp]
             L.or_n_bodies.argtypes = [vp]
             L.or_step.argtypes = [vp, C.c_int, C.c_int]
@@ -292,12 +293,26 @@ class OracleWorld:
         lib().or_asset_mass(self.h, asset, C.byref(m), com, I)
         return m.value, com, I.reshape(3, 3)
 
-    def add_envs(self, bodies: np.ndarray, pairs: np.ndarray) -> int:
+    def add_envs(self, bodies: np.ndarray, pairs) -> int:
+        """pairs: (n, 2) local body ids, or None for pile envs (R20: pairs found by the
+        broad phase at every detection)."""
         bodies = np.ascontiguousarray(bodies)
         assert bodies.dtype.itemsize == 104
+        if pairs is None:
+            return lib().or_add_envs(self.h, bodies.shape[0], bodies.ctypes.data, bodies.shape[1],
+                                     np.zeros(1, np.int32), -1)
         pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1)
         return lib().or_add_envs(self.h, bodies.shape[0], bodies.ctypes.data, bodies.shape[1],
                                  pairs, len(pairs) // 2)
+
+    def pile_pairs(self, env: int):
+        """(pairs (n, 2) of local body ids (point body, SDF body), colours (n,)) of a pile
+        env's last detection / solve."""
+        cap = 1 << 16
+        ab, col, n = np.zeros(2 * cap, np.int32), np.zeros(cap, np.int32), C.c_int()
+        if lib().or_get_pile_pairs(self.h, env, ab, col, cap, C.byref(n)) != 0:
+            raise ValueError("not a pile env, or too many pairs")
+        return ab[: 2 * n.value].reshape(-1, 2).copy(), col[: n.value].copy()
 
     @property
     def n_envs(self) -> int:
@@ -465,4 +480,6 @@ def world_from_scene(scene, n_threads: int = 0, lazy_bake: bool = False, **over)
             w.bake(i, a.sdf_res, a.sdf_pad, True, lazy_bake)
     for g in scene.groups:
         w.add_envs(g.bodies, g.pairs)
+    for pb in scene.piles:
+        w.add_envs(pb[None, :], None)
     return w

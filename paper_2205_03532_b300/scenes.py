@@ -583,10 +583,13 @@ class Scene:
     assets: List[Asset]
     groups: List[EnvGroup]
     sim: SimParams
+    # pile envs: BODY_DTYPE (n_bodies,) each; their pairs are found at every detection.
+    # They follow the groups' envs in env order.
+    piles: List[np.ndarray] = dataclasses.field(default_factory=list)
 
     @property
     def n_envs(self) -> int:
-        return sum(g.bodies.shape[0] for g in self.groups)
+        return sum(g.bodies.shape[0] for g in self.groups) + len(self.piles)
 
 
 def _body(asset, btype, pos, quat, mu, mass=0.0, linvel=(0, 0, 0), angvel=(0, 0, 0),
@@ -866,3 +869,67 @@ def pile_scene(n_envs: int = 256, seed: int = 0, n_nuts: int = 7, mode: str = "d
     pairs = [(k, n_nuts) for k in range(n_nuts)] + [(i, j) for i in range(n_nuts) for j in range(i + 1, n_nuts)]
     sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, frames=frames)
     return Scene("pile", [nut, plate], [EnvGroup(bodies, np.array(pairs, np.int32))], sim)
+
+
+# --------------------------------------------------------------------------------------
+# one env of hundreds of nuts (pile env): the pairs are found at every detection
+# --------------------------------------------------------------------------------------
+def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_samples: int = 5000,
+                       sdf_res: int = 128, plate_sdf_res: int = 128, mu: float = 0.3, n_substeps: int = 4,
+                       n_iters: int = 16, n_vel_iters: int = 1, frames: int = 120, gap_mm: float = 2.0,
+                       layers: int = 4, sink_mm: float = 0.02, overlap_mm: float = 1.0) -> Scene:
+    """The paper's Nuts scene: n_nuts ISO M16 nuts (the nut of nut_bolt_scene: 18,136
+    triangles, n_samples samples, its own SDF) in ONE env over a static plate (SDF only, no
+    samples; top face z = 0), as a pile env whose pairs every detection finds again.
+
+    mode "drop": the nuts start in a square lattice of columns (`layers` deep, cells of the
+    nut's bounding diameter plus gap_mm, jittered by up to a quarter of the gap), at random
+    orientations, the lowest layer gap_mm above the plate, and fall into a pile.
+    mode "heap": resting stacks of one to three nuts lying flat (random yaw), each sunk
+    sink_mm into the one below or the plate; the stacks stand on a square grid whose pitch
+    is the nut's across-corners width less overlap_mm, so that neighbouring stacks touch
+    where hexagon corners meet: nut-plate, nut-on-nut and side contacts from the first
+    substep, and each nut pairs with up to eight neighbours."""
+    if not 1 <= n_nuts <= 1023:
+        raise ValueError("n_nuts must be 1..1023 (a pile env holds 1024 bodies with the plate)")
+    rng = np.random.default_rng(seed)
+    P, af, _ = ISO_COARSE[16]
+    thick = 13.0e-3
+    nV, nT = nut_mesh(16, P, 13.0, af, 0.05, n_ang=84)
+    nut = Asset("nut_m16", nV, nT, sample_surface(nV, nT, n_samples, rng), 7800.0, sdf_res=sdf_res, sdf_pad=1e-3)
+    r = float(np.linalg.norm(nV, axis=1).max())            # bounding sphere
+    rc = float(np.linalg.norm(nV[:, :2], axis=1).max())    # across-corners half width
+    bodies = np.zeros(n_nuts + 1, dtype=BODY_DTYPE)
+    if mode == "drop":
+        cell = 2 * r + gap_mm * 1e-3
+        m = max(1, int(math.ceil(math.sqrt(n_nuts / layers))))
+        for k in range(n_nuts):
+            lay, rem = divmod(k, m * m)
+            iy, ix = divmod(rem, m)
+            jit = rng.uniform(-0.25, 0.25, 2) * gap_mm * 1e-3
+            c = ((ix - (m - 1) / 2) * cell + jit[0], (iy - (m - 1) / 2) * cell + jit[1],
+                 r + gap_mm * 1e-3 + lay * cell)
+            bodies[k] = _body(0, DYNAMIC, c, _random_quat(rng), mu)
+        half = m * cell / 2 + 0.02
+    elif mode == "heap":
+        pitch = 2 * rc - overlap_mm * 1e-3
+        heights = []
+        while sum(heights) < n_nuts:
+            heights.append(int(rng.integers(1, min(3, n_nuts - sum(heights)) + 1)))
+        m = max(1, int(math.ceil(math.sqrt(len(heights)))))
+        k = 0
+        for si, hgt in enumerate(heights):
+            iy, ix = divmod(si, m)
+            cx, cy = (ix - (m - 1) / 2) * pitch, (iy - (m - 1) / 2) * pitch
+            for level in range(hgt):
+                z = thick / 2 + level * thick - (level + 1) * sink_mm * 1e-3
+                bodies[k] = _body(0, DYNAMIC, (cx, cy, z), quat_axis_angle([0, 0, 1], rng.uniform(0, np.pi / 3)), mu)
+                k += 1
+        half = m * pitch / 2 + 0.02
+    else:
+        raise ValueError(f"unknown pile mode {mode!r}")
+    PV, PT = box_mesh(half, half, 0.005)
+    plate = Asset("plate", PV, PT, None, 7800.0, sdf_res=plate_sdf_res, sdf_pad=1e-3)
+    bodies[n_nuts] = _body(1, STATIC, (0.0, 0.0, -0.005), (0, 0, 0, 1), mu)
+    sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, n_vel_iters=n_vel_iters, frames=frames)
+    return Scene("nut_pile_env", [nut, plate], [], sim, piles=[bodies])
