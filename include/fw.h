@@ -213,6 +213,38 @@ FW_API fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *
                                    int n_per_env, const int *pairs, int n_pairs,
                                    int *first_env_out);
 
+/* Adds one pile environment: n_bodies bodies (1..1024; host descriptors) in one scene, the
+ * scenes of the paper's experiments where 1024 nuts, bowls or toruses fall into a pile in
+ * one environment (Sec. III-D, scene list; Table "contact statistics", row Nuts).  Its pairs are
+ * not listed: every detection finds them again (pair finding, part of contact handling in
+ * that table) -- for local bodies i < j, at least one of them dynamic or fixed-axis, i's
+ * samples against j's SDF when i has samples and j an SDF, else j's samples against i's
+ * SDF when j has samples and i an SDF, and only when the bodies' bounding spheres (about
+ * their asset origins) are within the contact offset plus two voxels of the SDF body's
+ * grid (no sample can have a candidate farther apart); pairs in (i, j) order.  Each pair's
+ * contacts come from the same narrow phase and Algorithm 1 as a listed pair's.  The solve
+ * (Sec. III-B) colours the pairs that have contacts greedily in pair order (each takes the
+ * lowest of 64 colours that no earlier pair sharing one of its movable bodies took; the
+ * last colour gathers the rest) and sweeps colour by colour, pair order within a colour:
+ * the same updates as one Gauss-Seidel sweep over the rows in that order.
+ * max_pairs, max_contacts: capacities of the pile's pair list (at most 65535) and of its
+ * contact rows (below 2^21) (0: 8 pairs and 192 contacts per body); pairs or rows beyond
+ * them are dropped and the next synchronising call returns FW_ERR_OVERFLOW.  Piles need contact_gen = 0 and the
+ * Gauss-Seidel solver, and are not differentiable (fw_record_rollout refuses them).
+ * *env_out receives the env id.  Errors: FW_ERR_ARG for bad sizes or descriptors, or a pile
+ * too large for the solve's shared memory (73 n_bodies + 11 max_pairs bytes); FW_ERR_STATE
+ * when a movable body's asset has neither samples nor an SDF. */
+FW_API fw_status fw_add_pile(fw_world *w, const fw_body_desc *bodies, int n_bodies, int max_pairs,
+                             int max_contacts, int *env_out);
+
+/* A pile env's current pairs (those of its last detection): pairs n x 2 local body ids
+ * (sample body, SDF body) in pair order, and if colors != NULL each pair's colour in the
+ * last solve (-1: no contacts, or no solve since the detection).  Host arrays of cap
+ * entries; synchronises.  *n_out receives the pair count; FW_ERR_OVERFLOW when it is more
+ * than cap.  The `pair` index of fw_get_contacts / fw_set_contacts for a pile env is this
+ * pair order.  Errors: FW_ERR_ARG when env is not a pile env. */
+FW_API fw_status fw_get_pile_pairs(fw_world *w, int env, int *pairs, int *colors, int cap, int *n_out);
+
 /* ---------------------------------------------------------------- stepping */
 
 /* Advances every environment by one frame dt as n_substeps substeps of
@@ -243,7 +275,8 @@ FW_API fw_status fw_get_contacts(fw_world *w, int env, fw_contact *out, int cap,
 
 /* Replaces the contacts of one env (host array; `pair` selects the pair of each one;
  * the contacts of a pair must be contiguous and in sweep order).  For solving given
- * contacts with fw_substep(detect = 0). */
+ * contacts with fw_substep(detect = 0).  A pile env keeps the pairs of its last detection
+ * (fw_get_pile_pairs); `pair` indexes them. */
 FW_API fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int n);
 
 /* ---------------------------------------------------------------- state */
@@ -422,7 +455,8 @@ FW_API fw_status fw_get_counts(fw_world *w, int *n_envs, int *n_bodies, int *n_p
 /* Where one environment's bodies and pairs sit in the world's global order (the index of its
  * first body in fw_get_state's arrays, its body count, the index of its first pair in
  * fw_adjoint_rollout's d_mu and its pair count); any pointer may be NULL.  With several
- * fw_add_env_bodies calls of different structures, this is how a caller finds a body.
+ * fw_add_env_bodies calls of different structures, this is how a caller finds a body.  A
+ * pile env has no listed pairs: first_pair = n_pairs = -1 (its pairs: fw_get_pile_pairs).
  * Errors: FW_ERR_ARG for env outside 0..n_envs-1. */
 FW_API fw_status fw_get_env_info(fw_world *w, int env, int *first_body, int *n_bodies, int *first_pair,
                                  int *n_pairs);

@@ -41,14 +41,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     bdir = os.path.join(PKG, "_build")
     os.makedirs(bdir, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in SOURCES:
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-I", os.path.join(ROOT, "include"), "-c", os.path.join(HERE, src), "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
+        cmds.append([NVCC, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-I", os.path.join(ROOT, "include"), "-c",
+                     os.path.join(HERE, src), "-o", obj])
         objs.append(obj)
+    if verbose:
+        for cmd in cmds:
+            print(" ".join(cmd), file=sys.stderr)
+    # the translation units are independent: compile them at the same time
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+        for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
+            f.result()
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp, "-cudart", "shared",
                            "-Xlinker", "-rpath=/usr/local/cuda/lib64"])

@@ -74,6 +74,23 @@ struct fw_world {
     int n_sm = 0, max_dyn_smem[4] = {0, 0, 0, 0};
     int solve_groups = 0, solve_warps = 0;
     int lam_rows = 0;   // rows per env whose impulses the solve keeps in shared memory (0: every row)
+    // pile envs (fw_add_pile): one region per pile in each pile buffer, every region of the
+    // same size (pile_pcap pairs, pile_icap items, pile_rcap rows)
+    std::vector<PileDev> piles;
+    int n_regular = 0;           // envs of listed pairs
+    int pile_pcap = 0, pile_icap = 0, pile_rcap = 0, pile_stride = 0;
+    size_t pile_smem = 0;
+    PileDev *d_piles = nullptr;
+    PairDev *d_ppairs = nullptr;
+    int2 *d_pitems = nullptr, *d_pitem_range = nullptr, *d_pcounts = nullptr;
+    DContact *d_pcontacts = nullptr;
+    int *d_pccounts = nullptr;   // contacts per pile pair
+    float4 *d_pscratch = nullptr, *d_pcand = nullptr;
+    int *d_pcand_count = nullptr;
+    PairMap *d_pmaps = nullptr;
+    Row *d_prows = nullptr;
+    PileSolveMem pmem = {nullptr};
+    int pile_optin = 0;
     // differentiable rollout (fw_record_rollout .. fw_adjoint_rollout)
     DiffState diff;
     bool diff_valid = false;
@@ -240,6 +257,79 @@ long long pair_sources(const fw_world *w, int asset_a) {
     return (long long)(w->cfg.contact_gen == 1 ? A.T.size() / 3 : A.S.size() / 3);
 }
 
+// pairs a pile found in its last detection (synchronises)
+fw_status pile_pair_count(fw_world *w, int pile, int *n) {
+    int2 c = make_int2(0, 0);
+    CK(cudaMemcpyAsync(&c, w->d_pcounts + pile, sizeof c, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    *n = c.x;
+    return FW_OK;
+}
+
+void pile_free(fw_world *w) {
+    dfree(w->d_piles); dfree(w->d_ppairs); dfree(w->d_pitems); dfree(w->d_pitem_range); dfree(w->d_pcounts);
+    dfree(w->d_pcontacts); dfree(w->d_pccounts); dfree(w->d_pscratch); dfree(w->d_pcand); dfree(w->d_pcand_count);
+    dfree(w->d_pmaps); dfree(w->d_prows);
+    dfree(w->pmem.color);
+}
+
+// The pile buffers: every pile gets regions of the same size, from the largest pile's
+// capacities (pairs, rows) and the largest sample count among the piles' bodies (the
+// per-pair winner scratch and the Generate batches per pair).
+fw_status pile_alloc(fw_world *w) {
+    pile_free(w);
+    const int n = (int)w->piles.size();
+    if (n == 0) return FW_OK;
+    int pcap = 1, rcap = 1, nb_max = 1;
+    long long ns_max = 1;
+    for (const PileDev &P : w->piles) {
+        pcap = std::max(pcap, P.pcap);
+        rcap = std::max(rcap, P.rcap);
+        nb_max = std::max(nb_max, P.n_bodies);
+        for (int i = 0; i < P.n_bodies; ++i)
+            ns_max = std::max(ns_max, (long long)w->assets[w->props[P.first_body + i].asset].S.size() / 3);
+    }
+    const long long icap = (long long)pcap * ((ns_max + kBatch - 1) / kBatch);
+    if (icap * n > 0x7FFFFFFFLL || 2 * ns_max * pcap * n > 0x7FFFFFFFLL || (long long)rcap * n > 0x7FFFFFFFLL)
+        return fail(w, FW_ERR_ARG, "pile buffers: too many pairs, samples or rows");
+    if (pile_smem_bytes(nb_max, pcap) > (size_t)w->pile_optin)
+        return fail(w, FW_ERR_ARG, "pile buffers: the piles do not fit the solve's shared memory together");
+    w->pile_pcap = pcap;
+    w->pile_rcap = rcap;
+    w->pile_icap = (int)icap;
+    w->pile_stride = (int)(2 * ns_max);
+    w->pile_smem = pile_smem_bytes(nb_max, pcap);
+    std::vector<PileDev> dev = w->piles;
+    for (int k = 0; k < n; ++k) {
+        PileDev &P = dev[k];
+        P.pair0 = k * pcap; P.pcap = pcap;
+        P.item0 = k * w->pile_icap; P.icap = w->pile_icap;
+        P.row0 = k * rcap; P.rcap = rcap;
+        P.stride = w->pile_stride;
+    }
+    const size_t np = (size_t)n * pcap, ni = (size_t)n * w->pile_icap;
+    CK(cudaMalloc(&w->d_piles, sizeof(PileDev) * n));
+    CK(cudaMemcpy(w->d_piles, dev.data(), sizeof(PileDev) * n, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&w->d_ppairs, sizeof(PairDev) * np));
+    CK(cudaMalloc(&w->d_pmaps, sizeof(PairMap) * np));
+    CK(cudaMalloc(&w->d_pitem_range, sizeof(int2) * np));
+    CK(cudaMalloc(&w->d_pccounts, sizeof(int) * np));
+    CK(cudaMalloc(&w->d_pcontacts, sizeof(DContact) * np * cap_pair(w)));
+    CK(cudaMalloc(&w->d_pscratch, sizeof(float4) * np * w->pile_stride));
+    CK(cudaMalloc(&w->d_pitems, sizeof(int2) * ni));
+    CK(cudaMalloc(&w->d_pcand, sizeof(float4) * 2 * (size_t)kBatch * ni));
+    CK(cudaMalloc(&w->d_pcand_count, sizeof(int) * ni));
+    CK(cudaMalloc(&w->d_pcounts, sizeof(int2) * n));
+    CK(cudaMalloc(&w->d_prows, sizeof(Row) * (size_t)n * rcap));
+    CK(cudaMalloc(&w->pmem.color, np));
+    // no pairs and no contacts until the first detection
+    CK(cudaMemsetAsync(w->d_pcounts, 0, sizeof(int2) * n, w->stream));
+    CK(cudaMemsetAsync(w->d_pccounts, 0, sizeof(int) * np, w->stream));
+    CK(cudaMemsetAsync(w->d_pcand_count, 0, sizeof(int) * ni, w->stream));
+    CK(cudaMemsetAsync(w->pmem.color, 0xFF, np, w->stream));
+    return FW_OK;
+}
+
 // (Re)builds the device copies of the topology, keeping the device state of bodies that
 // are already there.
 fw_status ensure_device(fw_world *w) {
@@ -304,13 +394,19 @@ fw_status ensure_device(fw_world *w) {
         }
     }
     if (ne > 0) {
+        // the per-env kernels see a pile env as one without bodies (the pile kernels own it)
+        std::vector<EnvDev> dev = w->envs;
+        for (EnvDev &E : dev)
+            if (E.pile >= 0) { E.n_bodies = 0; E.n_pairs = 0; E.row_cap = 0; E.movable = -1; }
         CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
-        CK(cudaMemcpy(w->d_envs, w->envs.data(), sizeof(EnvDev) * ne, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w->d_envs, dev.data(), sizeof(EnvDev) * ne, cudaMemcpyHostToDevice));
         long long rl = 0;
         for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + E.row_cap + kRowPad);
         w->rows_len = std::max(rl, 1LL);
         CK(cudaMalloc(&w->d_rows, sizeof(Row) * w->rows_len));
     }
+    st = pile_alloc(w);
+    if (st != FW_OK) return st;
     w->dev_bodies = nb;
     w->topo_dirty = false;
     drop_graph(w);
@@ -366,6 +462,38 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     return p;
 }
 
+// The parameters of the pile launches: the pile buffers in place of the listed pairs'.
+SimParams pile_params(const fw_world *w, float hs, int n_iters) {
+    SimParams p = sim_params(w, hs, n_iters);
+    const int n = (int)w->piles.size();
+    p.pairs = w->d_ppairs;
+    p.maps = w->d_pmaps;
+    p.items = w->d_pitems;
+    p.pair_item0 = nullptr;
+    p.n_items = n * w->pile_icap;
+    p.n_pairs = n * w->pile_pcap;
+    p.cand = w->d_pcand;
+    p.cand_count = w->d_pcand_count;
+    p.contacts = w->d_pcontacts;
+    p.counts = w->d_pccounts;
+    p.scratch = w->d_pscratch;
+    p.rows = w->d_prows;
+    p.pile_counts = w->d_pcounts;
+    p.item_range = w->d_pitem_range;
+    p.pile_pcap = w->pile_pcap;
+    p.pile_icap = w->pile_icap;
+    p.broad_phase = 0;   // the pile's pair list already holds only pairs within reach
+    return p;
+}
+
+// detection of every pile: pair list, maps, narrow phase, Algorithm 1
+fw_status enqueue_pile_detect(fw_world *w, const SimParams &q, cudaStream_t s) {
+    const int n = (int)w->piles.size();
+    CK(launch_pile_pairs(q, w->d_piles, n, w->d_ppairs, w->d_pitems, w->d_pitem_range, w->d_pcounts, s));
+    CK(launch_query(q, s));
+    return FW_OK;
+}
+
 SolveShape current_solve_shape(const fw_world *w, const SimParams &p) {
     return solve_shape(p.n_envs, p.lam_cap, w->solve_groups, w->solve_warps, w->max_dyn_smem, w->n_sm);
 }
@@ -376,7 +504,7 @@ fw_status check_status(fw_world *w) {
     if (st) {
         CK(cudaMemsetAsync(w->d_status, 0, sizeof st, w->stream));
         if (st & kStatusNonFinite) return fail(w, FW_ERR_NONFINITE, "a body state became non-finite");
-        if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts than fit");
+        if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts, or a pile more pairs or contact rows, than fit");
         if (st & kStatusBounds) return fail(w, FW_ERR_DEVICE_BOUNDS, "device index check failed");
         if (st & kStatusTimeout) return fail(w, FW_ERR_TIMEOUT, "a bounded device wait gave up");
     }
@@ -399,13 +527,22 @@ fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs
                            bool timed) {
     SimParams p = sim_params(w, hs, n_iters);
     const SolveShape sh = current_solve_shape(w, p);
+    const bool regular = w->n_regular > 0, piles = !w->piles.empty();
+    const SimParams q = piles ? pile_params(w, hs, n_iters) : p;
+    const int np = (int)w->piles.size();
     for (int k = 0; k < n_substeps; ++k) {
         if (timed) CK(cudaEventRecord(take_event(w), s));
-        if (detect) CK(launch_query(p, s));
+        if (detect && regular) CK(launch_query(p, s));
+        if (detect && piles) {
+            const fw_status st = enqueue_pile_detect(w, q, s);
+            if (st != FW_OK) return st;
+        }
         if (timed) CK(cudaEventRecord(take_event(w), s));
-        if (detect) CK(launch_reduce(p, s));
+        if (detect && regular) CK(launch_reduce(p, s));
+        if (detect && piles) CK(launch_reduce(q, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
-        CK(launch_solve(p, sh, s));
+        if (regular) CK(launch_solve(p, sh, s));
+        if (piles) CK(launch_pile_solve(q, w->d_piles, np, w->d_pcounts, w->pmem, w->d_prows, w->pile_smem, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
     }
     return FW_OK;
@@ -425,6 +562,7 @@ void diff_free(fw_world *w) {
 // Checks that every env is differentiable (at most one dynamic body, the point body a of
 // each of its pairs; no fixed-axis bodies) and returns each env's dynamic body.
 fw_status diff_envs(fw_world *w, std::vector<int> &dyn) {
+    if (!w->piles.empty()) return fail(w, FW_ERR_ARG, "differentiable rollout: pile envs are not supported");
     dyn.assign(w->envs.size(), -1);
     for (size_t e = 0; e < w->envs.size(); ++e) {
         const EnvDev &E = w->envs[e];
@@ -482,6 +620,57 @@ fw_status diff_alloc(fw_world *w, int S, int K) {
     return FW_OK;
 }
 
+// A body's constant properties from its descriptor (mass scaled from the asset's when the
+// descriptor gives one); false when its inertia is singular.
+bool body_props(const fw_world *w, const fw_body_desc &d, BodyProps &P) {
+    const AssetHost &A = w->assets[d.asset];
+    memset(&P, 0, sizeof P);
+    P.type = d.type;
+    P.asset = d.asset;
+    double scale = 1.0, mass = A.mass;
+    if (d.mass > 0.0f) { scale = (double)d.mass / A.mass; mass = d.mass; }
+    double Ib[9], Ii[9];
+    for (int k = 0; k < 9; ++k) Ib[k] = A.I[k] * scale;
+    if (!inv3(Ib, Ii)) return false;
+    P.mass = (float)mass;
+    P.invm = d.type == FW_BODY_DYNAMIC ? (float)(1.0 / mass) : 0.0f;
+    for (int a = 0; a < 3; ++a) P.com_b[a] = (float)A.com[a];
+    const int sym[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int k = 0; k < 6; ++k) {
+        P.Ib[k] = (float)Ib[3 * sym[k][0] + sym[k][1]];
+        P.Ib_inv[k] = (float)Ii[3 * sym[k][0] + sym[k][1]];
+    }
+    const double an = std::sqrt((double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] +
+                                (double)d.axis[2] * d.axis[2]);
+    for (int a = 0; a < 3; ++a) {
+        P.axis[a] = an > 0 ? (float)(d.axis[a] / an) : 0.0f;
+        P.force[a] = d.force[a];
+        P.torque[a] = d.torque[a];
+    }
+    P.mu = d.mu;
+    return true;
+}
+
+// Appends one validated body: its properties and its initial state (unit quaternion; a
+// static body at rest; a fixed-axis body without linear velocity, spinning about its axis).
+void append_body(fw_world *w, const fw_body_desc &d) {
+    BodyProps P;
+    body_props(w, d, P);
+    w->props.push_back(P);
+    const double qn = std::sqrt((double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] +
+                                (double)d.quat[2] * d.quat[2] + (double)d.quat[3] * d.quat[3]);
+    for (int a = 0; a < 3; ++a) w->h_pos.push_back(d.pos[a]);
+    for (int a = 0; a < 4; ++a) w->h_quat.push_back((float)(d.quat[a] / qn));
+    float v[3] = {d.linvel[0], d.linvel[1], d.linvel[2]}, om[3] = {d.angvel[0], d.angvel[1], d.angvel[2]};
+    if (d.type == FW_BODY_STATIC) { v[0] = v[1] = v[2] = 0; om[0] = om[1] = om[2] = 0; }
+    if (d.type == FW_BODY_FIXED_AXIS) {
+        const float s = om[0] * P.axis[0] + om[1] * P.axis[1] + om[2] * P.axis[2];
+        v[0] = v[1] = v[2] = 0;
+        for (int a = 0; a < 3; ++a) om[a] = s * P.axis[a];
+    }
+    for (int a = 0; a < 3; ++a) { w->h_vel.push_back(v[a]); w->h_ang.push_back(om[a]); }
+}
+
 }  // namespace
 
 // ===================================================================================== ABI
@@ -533,6 +722,7 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
     if (e == cudaSuccess) e = prepare_solve(optin, w->max_dyn_smem);
+    if (e == cudaSuccess) e = prepare_pile_solve(optin, &w->pile_optin);
     if (e == cudaSuccess && w->max_dyn_smem[0] < (int)solve_smem_bytes(kLamCapMax)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -558,6 +748,7 @@ fw_status fw_destroy(fw_world *w) {
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
     dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count); dfree(w->d_maps);
+    pile_free(w);
     for (auto e : w->ev_pool) cudaEventDestroy(e);
     for (auto e : w->ev_used) cudaEventDestroy(e);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
@@ -875,11 +1066,29 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
         const double an = (double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] + (double)d.axis[2] * d.axis[2];
         if (!(qn > 0)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: zero quaternion");
         if (d.type == FW_BODY_FIXED_AXIS && !(an > 0)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: zero axis");
+        BodyProps P;
+        if (!body_props(w, d, P)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: singular inertia");
     }
+    if (w->cfg.solver == 1)
+        for (int e = 0; e < n_envs; ++e) {
+            int movable = 0;
+            for (int i = 0; i < n_per_env; ++i) {
+                const int t = bd[e * n_per_env + i].type;
+                movable += (t == FW_BODY_DYNAMIC || t == FW_BODY_FIXED_AXIS) ? 1 : 0;
+            }
+            if (movable > 1)
+                return fail(w, FW_ERR_ARG, "fw_add_env_bodies: the Jacobi solver takes envs with one movable body");
+        }
     const int e0 = (int)w->envs.size();
     long long scratch = 0, rows = 0;
     for (auto &P : w->pairs) scratch = std::max(scratch, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
     for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap + kRowPad);
+    long long more = 0;
+    for (int e = 0; e < n_envs; ++e)
+        for (int k = 0; k < n_pairs; ++k) more += 2LL * pair_sources(w, bd[e * n_per_env + pairs[2 * k]].asset);
+    if (scratch + more > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many samples in total");
+    if (rows + (long long)n_envs * (n_pairs * cap_pair(w) + kRowPad) > 0x7FFFFFFFLL)
+        return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many contact rows in total");
     for (int e = 0; e < n_envs; ++e) {
         EnvDev E;
         memset(&E, 0, sizeof E);
@@ -889,56 +1098,14 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
         E.n_pairs = n_pairs;
         E.row_off = (int)rows;
         E.row_cap = n_pairs * cap_pair(w);
+        E.pile = -1;
         rows += E.row_cap + kRowPad;
-        for (int i = 0; i < n_per_env; ++i) {
-            const fw_body_desc &d = bd[e * n_per_env + i];
-            const AssetHost &A = w->assets[d.asset];
-            BodyProps P;
-            memset(&P, 0, sizeof P);
-            P.type = d.type;
-            P.asset = d.asset;
-            double scale = 1.0, mass = A.mass;
-            if (d.mass > 0.0f) { scale = (double)d.mass / A.mass; mass = d.mass; }
-            double Ib[9], Ii[9];
-            for (int k = 0; k < 9; ++k) Ib[k] = A.I[k] * scale;
-            if (!inv3(Ib, Ii)) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: singular inertia");
-            P.mass = (float)mass;
-            P.invm = d.type == FW_BODY_DYNAMIC ? (float)(1.0 / mass) : 0.0f;
-            for (int a = 0; a < 3; ++a) P.com_b[a] = (float)A.com[a];
-            const int sym[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-            for (int k = 0; k < 6; ++k) {
-                P.Ib[k] = (float)Ib[3 * sym[k][0] + sym[k][1]];
-                P.Ib_inv[k] = (float)Ii[3 * sym[k][0] + sym[k][1]];
-            }
-            const double an = std::sqrt((double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] +
-                                        (double)d.axis[2] * d.axis[2]);
-            for (int a = 0; a < 3; ++a) {
-                P.axis[a] = an > 0 ? (float)(d.axis[a] / an) : 0.0f;
-                P.force[a] = d.force[a];
-                P.torque[a] = d.torque[a];
-            }
-            P.mu = d.mu;
-            w->props.push_back(P);
-            const double qn = std::sqrt((double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] +
-                                        (double)d.quat[2] * d.quat[2] + (double)d.quat[3] * d.quat[3]);
-            for (int a = 0; a < 3; ++a) w->h_pos.push_back(d.pos[a]);
-            for (int a = 0; a < 4; ++a) w->h_quat.push_back((float)(d.quat[a] / qn));
-            float v[3] = {d.linvel[0], d.linvel[1], d.linvel[2]}, om[3] = {d.angvel[0], d.angvel[1], d.angvel[2]};
-            if (d.type == FW_BODY_STATIC) { v[0] = v[1] = v[2] = 0; om[0] = om[1] = om[2] = 0; }
-            if (d.type == FW_BODY_FIXED_AXIS) {
-                const float s = om[0] * P.axis[0] + om[1] * P.axis[1] + om[2] * P.axis[2];
-                v[0] = v[1] = v[2] = 0;
-                for (int a = 0; a < 3; ++a) om[a] = s * P.axis[a];
-            }
-            for (int a = 0; a < 3; ++a) { w->h_vel.push_back(v[a]); w->h_ang.push_back(om[a]); }
-        }
+        for (int i = 0; i < n_per_env; ++i) append_body(w, bd[e * n_per_env + i]);
         E.movable = -1;
         for (int i = 0; i < n_per_env; ++i) {
             const int t = bd[e * n_per_env + i].type;
             if (t == FW_BODY_DYNAMIC || t == FW_BODY_FIXED_AXIS) E.movable = (E.movable == -1) ? i : -2;
         }
-        if (E.movable == -2 && w->cfg.solver == 1)
-            return fail(w, FW_ERR_ARG, "fw_add_env_bodies: the Jacobi solver takes envs with one movable body");
         for (int k = 0; k < n_pairs; ++k) {
             PairDev P;
             memset(&P, 0, sizeof P);
@@ -952,13 +1119,63 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
             P.mu = (float)std::sqrt((double)w->props[P.a].mu * (double)w->props[P.b].mu);
             P.scratch_off = (int)scratch;
             scratch += 2LL * pair_sources(w, P.asset_a);
-            if (scratch > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many samples in total");
             w->pairs.push_back(P);
         }
         w->envs.push_back(E);
+        ++w->n_regular;
     }
     w->topo_dirty = true;
     if (first_env_out) *first_env_out = e0;
+    return FW_OK;
+}
+
+fw_status fw_add_pile(fw_world *w, const fw_body_desc *bd, int n_bodies, int max_pairs, int max_contacts,
+                      int *env_out) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (!bd || n_bodies < 1 || n_bodies > kMaxPileBodies || max_pairs < 0 || max_contacts < 0)
+        return fail(w, FW_ERR_ARG, "fw_add_pile: bad sizes (1..1024 bodies, capacities >= 0)");
+    if (w->cfg.contact_gen != 0 || w->cfg.solver != 0)
+        return fail(w, FW_ERR_ARG, "fw_add_pile: piles take per-sample contacts and the Gauss-Seidel solver");
+    const long long pcap = max_pairs > 0 ? max_pairs : (long long)kPilePairsPerBody * n_bodies;
+    const long long rcap = max_contacts > 0 ? max_contacts : (long long)kPileRowsPerBody * n_bodies;
+    if (pcap > kPileMaxPairs || rcap >= kPileMaxRows)
+        return fail(w, FW_ERR_ARG, "fw_add_pile: capacities too large (65535 pairs, 2^21 - 1 contact rows)");
+    if (pile_smem_bytes(n_bodies, (int)pcap) > (size_t)w->pile_optin)
+        return fail(w, FW_ERR_ARG, "fw_add_pile: the pile does not fit the solve's shared memory");
+    for (int i = 0; i < n_bodies; ++i) {
+        const fw_body_desc &d = bd[i];
+        if (d.asset < 0 || d.asset >= (int)w->assets.size() || d.type < 0 || d.type > 3)
+            return fail(w, FW_ERR_ARG, "fw_add_pile: bad body descriptor");
+        const double qn = (double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] +
+                          (double)d.quat[2] * d.quat[2] + (double)d.quat[3] * d.quat[3];
+        const double an = (double)d.axis[0] * d.axis[0] + (double)d.axis[1] * d.axis[1] + (double)d.axis[2] * d.axis[2];
+        if (!(qn > 0)) return fail(w, FW_ERR_ARG, "fw_add_pile: zero quaternion");
+        if (d.type == FW_BODY_FIXED_AXIS && !(an > 0)) return fail(w, FW_ERR_ARG, "fw_add_pile: zero axis");
+        BodyProps P;
+        if (!body_props(w, d, P)) return fail(w, FW_ERR_ARG, "fw_add_pile: singular inertia");
+        // a body takes part in pairs through its samples and / or its SDF, whichever it has
+        if (d.type != FW_BODY_STATIC && d.type != FW_BODY_KINEMATIC && w->assets[d.asset].S.empty() &&
+            !w->assets[d.asset].has_sdf)
+            return fail(w, FW_ERR_STATE, "fw_add_pile: a movable body has neither samples nor an SDF");
+    }
+    EnvDev E;
+    memset(&E, 0, sizeof E);
+    E.first_body = (int)w->props.size();
+    E.n_bodies = n_bodies;
+    E.movable = -1;
+    E.pile = (int)w->piles.size();
+    PileDev P;
+    memset(&P, 0, sizeof P);
+    P.env = (int)w->envs.size();
+    P.first_body = E.first_body;
+    P.n_bodies = n_bodies;
+    P.pcap = (int)pcap;
+    P.rcap = (int)rcap;
+    for (int i = 0; i < n_bodies; ++i) append_body(w, bd[i]);
+    w->piles.push_back(P);
+    w->envs.push_back(E);
+    w->topo_dirty = true;
+    if (env_out) *env_out = P.env;
     return FW_OK;
 }
 
@@ -1000,7 +1217,13 @@ fw_status fw_collide(fw_world *w) {
     fw_status st = ensure_device(w);
     if (st != FW_OK) return st;
     const SimParams p = sim_params(w, w->cfg.dt, 0);
-    CK(launch_detect(p, w->stream));
+    if (w->n_regular > 0) CK(launch_detect(p, w->stream));
+    if (!w->piles.empty()) {
+        const SimParams q = pile_params(w, w->cfg.dt, 0);
+        st = enqueue_pile_detect(w, q, w->stream);
+        if (st != FW_OK) return st;
+        CK(launch_reduce(q, w->stream));
+    }
     return FW_OK;
 }
 
@@ -1012,15 +1235,24 @@ fw_status fw_get_contacts(fw_world *w, int env, fw_contact *out, int cap, int *n
     if (st != FW_OK) return st;
     const EnvDev &E = w->envs[env];
     const int cp = cap_pair(w);
-    std::vector<int> counts(E.n_pairs);
-    CK(cudaMemcpyAsync(counts.data(), w->d_counts + E.first_pair, sizeof(int) * E.n_pairs, cudaMemcpyDeviceToHost,
-                       w->stream));
-    std::vector<DContact> dc((size_t)E.n_pairs * cp);
-    CK(cudaMemcpyAsync(dc.data(), w->d_contacts + (size_t)E.first_pair * cp, sizeof(DContact) * dc.size(),
-                       cudaMemcpyDeviceToHost, w->stream));
+    // the env's pairs: its listed pairs, or its pile's current pairs
+    int n_pairs = E.n_pairs;
+    const int *d_counts = w->d_counts + E.first_pair;
+    const DContact *d_con = w->d_contacts + (size_t)E.first_pair * cp;
+    if (E.pile >= 0) {
+        if ((st = pile_pair_count(w, E.pile, &n_pairs)) != FW_OK) return st;
+        d_counts = w->d_pccounts + (size_t)E.pile * w->pile_pcap;
+        d_con = w->d_pcontacts + (size_t)E.pile * w->pile_pcap * cp;
+    }
+    std::vector<int> counts(n_pairs);
+    if (n_pairs > 0)
+        CK(cudaMemcpyAsync(counts.data(), d_counts, sizeof(int) * n_pairs, cudaMemcpyDeviceToHost, w->stream));
+    std::vector<DContact> dc((size_t)n_pairs * cp);
+    if (n_pairs > 0)
+        CK(cudaMemcpyAsync(dc.data(), d_con, sizeof(DContact) * dc.size(), cudaMemcpyDeviceToHost, w->stream));
     CK(cudaStreamSynchronize(w->stream));
     int n = 0;
-    for (int k = 0; k < E.n_pairs; ++k)
+    for (int k = 0; k < n_pairs; ++k)
         for (int i = 0; i < std::min(counts[k], cp); ++i, ++n) {
             if (n >= cap) continue;
             const DContact &c = dc[(size_t)k * cp + i];
@@ -1049,12 +1281,20 @@ fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int n) {
     if (st != FW_OK) return st;
     const EnvDev &E = w->envs[env];
     const int cp = cap_pair(w);
-    std::vector<int> counts(E.n_pairs, 0);
-    std::vector<DContact> dc((size_t)E.n_pairs * cp);
+    int n_pairs = E.n_pairs;
+    int *d_counts = w->d_counts + E.first_pair;
+    DContact *d_con = w->d_contacts + (size_t)E.first_pair * cp;
+    if (E.pile >= 0) {   // the pile's pairs of its last detection keep their order
+        if ((st = pile_pair_count(w, E.pile, &n_pairs)) != FW_OK) return st;
+        d_counts = w->d_pccounts + (size_t)E.pile * w->pile_pcap;
+        d_con = w->d_pcontacts + (size_t)E.pile * w->pile_pcap * cp;
+    }
+    std::vector<int> counts(n_pairs, 0);
+    std::vector<DContact> dc((size_t)n_pairs * cp);
     int last_pair = 0;
     for (int i = 0; i < n; ++i) {
         const int k = in[i].pair;
-        if (k < 0 || k >= E.n_pairs || k < last_pair)
+        if (k < 0 || k >= n_pairs || k < last_pair)
             return fail(w, FW_ERR_ARG, "fw_set_contacts: pairs must be grouped in order");
         last_pair = k;
         if (counts[k] >= cp) return fail(w, FW_ERR_OVERFLOW, "fw_set_contacts: too many contacts for a pair");
@@ -1063,10 +1303,10 @@ fw_status fw_set_contacts(fw_world *w, int env, const fw_contact *in, int n) {
         c.phi = in[i].phi;
         c.sample_patch = (in[i].sample & 0xFFFFFF) | ((in[i].patch & 0xFF) << 24);
     }
-    CK(cudaMemcpyAsync(w->d_counts + E.first_pair, counts.data(), sizeof(int) * E.n_pairs, cudaMemcpyHostToDevice,
-                       w->stream));
-    CK(cudaMemcpyAsync(w->d_contacts + (size_t)E.first_pair * cp, dc.data(), sizeof(DContact) * dc.size(),
-                       cudaMemcpyHostToDevice, w->stream));
+    if (n_pairs > 0) {
+        CK(cudaMemcpyAsync(d_counts, counts.data(), sizeof(int) * n_pairs, cudaMemcpyHostToDevice, w->stream));
+        CK(cudaMemcpyAsync(d_con, dc.data(), sizeof(DContact) * dc.size(), cudaMemcpyHostToDevice, w->stream));
+    }
     CK(cudaStreamSynchronize(w->stream));
     return FW_OK;
 }
@@ -1297,7 +1537,7 @@ fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials
     fw_status st = ensure_device(w);
     if (st != FW_OK) return st;
     const int nb = (int)w->props.size();
-    if (nb == 0 || w->envs.empty()) return FW_OK;
+    if (nb == 0 || w->n_regular == 0) return FW_OK;   // the shape is that of the per-env solve
     // the state is saved and put back around every candidate, so tuning does not advance it
     float *save = nullptr;
     CK(cudaMalloc(&save, sizeof(float) * 13 * nb));
@@ -1556,6 +1796,17 @@ fw_status fw_get_detect_stats(fw_world *w, long long *n_candidates, long long *n
         CK(cudaMemcpy(c.data(), w->d_counts, sizeof(int) * np, cudaMemcpyDeviceToHost));
         for (int v : c) nk += v;
     }
+    for (size_t k = 0; k < w->piles.size(); ++k) {   // each pile: its items and pairs in use
+        int2 c;
+        CK(cudaMemcpy(&c, w->d_pcounts + k, sizeof c, cudaMemcpyDeviceToHost));
+        std::vector<int> ci(c.y), cp(c.x);
+        if (c.y > 0)
+            CK(cudaMemcpy(ci.data(), w->d_pcand_count + k * w->pile_icap, sizeof(int) * c.y, cudaMemcpyDeviceToHost));
+        if (c.x > 0)
+            CK(cudaMemcpy(cp.data(), w->d_pccounts + k * w->pile_pcap, sizeof(int) * c.x, cudaMemcpyDeviceToHost));
+        for (int v : ci) nc += v;
+        for (int v : cp) nk += v;
+    }
     if (n_candidates) *n_candidates = nc;
     if (n_contacts) *n_contacts = nk;
     return FW_OK;
@@ -1575,15 +1826,44 @@ fw_status fw_get_env_info(fw_world *w, int env, int *first_body, int *n_bodies, 
     const EnvDev &E = w->envs[env];
     if (first_body) *first_body = E.first_body;
     if (n_bodies) *n_bodies = E.n_bodies;
-    if (first_pair) *first_pair = E.first_pair;
-    if (n_pairs) *n_pairs = E.n_pairs;
+    if (first_pair) *first_pair = E.pile >= 0 ? -1 : E.first_pair;
+    if (n_pairs) *n_pairs = E.pile >= 0 ? -1 : E.n_pairs;
     return FW_OK;
+}
+
+fw_status fw_get_pile_pairs(fw_world *w, int env, int *pairs, int *colors, int cap, int *n_out) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (env < 0 || env >= (int)w->envs.size() || w->envs[env].pile < 0 || cap < 0 || (cap > 0 && !pairs) || !n_out)
+        return fail(w, FW_ERR_ARG, "fw_get_pile_pairs: bad argument (env must be a pile env)");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    const int k = w->envs[env].pile;
+    int n = 0;
+    if ((st = pile_pair_count(w, k, &n)) != FW_OK) return st;
+    *n_out = n;
+    const int m = std::min(n, cap);
+    if (m > 0) {
+        std::vector<PairDev> P(m);
+        std::vector<unsigned char> c(m);
+        CK(cudaMemcpy(P.data(), w->d_ppairs + (size_t)k * w->pile_pcap, sizeof(PairDev) * m, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(c.data(), w->pmem.color + (size_t)k * w->pile_pcap, m, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < m; ++q) {
+            pairs[2 * q] = P[q].local_a;
+            pairs[2 * q + 1] = P[q].local_b;
+            if (colors) colors[q] = c[q] == 255 ? -1 : (int)c[q];
+        }
+    }
+    st = check_status(w);
+    if (st != FW_OK) return st;
+    return n > cap ? fail(w, FW_ERR_OVERFLOW, "fw_get_pile_pairs: cap too small") : FW_OK;
 }
 
 int fw_launches_per_step(fw_world *w, int n_substeps) {
     if (!w || n_substeps < 1) return 0;
-    // per substep: the pairs' maps (per-sample generation only), query, reduction, solve
-    return (w->cfg.contact_gen == 0 ? 4 : 3) * n_substeps;
+    // per substep: envs of listed pairs -- the pairs' maps (per-sample generation only),
+    // query, reduction, solve; piles -- pair list, maps, query, reduction, pile solve
+    const int regular = w->n_regular > 0 ? (w->cfg.contact_gen == 0 ? 4 : 3) : 0;
+    return (regular + (w->piles.empty() ? 0 : 5)) * n_substeps;
 }
 
 const char *fw_last_error(const fw_world *w) {

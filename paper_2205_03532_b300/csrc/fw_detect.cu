@@ -165,6 +165,7 @@ __device__ __noinline__ void pair_map(const SimParams &p, const PairDev &P, cons
 __global__ void map_kernel(SimParams p) {
     const int pi = blockIdx.x * blockDim.x + threadIdx.x;
     if (pi >= p.n_pairs) return;
+    if (p.pile_counts && pi % p.pile_pcap >= p.pile_counts[pi / p.pile_pcap].x) return;
     const PairDev P = p.pairs[pi];
     PairMap M;
     pair_map(p, P, p.assets[P.asset_b], M);
@@ -780,6 +781,8 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 template <bool kTri, int kStore>
 __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     const int item = blockIdx.x;
+    // pile launches cover every pile's item region; items past a pile's count do nothing
+    if (p.pile_counts && item % p.pile_icap >= p.pile_counts[item / p.pile_icap].y) return;
     const int2 it = p.items[item];
     const int pi = it.x, base = it.y * kBatch;
     const PairDev P = p.pairs[pi];
@@ -865,12 +868,14 @@ template <int kW>
 __global__ void __launch_bounds__(32 * kW, 8) reduce_kernel(SimParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pi = blockIdx.x;
+    if (p.pile_counts && pi % p.pile_pcap >= p.pile_counts[pi / p.pile_pcap].x) return;
     const int NP = p.max_patches + kWin;
     const PatchSm S = carve_patch(smem_raw, NP);
     float4 *stage = reinterpret_cast<float4 *>(smem_raw + patch_smem_bytes(NP));
     init_patches<kW>(S, NP);
     float4 *scr = p.scratch + p.pairs[pi].scratch_off;
-    const int i0 = p.pair_item0[pi], i1 = p.pair_item0[pi + 1];
+    const int i0 = p.item_range ? p.item_range[pi].x : p.pair_item0[pi];
+    const int i1 = p.item_range ? p.item_range[pi].y : p.pair_item0[pi + 1];
     for (int it = i0; it < i1; ++it) {
         const int nc = p.cand_count[it];
         if (nc == 0) continue;
@@ -961,6 +966,133 @@ __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
     } else {
         phi[i] = __int_as_float(0x7f800000);
         nrm[3 * i] = 0.f; nrm[3 * i + 1] = 0.f; nrm[3 * i + 2] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Piles (pile envs): the pairs of every pile are found again before each detection.
+// Exclusive prefix sum over a block of up to 1024 threads (blockDim a multiple of 32);
+// returns the thread's offset, *total the block's sum.
+__device__ int block_scan(int v, int *warp_sums, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane < nw) warp_sums[lane] = x;   // inclusive over warps
+    }
+    __syncthreads();
+    const int before = warp > 0 ? warp_sums[warp - 1] : 0;
+    total = warp_sums[nw - 1];
+    __syncthreads();   // warp_sums may be reused by the caller's next scan
+    return before + incl - v;
+}
+
+// Per-body facts the pair rule of a pile reads, staged in shared memory: position and
+// bounding radius, the SDF's voxel size, and flags (movable, has samples, has an SDF).
+constexpr unsigned kPileMovable = 1u, kPileSamples = 2u, kPileGrid = 4u;
+struct PileStage {
+    float4 sph[kMaxPileBodies];
+    float h[kMaxPileBodies];
+    unsigned char fl[kMaxPileBodies];
+};
+
+// Pair rule of a pile for local bodies i < j: i's samples against j's SDF when i has samples
+// and j an SDF, else j's samples against i's SDF when j has samples and i an SDF; at least
+// one of the two movable; bounding spheres within the contact offset plus two voxels of the
+// SDF body (no candidate is possible farther apart).  Returns false for no pair.
+__device__ __forceinline__ bool pile_pair_rule(const PileStage &S, float offset, int i, int j, int &a, int &b) {
+    const unsigned fi = S.fl[i], fj = S.fl[j];
+    if (!((fi | fj) & kPileMovable)) return false;
+    if ((fi & kPileSamples) && (fj & kPileGrid)) { a = i; b = j; }
+    else if ((fj & kPileSamples) && (fi & kPileGrid)) { a = j; b = i; }
+    else return false;
+    const float4 A = S.sph[a], Bs = S.sph[b];
+    const V3 d = v3(A.x, A.y, A.z) - v3(Bs.x, Bs.y, Bs.z);
+    const float lim = A.w + Bs.w + offset + 2.0f * S.h[b];
+    return dot(d, d) <= lim * lim;
+}
+
+// One block per pile: the pile's pairs in (i, j) order into pairs[pair0 ..], their Generate
+// batches into items[item0 ..] and item_range, and counts[pile] = (pairs, items).  More
+// pairs or items than the pile's regions hold are dropped and flagged (overflow status).
+__global__ void __launch_bounds__(1024) pile_pairs_kernel(SimParams p, const PileDev *piles, PairDev *pairs,
+                                                          int2 *items, int2 *item_range, int2 *counts) {
+    __shared__ int warp_sums[32];
+    __shared__ PileStage S;
+    const PileDev P = piles[blockIdx.x];
+    const int t = threadIdx.x, n = P.n_bodies, b0 = P.first_body;
+    for (int i = t; i < n; i += blockDim.x) {
+        const BodyProps &Pi = p.props[b0 + i];
+        const AssetDev &Ai = p.assets[Pi.asset];
+        const V3 x = ld3(p.pos + 3 * (b0 + i));
+        S.sph[i] = make_float4(x.x, x.y, x.z, Ai.radius);
+        S.h[i] = Ai.h;
+        S.fl[i] = (unsigned char)(((Pi.type == FW_BODY_DYNAMIC || Pi.type == FW_BODY_FIXED_AXIS) ? kPileMovable : 0u) |
+                                  (Ai.ns > 0 ? kPileSamples : 0u) | ((Ai.cell32 || Ai.cell16) ? kPileGrid : 0u));
+    }
+    __syncthreads();
+    const float off = p.contact_offset;
+    int c = 0;
+    if (t < n)
+        for (int j = t + 1; j < n; ++j) {
+            int a, b;
+            c += pile_pair_rule(S, off, t, j, a, b) ? 1 : 0;
+        }
+    int total;
+    int k = block_scan(c, warp_sums, total);
+    if (t < n)
+        for (int j = t + 1; j < n; ++j) {
+            int a, b;
+            if (!pile_pair_rule(S, off, t, j, a, b)) continue;
+            if (k < P.pcap) {
+                PairDev D;
+                const BodyProps &Pa = p.props[b0 + a], &Pb = p.props[b0 + b];
+                D.a = b0 + a; D.b = b0 + b;
+                D.asset_a = Pa.asset; D.asset_b = Pb.asset;
+                D.env = P.env;
+                D.scratch_off = (P.pair0 + k) * P.stride;
+                D.mu = (float)sqrt((double)Pa.mu * (double)Pb.mu);
+                D.local_a = a; D.local_b = b;
+                D.pad_[0] = D.pad_[1] = D.pad_[2] = 0;
+                pairs[P.pair0 + k] = D;
+            }
+            ++k;
+        }
+    const int np = total < P.pcap ? total : P.pcap;
+    if (t == 0 && total > P.pcap) atomicOr(p.status, kStatusOverflow);
+    __syncthreads();   // the pairs are written
+    int base = 0;
+    for (int c0 = 0; c0 < np; c0 += blockDim.x) {
+        const int q = c0 + t;
+        int nb = 0;
+        if (q < np) {
+            const AssetDev &A = p.assets[pairs[P.pair0 + q].asset_a];
+            nb = (A.ns + kBatch - 1) / kBatch;
+        }
+        int chunk;
+        const int o = base + block_scan(nb, warp_sums, chunk);
+        if (q < np) {
+            const int lo = o < P.icap ? o : P.icap, hi = o + nb < P.icap ? o + nb : P.icap;
+            item_range[P.pair0 + q] = make_int2(P.item0 + lo, P.item0 + hi);
+            for (int u = lo; u < hi; ++u) items[P.item0 + u] = make_int2(P.pair0 + q, u - o);
+        }
+        base += chunk;
+    }
+    if (t == 0) {
+        if (base > P.icap) atomicOr(p.status, kStatusOverflow);
+        counts[blockIdx.x] = make_int2(np, base < P.icap ? base : P.icap);
     }
 }
 
@@ -1102,6 +1234,13 @@ cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
 cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt) {
     if (nt <= 0) return cudaSuccess;
     tri_pair_kernel<<<(nt + 255) / 256, 256, 0, s>>>(p, pair, x, phi, nrm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pile_pairs(const SimParams &p, const PileDev *piles, int n_piles, PairDev *pairs, int2 *items,
+                              int2 *item_range, int2 *counts, cudaStream_t s) {
+    if (n_piles <= 0) return cudaSuccess;
+    pile_pairs_kernel<<<n_piles, 1024, 0, s>>>(p, piles, pairs, items, item_range, counts);
     return cudaGetLastError();
 }
 

@@ -92,8 +92,25 @@ struct EnvDev {
     int row_off;             // offset of the env's rows in the row buffer
     int row_cap;             // rows available to the env
     int movable;             // local id of the only movable body, -1 none, -2 several
-    int pad_;
+    int pile;                // index of the env's pile (PileDev), -1 for an env of listed pairs
 };
+
+// A pile env: up to kMaxPileBodies bodies whose pairs a broad phase finds at every detection
+// (pile_pairs_kernel), solved colour by colour (pile_solve_kernel).  Its pairs, items,
+// contacts, candidates and rows live in regions of the world's pile buffers: pairs
+// [pair0, pair0 + pcap), items [item0, item0 + icap), rows [row0, row0 + rcap).
+struct PileDev {
+    int env, first_body, n_bodies;
+    int pair0, pcap;         // pair region (global pair index into the pile pair buffers)
+    int item0, icap;         // item region
+    int row0, rcap;          // row region
+    int stride;              // per-pair scratch stride in float4 (2 x the largest sample count)
+    int pad_[2];
+};
+constexpr int kMaxPileBodies = 1024;
+constexpr int kPilePairsPerBody = 8;    // pair capacity per body of a pile
+constexpr int kPileRowsPerBody = 192;   // row (contact) capacity per body of a pile
+constexpr int kMaxColors = 64;          // pair colours of a pile solve; the last gathers the rest
 
 // A reduced contact on the device.  sample_patch = sample | (patch << 24).
 struct __align__(16) DContact {
@@ -141,6 +158,12 @@ struct SimParams {
     float4 *cand;                          // n_items x kBatch x 2: (x_w, phi), (n_w, sample)
     int *cand_count;                       // n_items
     PairMap *maps;                         // n_pairs: each pair's map into its SDF grid
+    // pile launches (pile_counts non-null): pairs, items and contacts are the pile buffers,
+    // laid out in regions of pile_pcap pairs and pile_icap items per pile; pile_counts[k] =
+    // (pairs, items) found for pile k, item_range[pair] = its items [x, y)
+    const int2 *pile_counts;
+    const int2 *item_range;
+    int pile_pcap, pile_icap;
     int contact_gen;                       // 0: per sample, 1: per triangle (local minimisation)
     int multi_movable;                     // some env has several movable bodies (general sweep form)
     int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks
@@ -174,6 +197,9 @@ cudaError_t prepare_detect(int max_patches);
 cudaError_t launch_query(const SimParams &p, cudaStream_t s);    // narrow phase of every work item
 cudaError_t launch_reduce(const SimParams &p, cudaStream_t s);   // Algorithm 1 of every pair
 cudaError_t launch_detect(const SimParams &p, cudaStream_t s);   // both
+// every pile's pairs, items and item ranges from the broad phase (one block per pile)
+cudaError_t launch_pile_pairs(const SimParams &p, const PileDev *piles, int n_piles, PairDev *pairs, int2 *items,
+                              int2 *item_range, int2 *counts, cudaStream_t s);
 constexpr int kNoAllocMaxSamples = 65536;   // sample ids accepted by fw_reduce_noalloc
 cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d_cands, int n, fw_contact *d_out,
                                   int cap, int *d_counts, cudaStream_t s);
@@ -218,6 +244,18 @@ cudaError_t prepare_solve(int optin, int max_dyn[4]);
 SolveShape solve_shape(int n_envs, int lam_cap, int groups, int warps, const int max_dyn[4], int n_sm);
 cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
+// The pile solve's per-pair output kept for the API (global memory, one pile region each).
+struct PileSolveMem {
+    unsigned char *color;     // per pair: its colour in the last solve, 255 without rows
+};
+// The pile solve keeps per-pair tables in shared memory: a pair's rows as start | count << 21
+// and pair indices as 16 bits, hence these limits on a pile's capacities.
+constexpr int kPileMaxRows = 1 << 21;
+constexpr int kPileMaxPairs = 65535;
+size_t pile_smem_bytes(int n_bodies, int pcap);
+cudaError_t prepare_pile_solve(int optin, int *max_dyn);   // *max_dyn: dynamic shared memory allowed
+cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
+                              const PileSolveMem &m, Row *rows, size_t smem, cudaStream_t s);
 cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt);
 cudaError_t measure_l2_read(int device, long long bytes, int iters, float *gbs);
 

@@ -115,6 +115,21 @@ struct BodySm {
     float invm[kMaxBodies];
     float Iinv[kMaxBodies][6];
     float com[kMaxBodies][3];
+    // one lane updates an env's bodies: every body's velocity is written back
+    __device__ __forceinline__ bool writes(int) const { return true; }
+};
+
+// The bodies of a pile env in shared memory.  Pairs solved at the same time share no
+// movable body; a static or kinematic body's velocity is only read (never written back, so
+// that threads touching the same one do not race).
+struct PileBodies {
+    float (*v)[3];
+    float (*w)[3];
+    float *invm;
+    float (*Iinv)[6];
+    float (*com)[3];
+    const unsigned char *mov;   // 1: dynamic or fixed axis
+    __device__ __forceinline__ bool writes(int i) const { return mov[i] != 0; }
 };
 
 struct EnvSm {
@@ -144,7 +159,16 @@ __device__ __forceinline__ float eff_mass(float ima, float imb, V3 rad, V3 iad, 
     return den > 0.0f ? 1.0f / den : 0.0f;
 }
 
-__device__ __forceinline__ void build_row(Row &R, const DContact &c, const BodySm &B, int a, int b, float mu,
+// word offsets of the Row fields (static_assert above)
+enum RowWord : int {
+    kWN = 0, kWT1 = 3, kWT2 = 6, kWRAN = 9, kWRAT1 = 12, kWRAT2 = 15, kWRBN = 18, kWRBT1 = 21, kWRBT2 = 24,
+    kWIAN = 27, kWIAT1 = 30, kWIAT2 = 33, kWIBN = 36, kWIBT1 = 39, kWIBT2 = 42, kWKN = 45, kWKT1 = 46,
+    kWKT2 = 47, kWBIAS = 48, kWMU = 49, kWLN = 50, kWA = 53, kWB = 54
+};
+
+// One contact's rows (Row), built in registers and written as 15 float4.
+template <class BS>
+__device__ __forceinline__ void build_row(Row &R, const DContact &c, const BS &B, int a, int b, float mu,
                                           float hs, float baumgarte) {
     const V3 n = ld3(c.n), xa = ld3(c.xa);
     const float phi = c.phi;
@@ -156,61 +180,133 @@ __device__ __forceinline__ void build_row(Row &R, const DContact &c, const BodyS
     const V3 rbn = cross(rb, n), rbt1 = cross(rb, t1), rbt2 = cross(rb, t2);
     const V3 ian = sym_mul(B.Iinv[a], ran), iat1 = sym_mul(B.Iinv[a], rat1), iat2 = sym_mul(B.Iinv[a], rat2);
     const V3 ibn = sym_mul(B.Iinv[b], rbn), ibt1 = sym_mul(B.Iinv[b], rbt1), ibt2 = sym_mul(B.Iinv[b], rbt2);
-    st3(R.n, n); st3(R.t1, t1); st3(R.t2, t2);
-    st3(R.ra_n, ran); st3(R.ra_t1, rat1); st3(R.ra_t2, rat2);
-    st3(R.rb_n, rbn); st3(R.rb_t1, rbt1); st3(R.rb_t2, rbt2);
-    st3(R.ia_n, ian); st3(R.ia_t1, iat1); st3(R.ia_t2, iat2);
-    st3(R.ib_n, ibn); st3(R.ib_t1, ibt1); st3(R.ib_t2, ibt2);
+    float f[4 * kRowF4];
+    auto put = [&](int o, V3 v) { f[o] = v.x; f[o + 1] = v.y; f[o + 2] = v.z; };
+    put(kWN, n); put(kWT1, t1); put(kWT2, t2);
+    put(kWRAN, ran); put(kWRAT1, rat1); put(kWRAT2, rat2);
+    put(kWRBN, rbn); put(kWRBT1, rbt1); put(kWRBT2, rbt2);
+    put(kWIAN, ian); put(kWIAT1, iat1); put(kWIAT2, iat2);
+    put(kWIBN, ibn); put(kWIBT1, ibt1); put(kWIBT2, ibt2);
     const float ima = B.invm[a], imb = B.invm[b];
-    R.kn = eff_mass(ima, imb, ran, ian, rbn, ibn);
-    R.kt1 = eff_mass(ima, imb, rat1, iat1, rbt1, ibt1);
-    R.kt2 = eff_mass(ima, imb, rat2, iat2, rbt2, ibt2);
-    R.bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
-    R.mu = mu;
-    R.ln = 0.0f; R.lt1 = 0.0f; R.lt2 = 0.0f;
-    R.a = a; R.b = b;
+    f[kWKN] = eff_mass(ima, imb, ran, ian, rbn, ibn);
+    f[kWKT1] = eff_mass(ima, imb, rat1, iat1, rbt1, ibt1);
+    f[kWKT2] = eff_mass(ima, imb, rat2, iat2, rbt2, ibt2);
+    f[kWBIAS] = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    f[kWMU] = mu;
+    f[kWLN] = 0.0f; f[kWLN + 1] = 0.0f; f[kWLN + 2] = 0.0f;
+    f[kWA] = __int_as_float(a); f[kWB] = __int_as_float(b);
+#pragma unroll
+    for (int k = kWB + 1; k < 4 * kRowF4; ++k) f[k] = 0.0f;
+    float4 *q = reinterpret_cast<float4 *>(&R);
+#pragma unroll
+    for (int k = 0; k < kRowF4; ++k) q[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
-// One contact's Gauss-Seidel update in the general form: the normal row, then the two
-// friction rows projected jointly on the disk; L = (lambda_n, lambda_t1, lambda_t2, -).
-// The row is read as its 15 float4 (fields by constant word offsets, see Row), and the
-// disk projection scales by min(1, mu lambda_n / |lambda_t|) through a reciprocal square
-// root, as the fast form does.
-__device__ __forceinline__ void gs_row(const Row &R, float4 &L, BodySm &B, bool use_bias) {
-    const float4 *q = reinterpret_cast<const float4 *>(&R);
-    float f[4 * kRowF4];
+// 1. of a substep for body bi (slot lb of the body store): gravity, applied force and
+// torque and the gyroscopic term (dynamic bodies), the torque about the axis (fixed axis);
+// writes its velocity, angular velocity, centre of mass (world), inverse mass and world
+// inverse inertia (a fixed-axis body: a a^T / I_aa; others without rotation: zero).
+template <class BS>
+__device__ __forceinline__ void body_forces(const SimParams &p, int bi, int lb, float hs, BS &B) {
+    const BodyProps P = p.props[bi];
+    const float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
+    const M3 R = quat_to_mat(q);
+    V3 pos = ld3(p.pos + 3 * bi), v = ld3(p.linvel + 3 * bi), w = ld3(p.angvel + 3 * bi);
+    const V3 com = mul(R, ld3(P.com_b)) + pos;
+    float Iw[6], Ii[6] = {0, 0, 0, 0, 0, 0};
+    rot_sym(R, P.Ib, Iw);
+    if (P.type == FW_BODY_DYNAMIC) {
+        rot_sym(R, P.Ib_inv, Ii);
+        const V3 gv = v3(p.gravity[0], p.gravity[1], p.gravity[2]);
+        v = v + hs * (gv + P.invm * ld3(P.force));
+        const V3 tau = ld3(P.torque) - cross(w, sym_mul(Iw, w));
+        w = w + hs * sym_mul(Ii, tau);
+    } else if (P.type == FW_BODY_FIXED_AXIS) {
+        const V3 ax = ld3(P.axis);
+        const float Iaa = dot(ax, sym_mul(Iw, ax));
+        const float s = 1.0f / Iaa;
+        Ii[0] = ax.x * ax.x * s; Ii[1] = ax.y * ax.y * s; Ii[2] = ax.z * ax.z * s;
+        Ii[3] = ax.x * ax.y * s; Ii[4] = ax.x * ax.z * s; Ii[5] = ax.y * ax.z * s;
+        w = w + (hs * dot(ax, ld3(P.torque)) * s) * ax;
+    }
+    smv_set(B.v, lb, v);
+    smv_set(B.w, lb, w);
+    smv_set(B.com, lb, com);
+    B.invm[lb] = P.invm;
+    for (int k = 0; k < 6; ++k) B.Iinv[lb][k] = Ii[k];
+}
+
+// 4. of a substep for body bi: |omega| clamp, semi-implicit Euler of the centre of mass and
+// q <- normalize(q + hs/2 (omega, 0) q); writes the position and returns the new
+// quaternion (a static body keeps its own); a non-finite result sets the status bit.
+template <class BS>
+__device__ __forceinline__ float4 body_integrate(const SimParams &p, int bi, int lb, float hs, BS &B) {
+    const BodyProps P = p.props[bi];
+    float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
+    if (P.type == FW_BODY_STATIC) return q;
+    V3 w = smv(B.w, lb);
+    const V3 v = smv(B.v, lb);
+    if ((P.type == FW_BODY_DYNAMIC || P.type == FW_BODY_FIXED_AXIS) && p.max_angvel > 0.0f) {
+        const float wn = sqrtf(dot(w, w));
+        if (wn > p.max_angvel) w = (p.max_angvel / wn) * w;
+        smv_set(B.w, lb, w);
+    }
+    const V3 com = smv(B.com, lb) + hs * v;
+    // dq = (omega, 0) (x) q
+    const float dx = q.w * w.x + w.y * q.z - w.z * q.y;
+    const float dy = q.w * w.y + w.z * q.x - w.x * q.z;
+    const float dz = q.w * w.z + w.x * q.y - w.y * q.x;
+    const float dw = -(w.x * q.x + w.y * q.y + w.z * q.z);
+    const float hh = 0.5f * hs;
+    q.x += hh * dx; q.y += hh * dy; q.z += hh * dz; q.w += hh * dw;
+    const float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    q.x *= inv; q.y *= inv; q.z *= inv; q.w *= inv;
+    const M3 R = quat_to_mat(q);
+    const V3 pos = com - mul(R, ld3(P.com_b));
+    st3(p.pos + 3 * bi, pos);
+    const bool bad = !(isfinite(pos.x) && isfinite(pos.y) && isfinite(pos.z) && isfinite(q.x) && isfinite(q.y) &&
+                       isfinite(q.z) && isfinite(q.w));
+    if (bad) atomicOr(p.status, kStatusNonFinite);
+    return q;
+}
+
+// a row's 15 float4 as 60 words
+__device__ __forceinline__ void load_row_words(const Row *R, float (&f)[4 * kRowF4]) {
+    const float4 *q = reinterpret_cast<const float4 *>(R);
 #pragma unroll
     for (int k = 0; k < kRowF4; ++k) {
         const float4 v = q[k];
         f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
     }
-    // word offsets of the Row fields
-    enum { N = 0, T1 = 3, T2 = 6, RAN = 9, RAT1 = 12, RAT2 = 15, RBN = 18, RBT1 = 21, RBT2 = 24,
-           IAN = 27, IAT1 = 30, IAT2 = 33, IBN = 36, IBT1 = 39, IBT2 = 42, KN = 45, KT1 = 46, KT2 = 47,
-           BIAS = 48, MU = 49, A = 53, B_ = 54 };
+}
+
+// One contact's Gauss-Seidel update in the general form on the two bodies' velocities:
+// the normal row, then the two friction rows projected jointly on the disk; L =
+// (lambda_n, lambda_t1, lambda_t2, -).  The disk projection scales by
+// min(1, mu lambda_n / |lambda_t|) through a reciprocal square root, as the fast form does.
+// A row with a zero normal effective mass changes nothing.
+__device__ __forceinline__ void gs_core(const float (&f)[4 * kRowF4], float4 &L, V3 &va, V3 &wa, V3 &vb, V3 &wb,
+                                        float ima, float imb, bool use_bias) {
     auto w3 = [&](int o) { return v3(f[o], f[o + 1], f[o + 2]); };
-    if (f[KN] == 0.0f) return;
-    const int a = __float_as_int(f[A]), b = __float_as_int(f[B_]);
-    V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
-    const float ima = B.invm[a], imb = B.invm[b];
+    if (f[kWKN] == 0.0f) return;
     // normal row
-    const V3 n = w3(N);
-    float jv = dot(n, va - vb) + dot(w3(RAN), wa) - dot(w3(RBN), wb);
-    if (use_bias) jv += f[BIAS];
-    const float ln = fmaxf(L.x - f[KN] * jv, 0.0f);
+    const V3 n = w3(kWN);
+    float jv = dot(n, va - vb) + dot(w3(kWRAN), wa) - dot(w3(kWRBN), wb);
+    if (use_bias) jv += f[kWBIAS];
+    const float ln = fmaxf(L.x - f[kWKN] * jv, 0.0f);
     const float dl = ln - L.x;
     L.x = ln;
     va = va + (dl * ima) * n;
-    wa = wa + dl * w3(IAN);
+    wa = wa + dl * w3(kWIAN);
     vb = vb - (dl * imb) * n;
-    wb = wb - dl * w3(IBN);
+    wb = wb - dl * w3(kWIBN);
     // friction rows, projected jointly on the disk of radius mu lambda_n
-    const V3 t1 = w3(T1), t2 = w3(T2);
+    const V3 t1 = w3(kWT1), t2 = w3(kWT2);
     const V3 dv = va - vb;
-    const float j1 = dot(t1, dv) + dot(w3(RAT1), wa) - dot(w3(RBT1), wb);
-    const float j2 = dot(t2, dv) + dot(w3(RAT2), wa) - dot(w3(RBT2), wb);
-    float l1 = L.y - f[KT1] * j1, l2 = L.z - f[KT2] * j2;
-    const float sc = fminf(1.0f, (f[MU] * ln) * rsqrtf(__fmaf_rn(l1, l1, l2 * l2)));
+    const float j1 = dot(t1, dv) + dot(w3(kWRAT1), wa) - dot(w3(kWRBT1), wb);
+    const float j2 = dot(t2, dv) + dot(w3(kWRAT2), wa) - dot(w3(kWRBT2), wb);
+    float l1 = L.y - f[kWKT1] * j1, l2 = L.z - f[kWKT2] * j2;
+    const float sc = fminf(1.0f, (f[kWMU] * ln) * rsqrtf(__fmaf_rn(l1, l1, l2 * l2)));
     l1 *= sc;
     l2 *= sc;
     const float d1 = l1 - L.y, d2 = l2 - L.z;
@@ -218,11 +314,23 @@ __device__ __forceinline__ void gs_row(const Row &R, float4 &L, BodySm &B, bool 
     L.z = l2;
     const V3 pt = d1 * t1 + d2 * t2;
     va = va + ima * pt;
-    wa = wa + d1 * w3(IAT1) + d2 * w3(IAT2);
+    wa = wa + d1 * w3(kWIAT1) + d2 * w3(kWIAT2);
     vb = vb - imb * pt;
-    wb = wb - (d1 * w3(IBT1) + d2 * w3(IBT2));
-    smv_set(B.v, a, va); smv_set(B.w, a, wa);
-    smv_set(B.v, b, vb); smv_set(B.w, b, wb);
+    wb = wb - (d1 * w3(kWIBT1) + d2 * w3(kWIBT2));
+}
+
+// gs_core on one row with the bodies' velocities in the body store (read, updated, written
+// back where the store allows).
+template <class BS>
+__device__ __forceinline__ void gs_row(const Row &R, float4 &L, BS &B, bool use_bias) {
+    float f[4 * kRowF4];
+    load_row_words(&R, f);
+    if (f[kWKN] == 0.0f) return;
+    const int a = __float_as_int(f[kWA]), b = __float_as_int(f[kWB]);
+    V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
+    gs_core(f, L, va, wa, vb, wb, B.invm[a], B.invm[b], use_bias);
+    if (B.writes(a)) { smv_set(B.v, a, va); smv_set(B.w, a, wa); }
+    if (B.writes(b)) { smv_set(B.v, b, vb); smv_set(B.w, b, wb); }
 }
 
 // One Gauss-Seidel sweep over the env's rows in global memory, impulses in the rows (lane
@@ -521,10 +629,15 @@ __device__ bool sweep_fast(RowStream &rs, int total, int trips, float4 *lam, V3 
     const bool odd = gl & 1, leader = rs.leader;
     const int nch = (trips + kChunk - 1) / kChunk;   // chunks of steps; chunk nch is read ahead
     const int seq0 = rs.seq;
-    // A group without rows runs only discarded steps, which scale its chunk words by zero:
-    // make them zeros (shared memory may hold any bits, NaN patterns included).
+    // A group without rows runs steps whose results must leave its velocity as it is: zero
+    // rows and zero impulses are a fixed point of the step (every update vector zero, the
+    // impulses stay zero), but shared memory may hold any bits, NaN patterns included, and a
+    // chunk whose other groups all run real steps runs this group's steps unmasked.  So its
+    // chunk words and the impulse words its steps read (0 .. kChunk; past lam_cap they lie in
+    // the chunk buffers) are made zeros.
     if (nr == 0) {
         for (int k = gl; k < kChunkBufs * kChunkF4; k += G) rs.buf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = gl; k <= kChunk; k += G) lam[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
     for (int k = 0; k < kChunkBufs && k <= nch; ++k) issue_chunk(rs);
@@ -723,35 +836,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     BodySm &B = S.B;
     const float hs = p.hs;
     // 1. external forces; world inertia at the substep's start
-    for (int lb = gl; lb < E.n_bodies; lb += G) {
-        const int bi = E.first_body + lb;
-        const BodyProps P = p.props[bi];
-        const float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
-        const M3 R = quat_to_mat(q);
-        V3 pos = ld3(p.pos + 3 * bi), v = ld3(p.linvel + 3 * bi), w = ld3(p.angvel + 3 * bi);
-        const V3 com = mul(R, ld3(P.com_b)) + pos;
-        float Iw[6], Ii[6] = {0, 0, 0, 0, 0, 0};
-        rot_sym(R, P.Ib, Iw);
-        if (P.type == FW_BODY_DYNAMIC) {
-            rot_sym(R, P.Ib_inv, Ii);
-            const V3 gv = v3(p.gravity[0], p.gravity[1], p.gravity[2]);
-            v = v + hs * (gv + P.invm * ld3(P.force));
-            const V3 tau = ld3(P.torque) - cross(w, sym_mul(Iw, w));
-            w = w + hs * sym_mul(Ii, tau);
-        } else if (P.type == FW_BODY_FIXED_AXIS) {
-            const V3 ax = ld3(P.axis);
-            const float Iaa = dot(ax, sym_mul(Iw, ax));
-            const float s = 1.0f / Iaa;
-            Ii[0] = ax.x * ax.x * s; Ii[1] = ax.y * ax.y * s; Ii[2] = ax.z * ax.z * s;
-            Ii[3] = ax.x * ax.y * s; Ii[4] = ax.x * ax.z * s; Ii[5] = ax.y * ax.z * s;
-            w = w + (hs * dot(ax, ld3(P.torque)) * s) * ax;
-        }
-        smv_set(B.v, lb, v);
-        smv_set(B.w, lb, w);
-        smv_set(B.com, lb, com);
-        B.invm[lb] = P.invm;
-        for (int k = 0; k < 6; ++k) B.Iinv[lb][k] = Ii[k];
-    }
+    for (int lb = gl; lb < E.n_bodies; lb += G) body_forces(p, E.first_body + lb, lb, hs, B);
     // row offsets of the env's pairs
     if (gl == 0) {
         int acc = 0;
@@ -840,37 +925,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     __syncwarp();
     // 4. integration
     for (int lb = gl; lb < E.n_bodies; lb += G) {
-        const int bi = E.first_body + lb;
-        const BodyProps P = p.props[bi];
-        if (P.type != FW_BODY_STATIC) {
-            V3 w = smv(B.w, lb);
-            const V3 v = smv(B.v, lb);
-            if ((P.type == FW_BODY_DYNAMIC || P.type == FW_BODY_FIXED_AXIS) && p.max_angvel > 0.0f) {
-                const float wn = sqrtf(dot(w, w));
-                if (wn > p.max_angvel) w = (p.max_angvel / wn) * w;
-                smv_set(B.w, lb, w);
-            }
-            const V3 com = smv(B.com, lb) + hs * v;
-            float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
-            // dq = (omega, 0) (x) q
-            const float dx = q.w * w.x + w.y * q.z - w.z * q.y;
-            const float dy = q.w * w.y + w.z * q.x - w.x * q.z;
-            const float dz = q.w * w.z + w.x * q.y - w.y * q.x;
-            const float dw = -(w.x * q.x + w.y * q.y + w.z * q.z);
-            const float hh = 0.5f * hs;
-            q.x += hh * dx; q.y += hh * dy; q.z += hh * dz; q.w += hh * dw;
-            const float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-            q.x *= inv; q.y *= inv; q.z *= inv; q.w *= inv;
-            const M3 R = quat_to_mat(q);
-            const V3 pos = com - mul(R, ld3(P.com_b));
-            st3(p.pos + 3 * bi, pos);
-            S.q_new[lb][0] = q.x; S.q_new[lb][1] = q.y; S.q_new[lb][2] = q.z; S.q_new[lb][3] = q.w;
-            const bool bad = !(isfinite(pos.x) && isfinite(pos.y) && isfinite(pos.z) && isfinite(q.x) &&
-                               isfinite(q.y) && isfinite(q.z) && isfinite(q.w));
-            if (bad) atomicOr(p.status, kStatusNonFinite);
-        } else {
-            for (int k = 0; k < 4; ++k) S.q_new[lb][k] = p.quat[4 * bi + k];
-        }
+        const float4 q = body_integrate(p, E.first_body + lb, lb, hs, B);
+        S.q_new[lb][0] = q.x; S.q_new[lb][1] = q.y; S.q_new[lb][2] = q.z; S.q_new[lb][3] = q.w;
     }
     __syncwarp();
     // 5. optional bias-free sweeps
@@ -903,6 +959,279 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Piles: one block per pile env.  Rows of every pair with contacts; the pairs coloured
+// greedily in pair order (each takes the lowest colour that no earlier pair sharing one of
+// its movable bodies took; kMaxColors at most, the last gathering every pair left over);
+// Gauss-Seidel sweeps colour by colour.  The pairs of a colour share no movable body, so
+// the block's threads solve them at once (one thread per pair, its rows in order) with
+// exactly the updates of a sweep in colour order, pair order within a colour -- except the
+// last colour, which one thread sweeps in pair order.  Shared memory: the bodies
+// (PileBodies), their colour masks and the pairs' colours; row ranges and the colour order
+// of the pairs in global memory.
+
+// exclusive prefix sum over the block (blockDim a multiple of 32, at most 1024); *total:
+// the block's sum
+__device__ int pile_scan(int v, int *warp_sums, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane < nw) warp_sums[lane] = x;
+    }
+    __syncthreads();
+    const int before = warp > 0 ? warp_sums[warp - 1] : 0;
+    total = warp_sums[nw - 1];
+    __syncthreads();
+    return before + incl - v;
+}
+
+// A row's cache lines into L1 ahead of its use (a row is 240 bytes: two or three lines).
+__device__ __forceinline__ void prefetch_row_l1(const Row *R) {
+    const char *c = reinterpret_cast<const char *>(R);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(c));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(c + 128));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(c + 4 * kRowF4 * 4 - 16));
+}
+
+// The rows r0 .. r1 - 1 of one pair (bodies a, b) in order: the bodies' velocities stay in
+// registers for the pair (no other thread touches a movable one while the colour runs),
+// each row's 60 words are loaded while the row before it is solved, and the lines of the
+// rows two and three ahead are fetched into L1; the impulses go back into the rows.  The
+// same updates as gs_row row by row.
+template <bool kBias>
+__device__ __forceinline__ void pile_pair(Row *rows, int r0, int r1, int a, int b, PileBodies &B) {
+    if (r0 >= r1) return;
+    V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
+    const float ima = B.invm[a], imb = B.invm[b];
+    float f[4 * kRowF4], g[4 * kRowF4];
+    if (r0 + 1 < r1) prefetch_row_l1(rows + r0 + 1);
+    if (r0 + 2 < r1) prefetch_row_l1(rows + r0 + 2);
+    load_row_words(rows + r0, f);
+    auto solve = [&](int r, const float (&x)[4 * kRowF4]) {
+        float4 L = make_float4(x[kWLN], x[kWLN + 1], x[kWLN + 2], 0.0f);
+        gs_core(x, L, va, wa, vb, wb, ima, imb, kBias);
+        float *w = reinterpret_cast<float *>(rows + r);
+        w[kWLN] = L.x; w[kWLN + 1] = L.y; w[kWLN + 2] = L.z;
+    };
+    for (int r = r0; r < r1; r += 2) {
+        if (r + 3 < r1) prefetch_row_l1(rows + r + 3);
+        if (r + 1 < r1) load_row_words(rows + r + 1, g);
+        solve(r, f);
+        if (r + 1 >= r1) break;
+        if (r + 4 < r1) prefetch_row_l1(rows + r + 4);
+        if (r + 2 < r1) load_row_words(rows + r + 2, f);
+        solve(r + 1, g);
+    }
+    if (B.writes(a)) { smv_set(B.v, a, va); smv_set(B.w, a, wa); }
+    if (B.writes(b)) { smv_set(B.v, b, vb); smv_set(B.w, b, wb); }
+}
+
+// Per-pair tables of the pile solve in shared memory (see pile_smem_bytes).
+struct PileTables {
+    unsigned *ab;             // local ids a | b << 16, bit 15 / 31 set when a / b is movable
+    unsigned *rr;             // rows: start | count << 21 (within the pile's row region)
+    unsigned short *order;    // the pairs with rows by colour (pair order within the last colour)
+    unsigned char *col;       // colour, 254 before colouring, 255 without rows
+};
+constexpr unsigned kAbId = 0x3FFu;   // local ids are below kMaxPileBodies = 1024
+
+template <bool kBias>
+__device__ void pile_sweeps(PileBodies &B, Row *prow, const PileTables &T, const int *cstart, int n_colors,
+                            int n_sweeps) {
+    for (int it = 0; it < n_sweeps; ++it) {
+        for (int c = 0; c < n_colors; ++c) {
+            const bool serial = c == kMaxColors - 1;
+            if (!serial || threadIdx.x == 0) {
+                const int step = serial ? 1 : (int)blockDim.x;
+                for (int k = cstart[c] + (serial ? 0 : (int)threadIdx.x); k < cstart[c + 1]; k += step) {
+                    const int q = T.order[k];
+                    const unsigned rr = T.rr[q], ab = T.ab[q];
+                    const int r0 = (int)(rr & (kPileMaxRows - 1));
+                    pile_pair<kBias>(prow, r0, r0 + (int)(rr >> 21), (int)(ab & kAbId), (int)((ab >> 16) & kAbId), B);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int kPileThreads = 384;
+
+// The greedy colouring of the pairs with rows, in pair order, by one warp: a batch of 32
+// pairs is read into the lanes, then each pair of the batch in turn takes the lowest colour
+// that neither of its movable bodies has taken yet (bodies' colour masks in shared memory;
+// every lane computes the same colour, lane 0 updates the masks).
+__device__ void pile_colour_warp(const PileTables &T, unsigned long long *used, int np, int lane) {
+    for (int q0 = 0; q0 < np; q0 += 32) {
+        const int q = q0 + lane;
+        const bool has = q < np && T.col[q] != 255;
+        const unsigned my_ab = has ? T.ab[q] : 0u;
+        unsigned pend = __ballot_sync(0xffffffffu, has);
+        int mine = 255;
+        while (pend) {
+            const int k = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const unsigned abk = __shfl_sync(0xffffffffu, my_ab, k);
+            const int a = (int)(abk & kAbId), b = (int)((abk >> 16) & kAbId);
+            const unsigned long long ua = used[a], ub = used[b];   // zero for a body that never moves
+            int c = __ffsll((long long)~(ua | ub)) - 1;
+            if (c < 0 || c > kMaxColors - 1) c = kMaxColors - 1;
+            if (lane == k) mine = c;
+            __syncwarp();
+            if (lane == 0) {
+                if (abk & 0x8000u) used[a] = ua | (1ull << c);
+                if (abk & 0x80000000u) used[b] = ub | (1ull << c);
+            }
+            __syncwarp();
+        }
+        if (has) T.col[q] = (unsigned char)mine;
+    }
+}
+
+__global__ void __launch_bounds__(kPileThreads, 1) pile_solve_kernel(SimParams p, const PileDev *piles,
+                                                                      const int2 *counts, PileSolveMem M, Row *rows) {
+    extern __shared__ __align__(16) float pile_smem[];
+    __shared__ int warp_sums[32];
+    __shared__ int cstart[kMaxColors + 1];
+    __shared__ int fill[kMaxColors];
+    __shared__ int s_colors;
+    const PileDev P = piles[blockIdx.x];
+    const int n = P.n_bodies, t = threadIdx.x, NT = blockDim.x;
+    const int np = counts[blockIdx.x].x;
+    PileBodies B;
+    B.v = reinterpret_cast<float (*)[3]>(pile_smem);
+    B.w = reinterpret_cast<float (*)[3]>(pile_smem + 3 * n);
+    B.com = reinterpret_cast<float (*)[3]>(pile_smem + 6 * n);
+    B.Iinv = reinterpret_cast<float (*)[6]>(pile_smem + 9 * n);
+    B.invm = pile_smem + 15 * n;
+    unsigned long long *used = reinterpret_cast<unsigned long long *>(pile_smem + 16 * n);   // 64 n bytes in
+    PileTables T;
+    T.ab = reinterpret_cast<unsigned *>(used + n);
+    T.rr = T.ab + P.pcap;
+    T.order = reinterpret_cast<unsigned short *>(T.rr + P.pcap);
+    T.col = reinterpret_cast<unsigned char *>(T.order + P.pcap);
+    unsigned char *mov = T.col + P.pcap;
+    B.mov = mov;
+    Row *prow = rows + P.row0;
+    const float hs = p.hs;
+    // 1. external forces
+    for (int lb = t; lb < n; lb += NT) {
+        body_forces(p, P.first_body + lb, lb, hs, B);
+        const int ty = p.props[P.first_body + lb].type;
+        mov[lb] = (ty == FW_BODY_DYNAMIC || ty == FW_BODY_FIXED_AXIS) ? 1 : 0;
+        used[lb] = 0ull;
+    }
+    if (t < kMaxColors) fill[t] = 0;
+    if (t == 0) s_colors = 0;
+    __syncthreads();
+    // 2. each pair's rows (its contacts, at most cap_pair) placed in pair order, rows past the
+    // pile's row region dropped (overflow status); its bodies into the tables
+    int base = 0;
+    for (int c0 = 0; c0 < np; c0 += NT) {
+        const int q = c0 + t;
+        int nc = 0;
+        if (q < np) {
+            const int c = p.counts[P.pair0 + q];
+            nc = c < p.cap_pair ? c : p.cap_pair;
+        }
+        int chunk;
+        const int o = base + pile_scan(nc, warp_sums, chunk);
+        if (q < np) {
+            const int lo = o < P.rcap ? o : P.rcap, hi = o + nc < P.rcap ? o + nc : P.rcap;
+            T.rr[q] = (unsigned)lo | ((unsigned)(hi - lo) << 21);
+            T.col[q] = hi > lo ? 254 : 255;
+            const PairDev &D = p.pairs[P.pair0 + q];
+            const int a = D.local_a, b = D.local_b;
+            T.ab[q] = (unsigned)a | (mov[a] ? 0x8000u : 0u) | ((unsigned)b << 16) | (mov[b] ? 0x80000000u : 0u);
+        }
+        base += chunk;
+    }
+    if (t == 0 && base > P.rcap) atomicOr(p.status, kStatusOverflow);
+    __syncthreads();
+    // 3. warp 0 colours the pairs; the other warps build the rows, a warp per pair with rows,
+    // its lanes over the pair's contacts
+    const int lane = t & 31, warp = t >> 5, nw = NT >> 5;
+    if (warp == 0) {
+        pile_colour_warp(T, used, np, lane);
+    } else {
+        for (int q = warp - 1; q < np; q += nw - 1) {
+            const unsigned rr = T.rr[q];
+            const int cnt = (int)(rr >> 21);
+            if (cnt == 0) continue;
+            const int r0 = (int)(rr & (kPileMaxRows - 1));
+            const unsigned ab = T.ab[q];
+            const float mu = p.pairs[P.pair0 + q].mu;
+            const DContact *con = p.contacts + (size_t)(P.pair0 + q) * p.cap_pair;
+            for (int i = lane; i < cnt; i += 32)
+                build_row(prow[r0 + i], con[i], B, (int)(ab & kAbId), (int)((ab >> 16) & kAbId), mu, hs, p.baumgarte);
+        }
+    }
+    __syncthreads();
+    // 4. the pairs by colour: counts, starts, then each pair a slot in its colour (any order
+    // within a colour gives the same sweep: its pairs share no movable body)
+    for (int q = t; q < np; q += NT) {
+        const int c = T.col[q];
+        if (c != 255) {
+            atomicAdd(&fill[c], 1);
+            atomicMax(&s_colors, c + 1);
+        }
+        M.color[P.pair0 + q] = (unsigned char)c;
+    }
+    __syncthreads();
+    if (t == 0) {
+        cstart[0] = 0;
+        for (int c = 0; c < kMaxColors; ++c) {
+            cstart[c + 1] = cstart[c] + fill[c];
+            fill[c] = cstart[c];
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < np; q += NT) {
+        const int c = T.col[q];
+        if (c != 255 && c != kMaxColors - 1) T.order[atomicAdd(&fill[c], 1)] = (unsigned short)q;
+    }
+    // the last colour's pairs may share bodies: one thread sweeps them, in pair order
+    if (t == 0 && s_colors == kMaxColors) {
+        int k = cstart[kMaxColors - 1];
+        for (int q = 0; q < np; ++q)
+            if (T.col[q] == kMaxColors - 1) T.order[k++] = (unsigned short)q;
+    }
+    __syncthreads();
+    const int n_colors = s_colors;
+    // 5. Gauss-Seidel sweeps, colour by colour
+    pile_sweeps<true>(B, prow, T, cstart, n_colors, p.n_iters);
+    // 6. integration
+    for (int lb = t; lb < n; lb += NT) {
+        const int bi = P.first_body + lb;
+        const float4 q = body_integrate(p, bi, lb, hs, B);
+        p.quat[4 * bi] = q.x; p.quat[4 * bi + 1] = q.y; p.quat[4 * bi + 2] = q.z; p.quat[4 * bi + 3] = q.w;
+    }
+    __syncthreads();
+    // 7. optional bias-free sweeps
+    if (p.n_vel_iters > 0) pile_sweeps<false>(B, prow, T, cstart, n_colors, p.n_vel_iters);
+    for (int lb = t; lb < n; lb += NT) {
+        const int bi = P.first_body + lb;
+        const V3 v = smv(B.v, lb), w = smv(B.w, lb);
+        st3(p.linvel + 3 * bi, v);
+        st3(p.angvel + 3 * bi, w);
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z)))
+            atomicOr(p.status, kStatusNonFinite);
+    }
+}
+
 __global__ void normalize_quats_kernel(float *q, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -920,6 +1249,27 @@ cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s) {
 }
 
 size_t solve_smem_bytes(int lam_cap) { return sizeof(float4) * (size_t)env_stride_f4(lam_cap); }
+
+size_t pile_smem_bytes(int n_bodies, int pcap) {
+    // bodies (16 floats, a colour mask, a movable flag); per pair its bodies, its rows, an
+    // order slot and a colour (PileTables)
+    return (size_t)n_bodies * (16 * sizeof(float) + sizeof(unsigned long long) + 1) + (size_t)pcap * 11 + 16;
+}
+
+cudaError_t prepare_pile_solve(int optin, int *max_dyn) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, pile_solve_kernel);
+    if (e != cudaSuccess) return e;
+    *max_dyn = optin - (int)a.sharedSizeBytes;
+    return cudaFuncSetAttribute(pile_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+}
+
+cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
+                              const PileSolveMem &m, Row *rows, size_t smem, cudaStream_t s) {
+    if (n_piles <= 0) return cudaSuccess;
+    pile_solve_kernel<<<n_piles, kPileThreads, smem, s>>>(p, piles, counts, m, rows);
+    return cudaGetLastError();
+}
 
 template <int kGroups>
 static cudaError_t prepare_one(int optin, int *max_dyn) {

@@ -29,7 +29,8 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_set_timing", "fw_get_timings", "fw_set_solve_shape", "fw_autotune_solve", "fw_get_solve_shape",
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
-                 "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info",
+                 "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info", "fw_add_pile",
+                 "fw_get_pile_pairs",
                  "fw_launches_per_step",
                  "fw_last_error", "fw_measure_l2_read"]
 
@@ -81,6 +82,8 @@ def load_library(path: str = LIB_PATH):
         "fw_get_mass": (st, [vp, i, vp, vp, vp]),
         "fw_get_sdf_storage": (st, [vp, i, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
         "fw_add_env_bodies": (st, [vp, i, vp, i, vp, i, C.POINTER(i)]),
+        "fw_add_pile": (st, [vp, vp, i, i, i, C.POINTER(i)]),
+        "fw_get_pile_pairs": (st, [vp, i, vp, vp, i, C.POINTER(i)]),
         "fw_step": (st, [vp, i, i]),
         "fw_substep": (st, [vp, f, i, i]),
         "fw_collide": (st, [vp]),
@@ -232,6 +235,27 @@ class World:
         self._check(self.lib.fw_add_env_bodies(self.h, b.shape[0], b.ctypes.data, b.shape[1],
                                                p.ctypes.data if len(p) else None, len(p) // 2, C.byref(out)))
         return out.value
+
+    def add_pile(self, bodies: np.ndarray, max_pairs: int = 0, max_contacts: int = 0) -> int:
+        """One pile env of up to 1024 bodies whose pairs every detection finds again."""
+        b = np.ascontiguousarray(bodies, dtype=scenes.BODY_DTYPE).reshape(-1)
+        out = C.c_int()
+        self._check(self.lib.fw_add_pile(self.h, b.ctypes.data, len(b), max_pairs, max_contacts, C.byref(out)))
+        return out.value
+
+    def pile_pairs(self, env: int) -> Tuple[np.ndarray, np.ndarray]:
+        """A pile env's current pairs (n x 2 local body ids: sample body, SDF body) and each
+        pair's colour in the last solve (-1: no contacts)."""
+        cap = 1024
+        while True:
+            ab, col = np.zeros((cap, 2), np.int32), np.zeros(cap, np.int32)
+            n = C.c_int()
+            st = self.lib.fw_get_pile_pairs(self.h, env, ab.ctypes.data, col.ctypes.data, cap, C.byref(n))
+            if st == -6 and n.value > cap:
+                cap = n.value
+                continue
+            self._check(st)
+            return ab[: n.value].copy(), col[: n.value].copy()
 
     def counts(self) -> Tuple[int, int, int]:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
@@ -448,6 +472,8 @@ def world_from_scene(scene, fp16: bool = False, stream=None, **over) -> World:
             w.bake_sdf(i, a.sdf_res, a.sdf_pad, True)
     for g in scene.groups:
         w.add_env_bodies(g.bodies, g.pairs)
+    for pb in scene.piles:
+        w.add_pile(pb)
     return w
 
 

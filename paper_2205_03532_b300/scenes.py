@@ -879,12 +879,14 @@ def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_
                        n_iters: int = 16, n_vel_iters: int = 1, frames: int = 120, gap_mm: float = 2.0,
                        layers: int = 4, sink_mm: float = 0.02, overlap_mm: float = 1.0) -> Scene:
     """The paper's Nuts scene: n_nuts ISO M16 nuts (the nut of nut_bolt_scene: 18,136
-    triangles, n_samples samples, its own SDF) in ONE env over a static plate (SDF only, no
-    samples; top face z = 0), as a pile env whose pairs every detection finds again.
+    triangles, n_samples samples, its own SDF) in ONE env over a static support (SDF only, no
+    samples; its floor at z = 0), as a pile env whose pairs every detection finds again.
 
     mode "drop": the nuts start in a square lattice of columns (`layers` deep, cells of the
     nut's bounding diameter plus gap_mm, jittered by up to a quarter of the gap), at random
-    orientations, the lowest layer gap_mm above the plate, and fall into a pile.
+    orientations, the lowest layer gap_mm above the floor, and fall into a pile inside a
+    round tray (a box with a blind cylindrical hole 60 mm deep, 15 mm of floor below it,
+    the hole's wall 10 mm outside the lattice's corners) that keeps every nut on the floor.
     mode "heap": resting stacks of one to three nuts lying flat (random yaw), each sunk
     sink_mm into the one below or the plate; the stacks stand on a square grid whose pitch
     is the nut's across-corners width less overlap_mm, so that neighbouring stacks touch
@@ -910,7 +912,10 @@ def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_
             c = ((ix - (m - 1) / 2) * cell + jit[0], (iy - (m - 1) / 2) * cell + jit[1],
                  r + gap_mm * 1e-3 + lay * cell)
             bodies[k] = _body(0, DYNAMIC, c, _random_quat(rng), mu)
-        half = m * cell / 2 + 0.02
+        R = math.sqrt(2.0) * m * cell / 2 + 0.01
+        TV, TT = box_with_hole_mesh(2 * R + 0.04, 2 * R + 0.04, 0.075, R, 0.06, 64)
+        support = Asset("tray", TV, TT, None, 7800.0, sdf_res=plate_sdf_res, sdf_pad=1e-3)
+        support_z = 0.06
     elif mode == "heap":
         pitch = 2 * rc - overlap_mm * 1e-3
         heights = []
@@ -926,10 +931,11 @@ def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_
                 bodies[k] = _body(0, DYNAMIC, (cx, cy, z), quat_axis_angle([0, 0, 1], rng.uniform(0, np.pi / 3)), mu)
                 k += 1
         half = m * pitch / 2 + 0.02
+        PV, PT = box_mesh(half, half, 0.005)
+        support = Asset("plate", PV, PT, None, 7800.0, sdf_res=plate_sdf_res, sdf_pad=1e-3)
+        support_z = -0.005
     else:
         raise ValueError(f"unknown pile mode {mode!r}")
-    PV, PT = box_mesh(half, half, 0.005)
-    plate = Asset("plate", PV, PT, None, 7800.0, sdf_res=plate_sdf_res, sdf_pad=1e-3)
-    bodies[n_nuts] = _body(1, STATIC, (0.0, 0.0, -0.005), (0, 0, 0, 1), mu)
+    bodies[n_nuts] = _body(1, STATIC, (0.0, 0.0, support_z), (0, 0, 0, 1), mu)
     sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, n_vel_iters=n_vel_iters, frames=frames)
-    return Scene("nut_pile_env", [nut, plate], [], sim, piles=[bodies])
+    return Scene("nut_pile_env", [nut, support], [], sim, piles=[bodies])
