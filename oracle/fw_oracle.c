@@ -1397,6 +1397,22 @@ int or_get_pile_pairs(const or_world *w, int env, int *ab, int *color, int cap, 
     return E->ndp > cap ? -1 : 0;
 }
 
+/* The smallest decision margins of one pair's last detection. */
+int or_pair_margins(const or_world *w, int env, int pair, double *len, double *dot) {
+    if (env < 0 || env >= w->n_envs || pair < 0 || pair >= env_np(w, env)) return -1;
+    const pair_contacts_t *pc = &env_pcs(w, env)[pair];
+    *len = pc->m_len; *dot = pc->m_dot;
+    return 0;
+}
+
+/* A pile env's pair list at the current poses, without detecting their contacts (the
+ * broad phase alone; the pairs' contacts are cleared). */
+int or_find_pile_pairs(or_world *w, int env) {
+    if (env < 0 || env >= w->n_envs || !w->envs[env].pile) return -1;
+    pile_pairs(w, env);
+    return 0;
+}
+
 int or_env_margins(const or_world *w, int env, double *len, double *dot) {
     *len = w->env_mlen[env]; *dot = w->env_mdot[env];
     return 0;

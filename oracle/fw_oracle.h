@@ -166,6 +166,10 @@ int or_env_margins(const or_world *w, int env, double *len, double *dot);
 /* A pile env's current pairs (R20; from its last detection): (point body, SDF body) as
  * local body ids, in pair order, and each pair's colour in the last solve (-1: no contacts). */
 int or_get_pile_pairs(const or_world *w, int env, int *ab, int *color, int cap, int *n_out);
+/* One pair's smallest decision margins in its last detection (env-local pair index). */
+int or_pair_margins(const or_world *w, int env, int pair, double *len, double *dot);
+/* A pile env's pairs at the current poses (broad phase only; their contacts cleared). */
+int or_find_pile_pairs(or_world *w, int env);
 void or_reset_margins(or_world *w);
 /* State arrays, n_bodies entries: pos 3, quat 4, linvel 3, angvel 3. */
 int or_get_state(const or_world *w, double *pos, double *quat, double *linvel, double *angvel);

@@ -89,6 +89,8 @@ def lib():
             L.or_asset_mass.argtypes = [vp, C.c_int, C.POINTER(C.c_double), _f64, _f64]
             L.or_add_envs.argtypes = [vp, C.c_int, vp, C.c_int, _i32, C.c_int]
             L.or_get_pile_pairs.argtypes = [vp, C.c_int, _i32, _i32, C.c_int, C.POINTER(C.c_int)]
+            L.or_pair_margins.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.or_find_pile_pairs.argtypes = [vp, C.c_int]
             L.or_n_envs.argtypes = [vp]
             L.or_n_bodies.argtypes = [vp]
             L.or_step.argtypes = [vp, C.c_int, C.c_int]
@@ -362,6 +364,19 @@ class OracleWorld:
         c = np.ascontiguousarray(contacts, dtype=CONTACT_DTYPE)
         if lib().or_set_pair_contacts(self.h, env, pair, c.ctypes.data, len(c)) != 0:
             raise ValueError(f"or_set_pair_contacts: bad env {env} or pair {pair}")
+
+    def pair_margins(self, env: int, pair: int):
+        """the smallest decision margins (length, dot) of one pair's last detection"""
+        ml, md = C.c_double(), C.c_double()
+        if lib().or_pair_margins(self.h, env, pair, C.byref(ml), C.byref(md)) != 0:
+            raise ValueError(f"or_pair_margins: bad env {env} or pair {pair}")
+        return ml.value, md.value
+
+    def find_pile_pairs(self, env: int):
+        """the pile env's pairs at the current poses (broad phase only), as pile_pairs"""
+        if lib().or_find_pile_pairs(self.h, env) != 0:
+            raise ValueError(f"not a pile env: {env}")
+        return self.pile_pairs(env)
 
     def margins(self, env: int):
         ml, md = C.c_double(), C.c_double()
