@@ -98,6 +98,10 @@ typedef struct {
                                    sizes at 8 substeps x 64 iterations) */
     int device;                 /* CUDA device ordinal, default 0 */
     void *cuda_stream;          /* cudaStream_t to enqueue on, NULL: the world's own */
+    unsigned long long seed;    /* the seed the caller's scene generator drew its inputs
+                                   with, kept with the world for its records; no step of
+                                   the path draws a random number (poses, samples and
+                                   masses are inputs), so nothing reads it; default 0 */
 } fw_config;
 
 /* One body of an environment.  104 bytes, no padding. */

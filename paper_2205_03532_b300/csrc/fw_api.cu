@@ -696,6 +696,7 @@ void fw_config_default(fw_config *c) {
     c->solver = 0;
     c->device = 0;
     c->cuda_stream = nullptr;
+    c->seed = 0;
 }
 
 fw_status fw_create(const fw_config *cfg, fw_world **out) {

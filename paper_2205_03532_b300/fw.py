@@ -48,7 +48,7 @@ class FwConfig(C.Structure):
                 ("baumgarte", C.c_float), ("n_vel_iters", C.c_int), ("max_angvel", C.c_float),
                 ("sdf_fp16", C.c_int), ("contact_gen", C.c_int), ("tri_iters", C.c_int), ("sdf_band", C.c_float),
                 ("solver", C.c_int), ("device", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("seed", C.c_ulonglong)]
 
 
 CONTACT_DTYPE = np.dtype([("sample", np.int32), ("patch", np.int32), ("pair", np.int32),

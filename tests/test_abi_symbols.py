@@ -42,7 +42,7 @@ def test_config_defaults_without_gpu():
 
 
 def test_struct_layouts_match_header(tmp_path):
-    assert ctypes.sizeof(fw.FwConfig) == 80   # 18 four-byte values (gravity has 3), then a pointer
+    assert ctypes.sizeof(fw.FwConfig) == 88   # 18 four-byte values (gravity has 3), a pointer, the seed
     # every field offset of the binding's fw_config against the C compiler's, from the header
     names = [f[0] for f in fw.FwConfig._fields_]
     src = tmp_path / "offsets.c"
