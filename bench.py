@@ -452,8 +452,11 @@ def run_fw(args):
     dominant = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = {k: v for k, v in kernels[dominant].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roof["kernel"] = dominant
-    # deepest contact over a sample of envs at the end of the run (a stability indicator)
-    deepest = min([float(w.get_contacts(e)["phi"].min(initial=np.inf)) for e in range(0, n_env, max(1, n_env // 64))])
+    # deepest contact and patches per pair over a sample of envs at the end of the run
+    sample_c = [w.get_contacts(e) for e in range(0, n_env, max(1, n_env // 64))]
+    deepest = min([float(c["phi"].min(initial=np.inf)) for c in sample_c])
+    patches = [len(np.unique(c["pair"].astype(np.int64) * 1024 + c["patch"])) for c in sample_c]
+    patches_per_pair = float(np.mean(patches)) / max(n_pair / max(n_env, 1), 1e-9)
     single = None
     if tri_mode:
         single = single_pair_generate(sc, gen_cfg, fp16, dev)
@@ -500,6 +503,8 @@ def run_fw(args):
                "phase_ms_per_frame": {"query": qry_ms * sim.n_substeps, "reduce": red_ms * sim.n_substeps,
                                       "solve": sol_ms * sim.n_substeps},
                "contacts_per_env": c_mean, "deepest_contact_m": deepest, "candidates_per_pair": n_cand / max(n_pair, 1),
+               "contact_statistics": {"contacts_per_pair": n_cont / max(n_pair, 1), "patches_per_pair": patches_per_pair,
+                                      "paper_nut_bolt": {"contacts_per_pair": 195, "patches_per_pair": 53}},
                "solve_shape": list(w.solve_shape()), "autotuned": tuned is not None,
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),
