@@ -447,6 +447,25 @@ FW_API fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int
                                    int *warps_per_block, float *best_ms);
 FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block);
 
+/* Launch shape of detection (Sec. III-A narrow phase, Sec. III-C Algorithm 1):
+ * query_threads in {128, 256, 512} threads per work item of 1024 samples (each thread
+ * queries 1024 / query_threads samples; per-triangle generation always runs 256) and
+ * reduce_warps in {2, 4, 8} warps per pair; 0 for either: the default (256, 4).  Results
+ * do not depend on the shape: candidates are compacted in sample order and the reduction
+ * breaks every tie by depth and sample.  Errors: FW_ERR_ARG for other values.
+ * fw_get_detect_shape returns the shape in use. */
+FW_API fw_status fw_set_detect_shape(fw_world *w, int query_threads, int reduce_warps);
+FW_API fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduce_warps);
+/* Autotuner of that shape: at the current poses, runs one detection, then times `trials`
+ * query launches for each query size (with 4 reduction warps), and `trials` reduction
+ * launches of the fastest query's candidates for each warp count, and keeps the fastest of
+ * each (as fw_set_detect_shape would).  The body state is not touched; the contact buffer
+ * is left holding the contacts at the current poses.  Returns the chosen shape and the
+ * summed time of one query and one reduction launch (ms); any output pointer may be NULL.
+ * Synchronises. */
+FW_API fw_status fw_autotune_detect(fw_world *w, int trials, int *query_threads, int *reduce_warps,
+                                    float *best_ms);
+
 /* Totals of the last detection pass (synchronises): candidates (samples with phi below
  * the contact offset, Sec. III-A) summed over all pairs, and reduced contacts kept
  * (Algorithm 1) summed over all pairs.  Either pointer may be NULL.  Counts are those of

@@ -74,6 +74,7 @@ struct fw_world {
     int n_sm = 0, max_dyn_smem[4] = {0, 0, 0, 0};
     int solve_groups = 0, solve_warps = 0;
     int lam_rows = 0;   // rows per env whose impulses the solve keeps in shared memory (0: every row)
+    int query_threads = 0, reduce_warps = 0;   // detection launch shape (0: the defaults)
     // pile envs (fw_add_pile): one region per pile in each pile buffer, every region of the
     // same size (pile_pcap pairs, pile_icap items, pile_rcap rows)
     std::vector<PileDev> piles;
@@ -434,6 +435,8 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
         p.broad_phase |= (E.n_pairs > 1);
     }
     p.tri_iters = w->cfg.tri_iters;
+    p.query_threads = w->query_threads;
+    p.reduce_warps = w->reduce_warps;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;
     p.cand = w->d_cand;
@@ -1619,6 +1622,86 @@ fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials
     if (warps_per_block) *warps_per_block = bw;
     if (best_ms) *best_ms = best;
     return FW_OK;
+}
+
+fw_status fw_set_detect_shape(fw_world *w, int query_threads, int reduce_warps) {
+    if (!w) return FW_ERR_ARG;
+    if (!(query_threads == 0 || query_threads == 128 || query_threads == 256 || query_threads == 512) ||
+        !(reduce_warps == 0 || reduce_warps == 2 || reduce_warps == 4 || reduce_warps == 8))
+        return fail(w, FW_ERR_ARG, "fw_set_detect_shape: query_threads in {0,128,256,512}, reduce_warps in {0,2,4,8}");
+    if (w->query_threads != query_threads || w->reduce_warps != reduce_warps) drop_graph(w);
+    w->query_threads = query_threads;
+    w->reduce_warps = reduce_warps;
+    return FW_OK;
+}
+
+fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduce_warps) {
+    if (!w) return FW_ERR_ARG;
+    if (query_threads) *query_threads = w->query_threads > 0 ? w->query_threads : 256;
+    if (reduce_warps) *reduce_warps = w->reduce_warps > 0 ? w->reduce_warps : 4;
+    return FW_OK;
+}
+
+fw_status fw_autotune_detect(fw_world *w, int trials, int *query_threads, int *reduce_warps, float *best_ms) {
+    if (!ready(w)) return FW_ERR_ARG;
+    if (trials < 1) return fail(w, FW_ERR_ARG, "fw_autotune_detect: trials >= 1");
+    fw_status st = ensure_device(w);
+    if (st != FW_OK) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const bool piles = !w->piles.empty();
+    // one detection pass (query of every work item, then the reduction of every pair) for
+    // the given shape; the reduction reads only the query's output, so it is timed alone
+    auto time_phase = [&](int qt, int rw, bool query, float *ms) -> fw_status {
+        w->query_threads = qt;
+        w->reduce_warps = rw;
+        SimParams p = sim_params(w, w->cfg.dt, 0);
+        const SimParams q = piles ? pile_params(w, w->cfg.dt, 0) : p;
+        CK(cudaEventRecord(e0, w->stream));
+        for (int t = 0; t < trials; ++t) {
+            if (query) {
+                if (w->n_regular > 0) CK(launch_query(p, w->stream));
+                if (piles) CK(launch_query(q, w->stream));
+            } else {
+                if (w->n_regular > 0) CK(launch_reduce(p, w->stream));
+                if (piles) CK(launch_reduce(q, w->stream));
+            }
+        }
+        CK(cudaEventRecord(e1, w->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        *ms /= (float)trials;
+        return FW_OK;
+    };
+    // the pile pair lists (if any) and every query's output at the current poses
+    st = fw_collide(w);
+    int best_q = 256, best_r = 4;
+    float bq = 1e30f, br = 1e30f;
+    for (int qt : {256, 128, 512}) {   // the query with the default reduction
+        float ms = 0.f;
+        if (st == FW_OK) st = time_phase(qt, 4, true, &ms);
+        if (st == FW_OK && ms < bq) { bq = ms; best_q = qt; }
+    }
+    if (st == FW_OK) st = time_phase(best_q, 4, true, &bq);   // leave the best query's output
+    for (int rw : {4, 2, 8}) {
+        float ms = 0.f;
+        if (st == FW_OK) st = time_phase(best_q, rw, false, &ms);
+        if (st == FW_OK && ms < br) { br = ms; best_r = rw; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FW_OK) return st;
+    w->query_threads = best_q;
+    w->reduce_warps = best_r;
+    // the contacts of the chosen shape (every shape gives the same ones)
+    if (w->n_regular > 0) CK(launch_reduce(sim_params(w, w->cfg.dt, 0), w->stream));
+    if (piles) CK(launch_reduce(pile_params(w, w->cfg.dt, 0), w->stream));
+    drop_graph(w);
+    if (query_threads) *query_threads = best_q;
+    if (reduce_warps) *reduce_warps = best_r;
+    if (best_ms) *best_ms = bq + br;
+    return check_status(w);
 }
 
 fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_per_block) {

@@ -778,8 +778,12 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 }
 
 // ---------------------------------------------------------------------------------------
-template <bool kTri, int kStore>
-__global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
+// kThr threads per CTA (per-sample generation: 128, 256 or 512, chosen by the detection
+// autotuner; each thread queries kBatch / kThr samples; per-triangle generation: 256).
+template <bool kTri, int kStore, int kThr>
+__global__ void __launch_bounds__(kThr, kThr == 128 ? 5 : 1024 / kThr) query_kernel(SimParams p) {
+    static_assert(!kTri || kThr == kQueryThreads, "per-triangle generation runs 256 threads");
+    constexpr int NPER = kBatch / kThr, NW = kThr / 32;
     const int item = blockIdx.x;
     // pile launches cover every pile's item region; items past a pile's count do nothing
     if (p.pile_counts && item % p.pile_icap >= p.pile_counts[item / p.pile_icap].y) return;
@@ -802,9 +806,9 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float cutoff = p.contact_offset;
-    V3 xw[kQueryPerThread], nw[kQueryPerThread];
-    float ph[kQueryPerThread];
-    bool ok[kQueryPerThread];
+    V3 xw[NPER], nw[NPER];
+    float ph[NPER];
+    bool ok[NPER];
     if (kTri) {   // one candidate per triangle of the mesh, the pose shared in shared memory
         __shared__ PairXf Xs;
         __shared__ float4 tres[2 * kBatch];
@@ -815,9 +819,9 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
         __syncthreads();
         const unsigned okb = tri_batch<kStore>(Xs, ga, gb, base, tid, p.tri_iters, cutoff, tres);
 #pragma unroll
-        for (int u = 0; u < kQueryPerThread; ++u) {   // the thread's own results
+        for (int u = 0; u < NPER; ++u) {   // the thread's own results
             ok[u] = (okb >> u) & 1u;
-            const float4 r0 = tres[2 * (u * kQueryThreads + tid)], r1 = tres[2 * (u * kQueryThreads + tid) + 1];
+            const float4 r0 = tres[2 * (u * kThr + tid)], r1 = tres[2 * (u * kThr + tid) + 1];
             xw[u] = v3(r0.x, r0.y, r0.z);
             ph[u] = r0.w;
             nw[u] = v3(r1.x, r1.y, r1.z);
@@ -828,44 +832,44 @@ __global__ void __launch_bounds__(kQueryThreads, 4) query_kernel(SimParams p) {
         load_pose(p, P.a, X.RA, X.pA);
         load_pose(p, P.b, X.RB, X.pB);
 #pragma unroll
-        for (int u = 0; u < kQueryPerThread; ++u) {
-            const int i = base + u * kQueryThreads + tid;
+        for (int u = 0; u < NPER; ++u) {
+            const int i = base + u * kThr + tid;
             const float4 s = __ldg(&ga.samples[i < ga.ns ? i : ga.ns - 1]);
             ok[u] = query_sample<kStore>(M, X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
         }
     }
-    // compaction in sample order: local sample u * 256 + warp * 32 + lane
-    __shared__ int cnt[kQueryPerThread * kQueryWarps];
-    unsigned m[kQueryPerThread];
+    // compaction in sample order: local sample u * kThr + warp * 32 + lane
+    __shared__ int cnt[NPER * NW];
+    unsigned m[NPER];
 #pragma unroll
-    for (int u = 0; u < kQueryPerThread; ++u) {
+    for (int u = 0; u < NPER; ++u) {
         m[u] = __ballot_sync(0xffffffffu, ok[u]);
-        if (lane == 0) cnt[u * kQueryWarps + warp] = __popc(m[u]);
+        if (lane == 0) cnt[u * NW + warp] = __popc(m[u]);
     }
     __syncthreads();
-    int total = 0, off[kQueryPerThread];
+    int total = 0, off[NPER];
 #pragma unroll
-    for (int u = 0; u < kQueryPerThread; ++u) {
-        for (int w = 0; w < kQueryWarps; ++w) {
+    for (int u = 0; u < NPER; ++u) {
+        for (int w = 0; w < NW; ++w) {
             if (w == warp) off[u] = total;
-            total += cnt[u * kQueryWarps + w];
+            total += cnt[u * NW + w];
         }
     }
     float4 *out = p.cand + (size_t)item * 2 * kBatch;
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int u = 0; u < kQueryPerThread; ++u) {
+    for (int u = 0; u < NPER; ++u) {
         if (ok[u]) {
             const int k = off[u] + __popc(m[u] & lt);
             out[2 * k] = make_float4(xw[u].x, xw[u].y, xw[u].z, ph[u]);
-            out[2 * k + 1] = make_float4(nw[u].x, nw[u].y, nw[u].z, __int_as_float(base + u * kQueryThreads + tid));
+            out[2 * k + 1] = make_float4(nw[u].x, nw[u].y, nw[u].z, __int_as_float(base + u * kThr + tid));
         }
     }
     if (tid == 0) p.cand_count[item] = total;
 }
 
 template <int kW>
-__global__ void __launch_bounds__(32 * kW, 8) reduce_kernel(SimParams p) {
+__global__ void __launch_bounds__(32 * kW, kW >= 8 ? 4 : 8) reduce_kernel(SimParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pi = blockIdx.x;
     if (p.pile_counts && pi % p.pile_pcap >= p.pile_counts[pi / p.pile_pcap].x) return;
@@ -1200,15 +1204,22 @@ cudaError_t launch_reduce_noalloc(const SimParams &p, int device, const float *d
     return cudaGetLastError();
 }
 
-// Raises the kernels' dynamic shared-memory limit (outside any stream capture).
-cudaError_t prepare_detect(int max_patches) {
-    cudaError_t e = cudaFuncSetAttribute(reduce_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int kW>
+static cudaError_t prepare_reduce(int max_patches) {
+    cudaError_t e = cudaFuncSetAttribute(reduce_kernel<kW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)reduce_smem_bytes(max_patches, kStage));
     if (e != cudaSuccess) return e;
     // one reduction block per pair, all resident at once: ask for the largest shared-memory
     // share of the SM's on-chip memory
-    e = cudaFuncSetAttribute(reduce_kernel<kReduceWarps>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+    return cudaFuncSetAttribute(reduce_kernel<kW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// Raises the kernels' dynamic shared-memory limit (outside any stream capture).
+cudaError_t prepare_detect(int max_patches) {
+    cudaError_t e = prepare_reduce<2>(max_patches);
+    if (e == cudaSuccess) e = prepare_reduce<4>(max_patches);
+    if (e == cudaSuccess) e = prepare_reduce<8>(max_patches);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reduce_list_kernel<kReduceWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)reduce_smem_bytes(max_patches, kBatch));
@@ -1221,12 +1232,17 @@ cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    const int qt = p.query_threads > 0 ? p.query_threads : kQueryThreads;
     if (p.sdf_bricks) {
-        if (p.contact_gen == 1) query_kernel<true, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);
-        else query_kernel<false, kStoreBricks><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        if (p.contact_gen == 1) query_kernel<true, kStoreBricks, kQueryThreads><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        else if (qt == 128) query_kernel<false, kStoreBricks, 128><<<p.n_items, 128, 0, s>>>(p);
+        else if (qt == 512) query_kernel<false, kStoreBricks, 512><<<p.n_items, 512, 0, s>>>(p);
+        else query_kernel<false, kStoreBricks, 256><<<p.n_items, 256, 0, s>>>(p);
     } else {
-        if (p.contact_gen == 1) query_kernel<true, kStoreDense><<<p.n_items, kQueryThreads, 0, s>>>(p);
-        else query_kernel<false, kStoreDense><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        if (p.contact_gen == 1) query_kernel<true, kStoreDense, kQueryThreads><<<p.n_items, kQueryThreads, 0, s>>>(p);
+        else if (qt == 128) query_kernel<false, kStoreDense, 128><<<p.n_items, 128, 0, s>>>(p);
+        else if (qt == 512) query_kernel<false, kStoreDense, 512><<<p.n_items, 512, 0, s>>>(p);
+        else query_kernel<false, kStoreDense, 256><<<p.n_items, 256, 0, s>>>(p);
     }
     return cudaGetLastError();
 }
@@ -1246,7 +1262,11 @@ cudaError_t launch_pile_pairs(const SimParams &p, const PileDev *piles, int n_pi
 
 cudaError_t launch_reduce(const SimParams &p, cudaStream_t s) {
     if (p.n_pairs == 0) return cudaSuccess;
-    reduce_kernel<kReduceWarps><<<p.n_pairs, 32 * kReduceWarps, reduce_smem_bytes(p.max_patches, kStage), s>>>(p);
+    const size_t smem = reduce_smem_bytes(p.max_patches, kStage);
+    const int rw = p.reduce_warps > 0 ? p.reduce_warps : kReduceWarps;
+    if (rw == 2) reduce_kernel<2><<<p.n_pairs, 64, smem, s>>>(p);
+    else if (rw == 8) reduce_kernel<8><<<p.n_pairs, 256, smem, s>>>(p);
+    else reduce_kernel<4><<<p.n_pairs, 128, smem, s>>>(p);
     return cudaGetLastError();
 }
 

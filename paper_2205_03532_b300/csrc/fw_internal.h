@@ -169,6 +169,8 @@ struct SimParams {
     int sdf_bricks;                        // the assets' SDFs are held in narrow-band bricks
     int solver;                            // 0: Gauss-Seidel; 1: weighted Jacobi
     int broad_phase;                       // some env has several pairs: skip pairs far apart
+    int query_threads;                     // per-sample query CTA size (128, 256, 512; 0: 256)
+    int reduce_warps;                      // reduction warps per pair (2, 4, 8; 0: 4)
     int tri_iters;                         // descent steps per triangle
 };
 

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info", "fw_add_pile",
-                 "fw_get_pile_pairs",
+                 "fw_get_pile_pairs", "fw_set_detect_shape", "fw_get_detect_shape", "fw_autotune_detect",
                  "fw_launches_per_step",
                  "fw_last_error", "fw_measure_l2_read"]
 
@@ -84,6 +84,9 @@ def load_library(path: str = LIB_PATH):
         "fw_add_env_bodies": (st, [vp, i, vp, i, vp, i, C.POINTER(i)]),
         "fw_add_pile": (st, [vp, vp, i, i, i, C.POINTER(i)]),
         "fw_get_pile_pairs": (st, [vp, i, vp, vp, i, C.POINTER(i)]),
+        "fw_set_detect_shape": (st, [vp, i, i]),
+        "fw_get_detect_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
+        "fw_autotune_detect": (st, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_float)]),
         "fw_step": (st, [vp, i, i]),
         "fw_substep": (st, [vp, f, i, i]),
         "fw_collide": (st, [vp]),
@@ -384,6 +387,20 @@ class World:
         self._check(self.lib.fw_autotune_solve(self.h, n_substeps, n_iters, trials, C.byref(g), C.byref(w),
                                                C.byref(ms)))
         return g.value, w.value, ms.value
+
+    def set_detect_shape(self, query_threads: int = 0, reduce_warps: int = 0):
+        self._check(self.lib.fw_set_detect_shape(self.h, query_threads, reduce_warps))
+
+    def detect_shape(self):
+        a, b = C.c_int(), C.c_int()
+        self._check(self.lib.fw_get_detect_shape(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def autotune_detect(self, trials: int = 3):
+        """(query threads, reduction warps, ms of one query + one reduction launch)"""
+        a, b, ms = C.c_int(), C.c_int(), C.c_float()
+        self._check(self.lib.fw_autotune_detect(self.h, trials, C.byref(a), C.byref(b), C.byref(ms)))
+        return a.value, b.value, ms.value
 
     def solve_shape(self):
         g, w = C.c_int(), C.c_int()

@@ -260,3 +260,38 @@ def test_solve_shapes_give_bit_identical_results():
     assert w.solve_shape() == (2, 1)                     # 19 envs: two per warp, one warp per block
     with pytest.raises(fw.FwError):
         w.set_solve_shape(3, 1)
+
+
+def test_detect_shapes_give_identical_contacts_and_the_autotuner_keeps_them():
+    """Every detection launch shape (query threads 128 / 256 / 512, reduction warps 2 / 4 /
+    8) gives the same contacts bit for bit; the autotuner picks one of them and leaves the
+    state and the contacts as they were."""
+    fw = _fw()
+    sc = S.nut_bolt_scene(n_envs=24, seed=5)
+    w = fw.world_from_scene(sc)
+    for _ in range(2):
+        w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    s0 = [a.copy() for a in w.get_state()]
+    ref = None
+    for qt in (256, 128, 512):
+        for rw in (4, 2, 8):
+            w.set_detect_shape(qt, rw)
+            assert w.detect_shape() == (qt, rw)
+            w.collide()
+            got = [w.get_contacts(e) for e in range(sc.n_envs)]
+            if ref is None:
+                ref = got
+                assert sum(len(c) for c in ref) > 1000
+            else:
+                for a, b in zip(ref, got):
+                    assert a.tobytes() == b.tobytes(), (qt, rw)
+    qt, rw, ms = w.autotune_detect(trials=2)
+    assert qt in (128, 256, 512) and rw in (2, 4, 8) and ms > 0
+    assert w.detect_shape() == (qt, rw)
+    for a, b in zip(ref, [w.get_contacts(e) for e in range(sc.n_envs)]):
+        assert a.tobytes() == b.tobytes()
+    for a, b in zip(s0, w.get_state()):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(fw.FwError):
+        w.set_detect_shape(64, 4)
+    w.close()
