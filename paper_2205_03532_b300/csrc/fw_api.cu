@@ -90,7 +90,8 @@ struct fw_world {
     int *d_pcand_count = nullptr;
     PairMap *d_pmaps = nullptr;
     Row *d_prows = nullptr;
-    PileSolveMem pmem = {nullptr};
+    PileSolveMem pmem = {};
+    int pile_sweep_blocks = 0;   // blocks of the cooperative pile sweep kernel
     int pile_optin = 0;
     // differentiable rollout (fw_record_rollout .. fw_adjoint_rollout)
     DiffState diff;
@@ -271,7 +272,8 @@ void pile_free(fw_world *w) {
     dfree(w->d_piles); dfree(w->d_ppairs); dfree(w->d_pitems); dfree(w->d_pitem_range); dfree(w->d_pcounts);
     dfree(w->d_pcontacts); dfree(w->d_pccounts); dfree(w->d_pscratch); dfree(w->d_pcand); dfree(w->d_pcand_count);
     dfree(w->d_pmaps); dfree(w->d_prows);
-    dfree(w->pmem.color);
+    dfree(w->pmem.color); dfree(w->pmem.ab); dfree(w->pmem.rr); dfree(w->pmem.order); dfree(w->pmem.cstart);
+    dfree(w->pmem.ncol); dfree(w->pmem.bv); dfree(w->pmem.bw); dfree(w->pmem.bcom); dfree(w->pmem.bar);
 }
 
 // The pile buffers: every pile gets regions of the same size, from the largest pile's
@@ -323,6 +325,16 @@ fw_status pile_alloc(fw_world *w) {
     CK(cudaMalloc(&w->d_pcounts, sizeof(int2) * n));
     CK(cudaMalloc(&w->d_prows, sizeof(Row) * (size_t)n * rcap));
     CK(cudaMalloc(&w->pmem.color, np));
+    CK(cudaMalloc(&w->pmem.ab, sizeof(unsigned) * np));
+    CK(cudaMalloc(&w->pmem.rr, sizeof(unsigned) * np));
+    CK(cudaMalloc(&w->pmem.order, sizeof(int) * np));
+    CK(cudaMalloc(&w->pmem.cstart, sizeof(int) * n * (kMaxColors + 1)));
+    CK(cudaMalloc(&w->pmem.ncol, sizeof(int) * n));
+    const size_t nb = std::max<size_t>(w->props.size(), 1);
+    CK(cudaMalloc(&w->pmem.bv, sizeof(float4) * nb));
+    CK(cudaMalloc(&w->pmem.bw, sizeof(float4) * nb));
+    CK(cudaMalloc(&w->pmem.bcom, sizeof(float4) * nb));
+    CK(cudaMalloc(&w->pmem.bar, sizeof(unsigned)));
     // no pairs and no contacts until the first detection
     CK(cudaMemsetAsync(w->d_pcounts, 0, sizeof(int2) * n, w->stream));
     CK(cudaMemsetAsync(w->d_pccounts, 0, sizeof(int) * np, w->stream));
@@ -545,7 +557,9 @@ fw_status enqueue_substeps(fw_world *w, cudaStream_t s, int n_substeps, float hs
         if (detect && piles) CK(launch_reduce(q, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
         if (regular) CK(launch_solve(p, sh, s));
-        if (piles) CK(launch_pile_solve(q, w->d_piles, np, w->d_pcounts, w->pmem, w->d_prows, w->pile_smem, s));
+        if (piles)
+            CK(launch_pile_solve(q, w->d_piles, np, w->d_pcounts, w->pmem, w->d_prows, w->pile_smem,
+                                 w->pile_sweep_blocks, s));
         if (timed) CK(cudaEventRecord(take_event(w), s));
     }
     return FW_OK;
@@ -726,7 +740,7 @@ fw_status fw_create(const fw_config *cfg, fw_world **out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
     if (e == cudaSuccess) e = prepare_solve(optin, w->max_dyn_smem);
-    if (e == cudaSuccess) e = prepare_pile_solve(optin, &w->pile_optin);
+    if (e == cudaSuccess) e = prepare_pile_solve(optin, cfg->device, &w->pile_optin, &w->pile_sweep_blocks);
     if (e == cudaSuccess && w->max_dyn_smem[0] < (int)solve_smem_bytes(kLamCapMax)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1945,9 +1959,10 @@ fw_status fw_get_pile_pairs(fw_world *w, int env, int *pairs, int *colors, int c
 int fw_launches_per_step(fw_world *w, int n_substeps) {
     if (!w || n_substeps < 1) return 0;
     // per substep: envs of listed pairs -- the pairs' maps (per-sample generation only),
-    // query, reduction, solve; piles -- pair list, maps, query, reduction, pile solve
+    // query, reduction, solve; piles -- pair list, maps, query, reduction, the solve's prep
+    // and its cooperative sweeps (kernels only: the barrier reset is a memset)
     const int regular = w->n_regular > 0 ? (w->cfg.contact_gen == 0 ? 4 : 3) : 0;
-    return (regular + (w->piles.empty() ? 0 : 5)) * n_substeps;
+    return (regular + (w->piles.empty() ? 0 : 6)) * n_substeps;
 }
 
 const char *fw_last_error(const fw_world *w) {

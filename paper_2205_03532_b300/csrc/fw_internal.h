@@ -246,18 +246,29 @@ cudaError_t prepare_solve(int optin, int max_dyn[4]);
 SolveShape solve_shape(int n_envs, int lam_cap, int groups, int warps, const int max_dyn[4], int n_sm);
 cudaError_t launch_solve(const SimParams &p, const SolveShape &sh, cudaStream_t s);
 cudaError_t launch_normalize_quats(float *quat, int n, cudaStream_t s);
-// The pile solve's per-pair output kept for the API (global memory, one pile region each).
+// The pile solve's tables in global memory: prepared by one block per pile
+// (pile_prep_kernel), then read by the sweeps spread over the whole GPU (pile_sweep_kernel).
+// Per-pair arrays and `order` are in pile regions like the pair buffers.
 struct PileSolveMem {
     unsigned char *color;     // per pair: its colour in the last solve, 255 without rows
+    unsigned *ab, *rr;        // per pair: a | b << 16 (+ movable bits 15, 31), rows start | count << 21
+    int *order;               // the pairs with rows by colour
+    int *cstart;              // per pile: kMaxColors + 1 colour starts into `order`
+    int *ncol;                // per pile: colours used
+    float4 *bv, *bw, *bcom;   // per body (global id): velocity | inverse mass, angular velocity |
+                              // movable (1 or 0), centre of mass (world)
+    unsigned *bar;            // the sweep kernel's grid-barrier counter
 };
 // The pile solve keeps per-pair tables in shared memory: a pair's rows as start | count << 21
 // and pair indices as 16 bits, hence these limits on a pile's capacities.
 constexpr int kPileMaxRows = 1 << 21;
 constexpr int kPileMaxPairs = 65535;
 size_t pile_smem_bytes(int n_bodies, int pcap);
-cudaError_t prepare_pile_solve(int optin, int *max_dyn);   // *max_dyn: dynamic shared memory allowed
+// *max_dyn: the prep kernel's dynamic shared memory allowed; *sweep_blocks: blocks of the
+// cooperative sweep kernel (all resident at once) on `device`
+cudaError_t prepare_pile_solve(int optin, int device, int *max_dyn, int *sweep_blocks);
 cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
-                              const PileSolveMem &m, Row *rows, size_t smem, cudaStream_t s);
+                              const PileSolveMem &m, Row *rows, size_t smem, int sweep_blocks, cudaStream_t s);
 cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt);
 cudaError_t measure_l2_read(int device, long long bytes, int iters, float *gbs);
 

@@ -236,22 +236,19 @@ __device__ __forceinline__ void body_forces(const SimParams &p, int bi, int lb, 
     for (int k = 0; k < 6; ++k) B.Iinv[lb][k] = Ii[k];
 }
 
-// 4. of a substep for body bi: |omega| clamp, semi-implicit Euler of the centre of mass and
-// q <- normalize(q + hs/2 (omega, 0) q); writes the position and returns the new
+// 4. of a substep for body bi (constants P) from its velocity v, angular velocity w and
+// centre of mass com: |omega| clamp (w is updated), semi-implicit Euler of the centre of
+// mass and q <- normalize(q + hs/2 (omega, 0) q); writes the position and returns the new
 // quaternion (a static body keeps its own); a non-finite result sets the status bit.
-template <class BS>
-__device__ __forceinline__ float4 body_integrate(const SimParams &p, int bi, int lb, float hs, BS &B) {
-    const BodyProps P = p.props[bi];
+__device__ __forceinline__ float4 integrate_core(const SimParams &p, const BodyProps &P, int bi, float hs, V3 &w,
+                                                 V3 v, V3 com_now) {
     float4 q = make_float4(p.quat[4 * bi], p.quat[4 * bi + 1], p.quat[4 * bi + 2], p.quat[4 * bi + 3]);
     if (P.type == FW_BODY_STATIC) return q;
-    V3 w = smv(B.w, lb);
-    const V3 v = smv(B.v, lb);
     if ((P.type == FW_BODY_DYNAMIC || P.type == FW_BODY_FIXED_AXIS) && p.max_angvel > 0.0f) {
         const float wn = sqrtf(dot(w, w));
         if (wn > p.max_angvel) w = (p.max_angvel / wn) * w;
-        smv_set(B.w, lb, w);
     }
-    const V3 com = smv(B.com, lb) + hs * v;
+    const V3 com = com_now + hs * v;
     // dq = (omega, 0) (x) q
     const float dx = q.w * w.x + w.y * q.z - w.z * q.y;
     const float dy = q.w * w.y + w.z * q.x - w.x * q.z;
@@ -267,6 +264,16 @@ __device__ __forceinline__ float4 body_integrate(const SimParams &p, int bi, int
     const bool bad = !(isfinite(pos.x) && isfinite(pos.y) && isfinite(pos.z) && isfinite(q.x) && isfinite(q.y) &&
                        isfinite(q.z) && isfinite(q.w));
     if (bad) atomicOr(p.status, kStatusNonFinite);
+    return q;
+}
+
+// integrate_core for body bi in slot lb of a body store
+template <class BS>
+__device__ __forceinline__ float4 body_integrate(const SimParams &p, int bi, int lb, float hs, BS &B) {
+    const BodyProps P = p.props[bi];
+    V3 w = smv(B.w, lb);
+    const float4 q = integrate_core(p, P, bi, hs, w, smv(B.v, lb), smv(B.com, lb));
+    if (P.type != FW_BODY_STATIC) smv_set(B.w, lb, w);
     return q;
 }
 
@@ -998,48 +1005,7 @@ __device__ int pile_scan(int v, int *warp_sums, int &total) {
     return before + incl - v;
 }
 
-// A row's cache lines into L1 ahead of its use (a row is 240 bytes: two or three lines).
-__device__ __forceinline__ void prefetch_row_l1(const Row *R) {
-    const char *c = reinterpret_cast<const char *>(R);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(c));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(c + 128));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(c + 4 * kRowF4 * 4 - 16));
-}
-
-// The rows r0 .. r1 - 1 of one pair (bodies a, b) in order: the bodies' velocities stay in
-// registers for the pair (no other thread touches a movable one while the colour runs),
-// each row's 60 words are loaded while the row before it is solved, and the lines of the
-// rows two and three ahead are fetched into L1; the impulses go back into the rows.  The
-// same updates as gs_row row by row.
-template <bool kBias>
-__device__ __forceinline__ void pile_pair(Row *rows, int r0, int r1, int a, int b, PileBodies &B) {
-    if (r0 >= r1) return;
-    V3 va = smv(B.v, a), wa = smv(B.w, a), vb = smv(B.v, b), wb = smv(B.w, b);
-    const float ima = B.invm[a], imb = B.invm[b];
-    float f[4 * kRowF4], g[4 * kRowF4];
-    if (r0 + 1 < r1) prefetch_row_l1(rows + r0 + 1);
-    if (r0 + 2 < r1) prefetch_row_l1(rows + r0 + 2);
-    load_row_words(rows + r0, f);
-    auto solve = [&](int r, const float (&x)[4 * kRowF4]) {
-        float4 L = make_float4(x[kWLN], x[kWLN + 1], x[kWLN + 2], 0.0f);
-        gs_core(x, L, va, wa, vb, wb, ima, imb, kBias);
-        float *w = reinterpret_cast<float *>(rows + r);
-        w[kWLN] = L.x; w[kWLN + 1] = L.y; w[kWLN + 2] = L.z;
-    };
-    for (int r = r0; r < r1; r += 2) {
-        if (r + 3 < r1) prefetch_row_l1(rows + r + 3);
-        if (r + 1 < r1) load_row_words(rows + r + 1, g);
-        solve(r, f);
-        if (r + 1 >= r1) break;
-        if (r + 4 < r1) prefetch_row_l1(rows + r + 4);
-        if (r + 2 < r1) load_row_words(rows + r + 2, f);
-        solve(r + 1, g);
-    }
-    if (B.writes(a)) { smv_set(B.v, a, va); smv_set(B.w, a, wa); }
-    if (B.writes(b)) { smv_set(B.v, b, vb); smv_set(B.w, b, wb); }
-}
-
-// Per-pair tables of the pile solve in shared memory (see pile_smem_bytes).
+// Per-pair tables of the pile prep in shared memory (see pile_smem_bytes).
 struct PileTables {
     unsigned *ab;             // local ids a | b << 16, bit 15 / 31 set when a / b is movable
     unsigned *rr;             // rows: start | count << 21 (within the pile's row region)
@@ -1047,26 +1013,6 @@ struct PileTables {
     unsigned char *col;       // colour, 254 before colouring, 255 without rows
 };
 constexpr unsigned kAbId = 0x3FFu;   // local ids are below kMaxPileBodies = 1024
-
-template <bool kBias>
-__device__ void pile_sweeps(PileBodies &B, Row *prow, const PileTables &T, const int *cstart, int n_colors,
-                            int n_sweeps) {
-    for (int it = 0; it < n_sweeps; ++it) {
-        for (int c = 0; c < n_colors; ++c) {
-            const bool serial = c == kMaxColors - 1;
-            if (!serial || threadIdx.x == 0) {
-                const int step = serial ? 1 : (int)blockDim.x;
-                for (int k = cstart[c] + (serial ? 0 : (int)threadIdx.x); k < cstart[c + 1]; k += step) {
-                    const int q = T.order[k];
-                    const unsigned rr = T.rr[q], ab = T.ab[q];
-                    const int r0 = (int)(rr & (kPileMaxRows - 1));
-                    pile_pair<kBias>(prow, r0, r0 + (int)(rr >> 21), (int)(ab & kAbId), (int)((ab >> 16) & kAbId), B);
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
 
 constexpr int kPileThreads = 384;
 
@@ -1101,8 +1047,11 @@ __device__ void pile_colour_warp(const PileTables &T, unsigned long long *used, 
     }
 }
 
-__global__ void __launch_bounds__(kPileThreads, 1) pile_solve_kernel(SimParams p, const PileDev *piles,
-                                                                      const int2 *counts, PileSolveMem M, Row *rows) {
+// The pile solve, part 1 (one block per pile): external forces, each pair's rows placed
+// and built, the colours and the pairs by colour; hands the tables and the bodies' state to
+// the sweep kernel through PileSolveMem.
+__global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p, const PileDev *piles,
+                                                                     const int2 *counts, PileSolveMem M, Row *rows) {
     extern __shared__ __align__(16) float pile_smem[];
     __shared__ int warp_sums[32];
     __shared__ int cstart[kMaxColors + 1];
@@ -1189,6 +1138,8 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_solve_kernel(SimParams p
             atomicMax(&s_colors, c + 1);
         }
         M.color[P.pair0 + q] = (unsigned char)c;
+        M.ab[P.pair0 + q] = T.ab[q];
+        M.rr[P.pair0 + q] = T.rr[q];
     }
     __syncthreads();
     if (t == 0) {
@@ -1201,34 +1152,206 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_solve_kernel(SimParams p
     __syncthreads();
     for (int q = t; q < np; q += NT) {
         const int c = T.col[q];
-        if (c != 255 && c != kMaxColors - 1) T.order[atomicAdd(&fill[c], 1)] = (unsigned short)q;
+        if (c != 255 && c != kMaxColors - 1) M.order[P.pair0 + atomicAdd(&fill[c], 1)] = q;
     }
-    // the last colour's pairs may share bodies: one thread sweeps them, in pair order
+    // the last colour's pairs may share bodies: one warp sweeps them, in pair order
     if (t == 0 && s_colors == kMaxColors) {
         int k = cstart[kMaxColors - 1];
         for (int q = 0; q < np; ++q)
-            if (T.col[q] == kMaxColors - 1) T.order[k++] = (unsigned short)q;
+            if (T.col[q] == kMaxColors - 1) M.order[P.pair0 + k++] = q;
     }
-    __syncthreads();
-    const int n_colors = s_colors;
-    // 5. Gauss-Seidel sweeps, colour by colour
-    pile_sweeps<true>(B, prow, T, cstart, n_colors, p.n_iters);
-    // 6. integration
+    for (int c = t; c <= kMaxColors; c += NT) M.cstart[blockIdx.x * (kMaxColors + 1) + c] = cstart[c];
+    if (t == 0) M.ncol[blockIdx.x] = s_colors;
+    // 5. the bodies' state after the forces, for the sweeps
     for (int lb = t; lb < n; lb += NT) {
         const int bi = P.first_body + lb;
-        const float4 q = body_integrate(p, bi, lb, hs, B);
-        p.quat[4 * bi] = q.x; p.quat[4 * bi + 1] = q.y; p.quat[4 * bi + 2] = q.z; p.quat[4 * bi + 3] = q.w;
+        M.bv[bi] = make_float4(B.v[lb][0], B.v[lb][1], B.v[lb][2], B.invm[lb]);
+        M.bw[bi] = make_float4(B.w[lb][0], B.w[lb][1], B.w[lb][2], mov[lb] ? 1.0f : 0.0f);
+        M.bcom[bi] = make_float4(B.com[lb][0], B.com[lb][1], B.com[lb][2], 0.0f);
+    }
+}
+
+// ---- the pile solve, part 2: one cooperative kernel over the whole GPU
+constexpr int kSweepWarps = 8;                      // warps per block of the sweep kernel
+constexpr int kSweepChunk = 16;                     // rows per shared-memory chunk of a pair
+constexpr int kSweepBufF4 = 2 * kSweepChunk * kRowF4;   // two chunks per warp
+constexpr int kGridWaitTries = 1 << 22;             // bounded grid-barrier polls (64 ns sleeps)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *a) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float4 ldcg4(const float4 *a) { return __ldcg(a); }
+
+// Barrier of every block of the (cooperative) launch: block barrier, then thread 0 makes
+// the block's writes visible at device scope, arrives and waits (bounded) until `target`
+// blocks have arrived.  A wait that gives up sets the timeout status; the block then stops
+// waiting at later barriers (it only arrives), so that the launch always ends.
+__device__ void grid_barrier(unsigned *bar, unsigned target, unsigned *status, int *dead) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        if (!*dead) {
+            int tries = 0;
+            while (ld_acquire_gpu(bar) < target) {
+                if (++tries > kGridWaitTries) {
+                    atomicOr(status, kStatusTimeout);
+                    *dead = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
     }
     __syncthreads();
+}
+
+// The rows r0 .. r0 + n - 1 (global) of one pair between global bodies ga, gb, by one warp:
+// the lanes stream the rows through two shared-memory chunks of kSweepChunk rows (cp.async,
+// L2 only: the impulses were written by other SMs), lane 0 runs the Gauss-Seidel chain over
+// them with the bodies' velocities in registers (gs_core, the same update as gs_row) and
+// writes the impulses back; the velocities go back to global memory at the end (movable
+// bodies only).  Called by all 32 lanes.
+template <bool kBias>
+__device__ void sweep_pair_warp(const Row *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M,
+                                int lane) {
+    const float4 *src = reinterpret_cast<const float4 *>(rows);
+    const int nch = (n + kSweepChunk - 1) / kSweepChunk;
+    auto issue = [&](int ch) {
+        const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
+        float4 *dst = buf + (ch & 1) * kSweepChunk * kRowF4;
+        const float4 *s0 = src + (size_t)ch * kSweepChunk * kRowF4;
+        for (int k = lane; k < rows_in * kRowF4; k += 32) cp_async16(dst + k, s0 + k);
+        cp_async_commit();
+    };
+    V3 va, wa, vb, wb;
+    float ima = 0.f, imb = 0.f;
+    bool ma = false, mb = false;
+    if (lane == 0) {
+        const float4 a0 = ldcg4(M.bv + ga), a1 = ldcg4(M.bw + ga), b0 = ldcg4(M.bv + gb), b1 = ldcg4(M.bw + gb);
+        va = v3(a0.x, a0.y, a0.z); ima = a0.w; wa = v3(a1.x, a1.y, a1.z); ma = a1.w != 0.0f;
+        vb = v3(b0.x, b0.y, b0.z); imb = b0.w; wb = v3(b1.x, b1.y, b1.z); mb = b1.w != 0.0f;
+    }
+    issue(0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) {
+            issue(ch + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const float4 *cb = buf + (ch & 1) * kSweepChunk * kRowF4;
+            const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
+            auto load = [&](int r, float (&x)[4 * kRowF4]) {
+#pragma unroll
+                for (int k = 0; k < kRowF4; ++k) {
+                    const float4 v = cb[r * kRowF4 + k];
+                    x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+                }
+            };
+            auto solve = [&](int r, const float (&x)[4 * kRowF4]) {
+                float4 L = make_float4(x[kWLN], x[kWLN + 1], x[kWLN + 2], 0.0f);
+                gs_core(x, L, va, wa, vb, wb, ima, imb, kBias);
+                float *w = reinterpret_cast<float *>(const_cast<Row *>(rows) + ch * kSweepChunk + r);
+                w[kWLN] = L.x; w[kWLN + 1] = L.y; w[kWLN + 2] = L.z;
+            };
+            // the next row's words are read while one row is solved
+            float f[4 * kRowF4], g[4 * kRowF4];
+            load(0, f);
+            for (int r = 0; r < rows_in; r += 2) {
+                if (r + 1 < rows_in) load(r + 1, g);
+                solve(r, f);
+                if (r + 1 >= rows_in) break;
+                if (r + 2 < rows_in) load(r + 2, f);
+                solve(r + 1, g);
+            }
+        }
+        __syncwarp();   // the chunk's buffer is refilled two chunks later
+    }
+    if (lane == 0) {
+        if (ma) { M.bv[ga] = make_float4(va.x, va.y, va.z, ima); M.bw[ga] = make_float4(wa.x, wa.y, wa.z, 1.0f); }
+        if (mb) { M.bv[gb] = make_float4(vb.x, vb.y, vb.z, imb); M.bw[gb] = make_float4(wb.x, wb.y, wb.z, 1.0f); }
+    }
+}
+
+// n_sweeps Gauss-Seidel sweeps over every pile, colour by colour with a grid barrier after
+// each colour: within a colour the launch's warps take the pairs (any order: they share no
+// movable body); the last colour, whose pairs may share bodies, is swept by warp 0 of the
+// launch in pair order.
+template <bool kBias>
+__device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int n_piles, const PileSolveMem &M,
+                                  Row *rows, float4 *buf, int n_colors, int n_sweeps, unsigned &nbar, int *dead) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kSweepWarps + (threadIdx.x >> 5), W = gridDim.x * kSweepWarps;
+    for (int it = 0; it < n_sweeps; ++it) {
+        for (int c = 0; c < n_colors; ++c) {
+            const bool serial = c == kMaxColors - 1;
+            for (int k0 = 0; k0 < n_piles; ++k0) {
+                const PileDev &P = piles[k0];
+                const int *cs = M.cstart + k0 * (kMaxColors + 1);
+                const int b = cs[c], e = cs[c + 1];
+                if (serial && gw != 0) continue;
+                for (int k = b + (serial ? 0 : gw); k < e; k += serial ? 1 : W) {
+                    const int q = M.order[P.pair0 + k];
+                    const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
+                    const int r0 = (int)(rr & (kPileMaxRows - 1)), nr = (int)(rr >> 21);
+                    sweep_pair_warp<kBias>(rows + P.row0 + r0, nr, P.first_body + (int)(ab & kAbId),
+                                           P.first_body + (int)((ab >> 16) & kAbId), buf, M, lane);
+                }
+            }
+            ++nbar;
+            grid_barrier(M.bar, nbar * gridDim.x, p.status, dead);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimParams p, const PileDev *piles,
+                                                                          int n_piles, PileSolveMem M, Row *rows) {
+    extern __shared__ __align__(16) float4 sweep_smem[];
+    __shared__ int dead;
+    if (threadIdx.x == 0) dead = 0;
+    __syncthreads();
+    float4 *buf = sweep_smem + (threadIdx.x >> 5) * kSweepBufF4;
+    int n_colors = 0;
+    for (int k = 0; k < n_piles; ++k) n_colors = max(n_colors, M.ncol[k]);
+    unsigned nbar = 0;
+    const float hs = p.hs;
+    // 5. Gauss-Seidel sweeps
+    pile_sweep_passes<true>(p, piles, n_piles, M, rows, buf, n_colors, p.n_iters, nbar, &dead);
+    // 6. integration, a thread per body
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, GT = gridDim.x * blockDim.x;
+    for (int k = 0; k < n_piles; ++k) {
+        const PileDev &P = piles[k];
+        for (int lb = gt; lb < P.n_bodies; lb += GT) {
+            const int bi = P.first_body + lb;
+            const BodyProps Pb = p.props[bi];
+            const float4 v4 = ldcg4(M.bv + bi), w4 = ldcg4(M.bw + bi), c4 = ldcg4(M.bcom + bi);
+            V3 w = v3(w4.x, w4.y, w4.z);
+            const float4 q = integrate_core(p, Pb, bi, hs, w, v3(v4.x, v4.y, v4.z), v3(c4.x, c4.y, c4.z));
+            p.quat[4 * bi] = q.x; p.quat[4 * bi + 1] = q.y; p.quat[4 * bi + 2] = q.z; p.quat[4 * bi + 3] = q.w;
+            if (Pb.type != FW_BODY_STATIC) M.bw[bi] = make_float4(w.x, w.y, w.z, w4.w);
+        }
+    }
+    ++nbar;
+    grid_barrier(M.bar, nbar * gridDim.x, p.status, &dead);
     // 7. optional bias-free sweeps
-    if (p.n_vel_iters > 0) pile_sweeps<false>(B, prow, T, cstart, n_colors, p.n_vel_iters);
-    for (int lb = t; lb < n; lb += NT) {
-        const int bi = P.first_body + lb;
-        const V3 v = smv(B.v, lb), w = smv(B.w, lb);
-        st3(p.linvel + 3 * bi, v);
-        st3(p.angvel + 3 * bi, w);
-        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z)))
-            atomicOr(p.status, kStatusNonFinite);
+    if (p.n_vel_iters > 0) pile_sweep_passes<false>(p, piles, n_piles, M, rows, buf, n_colors, p.n_vel_iters, nbar, &dead);
+    for (int k = 0; k < n_piles; ++k) {
+        const PileDev &P = piles[k];
+        for (int lb = gt; lb < P.n_bodies; lb += GT) {
+            const int bi = P.first_body + lb;
+            const float4 v4 = ldcg4(M.bv + bi), w4 = ldcg4(M.bw + bi);
+            const V3 v = v3(v4.x, v4.y, v4.z), w = v3(w4.x, w4.y, w4.z);
+            st3(p.linvel + 3 * bi, v);
+            st3(p.angvel + 3 * bi, w);
+            if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z)))
+                atomicOr(p.status, kStatusNonFinite);
+        }
     }
 }
 
@@ -1256,19 +1379,47 @@ size_t pile_smem_bytes(int n_bodies, int pcap) {
     return (size_t)n_bodies * (16 * sizeof(float) + sizeof(unsigned long long) + 1) + (size_t)pcap * 11 + 16;
 }
 
-cudaError_t prepare_pile_solve(int optin, int *max_dyn) {
+cudaError_t prepare_pile_solve(int optin, int device, int *max_dyn, int *sweep_blocks) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, pile_solve_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&a, pile_prep_kernel);
     if (e != cudaSuccess) return e;
     *max_dyn = optin - (int)a.sharedSizeBytes;
-    return cudaFuncSetAttribute(pile_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+    e = cudaFuncSetAttribute(pile_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dyn);
+    if (e != cudaSuccess) return e;
+    const int smem = kSweepWarps * kSweepBufF4 * (int)sizeof(float4);
+    e = cudaFuncSetAttribute(pile_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, n_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pile_sweep_kernel, kSweepWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    // one block per SM (eight warps each: more warps than any colour of a 1,024-body pile has
+    // pairs), every block resident at once (the launch is cooperative); fewer blocks make the
+    // grid barriers cheaper
+    *sweep_blocks = per_sm * n_sm;
+    return *sweep_blocks > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
 cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
-                              const PileSolveMem &m, Row *rows, size_t smem, cudaStream_t s) {
+                              const PileSolveMem &m, Row *rows, size_t smem, int sweep_blocks, cudaStream_t s) {
     if (n_piles <= 0) return cudaSuccess;
-    pile_solve_kernel<<<n_piles, kPileThreads, smem, s>>>(p, piles, counts, m, rows);
-    return cudaGetLastError();
+    pile_prep_kernel<<<n_piles, kPileThreads, smem, s>>>(p, piles, counts, m, rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(m.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sweep_blocks);
+    cfg.blockDim = dim3(kSweepWarps * 32);
+    cfg.dynamicSmemBytes = kSweepWarps * kSweepBufF4 * sizeof(float4);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pile_sweep_kernel, p, piles, n_piles, m, rows);
 }
 
 template <int kGroups>

@@ -65,8 +65,8 @@ def test_env_info_and_launch_count(heap64):
     fb, nb, fp, np_ = gw.env_info(0)
     assert (fb, nb, fp, np_) == (0, 65, -1, -1)
     assert gw.counts() == (1, 65, 0)
-    # per substep: pair list, maps, query, reduction, pile solve
-    assert gw.launches_per_step(4) == 20
+    # per substep: pair list, maps, query, reduction, the pile solve's prep and sweeps
+    assert gw.launches_per_step(4) == 24
 
 
 def test_pair_list_matches_oracle(heap64):
