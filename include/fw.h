@@ -455,6 +455,16 @@ FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_
  * breaks every tie by depth and sample.  Errors: FW_ERR_ARG for other values.
  * fw_get_detect_shape returns the shape in use. */
 FW_API fw_status fw_set_detect_shape(fw_world *w, int query_threads, int reduce_warps);
+
+/* Test hook of failure detection (no counterpart in the paper): makes one of the kernels'
+ * bounded device waits run out, as a lost copy or a missing block would.  what = 1: every
+ * grid barrier of the pile sweep kernel waits for one more block than the launch has;
+ * what = 2: the fast solve's row stream issues no chunk copy, so the waits for its chunks
+ * see no arrival.  Each wait gives up after a bounded number of polls (about a second for a
+ * grid barrier, tens of milliseconds for a chunk), sets the timeout status and the
+ * kernel ends (its results are then meaningless); the next synchronising call returns
+ * FW_ERR_TIMEOUT and the world stays usable.  0 (default) turns it off. */
+FW_API fw_status fw_test_stall(fw_world *w, int what);
 FW_API fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduce_warps);
 /* Autotuner of that shape: at the current poses, runs one detection, then times `trials`
  * query launches for each query size (with 4 reduction warps), and `trials` reduction

@@ -75,6 +75,7 @@ struct fw_world {
     int solve_groups = 0, solve_warps = 0;
     int lam_rows = 0;   // rows per env whose impulses the solve keeps in shared memory (0: every row)
     int query_threads = 0, reduce_warps = 0;   // detection launch shape (0: the defaults)
+    int stall = 0;                             // fw_test_stall
     // pile envs (fw_add_pile): one region per pile in each pile buffer, every region of the
     // same size (pile_pcap pairs, pile_icap items, pile_rcap rows)
     std::vector<PileDev> piles;
@@ -448,6 +449,7 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     }
     p.tri_iters = w->cfg.tri_iters;
     p.query_threads = w->query_threads;
+    p.stall = w->stall;
     p.reduce_warps = w->reduce_warps;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;
@@ -518,10 +520,11 @@ fw_status check_status(fw_world *w) {
     CK(cudaMemcpy(&st, w->d_status, sizeof st, cudaMemcpyDeviceToHost));
     if (st) {
         CK(cudaMemsetAsync(w->d_status, 0, sizeof st, w->stream));
+        // a wait that gave up comes first: the garbage it leaves may also be non-finite
+        if (st & kStatusTimeout) return fail(w, FW_ERR_TIMEOUT, "a bounded device wait gave up");
         if (st & kStatusNonFinite) return fail(w, FW_ERR_NONFINITE, "a body state became non-finite");
         if (st & kStatusOverflow) return fail(w, FW_ERR_OVERFLOW, "a pair produced more contacts, or a pile more pairs or contact rows, than fit");
         if (st & kStatusBounds) return fail(w, FW_ERR_DEVICE_BOUNDS, "device index check failed");
-        if (st & kStatusTimeout) return fail(w, FW_ERR_TIMEOUT, "a bounded device wait gave up");
     }
     return FW_OK;
 }
@@ -1635,6 +1638,14 @@ fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials
     if (envs_per_warp) *envs_per_warp = bg;
     if (warps_per_block) *warps_per_block = bw;
     if (best_ms) *best_ms = best;
+    return FW_OK;
+}
+
+fw_status fw_test_stall(fw_world *w, int what) {
+    if (!w) return FW_ERR_ARG;
+    if (what < 0 || what > 2) return fail(w, FW_ERR_ARG, "fw_test_stall: 0, 1 or 2");
+    if (w->stall != what) drop_graph(w);
+    w->stall = what;
     return FW_OK;
 }
 

@@ -171,6 +171,9 @@ struct SimParams {
     int broad_phase;                       // some env has several pairs: skip pairs far apart
     int query_threads;                     // per-sample query CTA size (128, 256, 512; 0: 256)
     int reduce_warps;                      // reduction warps per pair (2, 4, 8; 0: 4)
+    int stall;                             // test hook (fw_test_stall): 1 the pile sweeps' grid
+                                           // barriers wait for one block too many, 2 the
+                                           // solve's row stream issues no copy
     int tri_iters;                         // descent steps per triangle
 };
 

@@ -547,6 +547,7 @@ struct RowStream {
     int ib;               // buffer of the next chunk to issue (seq mod kChunkBufs)
     bool leader;          // lane 0 of the group
     bool on;              // issuing (cleared after a wait gave up)
+    int seq_on;           // chunks issued while on (only those complete their phases)
 };
 
 __device__ __forceinline__ void issue_chunk(RowStream &rs) {
@@ -559,6 +560,7 @@ __device__ __forceinline__ void issue_chunk(RowStream &rs) {
     } else if (rs.nr > 0) {
         rs.pf = (rs.pf + kChunk) % rs.nr;
     }
+    if (rs.on) rs.seq_on = rs.seq + 1;
     ++rs.seq;
     rs.ib = rs.ib + 1 == kChunkBufs ? 0 : rs.ib + 1;
 }
@@ -731,7 +733,7 @@ __device__ bool sweep_fast(RowStream &rs, int total, int trips, float4 *lam, V3 
     // normally every issued chunk has been waited for; after a wait gave up, wait (bounded)
     // for the copies issued after it, so that none lands after the kernel has moved on
     const bool all_ok = __all_sync(0xffffffffu, ok);
-    for (int k = done; k < rs.seq; ++k) mbar_wait(rs.bar + 8u * (k % kChunkBufs), (unsigned)((k / kChunkBufs) & 1));
+    for (int k = done; k < rs.seq_on; ++k) mbar_wait(rs.bar + 8u * (k % kChunkBufs), (unsigned)((k / kChunkBufs) & 1));
     __syncwarp();
     return all_ok;
 }
@@ -912,9 +914,10 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     rs.nr = run_fast ? nr : 0;
     rs.pf = 0;
     rs.seq = 0;
+    rs.seq_on = 0;
     rs.ib = 0;
     rs.leader = gl == 0;
-    rs.on = true;
+    rs.on = p.stall != 2;   // test hook: no chunk is issued, so its wait runs out
     bool waits_ok = true;
     {
         const int total = run_fast ? nr * p.n_iters : 0;
@@ -1175,7 +1178,7 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p,
 constexpr int kSweepWarps = 8;                      // warps per block of the sweep kernel
 constexpr int kSweepChunk = 16;                     // rows per shared-memory chunk of a pair
 constexpr int kSweepBufF4 = 2 * kSweepChunk * kRowF4;   // two chunks per warp
-constexpr int kGridWaitTries = 1 << 22;             // bounded grid-barrier polls (64 ns sleeps)
+constexpr int kGridWaitTries = 1 << 20;             // bounded grid-barrier polls (about a second)
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *a) {
     unsigned v;
@@ -1305,7 +1308,7 @@ __device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int 
                 }
             }
             ++nbar;
-            grid_barrier(M.bar, nbar * gridDim.x, p.status, dead);
+            grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, dead);
         }
     }
 }
@@ -1338,7 +1341,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimPara
         }
     }
     ++nbar;
-    grid_barrier(M.bar, nbar * gridDim.x, p.status, &dead);
+    grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, &dead);
     // 7. optional bias-free sweeps
     if (p.n_vel_iters > 0) pile_sweep_passes<false>(p, piles, n_piles, M, rows, buf, n_colors, p.n_vel_iters, nbar, &dead);
     for (int k = 0; k < n_piles; ++k) {

@@ -31,6 +31,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_step_bwd", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info", "fw_add_pile",
                  "fw_get_pile_pairs", "fw_set_detect_shape", "fw_get_detect_shape", "fw_autotune_detect",
+                 "fw_test_stall",
                  "fw_launches_per_step",
                  "fw_last_error", "fw_measure_l2_read"]
 
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "fw_add_pile": (st, [vp, vp, i, i, i, C.POINTER(i)]),
         "fw_get_pile_pairs": (st, [vp, i, vp, vp, i, C.POINTER(i)]),
         "fw_set_detect_shape": (st, [vp, i, i]),
+        "fw_test_stall": (st, [vp, i]),
         "fw_get_detect_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
         "fw_autotune_detect": (st, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_float)]),
         "fw_step": (st, [vp, i, i]),
@@ -387,6 +389,10 @@ class World:
         self._check(self.lib.fw_autotune_solve(self.h, n_substeps, n_iters, trials, C.byref(g), C.byref(w),
                                                C.byref(ms)))
         return g.value, w.value, ms.value
+
+    def test_stall(self, what: int):
+        """test hook: 1 pile grid barriers, 2 solve chunk waits run out (bounded)"""
+        self._check(self.lib.fw_test_stall(self.h, what))
 
     def set_detect_shape(self, query_threads: int = 0, reduce_warps: int = 0):
         self._check(self.lib.fw_set_detect_shape(self.h, query_threads, reduce_warps))

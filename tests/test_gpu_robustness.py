@@ -149,3 +149,61 @@ def test_env_info_locates_bodies_of_uneven_env_groups():
         w.env_info(5)
     assert _status(e) == ERR_ARG
     w.close()
+
+
+def test_a_solve_chunk_wait_that_runs_out_is_reported_and_the_world_recovers():
+    """Failure detection on the device without a fault: with the test hook, the solve's row
+    stream issues no chunk copy, so its first bounded mbarrier wait sees no arrival and gives
+    up (after 2^20 polls, tens of milliseconds).  The kernel ends, the next synchronising call reports
+    FW_ERR_TIMEOUT, and once the hook is off the same world steps on as a fresh one does."""
+    import time
+    fw = _fw()
+    sc = S.nut_bolt_scene(n_envs=4, seed=2)
+    w = fw.world_from_scene(sc)
+    ref = fw.world_from_scene(sc)
+    s0 = [a.copy() for a in w.get_state()]
+    w.test_stall(2)
+    t0 = time.time()
+    w.step(1, 8)
+    with pytest.raises(fw.FwError) as e:
+        w.sync()
+    assert _status(e) == -7 and "wait" in str(e.value)
+    assert time.time() - t0 < 30
+    w.test_stall(0)
+    w.set_state(*s0)       # (set_state normalises the quaternions: the reference takes it too)
+    ref.set_state(*s0)
+    w.step(1, 8)
+    ref.step(1, 8)
+    for a, b in zip(w.get_state(), ref.get_state()):
+        np.testing.assert_array_equal(a, b)
+    w.close()
+    ref.close()
+
+
+def test_a_pile_grid_barrier_that_runs_out_is_reported_and_the_world_recovers():
+    """The pile sweep kernel's grid barrier with the test hook waits for one block more than
+    the cooperative launch has: every block gives up after about a second, stops waiting at
+    the later barriers, and the launch ends; FW_ERR_TIMEOUT is reported and the world steps
+    on afterwards."""
+    import time
+    fw = _fw()
+    sc = S.nut_pile_env_scene(12, seed=3, mode="heap", n_samples=2000, sdf_res=64, plate_sdf_res=64)
+    w = fw.world_from_scene(sc)
+    ref = fw.world_from_scene(sc)
+    s0 = [a.copy() for a in w.get_state()]
+    w.test_stall(1)
+    t0 = time.time()
+    w.step(1, 4)
+    with pytest.raises(fw.FwError) as e:
+        w.sync()
+    assert _status(e) == -7
+    assert time.time() - t0 < 30
+    w.test_stall(0)
+    w.set_state(*s0)
+    ref.set_state(*s0)
+    w.step(1, 4)
+    ref.step(1, 4)
+    for a, b in zip(w.get_state(), ref.get_state()):
+        np.testing.assert_array_equal(a, b)
+    w.close()
+    ref.close()
