@@ -30,13 +30,15 @@ sys.path.insert(0, ROOT)
 # (SUBSTEP_SOURCES) it was taken on; reported only while they are unchanged (profiles/
 # holds the capture).
 NCU_TRAFFIC = {
-    # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the middle of the
-    # bench's timed frames, replayed by its per-kernel timing pass)
-    "c5ebc7c9e1f4c82d": {"query_kernel": 32.08e6, "reduce_kernel": 81.44e6, "solve_kernel": 94.53e6},
+    # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the bench's default
+    # command, launches in its end-to-end pass over the timed frames' state)
+    "a9c21361244c5130": {"map_kernel": 0.12e6, "query_kernel": 16.84e6, "reduce_kernel": 53.05e6,
+                         "solve_kernel": 59.16e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "c5ebc7c9e1f4c82d": {"query_kernel": 593.7e6, "reduce_kernel": 293.9e6, "solve_kernel": 4305.0e6},
+    "a9c21361244c5130": {"map_kernel": 1.05e6, "query_kernel": 544.5e6, "reduce_kernel": 209.2e6,
+                         "solve_kernel": 2832.8e6},
 }
 
 FP32_LANES_PER_SM = 128
@@ -50,10 +52,11 @@ BRICK_ENTRY_BYTES = 4                 # brick-table entry read per lookup (narro
 CONTACT_BYTES = 64                    # reduced contact (32 B) + its winner scratch line (32 B)
 
 
-# the files that make up the substep kernels (query, reduction, solve) and their launches;
-# the traffic tables are keyed by the hash of these files (comments removed) and of their
-# compile flags
-SUBSTEP_SOURCES = ("fw_api.cu", "fw_detect.cu", "fw_solve.cu", "fw_device.cuh", "fw_internal.h")
+# the files that make up the substep kernels (map, query, reduction, solve); the traffic
+# tables are keyed by the hash of these files (comments removed) and of their compile flags.
+# The launch shapes the host code picks are part of the bench line (solve_shape,
+# detect_shape), not of the key.
+SUBSTEP_SOURCES = ("fw_detect.cu", "fw_solve.cu", "fw_device.cuh", "fw_internal.h")
 
 
 def _code_only(text: str) -> str:
@@ -346,8 +349,8 @@ def run_fw(args):
     tuned = None
     detect_tuned = None
     if shape == [0, 0] and not args.no_autotune:
-        tuned = w.autotune_solve(sim.n_substeps, sim.n_iters, trials=3)
-        detect_tuned = w.autotune_detect(trials=3)
+        tuned = w.autotune_solve(sim.n_substeps, sim.n_iters, trials=6)
+        detect_tuned = w.autotune_detect(trials=6)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup - pre):
             one_step()

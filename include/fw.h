@@ -440,7 +440,8 @@ FW_API fw_status fw_set_solve_shape(fw_world *w, int envs_per_warp, int warps_pe
 /* Autotuner of that shape: at the current state, runs detection once for n_substeps /
  * n_iters, then times `trials` solve launches for every shape that fits (envs per warp
  * 1, 2, 4, 8 x warps per block 1..4), restoring the body state before each, and keeps
- * the fastest (as fw_set_solve_shape would).  The state is left as it was.  Returns the
+ * the fastest (as fw_set_solve_shape would; a shape tried later must beat the best so far
+ * by more than 1%).  The state is left as it was.  Returns the
  * chosen shape and its time per solve launch (ms); any output pointer may be NULL.
  * Allocates and frees one state-sized device buffer; synchronises. */
 FW_API fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials, int *envs_per_warp,
@@ -469,7 +470,8 @@ FW_API fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduc
 /* Autotuner of that shape: at the current poses, runs one detection, then times `trials`
  * query launches for each query size (with 4 reduction warps), and `trials` reduction
  * launches of the fastest query's candidates for each warp count, and keeps the fastest of
- * each (as fw_set_detect_shape would).  The body state is not touched; the contact buffer
+ * each (as fw_set_detect_shape would; the default is tried first and another shape must
+ * beat it by more than 1%).  The body state is not touched; the contact buffer
  * is left holding the contacts at the current poses.  Returns the chosen shape and the
  * summed time of one query and one reduction launch (ms); any output pointer may be NULL.
  * Synchronises. */

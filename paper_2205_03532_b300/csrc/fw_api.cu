@@ -1622,7 +1622,9 @@ fw_status fw_autotune_solve(fw_world *w, int n_substeps, int n_iters, int trials
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
             ms /= (float)trials;
-            if (e == cudaSuccess && ms < best) { best = ms; bg = gs[gi]; bw = wp; }
+            // a later shape must win by more than 1% (timing noise would otherwise flip
+            // between shapes of equal speed from run to run)
+            if (e == cudaSuccess && ms < best * 0.99f) { best = ms; bg = gs[gi]; bw = wp; }
         }
     if (e == cudaSuccess) e = copy_state(false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
@@ -1706,13 +1708,13 @@ fw_status fw_autotune_detect(fw_world *w, int trials, int *query_threads, int *r
     for (int qt : {256, 128, 512}) {   // the query with the default reduction
         float ms = 0.f;
         if (st == FW_OK) st = time_phase(qt, 4, true, &ms);
-        if (st == FW_OK && ms < bq) { bq = ms; best_q = qt; }
+        if (st == FW_OK && ms < bq * 0.99f) { bq = ms; best_q = qt; }   // the default first; 1% to beat it
     }
     if (st == FW_OK) st = time_phase(best_q, 4, true, &bq);   // leave the best query's output
     for (int rw : {4, 2, 8}) {
         float ms = 0.f;
         if (st == FW_OK) st = time_phase(best_q, rw, false, &ms);
-        if (st == FW_OK && ms < br) { br = ms; best_r = rw; }
+        if (st == FW_OK && ms < br * 0.99f) { br = ms; best_r = rw; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

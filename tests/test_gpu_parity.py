@@ -242,29 +242,35 @@ def test_reduce_identical_candidates(scene, request):
 @pytest.mark.parametrize("max_patches", [3, 128])
 def test_reduce_synthetic_batches_and_capacity(max_patches):
     """Several Generate batches with a ragged tail and clustered normals; max_patches = 3
-    exercises AddPatch's replacement rule."""
+    exercises AddPatch's replacement rule.  Seeds whose input has a near-tie decision are
+    passed over (the oracle says which); at least two of four must compare exactly."""
     fw = _fw()
-    rng = np.random.default_rng(max_patches)
-    n = 3000
-    samples = np.sort(rng.choice(5000, n, replace=False))
-    dirs = rng.normal(size=(9, 3))
-    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
-    which = rng.integers(0, 9, n)
-    nn = dirs[which] + 0.05 * rng.normal(size=(n, 3))
-    nn /= np.linalg.norm(nn, axis=1)[:, None]
-    c = np.zeros(n, O.CANDIDATE_DTYPE)
-    c["sample"] = samples
-    c["phi"] = rng.uniform(-2e-4, 1e-4, n)
-    c["x"] = rng.uniform(-0.01, 0.01, (n, 3))
-    c["n"] = nn
-    w = fw.World(max_patches=max_patches)
-    oc, onp, ml, md = O.reduce(c, cos_patch=w.cfg.cos_patch, max_patches=max_patches)
-    gc, gnp = w.reduce(c)
-    if ml >= MARGIN_LEN and md >= MARGIN_DOT:
-        assert gnp == onp
-        _compare_contacts(gc, oc)
-    else:
-        pytest.skip(f"seeded input has a near-tie decision (margins {ml}, {md})")
+    checked = 0
+    for k in range(4):
+        rng = np.random.default_rng(max_patches + 1000 * k)
+        n = 3000
+        samples = np.sort(rng.choice(5000, n, replace=False))
+        dirs = rng.normal(size=(9, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        which = rng.integers(0, 9, n)
+        nn = dirs[which] + 0.05 * rng.normal(size=(n, 3))
+        nn /= np.linalg.norm(nn, axis=1)[:, None]
+        c = np.zeros(n, O.CANDIDATE_DTYPE)
+        c["sample"] = samples
+        c["phi"] = rng.uniform(-2e-4, 1e-4, n)
+        c["x"] = rng.uniform(-0.01, 0.01, (n, 3))
+        c["n"] = nn
+        w = fw.World(max_patches=max_patches)
+        oc, onp, ml, md = O.reduce(c, cos_patch=w.cfg.cos_patch, max_patches=max_patches)
+        gc, gnp = w.reduce(c)
+        w.close()
+        if ml >= MARGIN_LEN and md >= MARGIN_DOT:
+            assert gnp == onp
+            _compare_contacts(gc, oc)
+            checked += 1
+        assert len(set(gc["patch"])) <= max_patches
+    print(f"synthetic batches, max_patches {max_patches}: {checked} of 4 seeds compared exactly")
+    assert checked >= 2, checked
 
 
 @pytest.mark.parametrize("max_patches", [40, 128])
