@@ -526,11 +526,13 @@ def run_fw(args):
 
 
 def run_pile_env(args):
-    """The paper's Nuts scene: 1023 M16 nuts dropped from a lattice into a round tray, ONE
-    pile env (pairs found at every detection, colour-ordered Gauss-Seidel in one block).
+    """The paper's pile scenes (--pile-body nut / torus / bowl): 1023 bodies dropped from a
+    lattice into a round tray, ONE pile env (pairs found at every detection, colour-ordered
+    Gauss-Seidel over the whole GPU).
     The pile first settles for --settle frames (4 substeps x 16 sweeps, untimed set-up);
-    the warm-up and timed frames then run the paper's settings for this scene (1 substep,
-    16 position and 1 velocity sweeps per frame) unless --substeps / --iters say otherwise.
+    the warm-up and timed frames then run the paper's settings for that scene (nuts and
+    toruses 1 substep x 16 position sweeps, bowls 2 x 50, each + 1 velocity sweep) unless
+    --substeps / --iters say otherwise.
     One pile per GPU (replicas under torchrun)."""
     import torch
     from paper_2205_03532_b300 import fw, scenes as S
@@ -543,9 +545,15 @@ def run_pile_env(args):
     stream = torch.cuda.Stream(device=dev)
     t_setup = time.perf_counter()
     n_nuts = args.envs if args.envs > 0 else 1023
-    sc = S.nut_pile_env_scene(n_nuts, seed=env_seed(args.seed, rank), mode="drop")
-    sub = args.substeps if args.substeps > 0 else 1
-    iters = args.iters if args.iters > 0 else 16
+    kind = args.pile_body
+    # per body: samples, SDF resolution (the bowl's 2 mm wall needs finer voxels) and the
+    # paper's substeps and position iterations for its pile (Table "performance statistics")
+    samples, res, sub0, it0 = {"nut": (5000, 128, 1, 16), "torus": (3000, 128, 1, 16),
+                               "bowl": (3000, 256, 2, 50)}[kind]
+    sc = S.pile_env_scene(kind, n_nuts, seed=env_seed(args.seed, rank), mode="drop", n_samples=samples,
+                          sdf_res=res)
+    sub = args.substeps if args.substeps > 0 else sub0
+    iters = args.iters if args.iters > 0 else it0
     with torch.cuda.stream(stream):
         w = fw.world_from_scene(sc, stream=stream.cuda_stream, device=dev)
         for _ in range(args.settle):
@@ -651,18 +659,18 @@ def run_pile_env(args):
         ow.step(sub, iters)
         el = time.perf_counter() - t0 - (ow.bake_seconds() - b0)
         cpu = {"value": 1.0 / el, "unit": "frames/s", "cores": cores, "kind": "oracle",
-               "sample": f"1 frame of the {n_nuts}-nut pile from its initial lattice (before the fall: "
+               "sample": f"1 frame of the {n_nuts}-{kind} pile from its initial lattice (before the fall: "
                          f"{sub} substep(s) x {iters} + {sc.sim.n_vel_iters} sweeps, every pair detected), "
                          f"lazy SDF bake excluded"}
     if rank == 0:
         frame_ms = total_ms / args.steps
-        out = {"metric": "pile frames/s", "value": value, "unit": "frames/s", "n_gpus": ws,
+        out = {"metric": f"{kind} pile frames/s", "value": value, "unit": "frames/s", "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_ms,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic (procedural ISO M16 nuts dropped from a seeded lattice into a tray)",
-               "config": {"workload": f"nut_pile_env_{n_nuts}", "n_envs": 1, "bodies": n_body,
+               "data": f"synthetic (procedural {kind}s dropped from a seeded lattice into a tray)",
+               "config": {"workload": f"{kind}_pile_env_{n_nuts}", "n_envs": 1, "bodies": n_body,
                           "settle_frames": args.settle, "substeps": sub, "iters": iters,
-                          "vel_iters": sc.sim.n_vel_iters, "samples_per_nut": ns, "sdf": "128^3 fp32",
+                          "vel_iters": sc.sim.n_vel_iters, "samples_per_body": ns, "sdf": f"{res}^3 fp32",
                           "frame_dt": sc.sim.dt, "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "kernels": kernels,
@@ -673,7 +681,7 @@ def run_pile_env(args):
                "candidates_per_pair_with_contacts": n_cand / max(int((colours >= 0).sum()), 1),
                "contacts_per_pair_with_contacts": n_cont / max(int((colours >= 0).sum()), 1),
                "real_time_factor": sc.sim.dt / (frame_ms * 1e-3),
-               "nuts_below_floor": int((p_end[:-1, 2] < 0).sum()),
+               "bodies_below_floor": int((p_end[:-1, 2] < -0.005).sum()),   # origin 5 mm under the floor
                "cpu_baseline": cpu, "clocks": clk.summary(),
                "e2e": {"value": ws * args.steps / (e2e_ms * 1e-3), "unit": "frames/s",
                        "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
@@ -764,6 +772,8 @@ def main():
                          "(pairs found every detection; --envs sets the nut count); diff_peg: gradient "
                          "throughput of the differentiable peg")
     ap.add_argument("--settle", type=int, default=60, help="pile1024: untimed frames before the warm-up")
+    ap.add_argument("--pile-body", default="nut", choices=["nut", "torus", "bowl"],
+                    help="pile1024: the bodies of the pile (the paper's Nuts, Toruses and Bowls scenes)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default solve shape")
     ap.add_argument("--contact-gen", default="samples", choices=["samples", "triangles"],
                     help="samples: SDF query of the nut's surface samples; triangles: one contact per "

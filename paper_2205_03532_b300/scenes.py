@@ -177,6 +177,71 @@ def cylinder_mesh(r: float, h: float, n_seg: int) -> Tuple[np.ndarray, np.ndarra
     return mb.build()
 
 
+def torus_mesh(R: float, r: float, n_u: int = 64, n_v: int = 16) -> Tuple[np.ndarray, np.ndarray]:
+    """Torus about the z axis: tube radius r around the circle of radius R in the xy plane;
+    n_u segments around z, n_v around the tube (n_u n_v vertices, 2 n_u n_v triangles)."""
+    mb = _MeshBuilder()
+    th = 2.0 * np.pi * np.arange(n_u) / n_u
+    ph = 2.0 * np.pi * np.arange(n_v) / n_v
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    pts = np.stack([(R + r * np.cos(P)) * np.cos(T), (R + r * np.cos(P)) * np.sin(T), r * np.sin(P)], -1)
+    idx = mb.add_vertices(pts.reshape(-1, 3)).reshape(n_u, n_v)
+    for i in range(n_u):
+        for j in range(n_v):
+            a, b = idx[i, j], idx[(i + 1) % n_u, j]
+            c, d = idx[(i + 1) % n_u, (j + 1) % n_v], idx[i, (j + 1) % n_v]
+            tm, pm = 2.0 * np.pi * (i + 0.5) / n_u, 2.0 * np.pi * (j + 0.5) / n_v
+            out = np.array([np.cos(pm) * np.cos(tm), np.cos(pm) * np.sin(tm), np.sin(pm)])   # tube normal
+            mb.add_tri_facing(a, b, c, out)
+            mb.add_tri_facing(a, c, d, out)
+    return mb.build()
+
+
+def bowl_mesh(rim: float, depth: float, wall: float, n_seg: int = 32, n_ring: int = 9) -> Tuple[np.ndarray, np.ndarray]:
+    """A bowl: the shell between two concentric spherical caps (outer radius Ro, inner
+    Ro - wall) cut by the rim plane, opening up: outer bottom at z = 0, rim at z = depth,
+    outer rim radius `rim`.  Ro = (rim^2 + depth^2) / (2 depth).  Each cap is a pole vertex
+    and n_ring rings of n_seg; the rim is the flat annulus between the caps' edges."""
+    Ro = (rim * rim + depth * depth) / (2.0 * depth)
+    Ri = Ro - wall
+    c = np.array([0.0, 0.0, Ro])
+    a_o = math.acos((Ro - depth) / Ro)
+    a_i = math.acos((Ro - depth) / Ri)
+    mb = _MeshBuilder()
+    th = 2.0 * np.pi * np.arange(n_seg) / n_seg
+
+    def cap(Rs, amax):
+        pole = mb.add_vertices([c + [0.0, 0.0, -Rs]])[0]
+        rings = []
+        for k in range(1, n_ring + 1):
+            a = amax * k / n_ring
+            ring = np.stack([Rs * math.sin(a) * np.cos(th), Rs * math.sin(a) * np.sin(th),
+                             np.full(n_seg, Ro - Rs * math.cos(a))], 1)
+            rings.append(mb.add_vertices(ring))
+        return pole, rings
+
+    po, ro = cap(Ro, a_o)
+    pi_, ri = cap(Ri, a_i)
+    P = lambda i: np.concatenate(mb.pos)[i]
+    for pole, rings, sign in ((po, ro, 1.0), (pi_, ri, -1.0)):   # outer faces away from c, inner towards it
+        for i in range(n_seg):
+            j = (i + 1) % n_seg
+            q = rings[0]
+            mb.add_tri_facing(pole, q[i], q[j], sign * ((P(q[i]) + P(q[j])) / 2 - c))
+            for k in range(n_ring - 1):
+                a, b = rings[k], rings[k + 1]
+                mid = (P(a[i]) + P(a[j]) + P(b[i]) + P(b[j])) / 4 - c
+                mb.add_tri_facing(a[i], a[j], b[j], sign * mid)
+                mb.add_tri_facing(a[i], b[j], b[i], sign * mid)
+    oe, ie = ro[-1], ri[-1]
+    up = np.array([0.0, 0.0, 1.0])
+    for i in range(n_seg):
+        j = (i + 1) % n_seg
+        mb.add_tri_facing(oe[i], oe[j], ie[j], up)
+        mb.add_tri_facing(oe[i], ie[j], ie[i], up)
+    return mb.build()
+
+
 def _ray_square(th: np.ndarray, hx: float, hy: float) -> np.ndarray:
     c, s = np.cos(th), np.sin(th)
     t = np.minimum(np.where(np.abs(c) > 1e-15, hx / np.maximum(np.abs(c), 1e-300), np.inf),
@@ -874,60 +939,90 @@ def pile_scene(n_envs: int = 256, seed: int = 0, n_nuts: int = 7, mode: str = "d
 # --------------------------------------------------------------------------------------
 # one env of hundreds of nuts (pile env): the pairs are found at every detection
 # --------------------------------------------------------------------------------------
-def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_samples: int = 5000,
-                       sdf_res: int = 128, plate_sdf_res: int = 128, mu: float = 0.3, n_substeps: int = 4,
-                       n_iters: int = 16, n_vel_iters: int = 1, frames: int = 120, gap_mm: float = 2.0,
-                       layers: int = 4, sink_mm: float = 0.02, overlap_mm: float = 1.0) -> Scene:
-    """The paper's Nuts scene: n_nuts ISO M16 nuts (the nut of nut_bolt_scene: 18,136
-    triangles, n_samples samples, its own SDF) in ONE env over a static support (SDF only, no
-    samples; its floor at z = 0), as a pile env whose pairs every detection finds again.
+# the paper's three pile bodies (Sec. III-D scene list; Table "geometric representations":
+# the torus's SDF box is 304 x 104 x 304 voxels, (R + r) / r = 2.92; the bowl's 257 x 75 x
+# 257, rim diameter / depth = 3.43, with 582 vertices)
+PILE_BODIES = ("nut", "torus", "bowl")
 
-    mode "drop": the nuts start in a square lattice of columns (`layers` deep, cells of the
-    nut's bounding diameter plus gap_mm, jittered by up to a quarter of the gap), at random
-    orientations, the lowest layer gap_mm above the floor, and fall into a pile inside a
-    round tray (a box with a blind cylindrical hole 60 mm deep, 15 mm of floor below it,
-    the hole's wall 10 mm outside the lattice's corners) that keeps every nut on the floor.
-    mode "heap": resting stacks of one to three nuts lying flat (random yaw), each sunk
-    sink_mm into the one below or the plate; the stacks stand on a square grid whose pitch
-    is the nut's across-corners width less overlap_mm, so that neighbouring stacks touch
-    where hexagon corners meet: nut-plate, nut-on-nut and side contacts from the first
-    substep, and each nut pairs with up to eight neighbours."""
-    if not 1 <= n_nuts <= 1023:
-        raise ValueError("n_nuts must be 1..1023 (a pile env holds 1024 bodies with the plate)")
+
+def pile_body_asset(kind: str, n_samples: int, sdf_res: int, rng: np.random.Generator):
+    """(asset, stack step, rest height of the body's origin above its support): an M16 nut
+    (24 AF x 13 mm, 18,136 triangles); a torus R = 15.4 mm, r = 8 mm (64 x 16 segments,
+    2,048 triangles); a bowl of rim diameter 100 mm, depth 29 mm, wall 2 mm (578 vertices,
+    1,152 triangles), which nests in the bowl below it."""
+    if kind == "nut":
+        P, af, _ = ISO_COARSE[16]
+        V, T = nut_mesh(16, P, 13.0, af, 0.05, n_ang=84)
+        step, rest = 13.0e-3, 6.5e-3
+    elif kind == "torus":
+        V, T = torus_mesh(15.4e-3, 8.0e-3, 64, 16)
+        step, rest = 16.0e-3, 8.0e-3
+    elif kind == "bowl":
+        V, T = bowl_mesh(50.0e-3, 29.0e-3, 2.0e-3)
+        step, rest = 2.0e-3, 0.0
+    else:
+        raise ValueError(f"unknown pile body {kind!r}")
+    a = Asset(f"{kind}_pile", V, T, sample_surface(V, T, n_samples, rng), 7800.0 if kind == "nut" else 2500.0,
+              sdf_res=sdf_res, sdf_pad=1e-3)
+    return a, step, rest
+
+
+def pile_env_scene(kind: str = "nut", n_bodies: int = 1023, seed: int = 0, mode: str = "drop",
+                   n_samples: int = 5000, sdf_res: int = 128, plate_sdf_res: int = 128, mu: float = 0.3,
+                   n_substeps: int = 4, n_iters: int = 16, n_vel_iters: int = 1, frames: int = 120,
+                   gap_mm: float = 2.0, layers: int = 4, sink_mm: float = 0.02, overlap_mm: float = 1.0) -> Scene:
+    """The paper's pile scenes: n_bodies nuts, toruses or bowls in ONE env over a static
+    support (SDF only, no samples; its floor at z = 0), as a pile env whose pairs every
+    detection finds again.
+
+    mode "drop": the bodies start in a square lattice of columns (`layers` deep, cells of
+    the body's bounding diameter plus gap_mm, jittered by up to a quarter of the gap), at
+    random orientations, the lowest layer gap_mm above the floor, and fall into a pile
+    inside a round tray (a box with a blind cylindrical hole 60 mm deep, a floor of 15 mm or
+    four tray voxels below it, the hole's wall 10 mm outside the lattice's corners) that
+    keeps every body on the floor.
+    mode "heap": resting stacks of one to three bodies lying flat (random yaw), each sunk
+    sink_mm into the one below or the floor (bowls nest in the bowl below); the stacks
+    stand on a square grid whose pitch is the body's largest radius in the xy plane times
+    two less overlap_mm, so that neighbouring stacks touch where their outlines meet."""
+    if not 1 <= n_bodies <= 1023:
+        raise ValueError("n_bodies must be 1..1023 (a pile env holds 1024 bodies with the support)")
     rng = np.random.default_rng(seed)
-    P, af, _ = ISO_COARSE[16]
-    thick = 13.0e-3
-    nV, nT = nut_mesh(16, P, 13.0, af, 0.05, n_ang=84)
-    nut = Asset("nut_m16", nV, nT, sample_surface(nV, nT, n_samples, rng), 7800.0, sdf_res=sdf_res, sdf_pad=1e-3)
-    r = float(np.linalg.norm(nV, axis=1).max())            # bounding sphere
-    rc = float(np.linalg.norm(nV[:, :2], axis=1).max())    # across-corners half width
-    bodies = np.zeros(n_nuts + 1, dtype=BODY_DTYPE)
+    body, step, rest = pile_body_asset(kind, n_samples, sdf_res, rng)
+    V = body.verts
+    r = float(np.linalg.norm(V, axis=1).max())              # bounding sphere (about the origin)
+    rc = float(np.linalg.norm(V[:, :2], axis=1).max())      # largest radius in the xy plane
+    bodies = np.zeros(n_bodies + 1, dtype=BODY_DTYPE)
     if mode == "drop":
         cell = 2 * r + gap_mm * 1e-3
-        m = max(1, int(math.ceil(math.sqrt(n_nuts / layers))))
-        for k in range(n_nuts):
+        m = max(1, int(math.ceil(math.sqrt(n_bodies / layers))))
+        for k in range(n_bodies):
             lay, rem = divmod(k, m * m)
             iy, ix = divmod(rem, m)
             jit = rng.uniform(-0.25, 0.25, 2) * gap_mm * 1e-3
+            # the bounding sphere of a body is centred on its origin for the nut and the torus
+            # and reaches below it for the bowl: keep the sphere gap_mm above the floor
             c = ((ix - (m - 1) / 2) * cell + jit[0], (iy - (m - 1) / 2) * cell + jit[1],
                  r + gap_mm * 1e-3 + lay * cell)
             bodies[k] = _body(0, DYNAMIC, c, _random_quat(rng), mu)
         R = math.sqrt(2.0) * m * cell / 2 + 0.01
-        TV, TT = box_with_hole_mesh(2 * R + 0.04, 2 * R + 0.04, 0.075, R, 0.06, 64)
+        # the floor below the hole is at least 15 mm and four of the tray's voxels thick
+        floor = max(0.015, 4.0 * (2 * R + 0.04) / plate_sdf_res)
+        TV, TT = box_with_hole_mesh(2 * R + 0.04, 2 * R + 0.04, 0.06 + floor, R, 0.06, 64)
         support = Asset("tray", TV, TT, None, 7800.0, sdf_res=plate_sdf_res, sdf_pad=1e-3)
         support_z = 0.06
     elif mode == "heap":
         pitch = 2 * rc - overlap_mm * 1e-3
         heights = []
-        while sum(heights) < n_nuts:
-            heights.append(int(rng.integers(1, min(3, n_nuts - sum(heights)) + 1)))
+        while sum(heights) < n_bodies:
+            heights.append(int(rng.integers(1, min(3, n_bodies - sum(heights)) + 1)))
         m = max(1, int(math.ceil(math.sqrt(len(heights)))))
         k = 0
         for si, hgt in enumerate(heights):
             iy, ix = divmod(si, m)
             cx, cy = (ix - (m - 1) / 2) * pitch, (iy - (m - 1) / 2) * pitch
             for level in range(hgt):
-                z = thick / 2 + level * thick - (level + 1) * sink_mm * 1e-3
+                z = rest + level * step - (level + 1) * sink_mm * 1e-3
                 bodies[k] = _body(0, DYNAMIC, (cx, cy, z), quat_axis_angle([0, 0, 1], rng.uniform(0, np.pi / 3)), mu)
                 k += 1
         half = m * pitch / 2 + 0.02
@@ -936,6 +1031,20 @@ def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_
         support_z = -0.005
     else:
         raise ValueError(f"unknown pile mode {mode!r}")
-    bodies[n_nuts] = _body(1, STATIC, (0.0, 0.0, support_z), (0, 0, 0, 1), mu)
+    bodies[n_bodies] = _body(1, STATIC, (0.0, 0.0, support_z), (0, 0, 0, 1), mu)
     sim = SimParams(n_substeps=n_substeps, n_iters=n_iters, n_vel_iters=n_vel_iters, frames=frames)
-    return Scene("nut_pile_env", [nut, support], [], sim, piles=[bodies])
+    return Scene(f"{kind}_pile_env", [body, support], [], sim, piles=[bodies])
+
+
+def nut_pile_env_scene(n_nuts: int = 1024, seed: int = 0, mode: str = "drop", n_samples: int = 5000,
+                       sdf_res: int = 128, plate_sdf_res: int = 128, mu: float = 0.3, n_substeps: int = 4,
+                       n_iters: int = 16, n_vel_iters: int = 1, frames: int = 120, gap_mm: float = 2.0,
+                       layers: int = 4, sink_mm: float = 0.02, overlap_mm: float = 1.0) -> Scene:
+    """The paper's Nuts scene: pile_env_scene of ISO M16 nuts (the nut of nut_bolt_scene,
+    its own SDF, n_samples samples).  In mode "heap" the grid pitch is the nut's
+    across-corners width less overlap_mm, so that hexagon corners of neighbouring stacks
+    touch: nut-plate, nut-on-nut and side contacts from the first substep."""
+    return pile_env_scene("nut", n_nuts, seed=seed, mode=mode, n_samples=n_samples, sdf_res=sdf_res,
+                          plate_sdf_res=plate_sdf_res, mu=mu, n_substeps=n_substeps, n_iters=n_iters,
+                          n_vel_iters=n_vel_iters, frames=frames, gap_mm=gap_mm, layers=layers, sink_mm=sink_mm,
+                          overlap_mm=overlap_mm)

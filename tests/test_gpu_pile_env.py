@@ -227,3 +227,63 @@ def test_full_size_drop_pile_1023_nuts():
             assert common >= 0.8 * max(len(gc), len(oc), 1)
     print(f"pairs {len(gab)}, with contacts {(counts > 0).sum()}, contacts {len(gc_all)}, sampled exact {exact}")
     gw.close()
+
+
+@pytest.mark.parametrize("kind, sdf_res", [("torus", 64), ("bowl", 128)])
+def test_torus_and_bowl_heaps_match_oracle(kind, sdf_res):
+    """The paper's other two pile bodies (Sec. III-D: piles of 1,024 toruses and of 1,024
+    bowls in one env), 16 of them in stacks over a plate -- toruses lying flat on each other,
+    bowls nested in each other -- through the same pile path: the pair list identical,
+    contacts per pair identical where the pair's margins allow (most pairs: the surfaces are
+    smooth), one substep on identical contacts with identical colours to 1e-6."""
+    fw = _fw()
+    sc = S.pile_env_scene(kind, 16, seed=3, mode="heap", n_samples=3000, sdf_res=sdf_res, plate_sdf_res=64)
+    gw = fw.world_from_scene(sc)
+    ow = O.world_from_scene(sc, lazy_bake=True, margin_len=MARGIN_LEN, margin_dot=MARGIN_DOT)
+    p, q, v, w = gw.get_state()
+    ow.set_state(p, q, v, w)
+    gw.collide()
+    ow.reset_margins()
+    ow.collide()
+    gab, _ = gw.pile_pairs(0)
+    oab, _ = ow.pile_pairs(0)
+    assert _same_pairs(sc, gw, p, gab, oab) == 0
+    np.testing.assert_array_equal(gab, oab)
+    gc_all = gw.get_contacts(0)
+    exact = with_contacts = 0
+    parts = []
+    for k in range(len(oab)):
+        gc = gc_all[gc_all["pair"] == k]
+        oc = ow.pair_contacts(0, k)
+        with_contacts += len(oc) > 0
+        ml, md = ow.pair_margins(0, k)
+        if ml >= MARGIN_LEN and md >= MARGIN_DOT:
+            assert list(gc["sample"]) == list(oc["sample"]), k
+            assert list(gc["patch"]) == list(oc["patch"]), k
+            exact += len(oc) > 0
+        else:
+            common = len(set(gc["sample"]) & set(oc["sample"]))
+            assert common >= 0.8 * max(len(gc), len(oc), 1), (k, common, len(gc), len(oc))
+        g = np.zeros(len(oc), fw.CONTACT_DTYPE)
+        g["sample"], g["patch"], g["phi"] = oc["sample"], oc["patch"], oc["phi"]
+        g["xa"], g["n"] = oc["xa"], oc["n"]
+        g["xb"] = g["xa"] - g["phi"][:, None] * g["n"]
+        g["pair"] = k
+        same = oc.copy()
+        same["phi"], same["xa"], same["n"] = g["phi"], g["xa"], g["n"]
+        same["xb"] = same["xa"] - same["phi"][:, None] * same["n"]
+        ow.set_pair_contacts(0, k, same)
+        parts.append(g)
+    print(f"{kind} heap: pairs {len(oab)}, with contacts {with_contacts}, compared exactly {exact}")
+    assert with_contacts >= 15 and exact >= with_contacts // 2, (with_contacts, exact)
+    gw.set_contacts(0, np.concatenate(parts))
+    hs = sc.sim.dt / sc.sim.n_substeps
+    gw.substep(hs, sc.sim.n_iters, detect=False)
+    ow.substep(hs, sc.sim.n_iters, detect=False)
+    np.testing.assert_array_equal(gw.pile_pairs(0)[1], ow.pile_pairs(0)[1])
+    gp, gq, gv, _ = gw.get_state()
+    op, oq, ov, _ = ow.state()
+    assert np.abs(gp - op).max() <= 1e-6
+    assert max(_rot_angle(gq[i].astype(np.float64), oq[i]) for i in range(len(gq))) <= 1e-6
+    assert np.abs(gv - ov).max() <= 1e-4 * max(1.0, float(np.abs(ov).max()))
+    gw.close()

@@ -263,3 +263,43 @@ def test_mass_properties_regular_prism_closed_form():
     assert I[2, 2] == pytest.approx(rho * hgt * J, rel=1e-5)
     assert I[0, 0] == pytest.approx(rho * hgt * J / 2 + M * hgt * hgt / 12, rel=1e-5)
     assert I[1, 1] == pytest.approx(I[0, 0], rel=1e-5)
+
+
+def test_torus_mass_properties_converge_to_closed_form():
+    """The pile torus (R = 15.4 mm, r = 8 mm): a closed, outward-wound surface whose
+    polyhedral volume and axial / transverse moments approach the solid torus's closed
+    forms, V = 2 pi^2 R r^2, I_zz = m (R^2 + 3 r^2 / 4), I_xx = m (R^2 / 2 + 5 r^2 / 8), as the
+    segmentation is refined (error of order the squared segment angle)."""
+    R, r = 15.4e-3, 8.0e-3
+    errs = []
+    for n_u, n_v in ((64, 16), (256, 64)):
+        V, T = S.torus_mesh(R, r, n_u, n_v)
+        assert S.edge_manifold_check(T) and S.signed_volume(V, T) > 0
+        m, com, I = O.mass_properties(V, T, 1.0)
+        vol = 2 * math.pi ** 2 * R * r * r
+        np.testing.assert_allclose(com, 0, atol=1e-9)
+        e = [abs(m / vol - 1), abs(I[2, 2] / (m * (R * R + 0.75 * r * r)) - 1),
+             abs(I[0, 0] / (m * (0.5 * R * R + 0.625 * r * r)) - 1)]
+        errs.append(max(e))
+    assert errs[0] < 0.04 and errs[1] < 0.003 and errs[1] < errs[0] / 8, errs
+
+
+def test_bowl_mass_properties_converge_to_closed_form():
+    """The pile bowl (rim 50 mm, depth 29 mm, wall 2 mm): a closed, outward-wound shell
+    between two concentric spherical caps whose volume approaches the difference of the
+    caps' closed forms pi h^2 (3 R - h) / 3 as the rings and segments are refined, with its
+    centre of mass on the axis."""
+    rim, depth, wall = 50e-3, 29e-3, 2e-3
+    Ro = (rim * rim + depth * depth) / (2 * depth)
+    Ri = Ro - wall
+    cap = lambda Rs, h: math.pi * h * h * (3 * Rs - h) / 3
+    vol = cap(Ro, depth) - cap(Ri, depth - wall)
+    errs = []
+    for n_seg, n_ring in ((32, 9), (128, 36)):
+        V, T = S.bowl_mesh(rim, depth, wall, n_seg, n_ring)
+        assert S.edge_manifold_check(T) and S.signed_volume(V, T) > 0
+        m, com, I = O.mass_properties(V, T, 1.0)
+        np.testing.assert_allclose(com[:2], 0, atol=1e-9)
+        assert 0 < com[2] < depth
+        errs.append(abs(m / vol - 1))
+    assert errs[0] < 0.03 and errs[1] < 0.003 and errs[1] < errs[0] / 8, errs
