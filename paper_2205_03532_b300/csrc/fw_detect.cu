@@ -172,12 +172,13 @@ __global__ void map_kernel(SimParams p) {
     p.maps[pi] = M;
 }
 
-// The narrow phase of one sample through the pair's map: signed distance, and the world
-// normal (R_B g / |g|, float32) and world point (R_A s + p_A) for a candidate.  False when the
-// point is outside the SDF grid or the gradient vanishes (|grad| < 1e-12).
-template <int kStore = kStoreAny>
-__device__ __forceinline__ bool query_sample(const PairMap &M, const PairXf &X, const AssetDev &gb, float4 s,
-                                             V3 &xw, V3 &nw, float &phi) {
+// The narrow phase of one sample through the pair's map, in the grid's storage precision.
+// A candidate needs phi below the cutoff first: the gradient, the world normal and the world
+// point are formed only for such samples (whole warps of samples far from the SDF body
+// skip them; the values are those the full lookup would give).
+template <int kStore, bool kHalf>
+__device__ __forceinline__ bool query_sample_as(const PairMap &M, const PairXf &X, const AssetDev &gb, float4 s,
+                                                float cutoff, V3 &xw, V3 &nw, float &phi) {
     const float ux = __fmaf_rn(M.A[2], s.z, __fmaf_rn(M.A[1], s.y, __fmaf_rn(M.A[0], s.x, M.f[0])));
     const float uy = __fmaf_rn(M.A[5], s.z, __fmaf_rn(M.A[4], s.y, __fmaf_rn(M.A[3], s.x, M.f[1])));
     const float uz = __fmaf_rn(M.A[8], s.z, __fmaf_rn(M.A[7], s.y, __fmaf_rn(M.A[6], s.x, M.f[2])));
@@ -186,14 +187,25 @@ __device__ __forceinline__ bool query_sample(const PairMap &M, const PairXf &X, 
     const bool okx = cell_of(ux, M.c[0], gb.dims[0], ci, fx);
     const bool oky = cell_of(uy, M.c[1], gb.dims[1], cj, fy);
     const bool okz = cell_of(uz, M.c[2], gb.dims[2], ck, fz);
-    V3 g;
-    if (gb.cell16) sdf_cell_eval<true, kStore>(gb, ci, cj, ck, fx, fy, fz, phi, g);
-    else sdf_cell_eval<false, kStore>(gb, ci, cj, ck, fx, fy, fz, phi, g);
+    const CellCorners c = sdf_cell_corners<kHalf, kStore>(gb, ci, cj, ck);
+    phi = cell_value<kHalf>(gb, c, fx, fy, fz);
+    if (!(okx && oky && okz && phi < cutoff)) return false;
+    const V3 g = cell_gradient<kHalf>(gb, c, fx, fy, fz);
     const float gg = dot(g, g);
     const V3 nb = rsqrtf(fmaxf(gg, 1e-30f)) * g;   // unit to a few ulp; the decisions on it have margins
     nw = mul(X.RB, nb);
     xw = mul(X.RA, v3(s.x, s.y, s.z)) + X.pA;
-    return okx && oky && okz && (gg >= 1e-24f);
+    return gg >= 1e-24f;
+}
+
+// The narrow phase of one sample through the pair's map: true for a candidate (inside the
+// grid, phi below the cutoff, |grad| >= 1e-12), with its signed distance, world normal
+// (R_B g / |g|, float32) and world point (R_A s + p_A).
+template <int kStore = kStoreAny>
+__device__ __forceinline__ bool query_sample(const PairMap &M, const PairXf &X, const AssetDev &gb, float4 s,
+                                             float cutoff, V3 &xw, V3 &nw, float &phi) {
+    return gb.cell16 ? query_sample_as<kStore, true>(M, X, gb, s, cutoff, xw, nw, phi)
+                     : query_sample_as<kStore, false>(M, X, gb, s, cutoff, xw, nw, phi);
 }
 
 // Closest point of the triangle (a, b, c) to p: p's Voronoi region among the vertices,
@@ -835,7 +847,7 @@ __global__ void __launch_bounds__(kThr, kThr == 128 ? 5 : 1024 / kThr) query_ker
         for (int u = 0; u < NPER; ++u) {
             const int i = base + u * kThr + tid;
             const float4 s = __ldg(&ga.samples[i < ga.ns ? i : ga.ns - 1]);
-            ok[u] = query_sample<kStore>(M, X, gb, s, xw[u], nw[u], ph[u]) && (ph[u] < cutoff) && (i < ga.ns);
+            ok[u] = query_sample<kStore>(M, X, gb, s, cutoff, xw[u], nw[u], ph[u]) && (i < ga.ns);
         }
     }
     // compaction in sample order: local sample u * kThr + warp * 32 + lane
@@ -964,7 +976,7 @@ __global__ void query_pair_kernel(SimParams p, int pi, float *phi, float *nrm) {
     load_pose(p, P.b, X.RB, X.pB);
     V3 xw, nw;
     float f;
-    if (query_sample(Ms, X, gb, ga.samples[i], xw, nw, f)) {
+    if (query_sample(Ms, X, gb, ga.samples[i], __int_as_float(0x7f800000), xw, nw, f)) {   // every valid sample
         phi[i] = f;
         nrm[3 * i] = nw.x; nrm[3 * i + 1] = nw.y; nrm[3 * i + 2] = nw.z;
     } else {

@@ -122,6 +122,54 @@ __device__ __forceinline__ long long cell_offset(const AssetDev &g, int ci, int 
     return st >= 0 ? (long long)st * kBrickCells + l : 0;
 }
 
+// The 8 corner values of cell (ci, cj, ck) (order 000 100 010 110 001 101 011 111, x
+// fastest; phi / h in FP16 storage) and the brick's table entry st (< 0: left out).
+struct CellCorners {
+    float v[8];
+    int st;
+};
+template <bool kHalf, int kStore = kStoreAny>
+__device__ __forceinline__ CellCorners sdf_cell_corners(const AssetDev &g, int ci, int cj, int ck) {
+    CellCorners c;
+    const long long o = cell_offset<kStore>(g, ci, cj, ck, c.st);
+    if (kHalf) {
+        const uint4 q = __ldg(g.cell16 + o);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+        const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&q.z));
+        const float2 e = __half22float2(*reinterpret_cast<const __half2 *>(&q.w));
+        c.v[0] = a.x; c.v[1] = a.y; c.v[2] = b.x; c.v[3] = b.y;
+        c.v[4] = d.x; c.v[5] = d.y; c.v[6] = e.x; c.v[7] = e.y;
+    } else {
+        const float4 a = __ldg(g.cell32 + 2 * o), b = __ldg(g.cell32 + 2 * o + 1);
+        c.v[0] = a.x; c.v[1] = a.y; c.v[2] = a.z; c.v[3] = a.w;
+        c.v[4] = b.x; c.v[5] = b.y; c.v[6] = b.z; c.v[7] = b.w;
+    }
+    return c;
+}
+// The trilinear value of a cell's corners (the same lerps as sdf_cell_eval), in metres;
+// +-band for a brick left out.
+template <bool kHalf>
+__device__ __forceinline__ float cell_value(const AssetDev &g, const CellCorners &c, float fx, float fy, float fz) {
+    const float a00 = lerp_(c.v[0], c.v[1], fx), a10 = lerp_(c.v[2], c.v[3], fx);
+    const float a01 = lerp_(c.v[4], c.v[5], fx), a11 = lerp_(c.v[6], c.v[7], fx);
+    const float b0 = lerp_(a00, a10, fy), b1 = lerp_(a01, a11, fy);
+    const float val = lerp_(b0, b1, fz);
+    const float phi = kHalf ? val * g.h : val;
+    return c.st < 0 ? (c.st == -1 ? g.band : -g.band) : phi;
+}
+// The gradient of the trilinear interpolant (the same blends as sdf_cell_eval); zero for a
+// brick left out.
+template <bool kHalf>
+__device__ __forceinline__ V3 cell_gradient(const AssetDev &g, const CellCorners &c, float fx, float fy, float fz) {
+    const float *v = c.v;
+    const float gx = lerp_(lerp_(v[1] - v[0], v[3] - v[2], fy), lerp_(v[5] - v[4], v[7] - v[6], fy), fz);
+    const float gy = lerp_(lerp_(v[2] - v[0], v[3] - v[1], fx), lerp_(v[6] - v[4], v[7] - v[5], fx), fz);
+    const float gz = lerp_(lerp_(v[4] - v[0], v[5] - v[1], fx), lerp_(v[6] - v[2], v[7] - v[3], fx), fy);
+    const V3 gr = kHalf ? v3(gx, gy, gz) : g.inv_h * v3(gx, gy, gz);
+    return c.st < 0 ? v3(0.0f, 0.0f, 0.0f) : gr;
+}
+
 // Trilinear value and gradient in cell (ci, cj, ck) at fractions (fx, fy, fz) from the
 // cell-corner copy (the cell must be a valid cell of the grid: its one or two 16-byte loads
 // are in bounds).  A cell of a brick left out of the narrow band answers phi = +band (or
