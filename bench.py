@@ -31,14 +31,14 @@ sys.path.insert(0, ROOT)
 # holds the capture).
 NCU_TRAFFIC = {
     # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the bench's default
-    # command, launches in its end-to-end pass over the timed frames' state)
-    "a9c21361244c5130": {"map_kernel": 0.12e6, "query_kernel": 16.84e6, "reduce_kernel": 53.05e6,
-                         "solve_kernel": 59.16e6},
+    # command, launches in its per-kernel timing pass over the timed frames)
+    "091c3c194e6ce77a": {"map_kernel": 0.12e6, "query_kernel": 25.40e6, "reduce_kernel": 72.17e6,
+                         "solve_kernel": 90.34e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "a9c21361244c5130": {"map_kernel": 1.05e6, "query_kernel": 544.5e6, "reduce_kernel": 209.2e6,
-                         "solve_kernel": 2832.8e6},
+    "091c3c194e6ce77a": {"map_kernel": 0.7e6, "query_kernel": 582.1e6, "reduce_kernel": 273.0e6,
+                         "solve_kernel": 2995.2e6},
 }
 
 FP32_LANES_PER_SM = 128
@@ -285,6 +285,33 @@ def single_pair_generate(sc, gen_cfg, fp16, dev, frames=5):
             "candidates": n_cand, "contacts": n_cont}
 
 
+def solve_chain_floor(sc, snap, gen_cfg, fp16, dev, sim, sm_max, cycles_bench):
+    """One env of the workload alone (the first env's state at the start of the timed frames,
+    its contacts detected there), one substep from that state twenty times: the solve
+    kernel's cycles per row update for a single chain with the GPU otherwise idle."""
+    from paper_2205_03532_b300 import fw, scenes as S
+    g = sc.groups[0]
+    b = g.bodies[:1].copy()
+    nb = b.shape[1]
+    state = [t[:nb].cpu().numpy() for t in snap]
+    one = S.Scene(name=sc.name, assets=sc.assets, groups=[S.EnvGroup(bodies=b, pairs=g.pairs)], sim=sc.sim)
+    w = fw.world_from_scene(one, fp16=fp16, device=dev, **gen_cfg)
+    w.set_state(*state)
+    w.collide()
+    rows = len(w.get_contacts(0))
+    w.set_timing(True)
+    for _ in range(20):   # one substep per call (detection at the same state, then the solve)
+        w.set_state(*state)
+        w.step(1, sim.n_iters)
+    tim = w.get_timings()
+    w.set_timing(False)
+    w.close()
+    ms = tim["solve_ms"] / max(tim["solve_launches"], 1)
+    cyc = ms * 1e-3 * sm_max * 1e6 / max(rows * sim.n_iters, 1)
+    return {"rows": rows, "cycles_per_row_update_one_env": cyc, "frac_of_bench": cyc / cycles_bench,
+            "note": "the same solve kernel on one env alone: the chain-latency floor of this formulation"}
+
+
 def run_fw(args):
     import torch
     from paper_2205_03532_b300 import fw, scenes as S
@@ -465,6 +492,12 @@ def run_fw(args):
     single = None
     if tri_mode:
         single = single_pair_generate(sc, gen_cfg, fp16, dev)
+    # The solve's latency floor: the same kernel on ONE env (one warp on an idle GPU, the
+    # same contacts as the first env of the timed frames), cycles per row update.  The
+    # 1000-env kernel can be no faster per env than its longest env's chain alone.
+    if args.workload == "nut_bolt" and not tri_mode and args.solver == "gs":
+        kernels["solve_kernel"]["latency_floor"] = solve_chain_floor(sc, snap, gen_cfg, fp16, dev, sim, sm_max,
+                                                                     kernels["solve_kernel"]["cycles_per_row_update"])
     # ---- end to end through the public API with host buffers: state in, frame, state out
     pin = [torch.empty((n_body, k), dtype=torch.float32).pin_memory() for k in (3, 4, 3, 3)]
     torch.cuda.synchronize()
