@@ -90,7 +90,7 @@ struct fw_world {
     float4 *d_pscratch = nullptr, *d_pcand = nullptr;
     int *d_pcand_count = nullptr;
     PairMap *d_pmaps = nullptr;
-    Row *d_prows = nullptr;
+    float4 *d_prows = nullptr;   // kPileRowF4 float4 per row
     PileSolveMem pmem = {};
     int pile_sweep_blocks = 0;   // blocks of the cooperative pile sweep kernel
     int pile_optin = 0;
@@ -274,7 +274,7 @@ void pile_free(fw_world *w) {
     dfree(w->d_pcontacts); dfree(w->d_pccounts); dfree(w->d_pscratch); dfree(w->d_pcand); dfree(w->d_pcand_count);
     dfree(w->d_pmaps); dfree(w->d_prows);
     dfree(w->pmem.color); dfree(w->pmem.ab); dfree(w->pmem.rr); dfree(w->pmem.order); dfree(w->pmem.cstart);
-    dfree(w->pmem.ncol); dfree(w->pmem.bv); dfree(w->pmem.bw); dfree(w->pmem.bcom); dfree(w->pmem.bar);
+    dfree(w->pmem.ncol); dfree(w->pmem.bv); dfree(w->pmem.bw); dfree(w->pmem.bcom); dfree(w->pmem.binv); dfree(w->pmem.bar);
 }
 
 // The pile buffers: every pile gets regions of the same size, from the largest pile's
@@ -324,7 +324,7 @@ fw_status pile_alloc(fw_world *w) {
     CK(cudaMalloc(&w->d_pcand, sizeof(float4) * 2 * (size_t)kBatch * ni));
     CK(cudaMalloc(&w->d_pcand_count, sizeof(int) * ni));
     CK(cudaMalloc(&w->d_pcounts, sizeof(int2) * n));
-    CK(cudaMalloc(&w->d_prows, sizeof(Row) * (size_t)n * rcap));
+    CK(cudaMalloc(&w->d_prows, sizeof(float4) * kPileRowF4 * (size_t)n * rcap));
     CK(cudaMalloc(&w->pmem.color, np));
     CK(cudaMalloc(&w->pmem.ab, sizeof(unsigned) * np));
     CK(cudaMalloc(&w->pmem.rr, sizeof(unsigned) * np));
@@ -335,6 +335,7 @@ fw_status pile_alloc(fw_world *w) {
     CK(cudaMalloc(&w->pmem.bv, sizeof(float4) * nb));
     CK(cudaMalloc(&w->pmem.bw, sizeof(float4) * nb));
     CK(cudaMalloc(&w->pmem.bcom, sizeof(float4) * nb));
+    CK(cudaMalloc(&w->pmem.binv, 2 * sizeof(float4) * nb));
     CK(cudaMalloc(&w->pmem.bar, sizeof(unsigned)));
     // no pairs and no contacts until the first detection
     CK(cudaMemsetAsync(w->d_pcounts, 0, sizeof(int2) * n, w->stream));
@@ -494,7 +495,7 @@ SimParams pile_params(const fw_world *w, float hs, int n_iters) {
     p.contacts = w->d_pcontacts;
     p.counts = w->d_pccounts;
     p.scratch = w->d_pscratch;
-    p.rows = w->d_prows;
+    p.rows = nullptr;   // the pile kernels take the pile rows (kPileRowF4 float4 each) as an argument
     p.pile_counts = w->d_pcounts;
     p.item_range = w->d_pitem_range;
     p.pile_pcap = w->pile_pcap;

@@ -40,7 +40,6 @@ namespace {
 
 constexpr int kQueryThreads = 256;
 constexpr int kQueryPerThread = kBatch / kQueryThreads;   // 4 samples per thread
-constexpr int kQueryWarps = kQueryThreads / 32;
 constexpr int kReduceWarps = 4;
 constexpr int kStage = 256;              // candidates of a batch staged in shared memory
 constexpr int kWin = 32;                 // new patches (seeds) per round at most

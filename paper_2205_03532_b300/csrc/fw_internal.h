@@ -110,6 +110,7 @@ struct PileDev {
 constexpr int kMaxPileBodies = 1024;
 constexpr int kPilePairsPerBody = 8;    // pair capacity per body of a pile
 constexpr int kPileRowsPerBody = 192;   // row (contact) capacity per body of a pile
+constexpr int kPileRowF4 = 28;          // float4 per pile row (the two-body fast form of the sweeps)
 constexpr int kMaxColors = 64;          // pair colours of a pile solve; the last gathers the rest
 
 // A reduced contact on the device.  sample_patch = sample | (patch << 24).
@@ -260,6 +261,7 @@ struct PileSolveMem {
     int *ncol;                // per pile: colours used
     float4 *bv, *bw, *bcom;   // per body (global id): velocity | inverse mass, angular velocity |
                               // movable (1 or 0), centre of mass (world)
+    float4 *binv;             // per body: the world inverse inertia's six words (xx yy zz xy | xz yz - -)
     unsigned *bar;            // the sweep kernel's grid-barrier counter
 };
 // The pile solve keeps per-pair tables in shared memory: a pair's rows as start | count << 21
@@ -271,7 +273,7 @@ size_t pile_smem_bytes(int n_bodies, int pcap);
 // cooperative sweep kernel (all resident at once) on `device`
 cudaError_t prepare_pile_solve(int optin, int device, int *max_dyn, int *sweep_blocks);
 cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
-                              const PileSolveMem &m, Row *rows, size_t smem, int sweep_blocks, cudaStream_t s);
+                              const PileSolveMem &m, float4 *rows, size_t smem, int sweep_blocks, cudaStream_t s);
 cudaError_t launch_tri_pair(const SimParams &p, int pair, float *x, float *phi, float *nrm, cudaStream_t s, int nt);
 cudaError_t measure_l2_read(int device, long long bytes, int iters, float *gbs);
 

@@ -119,9 +119,8 @@ struct BodySm {
     __device__ __forceinline__ bool writes(int) const { return true; }
 };
 
-// The bodies of a pile env in shared memory.  Pairs solved at the same time share no
-// movable body; a static or kinematic body's velocity is only read (never written back, so
-// that threads touching the same one do not race).
+// The bodies of a pile env in the prep's shared memory (forces, then the rows' geometry and
+// masses); the sweeps read and write the movable bodies' velocities in global memory.
 struct PileBodies {
     float (*v)[3];
     float (*w)[3];
@@ -129,7 +128,6 @@ struct PileBodies {
     float (*Iinv)[6];
     float (*com)[3];
     const unsigned char *mov;   // 1: dynamic or fixed axis
-    __device__ __forceinline__ bool writes(int i) const { return mov[i] != 0; }
 };
 
 struct EnvSm {
@@ -480,6 +478,73 @@ __device__ __forceinline__ void couple_fast_row(float4 *fr, const float4 *fn) {
     fr[12].w = C[0][0];
     fr[13] = make_float4(C[0][1], C[0][2], C[1][0], C[1][1]);
     fr[14] = make_float4(C[1][2], C[2][0], C[2][1], C[2][2]);
+}
+
+// ---- pile rows: the fast form for two movable bodies
+// A pile pair's contact, kPileRowF4 float4.  Quarter q of the two bodies' velocities (q = 0
+// linear and 1 angular velocity of body a, 2 and 3 those of body b; one lane of the sweep
+// each) holds at float4 kPfQ q + k (k = 0, 1, 2: the normal n and the tangents t1, t2) the
+// quarter's part of the scaled Jacobian -k_k J_k (.w: the normal row's bias term
+// -k_n b in quarter 0, zero elsewhere) and at kPfQ q + 3 + k the update vector
+// (M^-1 J_k^T)_q, where for direction d = d_k
+//   q = 0: J = d,          M^-1 J^T = m_a^-1 d         q = 1: J = r_a x d,     I_a^-1 (r_a x d)
+//   q = 2: J = -d,         M^-1 J^T = -m_b^-1 d        q = 3: J = -(r_b x d), -I_b^-1 (r_b x d)
+// (the update of gs_core, whose impulse is -k_k (J_k v + bias)).  Float4 kPfC .. kPfC + 2
+// hold K_1, K_2, mu and the couplings C_jk to the pair's next row in the order of the fast
+// rows' float4 12 .. 14; float4 kPfL the impulses (lambda_n, lambda_t1, lambda_t2, 0),
+// which the sweeps update.  A contact with a zero normal effective mass is an all-zero row.
+constexpr int kPfQ = 6, kPfC = 24, kPfL = 27;
+static_assert(kPfL + 1 == kPileRowF4, "pile row layout");
+
+// Bodies a and b: centres of mass (world) ca, cb, world inverse inertias Ia, Ib (six stored
+// words), inverse masses ima, imb.
+__device__ __forceinline__ void build_pile_row(float4 *f, const DContact &c, V3 ca, V3 cb, const float *Ia,
+                                               const float *Ib, float ima, float imb, float mu, float hs,
+                                               float baumgarte) {
+    const V3 n = ld3(c.n), xa = ld3(c.xa);
+    const float phi = c.phi;
+    const V3 xb = xa - phi * n;
+    const V3 ra = xa - ca, rb = xb - cb;
+    V3 t1, t2;
+    tangent_basis(n, t1, t2);
+    const V3 d[3] = {n, t1, t2};
+    V3 J[3][4], W[3][4];
+    float k[3];
+    for (int j = 0; j < 3; ++j) {
+        const V3 rad = cross(ra, d[j]), rbd = cross(rb, d[j]);
+        const V3 iad = sym_mul(Ia, rad), ibd = sym_mul(Ib, rbd);
+        k[j] = eff_mass(ima, imb, rad, iad, rbd, ibd);
+        J[j][0] = d[j]; J[j][1] = rad; J[j][2] = -1.0f * d[j]; J[j][3] = -1.0f * rbd;
+        W[j][0] = ima * d[j]; W[j][1] = iad; W[j][2] = -imb * d[j]; W[j][3] = -1.0f * ibd;
+    }
+    for (int i = 0; i < kPileRowF4; ++i) f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k[0] == 0.0f) return;   // neither body can respond along n
+    const float bias = (phi > 0.0f) ? phi / hs : baumgarte * phi / hs;
+    float K[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < 3; ++j) {
+            const V3 sj = -k[j] * J[j][q];
+            f[kPfQ * q + j] = make_float4(sj.x, sj.y, sj.z, (q == 0 && j == 0) ? -k[0] * bias : 0.0f);
+            f[kPfQ * q + 3 + j] = make_float4(W[j][q].x, W[j][q].y, W[j][q].z, 0.0f);
+            K[j] += dot(sj, W[0][q]);   // K_j = -k_j J_j . M^-1 J_n^T
+        }
+    f[kPfC] = make_float4(K[1], K[2], mu, 0.0f);
+}
+
+// C_jk of pile row r against the pair's next row fn (nullptr: r is the pair's last row and
+// keeps zero couplings): next row's scaled Jacobian j dotted with this row's update vector k.
+__device__ __forceinline__ void couple_pile_row(float4 *fr, const float4 *fn) {
+    float C[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if (fn)
+        for (int q = 0; q < 4; ++q)
+            for (int j = 0; j < 3; ++j)
+                for (int kk = 0; kk < 3; ++kk) {
+                    const float4 a = fn[kPfQ * q + j], b = fr[kPfQ * q + 3 + kk];
+                    C[j][kk] += a.x * b.x + a.y * b.y + a.z * b.z;
+                }
+    fr[kPfC].w = C[0][0];
+    fr[kPfC + 1] = make_float4(C[0][1], C[0][2], C[1][0], C[1][1]);
+    fr[kPfC + 2] = make_float4(C[1][2], C[2][0], C[2][1], C[2][2]);
 }
 
 // smallest v over the warp's groups (lanes of a group hold the same v)
@@ -998,15 +1063,16 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
 }
 
 // ---------------------------------------------------------------------------------------
-// Piles: one block per pile env.  Rows of every pair with contacts; the pairs coloured
-// greedily in pair order (each takes the lowest colour that no earlier pair sharing one of
-// its movable bodies took; kMaxColors at most, the last gathering every pair left over);
-// Gauss-Seidel sweeps colour by colour.  The pairs of a colour share no movable body, so
-// the block's threads solve them at once (one thread per pair, its rows in order) with
+// Piles.  The prep (one block per pile env) applies the forces, places every pair's rows,
+// colours the pairs greedily in pair order (each takes the lowest colour that no earlier
+// pair sharing one of its movable bodies took; kMaxColors at most, the last gathering every
+// pair left over) and hands the tables and the bodies' state to the sweep kernel (one
+// cooperative launch over the GPU), which builds the rows (pile rows, the two-body fast
+// form) and runs the Gauss-Seidel sweeps colour by colour.  The pairs of a colour share no
+// movable body, so the warps solve them at once (a warp per pair, its rows in order) with
 // exactly the updates of a sweep in colour order, pair order within a colour -- except the
-// last colour, which one thread sweeps in pair order.  Shared memory: the bodies
-// (PileBodies), their colour masks and the pairs' colours; row ranges and the colour order
-// of the pairs in global memory.
+// last colour, which one warp sweeps in pair order.  The prep's shared memory: the bodies
+// (PileBodies), their colour masks and the pairs' tables (PileTables).
 
 // exclusive prefix sum over the block (blockDim a multiple of 32, at most 1024); *total:
 // the block's sum
@@ -1078,11 +1144,11 @@ __device__ void pile_colour_warp(const PileTables &T, unsigned long long *used, 
     }
 }
 
-// The pile solve, part 1 (one block per pile): external forces, each pair's rows placed
-// and built, the colours and the pairs by colour; hands the tables and the bodies' state to
-// the sweep kernel through PileSolveMem.
+// The pile solve, part 1 (one block per pile): external forces, each pair's rows placed,
+// the colours and the pairs by colour; hands the tables and the bodies' state to the sweep
+// kernel through PileSolveMem.
 __global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p, const PileDev *piles,
-                                                                     const int2 *counts, PileSolveMem M, Row *rows) {
+                                                                     const int2 *counts, PileSolveMem M) {
     extern __shared__ __align__(16) float pile_smem[];
     __shared__ int warp_sums[32];
     __shared__ int cstart[kMaxColors + 1];
@@ -1105,7 +1171,6 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p,
     T.col = reinterpret_cast<unsigned char *>(T.order + P.pcap);
     unsigned char *mov = T.col + P.pcap;
     B.mov = mov;
-    Row *prow = rows + P.row0;
     const float hs = p.hs;
     // 1. external forces
     for (int lb = t; lb < n; lb += NT) {
@@ -1141,24 +1206,9 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p,
     }
     if (t == 0 && base > P.rcap) atomicOr(p.status, kStatusOverflow);
     __syncthreads();
-    // 3. warp 0 colours the pairs; the other warps build the rows, a warp per pair with rows,
-    // its lanes over the pair's contacts
-    const int lane = t & 31, warp = t >> 5, nw = NT >> 5;
-    if (warp == 0) {
-        pile_colour_warp(T, used, np, lane);
-    } else {
-        for (int q = warp - 1; q < np; q += nw - 1) {
-            const unsigned rr = T.rr[q];
-            const int cnt = (int)(rr >> 21);
-            if (cnt == 0) continue;
-            const int r0 = (int)(rr & (kPileMaxRows - 1));
-            const unsigned ab = T.ab[q];
-            const float mu = p.pairs[P.pair0 + q].mu;
-            const DContact *con = p.contacts + (size_t)(P.pair0 + q) * p.cap_pair;
-            for (int i = lane; i < cnt; i += 32)
-                build_row(prow[r0 + i], con[i], B, (int)(ab & kAbId), (int)((ab >> 16) & kAbId), mu, hs, p.baumgarte);
-        }
-    }
+    // 3. warp 0 colours the pairs (the sweep kernel builds the rows, on every SM)
+    const int lane = t & 31, warp = t >> 5;
+    if (warp == 0) pile_colour_warp(T, used, np, lane);
     __syncthreads();
     // 4. the pairs by colour: counts, starts, then each pair a slot in its colour (any order
     // within a colour gives the same sweep: its pairs share no movable body)
@@ -1199,13 +1249,15 @@ __global__ void __launch_bounds__(kPileThreads, 1) pile_prep_kernel(SimParams p,
         M.bv[bi] = make_float4(B.v[lb][0], B.v[lb][1], B.v[lb][2], B.invm[lb]);
         M.bw[bi] = make_float4(B.w[lb][0], B.w[lb][1], B.w[lb][2], mov[lb] ? 1.0f : 0.0f);
         M.bcom[bi] = make_float4(B.com[lb][0], B.com[lb][1], B.com[lb][2], 0.0f);
+        M.binv[2 * bi] = make_float4(B.Iinv[lb][0], B.Iinv[lb][1], B.Iinv[lb][2], B.Iinv[lb][3]);
+        M.binv[2 * bi + 1] = make_float4(B.Iinv[lb][4], B.Iinv[lb][5], 0.0f, 0.0f);
     }
 }
 
 // ---- the pile solve, part 2: one cooperative kernel over the whole GPU
 constexpr int kSweepWarps = 8;                      // warps per block of the sweep kernel
 constexpr int kSweepChunk = 16;                     // rows per shared-memory chunk of a pair
-constexpr int kSweepBufF4 = 2 * kSweepChunk * kRowF4;   // two chunks per warp
+constexpr int kSweepBufF4 = 2 * kSweepChunk * kPileRowF4;   // two chunks per warp
 constexpr int kGridWaitTries = 1 << 20;             // bounded grid-barrier polls (about a second)
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *a) {
@@ -1240,74 +1292,149 @@ __device__ void grid_barrier(unsigned *bar, unsigned target, unsigned *status, i
     __syncthreads();
 }
 
-// The rows r0 .. r0 + n - 1 (global) of one pair between global bodies ga, gb, by one warp:
-// the lanes stream the rows through two shared-memory chunks of kSweepChunk rows (cp.async,
-// L2 only: the impulses were written by other SMs), lane 0 runs the Gauss-Seidel chain over
-// them with the bodies' velocities in registers (gs_core, the same update as gs_row) and
-// writes the impulses back; the velocities go back to global memory at the end (movable
-// bodies only).  Called by all 32 lanes.
+// A pile row as one lane of a pair's warp holds it: its quarter's part of the scaled
+// Jacobian (PfJ; formed into the scaled velocities one step before the row is solved), its
+// quarter's update vectors, the couplings and the impulse word (PfCW).
+struct PfJ {
+    float4 j[3];
+};
+struct PfCW {
+    float4 c[3];
+    float4 w[3];
+    float4 l;
+};
+__device__ __forceinline__ void read_pf_j(unsigned row, unsigned qo, PfJ &r) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.j[k] = lds4(row + qo + 16u * k);
+}
+__device__ __forceinline__ void read_pf_cw(unsigned row, unsigned qo, PfCW &r) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.w[k] = lds4(row + qo + 16u * (3 + k));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.c[k] = lds4(row + 16u * (kPfC + k));
+    r.l = lds4(row + 16u * kPfL);
+}
+// scaled velocities of a pile row at the velocity u: each lane dots its quarter, the four
+// lanes of the quarter group sum the parts (xor 1, then xor 2: the same sum on all four)
 template <bool kBias>
-__device__ void sweep_pair_warp(const Row *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M,
-                                int lane) {
-    const float4 *src = reinterpret_cast<const float4 *>(rows);
+__device__ __forceinline__ void pf_base(const PfJ &g, V3 u, float &bn, float &b1, float &b2) {
+    float pn = __fmaf_rn(g.j[0].z, u.z, __fmaf_rn(g.j[0].y, u.y, __fmaf_rn(g.j[0].x, u.x, kBias ? g.j[0].w : 0.0f)));
+    float p1 = __fmaf_rn(g.j[1].z, u.z, __fmaf_rn(g.j[1].y, u.y, __fmaf_rn(g.j[1].x, u.x, g.j[1].w)));
+    float p2 = __fmaf_rn(g.j[2].z, u.z, __fmaf_rn(g.j[2].y, u.y, __fmaf_rn(g.j[2].x, u.x, g.j[2].w)));
+    pn += __shfl_xor_sync(0xffffffffu, pn, 1);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+    bn = pn + __shfl_xor_sync(0xffffffffu, pn, 2);
+    b1 = p1 + __shfl_xor_sync(0xffffffffu, p1, 2);
+    b2 = p2 + __shfl_xor_sync(0xffffffffu, p2, 2);
+}
+// One Gauss-Seidel step of a pile pair, pipelined over three rows as gs_step: row j (f) is
+// solved from its carried scaled velocities while row j + 1's scaled velocities are formed
+// from its Jacobian part jn at the velocity before row j and the loads of row j + 1 (fn,
+// shared address rn) and row j + 2's Jacobian part (jnn, at rnn) are issued.  Lane 0
+// writes the new impulse word to the row in global memory (lam).
+template <bool kBias>
+__device__ __forceinline__ void pf_step(const PfCW &f, const PfJ &jn, PfCW &fn, PfJ &jnn, SweepRegs &st,
+                                        unsigned rn, unsigned rnn, unsigned qo, float4 *lam, bool leader) {
+    float bn, b1, b2;
+    pf_base<kBias>(jn, st.u, bn, b1, b2);
+    read_pf_cw(rn, qo, fn);
+    read_pf_j(rnn, qo, jnn);
+    const float4 L = f.l;
+    const float dl = fmaxf(st.sn, -L.x);                  // lambda_n' - lambda_n
+    const V3 u = st.u;
+    const V3 ud = v3(__fmaf_rn(dl, f.w[0].x, u.x), __fmaf_rn(dl, f.w[0].y, u.y), __fmaf_rn(dl, f.w[0].z, u.z));
+    const float xn = __fmaf_rn(f.c[0].w, dl, bn), x1 = __fmaf_rn(f.c[1].z, dl, b1), x2 = __fmaf_rn(f.c[2].y, dl, b2);
+    const float ln = L.x + dl;
+    const float t1 = __fmaf_rn(f.c[0].x, dl, st.s1 + L.y);
+    const float t2 = __fmaf_rn(f.c[0].y, dl, st.s2 + L.z);
+    const float sc = fminf(1.0f, (f.c[0].z * ln) * rsqrtf(__fmaf_rn(t1, t1, t2 * t2)));
+    const float e1 = __fmaf_rn(t1, sc, -L.y), e2 = __fmaf_rn(t2, sc, -L.z);
+    st.sn = __fmaf_rn(f.c[1].y, e2, __fmaf_rn(f.c[1].x, e1, xn));
+    st.s1 = __fmaf_rn(f.c[2].x, e2, __fmaf_rn(f.c[1].w, e1, x1));
+    st.s2 = __fmaf_rn(f.c[2].w, e2, __fmaf_rn(f.c[2].z, e1, x2));
+    st.u = v3(__fmaf_rn(e2, f.w[2].x, __fmaf_rn(e1, f.w[1].x, ud.x)),
+              __fmaf_rn(e2, f.w[2].y, __fmaf_rn(e1, f.w[1].y, ud.y)),
+              __fmaf_rn(e2, f.w[2].z, __fmaf_rn(e1, f.w[1].z, ud.z)));
+    if (leader) __stcg(lam, make_float4(ln, L.y + e1, L.z + e2, 0.0f));
+}
+
+// The rows 0 .. n - 1 (global, kPileRowF4 float4 each) of one pair between global bodies
+// ga, gb, by one warp: the lanes stream the rows through two shared-memory chunks of
+// kSweepChunk rows (cp.async, L2 only: the impulses were written by other SMs; chunk c + 1
+// is waited for at step 16 c + 14, whose loads reach its first row, and chunk c + 2 issued
+// into chunk c's buffer after it), and every lane runs the Gauss-Seidel chain on its quarter
+// of the two bodies' velocities (lane & 3, see build_pile_row; the other groups of four
+// lanes repeat the first's work).  The velocities go back to global memory at the end
+// (movable bodies only).  Called by all 32 lanes.
+template <bool kBias>
+__device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M, int lane) {
+    constexpr int kChunkF4P = kSweepChunk * kPileRowF4;
+    const int q = lane & 3;
+    const int gi = q < 2 ? ga : gb;
+    const float4 bv = ldcg4(M.bv + gi), bw = ldcg4(M.bw + gi);
+    SweepRegs st;
+    st.u = (q & 1) ? v3(bw.x, bw.y, bw.z) : v3(bv.x, bv.y, bv.z);
     const int nch = (n + kSweepChunk - 1) / kSweepChunk;
     auto issue = [&](int ch) {
         const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
-        float4 *dst = buf + (ch & 1) * kSweepChunk * kRowF4;
-        const float4 *s0 = src + (size_t)ch * kSweepChunk * kRowF4;
-        for (int k = lane; k < rows_in * kRowF4; k += 32) cp_async16(dst + k, s0 + k);
+        float4 *dst = buf + (ch & 1) * kChunkF4P;
+        const float4 *s0 = rows + (size_t)ch * kChunkF4P;
+        for (int k = lane; k < rows_in * kPileRowF4; k += 32) cp_async16(dst + k, s0 + k);
         cp_async_commit();
     };
-    V3 va, wa, vb, wb;
-    float ima = 0.f, imb = 0.f;
-    bool ma = false, mb = false;
-    if (lane == 0) {
-        const float4 a0 = ldcg4(M.bv + ga), a1 = ldcg4(M.bw + ga), b0 = ldcg4(M.bv + gb), b1 = ldcg4(M.bw + gb);
-        va = v3(a0.x, a0.y, a0.z); ima = a0.w; wa = v3(a1.x, a1.y, a1.z); ma = a1.w != 0.0f;
-        vb = v3(b0.x, b0.y, b0.z); imb = b0.w; wb = v3(b1.x, b1.y, b1.z); mb = b1.w != 0.0f;
-    }
     issue(0);
-    for (int ch = 0; ch < nch; ++ch) {
-        if (ch + 1 < nch) {
-            issue(ch + 1);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
+    if (nch > 1) {
+        issue(1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncwarp();
+    const unsigned b0 = smem_addr(buf), qo = 16u * kPfQ * q;
+    // shared address of row r (chunk r / kSweepChunk sits in buffer (r / kSweepChunk) & 1)
+    auto row_s = [&](int r) {
+        return b0 + 16u * (unsigned)(((r / kSweepChunk) & 1) * kChunkF4P + (r % kSweepChunk) * kPileRowF4);
+    };
+    // before step j: its loads reach the next chunk's first row at j = 16 c + 14
+    auto before = [&](int j) {
+        if (j % kSweepChunk == kSweepChunk - 2 && j / kSweepChunk + 1 < nch) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncwarp();
         }
-        __syncwarp();
-        if (lane == 0) {
-            const float4 *cb = buf + (ch & 1) * kSweepChunk * kRowF4;
-            const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
-            auto load = [&](int r, float (&x)[4 * kRowF4]) {
-#pragma unroll
-                for (int k = 0; k < kRowF4; ++k) {
-                    const float4 v = cb[r * kRowF4 + k];
-                    x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
-                }
-            };
-            auto solve = [&](int r, const float (&x)[4 * kRowF4]) {
-                float4 L = make_float4(x[kWLN], x[kWLN + 1], x[kWLN + 2], 0.0f);
-                gs_core(x, L, va, wa, vb, wb, ima, imb, kBias);
-                float *w = reinterpret_cast<float *>(const_cast<Row *>(rows) + ch * kSweepChunk + r);
-                w[kWLN] = L.x; w[kWLN + 1] = L.y; w[kWLN + 2] = L.z;
-            };
-            // the next row's words are read while one row is solved
-            float f[4 * kRowF4], g[4 * kRowF4];
-            load(0, f);
-            for (int r = 0; r < rows_in; r += 2) {
-                if (r + 1 < rows_in) load(r + 1, g);
-                solve(r, f);
-                if (r + 1 >= rows_in) break;
-                if (r + 2 < rows_in) load(r + 2, f);
-                solve(r + 1, g);
-            }
+    };
+    // after it, chunk c's rows are all in registers: its buffer takes chunk c + 2
+    auto after = [&](int j) {
+        if (j % kSweepChunk == kSweepChunk - 2 && j / kSweepChunk + 2 < nch) {
+            __syncwarp();
+            issue(j / kSweepChunk + 2);
         }
-        __syncwarp();   // the chunk's buffer is refilled two chunks later
+    };
+    // prologue: row 0's words and scaled velocities, row 1's Jacobian part (rows past n are
+    // read from the buffers but never used)
+    PfCW A, B;
+    PfJ JA, JB;
+    read_pf_cw(row_s(0), qo, A);
+    read_pf_j(row_s(0), qo, JA);
+    pf_base<kBias>(JA, st.u, st.sn, st.s1, st.s2);
+    read_pf_j(row_s(1), qo, JB);
+    const bool leader = lane == 0;
+    for (int j = 0; j < n; j += 2) {
+        before(j);
+        pf_step<kBias>(A, JB, B, JA, st, row_s(j + 1), row_s(j + 2), qo, rows + (size_t)kPileRowF4 * j + kPfL, leader);
+        after(j);
+        if (j + 1 >= n) break;
+        before(j + 1);
+        pf_step<kBias>(B, JA, A, JB, st, row_s(j + 2), row_s(j + 3), qo,
+                       rows + (size_t)kPileRowF4 * (j + 1) + kPfL, leader);
+        after(j + 1);
     }
-    if (lane == 0) {
-        if (ma) { M.bv[ga] = make_float4(va.x, va.y, va.z, ima); M.bw[ga] = make_float4(wa.x, wa.y, wa.z, 1.0f); }
-        if (mb) { M.bv[gb] = make_float4(vb.x, vb.y, vb.z, imb); M.bw[gb] = make_float4(wb.x, wb.y, wb.z, 1.0f); }
+    // (every chunk issued was waited for: chunk c at step 16 (c - 1) + 14 < n)
+    if (lane < 4 && bw.w != 0.0f) {
+        if (q & 1) M.bw[gi] = make_float4(st.u.x, st.u.y, st.u.z, bw.w);
+        else M.bv[gi] = make_float4(st.u.x, st.u.y, st.u.z, bv.w);
     }
+    __syncwarp();
 }
 
 // n_sweeps Gauss-Seidel sweeps over every pile, colour by colour with a grid barrier after
@@ -1316,7 +1443,7 @@ __device__ void sweep_pair_warp(const Row *rows, int n, int ga, int gb, float4 *
 // launch in pair order.
 template <bool kBias>
 __device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int n_piles, const PileSolveMem &M,
-                                  Row *rows, float4 *buf, int n_colors, int n_sweeps, unsigned &nbar, int *dead) {
+                                  float4 *rows, float4 *buf, int n_colors, int n_sweeps, unsigned &nbar, int *dead) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSweepWarps + (threadIdx.x >> 5), W = gridDim.x * kSweepWarps;
     for (int it = 0; it < n_sweeps; ++it) {
@@ -1331,8 +1458,9 @@ __device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int 
                     const int q = M.order[P.pair0 + k];
                     const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
                     const int r0 = (int)(rr & (kPileMaxRows - 1)), nr = (int)(rr >> 21);
-                    sweep_pair_warp<kBias>(rows + P.row0 + r0, nr, P.first_body + (int)(ab & kAbId),
-                                           P.first_body + (int)((ab >> 16) & kAbId), buf, M, lane);
+                    sweep_pair_warp<kBias>(rows + (size_t)kPileRowF4 * (P.row0 + r0), nr,
+                                           P.first_body + (int)(ab & kAbId), P.first_body + (int)((ab >> 16) & kAbId),
+                                           buf, M, lane);
                 }
             }
             ++nbar;
@@ -1342,7 +1470,7 @@ __device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int 
 }
 
 __global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimParams p, const PileDev *piles,
-                                                                          int n_piles, PileSolveMem M, Row *rows) {
+                                                                          int n_piles, PileSolveMem M, float4 *rows) {
     extern __shared__ __align__(16) float4 sweep_smem[];
     __shared__ int dead;
     if (threadIdx.x == 0) dead = 0;
@@ -1352,6 +1480,39 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimPara
     for (int k = 0; k < n_piles; ++k) n_colors = max(n_colors, M.ncol[k]);
     unsigned nbar = 0;
     const float hs = p.hs;
+    // 4. each pair's rows, a warp per pair with rows (the pairs in colour order), its lanes
+    // over the pair's contacts; then the couplings between the pair's neighbouring rows
+    {
+        const int lane = threadIdx.x & 31;
+        const int gw = blockIdx.x * kSweepWarps + (threadIdx.x >> 5), W = gridDim.x * kSweepWarps;
+        for (int k0 = 0; k0 < n_piles; ++k0) {
+            const PileDev &P = piles[k0];
+            const int total = M.cstart[k0 * (kMaxColors + 1) + kMaxColors];
+            for (int k = gw; k < total; k += W) {
+                const int q = M.order[P.pair0 + k];
+                const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
+                const int r0 = (int)(rr & (kPileMaxRows - 1)), cnt = (int)(rr >> 21);
+                const int a = P.first_body + (int)(ab & kAbId), b = P.first_body + (int)((ab >> 16) & kAbId);
+                const float4 ca = M.bcom[a], cb = M.bcom[b], ia0 = M.binv[2 * a], ia1 = M.binv[2 * a + 1];
+                const float4 ib0 = M.binv[2 * b], ib1 = M.binv[2 * b + 1];
+                const float Ia[6] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y};
+                const float Ib[6] = {ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y};
+                const float ima = M.bv[a].w, imb = M.bv[b].w;
+                const float mu = p.pairs[P.pair0 + q].mu;
+                const DContact *con = p.contacts + (size_t)(P.pair0 + q) * p.cap_pair;
+                float4 *pr = rows + (size_t)kPileRowF4 * (P.row0 + r0);
+                for (int i = lane; i < cnt; i += 32)
+                    build_pile_row(pr + kPileRowF4 * i, con[i], v3(ca.x, ca.y, ca.z), v3(cb.x, cb.y, cb.z), Ia, Ib,
+                                   ima, imb, mu, hs, p.baumgarte);
+                __syncwarp();   // the pair's rows (global) written before other lanes read them
+                for (int i = lane; i < cnt; i += 32)
+                    couple_pile_row(pr + kPileRowF4 * i, i + 1 < cnt ? pr + kPileRowF4 * (i + 1) : nullptr);
+                __syncwarp();
+            }
+        }
+    }
+    ++nbar;
+    grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, &dead);
     // 5. Gauss-Seidel sweeps
     pile_sweep_passes<true>(p, piles, n_piles, M, rows, buf, n_colors, p.n_iters, nbar, &dead);
     // 6. integration, a thread per body
@@ -1433,9 +1594,9 @@ cudaError_t prepare_pile_solve(int optin, int device, int *max_dyn, int *sweep_b
 }
 
 cudaError_t launch_pile_solve(const SimParams &p, const PileDev *piles, int n_piles, const int2 *counts,
-                              const PileSolveMem &m, Row *rows, size_t smem, int sweep_blocks, cudaStream_t s) {
+                              const PileSolveMem &m, float4 *rows, size_t smem, int sweep_blocks, cudaStream_t s) {
     if (n_piles <= 0) return cudaSuccess;
-    pile_prep_kernel<<<n_piles, kPileThreads, smem, s>>>(p, piles, counts, m, rows);
+    pile_prep_kernel<<<n_piles, kPileThreads, smem, s>>>(p, piles, counts, m);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(m.bar, 0, sizeof(unsigned), s);
