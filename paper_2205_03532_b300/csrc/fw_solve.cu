@@ -1366,26 +1366,35 @@ __device__ __forceinline__ void pf_step(const PfCW &f, const PfJ &jn, PfCW &fn, 
 // into chunk c's buffer after it), and every lane runs the Gauss-Seidel chain on its quarter
 // of the two bodies' velocities (lane & 3, see build_pile_row; the other groups of four
 // lanes repeat the first's work).  The velocities go back to global memory at the end
-// (movable bodies only).  Called by all 32 lanes.
+// (movable bodies only).  prefetched: the first chunks were issued by pile_prefetch before
+// the grid barrier ahead of the pair's colour.  Called by all 32 lanes.
+constexpr int kChunkF4P = kSweepChunk * kPileRowF4;
+// Chunk ch of a pair's n rows into the warp's buffer (ch & 1), by all 32 lanes (one commit group).
+__device__ __forceinline__ void pile_issue_chunk(const float4 *rows, int n, int ch, float4 *buf, int lane) {
+    const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
+    float4 *dst = buf + (ch & 1) * kChunkF4P;
+    const float4 *s0 = rows + (size_t)ch * kChunkF4P;
+    for (int k = lane; k < rows_in * kPileRowF4; k += 32) cp_async16(dst + k, s0 + k);
+    cp_async_commit();
+}
+// The first two chunks of a pair (the start of sweep_pair_warp), issued ahead of it.
+__device__ __forceinline__ void pile_prefetch(const float4 *rows, int n, float4 *buf, int lane) {
+    pile_issue_chunk(rows, n, 0, buf, lane);
+    if (n > kSweepChunk) pile_issue_chunk(rows, n, 1, buf, lane);
+}
+
 template <bool kBias>
-__device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M, int lane) {
-    constexpr int kChunkF4P = kSweepChunk * kPileRowF4;
+__device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M, int lane,
+                                bool prefetched) {
     const int q = lane & 3;
     const int gi = q < 2 ? ga : gb;
     const float4 bv = ldcg4(M.bv + gi), bw = ldcg4(M.bw + gi);
     SweepRegs st;
     st.u = (q & 1) ? v3(bw.x, bw.y, bw.z) : v3(bv.x, bv.y, bv.z);
     const int nch = (n + kSweepChunk - 1) / kSweepChunk;
-    auto issue = [&](int ch) {
-        const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
-        float4 *dst = buf + (ch & 1) * kChunkF4P;
-        const float4 *s0 = rows + (size_t)ch * kChunkF4P;
-        for (int k = lane; k < rows_in * kPileRowF4; k += 32) cp_async16(dst + k, s0 + k);
-        cp_async_commit();
-    };
-    issue(0);
+    auto issue = [&](int ch) { pile_issue_chunk(rows, n, ch, buf, lane); };
+    if (!prefetched) pile_prefetch(rows, n, buf, lane);
     if (nch > 1) {
-        issue(1);
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     } else {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -1437,31 +1446,85 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
     __syncwarp();
 }
 
+// A warp's first pair in each colour but the last (PileWork: row index, rows, bodies a, b
+// (global ids); rows = 0: none), and a bit per colour in which it has more pairs: built once
+// per launch, so that a colour's turn starts without the dependent loads of the tables.
+constexpr int kWorkColors = kMaxColors - 1;
+struct PileWarpWork {
+    int4 first[kWorkColors];
+    unsigned long long more;
+};
+__device__ void pile_warp_work(const PileSolveMem &M, const PileDev *piles, int n_piles, int n_colors, int gw, int W,
+                               int lane, PileWarpWork &ww) {
+    unsigned long long more = 0ull;
+    for (int c = lane; c < n_colors && c < kWorkColors; c += 32) {
+        int4 e = make_int4(0, 0, 0, 0);
+        bool found = false, again = false;
+        for (int k0 = 0; k0 < n_piles && !again; ++k0) {
+            const PileDev &P = piles[k0];
+            const int *cs = M.cstart + k0 * (kMaxColors + 1);
+            for (int k = cs[c] + gw; k < cs[c + 1]; k += W) {
+                if (found) { again = true; break; }
+                const int q = M.order[P.pair0 + k];
+                const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
+                e = make_int4(P.row0 + (int)(rr & (kPileMaxRows - 1)), (int)(rr >> 21),
+                              P.first_body + (int)(ab & kAbId), P.first_body + (int)((ab >> 16) & kAbId));
+                found = true;
+            }
+        }
+        ww.first[c] = e;
+        if (again) more |= 1ull << c;
+    }
+    more = __reduce_or_sync(0xffffffffu, (unsigned)more) | ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(more >> 32)) << 32);
+    if (lane == 0) ww.more = more;
+    __syncwarp();
+}
+
 // n_sweeps Gauss-Seidel sweeps over every pile, colour by colour with a grid barrier after
 // each colour: within a colour the launch's warps take the pairs (any order: they share no
 // movable body); the last colour, whose pairs may share bodies, is swept by warp 0 of the
-// launch in pair order.
+// launch in pair order.  A warp's first pair of a colour comes from its PileWarpWork; a
+// pair's rows (and impulses) do not change between its colour's turns, only the bodies'
+// velocities do, so before each barrier the warp issues the first chunks of its pair of the
+// next colour (with one colour, that pair may be the one just swept: no prefetch).
 template <bool kBias>
 __device__ void pile_sweep_passes(const SimParams &p, const PileDev *piles, int n_piles, const PileSolveMem &M,
-                                  float4 *rows, float4 *buf, int n_colors, int n_sweeps, unsigned &nbar, int *dead) {
+                                  float4 *rows, float4 *buf, const PileWarpWork &ww, int n_colors, int n_sweeps,
+                                  unsigned &nbar, int *dead) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSweepWarps + (threadIdx.x >> 5), W = gridDim.x * kSweepWarps;
+    bool pre = false;   // the first pair of the coming colour prefetched
     for (int it = 0; it < n_sweeps; ++it) {
         for (int c = 0; c < n_colors; ++c) {
             const bool serial = c == kMaxColors - 1;
-            for (int k0 = 0; k0 < n_piles; ++k0) {
-                const PileDev &P = piles[k0];
-                const int *cs = M.cstart + k0 * (kMaxColors + 1);
-                const int b = cs[c], e = cs[c + 1];
-                if (serial && gw != 0) continue;
-                for (int k = b + (serial ? 0 : gw); k < e; k += serial ? 1 : W) {
-                    const int q = M.order[P.pair0 + k];
-                    const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
-                    const int r0 = (int)(rr & (kPileMaxRows - 1)), nr = (int)(rr >> 21);
-                    sweep_pair_warp<kBias>(rows + (size_t)kPileRowF4 * (P.row0 + r0), nr,
-                                           P.first_body + (int)(ab & kAbId), P.first_body + (int)((ab >> 16) & kAbId),
-                                           buf, M, lane);
+            if (!serial) {
+                const int4 e = ww.first[c];
+                if (e.y > 0)
+                    sweep_pair_warp<kBias>(rows + (size_t)kPileRowF4 * e.x, e.y, e.z, e.w, buf, M, lane, pre);
+            }
+            if (serial || ((ww.more >> c) & 1ull)) {   // the rest (the last colour: warp 0 alone)
+                const int skip = serial ? -1 : ww.first[c].x;
+                for (int k0 = 0; k0 < n_piles; ++k0) {
+                    const PileDev &P = piles[k0];
+                    const int *cs = M.cstart + k0 * (kMaxColors + 1);
+                    const int b = cs[c], e = cs[c + 1];
+                    if (serial && gw != 0) continue;
+                    for (int k = b + (serial ? 0 : gw); k < e; k += serial ? 1 : W) {
+                        const int q = M.order[P.pair0 + k];
+                        const unsigned ab = M.ab[P.pair0 + q], rr = M.rr[P.pair0 + q];
+                        const int r0 = P.row0 + (int)(rr & (kPileMaxRows - 1)), nr = (int)(rr >> 21);
+                        if (r0 == skip) continue;
+                        sweep_pair_warp<kBias>(rows + (size_t)kPileRowF4 * r0, nr, P.first_body + (int)(ab & kAbId),
+                                               P.first_body + (int)((ab >> 16) & kAbId), buf, M, lane, false);
+                    }
                 }
+            }
+            // the next colour's first pair (none after the passes' last colour)
+            const int cn = c + 1 < n_colors ? c + 1 : 0;
+            pre = false;
+            if (n_colors > 1 && (c + 1 < n_colors || it + 1 < n_sweeps) && cn != kMaxColors - 1 && ww.first[cn].y > 0) {
+                pile_prefetch(rows + (size_t)kPileRowF4 * ww.first[cn].x, ww.first[cn].y, buf, lane);
+                pre = true;
             }
             ++nbar;
             grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, dead);
@@ -1511,10 +1574,14 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimPara
             }
         }
     }
+    __shared__ PileWarpWork s_work[kSweepWarps];
+    PileWarpWork &ww = s_work[threadIdx.x >> 5];
+    pile_warp_work(M, piles, n_piles, n_colors, blockIdx.x * kSweepWarps + (threadIdx.x >> 5),
+                   gridDim.x * kSweepWarps, threadIdx.x & 31, ww);
     ++nbar;
     grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, &dead);
     // 5. Gauss-Seidel sweeps
-    pile_sweep_passes<true>(p, piles, n_piles, M, rows, buf, n_colors, p.n_iters, nbar, &dead);
+    pile_sweep_passes<true>(p, piles, n_piles, M, rows, buf, ww, n_colors, p.n_iters, nbar, &dead);
     // 6. integration, a thread per body
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, GT = gridDim.x * blockDim.x;
     for (int k = 0; k < n_piles; ++k) {
@@ -1532,7 +1599,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 1) pile_sweep_kernel(SimPara
     ++nbar;
     grid_barrier(M.bar, nbar * gridDim.x + (p.stall == 1 ? 1u : 0u), p.status, &dead);
     // 7. optional bias-free sweeps
-    if (p.n_vel_iters > 0) pile_sweep_passes<false>(p, piles, n_piles, M, rows, buf, n_colors, p.n_vel_iters, nbar, &dead);
+    if (p.n_vel_iters > 0)
+        pile_sweep_passes<false>(p, piles, n_piles, M, rows, buf, ww, n_colors, p.n_vel_iters, nbar, &dead);
     for (int k = 0; k < n_piles; ++k) {
         const PileDev &P = piles[k];
         for (int lb = gt; lb < P.n_bodies; lb += GT) {
