@@ -1401,42 +1401,43 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
     }
     __syncwarp();
     const unsigned b0 = smem_addr(buf), qo = 16u * kPfQ * q;
-    // shared address of row r (chunk r / kSweepChunk sits in buffer (r / kSweepChunk) & 1)
-    auto row_s = [&](int r) {
-        return b0 + 16u * (unsigned)(((r / kSweepChunk) & 1) * kChunkF4P + (r % kSweepChunk) * kPileRowF4);
-    };
-    // before step j: its loads reach the next chunk's first row at j = 16 c + 14
-    auto before = [&](int j) {
-        if (j % kSweepChunk == kSweepChunk - 2 && j / kSweepChunk + 1 < nch) {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            __syncwarp();
-        }
-    };
-    // after it, chunk c's rows are all in registers: its buffer takes chunk c + 2
-    auto after = [&](int j) {
-        if (j % kSweepChunk == kSweepChunk - 2 && j / kSweepChunk + 2 < nch) {
-            __syncwarp();
-            issue(j / kSweepChunk + 2);
-        }
-    };
+    constexpr unsigned kRowBP = 16u * kPileRowF4, kChunkBP = 16u * kChunkF4P;
     // prologue: row 0's words and scaled velocities, row 1's Jacobian part (rows past n are
     // read from the buffers but never used)
     PfCW A, B;
     PfJ JA, JB;
-    read_pf_cw(row_s(0), qo, A);
-    read_pf_j(row_s(0), qo, JA);
+    read_pf_cw(b0, qo, A);
+    read_pf_j(b0, qo, JA);
     pf_base<kBias>(JA, st.u, st.sn, st.s1, st.s2);
-    read_pf_j(row_s(1), qo, JB);
+    read_pf_j(b0 + kRowBP, qo, JB);
     const bool leader = lane == 0;
-    for (int j = 0; j < n; j += 2) {
-        before(j);
-        pf_step<kBias>(A, JB, B, JA, st, row_s(j + 1), row_s(j + 2), qo, rows + (size_t)kPileRowF4 * j + kPfL, leader);
-        after(j);
-        if (j + 1 >= n) break;
-        before(j + 1);
-        pf_step<kBias>(B, JA, A, JB, st, row_s(j + 2), row_s(j + 3), qo,
-                       rows + (size_t)kPileRowF4 * (j + 1) + kPfL, leader);
-        after(j + 1);
+    // chunk c (buffer cur; chunk c + 1 in nxt) row by row, two steps per trip at constant
+    // shared-memory offsets; step 14 of the chunk loads the next chunk's first row: it waits
+    // for that chunk, and after it chunk c's buffer takes chunk c + 2.  A full chunk runs
+    // without step guards, the last partial one stops at row n.
+    for (int c = 0; c < nch; ++c) {
+        const unsigned cur = b0 + kChunkBP * (unsigned)(c & 1), nxt = b0 + kChunkBP * (unsigned)((c + 1) & 1);
+        float4 *lam = rows + (size_t)kChunkF4P * c + kPfL;
+        const int left = n - kSweepChunk * c;   // rows of this chunk and after
+        const bool full = left >= kSweepChunk;
+#pragma unroll
+        for (int jj = 0; jj < kSweepChunk; jj += 2) {
+            if (!full && jj >= left) break;
+            if (jj == kSweepChunk - 2 && c + 1 < nch) {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                __syncwarp();
+            }
+            const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
+            const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
+            const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
+            pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
+            if (jj == kSweepChunk - 2 && c + 2 < nch) {
+                __syncwarp();
+                issue(c + 2);
+            }
+            if (!full && jj + 1 >= left) break;
+            pf_step<kBias>(B, JA, A, JB, st, r2, r3, qo, lam + kPileRowF4 * (jj + 1), leader);
+        }
     }
     // (every chunk issued was waited for: chunk c at step 16 (c - 1) + 14 < n)
     if (lane < 4 && bw.w != 0.0f) {
