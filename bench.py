@@ -27,18 +27,19 @@ sys.path.insert(0, ROOT)
 
 # Per-launch DRAM traffic (read + write bytes) of the substep kernels from a one-pass ncu
 # capture of the default workload, keyed by the sha256 of the substep kernels' sources
-# (SUBSTEP_SOURCES) it was taken on; reported only while they are unchanged (profiles/
-# holds the capture).
+# (SUBSTEP_SOURCES) it was taken on; reported only while they are unchanged (the capture's
+# summary is kept under profiles/).
 NCU_TRAFFIC = {
-    # profiles/dram_traffic_nut_bolt_1000.md (1000 M16 nut-bolt envs, FP32, the bench's default
-    # command, launches in its per-kernel timing pass over the timed frames)
-    "091c3c194e6ce77a": {"map_kernel": 0.12e6, "query_kernel": 25.40e6, "reduce_kernel": 72.17e6,
-                         "solve_kernel": 90.34e6},
+    # 1000 M16 nut-bolt envs, FP32, the bench's launch shapes fixed (solve 2 envs per warp x
+    # 1 warp, query 256 threads, reduction 4 warps), launches in its per-kernel timing pass
+    # over the timed frames
+    "b305ab9c4b6046c4": {"map_kernel": 0.12e6, "query_kernel": 31.67e6, "reduce_kernel": 82.24e6,
+                         "solve_kernel": 132.94e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "091c3c194e6ce77a": {"map_kernel": 0.7e6, "query_kernel": 582.1e6, "reduce_kernel": 273.0e6,
-                         "solve_kernel": 2995.2e6},
+    "b305ab9c4b6046c4": {"map_kernel": 0.69e6, "query_kernel": 603.0e6, "reduce_kernel": 296.7e6,
+                         "solve_kernel": 3124.7e6},
 }
 
 FP32_LANES_PER_SM = 128
