@@ -791,8 +791,14 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 // ---------------------------------------------------------------------------------------
 // kThr threads per CTA (per-sample generation: 128, 256 or 512, chosen by the detection
 // autotuner; each thread queries kBatch / kThr samples; per-triangle generation: 256).
+// Resident blocks per SM the query kernel is compiled for.  Per-sample lookups wait on the
+// cell loads (L2 hits): five 256-thread blocks (48 registers a thread, a 20-byte spill) ran
+// 6.6% faster than four (64 registers) at 1000 nut-bolt envs, six (40 registers, more
+// spills) 2%.  Per-triangle generation keeps four (its 32 KB of face results per block).
+constexpr int query_min_blocks(bool tri, int thr) { return tri ? 1024 / thr : (thr <= 256 ? 5 : 1024 / thr); }
+
 template <bool kTri, int kStore, int kThr>
-__global__ void __launch_bounds__(kThr, kThr == 128 ? 5 : 1024 / kThr) query_kernel(SimParams p) {
+__global__ void __launch_bounds__(kThr, query_min_blocks(kTri, kThr)) query_kernel(SimParams p) {
     static_assert(!kTri || kThr == kQueryThreads, "per-triangle generation runs 256 threads");
     constexpr int NPER = kBatch / kThr, NW = kThr / 32;
     const int item = blockIdx.x;

@@ -1419,24 +1419,35 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
         const unsigned cur = b0 + kChunkBP * (unsigned)(c & 1), nxt = b0 + kChunkBP * (unsigned)((c + 1) & 1);
         float4 *lam = rows + (size_t)kChunkF4P * c + kPfL;
         const int left = n - kSweepChunk * c;   // rows of this chunk and after
-        const bool full = left >= kSweepChunk;
+        if (left >= kSweepChunk) {   // a full chunk: no step guards, one block of straight-line steps
 #pragma unroll
-        for (int jj = 0; jj < kSweepChunk; jj += 2) {
-            if (!full && jj >= left) break;
-            if (jj == kSweepChunk - 2 && c + 1 < nch) {
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                __syncwarp();
+            for (int jj = 0; jj < kSweepChunk; jj += 2) {
+                if (jj == kSweepChunk - 2 && c + 1 < nch) {
+                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                    __syncwarp();
+                }
+                const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
+                const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
+                const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
+                pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
+                if (jj == kSweepChunk - 2 && c + 2 < nch) {
+                    __syncwarp();
+                    issue(c + 2);
+                }
+                pf_step<kBias>(B, JA, A, JB, st, r2, r3, qo, lam + kPileRowF4 * (jj + 1), leader);
             }
-            const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
-            const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
-            const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
-            pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
-            if (jj == kSweepChunk - 2 && c + 2 < nch) {
-                __syncwarp();
-                issue(c + 2);
+        } else {   // the pair's last, partial chunk (no next chunk to wait for or to issue)
+#pragma unroll
+            for (int jj = 0; jj < kSweepChunk; jj += 2) {
+                if (jj >= left) break;
+                // rows past the chunk (read, never used) wrap into the other buffer: in bounds
+                const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
+                const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
+                const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
+                pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
+                if (jj + 1 >= left) break;
+                pf_step<kBias>(B, JA, A, JB, st, r2, r3, qo, lam + kPileRowF4 * (jj + 1), leader);
             }
-            if (!full && jj + 1 >= left) break;
-            pf_step<kBias>(B, JA, A, JB, st, r2, r3, qo, lam + kPileRowF4 * (jj + 1), leader);
         }
     }
     // (every chunk issued was waited for: chunk c at step 16 (c - 1) + 14 < n)
