@@ -416,7 +416,7 @@ fw_status ensure_device(fw_world *w) {
         CK(cudaMalloc(&w->d_envs, sizeof(EnvDev) * ne));
         CK(cudaMemcpy(w->d_envs, dev.data(), sizeof(EnvDev) * ne, cudaMemcpyHostToDevice));
         long long rl = 0;
-        for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + E.row_cap + kRowPad);
+        for (auto &E : w->envs) rl = std::max(rl, (long long)E.row_off + env_row_span(E));
         w->rows_len = std::max(rl, 1LL);
         CK(cudaMalloc(&w->d_rows, sizeof(Row) * w->rows_len));
     }
@@ -1104,12 +1104,12 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
     const int e0 = (int)w->envs.size();
     long long scratch = 0, rows = 0;
     for (auto &P : w->pairs) scratch = std::max(scratch, (long long)P.scratch_off + 2LL * pair_sources(w, P.asset_a));
-    for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + E.row_cap + kRowPad);
+    for (auto &E : w->envs) rows = std::max(rows, (long long)E.row_off + env_row_span(E));
     long long more = 0;
     for (int e = 0; e < n_envs; ++e)
         for (int k = 0; k < n_pairs; ++k) more += 2LL * pair_sources(w, bd[e * n_per_env + pairs[2 * k]].asset);
     if (scratch + more > 0x7FFFFFFFLL) return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many samples in total");
-    if (rows + (long long)n_envs * (n_pairs * cap_pair(w) + kRowPad) > 0x7FFFFFFFLL)
+    if (rows + (long long)n_envs * (2LL * n_pairs * cap_pair(w) + kRowPad) > 0x7FFFFFFFLL)
         return fail(w, FW_ERR_ARG, "fw_add_env_bodies: too many contact rows in total");
     for (int e = 0; e < n_envs; ++e) {
         EnvDev E;
@@ -1121,13 +1121,13 @@ fw_status fw_add_env_bodies(fw_world *w, int n_envs, const fw_body_desc *bd, int
         E.row_off = (int)rows;
         E.row_cap = n_pairs * cap_pair(w);
         E.pile = -1;
-        rows += E.row_cap + kRowPad;
-        for (int i = 0; i < n_per_env; ++i) append_body(w, bd[e * n_per_env + i]);
         E.movable = -1;
         for (int i = 0; i < n_per_env; ++i) {
             const int t = bd[e * n_per_env + i].type;
             if (t == FW_BODY_DYNAMIC || t == FW_BODY_FIXED_AXIS) E.movable = (E.movable == -1) ? i : -2;
         }
+        rows += env_row_span(E);
+        for (int i = 0; i < n_per_env; ++i) append_body(w, bd[e * n_per_env + i]);
         for (int k = 0; k < n_pairs; ++k) {
             PairDev P;
             memset(&P, 0, sizeof P);

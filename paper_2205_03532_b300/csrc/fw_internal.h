@@ -94,6 +94,10 @@ struct EnvDev {
     int movable;             // local id of the only movable body, -1 none, -2 several
     int pile;                // index of the env's pile (PileDev), -1 for an env of listed pairs
 };
+// Row-buffer slots (Row) an env's region spans: its rows and the kRowPad repeat rows; an env
+// of several movable bodies takes two slots per row (its two-body fast rows, kPileRowF4
+// float4 each, when the solve runs them).
+inline long long env_row_span(const EnvDev &E) { return (E.movable == -2 ? 2LL : 1LL) * E.row_cap + kRowPad; }
 
 // A pile env: up to kMaxPileBodies bodies whose pairs a broad phase finds at every detection
 // (pile_pairs_kernel), solved colour by colour (pile_solve_kernel).  Its pairs, items,

@@ -905,6 +905,14 @@ __device__ void sweep_jacobi(float4 *rows_, int nr, int n_sweeps, V3 &va, V3 &wa
 // kernel so the others keep their code and registers.
 enum : int { kVarGS = 0, kVarMulti = 1, kVarJacobi = 2 };
 
+// Rows per shared-memory chunk when an env of several movable bodies runs the two-body fast
+// rows: two chunks fit the env slot's chunk buffers.
+constexpr int kEnvPfChunk = 8;
+static_assert(2 * kEnvPfChunk * kPileRowF4 <= kChunkBufs * kChunkF4, "two-body row chunks fit the env slot");
+template <bool kBias>
+__device__ void sweep_env_pf(const SimParams &p, const EnvDev &E, const int *row_base, float4 *frows, BodySm &B,
+                             float4 *buf, int lane, int n_sweeps);
+
 template <int kGroups, int kVar>
 __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams p) {
     constexpr bool kMulti = kVar == kVarMulti, kJacobi = kVar == kVarJacobi;
@@ -956,7 +964,10 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     float4 *ring = chunk_buf;   // the general form's cp.async ring (it has no chunk stream)
     const int m = E.movable;
     const bool fast = (m != -2) && (kJacobi || nr <= p.lam_cap);
-    // several movable bodies: general rows, impulses in shared memory when they fit
+    // several movable bodies with the warp to itself: the two-body fast rows (pile rows), swept
+    // pair by pair with the pair's velocities carried by four lanes (sweep_env_pf); with
+    // several envs per warp, general rows, impulses in shared memory when they fit
+    const bool pf = kMulti && kGroups == 1 && valid && m == -2;
     const bool general_sm = kMulti && (m == -2) && nr <= p.lam_cap;
     float4 *frows = reinterpret_cast<float4 *>(rows);
     // 2. constraint preparation, one contact per lane, then the couplings between neighbours
@@ -966,7 +977,11 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         const int cnt = S.row_base[k + 1] - S.row_base[k];
         for (int i = gl; i < cnt; i += G) {
             const DContact &c = p.contacts[(long long)pi * p.cap_pair + i];
-            if (fast) {
+            if (pf) {
+                const int a = P.local_a, b = P.local_b;
+                build_pile_row(frows + kPileRowF4 * (S.row_base[k] + i), c, smv(B.com, a), smv(B.com, b), B.Iinv[a],
+                               B.Iinv[b], B.invm[a], B.invm[b], P.mu, hs, p.baumgarte);
+            } else if (fast) {
                 // Jacobi keeps its impulses in the row (float4 13, zeroed here) and has no
                 // shared-memory impulse words: its lam region is empty (lam_cap = 0)
                 float4 unused;
@@ -981,6 +996,14 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
     }
     __threadfence_block();
     __syncwarp();
+    if (pf) {   // couplings between a pair's neighbouring rows; the rows are read next by cp.async (L2)
+        for (int k = 0; k < E.n_pairs; ++k) {
+            const int r0 = S.row_base[k], cnt = S.row_base[k + 1] - r0;
+            for (int i = gl; i < cnt; i += G)
+                couple_pile_row(frows + kPileRowF4 * (r0 + i), i + 1 < cnt ? frows + kPileRowF4 * (r0 + i + 1) : nullptr);
+        }
+        __threadfence();
+    }
     const bool streamed = !kJacobi && fast && m >= 0 && nr > 0;   // rows read through the chunk stream
     if (streamed) {
         for (int r = gl; r < nr; r += G) couple_fast_row(frows + kRowF4 * r, frows + kRowF4 * (r + 1 < nr ? r + 1 : 0));
@@ -1021,7 +1044,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
         else waits_ok = sweep_fast<G, true>(rs, total, trips, lam, va, wa, gl);
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
     }
-    if (valid && !fast && gl == 0) {
+    if (pf) sweep_env_pf<true>(p, E, S.row_base, frows, B, chunk_buf, lane, p.n_iters);
+    else if (valid && !fast && gl == 0) {
         if (kMulti && general_sm) sweep_general(rows, nr, p.n_iters, ring, lam, B, true);
         else for (int it = 0; it < p.n_iters; ++it) sweep(rows, nr, B, true);
     }
@@ -1044,7 +1068,8 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) solve_kernel(SimParams
             waits_ok = sweep_fast<G, false>(rs, total, trips, lam, va, wa, gl);
         }
         if (run_fast && gl == 0) { smv_set(B.v, m, va); smv_set(B.w, m, wa); }
-        if (valid && !fast && gl == 0) {
+        if (pf) sweep_env_pf<false>(p, E, S.row_base, frows, B, chunk_buf, lane, p.n_vel_iters);
+        else if (valid && !fast && gl == 0) {
             if (kMulti && general_sm) sweep_general(rows, nr, p.n_vel_iters, ring, lam, B, false);
             else for (int it = 0; it < p.n_vel_iters; ++it) sweep(rows, nr, B, false);
         }
@@ -1359,41 +1384,41 @@ __device__ __forceinline__ void pf_step(const PfCW &f, const PfJ &jn, PfCW &fn, 
     if (leader) __stcg(lam, make_float4(ln, L.y + e1, L.z + e2, 0.0f));
 }
 
-// The rows 0 .. n - 1 (global, kPileRowF4 float4 each) of one pair between global bodies
-// ga, gb, by one warp: the lanes stream the rows through two shared-memory chunks of
-// kSweepChunk rows (cp.async, L2 only: the impulses were written by other SMs; chunk c + 1
-// is waited for at step 16 c + 14, whose loads reach its first row, and chunk c + 2 issued
-// into chunk c's buffer after it), and every lane runs the Gauss-Seidel chain on its quarter
-// of the two bodies' velocities (lane & 3, see build_pile_row; the other groups of four
-// lanes repeat the first's work).  The velocities go back to global memory at the end
-// (movable bodies only).  prefetched: the first chunks were issued by pile_prefetch before
-// the grid barrier ahead of the pair's colour.  Called by all 32 lanes.
-constexpr int kChunkF4P = kSweepChunk * kPileRowF4;
-// Chunk ch of a pair's n rows into the warp's buffer (ch & 1), by all 32 lanes (one commit group).
-__device__ __forceinline__ void pile_issue_chunk(const float4 *rows, int n, int ch, float4 *buf, int lane) {
-    const int rows_in = min(kSweepChunk, n - ch * kSweepChunk);
-    float4 *dst = buf + (ch & 1) * kChunkF4P;
-    const float4 *s0 = rows + (size_t)ch * kChunkF4P;
+// Chunk ch of a pair's n rows (kCh rows per chunk) into the warp's buffer (ch & 1), by all 32
+// lanes (one commit group).
+template <int kCh>
+__device__ __forceinline__ void pf_issue_chunk(const float4 *rows, int n, int ch, float4 *buf, int lane) {
+    constexpr int kChF4 = kCh * kPileRowF4;
+    const int rows_in = min(kCh, n - ch * kCh);
+    float4 *dst = buf + (ch & 1) * kChF4;
+    const float4 *s0 = rows + (size_t)ch * kChF4;
     for (int k = lane; k < rows_in * kPileRowF4; k += 32) cp_async16(dst + k, s0 + k);
     cp_async_commit();
 }
-// The first two chunks of a pair (the start of sweep_pair_warp), issued ahead of it.
-__device__ __forceinline__ void pile_prefetch(const float4 *rows, int n, float4 *buf, int lane) {
-    pile_issue_chunk(rows, n, 0, buf, lane);
-    if (n > kSweepChunk) pile_issue_chunk(rows, n, 1, buf, lane);
+// The first two chunks of a pair (the start of pf_pair_rows), issued ahead of it.
+template <int kCh>
+__device__ __forceinline__ void pf_prefetch(const float4 *rows, int n, float4 *buf, int lane) {
+    pf_issue_chunk<kCh>(rows, n, 0, buf, lane);
+    if (n > kCh) pf_issue_chunk<kCh>(rows, n, 1, buf, lane);
 }
 
-template <bool kBias>
-__device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M, int lane,
-                                bool prefetched) {
+// The rows 0 .. n - 1 (global, kPileRowF4 float4 each) of one pair, by one warp, from the
+// velocity quarter u of this lane (lane & 3, see build_pile_row; the other groups of four
+// lanes repeat the first's work), which it leaves as the pair's Gauss-Seidel update makes
+// it.  The lanes stream the rows through two shared-memory chunks of kCh rows at buf
+// (cp.async, L2 only: impulses may have been written by other SMs; chunk c + 1 is waited
+// for at step kCh c + kCh - 2, whose loads reach its first row, and chunk c + 2 issued into
+// chunk c's buffer after it); lane 0 writes each impulse word back.  prefetched: the first
+// chunks were issued by pf_prefetch.  Called by all 32 lanes.
+template <bool kBias, int kCh>
+__device__ void pf_pair_rows(float4 *rows, int n, float4 *buf, int lane, V3 &u, bool prefetched) {
+    constexpr int kChF4 = kCh * kPileRowF4;
     const int q = lane & 3;
-    const int gi = q < 2 ? ga : gb;
-    const float4 bv = ldcg4(M.bv + gi), bw = ldcg4(M.bw + gi);
     SweepRegs st;
-    st.u = (q & 1) ? v3(bw.x, bw.y, bw.z) : v3(bv.x, bv.y, bv.z);
-    const int nch = (n + kSweepChunk - 1) / kSweepChunk;
-    auto issue = [&](int ch) { pile_issue_chunk(rows, n, ch, buf, lane); };
-    if (!prefetched) pile_prefetch(rows, n, buf, lane);
+    st.u = u;
+    const int nch = (n + kCh - 1) / kCh;
+    auto issue = [&](int ch) { pf_issue_chunk<kCh>(rows, n, ch, buf, lane); };
+    if (!prefetched) pf_prefetch<kCh>(rows, n, buf, lane);
     if (nch > 1) {
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     } else {
@@ -1401,7 +1426,7 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
     }
     __syncwarp();
     const unsigned b0 = smem_addr(buf), qo = 16u * kPfQ * q;
-    constexpr unsigned kRowBP = 16u * kPileRowF4, kChunkBP = 16u * kChunkF4P;
+    constexpr unsigned kRowBP = 16u * kPileRowF4, kChunkBP = 16u * kChF4;
     // prologue: row 0's words and scaled velocities, row 1's Jacobian part (rows past n are
     // read from the buffers but never used)
     PfCW A, B;
@@ -1412,25 +1437,26 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
     read_pf_j(b0 + kRowBP, qo, JB);
     const bool leader = lane == 0;
     // chunk c (buffer cur; chunk c + 1 in nxt) row by row, two steps per trip at constant
-    // shared-memory offsets; step 14 of the chunk loads the next chunk's first row: it waits
-    // for that chunk, and after it chunk c's buffer takes chunk c + 2.  A full chunk runs
-    // without step guards, the last partial one stops at row n.
+    // shared-memory offsets; step kCh - 2 of the chunk loads the next chunk's first row: it
+    // waits for that chunk, and after it chunk c's buffer takes chunk c + 2.  A full chunk
+    // runs as one straight-line block of steps (step guards would split every step into its
+    // own block: measured slower), the last partial one stops at row n.
     for (int c = 0; c < nch; ++c) {
         const unsigned cur = b0 + kChunkBP * (unsigned)(c & 1), nxt = b0 + kChunkBP * (unsigned)((c + 1) & 1);
-        float4 *lam = rows + (size_t)kChunkF4P * c + kPfL;
-        const int left = n - kSweepChunk * c;   // rows of this chunk and after
-        if (left >= kSweepChunk) {   // a full chunk: no step guards, one block of straight-line steps
+        float4 *lam = rows + (size_t)kChF4 * c + kPfL;
+        const int left = n - kCh * c;   // rows of this chunk and after
+        if (left >= kCh) {
 #pragma unroll
-            for (int jj = 0; jj < kSweepChunk; jj += 2) {
-                if (jj == kSweepChunk - 2 && c + 1 < nch) {
+            for (int jj = 0; jj < kCh; jj += 2) {
+                if (jj == kCh - 2 && c + 1 < nch) {
                     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                     __syncwarp();
                 }
-                const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
-                const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
-                const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
+                const unsigned r1 = (jj + 1 < kCh) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kCh);
+                const unsigned r2 = (jj + 2 < kCh) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kCh);
+                const unsigned r3 = (jj + 3 < kCh) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kCh);
                 pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
-                if (jj == kSweepChunk - 2 && c + 2 < nch) {
+                if (jj == kCh - 2 && c + 2 < nch) {
                     __syncwarp();
                     issue(c + 2);
                 }
@@ -1438,22 +1464,66 @@ __device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf
             }
         } else {   // the pair's last, partial chunk (no next chunk to wait for or to issue)
 #pragma unroll
-            for (int jj = 0; jj < kSweepChunk; jj += 2) {
+            for (int jj = 0; jj < kCh; jj += 2) {
                 if (jj >= left) break;
                 // rows past the chunk (read, never used) wrap into the other buffer: in bounds
-                const unsigned r1 = (jj + 1 < kSweepChunk) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kSweepChunk);
-                const unsigned r2 = (jj + 2 < kSweepChunk) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kSweepChunk);
-                const unsigned r3 = (jj + 3 < kSweepChunk) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kSweepChunk);
+                const unsigned r1 = (jj + 1 < kCh) ? cur + kRowBP * (jj + 1) : nxt + kRowBP * (jj + 1 - kCh);
+                const unsigned r2 = (jj + 2 < kCh) ? cur + kRowBP * (jj + 2) : nxt + kRowBP * (jj + 2 - kCh);
+                const unsigned r3 = (jj + 3 < kCh) ? cur + kRowBP * (jj + 3) : nxt + kRowBP * (jj + 3 - kCh);
                 pf_step<kBias>(A, JB, B, JA, st, r1, r2, qo, lam + kPileRowF4 * jj, leader);
                 if (jj + 1 >= left) break;
                 pf_step<kBias>(B, JA, A, JB, st, r2, r3, qo, lam + kPileRowF4 * (jj + 1), leader);
             }
         }
     }
-    // (every chunk issued was waited for: chunk c at step 16 (c - 1) + 14 < n)
+    // (every chunk issued was waited for: chunk c at step kCh (c - 1) + kCh - 2 < n)
+    u = st.u;
+}
+
+// n_sweeps Gauss-Seidel sweeps of an env of several movable bodies over its two-body fast
+// rows, pair by pair in pair order (the order of the general form's sweep): the lanes take
+// the pair's velocity quarters from the env's body store, pf_pair_rows runs its rows, lanes
+// 0-3 write the quarters back before the next pair (which may share a body) reads them.
+// One env per warp: all 32 lanes take the same pairs.
+template <bool kBias>
+__device__ void sweep_env_pf(const SimParams &p, const EnvDev &E, const int *row_base, float4 *frows, BodySm &B,
+                             float4 *buf, int lane, int n_sweeps) {
+    const int q = lane & 3;
+    for (int it = 0; it < n_sweeps; ++it)
+        for (int k = 0; k < E.n_pairs; ++k) {
+            const int r0 = row_base[k], n = row_base[k + 1] - r0;
+            if (n == 0) continue;
+            const PairDev P = p.pairs[E.first_pair + k];
+            const int bi = q < 2 ? P.local_a : P.local_b;
+            V3 u = (q & 1) ? smv(B.w, bi) : smv(B.v, bi);
+            pf_pair_rows<kBias, kEnvPfChunk>(frows + (size_t)kPileRowF4 * r0, n, buf, lane, u, false);
+            __syncwarp();
+            if (lane < 4) {
+                if (q & 1) smv_set(B.w, bi, u);
+                else smv_set(B.v, bi, u);
+            }
+            __syncwarp();
+        }
+}
+
+__device__ __forceinline__ void pile_prefetch(const float4 *rows, int n, float4 *buf, int lane) {
+    pf_prefetch<kSweepChunk>(rows, n, buf, lane);
+}
+
+// One pile pair between global bodies ga, gb (pf_pair_rows with kSweepChunk-row chunks):
+// the lane's velocity quarter comes from global memory (L2: other SMs wrote it) and goes
+// back there at the end (movable bodies only).
+template <bool kBias>
+__device__ void sweep_pair_warp(float4 *rows, int n, int ga, int gb, float4 *buf, const PileSolveMem &M, int lane,
+                                bool prefetched) {
+    const int q = lane & 3;
+    const int gi = q < 2 ? ga : gb;
+    const float4 bv = ldcg4(M.bv + gi), bw = ldcg4(M.bw + gi);
+    V3 u = (q & 1) ? v3(bw.x, bw.y, bw.z) : v3(bv.x, bv.y, bv.z);
+    pf_pair_rows<kBias, kSweepChunk>(rows, n, buf, lane, u, prefetched);
     if (lane < 4 && bw.w != 0.0f) {
-        if (q & 1) M.bw[gi] = make_float4(st.u.x, st.u.y, st.u.z, bw.w);
-        else M.bv[gi] = make_float4(st.u.x, st.u.y, st.u.z, bv.w);
+        if (q & 1) M.bw[gi] = make_float4(u.x, u.y, u.z, bw.w);
+        else M.bv[gi] = make_float4(u.x, u.y, u.z, bv.w);
     }
     __syncwarp();
 }

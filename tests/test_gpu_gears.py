@@ -118,11 +118,14 @@ def test_collide_per_pair(gears):
                 assert abs(len(g) - len(o)) <= max(3, 0.15 * len(o)), (env, pair, len(g), len(o))
 
 
-def test_solve_identical_contacts_one_substep(gears):
+@pytest.mark.parametrize("shape", [(0, 0), (1, 1)])
+def test_solve_identical_contacts_one_substep(gears, shape):
     """Both pairs' contacts given to both sides (float32-rounded), one substep: the general
-    sweep form (two movable fixed-axis bodies, pairs in order)."""
+    sweep form (two movable fixed-axis bodies, pairs in order) at the default shape, and the
+    two-body fast rows (one env per warp, pair by pair) at shape (1, 1)."""
     sc, gw, ow = gears
     fw = _fw()
+    gw.set_solve_shape(*shape)
     hs = sc.sim.dt / sc.sim.n_substeps
     p, q, v, w = gw.get_state()
     ow.set_state(p, q, v, w)
@@ -143,11 +146,12 @@ def test_solve_identical_contacts_one_substep(gears):
         gw.set_contacts(env, np.concatenate(parts))
     gw.substep(hs, sc.sim.n_iters, detect=False)
     ow.substep(hs, sc.sim.n_iters, detect=False)
+    gw.set_solve_shape(0, 0)
     gp, gq, gv, gom = gw.get_state()
     op, oq, ov, oom = ow.state()
     for i in range(len(gp)):
-        assert np.linalg.norm(gp[i] - op[i]) <= 1e-6, (i, gp[i], op[i])
-        assert _rot_angle(gq[i].astype(np.float64), oq[i]) <= 1e-6, (i, gq[i], oq[i])
+        assert np.linalg.norm(gp[i] - op[i]) <= 1e-6, (i, shape, gp[i], op[i])
+        assert _rot_angle(gq[i].astype(np.float64), oq[i]) <= 1e-6, (i, shape, gq[i], oq[i])
     assert np.max(np.abs(gom - oom)) <= 1e-4 * max(1.0, float(np.max(np.abs(oom))))
 
 

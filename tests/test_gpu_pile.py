@@ -73,9 +73,14 @@ def test_collide_per_pair_and_broad_phase(stacks):
     assert far > 20 and near > 20, (far, near)
 
 
-def test_solve_identical_contacts_one_substep(stacks):
+@pytest.mark.parametrize("shape", [(0, 0), (1, 1)])
+def test_solve_identical_contacts_one_substep(stacks, shape):
+    """Identical contacts, one substep: the default shape (two envs per warp: the general
+    form, lane 0 of an env's lanes over full rows) and one env per warp (the two-body fast
+    rows, pair by pair with four lanes per pair)."""
     sc, gw, ow = stacks
     fw = _fw()
+    gw.set_solve_shape(*shape)
     hs = sc.sim.dt / sc.sim.n_substeps
     p, q, v, w = gw.get_state()
     ow.set_state(p, q, v, w)
@@ -97,11 +102,12 @@ def test_solve_identical_contacts_one_substep(stacks):
         gw.set_contacts(env, np.concatenate(parts))
     gw.substep(hs, sc.sim.n_iters, detect=False)
     ow.substep(hs, sc.sim.n_iters, detect=False)
+    gw.set_solve_shape(0, 0)
     gp, gq = gw.get_state()[:2]
     op, oq = ow.state()[:2]
     for i in range(len(gp)):
-        assert np.linalg.norm(gp[i] - op[i]) <= 1e-6, (i, gp[i], op[i])
-        assert _rot_angle(gq[i].astype(np.float64), oq[i]) <= 1e-6, (i, gq[i], oq[i])
+        assert np.linalg.norm(gp[i] - op[i]) <= 1e-6, (i, shape, gp[i], op[i])
+        assert _rot_angle(gq[i].astype(np.float64), oq[i]) <= 1e-6, (i, shape, gq[i], oq[i])
 
 
 def test_one_frame_of_stacks(stacks):

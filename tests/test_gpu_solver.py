@@ -207,9 +207,11 @@ def test_frictionless_two_body_momentum_on_gpu():
 def test_solve_shapes_give_bit_identical_results():
     """Envs sharing a warp (2 or 4 per warp) and blocks of several warps run the same
     arithmetic per env as one env per warp: states agree bit for bit.  Fast-form envs
-    (one dynamic cube on a static slab) and general-form envs (two dynamic cubes) are
-    interleaved so that warps hold both kinds, and the env count leaves ragged warps and
-    blocks."""
+    (one dynamic cube on a static slab) and envs of two movable bodies (two dynamic cubes)
+    are interleaved so that warps hold both kinds, and the env count leaves ragged warps
+    and blocks.  The two-movable envs run the general form when they share a warp and the
+    two-body fast rows with a warp each (shapes (1, w)): bit for bit within each of the
+    two, and to float32 rounding between them."""
     fw = _fw()
     V, T, Sp = _cube(n=900)
     GV, GT = S.box_mesh(0.05, 0.05, 0.005)
@@ -251,11 +253,19 @@ def test_solve_shapes_give_bit_identical_results():
         for _ in range(3):
             w.step(4, 16)
         results[shape] = w.get_state()
-    ref = results[(1, 1)]
+    ref, refg = results[(1, 1)], results[(2, 1)]
     assert np.abs(ref[0] - s0[0]).max() > 1e-5          # the bodies did move
+    general = np.zeros(len(ref[0]), bool)              # the bodies of the two-movable envs
+    for e in (5, 6, 7, 12):
+        general[2 * e:2 * e + 2] = True
     for shape, st in results.items():
-        for x, y in zip(st, ref):
-            np.testing.assert_array_equal(x, y, err_msg=str(shape))
+        for x, y, yg in zip(st, ref, refg):
+            np.testing.assert_array_equal(x[~general], y[~general], err_msg=str(shape))
+            np.testing.assert_array_equal(x[general], (y if shape[0] == 1 else yg)[general], err_msg=str(shape))
+            # the two forms sum in different float32 orders; over 12 substeps of two cubes in
+            # contact the difference grows to ~3e-5 (angular velocity); their per-substep parity
+            # with the FP64 oracle (1e-6) is checked in the gear and pile tests
+            np.testing.assert_allclose(y[general], yg[general], rtol=1e-2, atol=1e-4, err_msg=str(shape))
     w.set_solve_shape(0, 0)
     assert w.solve_shape() == (2, 1)                     # 19 envs: two per warp, one warp per block
     with pytest.raises(fw.FwError):
