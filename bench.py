@@ -33,13 +33,13 @@ NCU_TRAFFIC = {
     # 1000 M16 nut-bolt envs, FP32, the bench's launch shapes fixed (solve 2 envs per warp x
     # 1 warp, query 256 threads, reduction 4 warps), launches in its per-kernel timing pass
     # over the timed frames
-    "b305ab9c4b6046c4": {"map_kernel": 0.12e6, "query_kernel": 31.67e6, "reduce_kernel": 82.24e6,
-                         "solve_kernel": 132.94e6},
+    "8317c2056ae96a78": {"map_kernel": 0.12e6, "query_kernel": 33.17e6, "reduce_kernel": 82.35e6,
+                         "solve_kernel": 123.22e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "b305ab9c4b6046c4": {"map_kernel": 0.69e6, "query_kernel": 603.0e6, "reduce_kernel": 296.7e6,
-                         "solve_kernel": 3124.7e6},
+    "8317c2056ae96a78": {"map_kernel": 0.70e6, "query_kernel": 624.1e6, "reduce_kernel": 296.1e6,
+                         "solve_kernel": 3119.2e6},
 }
 
 FP32_LANES_PER_SM = 128
