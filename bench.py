@@ -545,7 +545,8 @@ def run_fw(args):
                "contact_statistics": {"contacts_per_pair": n_cont / max(n_pair, 1), "patches_per_pair": patches_per_pair,
                                       "paper_nut_bolt": {"contacts_per_pair": 195, "patches_per_pair": 53}},
                "solve_shape": list(w.solve_shape()), "autotuned": tuned is not None,
-               "detect_shape": {"query_threads": w.detect_shape()[0], "reduce_warps": w.detect_shape()[1]},
+               "detect_shape": {"query_threads": w.detect_shape()[0], "reduce_warps": w.detect_shape()[1],
+                                "query_cull": w.query_cull()},
                "graph_gap_ms_per_frame": total_ms / args.steps - (qry_ms + red_ms + sol_ms) * sim.n_substeps,
                "real_time_factor": (sim.dt / sim.n_substeps) / (total_ms / args.steps / sim.n_substeps * 1e-3) * n_env,
                "cpu_baseline": cpu, "clocks": clk.summary(),

@@ -457,6 +457,20 @@ FW_API fw_status fw_get_solve_shape(fw_world *w, int *envs_per_warp, int *warps_
  * fw_get_detect_shape returns the shape in use. */
 FW_API fw_status fw_set_detect_shape(fw_world *w, int query_threads, int reduce_warps);
 
+/* The narrow phase's cull (Sec. III-A; on by default): each warp's 32 consecutive sample
+ * points (the samples an asset is given sorted along a space-filling curve stay close)
+ * lie in a bounding sphere computed when the asset is added; when the sphere lies outside
+ * the other body's grid box, or that body's SDF at the sphere's centre exceeds the contact
+ * offset by more than the interpolated field can change over the radius (2.5 x radius, an
+ * interpolated distance field changing by at most sqrt(3) per unit length, plus FP16
+ * rounding, plus one voxel), none of the 32 can be a candidate and their lookups are
+ * skipped.  Dense SDF storage only.  The candidates, and
+ * everything after them, are the same with the cull on or off.  on: 1 or 0; errors:
+ * FW_ERR_ARG for other values.  fw_get_query_cull writes 1 or 0 to *on (the setting in use,
+ * which fw_autotune_detect may have changed). */
+FW_API fw_status fw_set_query_cull(fw_world *w, int on);
+FW_API fw_status fw_get_query_cull(fw_world *w, int *on);
+
 /* Test hook of failure detection (no counterpart in the paper): makes one of the kernels'
  * bounded device waits run out, as a lost copy or a missing block would.  what = 1: every
  * grid barrier of the pile sweep kernel waits for one more block than the launch has;
@@ -471,7 +485,10 @@ FW_API fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduc
  * query launches for each query size (with 4 reduction warps), and `trials` reduction
  * launches of the fastest query's candidates for each warp count, and keeps the fastest of
  * each (as fw_set_detect_shape would; the default is tried first and another shape must
- * beat it by more than 1%).  The body state is not touched; the contact buffer
+ * beat it by more than 1%).  Between the two it times the chosen query with the cull
+ * (fw_set_query_cull) on and off and turns it off only when that is faster by more than 1%.
+ * Every timed configuration first runs one untimed pass (its kernels' first launch loads
+ * their module).  The body state is not touched; the contact buffer
  * is left holding the contacts at the current poses.  Returns the chosen shape and the
  * summed time of one query and one reduction launch (ms); any output pointer may be NULL.
  * Synchronises. */

@@ -20,6 +20,7 @@ struct AssetHost {
     std::vector<float> S;   // samples, 3 per point
     double density = 0, mass = 0, com[3] = {0, 0, 0}, I[9] = {0};
     float4 *d_samples = nullptr;
+    float4 *d_spheres = nullptr;  // AssetDev::spheres
     float4 *d_tri = nullptr;      // 3 per triangle, asset frame
     bool has_sdf = false;
     float lo[3] = {0, 0, 0}, h = 0;
@@ -57,6 +58,7 @@ struct fw_world {
     int *d_counts = nullptr;
     float4 *d_scratch = nullptr;
     int2 *d_items = nullptr;     // detection work list (pair, batch)
+    unsigned *d_cull = nullptr;  // per item: its cull mask (SimParams::cull_mask)
     int *d_pair_item0 = nullptr;
     float4 *d_cand = nullptr;    // candidates of every item
     int *d_cand_count = nullptr;
@@ -76,6 +78,7 @@ struct fw_world {
     int lam_rows = 0;   // rows per env whose impulses the solve keeps in shared memory (0: every row)
     int query_threads = 0, reduce_warps = 0;   // detection launch shape (0: the defaults)
     int stall = 0;                             // fw_test_stall
+    int no_cull = 0;                           // fw_set_query_cull(0)
     // pile envs (fw_add_pile): one region per pile in each pile buffer, every region of the
     // same size (pile_pcap pairs, pile_icap items, pile_rcap rows)
     std::vector<PileDev> piles;
@@ -215,6 +218,7 @@ AssetDev asset_view(const AssetHost &A, bool fp16) {
     AssetDev g;
     memset(&g, 0, sizeof g);
     g.samples = A.d_samples;
+    g.spheres = A.d_spheres;
     g.ns = (int)(A.S.size() / 3);
     g.tri = A.d_tri;
     g.nt = (int)(A.T.size() / 3);
@@ -363,6 +367,7 @@ fw_status ensure_device(fw_world *w) {
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows);
     dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count); dfree(w->d_maps);
+    dfree(w->d_cull);
     w->n_items = 0;
     const int np = (int)w->pairs.size(), ne = (int)w->envs.size();
     const int cp = cap_pair(w);
@@ -406,6 +411,7 @@ fw_status ensure_device(fw_world *w) {
             CK(cudaMemcpy(w->d_items, items.data(), sizeof(int2) * w->n_items, cudaMemcpyHostToDevice));
             CK(cudaMalloc(&w->d_cand, sizeof(float4) * 2 * (size_t)kBatch * w->n_items));
             CK(cudaMalloc(&w->d_cand_count, sizeof(int) * w->n_items));
+            CK(cudaMalloc(&w->d_cull, sizeof(unsigned) * w->n_items));
         }
     }
     if (ne > 0) {
@@ -451,6 +457,8 @@ SimParams sim_params(const fw_world *w, float hs, int n_iters) {
     p.tri_iters = w->cfg.tri_iters;
     p.query_threads = w->query_threads;
     p.stall = w->stall;
+    p.cull = !w->no_cull;
+    p.cull_mask = w->d_cull;
     p.reduce_warps = w->reduce_warps;
     p.pair_item0 = w->d_pair_item0;
     p.n_items = w->n_items;
@@ -496,6 +504,7 @@ SimParams pile_params(const fw_world *w, float hs, int n_iters) {
     p.counts = w->d_pccounts;
     p.scratch = w->d_pscratch;
     p.rows = nullptr;   // the pile kernels take the pile rows (kPileRowF4 float4 each) as an argument
+    p.cull_mask = nullptr;   // no cull over the pile regions
     p.pile_counts = w->d_pcounts;
     p.item_range = w->d_pitem_range;
     p.pile_pcap = w->pile_pcap;
@@ -762,7 +771,7 @@ fw_status fw_destroy(fw_world *w) {
     drop_graph(w);
     diff_free(w);
     for (auto &A : w->assets) {
-        dfree(A.d_samples); dfree(A.d_tri); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
+        dfree(A.d_samples); dfree(A.d_spheres); dfree(A.d_tri); dfree(A.d_grid); dfree(A.d_cell32); dfree(A.d_cell16);
         dfree(A.d_brick);
     }
     dfree(w->d_assets);
@@ -770,6 +779,7 @@ fw_status fw_destroy(fw_world *w) {
     dfree(w->d_pos); dfree(w->d_quat); dfree(w->d_vel); dfree(w->d_ang);
     dfree(w->d_contacts); dfree(w->d_counts); dfree(w->d_scratch); dfree(w->d_rows); dfree(w->d_status);
     dfree(w->d_items); dfree(w->d_pair_item0); dfree(w->d_cand); dfree(w->d_cand_count); dfree(w->d_maps);
+    dfree(w->d_cull);
     pile_free(w);
     for (auto e : w->ev_pool) cudaEventDestroy(e);
     for (auto e : w->ev_used) cudaEventDestroy(e);
@@ -807,6 +817,29 @@ fw_status fw_add_mesh_asset(fw_world *w, const float *verts, int n_verts, const 
         for (int i = 0; i < n_samples; ++i) s4[i] = make_float4(A.S[3 * i], A.S[3 * i + 1], A.S[3 * i + 2], 0.f);
         CK(cudaMalloc(&A.d_samples, sizeof(float4) * n_samples));
         CK(cudaMemcpy(A.d_samples, s4.data(), sizeof(float4) * n_samples, cudaMemcpyHostToDevice));
+        // a bounding sphere per group of kCullGroup consecutive samples: the centre of the
+        // group's box, the largest distance to it (float64, then rounded up)
+        const int ng = (n_samples + kCullGroup - 1) / kCullGroup;
+        std::vector<float4> sp(ng);
+        for (int g = 0; g < ng; ++g) {
+            double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+            const int i1 = std::min(n_samples, (g + 1) * kCullGroup);
+            for (int i = g * kCullGroup; i < i1; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = std::min(mn[a], (double)A.S[3 * i + a]);
+                    mx[a] = std::max(mx[a], (double)A.S[3 * i + a]);
+                }
+            const float c[3] = {(float)(0.5 * (mn[0] + mx[0])), (float)(0.5 * (mn[1] + mx[1])), (float)(0.5 * (mn[2] + mx[2]))};
+            double r2 = 0.0;
+            for (int i = g * kCullGroup; i < i1; ++i) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) d2 += ((double)A.S[3 * i + a] - c[a]) * ((double)A.S[3 * i + a] - c[a]);
+                r2 = std::max(r2, d2);
+            }
+            sp[g] = make_float4(c[0], c[1], c[2], std::nextafter((float)std::sqrt(r2), INFINITY));
+        }
+        CK(cudaMalloc(&A.d_spheres, sizeof(float4) * ng));
+        CK(cudaMemcpy(A.d_spheres, sp.data(), sizeof(float4) * ng, cudaMemcpyHostToDevice));
     }
     {   // the faces, for the per-triangle contact generator
         std::vector<float4> t4(3 * (size_t)n_tris);
@@ -1652,6 +1685,20 @@ fw_status fw_test_stall(fw_world *w, int what) {
     return FW_OK;
 }
 
+fw_status fw_set_query_cull(fw_world *w, int on) {
+    if (!w) return FW_ERR_ARG;
+    if (on != 0 && on != 1) return fail(w, FW_ERR_ARG, "fw_set_query_cull: 0 or 1");
+    if (w->no_cull != !on) drop_graph(w);
+    w->no_cull = !on;
+    return FW_OK;
+}
+
+fw_status fw_get_query_cull(fw_world *w, int *on) {
+    if (!w || !on) return FW_ERR_ARG;
+    *on = w->no_cull ? 0 : 1;
+    return FW_OK;
+}
+
 fw_status fw_set_detect_shape(fw_world *w, int query_threads, int reduce_warps) {
     if (!w) return FW_ERR_ARG;
     if (!(query_threads == 0 || query_threads == 128 || query_threads == 256 || query_threads == 512) ||
@@ -1686,8 +1733,9 @@ fw_status fw_autotune_detect(fw_world *w, int trials, int *query_threads, int *r
         w->reduce_warps = rw;
         SimParams p = sim_params(w, w->cfg.dt, 0);
         const SimParams q = piles ? pile_params(w, w->cfg.dt, 0) : p;
-        CK(cudaEventRecord(e0, w->stream));
-        for (int t = 0; t < trials; ++t) {
+        // one untimed pass first: a kernel's first launch also loads its module
+        for (int t = -1; t < trials; ++t) {
+            if (t == 0) CK(cudaEventRecord(e0, w->stream));
             if (query) {
                 if (w->n_regular > 0) CK(launch_query(p, w->stream));
                 if (piles) CK(launch_query(q, w->stream));
@@ -1710,6 +1758,20 @@ fw_status fw_autotune_detect(fw_world *w, int trials, int *query_threads, int *r
         float ms = 0.f;
         if (st == FW_OK) st = time_phase(qt, 4, true, &ms);
         if (st == FW_OK && ms < bq * 0.99f) { bq = ms; best_q = qt; }   // the default first; 1% to beat it
+    }
+    // the cull (fw_set_query_cull) with the chosen query: kept unless the query runs faster
+    // without it (it costs the map kernel the groups' tests and saves nothing where few
+    // groups are far from the other body)
+    bool cull = true;
+    {
+        const int keep = w->no_cull;
+        float on_ms = 0.f, off_ms = 0.f;
+        w->no_cull = 0;
+        if (st == FW_OK) st = time_phase(best_q, 4, true, &on_ms);
+        w->no_cull = 1;
+        if (st == FW_OK) st = time_phase(best_q, 4, true, &off_ms);
+        cull = !(st == FW_OK && off_ms < on_ms * 0.99f);
+        w->no_cull = st == FW_OK ? (cull ? 0 : 1) : keep;
     }
     if (st == FW_OK) st = time_phase(best_q, 4, true, &bq);   // leave the best query's output
     for (int rw : {4, 2, 8}) {

@@ -160,6 +160,35 @@ __device__ __noinline__ void pair_map(const SimParams &p, const PairDev &P, cons
     M.pad_ = 0;
 }
 
+// Whether no sample of a group can be a candidate, from its bounding sphere sp (centre in
+// the frame of the pair's point body, radius): the sphere lies outside the grid box of the
+// SDF body gb on some axis (a sample outside the grid is no candidate), or the SDF at its
+// centre exceeds the cutoff by more than the interpolated field can change over the radius
+// (at most sqrt(3) per unit length for a distance field; 2.5 covers FP16 rounding), plus a
+// voxel.  Dense storage (a narrow band's clamped values do not bound the field).
+template <bool kHalf>
+__device__ __forceinline__ bool group_culled_as(const PairMap &M, const AssetDev &gb, float4 sp, float cutoff) {
+    const float u[3] = {__fmaf_rn(M.A[2], sp.z, __fmaf_rn(M.A[1], sp.y, __fmaf_rn(M.A[0], sp.x, M.f[0]))),
+                        __fmaf_rn(M.A[5], sp.z, __fmaf_rn(M.A[4], sp.y, __fmaf_rn(M.A[3], sp.x, M.f[1]))),
+                        __fmaf_rn(M.A[8], sp.z, __fmaf_rn(M.A[7], sp.y, __fmaf_rn(M.A[6], sp.x, M.f[2])))};
+    const float ru = sp.w * gb.inv_h * 1.0001f + 1e-3f;   // the radius in voxels, with a margin for the map's rounding
+    for (int a = 0; a < 3; ++a) {
+        const float g = u[a] + (float)M.c[a];             // the centre's grid coordinate
+        if (g + ru < 0.0f || g - ru > (float)(gb.dims[a] - 1)) return true;
+    }
+    int ci, cj, ck;
+    float fx, fy, fz;
+    const bool okx = cell_of(u[0], M.c[0], gb.dims[0], ci, fx);
+    const bool oky = cell_of(u[1], M.c[1], gb.dims[1], cj, fy);
+    const bool okz = cell_of(u[2], M.c[2], gb.dims[2], ck, fz);
+    const CellCorners c = sdf_cell_corners<kHalf, kStoreDense>(gb, ci, cj, ck);
+    const float phi = cell_value<kHalf>(gb, c, fx, fy, fz);
+    return okx && oky && okz && phi - 2.5f * sp.w > cutoff + gb.h;
+}
+__device__ __forceinline__ bool group_culled(const PairMap &M, const AssetDev &gb, float4 sp, float cutoff) {
+    return gb.cell16 ? group_culled_as<true>(M, gb, sp, cutoff) : group_culled_as<false>(M, gb, sp, cutoff);
+}
+
 // Every pair's map for the coming query (one thread per pair).
 __global__ void map_kernel(SimParams p) {
     const int pi = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,6 +198,59 @@ __global__ void map_kernel(SimParams p) {
     PairMap M;
     pair_map(p, P, p.assets[P.asset_b], M);
     p.maps[pi] = M;
+}
+
+// The maps as map_kernel forms them, and the cull masks of the pairs' items
+// (fw_set_query_cull; dense storage): a block takes kCullPairs pairs; its first warp forms
+// their maps, a lane per pair (an FP64 warp instruction occupies the FP64 pipe for the whole
+// warp however few lanes are active, so the maps are formed by as few warps as they are in
+// map_kernel), then warp w tests pair w's groups: bit g of an item's mask, from lane g, is set
+// when the item's samples 32 g .. 32 g + 31 can be no candidate (group_culled).
+constexpr int kCullPairs = 16;
+__global__ void __launch_bounds__(32 * kCullPairs, 2) map_cull_kernel(SimParams p) {
+    __shared__ PairMap maps[kCullPairs];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, p0 = blockIdx.x * kCullPairs;
+    if (warp == 0 && lane < kCullPairs) {
+        const int pi = p0 + lane;
+        if (pi < p.n_pairs) {
+            const PairDev P = p.pairs[pi];
+            PairMap M;
+            pair_map(p, P, p.assets[P.asset_b], M);
+            p.maps[pi] = M;
+            maps[lane] = M;
+        }
+    }
+    __syncthreads();
+    const int pi = p0 + warp;
+    if (pi >= p.n_pairs) return;   // the same on every lane of the warp
+    const PairDev P = p.pairs[pi];
+    const AssetDev ga = p.assets[P.asset_a], gb = p.assets[P.asset_b];
+    const int i0 = p.pair_item0[pi], i1 = p.pair_item0[pi + 1];
+    if (ga.spheres == nullptr || gb.brick != nullptr) {
+        for (int it = i0 + lane; it < i1; it += 32) p.cull_mask[it] = 0u;
+        return;
+    }
+    const PairMap M = maps[warp];
+    static_assert(kBatch / kCullGroup == 32, "one cull-mask bit per lane");
+    constexpr int kU = 4;   // items tested at once: their loads in flight together
+    for (int b0 = i0; b0 < i1; b0 += kU) {
+        float4 sp[kU];
+        bool has[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int g = (b0 + k - i0) * (kBatch / kCullGroup) + lane;
+            has[k] = b0 + k < i1 && g * kCullGroup < ga.ns;
+            sp[k] = has[k] ? __ldg(&ga.spheres[g]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        bool culled[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) culled[k] = has[k] && group_culled(M, gb, sp[k], p.contact_offset);
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, culled[k]);
+            if (lane == 0 && b0 + k < i1) p.cull_mask[b0 + k] = m;
+        }
+    }
 }
 
 // The narrow phase of one sample through the pair's map, in the grid's storage precision.
@@ -797,9 +879,10 @@ __device__ __forceinline__ void load_list(float4 *stage, const float *cands, int
 // spills) 2%.  Per-triangle generation keeps four (its 32 KB of face results per block).
 constexpr int query_min_blocks(bool tri, int thr) { return tri ? 1024 / thr : (thr <= 256 ? 5 : 1024 / thr); }
 
-template <bool kTri, int kStore, int kThr>
+template <bool kTri, int kStore, int kThr, bool kCull = false>
 __global__ void __launch_bounds__(kThr, query_min_blocks(kTri, kThr)) query_kernel(SimParams p) {
     static_assert(!kTri || kThr == kQueryThreads, "per-triangle generation runs 256 threads");
+    static_assert(!kCull || (!kTri && kStore == kStoreDense), "the cull is of dense per-sample queries");
     constexpr int NPER = kBatch / kThr, NW = kThr / 32;
     const int item = blockIdx.x;
     // pile launches cover every pile's item region; items past a pile's count do nothing
@@ -848,9 +931,18 @@ __global__ void __launch_bounds__(kThr, query_min_blocks(kTri, kThr)) query_kern
         PairXf X;
         load_pose(p, P.a, X.RA, X.pA);
         load_pose(p, P.b, X.RB, X.pB);
+        // the cull (fw_set_query_cull): the warp's kCullGroup consecutive samples of a round
+        // are skipped when map_cull_kernel set their bit in the item's mask (a separate
+        // instantiation: the skip's branches cost the loop time where nothing is culled)
+        static_assert(kCullGroup == 32 && kThr % 32 == 0, "a cull group is one warp's round");
+        const unsigned cmask = kCull ? __ldg(&p.cull_mask[item]) : 0u;
 #pragma unroll
         for (int u = 0; u < NPER; ++u) {
             const int i = base + u * kThr + tid;
+            if (kCull && ((cmask >> ((u * kThr) / kCullGroup + warp)) & 1u)) {   // the same on every lane
+                ok[u] = false;
+                continue;
+            }
             const float4 s = __ldg(&ga.samples[i < ga.ns ? i : ga.ns - 1]);
             ok[u] = query_sample<kStore>(M, X, gb, s, cutoff, xw[u], nw[u], ph[u]) && (i < ga.ns);
         }
@@ -1244,12 +1336,21 @@ cudaError_t prepare_detect(int max_patches) {
 
 cudaError_t launch_query(const SimParams &p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
+    // the cull (fw_set_query_cull) over dense storage, per-sample generation
+    const bool cull = p.cull && p.cull_mask && !p.sdf_bricks && p.contact_gen == 0;
     if (p.contact_gen == 0) {
-        map_kernel<<<(p.n_pairs + 127) / 128, 128, 0, s>>>(p);
+        if (cull) map_cull_kernel<<<(p.n_pairs + kCullPairs - 1) / kCullPairs, 32 * kCullPairs, 0, s>>>(p);
+        else map_kernel<<<(p.n_pairs + 127) / 128, 128, 0, s>>>(p);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     const int qt = p.query_threads > 0 ? p.query_threads : kQueryThreads;
+    if (cull) {
+        if (qt == 128) query_kernel<false, kStoreDense, 128, true><<<p.n_items, 128, 0, s>>>(p);
+        else if (qt == 512) query_kernel<false, kStoreDense, 512, true><<<p.n_items, 512, 0, s>>>(p);
+        else query_kernel<false, kStoreDense, 256, true><<<p.n_items, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     if (p.sdf_bricks) {
         if (p.contact_gen == 1) query_kernel<true, kStoreBricks, kQueryThreads><<<p.n_items, kQueryThreads, 0, s>>>(p);
         else if (qt == 128) query_kernel<false, kStoreBricks, 128><<<p.n_items, 128, 0, s>>>(p);

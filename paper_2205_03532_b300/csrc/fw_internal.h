@@ -51,7 +51,12 @@ struct AssetDev {
     int bdims[3];            // bricks per axis
     float band;              // metres
     float radius;            // bounding sphere about the asset origin: every vertex and sample
+    // per group of kCullGroup consecutive samples (the samples come sorted along a space-
+    // filling curve): a bounding sphere (centre in the asset frame, radius rounded up); NULL
+    // without samples
+    const float4 *spheres;
 };
+constexpr int kCullGroup = 32;   // samples per bounding sphere of the query's cull (one warp's)
 
 struct BodyProps {           // constant per body
     int type, asset;
@@ -176,6 +181,9 @@ struct SimParams {
     int broad_phase;                       // some env has several pairs: skip pairs far apart
     int query_threads;                     // per-sample query CTA size (128, 256, 512; 0: 256)
     int reduce_warps;                      // reduction warps per pair (2, 4, 8; 0: 4)
+    int cull;                              // the query's bounding-sphere cull of sample groups
+    unsigned *cull_mask;                   // per item: bit g set when its sample group g is culled
+                                           // (written by map_kernel; NULL: no cull)
     int stall;                             // test hook (fw_test_stall): 1 the pile sweeps' grid
                                            // barriers wait for one block too many, 2 the
                                            // solve's row stream issues no copy

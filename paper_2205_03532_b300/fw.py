@@ -30,7 +30,7 @@ ABI_FUNCTIONS = ["fw_config_default", "fw_create", "fw_destroy", "fw_add_mesh_as
                  "fw_record_rollout", "fw_replay_rollout", "fw_adjoint_rollout", "fw_step_fwd_ckpt",
                  "fw_step_bwd", "fw_get_tape",
                  "fw_set_body_params", "fw_get_detect_stats", "fw_get_counts", "fw_get_env_info", "fw_add_pile",
-                 "fw_get_pile_pairs", "fw_set_detect_shape", "fw_get_detect_shape", "fw_autotune_detect",
+                 "fw_get_pile_pairs", "fw_set_detect_shape", "fw_set_query_cull", "fw_get_query_cull", "fw_get_detect_shape", "fw_autotune_detect",
                  "fw_test_stall",
                  "fw_launches_per_step",
                  "fw_last_error", "fw_measure_l2_read"]
@@ -86,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         "fw_add_pile": (st, [vp, vp, i, i, i, C.POINTER(i)]),
         "fw_get_pile_pairs": (st, [vp, i, vp, vp, i, C.POINTER(i)]),
         "fw_set_detect_shape": (st, [vp, i, i]),
+        "fw_set_query_cull": (st, [vp, i]),
+        "fw_get_query_cull": (st, [vp, C.POINTER(i)]),
         "fw_test_stall": (st, [vp, i]),
         "fw_get_detect_shape": (st, [vp, C.POINTER(i), C.POINTER(i)]),
         "fw_autotune_detect": (st, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_float)]),
@@ -396,6 +398,16 @@ class World:
 
     def set_detect_shape(self, query_threads: int = 0, reduce_warps: int = 0):
         self._check(self.lib.fw_set_detect_shape(self.h, query_threads, reduce_warps))
+
+    def set_query_cull(self, on: bool):
+        """The narrow phase's bounding-sphere cull of sample groups (on by default; the
+        results are the same either way)."""
+        self._check(self.lib.fw_set_query_cull(self.h, 1 if on else 0))
+
+    def query_cull(self) -> bool:
+        v = C.c_int()
+        self._check(self.lib.fw_get_query_cull(self.h, C.byref(v)))
+        return bool(v.value)
 
     def detect_shape(self):
         a, b = C.c_int(), C.c_int()
