@@ -32,14 +32,14 @@ sys.path.insert(0, ROOT)
 NCU_TRAFFIC = {
     # 1000 M16 nut-bolt envs, FP32, the bench's launch shapes fixed (solve 2 envs per warp x
     # 1 warp, query 256 threads, reduction 4 warps), launches in its per-kernel timing pass
-    # over the timed frames
-    "8317c2056ae96a78": {"map_kernel": 0.12e6, "query_kernel": 33.17e6, "reduce_kernel": 82.35e6,
-                         "solve_kernel": 123.22e6},
+    # over the timed frames, the query's cull off
+    "80602d678449af17": {"map_kernel": 0.12e6, "query_kernel": 35.85e6, "reduce_kernel": 86.24e6,
+                         "solve_kernel": 126.06e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "8317c2056ae96a78": {"map_kernel": 0.70e6, "query_kernel": 624.1e6, "reduce_kernel": 296.1e6,
-                         "solve_kernel": 3119.2e6},
+    "80602d678449af17": {"map_kernel": 0.74e6, "query_kernel": 632.6e6, "reduce_kernel": 303.6e6,
+                         "solve_kernel": 3143.3e6},
 }
 
 FP32_LANES_PER_SM = 128
@@ -379,6 +379,8 @@ def run_fw(args):
     if shape == [0, 0] and not args.no_autotune:
         tuned = w.autotune_solve(sim.n_substeps, sim.n_iters, trials=6)
         detect_tuned = w.autotune_detect(trials=6)
+    if args.query_cull != "auto":   # after the autotuner, which may have changed it
+        w.set_query_cull(args.query_cull == "on")
     with torch.cuda.stream(stream):
         for _ in range(args.warmup - pre):
             one_step()
@@ -439,9 +441,11 @@ def run_fw(args):
     sol_flops = n_cont * (SOLVE_FLOPS_PER_CONTACT_SWEEP * sim.n_iters + SOLVE_FLOPS_PER_CONTACT_PREP)
     alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     src = _src_hash()
-    # the table was taken on the default workload only (1000 M16 envs, FP32)
+    # the table was taken on the default workload only (1000 M16 envs, FP32), with the
+    # query's cull off (the autotuner's choice there; the cull runs other kernels)
     default_run = (args.workload == "nut_bolt" and not fp16 and sc.n_envs == 1000 and not tri_mode
-                   and args.sdf_band == 0 and args.solver == "gs" and args.substeps == 0 and args.iters == 0)
+                   and args.sdf_band == 0 and args.solver == "gs" and args.substeps == 0 and args.iters == 0
+                   and not w.query_cull())
     traffic = NCU_TRAFFIC.get(src, {}) if default_run else {}
     l2_traffic = NCU_L2.get(src, {}) if default_run else {}
     l2_gbs = fw.measure_l2_read(dev)   # untimed: the L2 roofline's denominator on this device
@@ -810,6 +814,9 @@ def main():
     ap.add_argument("--pile-body", default="nut", choices=["nut", "torus", "bowl"],
                     help="pile1024: the bodies of the pile (the paper's Nuts, Toruses and Bowls scenes)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default solve shape")
+    ap.add_argument("--query-cull", choices=["auto", "on", "off"], default="auto",
+                    help="the narrow phase's sample-group cull: the detection autotuner's choice (auto; on "
+                         "without the autotuner), or forced on / off")
     ap.add_argument("--contact-gen", default="samples", choices=["samples", "triangles"],
                     help="samples: SDF query of the nut's surface samples; triangles: one contact per "
                          "face of the nut's mesh by local minimisation over the face")
