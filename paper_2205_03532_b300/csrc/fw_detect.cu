@@ -548,6 +548,39 @@ __device__ __forceinline__ int depth_rank(const unsigned *kord, const short *cl,
     return lt;
 }
 
+// The same depth order by sorting: the m pairs (kord[i], cl[i]) are sorted in place,
+// ascending by depth then candidate (a bitonic network over the next power of two, padded
+// with keys after every real one), so that cl[r] is the candidate of depth rank r.  The keys
+// are distinct (one per candidate), so the order is the one depth_rank gives.  m <= kBatch;
+// executed by all 32 * kW threads, ends with a block barrier.
+constexpr int kRankSort = 128;   // above this many unassigned candidates, sort instead of count
+template <int kW>
+__device__ void depth_sort(unsigned *kord, short *cl, int m) {
+    constexpr int NT = 32 * kW;
+    const int tid = threadIdx.x;
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = m + tid; i < P; i += NT) {   // pads: above any finite depth and any candidate
+        kord[i] = 0xFFFFFFFFu;
+        cl[i] = (short)0x7FFF;
+    }
+    bsync<kW>();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < (P >> 1); t += NT) {
+                const int i = 2 * t - (t & (j - 1)), l = i + j;   // the pair (i, i + j), i's bit j clear
+                const unsigned ka = kord[i], kb = kord[l];
+                const short ca = cl[i], cb = cl[l];
+                const bool gt = ka > kb || (ka == kb && ca > cb);
+                if (gt == ((i & k) == 0)) {   // out of this block's direction: swap
+                    kord[i] = kb; kord[l] = ka;
+                    cl[i] = cb; cl[l] = ca;
+                }
+            }
+            bsync<kW>();
+        }
+}
+
 __device__ __forceinline__ void copy_patch(const PatchSm &S, int NP, int from, int to) {
     S.pn4[to] = S.pn4[from];
     for (int k = 0; k < 3; ++k) {
@@ -728,18 +761,33 @@ __device__ void reduce_batch(const PatchSm &S, int NP, const float4 *cd, int nc,
         if (won) scratch_put(scr, id, cpos(cd, c), cphi(cd, c), cnrm(cd, c));
     }
     const int m = *S.nun;
-    int rk[kPer], rc[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int i = tid + u * NT;
-        rk[u] = i < m ? depth_rank(S.kord, S.cl, m, i) : -1;
-        rc[u] = i < m ? S.cl[i] : 0;
-    }
-    bsync<kW>();
     int *order = reinterpret_cast<int *>(S.kord);   // the depth order replaces the keys
+    if (m > kRankSort) {   // many: sort (O(m log^2 m) work against the count's O(m^2))
+        depth_sort<kW>(S.kord, S.cl, m);
+        int oc[kPer];
 #pragma unroll
-    for (int u = 0; u < kPer; ++u)
-        if (rk[u] >= 0) order[rk[u]] = rc[u];
+        for (int u = 0; u < kPer; ++u) {
+            const int i = tid + u * NT;
+            oc[u] = i < m ? S.cl[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {   // writes kord, which no thread reads any more
+            const int i = tid + u * NT;
+            if (i < m) order[i] = oc[u];
+        }
+    } else {
+        int rk[kPer], rc[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int i = tid + u * NT;
+            rk[u] = i < m ? depth_rank(S.kord, S.cl, m, i) : -1;
+            rc[u] = i < m ? S.cl[i] : 0;
+        }
+        bsync<kW>();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u)
+            if (rk[u] >= 0) order[rk[u]] = rc[u];
+    }
     bsync<kW>();
     // ---- rounds of FindDeepest, BinReduce, AddPatch
     int pos = 0, ns_prev = 0;
