@@ -598,6 +598,12 @@ def run_pile_env(args):
         for _ in range(args.settle):
             w.step(4, 16)
     w.sync()
+    # the detection autotuner on the settled pile (untimed set-up: query and reduction
+    # shapes, and whether the sample-group cull pays)
+    if not args.no_autotune:
+        w.autotune_detect(trials=6)
+    if args.query_cull != "auto":
+        w.set_query_cull(args.query_cull == "on")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
     n_env, n_body, _ = w.counts()
     with torch.cuda.stream(stream):
@@ -714,6 +720,8 @@ def run_pile_env(args):
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "kernels": kernels,
                "phase_ms_per_frame": {"detect": det_ms * sub, "reduce": red_ms * sub, "solve": sol_ms * sub},
+               "detect_shape": {"query_threads": w.detect_shape()[0], "reduce_warps": w.detect_shape()[1],
+                                "query_cull": w.query_cull()},
                "pairs": n_pairs, "pairs_with_contacts": int((colours >= 0).sum()),
                "colours": int(colours.max() + 1) if n_pairs else 0,
                "candidates": n_cand, "contacts": n_cont,

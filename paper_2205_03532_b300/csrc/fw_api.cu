@@ -88,6 +88,7 @@ struct fw_world {
     PileDev *d_piles = nullptr;
     PairDev *d_ppairs = nullptr;
     int2 *d_pitems = nullptr, *d_pitem_range = nullptr, *d_pcounts = nullptr;
+    unsigned *d_pcull = nullptr;   // per pile item: its cull mask (SimParams::cull_mask)
     DContact *d_pcontacts = nullptr;
     int *d_pccounts = nullptr;   // contacts per pile pair
     float4 *d_pscratch = nullptr, *d_pcand = nullptr;
@@ -276,7 +277,7 @@ fw_status pile_pair_count(fw_world *w, int pile, int *n) {
 void pile_free(fw_world *w) {
     dfree(w->d_piles); dfree(w->d_ppairs); dfree(w->d_pitems); dfree(w->d_pitem_range); dfree(w->d_pcounts);
     dfree(w->d_pcontacts); dfree(w->d_pccounts); dfree(w->d_pscratch); dfree(w->d_pcand); dfree(w->d_pcand_count);
-    dfree(w->d_pmaps); dfree(w->d_prows);
+    dfree(w->d_pmaps); dfree(w->d_prows); dfree(w->d_pcull);
     dfree(w->pmem.color); dfree(w->pmem.ab); dfree(w->pmem.rr); dfree(w->pmem.order); dfree(w->pmem.cstart);
     dfree(w->pmem.ncol); dfree(w->pmem.bv); dfree(w->pmem.bw); dfree(w->pmem.bcom); dfree(w->pmem.binv); dfree(w->pmem.bar);
 }
@@ -325,6 +326,7 @@ fw_status pile_alloc(fw_world *w) {
     CK(cudaMalloc(&w->d_pcontacts, sizeof(DContact) * np * cap_pair(w)));
     CK(cudaMalloc(&w->d_pscratch, sizeof(float4) * np * w->pile_stride));
     CK(cudaMalloc(&w->d_pitems, sizeof(int2) * ni));
+    CK(cudaMalloc(&w->d_pcull, sizeof(unsigned) * ni));
     CK(cudaMalloc(&w->d_pcand, sizeof(float4) * 2 * (size_t)kBatch * ni));
     CK(cudaMalloc(&w->d_pcand_count, sizeof(int) * ni));
     CK(cudaMalloc(&w->d_pcounts, sizeof(int2) * n));
@@ -504,7 +506,8 @@ SimParams pile_params(const fw_world *w, float hs, int n_iters) {
     p.counts = w->d_pccounts;
     p.scratch = w->d_pscratch;
     p.rows = nullptr;   // the pile kernels take the pile rows (kPileRowF4 float4 each) as an argument
-    p.cull_mask = nullptr;   // no cull over the pile regions
+    p.cull = !w->no_cull;
+    p.cull_mask = w->d_pcull;
     p.pile_counts = w->d_pcounts;
     p.item_range = w->d_pitem_range;
     p.pile_pcap = w->pile_pcap;

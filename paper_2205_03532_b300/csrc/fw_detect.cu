@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32 * kCullPairs, 2) map_cull_kernel(SimParams 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, p0 = blockIdx.x * kCullPairs;
     if (warp == 0 && lane < kCullPairs) {
         const int pi = p0 + lane;
-        if (pi < p.n_pairs) {
+        if (pi < p.n_pairs && !(p.pile_counts && pi % p.pile_pcap >= p.pile_counts[pi / p.pile_pcap].x)) {
             const PairDev P = p.pairs[pi];
             PairMap M;
             pair_map(p, P, p.assets[P.asset_b], M);
@@ -223,9 +223,17 @@ __global__ void __launch_bounds__(32 * kCullPairs, 2) map_cull_kernel(SimParams 
     __syncthreads();
     const int pi = p0 + warp;
     if (pi >= p.n_pairs) return;   // the same on every lane of the warp
+    if (p.pile_counts && pi % p.pile_pcap >= p.pile_counts[pi / p.pile_pcap].x) return;   // past a pile's pairs
     const PairDev P = p.pairs[pi];
     const AssetDev ga = p.assets[P.asset_a], gb = p.assets[P.asset_b];
-    const int i0 = p.pair_item0[pi], i1 = p.pair_item0[pi + 1];
+    if (p.broad_phase) {   // the query skips the pair's items (query_kernel): no mask is read
+        const V3 dp = ld3(p.pos + 3 * P.a) - ld3(p.pos + 3 * P.b);
+        const float lim = ga.radius + gb.radius + p.contact_offset + 2.0f * gb.h;
+        if (dot(dp, dp) > lim * lim) return;
+    }
+    // the pair's items: batch it - i0 of its samples is item it
+    const int i0 = p.item_range ? p.item_range[pi].x : p.pair_item0[pi];
+    const int i1 = p.item_range ? p.item_range[pi].y : p.pair_item0[pi + 1];
     if (ga.spheres == nullptr || gb.brick != nullptr) {
         for (int it = i0 + lane; it < i1; it += 32) p.cull_mask[it] = 0u;
         return;

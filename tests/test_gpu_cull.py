@@ -2,7 +2,8 @@
 consecutive samples is skipped only when none of them can be a candidate, so the
 candidates, the contacts and the states after them are the same bit for bit with the cull
 on and off -- on the peg, the nut-bolt pair, the mixed nut-bolt sizes, the gear train
-(FP16 SDFs) and the 7-nut piles (bodies apart, coming together).
+(FP16 SDFs), the 7-nut piles (bodies apart, coming together) and the pile envs (nuts,
+toruses and bowls heaped on a plate; pair lists found on the device).
 """
 import numpy as np
 import pytest
@@ -17,6 +18,11 @@ SCENES = {
     "mixed": lambda: (S.mixed_nut_bolt_scene(n_envs=8, seed=3), True),
     "gears": lambda: (S.gear_scene(n_envs=6, seed=4), True),
     "pile": lambda: (S.pile_scene(n_envs=3, seed=5, n_nuts=7), False),
+    "pile_env_nut": lambda: (S.nut_pile_env_scene(64, seed=1, mode="heap"), False),
+    "pile_env_torus": lambda: (S.pile_env_scene("torus", 16, seed=3, mode="heap", n_samples=3000, sdf_res=64,
+                                                plate_sdf_res=64), False),
+    "pile_env_bowl": lambda: (S.pile_env_scene("bowl", 16, seed=3, mode="heap", n_samples=3000, sdf_res=128,
+                                               plate_sdf_res=64), False),
 }
 
 
