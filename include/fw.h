@@ -486,7 +486,8 @@ FW_API fw_status fw_get_detect_shape(fw_world *w, int *query_threads, int *reduc
  * launches of the fastest query's candidates for each warp count, and keeps the fastest of
  * each (as fw_set_detect_shape would; the default is tried first and another shape must
  * beat it by more than 1%).  Between the two it times the chosen query with the cull
- * (fw_set_query_cull) on and off and turns it off only when that is faster by more than 1%.
+ * (fw_set_query_cull) on and off and keeps it on only when that is faster by more than 10%
+ * (what the cull saves can shrink as bodies come together; its cost does not).
  * Every timed configuration first runs one untimed pass (its kernels' first launch loads
  * their module).  The body state is not touched; the contact buffer
  * is left holding the contacts at the current poses.  Returns the chosen shape and the
