@@ -1012,14 +1012,21 @@ __global__ void __launch_bounds__(kThr, query_min_blocks(kTri, kThr)) query_kern
         if (lane == 0) cnt[u * NW + warp] = __popc(m[u]);
     }
     __syncthreads();
-    int total = 0, off[NPER];
+    // offsets: an exclusive scan of the NPER * NW = 32 counts in (round, warp) order, by
+    // every warp for itself (lane l holds count l; shuffles, no further barrier)
+    static_assert(NPER * NW == 32, "one count per lane");
+    const int cl = cnt[lane];
+    int incl = cl;
 #pragma unroll
-    for (int u = 0; u < NPER; ++u) {
-        for (int w = 0; w < NW; ++w) {
-            if (w == warp) off[u] = total;
-            total += cnt[u * NW + w];
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
+    const int excl = incl - cl;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int off[NPER];
+#pragma unroll
+    for (int u = 0; u < NPER; ++u) off[u] = __shfl_sync(0xffffffffu, excl, u * NW + warp);
     float4 *out = p.cand + (size_t)item * 2 * kBatch;
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
