@@ -33,13 +33,13 @@ NCU_TRAFFIC = {
     # 1000 M16 nut-bolt envs, FP32, the bench's launch shapes fixed (solve 2 envs per warp x
     # 1 warp, query 256 threads, reduction 4 warps), launches in its per-kernel timing pass
     # over the timed frames, the query's cull off
-    "1579dedc3578250e": {"map_kernel": 0.12e6, "query_kernel": 36.03e6, "reduce_kernel": 86.62e6,
-                         "solve_kernel": 137.66e6},
+    "0a232dc5237be478": {"map_kernel": 0.12e6, "query_kernel": 34.26e6, "reduce_kernel": 86.76e6,
+                         "solve_kernel": 127.13e6},
 }
 # per-launch L2 traffic (lts__t_bytes.sum, one ncu pass) on the same workload, same keying
 NCU_L2 = {
-    "1579dedc3578250e": {"map_kernel": 0.77e6, "query_kernel": 632.4e6, "reduce_kernel": 307.8e6,
-                         "solve_kernel": 3150.1e6},
+    "0a232dc5237be478": {"map_kernel": 0.74e6, "query_kernel": 603.9e6, "reduce_kernel": 307.2e6,
+                         "solve_kernel": 3144.2e6},
 }
 
 FP32_LANES_PER_SM = 128
