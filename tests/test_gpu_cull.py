@@ -56,3 +56,27 @@ def test_cull_switch_refuses_other_values():
     with pytest.raises(fw.FwError):
         w._check(w.lib.fw_set_query_cull(w.h, 2))
     w.close()
+
+
+def test_cull_setting_reads_back_and_the_autotuner_changes_no_contact():
+    """fw_get_query_cull reports the setting in use (on by default); the detection
+    autotuner may turn it either way, and the contacts it leaves are those of the setting
+    before it"""
+    from paper_2205_03532_b300 import fw
+    sc = S.nut_bolt_scene(n_envs=8, seed=2)
+    w = fw.world_from_scene(sc)
+    assert w.query_cull() is True
+    w.set_query_cull(False)
+    assert w.query_cull() is False
+    w.set_query_cull(True)
+    w.step(sc.sim.n_substeps, sc.sim.n_iters)
+    w.collide()
+    before = [w.get_contacts(e).tobytes() for e in range(w.counts()[0])]
+    w.autotune_detect(trials=2)
+    assert isinstance(w.query_cull(), bool)
+    after = [w.get_contacts(e).tobytes() for e in range(w.counts()[0])]
+    assert before == after
+    w.set_query_cull(not w.query_cull())
+    w.collide()
+    assert [w.get_contacts(e).tobytes() for e in range(w.counts()[0])] == before
+    w.close()
